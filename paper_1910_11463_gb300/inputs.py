@@ -1,0 +1,205 @@
+"""Seeded synthetic inputs for the S_N transport problems: PRNG, angular
+quadrature, meshes and cross sections.
+
+This module is the problem *definition* only.  It holds no arithmetic of the
+method (no discretisation, no multigrid, no source iteration): it produces the
+arrays that both the CUDA path and the CPU oracle take as inputs, so that both
+see bit-identical data.
+
+* PRNG: SplitMix64 (Steele, Lea & Flood, "Fast splittable pseudorandom number
+  generators", OOPSLA 2014), u = (x >> 11) * 2^-53.
+* Quadrature: level-symmetric S_N sets (Lewis & Miller tables), the angular
+  quadrature of Eq. (angular_quad), phi = sum_m w_m psi_m, weights summing to
+  4*pi.  The paper itself used a square Chebyshev-Legendre S4 set (Sec. 4);
+  the workloads here use level-symmetric S2/S4/S8.
+* Meshes: the unit cube split into n^3 axis-aligned hexahedra (Q1 DG, 8 DOFs
+  per element, DOF = 8*e + a, e = ix + n*(iy + n*iz), a = ax + 2*ay + 4*az).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_C1 = np.uint64(0xBF58476D1CE4E5B9)
+_C2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64_stream(seed: int, count: int) -> np.ndarray:
+    """The first `count` outputs of SplitMix64 started at state `seed`."""
+    k = np.arange(1, count + 1, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed) + k * _GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * _C1
+        z = (z ^ (z >> np.uint64(27))) * _C2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform01(seed: int, count: int) -> np.ndarray:
+    """Doubles in [0, 1) with 53 random bits each, drawn in order."""
+    z = splitmix64_stream(seed, count)
+    return (z >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+
+
+# ---------------------------------------------------------------------------
+# Level-symmetric quadrature
+# ---------------------------------------------------------------------------
+
+_LS_MU1 = {2: 1.0 / math.sqrt(3.0), 4: 0.3500212, 8: math.sqrt(1.0 / 21.0)}
+
+
+def level_symmetric(order: int):
+    """Level-symmetric S_N set for N in {2, 4, 8}.
+
+    Returns (omega[M,3], w[M]) with M = N(N+2).  Octants are ordered by sign
+    (x fastest, '+' first); inside an octant the points are the index triples
+    (i, j, k), i + j + k = N/2 + 2, in lexicographic order, with direction
+    cosines (mu_i, mu_j, mu_k), mu_i^2 = mu_1^2 + (i-1) 2 (1 - 3 mu_1^2)/(N-2).
+    Weights: S2, S4 equal; S8 from the per-octant moment conditions
+    sum w = 1, sum w mu^4 = 1/5, sum w mu^6 = 1/7 over the three point classes.
+    The weights are scaled to sum to 4*pi.
+    """
+    if order not in _LS_MU1:
+        raise ValueError("level_symmetric: order must be 2, 4 or 8")
+    n_half = order // 2
+    mu1 = _LS_MU1[order]
+    if order == 2:
+        mus = [mu1]
+    else:
+        step = 2.0 * (1.0 - 3.0 * mu1 * mu1) / (order - 2)
+        mus = [math.sqrt(mu1 * mu1 + i * step) for i in range(n_half)]
+    triples = [(i, j, k)
+               for i in range(1, n_half + 1)
+               for j in range(1, n_half + 1)
+               for k in range(1, n_half + 1) if i + j + k == n_half + 2]
+    if order == 8:
+        classes = {(1, 1, 4): 0, (1, 2, 3): 1, (2, 2, 2): 2}
+        # per-octant moment system: rows = moments 0, 4, 6 of mu_x
+        A = np.zeros((3, 3))
+        for t in triples:
+            c = classes[tuple(sorted(t))]
+            mx = mus[t[0] - 1]
+            A[0, c] += 1.0
+            A[1, c] += mx ** 4
+            A[2, c] += mx ** 6
+        wc = np.linalg.solve(A, np.array([1.0, 0.2, 1.0 / 7.0]))
+        w_oct = [wc[classes[tuple(sorted(t))]] for t in triples]
+    else:
+        w_oct = [1.0 / len(triples)] * len(triples)
+    omega, w = [], []
+    scale = 4.0 * math.pi / 8.0
+    for octant in range(8):
+        sx = -1.0 if octant & 1 else 1.0
+        sy = -1.0 if octant & 2 else 1.0
+        sz = -1.0 if octant & 4 else 1.0
+        for t, wt in zip(triples, w_oct):
+            omega.append((sx * mus[t[0] - 1], sy * mus[t[1] - 1], sz * mus[t[2] - 1]))
+            w.append(wt * scale)
+    return np.ascontiguousarray(np.array(omega, dtype=np.float64)), np.array(w, dtype=np.float64)
+
+
+# ---------------------------------------------------------------------------
+# Problems
+# ---------------------------------------------------------------------------
+
+@dataclass
+class HexProblem:
+    """Unit cube, n^3 hexahedra, Q1 upwind DG, one energy group."""
+    name: str
+    n: int
+    omega: np.ndarray          # (M, 3) direction cosines
+    w: np.ndarray              # (M,) quadrature weights, sum 4*pi
+    sigma_t: np.ndarray        # (E,) per element
+    sigma_s: np.ndarray        # (E,)
+    q: np.ndarray              # (E,) isotropic source strength (divided by 4*pi in the equation)
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def E(self) -> int:
+        return self.n ** 3
+
+    @property
+    def N(self) -> int:
+        return 8 * self.n ** 3
+
+    @property
+    def M(self) -> int:
+        return self.omega.shape[0]
+
+
+def element_index_grid(n: int):
+    """(ix, iy, iz) of every element, e = ix + n*(iy + n*iz)."""
+    e = np.arange(n ** 3)
+    return e % n, (e // n) % n, e // (n * n)
+
+
+def hex_uniform(n: int, order: int, sigma_t: float, ratio: float, q: float = 1.0,
+                name: str = "hex_uniform") -> HexProblem:
+    omega, w = level_symmetric(order)
+    E = n ** 3
+    st = np.full(E, float(sigma_t))
+    return HexProblem(name, n, omega, w, st, st * ratio, np.full(E, float(q)),
+                      {"order": order, "sigma": "uniform", "ratio": ratio})
+
+
+def hex_random(n: int, order: int, ratio: float, seed: int = 1, lo: float = 0.5,
+               hi: float = 2.0, log_uniform: bool = False, source_block=None,
+               name: str = "hex_random") -> HexProblem:
+    """sigma_t drawn per element in element order: U[lo,hi] -> lo + (hi-lo) u,
+    log-U[lo,hi] -> 10^(log10 lo + (log10 hi - log10 lo) u); sigma_s = ratio*sigma_t.
+    source_block = (a, b): q = 1 on elements with all indices in [a, b), else 0."""
+    omega, w = level_symmetric(order)
+    E = n ** 3
+    u = uniform01(seed, E)
+    if log_uniform:
+        a, b = math.log10(lo), math.log10(hi)
+        st = 10.0 ** (a + (b - a) * u)
+    else:
+        st = lo + (hi - lo) * u
+    if source_block is None:
+        q = np.ones(E)
+    else:
+        ix, iy, iz = element_index_grid(n)
+        a, b = source_block
+        inside = (ix >= a) & (ix < b) & (iy >= a) & (iy < b) & (iz >= a) & (iz < b)
+        q = inside.astype(np.float64)
+    return HexProblem(name, n, omega, w, st, st * ratio, q,
+                      {"order": order, "seed": seed, "ratio": ratio,
+                       "sigma": ("log-U" if log_uniform else "U") + f"[{lo},{hi}]"})
+
+
+def detector_elements(n: int, lo: int = 0, hi: int = 4) -> np.ndarray:
+    """Elements with all indices in [lo, hi) (a corner block)."""
+    ix, iy, iz = element_index_grid(n)
+    return ((ix >= lo) & (ix < hi) & (iy >= lo) & (iy < hi) & (iz >= lo) & (iz < hi))
+
+
+def config(name: str) -> HexProblem:
+    """The named synthetic workloads.
+
+    hex8_s2     : 8^3 hex (4,096 DOFs/direction), S2 (8 directions), sigma_t = 1,
+                  sigma_s = 0.5, q = 1, vacuum boundaries.
+    hex32_s4    : 32^3 hex (262,144 DOFs/direction), S4 (24 directions),
+                  sigma_t ~ U[0.5, 2] per element (seed 1), sigma_s = 0.8 sigma_t, q = 1.
+    hex24_s4_adj: 24^3 hex (110,592 DOFs/direction), S4, sigma_t ~ U[0.5, 2],
+                  sigma_s = 0.7 sigma_t, q = 1 in the central 8^3 block.
+    hex64_s8    : 64^3 hex (2,097,152 DOFs/direction), S8 (80 directions),
+                  sigma_t ~ log-U[0.1, 100], sigma_s = 0.95 sigma_t, q = 1.
+    """
+    if name == "hex8_s2":
+        return hex_uniform(8, 2, 1.0, 0.5, 1.0, name)
+    if name == "hex32_s4":
+        return hex_random(32, 4, 0.8, seed=1, name=name)
+    if name == "hex24_s4_adj":
+        return hex_random(24, 4, 0.7, seed=1, source_block=(8, 16), name=name)
+    if name == "hex64_s8":
+        return hex_random(64, 8, 0.95, seed=1, lo=0.1, hi=100.0, log_uniform=True, name=name)
+    raise KeyError(name)
+
+
+def small_hex(n: int, order: int = 2, seed: int = 7, ratio: float = 0.5) -> HexProblem:
+    """Small seeded problem for parity tests (spans several tiles, ragged sizes)."""
+    return hex_random(n, order, ratio, seed=seed, name=f"hex{n}_s{order}_seed{seed}")

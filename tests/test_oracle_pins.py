@@ -1,0 +1,361 @@
+"""Pins of the CPU oracle against facts the paper and the mathematics fix.
+
+Nothing here compares the oracle with itself: each check is a closed form, an
+invariant, a library routine on a special case, or a direct solve of the
+paper's block system (Sec. 3)."""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spl
+
+from oracle import oracle as O
+from paper_1910_11463_gb300 import inputs as I
+from tests._mesh import csr_dense, hex_nodes, q1_l2_error
+
+
+# ---------------------------------------------------------------------------
+# Quadrature (Eq. angular_quad): weights sum to the measure of the sphere
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("order", [2, 4, 8])
+def test_level_symmetric_moments(order):
+    om, w = I.level_symmetric(order)
+    assert om.shape == (order * (order + 2), 3)
+    assert abs(w.sum() - 4 * math.pi) < 1e-13
+    np.testing.assert_allclose(np.linalg.norm(om, axis=1), 1.0, atol=1e-14)
+    for d in range(3):
+        assert abs(np.dot(w, om[:, d])) < 1e-13                      # odd moments vanish
+        assert abs(np.dot(w, om[:, d] ** 3)) < 1e-13
+        assert abs(np.dot(w, om[:, d] ** 2) - 4 * math.pi / 3) < 1e-12  # int mu^2 = 4 pi / 3
+    assert abs(np.dot(w, om[:, 0] * om[:, 1])) < 1e-13
+    if order == 8:   # S8 weights integrate mu^4 and mu^6 exactly
+        assert abs(np.dot(w, om[:, 0] ** 4) - 4 * math.pi / 5) < 1e-12
+        assert abs(np.dot(w, om[:, 0] ** 6) - 4 * math.pi / 7) < 1e-12
+        np.testing.assert_allclose(sorted(set(np.round(w / (4 * math.pi / 8), 7))),
+                                   [0.0907407, 0.0925926, 0.1209877], atol=1e-7)
+
+
+def test_splitmix64_reference_values():
+    # SplitMix64 from state 0: published first outputs of the generator
+    z = I.splitmix64_stream(0, 3)
+    assert [int(v) for v in z] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+# ---------------------------------------------------------------------------
+# DG assembly (Eq. weak_form_transport): the discrete space holds every
+# trilinear function, and its advection image, so upwind DG must reproduce a
+# trilinear exact solution to round-off.
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dirn", [0, 7, 13, 22])
+def test_dg_reproduces_trilinear_solution(dirn):
+    n = 3
+    rng = np.random.default_rng(dirn)
+    om = I.level_symmetric(4)[0][dirn]
+    st = 0.5 + rng.random(n ** 3)
+    c = rng.standard_normal(8)
+    X = hex_nodes(n)
+    x, y, z = X[:, 0], X[:, 1], X[:, 2]
+    psi = c[0] + c[1] * x + c[2] * y + c[3] * z + c[4] * x * y + c[5] * y * z + c[6] * x * z + c[7] * x * y * z
+    gx = c[1] + c[4] * y + c[6] * z + c[7] * y * z
+    gy = c[2] + c[4] * x + c[5] * z + c[7] * x * z
+    gz = c[3] + c[5] * y + c[6] * x + c[7] * x * y
+    f = om[0] * gx + om[1] * gy + om[2] * gz + np.repeat(st, 8) * psi
+    N = 8 * n ** 3
+    for scaled in (True, False):
+        r, cc, v = O.hex_assemble(n, om, st, scaled=scaled)
+        b = O.hex_rhs(n, om, st, f, psi, scaled=scaled)
+        sol = spl.spsolve(sp.csr_matrix((v, cc, r), shape=(N, N)).tocsc(), b)
+        assert np.abs(sol - psi).max() < 1e-12
+
+
+def test_scaled_operator_structure():
+    """Sec. 1.3: after block-inverse scaling the diagonal is exactly 1 and the
+    matrix is block lower triangular in upwind order (nnz per SURVEY counts)."""
+    om = I.level_symmetric(2)[0][0]
+    r, c, v = O.hex_assemble(8, om, np.ones(512))
+    assert len(c) == 47104
+    N = 4096
+    for i in range(N):
+        cols = c[r[i]:r[i + 1]]
+        assert np.all(np.diff(cols) > 0)
+        d = np.where(cols == i)[0]
+        assert len(d) == 1 and v[r[i] + d[0]] == 1.0
+        assert np.all((cols // 8 == i // 8) <= (cols == i))   # no other entry in the own block
+        assert np.all(cols // 8 <= i // 8)                      # all-positive direction: upwind = lower index
+
+
+def test_sweep_equals_dense_solve():
+    n = 3
+    rng = np.random.default_rng(5)
+    st = 0.2 + 3 * rng.random(n ** 3)
+    N = 8 * n ** 3
+    for om in I.level_symmetric(2)[0]:
+        src = rng.random(N)
+        rL, cL, vL = O.hex_assemble(n, om, st, scaled=False)
+        bL = O.hex_rhs(n, om, st, src, scaled=False)
+        ref = np.linalg.solve(csr_dense(rL, cL, vL, N), bL)
+        r, c, v = O.hex_assemble(n, om, st, scaled=True)
+        b = O.hex_rhs(n, om, st, src, scaled=True)
+        x, order = O.sweep(r, c, v, b)
+        assert np.abs(x - ref).max() <= 1e-13 * np.abs(ref).max()
+        assert sorted(order) == list(range(n ** 3))
+        assert np.linalg.norm(sp.csr_matrix((v, c, r), shape=(N, N)) @ x - b) <= 1e-14 * np.linalg.norm(b)
+
+
+def test_pure_absorber_plane_wave_attenuation():
+    """sigma_s = 0, no volume source, inflow psi = exp(-sigma_t Omega.x): the exact
+    solution attenuates exponentially along every characteristic.  Q1 DG error
+    must fall at (close to) second order under refinement."""
+    om = I.level_symmetric(4)[0][4]
+    st = 1.5
+    errs = []
+    for n in (4, 8, 16):
+        X = hex_nodes(n)
+        g = np.exp(-st * X @ om)
+        r, c, v = O.hex_assemble(n, om, np.full(n ** 3, st))
+        b = O.hex_rhs(n, om, np.full(n ** 3, st), np.zeros(8 * n ** 3), g)
+        x, _ = O.sweep(r, c, v, b)
+        errs.append(q1_l2_error(n, x, lambda P: np.exp(-st * P @ om)))
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(rates > 1.8), (errs, rates)
+
+
+# ---------------------------------------------------------------------------
+# AIR setup pins
+# ---------------------------------------------------------------------------
+
+def _strength_sets(L, thr):
+    S = []
+    for i in range(L.n):
+        cols = L.col[L.rowptr[i]:L.rowptr[i + 1]]
+        vals = L.val[L.rowptr[i]:L.rowptr[i + 1]]
+        off = cols != i
+        m = np.abs(vals[off]).max() if off.any() else 0.0
+        S.append(set(cols[off & (np.abs(vals) >= thr * m)].tolist()) if m > 0 else set())
+    return S
+
+
+def _c1_hierarchies(distance=1, dirs=(0, 5)):
+    p = I.config("hex8_s2")
+    out = []
+    for m in dirs:
+        r, c, v = O.hex_assemble(p.n, p.omega[m], p.sigma_t)
+        out.append((r, c, v, O.Hierarchy(r, c, v, O.default_params(distance=distance))))
+    return out
+
+
+@pytest.mark.parametrize("distance", [1, 2])
+def test_lair_defining_identity(distance):
+    """lAIR: (Z A_FF + A_CF)[i, R_i] = 0 on the pattern of every C row."""
+    for r, c, v, H in _c1_hierarchies(distance):
+        for L in H.levels()[:-1]:
+            A = sp.csr_matrix((L.val, L.col, L.rowptr), shape=(L.n, L.n)).tolil()
+            for ic in range(len(L.cpts)):
+                i = L.cpts[ic]
+                pat = L.zcol[L.zrowptr[ic]:L.zrowptr[ic + 1]]
+                z = L.zval[L.zrowptr[ic]:L.zrowptr[ic + 1]]
+                if len(pat) == 0:
+                    continue
+                assert np.all(L.cf[pat] == 0)
+                sub = A[pat, :][:, pat].toarray()
+                res = z @ sub + A[i, pat].toarray().ravel()
+                assert np.abs(res).max() <= 1e-12 * max(1.0, np.abs(sub).max())
+
+
+def _pmis_keys(n, level, seed=3):
+    """(lambda, h, i) key reading: h_i = top 32 bits of the first SplitMix64
+    output from state seed ^ (level << 40) ^ i."""
+    h = np.array([int(I.splitmix64_stream(seed ^ (level << 40) ^ i, 1)[0]) >> 32 for i in range(n)])
+    return h
+
+
+def test_pmis_invariants_and_determinism():
+    """PMIS (De Sterck, Yang, Heys): rounds pick local key maxima among the
+    undecided points of S + S^T as C, then make their strong dependents F.
+    Hence: every F point that started undecided depends strongly on a C point;
+    no two C points depend strongly on each other; and if C point i depends
+    strongly on C point j, i was chosen first, so key(i) > key(j)."""
+    for r, c, v, H in _c1_hierarchies():
+        H2 = O.Hierarchy(r, c, v)
+        for l, L in enumerate(H.levels()[:-1]):
+            S = _strength_sets(L, 0.25)
+            lam = np.zeros(L.n, int)
+            for i in range(L.n):
+                for j in S[i]:
+                    lam[j] += 1
+            h = _pmis_keys(L.n, l)
+            key = lambda i: (lam[i], h[i], i)
+            assert set(np.unique(L.cf).tolist()) <= {0, 1}
+            C = set(np.where(L.cf == 1)[0].tolist())
+            for i in range(L.n):
+                if L.cf[i] == 1:
+                    assert lam[i] > 0
+                    for j in S[i] & C:
+                        assert i not in S[j]
+                        assert key(i) > key(j)
+                elif lam[i] > 0:
+                    assert S[i] & C
+            L2 = H2.level(l)
+            assert np.array_equal(L.cf, L2.cf) and np.array_equal(L.zcol, L2.zcol)
+            assert np.array_equal(L.zval, L2.zval) and np.array_equal(L.val, L2.val)
+
+
+def test_one_point_interpolation_picks_strongest_c_neighbour():
+    for r, c, v, H in _c1_hierarchies():
+        for L in H.levels()[:-1]:
+            S = _strength_sets(L, 0.25)
+            cmap = -np.ones(L.n, int)
+            cmap[L.cpts] = np.arange(len(L.cpts))
+            for i in range(L.n):
+                if L.cf[i] == 1:
+                    assert L.pmap[i] == cmap[i]
+                    continue
+                cand = [(abs(L.val[p]), -L.col[p]) for p in range(L.rowptr[i], L.rowptr[i + 1])
+                        if L.col[p] in S[i] and L.cf[L.col[p]] == 1]
+                if not cand:
+                    assert L.pmap[i] == -1
+                else:
+                    assert L.pmap[i] == cmap[-max(cand)[1]]
+
+
+def test_rap_equals_dense_product():
+    for r, c, v, H in _c1_hierarchies():
+        levs = H.levels()
+        for l, L in enumerate(levs[:-1]):
+            if L.n > 2000:
+                continue
+            A = csr_dense(L.rowptr, L.col, L.val, L.n)
+            nc = len(L.cpts)
+            R = np.zeros((nc, L.n))
+            for ic in range(nc):
+                R[ic, L.cpts[ic]] = 1.0
+                for p in range(L.zrowptr[ic], L.zrowptr[ic + 1]):
+                    R[ic, L.zcol[p]] = L.zval[p]
+            P = np.zeros((L.n, nc))
+            for i in range(L.n):
+                if L.pmap[i] >= 0:
+                    P[i, L.pmap[i]] = 1.0
+            Ac = csr_dense(levs[l + 1].rowptr, levs[l + 1].col, levs[l + 1].val, nc)
+            ref = R @ A @ P
+            assert np.abs(Ac - ref).max() <= 1e-13 * np.abs(ref).max()
+            # structure = symbolic product of the patterns
+            sym = ((np.abs(R) > 0).astype(int) @ (np.abs(A) > 0).astype(int) @ (P > 0).astype(int)) > 0
+            assert np.array_equal(sym, csr_dense(levs[l + 1].rowptr, levs[l + 1].col,
+                                                 np.ones(levs[l + 1].nnz), nc) > 0)
+
+
+def _chain(n, seed=0):
+    rng = np.random.default_rng(seed)
+    sub = -(0.3 + 0.6 * rng.random(n - 1))
+    rowptr = [0]
+    col, val = [], []
+    for i in range(n):
+        if i > 0:
+            col.append(i - 1)
+            val.append(sub[i - 1])
+        col.append(i)
+        val.append(1.0)
+        rowptr.append(len(col))
+    return np.array(rowptr), np.array(col), np.array(val)
+
+
+def test_upwind_chain_gives_ideal_restriction_and_exact_cycle():
+    """1-D upwind chain (reduction-based AMG textbook case): dist-1 lAIR equals
+    the ideal restriction -A_CF A_FF^{-1}, and with an exact coarsest solve the
+    V-cycle reaches the exact solution after finitely many cycles."""
+    n = 200
+    r, c, v = _chain(n)
+    prm = O.default_params(max_coarse=8, coarse_sweeps=20)
+    H = O.Hierarchy(r, c, v, prm)
+    levs = H.levels()
+    for L in levs[:-1]:
+        A = csr_dense(L.rowptr, L.col, L.val, L.n)
+        F = np.where(L.cf == 0)[0]
+        Cp = L.cpts
+        ideal = -A[np.ix_(Cp, F)] @ np.linalg.inv(A[np.ix_(F, F)])
+        Z = np.zeros((len(Cp), L.n))
+        for ic in range(len(Cp)):
+            Z[ic, L.zcol[L.zrowptr[ic]:L.zrowptr[ic + 1]]] = L.zval[L.zrowptr[ic]:L.zrowptr[ic + 1]]
+        np.testing.assert_allclose(Z[:, F], ideal, atol=1e-14)
+    assert levs[-1].n <= 8
+    b = np.random.default_rng(1).random(n)
+    x = np.zeros(n)
+    exact = np.linalg.solve(csr_dense(r, c, v, n), b)
+    for _ in range(len(levs) + 1):
+        x = H.vcycle(b, x)
+    assert np.abs(x - exact).max() <= 1e-13 * np.abs(exact).max()
+
+
+def test_air_solution_equals_sweep_c1():
+    """An AIR-converged solve of every C1 direction equals the exact sweep."""
+    p = I.config("hex8_s2")
+    rng = np.random.default_rng(2)
+    for m in range(p.M):
+        r, c, v = O.hex_assemble(p.n, p.omega[m], p.sigma_t)
+        b = rng.random(p.N)
+        H = O.Hierarchy(r, c, v)
+        x, hist, rc = H.solve(b, tol=1e-12, maxit=100)
+        assert rc == 0
+        xs, _ = O.sweep(r, c, v, b)
+        assert np.linalg.norm(x - xs) <= 1e-10 * np.linalg.norm(xs)
+        rho = (hist[-1] / hist[0]) ** (1.0 / (len(hist) - 1))
+        assert rho < 0.35   # Jacobi-relaxed AIR band on 3-D hex meshes (Sec. 2 tables: ~0.1-0.3)
+
+
+# ---------------------------------------------------------------------------
+# Source iteration (Eq. sn_transport, Sec. 3)
+# ---------------------------------------------------------------------------
+
+def test_si_constant_inflow_reaches_infinite_medium_flux():
+    """Isotropic inflow psi = phi_inf / (4 pi) with phi_inf = q / (sigma_t - sigma_s)
+    makes the infinite-medium flux the exact SI fixed point (DG reproduces
+    constants), the same solution as a homogeneous reflecting medium."""
+    p = I.config("hex8_s2")
+    phi_inf = 1.0 / (1.0 - 0.5)
+    phi, psi, info = O.si_hex(p, tol=1e-12, inner_tol=1e-12, g_inflow=phi_inf / (4 * math.pi))
+    assert info["rc"] == 0
+    assert np.abs(phi - phi_inf).max() < 1e-9
+    np.testing.assert_allclose(psi, phi_inf / (4 * math.pi), atol=1e-10)
+
+
+def test_si_fixed_point_solves_block_system():
+    """Sec. 3: SI is Richardson on the Schur complement of the block system
+    [L_m, -sigma_s M/(4pi); w_m I, -I] [psi; phi] = [M q/(4pi); 0].  Its fixed
+    point must equal a dense direct solve of that block system."""
+    prob = I.hex_random(2, 2, 0.6, seed=11)
+    n, M, N, E = prob.n, prob.M, prob.N, prob.E
+    Ls, Ms = [], []
+    for m in range(M):
+        r, c, v = O.hex_assemble(n, prob.omega[m], prob.sigma_t, scaled=False)
+        Ls.append(csr_dense(r, c, v, N))
+    # mass matrix columns from the (pinned) right-hand side builder
+    Mass = np.stack([O.hex_rhs(n, prob.omega[0], prob.sigma_t, np.eye(N)[j], scaled=False) for j in range(N)], 1)
+    sig_s = np.repeat(prob.sigma_s, 8)
+    q = np.repeat(prob.q, 8)
+    K = np.zeros(((M + 1) * N, (M + 1) * N))
+    rhs = np.zeros((M + 1) * N)
+    for m in range(M):
+        K[m * N:(m + 1) * N, m * N:(m + 1) * N] = Ls[m]
+        K[m * N:(m + 1) * N, M * N:] = -Mass * sig_s[None, :] / (4 * math.pi)
+        rhs[m * N:(m + 1) * N] = Mass @ q / (4 * math.pi)
+        K[M * N:, m * N:(m + 1) * N] = prob.w[m] * np.eye(N)
+    K[M * N:, M * N:] = -np.eye(N)
+    ref = np.linalg.solve(K, rhs)
+    for use_sweep in (True, False):
+        phi, psi, info = O.si_hex(prob, tol=1e-14, max_iters=200, inner_tol=1e-14, use_sweep=use_sweep)
+        assert np.abs(phi - ref[M * N:]).max() <= 1e-12 * np.abs(ref).max()
+        assert np.abs(psi.ravel() - ref[:M * N]).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_si_air_equals_si_sweep_and_contracts_like_scattering_ratio():
+    p = I.config("hex8_s2")
+    phi_s, _, info_s = O.si_hex(p, tol=1e-10, use_sweep=True)
+    phi_a, _, info_a = O.si_hex(p, tol=1e-10, inner_tol=1e-12)
+    assert info_a["rc"] == 0
+    assert np.linalg.norm(phi_a - phi_s) <= 1e-10 * np.linalg.norm(phi_s)
+    # spectral radius of SI is at most sigma_s / sigma_t = 0.5
+    it = info_s["si_iters"]
+    assert it <= math.ceil(math.log(1e-10) / math.log(0.5)) + 3
