@@ -1,0 +1,218 @@
+/*
+ * libpair: GB300 (sm_103a) pAIR inside S_N source iteration for upwind-DG
+ * transport.  Method: Hanophy, Southworth, Li, Morel, Manteuffel, "Parallel
+ * approximate ideal restriction multigrid for solving the S_N transport
+ * equations" (arXiv 1910.11463).
+ *
+ * Conventions (every entry point):
+ *  - Array arguments are caller-owned DEVICE pointers (CUDA global memory,
+ *    contiguous) unless a comment says "host".  The library never frees them.
+ *  - Hierarchies (pair_hier) are library-owned and released by air_free().
+ *  - Work is ordered on the caller's stream ('stream' is a cudaStream_t; 0 is
+ *    the legacy default stream).  Calls that return host-visible results
+ *    (sizes, convergence info) synchronise that stream before returning.
+ *  - Every call returns a pair_status; no C++ exception crosses this boundary.
+ *    On error the outputs are unspecified and pair_last_error() returns a
+ *    message (per calling thread).
+ *  - Indices are 0-based int32; CSR column indices must be sorted ascending
+ *    within each row.  Floating point data is IEEE binary64 unless stated.
+ *  - A handle must not be used from two streams at the same time.
+ */
+#ifndef PAIR_H
+#define PAIR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PAIR_OK = 0,
+    PAIR_ERR_ARG = -1,            /* invalid argument (null pointer, size, parameter range) */
+    PAIR_ERR_OOM = -2,            /* device allocation failed */
+    PAIR_ERR_SINGULAR = -3,       /* singular element block (zero pivot) */
+    PAIR_ERR_NOT_CONVERGED = -4,  /* iteration limit reached before the tolerance */
+    PAIR_ERR_COARSEN_STALL = -5,  /* reserved */
+    PAIR_ERR_NAN = -6,            /* NaN/Inf found in an input or a residual */
+    PAIR_ERR_DEVICE_TIMEOUT = -7, /* a bounded device-side wait expired */
+    PAIR_ERR_CUDA = -8,           /* a CUDA runtime call failed */
+    PAIR_ERR_UNSUPPORTED = -9,    /* size outside what this build handles (message says which) */
+    PAIR_ERR_DEVICE = -10         /* a kernel reported an internal bound violation */
+} pair_status;
+
+typedef struct pair_hier_s *pair_hier;
+
+/* AIR parameters (Sec. 1.2 AIR, Sec. 4 parameter choices, Eq. soc).
+ *  distance      1 or 2: neighbourhood of the lAIR local solves (Sec. 1.2, Sec. 4.1.1)
+ *  theta         strength threshold for the CF splitting (paper: 0.25, Sec. 4)
+ *  eps_R         strength threshold for the R sparsity pattern (Eq. soc; paper 0.01)
+ *  phi_R         filter applied to R after it is built (Sec. 4.1.2; 0 = off)
+ *  phi_A         filter applied to every coarse operator, diagonal kept (0 = off)
+ *  max_levels    level cap (including the finest)
+ *  max_coarse    a level with at most this many rows is the coarsest
+ *  coarse_sweeps pointwise Jacobi sweeps on the coarsest level
+ *  seed          PMIS key hash seed
+ *  precision     0: hierarchy values and V-cycle in FP64;
+ *                1: FP32 hierarchy and V-cycle under FP64 iterative refinement */
+typedef struct {
+    int distance;
+    double theta, eps_R, phi_R, phi_A;
+    int max_levels, max_coarse, coarse_sweeps;
+    uint64_t seed;
+    int precision;
+} air_params;
+
+/* Fills the defaults: distance 1, theta 0.25, eps_R 0.01, phi_R 0, phi_A 0,
+ * max_levels 25, max_coarse 100, coarse_sweeps 20, seed 3, precision 1. */
+void air_params_default(air_params *p);
+
+/* A square CSR matrix in device memory. */
+typedef struct {
+    int n;              /* rows = columns */
+    int nnz;            /* rowptr[n] */
+    const int *rowptr;  /* n + 1 */
+    const int *col;     /* nnz, ascending within a row */
+    const double *val;  /* nnz */
+} pair_csr;
+
+/* Per-level sizes of one matrix of a (possibly batched) hierarchy. */
+typedef struct {
+    int n;          /* rows of this level */
+    int nnz;        /* stored entries of A_l */
+    int nc;         /* coarse points (0 on the coarsest level) */
+    int nnz_R;      /* stored entries of Z (R = [Z, I] has nnz_R + nc) */
+    int coarsest;   /* 1 on the last level of this matrix */
+    int pmis_rounds;
+    int n_singular; /* lAIR local systems found singular (their R row is injection) */
+} pair_level_info;
+
+typedef struct {
+    int iters;          /* V-cycles (refinement steps) taken by the slowest matrix */
+    double rel_resid;   /* max over matrices of ||b - A x|| / ||b|| at exit (FP64) */
+    double rho;         /* mean convergence factor (||r_k||/||r_0||)^(1/k) over matrices */
+} air_solve_info;
+
+/*
+ * air_setup: AIR hierarchies for 'count' independent square matrices A[0..count-1]
+ * (Sec. 1.2; Sec. 4.1.1 Eq. soc; Sec. 4.1.2), built together: every level of
+ * all matrices is processed by one launch per setup step.
+ * Steps per level: strength (|a_ij| >= theta max_{k!=i}|a_ik|), PMIS CF
+ * splitting with key (lambda_i, hash(seed, level, i), i), one-point
+ * interpolation to the strongest C neighbour, lAIR restriction R = [Z, I]
+ * from FP64 LU solves on distance-1/2 strong F neighbourhoods (pattern from
+ * eps_R), optional phi_R filter, Galerkin A_c = R A P, optional phi_A filter.
+ * All setup arithmetic is FP64 with no fused multiply-add, in the order
+ * documented with the kernels, so results are reproducible bit for bit.
+ *   A      host array of 'count' descriptors of device CSR matrices (copied)
+ *   out    receives the new handle
+ * Errors: PAIR_ERR_ARG (count < 1, null pointers, n < 1, distance not 1/2),
+ * PAIR_ERR_UNSUPPORTED (an lAIR pattern larger than the local-solve limit).
+ */
+pair_status air_setup(const pair_csr *A, int count, const air_params *prm, void *stream, pair_hier *out);
+
+/* One V-cycle on every matrix of the batch (Sec. 1.2): x <- x + V(b - A x).
+ * No pre-relaxation; restrict the residual with R, recurse with zero initial
+ * guess, prolong with P (one-point), post-relax F-Jacobi then C-Jacobi
+ * (omega = 1); coarsest level: coarse_sweeps Jacobi sweeps.  The level-0
+ * residual is FP64; the cycle runs in the hierarchy's precision.
+ *   b, x   concatenation of the right-hand sides / iterates of all matrices
+ *          (length = sum of n), x updated in place. */
+pair_status air_vcycle(pair_hier h, const double *b, double *x, void *stream);
+
+/* Repeats air_vcycle until ||b - A x||_2 <= tol ||b||_2 for every matrix (FP64
+ * residual) or maxit cycles (Sec. 2.1 solve loop).  Matrices that converge
+ * stop being updated.  'info' (host, may be NULL) receives the totals.
+ * Returns PAIR_ERR_NOT_CONVERGED if a matrix misses the tolerance. */
+pair_status air_solve(pair_hier h, const double *b, double *x, double tol, int maxit, void *stream,
+                      air_solve_info *info);
+
+/* Number of matrices in the batch and levels of matrix 'mat' (host out). */
+pair_status air_hier_nlevels(pair_hier h, int mat, int *nlevels);
+pair_status air_level_info(pair_hier h, int mat, int level, pair_level_info *out);
+
+/* Copies level 'level' of matrix 'mat' to HOST arrays (any may be NULL), with
+ * indices local to that matrix: A_l (rowptr n+1, col nnz, val nnz), the CF
+ * splitting cf (n bytes: 1 C, 0 F; undefined on the coarsest level), pmap (n:
+ * coarse column of P for each row or -1), cpts (nc: fine index of each coarse
+ * point) and Z (zrowptr nc+1, zcol nnz_R fine indices, zval nnz_R). */
+pair_status air_level_export(pair_hier h, int mat, int level, int *rowptr, int *col, double *val,
+                             signed char *cf, int *pmap, int *cpts, int *zrowptr, int *zcol, double *zval);
+
+void air_free(pair_hier h);
+
+/* ---------------------------------------------------------------------------
+ * Upwind DG transport on the unit cube split into n^3 hexahedra, Q1 elements
+ * (Eq. weak_form_transport), element e = ix + n (iy + n iz), DOF 8 e + a with
+ * local node a = ax + 2 ay + 4 az.  Vacuum boundaries unless g_inflow != 0.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int n;              /* elements per axis */
+} pair_mesh;
+
+typedef struct {
+    int M;                  /* directions */
+    const double *omega;    /* HOST, M x 3 direction cosines */
+    const double *w;        /* HOST, M weights (sum 4 pi for a full set) */
+} pair_quad;
+
+/* Stored entries of the block-scaled operator A = D^{-1} L of direction
+ * 'omega' (host, 3 doubles): 8 per row for the identity diagonal plus 4 per
+ * inflow face with an upwind neighbour (Sec. 1.3). */
+pair_status dg_hex_nnz(const pair_mesh *mesh, const double *omega, int *nnz);
+
+/* Assembles A = D^{-1} L for one direction (Eq. weak_form_transport, block
+ * scaling of Sec. 1.3) into caller-allocated device CSR arrays (rowptr N+1,
+ * col/val dg_hex_nnz entries).  Diagonal block = identity (stored as its
+ * diagonal); off-diagonal face blocks D_K^{-1} L_KK' (8 x 4).  FP64, element
+ * blocks factored by LU with partial pivoting, no fused multiply-add.
+ *   sigma_t  device, n^3 values. */
+pair_status dg_assemble_hex(const pair_mesh *mesh, const double *omega, const double *sigma_t,
+                            int *rowptr, int *col, double *val, void *stream);
+
+/* Source-iteration controls. */
+typedef struct {
+    double tol;          /* stop when ||phi^{n+1} - phi^n|| <= tol ||phi^{n+1}|| (2-norm) */
+    int max_iters;       /* SI iterations (1 = exactly one iteration) */
+    double inner_tol;    /* per-direction solve: ||b - A psi|| <= inner_tol ||b|| */
+    int inner_maxit;     /* V-cycles per direction solve */
+    int batch;           /* directions per batch (0: all that fit the memory budget) */
+    double mem_budget_gb;/* device memory for hierarchies (0: 60% of free memory) */
+    double g_inflow;     /* isotropic inflow angular flux on the inflow boundary (0: vacuum) */
+    int use_graphs;      /* capture the V-cycle of a batch in a CUDA graph */
+} si_params;
+
+void si_params_default(si_params *p);   /* 1e-8, 500, 1e-8, 100, 0, 0, 0, 1 */
+
+typedef struct {
+    int si_iters;
+    double si_change;        /* last ||phi^{n+1}-phi^n|| / ||phi^{n+1}|| */
+    int vcycles;             /* total V-cycles (refinement steps) over all solves */
+    double max_inner_resid;  /* max final relative FP64 residual over direction solves */
+    int batches;             /* direction batches per SI iteration */
+    int rebuilt;             /* 1 if hierarchies were rebuilt every SI iteration */
+    double t_setup_ms;       /* assembly + AIR setup time (device events) */
+    double t_solve_ms;       /* RHS build + solves + scalar-flux sums (device events) */
+    int levels_max;          /* deepest hierarchy */
+    double op_complexity;    /* sum_l nnz(A_l) / nnz(A_0), mean over directions */
+} si_info;
+
+/* Source iteration (Eq. sn_transport with Eq. angular_quad): each iteration
+ * solves every direction m with AIR, A_m psi_m = D_m^{-1} M (sigma_s phi^n + q)/(4 pi),
+ * from psi = 0 to inner_tol, then phi^{n+1} = sum_m w_m psi_m (FP64, fixed m
+ * order).
+ *   sigma_t, sigma_s, q   device, n^3 per-element values
+ *   phi      device, N = 8 n^3: in = initial guess, out = result
+ *   psi      device N*M (direction-major) or NULL
+ *   air      AIR parameters (precision selects FP64 or FP32-refined)
+ *   info     host, may be NULL. */
+pair_status si_solve(const pair_mesh *mesh, const pair_quad *quad, const double *sigma_t, const double *sigma_s,
+                     const double *q, const air_params *air, const si_params *sp, double *phi, double *psi,
+                     void *stream, si_info *info);
+
+const char *pair_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PAIR_H */

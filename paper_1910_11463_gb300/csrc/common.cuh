@@ -1,0 +1,148 @@
+// Internal declarations of libpair (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/pair.h"
+
+namespace pr {
+
+struct Error {
+    pair_status st;
+    std::string msg;
+};
+
+[[noreturn]] void fail(pair_status st, const std::string &msg);
+void cuda_check(cudaError_t e, const char *what, const char *file, int line);
+
+#define PR_CUDA(call) ::pr::cuda_check((call), #call, __FILE__, __LINE__)
+#define PR_LAUNCH() ::pr::cuda_check(cudaGetLastError(), "kernel launch", __FILE__, __LINE__)
+#define PR_REQUIRE(cond, st, msg) \
+    do {                          \
+        if (!(cond)) ::pr::fail((st), (msg)); \
+    } while (0)
+
+// Device error word bits (set by kernels, read by the host after a phase).
+enum : int {
+    DERR_HASH_OVERFLOW = 1,
+    DERR_PATTERN_TOO_LARGE = 2,
+    DERR_BOUNDS = 4,
+    DERR_TIMEOUT = 8,
+};
+
+template <class T>
+T *dmalloc(size_t count, cudaStream_t s) {
+    if (count == 0) count = 1;
+    void *p = nullptr;
+    cudaError_t e = cudaMallocAsync(&p, count * sizeof(T), s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        fail(PAIR_ERR_OOM, std::string("device allocation of ") + std::to_string(count * sizeof(T)) +
+                               " bytes failed: " + cudaGetErrorString(e));
+    }
+    return static_cast<T *>(p);
+}
+inline void dfree(void *p, cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
+}
+
+inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+// Exclusive scan of int counts (n entries) into out (n+1 entries, out[n] = total);
+// returns the total (synchronises the stream).
+long long scan_exclusive(const int *in, int *out, int n, cudaStream_t s, bool want_total = true);
+
+// ---------------------------------------------------------------------------
+// Hierarchy storage.  A hierarchy holds a batch of independent matrices
+// ("directions"); level l stores the concatenation of the level-l operators of
+// every matrix that has a level l, in matrix order.
+// ---------------------------------------------------------------------------
+enum : int8_t { CF_F = 0, CF_C = 1, CF_COARSEST = 2 };
+
+struct Level {
+    int n = 0;
+    long long nnz = 0;
+    int *rowptr = nullptr, *col = nullptr;
+    double *val = nullptr;
+    float *val32 = nullptr;
+    double *dinv = nullptr;
+    float *dinv32 = nullptr;
+    int8_t *cf = nullptr;     // CF_F / CF_C / CF_COARSEST
+    int *pmap = nullptr;      // P column per row (coarse index) or -1
+    int *rowdir = nullptr;    // matrix slot of each row
+    int nc = 0;
+    int *cpts = nullptr;      // fine row of every coarse point
+    int *zrowptr = nullptr, *zcol = nullptr;
+    double *zval = nullptr;
+    float *zval32 = nullptr;
+    long long nnzZ = 0;
+    // per matrix slot (host): first row, rows, coarse points, coarsest flag, stats
+    std::vector<int> row0, nrows, ncdir, nnzdir, nnzZdir, singular;
+    std::vector<char> coarsest;
+    int pmis_rounds = 0;
+    int *d_row0 = nullptr;    // device copy of row0 (size ndir)
+    // coarsest segments (device): first row and rows of each matrix that ends here
+    int n_cseg = 0;
+    int *d_cseg_row0 = nullptr, *d_cseg_n = nullptr;
+    // V-cycle work vectors (precision of the hierarchy)
+    void *vb = nullptr, *vx = nullptr, *vxn = nullptr, *vy = nullptr;
+};
+
+struct Hier {
+    int ndir = 0;
+    air_params prm{};
+    cudaStream_t stream = nullptr;   // private stream
+    std::vector<int> n0;             // rows per matrix at level 0
+    std::vector<Level> lev;
+    // Level-0 block form of the structured hex operator (set by the SI driver)
+    bool bsr0 = false;
+    int hex_n = 0;
+    double *bsr64 = nullptr;  // [dir][elem][axis][row a][4]
+    float *bsr32 = nullptr;
+    int8_t *dsign = nullptr;  // [dir][3] sign of Omega components
+    // solve state
+    double *partials = nullptr;  // [dir][max blocks]
+    int maxblk = 0;
+    double *rnorm = nullptr, *bnorm = nullptr, *rnorm0 = nullptr;  // [dir]
+    int *active = nullptr;                                         // [dir]
+    int *d_err = nullptr;
+    int *d_n0 = nullptr, *d_row00 = nullptr;  // level-0 rows per matrix and first rows
+    cudaGraphExec_t graph = nullptr;
+    const double *graph_b = nullptr;
+    double *graph_x = nullptr;
+    double graph_tol = -1;
+    ~Hier();
+};
+
+// setup.cu
+void build_hierarchy(Hier &h);   // levels from lev[0] (CSR FP64), on h.stream
+void free_level(Level &L, cudaStream_t s);
+
+// cycle.cu
+// r = b - A0 x (FP64), cast into lev[0].vb; per-matrix ||r||; active[d] = ||r|| > tol ||b||
+void residual0(Hier &h, const double *b, const double *x, double tol, bool update_active);
+void vcycle_correct(Hier &h, double *x);       // x += V(lev[0].vb), zero initial guess
+void norms0(Hier &h, const double *v, double *out);  // per-matrix 2-norms of a level-0 vector
+void alloc_cycle_vectors(Hier &h);
+
+// assemble.cu
+void hex_assemble(int n, int ndir, const double *omega_d, const double *sigma_t, int *rowptr, int *col,
+                  double *val, double *bsr64, float *bsr32, double *W, double *Gin, int *d_err, cudaStream_t s);
+long long hex_nnz(int n, const double *omega_h);
+
+// si.cu
+struct BatchSolve {
+    int iters = 0;
+    double max_rel = 0;
+    double rho_sum = 0;
+    int rho_cnt = 0;
+};
+BatchSolve solve_batch(Hier &h, const double *b, double *x, double tol, int maxit, bool use_graph);
+void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t, const double *sigma_s,
+            const double *q, const air_params &prm, const si_params &sp, double *phi, double *psi,
+            cudaStream_t user, si_info *info);
+
+}  // namespace pr

@@ -1,0 +1,418 @@
+// AIR V-cycle on the GPU (Sec. 1.2; relaxation Sec. 2 and Sec. 4: pointwise
+// Jacobi).  Correction form with zero initial guess on every level:
+//   level 0: r = b - A x (FP64, cast to the cycle precision T), per-matrix ||r||
+//   down:    b_{l+1} = R_l b_l, R row = [Z_i, 1] (restriction of the residual)
+//   coarsest: coarse_sweeps Jacobi sweeps from 0 (one CTA per matrix segment)
+//   up:      y_l = P x_{l+1} (one-point: y_i = x_{l+1}[pmap(i)])
+//            F rows: xn = y + D^{-1}(b - A y);  C rows: xn = y
+//            C rows: x = xn + D^{-1}(b - A xn); F rows: x = xn   (level 0: x_FP64 += x)
+// Level 0 of the structured hex operator is stored in block form (identity
+// diagonal implicit, three 8 x 4 face blocks per element, 16-byte row loads);
+// coarse levels are CSR with a group of G lanes per row.
+#include <algorithm>
+#include <type_traits>
+
+#include "common.cuh"
+
+namespace pr {
+
+namespace {
+
+constexpr int BS = 256;
+
+__device__ __forceinline__ int face_node(int d, int o, int t) {
+    return d == 0 ? (o | (t << 1)) : d == 1 ? ((t & 1) | (o << 1) | ((t >> 1) << 2)) : (t | (o << 2));
+}
+
+template <class T>
+struct V4 {
+    T x, y, z, w;
+};
+
+__device__ __forceinline__ V4<float> load4(const float *p) {
+    float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+    return {v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ V4<double> load4(const double *p) {
+    double2 a = __ldg(reinterpret_cast<const double2 *>(p));
+    double2 b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+    return {a.x, a.y, b.x, b.y};
+}
+
+// Off-diagonal part of row (m, e, a) of the hex block operator applied to v
+// (v points at direction m's vector).  Returns sum_faces sum_t A v.
+template <class T, class TV>
+__device__ __forceinline__ T bsr_offdiag(int n, long long E, int m, int e, int a, const int8_t *dsign, const T *vals,
+                                         const TV *v) {
+    int idx[3] = {e % n, (e / n) % n, e / (n * n)};
+    const int stride[3] = {1, n, n * n};
+    T acc = T(0);
+    const T *base = vals + (((long long)m * E + e) * 3) * 32 + a * 4;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        int sg = dsign[3 * m + d];
+        if (sg == 0) continue;
+        bool has = sg > 0 ? idx[d] > 0 : idx[d] < n - 1;
+        if (!has) continue;
+        int ep = sg > 0 ? e - stride[d] : e + stride[d];
+        int o = sg > 0 ? 1 : 0;
+        V4<T> w = load4(base + d * 32);
+        const TV *xb = v + 8LL * ep;
+        acc += w.x * (T)xb[face_node(d, o, 0)];
+        acc += w.y * (T)xb[face_node(d, o, 1)];
+        acc += w.z * (T)xb[face_node(d, o, 2)];
+        acc += w.w * (T)xb[face_node(d, o, 3)];
+    }
+    return acc;
+}
+
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double sh[32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0) {
+        int nw = (blockDim.x + 31) >> 5;
+        for (int k = 0; k < nw; ++k) s += sh[k];
+    }
+    __syncthreads();
+    return s;
+}
+
+// ---- level-0 FP64 residual --------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(BS) k_res0_bsr(int n, int N, const int8_t *dsign, const double *bsr64,
+                                                 const double *b, const double *x, T *r, double *partials,
+                                                 int maxblk, const int *active) {
+    int m = blockIdx.y;
+    if (active && !active[m]) return;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double s2 = 0.0;
+    long long E = (long long)N / 8;
+    if (i < N) {
+        long long gi = (long long)m * N + i;
+        double acc = b[gi] - x[gi];
+        acc -= bsr_offdiag<double, double>(n, E, m, i >> 3, i & 7, dsign, bsr64, x + (long long)m * N);
+        r[gi] = (T)acc;
+        s2 = acc * acc;
+    }
+    double tot = block_sum(s2);
+    if (threadIdx.x == 0) partials[(long long)m * maxblk + blockIdx.x] = tot;
+}
+
+template <class T>
+__global__ void __launch_bounds__(BS) k_res0_csr(const int *row0, const int *nrow, const int *rowptr, const int *col,
+                                                 const double *val, const double *b, const double *x, T *r,
+                                                 double *partials, int maxblk, const int *active) {
+    int m = blockIdx.y;
+    if (active && !active[m]) return;
+    int li = blockIdx.x * blockDim.x + threadIdx.x;
+    double s2 = 0.0;
+    if (li < nrow[m]) {
+        int i = row0[m] + li;
+        double acc = 0.0;
+        for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) acc += val[p] * x[col[p]];
+        acc = b[i] - acc;
+        r[i] = (T)acc;
+        s2 = acc * acc;
+    }
+    double tot = block_sum(s2);
+    if (threadIdx.x == 0) partials[(long long)m * maxblk + blockIdx.x] = tot;
+}
+
+// per-matrix norm from the partials in fixed block order (deterministic)
+__global__ void k_norm_final(int ndir, const double *partials, int maxblk, double *out, const double *bnorm,
+                             double tol, int *active) {
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= ndir) return;
+    if (active && !active[m]) return;
+    double s = 0.0;
+    for (int k = 0; k < maxblk; ++k) s += partials[(long long)m * maxblk + k];
+    double nr = sqrt(s);
+    out[m] = nr;
+    if (active && bnorm) active[m] = nr > tol * bnorm[m] ? 1 : 0;
+}
+
+__global__ void k_sumsq_rows(const int *row0, const int *nrow, const double *v, double *partials, int maxblk) {
+    int m = blockIdx.y;
+    int li = blockIdx.x * blockDim.x + threadIdx.x;
+    double s2 = 0.0;
+    if (li < nrow[m]) {
+        double a = v[row0[m] + li];
+        s2 = a * a;
+    }
+    double tot = block_sum(s2);
+    if (threadIdx.x == 0) partials[(long long)m * maxblk + blockIdx.x] = tot;
+}
+
+// ---- restriction ---------------------------------------------------------------
+template <class T, int G>
+__global__ void __launch_bounds__(BS) k_restrict(int nc, const int *cpts, const int *zrowptr, const int *zcol,
+                                                 const T *zval, const T *bf, T *bc) {
+    long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int ic = (int)(tid / G);
+    int g = threadIdx.x % G;
+    T acc = T(0);
+    if (ic < nc) {
+        for (int p = zrowptr[ic] + g; p < zrowptr[ic + 1]; p += G) acc += zval[p] * bf[zcol[p]];
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, G);
+    if (ic < nc && g == 0) bc[ic] = acc + bf[cpts[ic]];
+}
+
+// ---- prolongation y = P x_c --------------------------------------------------
+template <class T>
+__global__ void k_prolong(int n, const int8_t *cf, const int *pmap, const T *xc, T *y) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (cf[i] == CF_COARSEST) return;
+    int p = pmap[i];
+    y[i] = p >= 0 ? xc[p] : T(0);
+}
+
+// ---- CSR relaxation ------------------------------------------------------------
+// phase 0 (F): xn = y + dinv (b - A y) on F rows, xn = y on C rows
+// phase 1 (C): out = xn + dinv (b - A xn) on C rows, out = xn on F rows;
+//              level 0 (x64 != null): x64 += out, coarsest rows x64 += xco
+template <class T, int G>
+__global__ void __launch_bounds__(BS) k_relax_csr(int n, const int *rowptr, const int *col, const T *val,
+                                                  const T *dinv, const int8_t *cf, const T *b, const T *in, T *out,
+                                                  int phase, double *x64, const T *xco, const int *active,
+                                                  const int *rowdir) {
+    long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int i = (int)(tid / G);
+    int g = threadIdx.x % G;
+    bool valid = i < n;
+    int8_t c = valid ? cf[i] : CF_COARSEST;
+    if (valid && active && !active[rowdir[i]]) valid = false;
+    bool work = valid && c == (phase == 0 ? CF_F : CF_C);
+    T acc = T(0);
+    if (work)
+        for (int p = rowptr[i] + g; p < rowptr[i + 1]; p += G) acc += val[p] * in[col[p]];
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, G);
+    if (!valid || g != 0) return;
+    T v;
+    if (c == CF_COARSEST) {
+        if (x64 && phase == 1) x64[i] += (double)xco[i];
+        return;
+    }
+    v = work ? in[i] + dinv[i] * (b[i] - acc) : in[i];
+    if (phase == 1 && x64) x64[i] += (double)v;
+    else out[i] = v;
+}
+
+// ---- BSR (hex level 0) relaxation, unit diagonal ------------------------------
+template <class T>
+__global__ void __launch_bounds__(BS) k_relax_bsr(int n, int N, const int8_t *dsign, const T *vals, const int8_t *cf,
+                                                  const T *b, const T *in, T *out, int phase, double *x64,
+                                                  const int *active) {
+    int m = blockIdx.y;
+    if (active && !active[m]) return;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    long long gi = (long long)m * N + i;
+    int8_t c = cf[gi];
+    T v = in[gi];
+    if (c == (phase == 0 ? CF_F : CF_C)) {
+        T acc = bsr_offdiag<T, T>(n, (long long)N / 8, m, i >> 3, i & 7, dsign, vals, in + (long long)m * N);
+        v = v + (b[gi] - (acc + v));
+    }
+    if (phase == 1) x64[gi] += (double)v;
+    else out[gi] = v;
+}
+
+// ---- coarsest level: Jacobi sweeps, one CTA per matrix segment ---------------
+template <class T>
+__global__ void k_coarsest(const int *seg_row0, const int *seg_n, const int *rowptr, const int *col, const T *val,
+                           const T *dinv, const T *b, T *x, T *xt, int sweeps) {
+    int r0 = seg_row0[blockIdx.x], nr = seg_n[blockIdx.x];
+    for (int i = threadIdx.x; i < nr; i += blockDim.x) x[r0 + i] = T(0);
+    __syncthreads();
+    T *cur = x, *nxt = xt;
+    for (int s = 0; s < sweeps; ++s) {
+        for (int li = threadIdx.x; li < nr; li += blockDim.x) {
+            int i = r0 + li;
+            T acc = T(0);
+            for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) acc += val[p] * cur[col[p]];
+            nxt[i] = cur[i] + dinv[i] * (b[i] - acc);
+        }
+        __syncthreads();
+        T *t = cur; cur = nxt; nxt = t;
+    }
+    if (cur != x)
+        for (int li = threadIdx.x; li < nr; li += blockDim.x) x[r0 + li] = cur[r0 + li];
+}
+
+template <class T>
+const T *lv_val(const Level &L);
+template <>
+const float *lv_val<float>(const Level &L) { return L.val32; }
+template <>
+const double *lv_val<double>(const Level &L) { return L.val; }
+template <class T>
+const T *lv_dinv(const Level &L);
+template <>
+const float *lv_dinv<float>(const Level &L) { return L.dinv32; }
+template <>
+const double *lv_dinv<double>(const Level &L) { return L.dinv; }
+template <class T>
+const T *lv_zval(const Level &L);
+template <>
+const float *lv_zval<float>(const Level &L) { return L.zval32; }
+template <>
+const double *lv_zval<double>(const Level &L) { return L.zval; }
+
+int pick_group(long long nnz, int n) {
+    double avg = n > 0 ? (double)nnz / n : 0;
+    if (avg <= 6) return 1;
+    if (avg <= 14) return 4;
+    if (avg <= 40) return 8;
+    return 16;
+}
+
+template <class T, int G>
+void launch_relax(const Level &L, const T *b, const T *in, T *out, int phase, double *x64, const T *xco,
+                  const int *active, cudaStream_t s) {
+    k_relax_csr<T, G><<<blocks_for((long long)L.n * G, BS), BS, 0, s>>>(
+        L.n, L.rowptr, L.col, lv_val<T>(L), lv_dinv<T>(L), L.cf, b, in, out, phase, x64, xco, active, L.rowdir);
+}
+
+template <class T>
+void relax_csr(const Level &L, const T *b, const T *in, T *out, int phase, double *x64, const T *xco,
+               const int *active, cudaStream_t s) {
+    switch (pick_group(L.nnz, L.n)) {
+        case 1: launch_relax<T, 1>(L, b, in, out, phase, x64, xco, active, s); break;
+        case 4: launch_relax<T, 4>(L, b, in, out, phase, x64, xco, active, s); break;
+        case 8: launch_relax<T, 8>(L, b, in, out, phase, x64, xco, active, s); break;
+        default: launch_relax<T, 16>(L, b, in, out, phase, x64, xco, active, s); break;
+    }
+    PR_LAUNCH();
+}
+
+template <class T>
+void restrict_(const Level &L, const T *bf, T *bc, cudaStream_t s) {
+    int G = pick_group(L.nnzZ, L.nc);
+    switch (G) {
+        case 1: k_restrict<T, 1><<<blocks_for((long long)L.nc, BS), BS, 0, s>>>(L.nc, L.cpts, L.zrowptr, L.zcol, lv_zval<T>(L), bf, bc); break;
+        case 4: k_restrict<T, 4><<<blocks_for((long long)L.nc * 4, BS), BS, 0, s>>>(L.nc, L.cpts, L.zrowptr, L.zcol, lv_zval<T>(L), bf, bc); break;
+        case 8: k_restrict<T, 8><<<blocks_for((long long)L.nc * 8, BS), BS, 0, s>>>(L.nc, L.cpts, L.zrowptr, L.zcol, lv_zval<T>(L), bf, bc); break;
+        default: k_restrict<T, 16><<<blocks_for((long long)L.nc * 16, BS), BS, 0, s>>>(L.nc, L.cpts, L.zrowptr, L.zcol, lv_zval<T>(L), bf, bc); break;
+    }
+    PR_LAUNCH();
+}
+
+template <class T>
+void vcycle_t(Hier &h, double *x64) {
+    cudaStream_t s = h.stream;
+    int NL = (int)h.lev.size();
+    const int *active = h.active;
+    for (int l = 0; l < NL; ++l) {
+        Level &L = h.lev[l];
+        if (l + 1 < NL) restrict_<T>(L, (const T *)L.vb, (T *)h.lev[l + 1].vb, s);
+        if (L.n_cseg) {
+            k_coarsest<T><<<L.n_cseg, 256, 0, s>>>(L.d_cseg_row0, L.d_cseg_n, L.rowptr, L.col, lv_val<T>(L),
+                                                   lv_dinv<T>(L), (const T *)L.vb, (T *)L.vx, (T *)L.vxn,
+                                                   h.prm.coarse_sweeps);
+            PR_LAUNCH();
+        }
+    }
+    for (int l = NL - 2; l >= 0; --l) {
+        Level &L = h.lev[l];
+        const Level &C = h.lev[l + 1];
+        k_prolong<T><<<blocks_for(L.n, BS), BS, 0, s>>>(L.n, L.cf, L.pmap, (const T *)C.vx, (T *)L.vy);
+        PR_LAUNCH();
+        if (l == 0 && h.bsr0) {
+            int N = h.n0[0];
+            dim3 grid(blocks_for(N, BS), h.ndir);
+            const T *vals = std::is_same<T, float>::value ? (const T *)h.bsr32 : (const T *)h.bsr64;
+            k_relax_bsr<T><<<grid, BS, 0, s>>>(h.hex_n, N, h.dsign, vals, L.cf, (const T *)L.vb, (const T *)L.vy,
+                                               (T *)L.vxn, 0, nullptr, active);
+            PR_LAUNCH();
+            k_relax_bsr<T><<<grid, BS, 0, s>>>(h.hex_n, N, h.dsign, vals, L.cf, (const T *)L.vb, (const T *)L.vxn,
+                                               nullptr, 1, x64, active);
+            PR_LAUNCH();
+        } else {
+            const int *act = l == 0 ? active : nullptr;
+            relax_csr<T>(L, (const T *)L.vb, (const T *)L.vy, (T *)L.vxn, 0, nullptr, nullptr, act, s);
+            relax_csr<T>(L, (const T *)L.vb, (const T *)L.vxn, (T *)L.vx, 1, l == 0 ? x64 : nullptr,
+                         (const T *)L.vx, act, s);
+        }
+    }
+    if (NL == 1) {   // single-level hierarchies: x += coarsest solution
+        Level &L = h.lev[0];
+        relax_csr<T>(L, (const T *)L.vb, (const T *)L.vx, (T *)L.vxn, 1, x64, (const T *)L.vx, active, s);
+    }
+}
+
+}  // namespace
+
+void alloc_cycle_vectors(Hier &h) {
+    size_t es = h.prm.precision == 1 ? sizeof(float) : sizeof(double);
+    for (auto &L : h.lev) {
+        size_t n = (size_t)std::max(L.n, 1);
+        L.vb = dmalloc<char>(n * es, h.stream);
+        L.vx = dmalloc<char>(n * es, h.stream);
+        L.vxn = dmalloc<char>(n * es, h.stream);
+        L.vy = dmalloc<char>(n * es, h.stream);
+        PR_CUDA(cudaMemsetAsync(L.vx, 0, n * es, h.stream));
+        PR_CUDA(cudaMemsetAsync(L.vxn, 0, n * es, h.stream));
+        PR_CUDA(cudaMemsetAsync(L.vy, 0, n * es, h.stream));
+    }
+    int mb = 1;
+    for (int d = 0; d < h.ndir; ++d) mb = std::max<int>(mb, (int)blocks_for(h.n0[d], BS));
+    h.maxblk = mb;
+    h.partials = dmalloc<double>((size_t)mb * h.ndir, h.stream);
+    h.rnorm = dmalloc<double>(h.ndir, h.stream);
+    h.rnorm0 = dmalloc<double>(h.ndir, h.stream);
+    h.bnorm = dmalloc<double>(h.ndir, h.stream);
+    h.active = dmalloc<int>(h.ndir, h.stream);
+}
+
+void residual0(Hier &h, const double *b, const double *x, double tol, bool update_active) {
+    cudaStream_t s = h.stream;
+    PR_CUDA(cudaMemsetAsync(h.partials, 0, sizeof(double) * h.maxblk * h.ndir, s));
+    int *act = update_active ? h.active : nullptr;
+    Level &L = h.lev[0];
+    dim3 grid(h.maxblk, h.ndir);
+    bool f32 = h.prm.precision == 1;
+    if (h.bsr0) {
+        int N = h.n0[0];
+        if (f32)
+            k_res0_bsr<float><<<grid, BS, 0, s>>>(h.hex_n, N, h.dsign, h.bsr64, b, x, (float *)L.vb, h.partials,
+                                                  h.maxblk, act);
+        else
+            k_res0_bsr<double><<<grid, BS, 0, s>>>(h.hex_n, N, h.dsign, h.bsr64, b, x, (double *)L.vb, h.partials,
+                                                   h.maxblk, act);
+    } else {
+        if (f32)
+            k_res0_csr<float><<<grid, BS, 0, s>>>(h.d_row00, h.d_n0, L.rowptr, L.col, L.val, b, x, (float *)L.vb,
+                                                  h.partials, h.maxblk, act);
+        else
+            k_res0_csr<double><<<grid, BS, 0, s>>>(h.d_row00, h.d_n0, L.rowptr, L.col, L.val, b, x, (double *)L.vb,
+                                                   h.partials, h.maxblk, act);
+    }
+    PR_LAUNCH();
+    k_norm_final<<<blocks_for(h.ndir, 128), 128, 0, s>>>(h.ndir, h.partials, h.maxblk, h.rnorm, h.bnorm, tol, act);
+    PR_LAUNCH();
+}
+
+void norms0(Hier &h, const double *v, double *out) {
+    cudaStream_t s = h.stream;
+    PR_CUDA(cudaMemsetAsync(h.partials, 0, sizeof(double) * h.maxblk * h.ndir, s));
+    dim3 grid(h.maxblk, h.ndir);
+    k_sumsq_rows<<<grid, BS, 0, s>>>(h.d_row00, h.d_n0, v, h.partials, h.maxblk);
+    PR_LAUNCH();
+    k_norm_final<<<blocks_for(h.ndir, 128), 128, 0, s>>>(h.ndir, h.partials, h.maxblk, out, nullptr, 0.0, nullptr);
+    PR_LAUNCH();
+}
+
+void vcycle_correct(Hier &h, double *x) {
+    if (h.prm.precision == 1) vcycle_t<float>(h, x);
+    else vcycle_t<double>(h, x);
+}
+
+}  // namespace pr

@@ -1,0 +1,847 @@
+// AIR setup on the GPU (Sec. 1.2; Sec. 4.1.1 Eq. soc; Sec. 4.1.2 filtering).
+//
+// A hierarchy holds a batch of independent matrices; every level of every
+// matrix is processed by one launch per step.  Compiled with --fmad=false and
+// written so that each floating-point result is formed by the same operations
+// in the same order as the plain definitions below, hence reproducible bit for
+// bit:
+//   strength   S_i = {j != i : |a_ij| >= theta * max_{k != i} |a_ik|}, empty if the max is 0
+//   PMIS       key_i = (lambda_i, h_i, i), lambda_i = #{k : i in S_k},
+//              h_i = top 32 bits of SplitMix64 at state seed ^ (level << 40) ^ i (local i);
+//              lambda_i = 0 -> F; rounds: undecided local key maxima over S + S^T -> C,
+//              undecided rows depending strongly on a new C -> F
+//   P          one-point: F row -> strongest C neighbour in S_i (first maximum), weight 1
+//   lAIR       C row i, pattern R_i = strong (eps_R) F neighbours (distance 1, or 2 via F
+//              points), A[R_i,R_i]^T z = -A[i,R_i]^T by LU with partial pivoting (first max
+//              pivot, full row swaps, column-oriented substitutions); optional phi_R filter
+//   RAP        (AP)[k,c] = sum over l ascending (pmap(l) = c) of a_kl, starting from 0.0;
+//              (RAP)[i,c] = sum over the R row in ascending column order (identity at
+//              its place) of R_ik (AP)[k,c], starting from 0.0; every structural product
+//              kept; optional phi_A filter of off-diagonal entries
+#include <algorithm>
+#include <cstdio>
+
+#include "common.cuh"
+
+namespace pr {
+
+namespace {
+
+constexpr int8_t ST_U = -1, ST_F = 0, ST_C = 1;
+
+__device__ __forceinline__ uint64_t splitmix_first(uint64_t state) {
+    uint64_t z = state + 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ double lookup(const int *rowptr, const int *col, const double *val, int i, int j) {
+    int lo = rowptr[i], hi = rowptr[i + 1] - 1;
+    while (lo <= hi) {
+        int m = (lo + hi) >> 1;
+        int c = col[m];
+        if (c == j) return val[m];
+        if (c < j) lo = m + 1; else hi = m - 1;
+    }
+    return 0.0;
+}
+
+__global__ void k_dinv(int n, const int *rowptr, const int *col, const double *val, double *dinv, float *dinv32) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double d = lookup(rowptr, col, val, i, i);
+    double r = (d != 0.0) ? 1.0 / d : 0.0;
+    dinv[i] = r;
+    if (dinv32) dinv32[i] = (float)r;
+}
+
+// bit 0: S (theta), bit 1: S^R (eps_R)
+__global__ void k_strength(int n, const int *rowptr, const int *col, const double *val, const int *rowdir,
+                           const char *dwork, double theta, double epsR, uint8_t *S) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int p0 = rowptr[i], p1 = rowptr[i + 1];
+    if (!dwork[rowdir[i]]) {
+        for (int p = p0; p < p1; ++p) S[p] = 0;
+        return;
+    }
+    double m = 0.0;
+    for (int p = p0; p < p1; ++p)
+        if (col[p] != i) { double v = fabs(val[p]); if (v > m) m = v; }
+    double t1 = theta * m, t2 = epsR * m;
+    for (int p = p0; p < p1; ++p) {
+        uint8_t s = 0;
+        if (col[p] != i && m > 0.0) {
+            double a = fabs(val[p]);
+            if (a >= t1) s |= 1;
+            if (a >= t2) s |= 2;
+        }
+        S[p] = s;
+    }
+}
+
+__global__ void k_lambda(int n, const int *rowptr, const int *col, const uint8_t *S, unsigned *lam) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int p = rowptr[i]; p < rowptr[i + 1]; ++p)
+        if (S[p] & 1) atomicAdd(&lam[col[p]], 1u);
+}
+
+__global__ void k_pmis_init(int n, const int *rowdir, const char *dwork, const int *row0, const unsigned *lam,
+                            int level, unsigned long long seed, uint64_t *key, int8_t *state, int *undecided) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int d = rowdir[i];
+    if (!dwork[d]) { state[i] = ST_F; key[i] = 0; return; }
+    uint64_t li = (uint64_t)(i - row0[d]);
+    uint32_t hh = (uint32_t)(splitmix_first(seed ^ ((uint64_t)level << 40) ^ li) >> 32);
+    key[i] = ((uint64_t)lam[i] << 32) | hh;
+    int8_t s = lam[i] == 0 ? ST_F : ST_U;
+    state[i] = s;
+    if (s == ST_U) atomicAdd(undecided, 1);
+}
+
+__device__ __forceinline__ bool key_gt(uint64_t kj, int j, uint64_t ki, int i) {
+    return kj > ki || (kj == ki && j > i);
+}
+
+__global__ void k_pmis_mark(int n, const int *rowptr, const int *col, const uint8_t *S, const uint64_t *key,
+                            const int8_t *state, int *notmax, int round) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || state[i] != ST_U) return;
+    uint64_t ki = key[i];
+    for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+        if (!(S[p] & 1)) continue;
+        int j = col[p];
+        if (state[j] != ST_U) continue;
+        if (key_gt(key[j], j, ki, i)) notmax[i] = round;
+        else notmax[j] = round;
+    }
+}
+
+__global__ void k_pmis_update(int n, const int *rowptr, const int *col, const uint8_t *S, const int8_t *state,
+                              int8_t *next, const int *notmax, int round, int *undecided) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int8_t s = state[i];
+    if (s != ST_U) { next[i] = s; return; }
+    if (notmax[i] != round) { next[i] = ST_C; return; }
+    for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+        if (!(S[p] & 1)) continue;
+        int j = col[p];
+        if (state[j] == ST_U && notmax[j] != round) { next[i] = ST_F; return; }
+    }
+    next[i] = ST_U;
+    atomicAdd(undecided, 1);
+}
+
+__global__ void k_count_c(int n, const int *rowdir, const int8_t *state, int *ncdir) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (state[i] == ST_C) atomicAdd(&ncdir[rowdir[i]], 1);
+}
+
+__global__ void k_cf_final(int n, const int *rowdir, const char *cont, const int8_t *state, int8_t *cf, int *isC) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    bool c = cont[rowdir[i]];
+    cf[i] = c ? (state[i] == ST_C ? CF_C : CF_F) : CF_COARSEST;
+    isC[i] = (c && state[i] == ST_C) ? 1 : 0;
+}
+
+__global__ void k_cpts(int n, const int8_t *cf, const int *cidx, int *cpts) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (cf[i] == CF_C) cpts[cidx[i]] = i;
+}
+
+__global__ void k_pmap(int n, const int *rowptr, const int *col, const double *val, const uint8_t *S,
+                       const int8_t *cf, const int *cidx, int *pmap) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int8_t c = cf[i];
+    if (c == CF_COARSEST) { pmap[i] = -1; return; }
+    if (c == CF_C) { pmap[i] = cidx[i]; return; }
+    int best = -1;
+    double bv = -1.0;
+    for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+        int j = col[p];
+        if ((S[p] & 1) && cf[j] == CF_C) {
+            double v = fabs(val[p]);
+            if (v > bv) { bv = v; best = j; }
+        }
+    }
+    pmap[i] = best >= 0 ? cidx[best] : -1;
+}
+
+// ---- lAIR ------------------------------------------------------------------
+__global__ void k_lair_ncand(int nc, const int *cpts, const int *rowptr, const int *col, const uint8_t *S,
+                             const int8_t *cf, int distance, int *ncand) {
+    int ic = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ic >= nc) return;
+    int i = cpts[ic];
+    int c = 0;
+    for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+        int j = col[p];
+        if ((S[p] & 2) && cf[j] == CF_F) {
+            ++c;
+            if (distance >= 2)
+                for (int q = rowptr[j]; q < rowptr[j + 1]; ++q)
+                    if ((S[q] & 2) && cf[col[q]] == CF_F) ++c;
+        }
+    }
+    ncand[ic] = c;
+}
+
+__global__ void k_lair_pattern(int nc, const int *cpts, const int *rowptr, const int *col, const uint8_t *S,
+                               const int8_t *cf, int distance, const int *candptr, int *cand, int *npat) {
+    int ic = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ic >= nc) return;
+    int i = cpts[ic];
+    int *c = cand + candptr[ic];
+    int m = 0;
+    for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+        int j = col[p];
+        if ((S[p] & 2) && cf[j] == CF_F) c[m++] = j;
+    }
+    if (distance >= 2) {
+        int m1 = m;
+        for (int t = 0; t < m1; ++t) {
+            int j = c[t];
+            for (int q = rowptr[j]; q < rowptr[j + 1]; ++q)
+                if ((S[q] & 2) && cf[col[q]] == CF_F) c[m++] = col[q];
+        }
+        for (int a = 1; a < m; ++a) {   // insertion sort, then unique
+            int v = c[a], b = a;
+            while (b > 0 && c[b - 1] > v) { c[b] = c[b - 1]; --b; }
+            c[b] = v;
+        }
+        int u = 0;
+        for (int a = 0; a < m; ++a)
+            if (u == 0 || c[u - 1] != c[a]) c[u++] = c[a];
+        m = u;
+    }
+    npat[ic] = m;
+}
+
+__global__ void k_max_int(const int *v, int n, int *out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) atomicMax(out, v[i]);
+}
+
+// Warp per C row.  Shared memory per warp: M (nmax^2 doubles), y (nmax
+// doubles), pattern (nmax ints), pivots (nmax ints).
+__global__ void k_lair_solve(int nc, const int *cpts, const int *rowptr, const int *col, const double *val,
+                             const int *candptr, const int *cand, const int *npat, const int *zrowptr, int *zcol,
+                             double *zval, int *keep, int *nsing_dir, const int *rowdir, double phi_R, int nmax) {
+    extern __shared__ double smem[];
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int wpb = blockDim.x >> 5;
+    size_t per = (size_t)nmax * nmax + nmax + nmax;   // doubles (ints packed into the tail)
+    double *M = smem + warp * per;
+    double *y = M + (size_t)nmax * nmax;
+    int *pat = (int *)(y + nmax);
+    int *piv = pat + nmax;
+    for (int ic = blockIdx.x * wpb + warp; ic < nc; ic += gridDim.x * wpb) {
+        int i = cpts[ic];
+        int np = npat[ic];
+        const int *cp = cand + candptr[ic];
+        for (int t = lane; t < np; t += 32) pat[t] = cp[t];
+        __syncwarp();
+        double mx = 0.0;
+        for (int idx = lane; idx < np * np; idx += 32) {
+            int r = idx / np, c = idx - r * np;
+            double v = lookup(rowptr, col, val, pat[c], pat[r]);   // transposed block
+            M[idx] = v;
+            mx = fmax(mx, fabs(v));
+        }
+        for (int r = lane; r < np; r += 32) y[r] = -lookup(rowptr, col, val, i, pat[r]);
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        double tiny = 1e-14 * mx;
+        __syncwarp();
+        bool singular = false;
+        for (int k = 0; k < np; ++k) {
+            // pivot: largest |M[r][k]|, r >= k, smallest r among equals
+            double bv = -1.0;
+            int br = k;
+            for (int r = k + lane; r < np; r += 32) {
+                double v = fabs(M[r * np + k]);
+                if (v > bv) { bv = v; br = r; }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                int orr = __shfl_xor_sync(0xffffffffu, br, o);
+                if (ov > bv || (ov == bv && orr < br)) { bv = ov; br = orr; }
+            }
+            if (!(bv > tiny)) { singular = true; break; }
+            if (lane == 0) piv[k] = br;
+            if (br != k)
+                for (int c = lane; c < np; c += 32) {
+                    double t = M[k * np + c];
+                    M[k * np + c] = M[br * np + c];
+                    M[br * np + c] = t;
+                }
+            __syncwarp();
+            double dk = M[k * np + k];
+            for (int r = k + 1 + lane; r < np; r += 32) M[r * np + k] = M[r * np + k] / dk;
+            __syncwarp();
+            int w = np - k - 1;
+            for (int idx = lane; idx < w * w; idx += 32) {
+                int r = k + 1 + idx / w, c = k + 1 + idx % w;
+                M[r * np + c] = M[r * np + c] - M[r * np + k] * M[k * np + c];
+            }
+            __syncwarp();
+        }
+        int kept = 0;
+        if (!singular && np > 0) {
+            if (lane == 0) {
+                for (int k = 0; k < np; ++k)
+                    if (piv[k] != k) { double t = y[k]; y[k] = y[piv[k]]; y[piv[k]] = t; }
+            }
+            __syncwarp();
+            for (int k = 0; k < np; ++k) {
+                double yk = y[k];
+                for (int r = k + 1 + lane; r < np; r += 32) y[r] = y[r] - M[r * np + k] * yk;
+                __syncwarp();
+            }
+            for (int k = np - 1; k >= 0; --k) {
+                if (lane == 0) y[k] = y[k] / M[k * np + k];
+                __syncwarp();
+                double yk = y[k];
+                for (int r = lane; r < k; r += 32) y[r] = y[r] - M[r * np + k] * yk;
+                __syncwarp();
+            }
+            double zm = 0.0;
+            for (int t = lane; t < np; t += 32) zm = fmax(zm, fabs(y[t]));
+            for (int o = 16; o > 0; o >>= 1) zm = fmax(zm, __shfl_xor_sync(0xffffffffu, zm, o));
+            double thr = phi_R * zm;
+            // keep in ascending order: ballot-compacted write
+            int base = zrowptr[ic];
+            for (int t0 = 0; t0 < np; t0 += 32) {
+                int t = t0 + lane;
+                bool k_ = t < np && !(phi_R > 0.0 && fabs(y[t]) < thr);
+                unsigned msk = __ballot_sync(0xffffffffu, k_);
+                if (k_) {
+                    int off = kept + __popc(msk & ((1u << lane) - 1u));
+                    zcol[base + off] = pat[t];
+                    zval[base + off] = y[t];
+                }
+                kept += __popc(msk);
+            }
+        } else if (singular && lane == 0) {
+            atomicAdd(&nsing_dir[rowdir[i]], 1);
+        }
+        if (lane == 0) keep[ic] = kept;
+        __syncwarp();
+    }
+}
+
+__global__ void k_compact_rows(int nrows, const int *oldptr, const int *newptr, const int *col_in,
+                               const double *val_in, int *col_out, double *val_out) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrows) return;
+    int o = oldptr[r], nn = newptr[r], cnt = newptr[r + 1] - newptr[r];
+    for (int t = 0; t < cnt; ++t) { col_out[nn + t] = col_in[o + t]; val_out[nn + t] = val_in[o + t]; }
+}
+
+// ---- RAP ---------------------------------------------------------------------
+__global__ void k_ap(int n, const int *rowptr, const int *col, const double *val, const int *pmap,
+                     const int8_t *cf, int *aplen, int *apcol, double *apval) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    if (cf[k] == CF_COARSEST) { aplen[k] = 0; return; }
+    int s = rowptr[k];
+    int len = 0;
+    for (int p = rowptr[k]; p < rowptr[k + 1]; ++p) {
+        int c = pmap[col[p]];
+        if (c < 0) continue;
+        int t = 0;
+        while (t < len && apcol[s + t] != c) ++t;
+        if (t == len) { apcol[s + t] = c; apval[s + t] = 0.0; ++len; }
+        apval[s + t] = apval[s + t] + val[p];
+    }
+    for (int a = 1; a < len; ++a) {
+        int c = apcol[s + a];
+        double v = apval[s + a];
+        int b = a;
+        while (b > 0 && apcol[s + b - 1] > c) { apcol[s + b] = apcol[s + b - 1]; apval[s + b] = apval[s + b - 1]; --b; }
+        apcol[s + b] = c;
+        apval[s + b] = v;
+    }
+    aplen[k] = len;
+}
+
+__global__ void k_rap_bound(int nc, const int *cpts, const int *zrowptr, const int *zcol, const int *aplen, int *U) {
+    int ic = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ic >= nc) return;
+    int u = aplen[cpts[ic]];
+    for (int t = zrowptr[ic]; t < zrowptr[ic + 1]; ++t) u += aplen[zcol[t]];
+    U[ic] = u;
+}
+
+__device__ __forceinline__ unsigned hslot(int c, unsigned mask) { return ((unsigned)c * 2654435761u) & mask; }
+
+// Warp per coarse row.  Table: keys (int, -1 empty) and values, in shared
+// memory (cap = hcap) or in global scratch (cap per row given by gcap/gptr).
+// Output: sorted, filtered entries at ucol/uval[uptr[ic]...], count in cnt[ic].
+__global__ void k_rap(int nrows_work, const int *worklist, int nc, const int *cpts, const int *zrowptr,
+                      const int *zcol, const double *zval, const int *aprow, const int *aplen, const int *apcol,
+                      const double *apval, const int *uptr, const int *U, double phiA, int *cnt, int *ucol,
+                      double *uval, int hcap, const long long *gptr, int *gkeys, double *gvals, int *overflow, int *err) {
+    extern __shared__ double smem2[];
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int wpb = blockDim.x >> 5;
+    for (int w = blockIdx.x * wpb + warp; w < nrows_work; w += gridDim.x * wpb) {
+        int ic = worklist ? worklist[w] : w;
+        int *keys;
+        double *vals;
+        int cap;
+        if (gptr) {
+            long long off = gptr[w];
+            cap = (int)(gptr[w + 1] - off);
+            keys = gkeys + off;
+            vals = gvals + off;
+        } else {
+            cap = hcap;
+            vals = smem2 + (size_t)warp * hcap;
+            keys = (int *)(smem2 + (size_t)wpb * hcap) + (size_t)warp * hcap;
+            if (2 * U[ic] > cap) {
+                if (lane == 0) { cnt[ic] = -1; atomicAdd(overflow, 1); }
+                continue;
+            }
+        }
+        unsigned mask = (unsigned)cap - 1u;
+        for (int t = lane; t < cap; t += 32) keys[t] = -1;
+        __syncwarp();
+        int i = cpts[ic];
+        int z0 = zrowptr[ic], z1 = zrowptr[ic + 1];
+        bool placed = false;
+        int t = z0;
+        while (true) {
+            int k;
+            double r;
+            if (!placed && (t == z1 || zcol[t] > i)) { k = i; r = 1.0; placed = true; }
+            else if (t < z1) { k = zcol[t]; r = zval[t]; ++t; }
+            else break;
+            int a0 = aprow[k], al = aplen[k];
+            for (int q = lane; q < al; q += 32) {
+                int c = apcol[a0 + q];
+                double v = apval[a0 + q];
+                unsigned hs = hslot(c, mask);
+                int probes = 0;
+                bool ok = false;
+                while (probes++ < cap) {
+                    int prev = atomicCAS(&keys[hs], -1, c);
+                    if (prev == -1) { vals[hs] = 0.0; ok = true; break; }
+                    if (prev == c) { ok = true; break; }
+                    hs = (hs + 1) & mask;
+                }
+                if (ok) vals[hs] = vals[hs] + r * v;
+                else atomicOr(err, DERR_HASH_OVERFLOW);
+            }
+            __syncwarp();
+        }
+        // compact to the scratch output (unsorted), then rank-sort back into the table
+        int base = uptr[ic];
+        int m = 0;
+        for (int s0 = 0; s0 < cap; s0 += 32) {
+            int s = s0 + lane;
+            bool occ = s < cap && keys[s] >= 0;
+            unsigned msk = __ballot_sync(0xffffffffu, occ);
+            if (occ) {
+                int off = m + __popc(msk & ((1u << lane) - 1u));
+                ucol[base + off] = keys[s];
+                uval[base + off] = vals[s];
+            }
+            m += __popc(msk);
+        }
+        __syncwarp();
+        for (int e = lane; e < m; e += 32) {
+            int ce = ucol[base + e];
+            int rank = 0;
+            for (int f = 0; f < m; ++f) rank += ucol[base + f] < ce;
+            keys[rank] = ce;
+            vals[rank] = uval[base + e];
+        }
+        __syncwarp();
+        double mx = 0.0;
+        for (int e = lane; e < m; e += 32)
+            if (keys[e] != ic) mx = fmax(mx, fabs(vals[e]));
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        double thr = phiA * mx;
+        int kept = 0;
+        for (int e0 = 0; e0 < m; e0 += 32) {
+            int e = e0 + lane;
+            bool k_ = e < m && !(phiA > 0.0 && keys[e] != ic && fabs(vals[e]) < thr);
+            unsigned msk = __ballot_sync(0xffffffffu, k_);
+            if (k_) {
+                int off = kept + __popc(msk & ((1u << lane) - 1u));
+                ucol[base + off] = keys[e];
+                uval[base + off] = vals[e];
+            }
+            kept += __popc(msk);
+        }
+        if (lane == 0) cnt[ic] = kept;
+        __syncwarp();
+    }
+}
+
+__global__ void k_gather_rowdir(int nc, const int *cpts, const int *rowdir, int *rowdir_c) {
+    int ic = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ic < nc) rowdir_c[ic] = rowdir[cpts[ic]];
+}
+
+__global__ void k_rowlen_dir(int n, const int *rowptr, const int *rowdir, long long *nnzdir) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) atomicAdd((unsigned long long *)&nnzdir[rowdir[i]], (unsigned long long)(rowptr[i + 1] - rowptr[i]));
+}
+
+__global__ void k_cast(long long n, const double *a, float *b) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (float)a[i];
+}
+
+__global__ void k_fill_int8(int n, int8_t *a, int8_t v) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = v;
+}
+
+__global__ void k_fill_int(int n, int *a, int v) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = v;
+}
+
+__global__ void k_overflow_list(int nc, const int *cnt, int *flag) {
+    int ic = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ic < nc) flag[ic] = cnt[ic] < 0 ? 1 : 0;
+}
+
+__global__ void k_overflow_rows(int nc, const int *flag, const int *pos, const int *U, int *list, long long *capw) {
+    int ic = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ic >= nc || !flag[ic]) return;
+    int w = pos[ic];
+    list[w] = ic;
+    long long c = 64;
+    while (c < 2LL * U[ic]) c <<= 1;
+    capw[w] = c;
+}
+
+__global__ void k_prefix_ll(int n, long long *v) {
+    // single thread: exclusive prefix in place, v[n] = total (overflow rows are few)
+    if (blockIdx.x || threadIdx.x) return;
+    long long s = 0;
+    for (int i = 0; i < n; ++i) { long long t = v[i]; v[i] = s; s += t; }
+    v[n] = s;
+}
+
+template <class T>
+void d2h(T *h, const T *d, size_t count, cudaStream_t s) {
+    PR_CUDA(cudaMemcpyAsync(h, d, count * sizeof(T), cudaMemcpyDeviceToHost, s));
+    PR_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace
+
+void free_level(Level &L, cudaStream_t s) {
+    void *ptrs[] = {L.rowptr, L.col, L.val, L.val32, L.dinv, L.dinv32, L.cf, L.pmap, L.rowdir, L.cpts,
+                    L.zrowptr, L.zcol, L.zval, L.zval32, L.d_row0, L.d_cseg_row0, L.d_cseg_n,
+                    L.vb, L.vx, L.vxn, L.vy};
+    for (void *p : ptrs) dfree(p, s);
+    L = Level();
+}
+
+static void finish_segments(Hier &h, Level &L) {
+    cudaStream_t s = h.stream;
+    std::vector<int> r0, nn;
+    for (int d = 0; d < h.ndir; ++d)
+        if (L.nrows[d] > 0 && L.coarsest[d]) { r0.push_back(L.row0[d]); nn.push_back(L.nrows[d]); }
+    L.n_cseg = (int)r0.size();
+    if (L.n_cseg) {
+        L.d_cseg_row0 = dmalloc<int>(L.n_cseg, s);
+        L.d_cseg_n = dmalloc<int>(L.n_cseg, s);
+        PR_CUDA(cudaMemcpyAsync(L.d_cseg_row0, r0.data(), sizeof(int) * r0.size(), cudaMemcpyHostToDevice, s));
+        PR_CUDA(cudaMemcpyAsync(L.d_cseg_n, nn.data(), sizeof(int) * nn.size(), cudaMemcpyHostToDevice, s));
+        PR_CUDA(cudaStreamSynchronize(s));
+    }
+}
+
+void build_hierarchy(Hier &h) {
+    cudaStream_t s = h.stream;
+    const air_params &prm = h.prm;
+    const int ND = h.ndir;
+    const int BS = 256;
+    int *d_count = dmalloc<int>(1, s);
+    char *dwork = dmalloc<char>(ND, s);
+    char *dcont = dmalloc<char>(ND, s);
+    int *dnc = dmalloc<int>(ND, s);
+    long long *dnnz = dmalloc<long long>(ND, s);
+    for (int l = 0;; ++l) {
+        Level &L = h.lev[l];
+        int n = L.n;
+        L.dinv = dmalloc<double>(n, s);
+        if (prm.precision == 1) L.dinv32 = dmalloc<float>(n, s);
+        k_dinv<<<blocks_for(n, BS), BS, 0, s>>>(n, L.rowptr, L.col, L.val, L.dinv, L.dinv32);
+        PR_LAUNCH();
+        L.cf = dmalloc<int8_t>(n, s);
+        L.pmap = dmalloc<int>(n, s);
+        // per-matrix stats of this level
+        PR_CUDA(cudaMemsetAsync(dnnz, 0, sizeof(long long) * ND, s));
+        k_rowlen_dir<<<blocks_for(n, BS), BS, 0, s>>>(n, L.rowptr, L.rowdir, dnnz);
+        PR_LAUNCH();
+        std::vector<long long> nnzd(ND);
+        d2h(nnzd.data(), dnnz, ND, s);
+        L.nnzdir.assign(ND, 0);
+        for (int d = 0; d < ND; ++d) L.nnzdir[d] = (int)nnzd[d];
+        L.ncdir.assign(ND, 0);
+        L.nnzZdir.assign(ND, 0);
+        L.singular.assign(ND, 0);
+        L.coarsest.assign(ND, 0);
+        std::vector<char> work(ND, 0);
+        bool any = false;
+        for (int d = 0; d < ND; ++d) {
+            if (L.nrows[d] == 0) continue;
+            bool last = L.nrows[d] <= prm.max_coarse || l >= prm.max_levels - 1 || l >= 63;
+            L.coarsest[d] = last;
+            work[d] = !last;
+            any |= !last;
+        }
+        if (!any) {
+            k_fill_int8<<<blocks_for(n, BS), BS, 0, s>>>(n, L.cf, CF_COARSEST);
+            PR_LAUNCH();
+            k_fill_int<<<blocks_for(n, BS), BS, 0, s>>>(n, L.pmap, -1);
+            PR_LAUNCH();
+            finish_segments(h, L);
+            break;
+        }
+        PR_CUDA(cudaMemcpyAsync(dwork, work.data(), ND, cudaMemcpyHostToDevice, s));
+        long long nnz = L.nnz;
+        uint8_t *S = dmalloc<uint8_t>(nnz, s);
+        k_strength<<<blocks_for(n, BS), BS, 0, s>>>(n, L.rowptr, L.col, L.val, L.rowdir, dwork, prm.theta,
+                                                    prm.eps_R, S);
+        PR_LAUNCH();
+        unsigned *lam = dmalloc<unsigned>(n, s);
+        PR_CUDA(cudaMemsetAsync(lam, 0, sizeof(unsigned) * n, s));
+        k_lambda<<<blocks_for(n, BS), BS, 0, s>>>(n, L.rowptr, L.col, S, lam);
+        PR_LAUNCH();
+        uint64_t *key = dmalloc<uint64_t>(n, s);
+        int8_t *st0 = dmalloc<int8_t>(n, s), *st1 = dmalloc<int8_t>(n, s);
+        int *notmax = dmalloc<int>(n, s);
+        PR_CUDA(cudaMemsetAsync(notmax, 0, sizeof(int) * n, s));
+        PR_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int), s));
+        k_pmis_init<<<blocks_for(n, BS), BS, 0, s>>>(n, L.rowdir, dwork, L.d_row0, lam, l,
+                                                     (unsigned long long)prm.seed, key, st0, d_count);
+        PR_LAUNCH();
+        int und = 0;
+        d2h(&und, d_count, 1, s);
+        int round = 0;
+        while (und > 0) {
+            ++round;
+            PR_REQUIRE(round < 10000, PAIR_ERR_DEVICE, "PMIS did not terminate");
+            k_pmis_mark<<<blocks_for(n, BS), BS, 0, s>>>(n, L.rowptr, L.col, S, key, st0, notmax, round);
+            PR_LAUNCH();
+            PR_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int), s));
+            k_pmis_update<<<blocks_for(n, BS), BS, 0, s>>>(n, L.rowptr, L.col, S, st0, st1, notmax, round, d_count);
+            PR_LAUNCH();
+            std::swap(st0, st1);
+            d2h(&und, d_count, 1, s);
+        }
+        L.pmis_rounds = round;
+        PR_CUDA(cudaMemsetAsync(dnc, 0, sizeof(int) * ND, s));
+        k_count_c<<<blocks_for(n, BS), BS, 0, s>>>(n, L.rowdir, st0, dnc);
+        PR_LAUNCH();
+        std::vector<int> ncd(ND);
+        d2h(ncd.data(), dnc, ND, s);
+        std::vector<char> cont(ND, 0);
+        bool anycont = false;
+        for (int d = 0; d < ND; ++d) {
+            if (!work[d]) continue;
+            int nc_ = ncd[d];
+            bool stall = nc_ == 0 || (double)nc_ >= 0.9 * (double)L.nrows[d];
+            if (stall) L.coarsest[d] = 1;
+            else { cont[d] = 1; anycont = true; L.ncdir[d] = nc_; }
+        }
+        PR_CUDA(cudaMemcpyAsync(dcont, cont.data(), ND, cudaMemcpyHostToDevice, s));
+        int *isC = dmalloc<int>(n, s);
+        int *cidx = dmalloc<int>(n + 1, s);
+        k_cf_final<<<blocks_for(n, BS), BS, 0, s>>>(n, L.rowdir, dcont, st0, L.cf, isC);
+        PR_LAUNCH();
+        long long nct = scan_exclusive(isC, cidx, n, s);
+        dfree(isC, s); dfree(lam, s); dfree(key, s); dfree(st0, s); dfree(st1, s); dfree(notmax, s);
+        if (!anycont || nct == 0) {
+            k_fill_int<<<blocks_for(n, BS), BS, 0, s>>>(n, L.pmap, -1);
+            PR_LAUNCH();
+            dfree(S, s); dfree(cidx, s);
+            finish_segments(h, L);
+            break;
+        }
+        int nc = (int)nct;
+        L.nc = nc;
+        L.cpts = dmalloc<int>(nc, s);
+        k_cpts<<<blocks_for(n, BS), BS, 0, s>>>(n, L.cf, cidx, L.cpts);
+        PR_LAUNCH();
+        k_pmap<<<blocks_for(n, BS), BS, 0, s>>>(n, L.rowptr, L.col, L.val, S, L.cf, cidx, L.pmap);
+        PR_LAUNCH();
+        dfree(cidx, s);
+
+        // ---- lAIR -----------------------------------------------------------
+        int *ncand = dmalloc<int>(nc, s);
+        k_lair_ncand<<<blocks_for(nc, BS), BS, 0, s>>>(nc, L.cpts, L.rowptr, L.col, S, L.cf, prm.distance, ncand);
+        PR_LAUNCH();
+        int *candptr = dmalloc<int>(nc + 1, s);
+        long long ncandt = scan_exclusive(ncand, candptr, nc, s);
+        int *cand = dmalloc<int>(ncandt, s);
+        int *npat = ncand;   // reuse
+        k_lair_pattern<<<blocks_for(nc, BS), BS, 0, s>>>(nc, L.cpts, L.rowptr, L.col, S, L.cf, prm.distance, candptr,
+                                                         cand, npat);
+        PR_LAUNCH();
+        PR_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int), s));
+        k_max_int<<<blocks_for(nc, BS), BS, 0, s>>>(npat, nc, d_count);
+        PR_LAUNCH();
+        int nmax = 0;
+        d2h(&nmax, d_count, 1, s);
+        const int NMAX_LIMIT = 160;
+        PR_REQUIRE(nmax <= NMAX_LIMIT, PAIR_ERR_UNSUPPORTED,
+                   "lAIR local system of size " + std::to_string(nmax) + " exceeds the limit of " +
+                       std::to_string(NMAX_LIMIT) + " (raise eps_R or use distance 1)");
+        int *zr = dmalloc<int>(nc + 1, s);
+        long long nz = scan_exclusive(npat, zr, nc, s);
+        int *zc = dmalloc<int>(nz, s);
+        double *zv = dmalloc<double>(nz, s);
+        int *keep = dmalloc<int>(nc, s);
+        int *dsing = dmalloc<int>(ND, s);
+        PR_CUDA(cudaMemsetAsync(dsing, 0, sizeof(int) * ND, s));
+        {
+            int nm = std::max(nmax, 1);
+            size_t per = ((size_t)nm * nm + 2 * nm) * sizeof(double);
+            int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (200 * 1024) / per));
+            size_t sm = per * wpb;
+            if (sm > 48 * 1024)
+                PR_CUDA(cudaFuncSetAttribute(k_lair_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            unsigned grid = std::min<unsigned>(blocks_for(nc, wpb), 152u * 64u);
+            k_lair_solve<<<grid, 32 * wpb, sm, s>>>(nc, L.cpts, L.rowptr, L.col, L.val, candptr, cand, npat, zr, zc,
+                                                    zv, keep, dsing, L.rowdir, prm.phi_R, nm);
+            PR_LAUNCH();
+        }
+        d2h(L.singular.data(), dsing, ND, s);
+        dfree(dsing, s);
+        int *zr2 = dmalloc<int>(nc + 1, s);
+        long long nz2 = scan_exclusive(keep, zr2, nc, s);
+        if (nz2 != nz) {
+            int *zc2 = dmalloc<int>(nz2, s);
+            double *zv2 = dmalloc<double>(nz2, s);
+            k_compact_rows<<<blocks_for(nc, BS), BS, 0, s>>>(nc, zr, zr2, zc, zv, zc2, zv2);
+            PR_LAUNCH();
+            dfree(zc, s); dfree(zv, s); dfree(zr, s);
+            zc = zc2; zv = zv2;
+        } else {
+            dfree(zr, s);
+        }
+        L.zrowptr = zr2; L.zcol = zc; L.zval = zv; L.nnzZ = nz2;
+        dfree(keep, s); dfree(cand, s); dfree(candptr, s); dfree(ncand, s);
+        dfree(S, s);
+
+        // ---- RAP ------------------------------------------------------------
+        int *aplen = dmalloc<int>(n, s);
+        int *apcol = dmalloc<int>(nnz, s);
+        double *apval = dmalloc<double>(nnz, s);
+        k_ap<<<blocks_for(n, BS), BS, 0, s>>>(n, L.rowptr, L.col, L.val, L.pmap, L.cf, aplen, apcol, apval);
+        PR_LAUNCH();
+        int *U = dmalloc<int>(nc, s);
+        k_rap_bound<<<blocks_for(nc, BS), BS, 0, s>>>(nc, L.cpts, L.zrowptr, L.zcol, aplen, U);
+        PR_LAUNCH();
+        int *uptr = dmalloc<int>(nc + 1, s);
+        long long ut = scan_exclusive(U, uptr, nc, s);
+        int *ucol = dmalloc<int>(ut, s);
+        double *uval = dmalloc<double>(ut, s);
+        int *cnt = dmalloc<int>(nc, s);
+        {
+            const int hcap = 2048, wpb = 4;
+            size_t sm = (size_t)hcap * wpb * (sizeof(double) + sizeof(int));
+            PR_CUDA(cudaFuncSetAttribute(k_rap, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            PR_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int), s));
+            unsigned grid = std::min<unsigned>(blocks_for(nc, wpb), 152u * 32u);
+            k_rap<<<grid, 32 * wpb, sm, s>>>(nc, nullptr, nc, L.cpts, L.zrowptr, L.zcol, L.zval, L.rowptr, aplen,
+                                             apcol, apval, uptr, U, prm.phi_A, cnt, ucol, uval, hcap, nullptr,
+                                             nullptr, nullptr, d_count, h.d_err);
+            PR_LAUNCH();
+            int nover = 0;
+            d2h(&nover, d_count, 1, s);
+            if (nover > 0) {
+                int *flag = dmalloc<int>(nc, s), *pos = dmalloc<int>(nc + 1, s);
+                k_overflow_list<<<blocks_for(nc, BS), BS, 0, s>>>(nc, cnt, flag);
+                PR_LAUNCH();
+                scan_exclusive(flag, pos, nc, s);
+                int *list = dmalloc<int>(nover, s);
+                long long *capw = dmalloc<long long>(nover + 1, s);
+                k_overflow_rows<<<blocks_for(nc, BS), BS, 0, s>>>(nc, flag, pos, U, list, capw);
+                PR_LAUNCH();
+                k_prefix_ll<<<1, 1, 0, s>>>(nover, capw);
+                PR_LAUNCH();
+                long long gtot = 0;
+                d2h(&gtot, capw + nover, 1, s);
+                int *gk = dmalloc<int>(gtot, s);
+                double *gv = dmalloc<double>(gtot, s);
+                k_rap<<<std::min<unsigned>(nover, 152u * 16u), 32, 0, s>>>(
+                    nover, list, nc, L.cpts, L.zrowptr, L.zcol, L.zval, L.rowptr, aplen, apcol, apval, uptr, U,
+                    prm.phi_A, cnt, ucol, uval, 0, capw, gk, gv, d_count, h.d_err);
+                PR_LAUNCH();
+                dfree(gk, s); dfree(gv, s); dfree(list, s); dfree(capw, s); dfree(flag, s); dfree(pos, s);
+            }
+        }
+        Level C;
+        C.n = nc;
+        C.rowptr = dmalloc<int>(nc + 1, s);
+        C.nnz = scan_exclusive(cnt, C.rowptr, nc, s);
+        C.col = dmalloc<int>(C.nnz, s);
+        C.val = dmalloc<double>(C.nnz, s);
+        k_compact_rows<<<blocks_for(nc, BS), BS, 0, s>>>(nc, uptr, C.rowptr, ucol, uval, C.col, C.val);
+        PR_LAUNCH();
+        dfree(ucol, s); dfree(uval, s); dfree(uptr, s); dfree(U, s); dfree(cnt, s);
+        dfree(aplen, s); dfree(apcol, s); dfree(apval, s);
+        C.rowdir = dmalloc<int>(nc, s);
+        k_gather_rowdir<<<blocks_for(nc, BS), BS, 0, s>>>(nc, L.cpts, L.rowdir, C.rowdir);
+        PR_LAUNCH();
+        // nnz of Z per matrix (host, from the coarse row ranges)
+        {
+            std::vector<int> zrh(nc + 1);
+            d2h(zrh.data(), L.zrowptr, nc + 1, s);
+            C.row0.assign(ND, 0);
+            C.nrows.assign(ND, 0);
+            int r = 0;
+            for (int d = 0; d < ND; ++d) {
+                C.row0[d] = r;
+                C.nrows[d] = cont[d] ? L.ncdir[d] : 0;
+                L.nnzZdir[d] = zrh[r + C.nrows[d]] - zrh[r];
+                r += C.nrows[d];
+            }
+        }
+        C.d_row0 = dmalloc<int>(ND, s);
+        PR_CUDA(cudaMemcpyAsync(C.d_row0, C.row0.data(), sizeof(int) * ND, cudaMemcpyHostToDevice, s));
+        finish_segments(h, L);
+        h.lev.push_back(C);
+    }
+    int err = 0;
+    d2h(&err, h.d_err, 1, s);
+    dfree(d_count, s); dfree(dwork, s); dfree(dcont, s); dfree(dnc, s); dfree(dnnz, s);
+    PR_REQUIRE(err == 0, PAIR_ERR_DEVICE, "setup kernel reported device error bits " + std::to_string(err));
+    // FP32 copies for the inner V-cycle
+    if (prm.precision == 1) {
+        for (size_t l = 0; l < h.lev.size(); ++l) {
+            Level &L = h.lev[l];
+            if (!(l == 0 && h.bsr0)) {
+                L.val32 = dmalloc<float>(L.nnz, s);
+                k_cast<<<blocks_for(L.nnz, BS), BS, 0, s>>>(L.nnz, L.val, L.val32);
+                PR_LAUNCH();
+            }
+            if (L.nnzZ) {
+                L.zval32 = dmalloc<float>(L.nnzZ, s);
+                k_cast<<<blocks_for(L.nnzZ, BS), BS, 0, s>>>(L.nnzZ, L.zval, L.zval32);
+                PR_LAUNCH();
+            }
+        }
+    }
+    PR_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace pr

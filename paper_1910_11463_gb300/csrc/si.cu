@@ -1,0 +1,425 @@
+// AIR solve loop and S_N source iteration (Eq. sn_transport, Eq. angular_quad).
+//
+// Each SI iteration, for every direction batch:
+//   b_m = W_m s + g Gin_m,   s_K = (sigma_s,K phi_K + q_K) / (4 pi),  W = D^{-1} M
+//   psi_m = 0; repeat { r = b - A psi (FP64); stop if ||r|| <= tol ||b||;
+//                       psi += V(r) }   (V in FP64 or FP32)
+//   phi^{n+1} += sum_m w_m psi_m  (FP64, directions in fixed order)
+// then ||phi^{n+1} - phi^n|| / ||phi^{n+1}|| closes the iteration.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace pr {
+
+namespace {
+
+constexpr int BS = 256;
+
+__global__ void k_rhs(int n, int ndir, const double *W, const double *Gin, double g, const double *sigma_s,
+                      const double *q, const double *phi, double *b) {
+    long long E = (long long)n * n * n;
+    long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= 8 * E * ndir) return;
+    long long m = tid / (8 * E);
+    long long r = tid % (8 * E);
+    long long e = r >> 3;
+    int a = (int)(r & 7);
+    const double inv4pi = 1.0 / (4.0 * 3.14159265358979323846);
+    double ss = sigma_s[e], qq = q[e];
+    const double *w = W + ((m * E + e) * 8 + a) * 8;
+    const double *ph = phi + 8 * e;
+    double acc = 0.0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc += w[c] * ((ss * ph[c] + qq) * inv4pi);
+    if (Gin) acc += g * Gin[tid];
+    b[tid] = acc;
+}
+
+__global__ void k_phi_acc(long long N, int nd, const double *w, const double *x, double *phinew) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double acc = phinew[i];
+    for (int m = 0; m < nd; ++m) acc += w[m] * x[(long long)m * N + i];
+    phinew[i] = acc;
+}
+
+__global__ void k_diff_partials(long long N, const double *a, const double *b, double *part) {
+    __shared__ double sh[2][32];
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double d2 = 0.0, n2 = 0.0;
+    if (i < N) {
+        double d = a[i] - b[i];
+        d2 = d * d;
+        n2 = a[i] * a[i];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        d2 += __shfl_down_sync(0xffffffffu, d2, o);
+        n2 += __shfl_down_sync(0xffffffffu, n2, o);
+    }
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) { sh[0][w] = d2; sh[1][w] = n2; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s0 = 0, s1 = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { s0 += sh[0][k]; s1 += sh[1][k]; }
+        part[2 * blockIdx.x] = s0;
+        part[2 * blockIdx.x + 1] = s1;
+    }
+}
+
+__global__ void k_diff_final(int nb, const double *part, double *out) {
+    if (blockIdx.x || threadIdx.x) return;
+    double s0 = 0, s1 = 0;
+    for (int k = 0; k < nb; ++k) { s0 += part[2 * k]; s1 += part[2 * k + 1]; }
+    out[0] = sqrt(s0);
+    out[1] = sqrt(s1);
+}
+
+__global__ void k_fill_dir(int *rowdir, long long N, int ndir) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N * ndir) rowdir[i] = (int)(i / N);
+}
+
+}  // namespace
+
+
+// One-time capture of [V-cycle correction; residual] for fixed (b, x, tol).
+static void ensure_graph(Hier &h, const double *b, double *x, double tol) {
+    if (h.graph && h.graph_b == b && h.graph_x == x && h.graph_tol == tol) return;
+    if (h.graph) { cudaGraphExecDestroy(h.graph); h.graph = nullptr; }
+    cudaGraph_t g;
+    PR_CUDA(cudaStreamBeginCapture(h.stream, cudaStreamCaptureModeThreadLocal));
+    try {
+        vcycle_correct(h, x);
+        residual0(h, b, x, tol, true);
+    } catch (...) {
+        cudaGraph_t dummy;
+        cudaStreamEndCapture(h.stream, &dummy);
+        if (dummy) cudaGraphDestroy(dummy);
+        throw;
+    }
+    PR_CUDA(cudaStreamEndCapture(h.stream, &g));
+    PR_CUDA(cudaGraphInstantiate(&h.graph, g, 0));
+    cudaGraphDestroy(g);
+    h.graph_b = b;
+    h.graph_x = x;
+    h.graph_tol = tol;
+}
+
+// Solves every matrix of the hierarchy from the given x to ||b - A x|| <= tol ||b||.
+BatchSolve solve_batch(Hier &h, const double *b, double *x, double tol, int maxit, bool use_graph) {
+    cudaStream_t s = h.stream;
+    int nd = h.ndir;
+    norms0(h, b, h.bnorm);
+    std::vector<int> ones(nd, 1);
+    PR_CUDA(cudaMemcpyAsync(h.active, ones.data(), sizeof(int) * nd, cudaMemcpyHostToDevice, s));
+    residual0(h, b, x, tol, true);
+    std::vector<double> r0(nd), rn(nd), bn(nd);
+    std::vector<int> act(nd), itd(nd, 0);
+    PR_CUDA(cudaMemcpyAsync(r0.data(), h.rnorm, sizeof(double) * nd, cudaMemcpyDeviceToHost, s));
+    PR_CUDA(cudaMemcpyAsync(bn.data(), h.bnorm, sizeof(double) * nd, cudaMemcpyDeviceToHost, s));
+    PR_CUDA(cudaMemcpyAsync(act.data(), h.active, sizeof(int) * nd, cudaMemcpyDeviceToHost, s));
+    PR_CUDA(cudaStreamSynchronize(s));
+    for (int d = 0; d < nd; ++d)
+        if (!std::isfinite(r0[d]) || !std::isfinite(bn[d])) fail(PAIR_ERR_NAN, "NaN/Inf in right-hand side or residual");
+    if (use_graph) ensure_graph(h, b, x, tol);
+    int k = 0;
+    bool any = std::any_of(act.begin(), act.end(), [](int a) { return a != 0; });
+    while (any && k < maxit) {
+        if (use_graph) {
+            PR_CUDA(cudaGraphLaunch(h.graph, s));
+        } else {
+            vcycle_correct(h, x);
+            residual0(h, b, x, tol, true);
+        }
+        ++k;
+        PR_CUDA(cudaMemcpyAsync(act.data(), h.active, sizeof(int) * nd, cudaMemcpyDeviceToHost, s));
+        PR_CUDA(cudaStreamSynchronize(s));
+        any = false;
+        for (int d = 0; d < nd; ++d) {
+            if (act[d]) { any = true; itd[d] = k + 1; }
+            else if (itd[d] == 0) itd[d] = k;
+        }
+    }
+    PR_CUDA(cudaMemcpyAsync(rn.data(), h.rnorm, sizeof(double) * nd, cudaMemcpyDeviceToHost, s));
+    PR_CUDA(cudaStreamSynchronize(s));
+    BatchSolve out;
+    out.iters = k;
+    for (int d = 0; d < nd; ++d) {
+        if (!std::isfinite(rn[d])) fail(PAIR_ERR_NAN, "NaN/Inf in a residual during the AIR solve");
+        double rel = bn[d] > 0 ? rn[d] / bn[d] : 0.0;
+        out.max_rel = std::max(out.max_rel, rel);
+        int kd = std::min(itd[d], k);
+        if (kd > 0 && r0[d] > 0 && rn[d] > 0) {
+            out.rho_sum += std::pow(rn[d] / r0[d], 1.0 / kd);
+            out.rho_cnt++;
+        }
+    }
+    if (any) {
+        char buf[160];
+        snprintf(buf, sizeof buf, "AIR solve reached %d cycles with relative residual %.3e > %.3e", k, out.max_rel,
+                 tol);
+        fail(PAIR_ERR_NOT_CONVERGED, buf);
+    }
+    return out;
+}
+
+Hier::~Hier() {
+    if (graph) cudaGraphExecDestroy(graph);
+    if (stream) {
+        for (auto &L : lev) free_level(L, stream);
+        void *ptrs[] = {bsr64, bsr32, dsign, partials, rnorm, bnorm, rnorm0, active, d_err, d_n0, d_row00};
+        for (void *p : ptrs) dfree(p, stream);
+        cudaStreamSynchronize(stream);
+        cudaStreamDestroy(stream);
+    }
+}
+
+// ---- source iteration ---------------------------------------------------------
+namespace {
+
+__global__ void k_iota_dirs(int nd, long long N, int *row0, int *n0) {
+    int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d < nd) { row0[d] = (int)(d * N); n0[d] = (int)N; }
+}
+
+size_t bytes_per_dir(int n, int precision, bool gin) {
+    size_t E = (size_t)n * n * n, N = 8 * E;
+    double om[3] = {1, 1, 1};
+    size_t nnz0 = (size_t)hex_nnz(n, om);
+    size_t lvl0 = nnz0 * 12 + N * 96 + (precision ? N * 48 : 0) + E * 512 + (gin ? N * 8 : 0);
+    size_t coarse = nnz0 * 12 * 3 / 2 + nnz0 * 8;   // coarse operators, Z, setup scratch
+    size_t vec = N * (8 * 3 + 4 * 8);
+    return lvl0 + coarse + vec;
+}
+
+struct HexBatch {
+    int m0 = 0, nd = 0;
+    Hier *h = nullptr;
+    double *W = nullptr, *Gin = nullptr, *b = nullptr, *xown = nullptr;
+};
+
+void free_batch_ops(HexBatch &B) {
+    if (!B.h) return;
+    cudaStream_t s = B.h->stream;
+    dfree(B.W, s); dfree(B.Gin, s);
+    B.W = B.Gin = nullptr;
+    delete B.h;   // synchronises and destroys its stream
+    B.h = nullptr;
+}
+
+void build_batch(HexBatch &B, int n, const double *omega_h, const double *omega_d, const double *sigma_t,
+                 const air_params &prm, bool gin) {
+    Hier *h = new Hier;
+    B.h = h;
+    PR_CUDA(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    cudaStream_t s = h->stream;
+    int nd = B.nd;
+    long long E = (long long)n * n * n, N = 8 * E;
+    h->ndir = nd;
+    h->prm = prm;
+    h->bsr0 = true;
+    h->hex_n = n;
+    h->n0.assign(nd, (int)N);
+    h->d_err = dmalloc<int>(1, s);
+    PR_CUDA(cudaMemsetAsync(h->d_err, 0, sizeof(int), s));
+    std::vector<int8_t> sg(3 * nd);
+    long long nnz = 0;
+    for (int d = 0; d < nd; ++d) {
+        const double *om = omega_h + 3 * (B.m0 + d);
+        for (int k = 0; k < 3; ++k) sg[3 * d + k] = om[k] > 0 ? 1 : (om[k] < 0 ? -1 : 0);
+        nnz += hex_nnz(n, om);
+    }
+    PR_REQUIRE(nnz < 0x7fffffffLL, PAIR_ERR_UNSUPPORTED, "direction batch exceeds 2^31 stored entries");
+    h->dsign = dmalloc<int8_t>(3 * nd, s);
+    PR_CUDA(cudaMemcpyAsync(h->dsign, sg.data(), 3 * nd, cudaMemcpyHostToDevice, s));
+    h->lev.resize(1);
+    Level &L = h->lev[0];
+    L.n = (int)(N * nd);
+    L.nnz = nnz;
+    L.rowptr = dmalloc<int>(L.n + 1, s);
+    L.col = dmalloc<int>(nnz, s);
+    L.val = dmalloc<double>(nnz, s);
+    L.rowdir = dmalloc<int>(L.n, s);
+    k_fill_dir<<<blocks_for(L.n, BS), BS, 0, s>>>(L.rowdir, N, nd);
+    PR_LAUNCH();
+    L.row0.resize(nd);
+    L.nrows.assign(nd, (int)N);
+    for (int d = 0; d < nd; ++d) L.row0[d] = (int)(d * N);
+    L.d_row0 = dmalloc<int>(nd, s);
+    h->d_row00 = dmalloc<int>(nd, s);
+    h->d_n0 = dmalloc<int>(nd, s);
+    k_iota_dirs<<<blocks_for(nd, 64), 64, 0, s>>>(nd, N, L.d_row0, h->d_n0);
+    PR_LAUNCH();
+    PR_CUDA(cudaMemcpyAsync(h->d_row00, L.d_row0, sizeof(int) * nd, cudaMemcpyDeviceToDevice, s));
+    h->bsr64 = dmalloc<double>((size_t)nd * E * 96, s);
+    if (prm.precision == 1) h->bsr32 = dmalloc<float>((size_t)nd * E * 96, s);
+    B.W = dmalloc<double>((size_t)nd * E * 64, s);
+    if (gin) B.Gin = dmalloc<double>((size_t)nd * N, s);
+    hex_assemble(n, nd, omega_d + 3 * B.m0, sigma_t, L.rowptr, L.col, L.val, h->bsr64, h->bsr32, B.W, B.Gin,
+                 h->d_err, s);
+    build_hierarchy(*h);
+    alloc_cycle_vectors(*h);
+}
+
+}  // namespace
+
+void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t, const double *sigma_s,
+            const double *q, const air_params &prm, const si_params &sp, double *phi, double *psi,
+            cudaStream_t user, si_info *info) {
+    int n = mesh.n, M = quad.M;
+    long long E = (long long)n * n * n, N = 8 * E;
+    PR_CUDA(cudaStreamSynchronize(user));
+    bool gin = sp.g_inflow != 0.0;
+    // direction batches admitted by memory
+    size_t per = bytes_per_dir(n, prm.precision, gin);
+    size_t freeb = 0, totb = 0;
+    PR_CUDA(cudaMemGetInfo(&freeb, &totb));
+    double budget = sp.mem_budget_gb > 0 ? sp.mem_budget_gb * 1e9 : 0.6 * (double)freeb;
+    int B = sp.batch > 0 ? std::min(sp.batch, M) : M;
+    B = std::min<long long>(B, std::max<long long>(1, (long long)(budget / (double)per)));
+    B = (int)std::min<long long>(B, std::max<long long>(1, (0x7fffffffLL / 64) / N));
+    PR_REQUIRE(B >= 1, PAIR_ERR_OOM, "memory budget below one direction hierarchy");
+    int nb = (M + B - 1) / B;
+    bool resident = (double)per * M <= budget;
+    // per-call device state on a private stream
+    cudaStream_t s;
+    PR_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    struct Cleanup {
+        cudaStream_t s;
+        std::vector<HexBatch> *bs;
+        std::vector<void *> bufs;
+        ~Cleanup() {
+            for (auto &b : *bs) {
+                if (b.h) { dfree(b.b, b.h->stream); dfree(b.xown, b.h->stream); }
+                free_batch_ops(b);
+            }
+            for (void *p : bufs) cudaFreeAsync(p, s);
+            cudaStreamSynchronize(s);
+            cudaStreamDestroy(s);
+        }
+    };
+    std::vector<HexBatch> batches(nb);
+    Cleanup cl{s, &batches, {}};
+    double *omega_d = dmalloc<double>(3 * M, s);
+    cl.bufs.push_back(omega_d);
+    PR_CUDA(cudaMemcpyAsync(omega_d, quad.omega, sizeof(double) * 3 * M, cudaMemcpyHostToDevice, s));
+    double *w_d = dmalloc<double>(M, s);
+    cl.bufs.push_back(w_d);
+    PR_CUDA(cudaMemcpyAsync(w_d, quad.w, sizeof(double) * M, cudaMemcpyHostToDevice, s));
+    double *phinew = dmalloc<double>(N, s);
+    cl.bufs.push_back(phinew);
+    int nbk = (int)blocks_for(N, BS);
+    double *part = dmalloc<double>(2 * (size_t)nbk, s);
+    cl.bufs.push_back(part);
+    double *dres = dmalloc<double>(2, s);
+    cl.bufs.push_back(dres);
+    PR_CUDA(cudaStreamSynchronize(s));
+    for (int b = 0; b < nb; ++b) { batches[b].m0 = b * B; batches[b].nd = std::min(B, M - b * B); }
+
+    cudaEvent_t e0, e1;
+    PR_CUDA(cudaEventCreate(&e0));
+    PR_CUDA(cudaEventCreate(&e1));
+    double t_setup = 0, t_solve = 0;
+    int vcycles = 0, levels_max = 0;
+    double max_inner = 0, opc_sum = 0, change = 0;
+    int opc_cnt = 0, it = 0;
+    bool converged = false;
+    auto elapsed = [&](cudaStream_t st) {
+        PR_CUDA(cudaEventRecord(e1, st));
+        PR_CUDA(cudaEventSynchronize(e1));
+        float ms = 0;
+        PR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        return (double)ms;
+    };
+    for (it = 0; it < sp.max_iters; ++it) {
+        PR_CUDA(cudaMemsetAsync(phinew, 0, sizeof(double) * N, s));
+        PR_CUDA(cudaStreamSynchronize(s));
+        for (int bi = 0; bi < nb; ++bi) {
+            HexBatch &Bt = batches[bi];
+            if (!Bt.h) {
+                // setup phase on the batch stream (timed)
+                cudaStream_t tmp;
+                PR_CUDA(cudaStreamCreateWithFlags(&tmp, cudaStreamNonBlocking));
+                PR_CUDA(cudaEventRecord(e0, tmp));
+                PR_CUDA(cudaStreamSynchronize(tmp));
+                build_batch(Bt, n, quad.omega, omega_d, sigma_t, prm, gin);
+                PR_CUDA(cudaStreamSynchronize(Bt.h->stream));
+                PR_CUDA(cudaEventRecord(e1, tmp));
+                PR_CUDA(cudaEventSynchronize(e1));
+                float ms = 0;
+                PR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                t_setup += ms;
+                cudaStreamDestroy(tmp);
+                cudaStream_t hs = Bt.h->stream;
+                Bt.b = dmalloc<double>((size_t)Bt.nd * N, hs);
+                if (!psi) Bt.xown = dmalloc<double>((size_t)Bt.nd * N, hs);
+                Hier &h = *Bt.h;
+                for (int d = 0; d < Bt.nd; ++d) {
+                    int nl = 0;
+                    long long tot = 0;
+                    for (auto &L : h.lev)
+                        if (L.nrows.size() && L.nrows[d] > 0) { ++nl; tot += L.nnzdir[d]; }
+                    levels_max = std::max(levels_max, nl);
+                    opc_sum += (double)tot / (double)h.lev[0].nnzdir[d];
+                    ++opc_cnt;
+                }
+            }
+            Hier &h = *Bt.h;
+            cudaStream_t hs = h.stream;
+            double *x = psi ? psi + (size_t)Bt.m0 * N : Bt.xown;
+            PR_CUDA(cudaEventRecord(e0, hs));
+            k_rhs<<<blocks_for((long long)Bt.nd * N, BS), BS, 0, hs>>>(n, Bt.nd, Bt.W, Bt.Gin, sp.g_inflow, sigma_s, q,
+                                                                      phi, Bt.b);
+            PR_LAUNCH();
+            PR_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * Bt.nd * N, hs));
+            BatchSolve bs = solve_batch(h, Bt.b, x, sp.inner_tol, sp.inner_maxit, sp.use_graphs != 0);
+            vcycles += bs.iters * Bt.nd;
+            max_inner = std::max(max_inner, bs.max_rel);
+            k_phi_acc<<<blocks_for(N, BS), BS, 0, hs>>>(N, Bt.nd, w_d + Bt.m0, x, phinew);
+            PR_LAUNCH();
+            t_solve += elapsed(hs);
+            if (!resident) {
+                dfree(Bt.b, hs); dfree(Bt.xown, hs);
+                Bt.b = Bt.xown = nullptr;
+                free_batch_ops(Bt);
+            }
+        }
+        k_diff_partials<<<nbk, BS, 0, s>>>(N, phinew, phi, part);
+        PR_LAUNCH();
+        k_diff_final<<<1, 1, 0, s>>>(nbk, part, dres);
+        PR_LAUNCH();
+        double hr[2];
+        PR_CUDA(cudaMemcpyAsync(hr, dres, sizeof hr, cudaMemcpyDeviceToHost, s));
+        PR_CUDA(cudaMemcpyAsync(phi, phinew, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+        PR_CUDA(cudaStreamSynchronize(s));
+        change = hr[1] > 0 ? hr[0] / hr[1] : 0.0;
+        if (!std::isfinite(change)) fail(PAIR_ERR_NAN, "NaN/Inf in the scalar flux");
+        if (change <= sp.tol) { converged = true; ++it; break; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (info) {
+        info->si_iters = std::min(it, sp.max_iters);
+        info->si_change = change;
+        info->vcycles = vcycles;
+        info->max_inner_resid = max_inner;
+        info->batches = nb;
+        info->rebuilt = resident ? 0 : 1;
+        info->t_setup_ms = t_setup;
+        info->t_solve_ms = t_solve;
+        info->levels_max = levels_max;
+        info->op_complexity = opc_cnt ? opc_sum / opc_cnt : 0;
+    }
+    if (!converged && sp.max_iters > 1) {
+        char buf[128];
+        snprintf(buf, sizeof buf, "source iteration: %d iterations, change %.3e > %.3e", sp.max_iters, change, sp.tol);
+        fail(PAIR_ERR_NOT_CONVERGED, buf);
+    }
+}
+
+}  // namespace pr

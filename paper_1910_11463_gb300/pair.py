@@ -1,0 +1,294 @@
+"""Python binding of libpair (ctypes).  Argument marshalling only: every step
+runs in the library's CUDA kernels.  PyTorch supplies device memory and the
+current CUDA stream.  The binding fails loudly if the library is missing."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libpair.so")
+
+PAIR_OK = 0
+STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_OOM", -3: "ERR_SINGULAR", -4: "ERR_NOT_CONVERGED",
+          -5: "ERR_COARSEN_STALL", -6: "ERR_NAN", -7: "ERR_DEVICE_TIMEOUT", -8: "ERR_CUDA",
+          -9: "ERR_UNSUPPORTED", -10: "ERR_DEVICE"}
+
+
+class PairError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class air_params(C.Structure):
+    _fields_ = [("distance", C.c_int), ("theta", C.c_double), ("eps_R", C.c_double), ("phi_R", C.c_double),
+                ("phi_A", C.c_double), ("max_levels", C.c_int), ("max_coarse", C.c_int),
+                ("coarse_sweeps", C.c_int), ("seed", C.c_uint64), ("precision", C.c_int)]
+
+
+class pair_csr(C.Structure):
+    _fields_ = [("n", C.c_int), ("nnz", C.c_int), ("rowptr", C.c_void_p), ("col", C.c_void_p),
+                ("val", C.c_void_p)]
+
+
+class pair_level_info(C.Structure):
+    _fields_ = [("n", C.c_int), ("nnz", C.c_int), ("nc", C.c_int), ("nnz_R", C.c_int), ("coarsest", C.c_int),
+                ("pmis_rounds", C.c_int), ("n_singular", C.c_int)]
+
+
+class air_solve_info(C.Structure):
+    _fields_ = [("iters", C.c_int), ("rel_resid", C.c_double), ("rho", C.c_double)]
+
+
+class pair_mesh(C.Structure):
+    _fields_ = [("n", C.c_int)]
+
+
+class pair_quad(C.Structure):
+    _fields_ = [("M", C.c_int), ("omega", C.c_void_p), ("w", C.c_void_p)]
+
+
+class si_params(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_iters", C.c_int), ("inner_tol", C.c_double), ("inner_maxit", C.c_int),
+                ("batch", C.c_int), ("mem_budget_gb", C.c_double), ("g_inflow", C.c_double),
+                ("use_graphs", C.c_int)]
+
+
+class si_info(C.Structure):
+    _fields_ = [("si_iters", C.c_int), ("si_change", C.c_double), ("vcycles", C.c_int),
+                ("max_inner_resid", C.c_double), ("batches", C.c_int), ("rebuilt", C.c_int),
+                ("t_setup_ms", C.c_double), ("t_solve_ms", C.c_double), ("levels_max", C.c_int),
+                ("op_complexity", C.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """Loads libpair.so (built by build.py / __graft_entry__.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libpair.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        vp, i, d = C.c_void_p, C.c_int, C.c_double
+        sig = {
+            "air_params_default": (None, [C.POINTER(air_params)]),
+            "si_params_default": (None, [C.POINTER(si_params)]),
+            "pair_last_error": (C.c_char_p, []),
+            "air_setup": (i, [C.POINTER(pair_csr), i, C.POINTER(air_params), vp, C.POINTER(vp)]),
+            "air_vcycle": (i, [vp, vp, vp, vp]),
+            "air_solve": (i, [vp, vp, vp, d, i, vp, C.POINTER(air_solve_info)]),
+            "air_hier_nlevels": (i, [vp, i, C.POINTER(i)]),
+            "air_level_info": (i, [vp, i, i, C.POINTER(pair_level_info)]),
+            "air_level_export": (i, [vp, i, i] + [vp] * 9),
+            "air_free": (None, [vp]),
+            "dg_hex_nnz": (i, [C.POINTER(pair_mesh), vp, C.POINTER(i)]),
+            "dg_assemble_hex": (i, [C.POINTER(pair_mesh), vp, vp, vp, vp, vp, vp]),
+            "si_solve": (i, [C.POINTER(pair_mesh), C.POINTER(pair_quad), vp, vp, vp, C.POINTER(air_params),
+                             C.POINTER(si_params), vp, vp, vp, C.POINTER(si_info)]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(st: int):
+    if st != PAIR_OK:
+        raise PairError(st, lib().pair_last_error().decode())
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dptr(t: torch.Tensor):
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous(), "device tensors must be contiguous CUDA tensors"
+    return C.c_void_p(t.data_ptr())
+
+
+def _np_ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def default_air_params(**kw) -> air_params:
+    p = air_params()
+    lib().air_params_default(C.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def default_si_params(**kw) -> si_params:
+    p = si_params()
+    lib().si_params_default(C.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+# ---------------------------------------------------------------------------
+# AIR on user matrices
+# ---------------------------------------------------------------------------
+
+@dataclass
+class LevelData:
+    n: int
+    nnz: int
+    nc: int
+    nnz_R: int
+    coarsest: bool
+    pmis_rounds: int
+    n_singular: int
+    rowptr: np.ndarray
+    col: np.ndarray
+    val: np.ndarray
+    cf: np.ndarray | None
+    pmap: np.ndarray | None
+    cpts: np.ndarray | None
+    zrowptr: np.ndarray | None
+    zcol: np.ndarray | None
+    zval: np.ndarray | None
+
+
+class Hierarchy:
+    """AIR hierarchies of a batch of CSR matrices (device tensors).  Vectors
+    passed to vcycle/solve are the concatenation over the batch."""
+
+    def __init__(self, mats, params: air_params | None = None):
+        self.params = params or default_air_params()
+        self._keep = []
+        descs = (pair_csr * len(mats))()
+        for k, (rowptr, col, val) in enumerate(mats):
+            rowptr = rowptr.to(torch.int32).contiguous()
+            col = col.to(torch.int32).contiguous()
+            val = val.to(torch.float64).contiguous()
+            self._keep += [rowptr, col, val]
+            descs[k] = pair_csr(rowptr.numel() - 1, col.numel(), rowptr.data_ptr(), col.data_ptr(), val.data_ptr())
+        self.sizes = [descs[k].n for k in range(len(mats))]
+        self.count = len(mats)
+        h = C.c_void_p()
+        _check(lib().air_setup(descs, len(mats), C.byref(self.params), _stream(), C.byref(h)))
+        self._h = h
+        self._keep = []
+
+    def free(self):
+        if getattr(self, "_h", None):
+            lib().air_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def nlevels(self, mat: int = 0) -> int:
+        v = C.c_int()
+        _check(lib().air_hier_nlevels(self._h, mat, C.byref(v)))
+        return v.value
+
+    def level(self, mat: int, l: int) -> LevelData:
+        inf = pair_level_info()
+        _check(lib().air_level_info(self._h, mat, l, C.byref(inf)))
+        n, nnz, nc, nz = inf.n, inf.nnz, inf.nc, inf.nnz_R
+        rowptr = np.zeros(n + 1, np.int32)
+        col = np.zeros(nnz, np.int32)
+        val = np.zeros(nnz)
+        if inf.coarsest:
+            _check(lib().air_level_export(self._h, mat, l, _np_ptr(rowptr), _np_ptr(col), _np_ptr(val),
+                                          None, None, None, None, None, None))
+            return LevelData(n, nnz, 0, 0, True, inf.pmis_rounds, inf.n_singular, rowptr, col, val,
+                             None, None, None, None, None, None)
+        cf = np.zeros(n, np.int8)
+        pmap = np.zeros(n, np.int32)
+        cpts = np.zeros(nc, np.int32)
+        zr = np.zeros(nc + 1, np.int32)
+        zc = np.zeros(nz, np.int32)
+        zv = np.zeros(nz)
+        _check(lib().air_level_export(self._h, mat, l, _np_ptr(rowptr), _np_ptr(col), _np_ptr(val), _np_ptr(cf),
+                                      _np_ptr(pmap), _np_ptr(cpts), _np_ptr(zr), _np_ptr(zc), _np_ptr(zv)))
+        return LevelData(n, nnz, nc, nz, False, inf.pmis_rounds, inf.n_singular, rowptr, col, val, cf, pmap, cpts,
+                         zr, zc, zv)
+
+    def vcycle(self, b: torch.Tensor, x: torch.Tensor) -> torch.Tensor:
+        _check(lib().air_vcycle(self._h, _dptr(b), _dptr(x), _stream()))
+        return x
+
+    def solve(self, b: torch.Tensor, x: torch.Tensor | None = None, tol: float = 1e-8, maxit: int = 100,
+              raise_on_fail: bool = True):
+        if x is None:
+            x = torch.zeros_like(b)
+        info = air_solve_info()
+        st = lib().air_solve(self._h, _dptr(b), _dptr(x), tol, maxit, _stream(), C.byref(info))
+        if raise_on_fail or st not in (PAIR_OK, -4):
+            _check(st)
+        return x, {"iters": info.iters, "rel_resid": info.rel_resid, "rho": info.rho, "status": st}
+
+
+# ---------------------------------------------------------------------------
+# DG transport
+# ---------------------------------------------------------------------------
+
+def dg_hex_nnz(n: int, omega) -> int:
+    om = np.ascontiguousarray(omega, dtype=np.float64)
+    v = C.c_int()
+    _check(lib().dg_hex_nnz(C.byref(pair_mesh(n)), _np_ptr(om), C.byref(v)))
+    return v.value
+
+
+def dg_assemble_hex(n: int, omega, sigma_t: torch.Tensor):
+    """Block-scaled upwind DG operator of one direction, device CSR tensors."""
+    om = np.ascontiguousarray(omega, dtype=np.float64)
+    nnz = dg_hex_nnz(n, om)
+    dev = sigma_t.device
+    N = 8 * n ** 3
+    rowptr = torch.empty(N + 1, dtype=torch.int32, device=dev)
+    col = torch.empty(nnz, dtype=torch.int32, device=dev)
+    val = torch.empty(nnz, dtype=torch.float64, device=dev)
+    st = sigma_t.to(torch.float64).contiguous()
+    _check(lib().dg_assemble_hex(C.byref(pair_mesh(n)), _np_ptr(om), _dptr(st), _dptr(rowptr), _dptr(col),
+                                 _dptr(val), _stream()))
+    return rowptr, col, val
+
+
+def si_solve(n: int, omega, w, sigma_t, sigma_s, q, air: air_params | None = None, si: si_params | None = None,
+             phi0=None, want_psi: bool = False, device="cuda"):
+    """Source iteration on the n^3 hex mesh.  Cross sections may be CPU or CUDA
+    tensors (CPU inputs are copied to the device and phi is returned on the
+    device).  Returns (phi, psi or None, info dict)."""
+    air = air or default_air_params()
+    si = si or default_si_params()
+    om = np.ascontiguousarray(omega, dtype=np.float64)
+    ww = np.ascontiguousarray(w, dtype=np.float64)
+    M = om.shape[0]
+    N = 8 * n ** 3
+
+    def dev_t(t):
+        t = torch.as_tensor(t, dtype=torch.float64)
+        return t.to(device, non_blocking=True).contiguous()
+
+    st, ss, qq = dev_t(sigma_t), dev_t(sigma_s), dev_t(q)
+    phi = torch.zeros(N, dtype=torch.float64, device=device) if phi0 is None else dev_t(phi0).clone()
+    psi = torch.empty((M, N), dtype=torch.float64, device=device) if want_psi else None
+    info = si_info()
+    quad = pair_quad(M, om.ctypes.data, ww.ctypes.data)
+    rc = lib().si_solve(C.byref(pair_mesh(n)), C.byref(quad), _dptr(st), _dptr(ss), _dptr(qq), C.byref(air),
+                        C.byref(si), _dptr(phi), _dptr(psi) if psi is not None else None, _stream(), C.byref(info))
+    _check(rc)
+    return phi, psi, {f: getattr(info, f) for f, _ in si_info._fields_}
+
+
+def si_solve_problem(prob, **kw):
+    """si_solve on an inputs.HexProblem."""
+    return si_solve(prob.n, prob.omega, prob.w, prob.sigma_t, prob.sigma_s, prob.q, **kw)

@@ -1,0 +1,214 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Bit-exact: scaled DG operator, CF splittings, P maps, R patterns and values,
+Galerkin operator structure and values on every level.  FP64 V-cycle and solves
+within 1e-12 / 1e-10 relative; FP32-refined results within the stated
+tolerances (final FP64 residual <= tol, ||phi - phi_oracle|| / ||phi|| <= 1e-7)."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O
+from paper_1910_11463_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pair():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    from paper_1910_11463_gb300 import pair as P
+    return P
+
+
+def _gpu_csr(pair, n, om, st):
+    return pair.dg_assemble_hex(n, om, torch.as_tensor(st, dtype=torch.float64, device="cuda"))
+
+
+def _cpu(t):
+    return t.cpu().numpy()
+
+
+@pytest.mark.parametrize("n,order,seed", [(8, 2, 0), (5, 4, 3), (3, 8, 9)])
+def test_assembly_bit_exact(pair, n, order, seed):
+    prob = I.small_hex(n, order=order, seed=seed)
+    for m in range(prob.M):
+        r, c, v = O.hex_assemble(n, prob.omega[m], prob.sigma_t)
+        gr, gc, gv = _gpu_csr(pair, n, prob.omega[m], prob.sigma_t)
+        assert np.array_equal(_cpu(gr), r)
+        assert np.array_equal(_cpu(gc), c)
+        assert np.array_equal(_cpu(gv).view(np.uint64), v.view(np.uint64)), f"direction {m}"
+
+
+def _compare_hierarchies(H_o, H_g, mat):
+    lo = H_o.levels()
+    assert H_g.nlevels(mat) == len(lo)
+    for l, Lo in enumerate(lo):
+        Lg = H_g.level(mat, l)
+        assert Lg.n == Lo.n and Lg.coarsest == Lo.coarsest, (mat, l)
+        assert np.array_equal(Lg.rowptr, Lo.rowptr) and np.array_equal(Lg.col, Lo.col), (mat, l)
+        assert np.array_equal(Lg.val.view(np.uint64), Lo.val.view(np.uint64)), (mat, l)
+        if Lo.coarsest:
+            continue
+        assert np.array_equal(Lg.cf, Lo.cf), (mat, l)
+        assert np.array_equal(Lg.pmap, Lo.pmap), (mat, l)
+        assert np.array_equal(Lg.cpts, Lo.cpts), (mat, l)
+        assert np.array_equal(Lg.zrowptr, Lo.zrowptr) and np.array_equal(Lg.zcol, Lo.zcol), (mat, l)
+        assert np.array_equal(Lg.zval.view(np.uint64), Lo.zval.view(np.uint64)), (mat, l)
+        assert Lg.n_singular == Lo.n_singular
+
+
+@pytest.mark.parametrize("distance,phi_R", [(1, 0.0), (2, 0.0), (1, 0.1)])
+def test_setup_bit_exact_batched(pair, distance, phi_R):
+    prob = I.small_hex(8, order=2, seed=1)
+    mats_o, mats_g = [], []
+    for m in range(prob.M):
+        mats_o.append(O.hex_assemble(prob.n, prob.omega[m], prob.sigma_t))
+        mats_g.append(_gpu_csr(pair, prob.n, prob.omega[m], prob.sigma_t))
+    prm_g = pair.default_air_params(distance=distance, phi_R=phi_R, precision=0)
+    prm_o = O.default_params(distance=distance, phi_R=phi_R)
+    H_g = pair.Hierarchy(mats_g, prm_g)
+    for m in range(prob.M):
+        H_o = O.Hierarchy(*mats_o[m], prm_o)
+        _compare_hierarchies(H_o, H_g, m)
+
+
+def test_setup_deterministic_and_batch_independent(pair):
+    prob = I.small_hex(6, order=4, seed=2)
+    mats = [_gpu_csr(pair, prob.n, prob.omega[m], prob.sigma_t) for m in range(6)]
+    H1 = pair.Hierarchy(mats, pair.default_air_params(precision=0))
+    H2 = pair.Hierarchy(mats, pair.default_air_params(precision=0))
+    for m in range(6):
+        Hs = pair.Hierarchy([mats[m]], pair.default_air_params(precision=0))
+        for l in range(H1.nlevels(m)):
+            a, b, c = H1.level(m, l), H2.level(m, l), Hs.level(0, l)
+            for f in ("rowptr", "col", "val", "cf", "pmap", "zcol", "zval"):
+                x, y, z = getattr(a, f), getattr(b, f), getattr(c, f)
+                if x is None:
+                    continue
+                assert np.array_equal(x, y) and np.array_equal(x, z), (m, l, f)
+
+
+def test_chain_generic_csr(pair):
+    n = 300
+    rng = np.random.default_rng(0)
+    sub = -(0.3 + 0.6 * rng.random(n - 1))
+    rowptr = [0]
+    col, val = [], []
+    for i in range(n):
+        if i:
+            col.append(i - 1)
+            val.append(sub[i - 1])
+        col.append(i)
+        val.append(1.0)
+        rowptr.append(len(col))
+    r, c, v = np.array(rowptr, np.int32), np.array(col, np.int32), np.array(val)
+    prm_o = O.default_params(max_coarse=8)
+    prm_g = pair.default_air_params(max_coarse=8, precision=0)
+    H_o = O.Hierarchy(r, c, v, prm_o)
+    dev = [torch.as_tensor(a, device="cuda") for a in (r, c, v)]
+    H_g = pair.Hierarchy([dev], prm_g)
+    _compare_hierarchies(H_o, H_g, 0)
+
+
+def test_vcycle_fp64_matches_oracle(pair):
+    prob = I.small_hex(8, order=2, seed=4)
+    rng = np.random.default_rng(0)
+    mats_o = [O.hex_assemble(prob.n, prob.omega[m], prob.sigma_t) for m in range(prob.M)]
+    mats_g = [_gpu_csr(pair, prob.n, prob.omega[m], prob.sigma_t) for m in range(prob.M)]
+    H_g = pair.Hierarchy(mats_g, pair.default_air_params(precision=0))
+    b = rng.random(prob.M * prob.N)
+    x0 = rng.random(prob.M * prob.N)
+    xg = torch.as_tensor(x0, device="cuda").clone()
+    H_g.vcycle(torch.as_tensor(b, device="cuda"), xg)
+    xg = _cpu(xg)
+    for m in range(prob.M):
+        sl = slice(m * prob.N, (m + 1) * prob.N)
+        H_o = O.Hierarchy(*mats_o[m])
+        xo = H_o.vcycle(b[sl], x0[sl])
+        assert np.linalg.norm(xg[sl] - xo) <= 1e-12 * np.linalg.norm(xo)
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-10)])
+def test_air_solve_equals_sweep(pair, precision, tol):
+    prob = I.small_hex(7, order=2, seed=6)
+    rng = np.random.default_rng(1)
+    mats_o = [O.hex_assemble(prob.n, prob.omega[m], prob.sigma_t) for m in range(prob.M)]
+    mats_g = [_gpu_csr(pair, prob.n, prob.omega[m], prob.sigma_t) for m in range(prob.M)]
+    H_g = pair.Hierarchy(mats_g, pair.default_air_params(precision=precision))
+    b = rng.random(prob.M * prob.N)
+    x, info = H_g.solve(torch.as_tensor(b, device="cuda"), tol=tol, maxit=100)
+    x = _cpu(x)
+    assert info["rel_resid"] <= tol and 0 < info["rho"] < 0.5
+    for m in range(prob.M):
+        sl = slice(m * prob.N, (m + 1) * prob.N)
+        xs, _ = O.sweep(*mats_o[m], b[sl])
+        assert np.linalg.norm(x[sl] - xs) <= 1e-9 * np.linalg.norm(xs)
+
+
+def test_si_fp64_matches_oracle_c1(pair):
+    prob = I.config("hex8_s2")
+    ref, _, info_o = O.si_hex(prob, tol=1e-8, inner_tol=1e-10)
+    phi, psi, info = pair.si_solve_problem(prob, air=pair.default_air_params(precision=0),
+                                           si=pair.default_si_params(tol=1e-8, inner_tol=1e-10), want_psi=True)
+    phi = _cpu(phi)
+    assert info["si_iters"] == info_o["si_iters"]
+    assert np.linalg.norm(phi - ref) <= 1e-10 * np.linalg.norm(ref)
+    assert info["max_inner_resid"] <= 1e-10
+
+
+def test_si_fp32_refined_matches_oracle(pair):
+    prob = I.small_hex(10, order=4, seed=8, ratio=0.8)
+    ref, _, info_o = O.si_hex(prob, tol=1e-10, inner_tol=1e-11)
+    phi, _, info = pair.si_solve_problem(prob, air=pair.default_air_params(precision=1),
+                                         si=pair.default_si_params(tol=1e-10, inner_tol=1e-9))
+    phi = _cpu(phi)
+    assert info["max_inner_resid"] <= 1e-9
+    assert np.linalg.norm(phi - ref) <= 1e-7 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_si_constant_inflow_fixed_point(pair, precision):
+    prob = I.hex_uniform(6, 4, 2.0, 0.75, 1.0)
+    phi_inf = 1.0 / (2.0 - 1.5)
+    phi, _, info = pair.si_solve_problem(prob, air=pair.default_air_params(precision=precision),
+                                         si=pair.default_si_params(tol=1e-12, inner_tol=1e-12,
+                                                                   g_inflow=phi_inf / (4 * math.pi)))
+    assert np.abs(_cpu(phi) - phi_inf).max() < 1e-8
+
+
+@pytest.mark.parametrize("n", [1, 2, 3])
+def test_si_tiny_meshes(pair, n):
+    """Degenerate sizes: one element (no couplings), single-level hierarchies."""
+    prob = I.small_hex(n, order=2, seed=n)
+    ref, _, _ = O.si_hex(prob, tol=1e-10, inner_tol=1e-12)
+    phi, _, info = pair.si_solve_problem(prob, air=pair.default_air_params(precision=0),
+                                         si=pair.default_si_params(tol=1e-10, inner_tol=1e-12))
+    assert np.linalg.norm(_cpu(phi) - ref) <= 1e-9 * np.linalg.norm(ref)
+
+
+def test_batched_si_equals_unbatched(pair):
+    prob = I.small_hex(6, order=4, seed=12)
+    a = pair.default_air_params(precision=0)
+    p1, _, i1 = pair.si_solve_problem(prob, air=a, si=pair.default_si_params(tol=1e-9, inner_tol=1e-11, batch=0))
+    p2, _, i2 = pair.si_solve_problem(prob, air=a, si=pair.default_si_params(tol=1e-9, inner_tol=1e-11, batch=5))
+    assert i2["batches"] == 5
+    assert np.linalg.norm(_cpu(p1) - _cpu(p2)) <= 1e-12 * np.linalg.norm(_cpu(p1))
+
+
+def test_c2_direction_full_size_setup_bit_exact(pair):
+    """Full-size hex32 S4 (262,144 DOFs): assembly and the whole hierarchy of
+    two directions are bit-identical to the oracle's."""
+    prob = I.config("hex32_s4")
+    for m in (0, 13):
+        mo = O.hex_assemble(prob.n, prob.omega[m], prob.sigma_t)
+        mg = _gpu_csr(pair, prob.n, prob.omega[m], prob.sigma_t)
+        assert np.array_equal(_cpu(mg[2]).view(np.uint64), mo[2].view(np.uint64))
+        H_g = pair.Hierarchy([mg], pair.default_air_params(precision=0))
+        _compare_hierarchies(O.Hierarchy(*mo), H_g, 0)
