@@ -23,6 +23,12 @@
 
 #include <stdint.h>
 
+#if defined(__GNUC__)
+#define PAIR_API __attribute__((visibility("default")))
+#else
+#define PAIR_API
+#endif
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -65,7 +71,7 @@ typedef struct {
 
 /* Fills the defaults: distance 1, theta 0.25, eps_R 0.01, phi_R 0, phi_A 0,
  * max_levels 25, max_coarse 100, coarse_sweeps 20, seed 3, precision 1. */
-void air_params_default(air_params *p);
+PAIR_API void air_params_default(air_params *p);
 
 /* A square CSR matrix in device memory. */
 typedef struct {
@@ -109,7 +115,7 @@ typedef struct {
  * Errors: PAIR_ERR_ARG (count < 1, null pointers, n < 1, distance not 1/2),
  * PAIR_ERR_UNSUPPORTED (an lAIR pattern larger than the local-solve limit).
  */
-pair_status air_setup(const pair_csr *A, int count, const air_params *prm, void *stream, pair_hier *out);
+PAIR_API pair_status air_setup(const pair_csr *A, int count, const air_params *prm, void *stream, pair_hier *out);
 
 /* One V-cycle on every matrix of the batch (Sec. 1.2): x <- x + V(b - A x).
  * No pre-relaxation; restrict the residual with R, recurse with zero initial
@@ -118,28 +124,28 @@ pair_status air_setup(const pair_csr *A, int count, const air_params *prm, void 
  * residual is FP64; the cycle runs in the hierarchy's precision.
  *   b, x   concatenation of the right-hand sides / iterates of all matrices
  *          (length = sum of n), x updated in place. */
-pair_status air_vcycle(pair_hier h, const double *b, double *x, void *stream);
+PAIR_API pair_status air_vcycle(pair_hier h, const double *b, double *x, void *stream);
 
 /* Repeats air_vcycle until ||b - A x||_2 <= tol ||b||_2 for every matrix (FP64
  * residual) or maxit cycles (Sec. 2.1 solve loop).  Matrices that converge
  * stop being updated.  'info' (host, may be NULL) receives the totals.
  * Returns PAIR_ERR_NOT_CONVERGED if a matrix misses the tolerance. */
-pair_status air_solve(pair_hier h, const double *b, double *x, double tol, int maxit, void *stream,
+PAIR_API pair_status air_solve(pair_hier h, const double *b, double *x, double tol, int maxit, void *stream,
                       air_solve_info *info);
 
 /* Number of matrices in the batch and levels of matrix 'mat' (host out). */
-pair_status air_hier_nlevels(pair_hier h, int mat, int *nlevels);
-pair_status air_level_info(pair_hier h, int mat, int level, pair_level_info *out);
+PAIR_API pair_status air_hier_nlevels(pair_hier h, int mat, int *nlevels);
+PAIR_API pair_status air_level_info(pair_hier h, int mat, int level, pair_level_info *out);
 
 /* Copies level 'level' of matrix 'mat' to HOST arrays (any may be NULL), with
  * indices local to that matrix: A_l (rowptr n+1, col nnz, val nnz), the CF
  * splitting cf (n bytes: 1 C, 0 F; undefined on the coarsest level), pmap (n:
  * coarse column of P for each row or -1), cpts (nc: fine index of each coarse
  * point) and Z (zrowptr nc+1, zcol nnz_R fine indices, zval nnz_R). */
-pair_status air_level_export(pair_hier h, int mat, int level, int *rowptr, int *col, double *val,
+PAIR_API pair_status air_level_export(pair_hier h, int mat, int level, int *rowptr, int *col, double *val,
                              signed char *cf, int *pmap, int *cpts, int *zrowptr, int *zcol, double *zval);
 
-void air_free(pair_hier h);
+PAIR_API void air_free(pair_hier h);
 
 /* ---------------------------------------------------------------------------
  * Upwind DG transport on the unit cube split into n^3 hexahedra, Q1 elements
@@ -159,7 +165,7 @@ typedef struct {
 /* Stored entries of the block-scaled operator A = D^{-1} L of direction
  * 'omega' (host, 3 doubles): 8 per row for the identity diagonal plus 4 per
  * inflow face with an upwind neighbour (Sec. 1.3). */
-pair_status dg_hex_nnz(const pair_mesh *mesh, const double *omega, int *nnz);
+PAIR_API pair_status dg_hex_nnz(const pair_mesh *mesh, const double *omega, int *nnz);
 
 /* Assembles A = D^{-1} L for one direction (Eq. weak_form_transport, block
  * scaling of Sec. 1.3) into caller-allocated device CSR arrays (rowptr N+1,
@@ -167,7 +173,7 @@ pair_status dg_hex_nnz(const pair_mesh *mesh, const double *omega, int *nnz);
  * diagonal); off-diagonal face blocks D_K^{-1} L_KK' (8 x 4).  FP64, element
  * blocks factored by LU with partial pivoting, no fused multiply-add.
  *   sigma_t  device, n^3 values. */
-pair_status dg_assemble_hex(const pair_mesh *mesh, const double *omega, const double *sigma_t,
+PAIR_API pair_status dg_assemble_hex(const pair_mesh *mesh, const double *omega, const double *sigma_t,
                             int *rowptr, int *col, double *val, void *stream);
 
 /* Source-iteration controls. */
@@ -182,7 +188,7 @@ typedef struct {
     int use_graphs;      /* capture the V-cycle of a batch in a CUDA graph */
 } si_params;
 
-void si_params_default(si_params *p);   /* 1e-8, 500, 1e-8, 100, 0, 0, 0, 1 */
+PAIR_API void si_params_default(si_params *p);   /* 1e-8, 500, 1e-8, 100, 0, 0, 0, 1 */
 
 typedef struct {
     int si_iters;
@@ -206,11 +212,11 @@ typedef struct {
  *   psi      device N*M (direction-major) or NULL
  *   air      AIR parameters (precision selects FP64 or FP32-refined)
  *   info     host, may be NULL. */
-pair_status si_solve(const pair_mesh *mesh, const pair_quad *quad, const double *sigma_t, const double *sigma_s,
+PAIR_API pair_status si_solve(const pair_mesh *mesh, const pair_quad *quad, const double *sigma_t, const double *sigma_s,
                      const double *q, const air_params *air, const si_params *sp, double *phi, double *psi,
                      void *stream, si_info *info);
 
-const char *pair_last_error(void);
+PAIR_API const char *pair_last_error(void);
 
 #ifdef __cplusplus
 }
