@@ -232,20 +232,34 @@ __global__ void k_max_int(const int *v, int n, int *out) {
 
 // Warp per C row.  Shared memory per warp: M (nmax^2 doubles), y (nmax
 // doubles), pattern (nmax ints), pivots (nmax ints).
-__global__ void k_lair_solve(int nc, const int *cpts, const int *rowptr, const int *col, const double *val,
-                             const int *candptr, const int *cand, const int *npat, const int *zrowptr, int *zcol,
-                             double *zval, int *keep, int *nsing_dir, const int *rowdir, double phi_R, int nmax) {
+// Small mode (worklist == null): systems of size <= nmax use shared memory;
+// larger ones are counted in *nbig and left for big mode.  Big mode: rows from
+// worklist, workspace in global memory at gbuf + goff[w].
+__global__ void k_lair_solve(int nwork, const int *worklist, const int *cpts, const int *rowptr, const int *col,
+                             const double *val, const int *candptr, const int *cand, const int *npat,
+                             const int *zrowptr, int *zcol, double *zval, int *keep, int *nsing_dir,
+                             const int *rowdir, double phi_R, int nmax, const long long *goff, double *gbuf,
+                             int *nbig) {
     extern __shared__ double smem[];
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int wpb = blockDim.x >> 5;
-    size_t per = (size_t)nmax * nmax + nmax + nmax;   // doubles (ints packed into the tail)
-    double *M = smem + warp * per;
-    double *y = M + (size_t)nmax * nmax;
-    int *pat = (int *)(y + nmax);
-    int *piv = pat + nmax;
-    for (int ic = blockIdx.x * wpb + warp; ic < nc; ic += gridDim.x * wpb) {
+    for (int w = blockIdx.x * wpb + warp; w < nwork; w += gridDim.x * wpb) {
+        int ic = worklist ? worklist[w] : w;
         int i = cpts[ic];
         int np = npat[ic];
+        double *M;
+        if (worklist) {
+            M = gbuf + goff[w];
+        } else {
+            if (np > nmax) {
+                if (lane == 0) { keep[ic] = -1; atomicAdd(nbig, 1); }
+                continue;
+            }
+            M = smem + (size_t)warp * ((size_t)nmax * nmax + 2 * nmax);
+        }
+        double *y = M + (size_t)np * np;
+        int *pat = (int *)(y + np);
+        int *piv = pat + np;
         const int *cp = cand + candptr[ic];
         for (int t = lane; t < np; t += 32) pat[t] = cp[t];
         __syncwarp();
@@ -527,6 +541,15 @@ __global__ void k_overflow_rows(int nc, const int *flag, const int *pos, const i
     capw[w] = c;
 }
 
+__global__ void k_big_rows(int nc, const int *flag, const int *pos, const int *npat, int *list, long long *goff) {
+    int ic = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ic >= nc || !flag[ic]) return;
+    int w = pos[ic];
+    long long np = npat[ic];
+    list[w] = ic;
+    goff[w] = np * np + 2 * np;
+}
+
 __global__ void k_prefix_ll(int n, long long *v) {
     // single thread: exclusive prefix in place, v[n] = total (overflow rows are few)
     if (blockIdx.x || threadIdx.x) return;
@@ -700,10 +723,6 @@ void build_hierarchy(Hier &h) {
         PR_LAUNCH();
         int nmax = 0;
         d2h(&nmax, d_count, 1, s);
-        const int NMAX_LIMIT = 160;
-        PR_REQUIRE(nmax <= NMAX_LIMIT, PAIR_ERR_UNSUPPORTED,
-                   "lAIR local system of size " + std::to_string(nmax) + " exceeds the limit of " +
-                       std::to_string(NMAX_LIMIT) + " (raise eps_R or use distance 1)");
         int *zr = dmalloc<int>(nc + 1, s);
         long long nz = scan_exclusive(npat, zr, nc, s);
         int *zc = dmalloc<int>(nz, s);
@@ -712,16 +731,41 @@ void build_hierarchy(Hier &h) {
         int *dsing = dmalloc<int>(ND, s);
         PR_CUDA(cudaMemsetAsync(dsing, 0, sizeof(int) * ND, s));
         {
-            int nm = std::max(nmax, 1);
+            const int NSMALL = 64;
+            int nm = std::max(1, std::min(nmax, NSMALL));
             size_t per = ((size_t)nm * nm + 2 * nm) * sizeof(double);
             int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (200 * 1024) / per));
             size_t sm = per * wpb;
             if (sm > 48 * 1024)
                 PR_CUDA(cudaFuncSetAttribute(k_lair_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            PR_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int), s));
             unsigned grid = std::min<unsigned>(blocks_for(nc, wpb), 152u * 64u);
-            k_lair_solve<<<grid, 32 * wpb, sm, s>>>(nc, L.cpts, L.rowptr, L.col, L.val, candptr, cand, npat, zr, zc,
-                                                    zv, keep, dsing, L.rowdir, prm.phi_R, nm);
+            k_lair_solve<<<grid, 32 * wpb, sm, s>>>(nc, nullptr, L.cpts, L.rowptr, L.col, L.val, candptr, cand, npat,
+                                                    zr, zc, zv, keep, dsing, L.rowdir, prm.phi_R, nm, nullptr,
+                                                    nullptr, d_count);
             PR_LAUNCH();
+            int nbig = 0;
+            d2h(&nbig, d_count, 1, s);
+            if (nbig > 0) {
+                int *flag = dmalloc<int>(nc, s), *pos = dmalloc<int>(nc + 1, s);
+                k_overflow_list<<<blocks_for(nc, BS), BS, 0, s>>>(nc, keep, flag);
+                PR_LAUNCH();
+                scan_exclusive(flag, pos, nc, s);
+                int *list = dmalloc<int>(nbig, s);
+                long long *goff = dmalloc<long long>(nbig + 1, s);
+                k_big_rows<<<blocks_for(nc, BS), BS, 0, s>>>(nc, flag, pos, npat, list, goff);
+                PR_LAUNCH();
+                k_prefix_ll<<<1, 1, 0, s>>>(nbig, goff);
+                PR_LAUNCH();
+                long long gtot = 0;
+                d2h(&gtot, goff + nbig, 1, s);
+                double *gbuf = dmalloc<double>(gtot, s);
+                k_lair_solve<<<std::min<unsigned>(nbig, 152u * 16u), 32, 0, s>>>(
+                    nbig, list, L.cpts, L.rowptr, L.col, L.val, candptr, cand, npat, zr, zc, zv, keep, dsing,
+                    L.rowdir, prm.phi_R, nmax, goff, gbuf, d_count);
+                PR_LAUNCH();
+                dfree(gbuf, s); dfree(goff, s); dfree(list, s); dfree(flag, s); dfree(pos, s);
+            }
         }
         d2h(L.singular.data(), dsing, ND, s);
         dfree(dsing, s);
