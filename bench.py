@@ -1,0 +1,357 @@
+#!/usr/bin/env python
+"""Benchmark: pAIR source iteration for upwind-DG S_N transport on one GB300.
+
+Metric: DOF*directions solved per second per source iteration, every
+direction's AIR solve reaching a relative FP64 residual of 1e-8.
+
+Workload (default): unit cube, 32^3 hexahedra, trilinear Q1 upwind DG
+(262,144 DOFs per direction), level-symmetric S4 (24 directions) in one
+batch, sigma_t ~ U[0.5, 2] per element (SplitMix64 seed 1), sigma_s = 0.8
+sigma_t, q = 1, vacuum boundaries.  Synthetic, seeded inputs.
+
+One timed step = one full pass of the path from resident inputs: DG assembly
+and block scaling of all directions, AIR setup of every hierarchy (strength,
+PMIS, one-point P, lAIR, Galerkin RAP), then one source iteration (right-hand
+sides, every direction solved from psi = 0 to 1e-8 with FP32 V-cycles under
+FP64 iterative refinement, scalar-flux quadrature sum).  Hierarchies are
+rebuilt every step, as in the paper's memory mode.  Each step moves well over
+1 GB, far more than the 129 MB L2, so no explicit flush is needed between steps.
+
+--impl reference times the CPU oracle (the plain C implementation the tests
+check against) on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DOF*directions solved/s per source iteration (AIR to 1e-8 FP64 residual)"
+UNIT = "DOF*dir/s"
+WORKLOADS = {
+    "hex32_s4": "unit cube 32^3 hex Q1 upwind DG (262,144 DOFs/dir), S4 level-symmetric (24 dirs) in one batch, "
+                "sigma_t~U[0.5,2] seed 1, sigma_s=0.8 sigma_t, q=1, vacuum",
+    "hex8_s2": "unit cube 8^3 hex Q1 upwind DG (4,096 DOFs/dir), S2 (8 dirs), sigma_t=1, sigma_s=0.5, q=1, vacuum",
+    "hex24_s4_adj": "unit cube 24^3 hex Q1 (110,592 DOFs/dir), S4 (24 dirs), sigma_t~U[0.5,2], sigma_s=0.7 sigma_t, "
+                    "q=1 in central 8^3",
+    "hex64_s8": "unit cube 64^3 hex Q1 (2,097,152 DOFs/dir), S8 (80 dirs) in HBM-admitted batches, "
+                "sigma_t~logU[0.1,100], sigma_s=0.95 sigma_t, q=1",
+}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.out = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.out.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons, power = [], None, set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.out:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+def cpu_baseline_oracle(prob, max_seconds: float = 20.0, min_dirs: int = 1):
+    """The CPU oracle, as it stands, on the host: one source-iteration step
+    (assembly, AIR setup and a 1e-8 solve of every sampled direction, scalar
+    flux sum) over as many directions as fit the time bound."""
+    from oracle import oracle as O
+    from paper_1910_11463_gb300 import inputs as I
+    O.build()
+    done, t_total = 0, 0.0
+    while done < prob.M:
+        sub = I.HexProblem(prob.name, prob.n, prob.omega[done:done + 1].copy(), prob.w[done:done + 1].copy(),
+                           prob.sigma_t, prob.sigma_s, prob.q)
+        t0 = time.perf_counter()
+        O.si_hex(sub, tol=1e-8, max_iters=1, inner_tol=1e-8, inner_maxit=500)
+        t_total += time.perf_counter() - t0
+        done += 1
+        if done >= min_dirs and t_total >= max_seconds:
+            break
+    return {"value": prob.N * done / t_total, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{done} of {prob.M} directions of the same workload, one SI step each "
+                      f"(assembly + AIR setup + 1e-8 solve + phi sum), single-threaded C oracle, {t_total:.2f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1910_11463_gb300 import inputs as I
+    prob = I.config(args.config)
+    # each step: one direction of the workload through the oracle (bounded CPU sample)
+    from oracle import oracle as O
+    O.build()
+    times = []
+    for k in range(args.warmup + args.steps):
+        m = k % prob.M
+        sub = I.HexProblem(prob.name, prob.n, prob.omega[m:m + 1].copy(), prob.w[m:m + 1].copy(),
+                           prob.sigma_t, prob.sigma_s, prob.q)
+        t0 = time.perf_counter()
+        O.si_hex(sub, tol=1e-8, max_iters=1, inner_tol=1e-8, inner_maxit=500)
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    value = prob.N / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.config + ": " + WORKLOADS[args.config],
+                       "step": "one direction of the workload per step: assembly + AIR setup + 1e-8 solve + phi sum"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} timed directions (after {args.warmup} warm-up), "
+                                       "single-threaded C oracle"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__ as g
+    rank, world, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    g.build()
+    from paper_1910_11463_gb300 import inputs as I
+    from paper_1910_11463_gb300 import pair
+
+    prob = I.config(args.config)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    st = torch.as_tensor(prob.sigma_t, device=dev)
+    ss = torch.as_tensor(prob.sigma_s, device=dev)
+    qq = torch.as_tensor(prob.q, device=dev)
+    N, M = prob.N, prob.M
+    air = pair.default_air_params(precision=args.precision)
+    si = pair.default_si_params(tol=1e-8, max_iters=1, inner_tol=1e-8, inner_maxit=200)
+    phi = torch.zeros(N, dtype=torch.float64, device=dev)
+    quad = (prob.omega, prob.w)
+
+    def step(phi_in, air_p, si_p):
+        out, _, info = pair.si_solve(prob.n, quad[0], quad[1], st, ss, qq, air=air_p, si=si_p, phi0=phi_in)
+        return out, info
+
+    # warm-up: the SI continues from step to step (phi^n -> phi^{n+1})
+    for _ in range(args.warmup):
+        phi, info = step(phi, air, si)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    infos = []
+    clocks = ClockSampler(torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = pair.kernel_launches()
+    clocks.start()
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        phi, info = step(phi, air, si)
+        infos.append(info)
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    launches = pair.kernel_launches() - launches0
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = N * M * world / (ms * 1e-3)
+
+    # phase split and level-0 kernel roofline from the library's device events
+    def tot(key):
+        return sum(i[key] for i in infos)
+    t_setup, t_solve = tot("t_setup_ms") / args.steps, tot("t_solve_ms") / args.steps
+    phases = [sum(i["t_setup_phase_ms"][k] for i in infos) / args.steps for k in range(4)]
+    peak, peak_kind = measured_peaks()
+    kern = {
+        "k_res0_bsr (FP64 outer residual, level 0)": (tot("t_res0_ms"), tot("n_res0"), tot("gb_res0")),
+        "k_relax_bsr (FP32 F-F-C Jacobi, level 0)": (tot("t_relax0_ms"), tot("n_relax0"), tot("gb_relax0")),
+    }
+    rl = {}
+    for name, (t_ms, n_l, gb) in kern.items():
+        rl[name] = {"achieved": gb / (t_ms * 1e-3) if t_ms > 0 else None, "launches": n_l,
+                    "ms_per_launch": t_ms / max(n_l, 1), "gb_per_launch": gb / max(n_l, 1),
+                    "share_of_step": t_ms / args.steps / ms}
+    dom = max(rl, key=lambda k: rl[k]["share_of_step"])
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tfile):
+        with open(tfile) as f:
+            tj = json.load(f)
+        entry = tj.get(dom.split()[0])
+        if entry and entry.get("source_sha") == pair.kernel_source_sha(entry.get("source", "cycle.cu")):
+            traffic = entry["bytes_per_launch"] * (rl[dom]["gb_per_launch"] / entry["gb_per_launch_at_capture"])
+    achieved = rl[dom]["achieved"]
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None, "traffic": traffic,
+                "kernel": dom, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs copy test)",
+                "algorithmic_bytes": "per launch: FP64 face-block rows + b, psi read + r written (residual); "
+                                     "see DESIGN.md",
+                "kernels": rl}
+
+    # e2e: the same step through the public API with host buffers (pinned),
+    # copies in and phi back to the host inside the timed region
+    h_st = torch.as_tensor(prob.sigma_t).pin_memory()
+    h_ss = torch.as_tensor(prob.sigma_s).pin_memory()
+    h_q = torch.as_tensor(prob.q).pin_memory()
+    h_phi = phi.cpu().pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier()
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        out, _, _ = pair.si_solve(prob.n, quad[0], quad[1], h_st, h_ss, h_q, air=air, si=si, phi0=h_phi)
+        h_phi = out.cpu()
+    e1.record(stream)
+    barrier()
+    ms_e2e = e0.elapsed_time(e1) / e2e_steps
+    e2e = {"value": N * M * world / (ms_e2e * 1e-3), "unit": UNIT,
+           "h2d_bytes_per_step": 3 * prob.E * 8 + N * 8, "d2h_bytes_per_step": N * 8,
+           "ms_per_step": ms_e2e}
+
+    # comparator: plain FP64 pAIR, one direction at a time, no graphs (same GPU)
+    fp64 = None
+    if not args.no_fp64_baseline:
+        air64 = pair.default_air_params(precision=0)
+        si64 = pair.default_si_params(tol=1e-8, max_iters=1, inner_tol=1e-8, inner_maxit=200, batch=1,
+                                      use_graphs=0)
+        step(phi, air64, si64)
+        barrier()
+        e0.record(stream)
+        _, i64 = step(phi, air64, si64)
+        e1.record(stream)
+        barrier()
+        ms64 = e0.elapsed_time(e1)
+        fp64 = {"value": N * M / (ms64 * 1e-3), "ms_per_step": ms64, "setup_ms": i64["t_setup_ms"],
+                "solve_ms": i64["t_solve_ms"], "vcycles": i64["vcycles"],
+                "speedup_of_fp32_refined_batched": (N * M / (ms * 1e-3)) / (N * M / (ms64 * 1e-3))}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+    last = infos[-1]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 V-cycle + f64 residual/setup" if args.precision else "f64",
+        "data": "synthetic",
+        "config": {"workload": args.config + ": " + WORKLOADS[args.config],
+                   "step": "assembly + AIR setup (rebuilt each step) + 1 source iteration, all directions solved "
+                           "from psi=0 to 1e-8 relative FP64 residual",
+                   "l2": "working set per step > 1 GB >> 129 MB L2 (no flush needed)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU, all directions in one batch",
+                   "precision": "FP32 hierarchy/V-cycle, FP64 refinement" if args.precision else "FP64"},
+        "solve_only": {"value": N * M / (t_solve * 1e-3), "ms_per_step": t_solve,
+                       "note": "RHS + solves + phi sum with resident hierarchies"},
+        "setup_ms": t_setup, "setup_phase_ms": {"strength+pmis": phases[0], "p+lair": phases[1],
+                                                "rap": phases[2], "assembly+other": phases[3]},
+        "vcycles_per_direction": last["vcycles"] / M, "levels": last["levels_max"],
+        "op_complexity": last["op_complexity"], "max_inner_resid": last["max_inner_resid"],
+        "roofline": roofline, "clocks": clk, "e2e": e2e, "gpu_launches": launches,
+        "fp64_one_direction": fp64,
+    }
+    if world == 1 or rank == 0:
+        line["cpu_baseline"] = cpu_baseline_oracle(prob, max_seconds=args.cpu_seconds) if not args.no_cpu else None
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", default="hex32_s4", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", type=int, default=1, choices=[0, 1])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp64-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)   # timing rule: at least three untimed warm-up steps
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

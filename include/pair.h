@@ -60,17 +60,21 @@ typedef struct pair_hier_s *pair_hier;
  *  coarse_sweeps pointwise Jacobi sweeps on the coarsest level
  *  seed          PMIS key hash seed
  *  precision     0: hierarchy values and V-cycle in FP64;
- *                1: FP32 hierarchy and V-cycle under FP64 iterative refinement */
+ *                1: FP32 hierarchy and V-cycle under FP64 iterative refinement
+ *  f_sweeps      F-point Jacobi sweeps of the post-relaxation before its C-point
+ *                sweep (1: F-C, 2: F-F-C) */
 typedef struct {
     int distance;
     double theta, eps_R, phi_R, phi_A;
     int max_levels, max_coarse, coarse_sweeps;
     uint64_t seed;
     int precision;
+    int f_sweeps;
 } air_params;
 
 /* Fills the defaults: distance 1, theta 0.25, eps_R 0.01, phi_R 0, phi_A 0,
- * max_levels 25, max_coarse 100, coarse_sweeps 20, seed 3, precision 1. */
+ * max_levels 25, max_coarse 100, coarse_sweeps 20, seed 3, precision 1,
+ * f_sweeps 2. */
 PAIR_API void air_params_default(air_params *p);
 
 /* A square CSR matrix in device memory. */
@@ -119,8 +123,9 @@ PAIR_API pair_status air_setup(const pair_csr *A, int count, const air_params *p
 
 /* One V-cycle on every matrix of the batch (Sec. 1.2): x <- x + V(b - A x).
  * No pre-relaxation; restrict the residual with R, recurse with zero initial
- * guess, prolong with P (one-point), post-relax F-Jacobi then C-Jacobi
- * (omega = 1); coarsest level: coarse_sweeps Jacobi sweeps.  The level-0
+ * guess, prolong with P (one-point), post-relax with f_sweeps F-Jacobi sweeps
+ * then one C-Jacobi sweep (omega = 1); coarsest level: coarse_sweeps Jacobi
+ * sweeps.  The level-0
  * residual is FP64; the cycle runs in the hierarchy's precision.
  *   b, x   concatenation of the right-hand sides / iterates of all matrices
  *          (length = sum of n), x updated in place. */
@@ -201,6 +206,15 @@ typedef struct {
     double t_solve_ms;       /* RHS build + solves + scalar-flux sums (device events) */
     int levels_max;          /* deepest hierarchy */
     double op_complexity;    /* sum_l nnz(A_l) / nnz(A_0), mean over directions */
+    /* device-event timings of the level-0 kernels and their algorithmic traffic
+     * (bytes the method must move: operator entries, vectors read and written) */
+    double t_res0_ms;        /* FP64 residual r = b - A psi, all launches */
+    int n_res0;
+    double gb_res0;          /* algorithmic GB over those launches */
+    double t_relax0_ms;      /* level-0 F- and C-Jacobi passes, all launches */
+    int n_relax0;
+    double gb_relax0;
+    double t_setup_phase_ms[4]; /* strength+PMIS, P+lAIR, Galerkin RAP, other setup */
 } si_info;
 
 /* Source iteration (Eq. sn_transport with Eq. angular_quad): each iteration
@@ -217,6 +231,11 @@ PAIR_API pair_status si_solve(const pair_mesh *mesh, const pair_quad *quad, cons
                      void *stream, si_info *info);
 
 PAIR_API const char *pair_last_error(void);
+
+/* Library kernels launched so far by this process (graph replays count each
+ * captured kernel once per replay).  Instrumentation for benchmarks; not
+ * thread-safe with concurrent library calls. */
+PAIR_API long long pair_kernel_launches(void);
 
 #ifdef __cplusplus
 }

@@ -29,8 +29,9 @@
  *   of SplitMix64 at state seed ^ (level << 40) ^ i; lambda_i = 0 -> F;
  *   one-point P takes the strongest C neighbour (first maximum);
  *   distance-2 pattern = strong F neighbours of the distance-1 pattern;
- *   V-cycle: no pre-relaxation, post F- then C-Jacobi, coarsest 'coarse_sweeps'
- *   Jacobi sweeps.
+ *   V-cycle: no pre-relaxation; post-relaxation f_sweeps F-Jacobi sweeps then one
+ *   C-Jacobi sweep (default 2: the F-F-C ordering usual for AIR); coarsest level
+ *   'coarse_sweeps' Jacobi sweeps.
  */
 #include <math.h>
 #include <stdint.h>
@@ -456,6 +457,7 @@ typedef struct {
     double theta, eps_R, phi_R, phi_A;
     int max_levels, max_coarse, coarse_sweeps;
     uint64_t seed;
+    int f_sweeps;   /* F-Jacobi sweeps before the C-Jacobi sweep (1: FC, 2: FFC) */
 } or_params;
 
 typedef struct {
@@ -763,7 +765,7 @@ void or_hier_free(void *hp)
 void or_params_default(or_params *p)
 {
     p->distance = 1; p->theta = 0.25; p->eps_R = 0.01; p->phi_R = 0.0; p->phi_A = 0.0;
-    p->max_levels = 25; p->max_coarse = 100; p->coarse_sweeps = 20; p->seed = 3;
+    p->max_levels = 25; p->max_coarse = 100; p->coarse_sweeps = 20; p->seed = 3; p->f_sweeps = 2;
 }
 
 /* AIR setup on a CSR matrix with sorted columns (copied). */
@@ -896,9 +898,11 @@ static void vcycle_level(const ohier *H, int l, const double *b, double *x)
     vcycle_level(H, l + 1, bc, xc);
     /* one-point prolongation: x_i += xc[pmap(i)] */
     for (int i = 0; i < n; ++i) if (L->pmap[i] >= 0) x[i] = x[i] + xc[L->pmap[i]];
-    /* post-relaxation: F-Jacobi then C-Jacobi (omega = 1) */
-    residual(L, b, x, r);
-    for (int i = 0; i < n; ++i) if (L->cf[i] == 0) x[i] = x[i] + L->dinv[i] * r[i];
+    /* post-relaxation: f_sweeps F-Jacobi sweeps, then C-Jacobi (omega = 1) */
+    for (int s = 0; s < H->prm.f_sweeps; ++s) {
+        residual(L, b, x, r);
+        for (int i = 0; i < n; ++i) if (L->cf[i] == 0) x[i] = x[i] + L->dinv[i] * r[i];
+    }
     residual(L, b, x, r);
     for (int i = 0; i < n; ++i) if (L->cf[i] == 1) x[i] = x[i] + L->dinv[i] * r[i];
     free(r); free(bc); free(xc);

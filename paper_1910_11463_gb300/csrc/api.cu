@@ -46,6 +46,7 @@ void check_params(const air_params *p) {
     PR_REQUIRE(p->max_levels >= 1 && p->max_coarse >= 1 && p->coarse_sweeps >= 0, PAIR_ERR_ARG,
                "max_levels, max_coarse must be >= 1 and coarse_sweeps >= 0");
     PR_REQUIRE(p->precision == 0 || p->precision == 1, PAIR_ERR_ARG, "precision must be 0 (FP64) or 1 (FP32)");
+    PR_REQUIRE(p->f_sweeps >= 1 && p->f_sweeps <= 8, PAIR_ERR_ARG, "f_sweeps must lie in [1, 8]");
 }
 
 __global__ void k_concat_rowptr(int n, const int *in, int *out, int off) {
@@ -93,6 +94,7 @@ void air_params_default(air_params *p) {
     p->coarse_sweeps = 20;
     p->seed = 3;
     p->precision = 1;
+    p->f_sweeps = 2;
 }
 
 void si_params_default(si_params *p) {
@@ -108,6 +110,8 @@ void si_params_default(si_params *p) {
 }
 
 const char *pair_last_error(void) { return g_last_error.c_str(); }
+
+long long pair_kernel_launches(void) { return pr::g_launches; }
 
 pair_status air_setup(const pair_csr *A, int count, const air_params *prm, void *stream, pair_hier *out) {
     return guarded([&] {

@@ -19,7 +19,10 @@ struct Error {
 void cuda_check(cudaError_t e, const char *what, const char *file, int line);
 
 #define PR_CUDA(call) ::pr::cuda_check((call), #call, __FILE__, __LINE__)
-#define PR_LAUNCH() ::pr::cuda_check(cudaGetLastError(), "kernel launch", __FILE__, __LINE__)
+// Every kernel launch of the library is followed by PR_LAUNCH(), which also
+// counts it (launches recorded while capturing a graph are counted per replay).
+extern long long g_launches;
+#define PR_LAUNCH() (++::pr::g_launches, ::pr::cuda_check(cudaGetLastError(), "kernel launch", __FILE__, __LINE__))
 #define PR_REQUIRE(cond, st, msg) \
     do {                          \
         if (!(cond)) ::pr::fail((st), (msg)); \
@@ -110,7 +113,16 @@ struct Hier {
     int *active = nullptr;                                         // [dir]
     int *d_err = nullptr;
     int *d_n0 = nullptr, *d_row00 = nullptr;  // level-0 rows per matrix and first rows
+    // instrumentation: CUDA events around the level-0 kernels (also inside graphs)
+    bool prof = false;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    double t_res0 = 0, t_relax0 = 0, gb_res0 = 0, gb_relax0 = 0;
+    long long n_res0 = 0, n_relax0 = 0;
+    // per matrix: level-0 algorithmic bytes of one residual / one F+C relaxation pass
+    std::vector<double> bytes_res0, bytes_relax0;
+    double t_phase[4] = {0, 0, 0, 0};   // setup: strength+PMIS, P+lAIR, RAP, other
     cudaGraphExec_t graph = nullptr;
+    long long graph_kernels = 0;
     const double *graph_b = nullptr;
     double *graph_x = nullptr;
     double graph_tol = -1;
@@ -127,6 +139,8 @@ void residual0(Hier &h, const double *b, const double *x, double tol, bool updat
 void vcycle_correct(Hier &h, double *x);       // x += V(lev[0].vb), zero initial guess
 void norms0(Hier &h, const double *v, double *out);  // per-matrix 2-norms of a level-0 vector
 void alloc_cycle_vectors(Hier &h);
+void level0_bytes(Hier &h);   // fills bytes_res0 / bytes_relax0 (hex block form)
+void prof_enable(Hier &h);
 
 // assemble.cu
 void hex_assemble(int n, int ndir, const double *omega_d, const double *sigma_t, int *rowptr, int *col,

@@ -320,26 +320,35 @@ void vcycle_t(Hier &h, double *x64) {
             PR_LAUNCH();
         }
     }
+    const int fs = h.prm.f_sweeps;
     for (int l = NL - 2; l >= 0; --l) {
         Level &L = h.lev[l];
         const Level &C = h.lev[l + 1];
         k_prolong<T><<<blocks_for(L.n, BS), BS, 0, s>>>(L.n, L.cf, L.pmap, (const T *)C.vx, (T *)L.vy);
         PR_LAUNCH();
+        // F sweeps ping-pong between vy and vxn; the C sweep reads the last one
+        T *bufs[2] = {(T *)L.vy, (T *)L.vxn};
+        int cur = 0;
         if (l == 0 && h.bsr0) {
             int N = h.n0[0];
             dim3 grid(blocks_for(N, BS), h.ndir);
             const T *vals = std::is_same<T, float>::value ? (const T *)h.bsr32 : (const T *)h.bsr64;
-            k_relax_bsr<T><<<grid, BS, 0, s>>>(h.hex_n, N, h.dsign, vals, L.cf, (const T *)L.vb, (const T *)L.vy,
-                                               (T *)L.vxn, 0, nullptr, active);
+            if (h.prof) PR_CUDA(cudaEventRecord(h.ev[2], s));
+            for (int f = 0; f < fs; ++f, cur ^= 1) {
+                k_relax_bsr<T><<<grid, BS, 0, s>>>(h.hex_n, N, h.dsign, vals, L.cf, (const T *)L.vb, bufs[cur],
+                                                   bufs[cur ^ 1], 0, nullptr, active);
+                PR_LAUNCH();
+            }
+            k_relax_bsr<T><<<grid, BS, 0, s>>>(h.hex_n, N, h.dsign, vals, L.cf, (const T *)L.vb, bufs[cur], nullptr,
+                                               1, x64, active);
             PR_LAUNCH();
-            k_relax_bsr<T><<<grid, BS, 0, s>>>(h.hex_n, N, h.dsign, vals, L.cf, (const T *)L.vb, (const T *)L.vxn,
-                                               nullptr, 1, x64, active);
-            PR_LAUNCH();
+            if (h.prof) PR_CUDA(cudaEventRecord(h.ev[3], s));
         } else {
             const int *act = l == 0 ? active : nullptr;
-            relax_csr<T>(L, (const T *)L.vb, (const T *)L.vy, (T *)L.vxn, 0, nullptr, nullptr, act, s);
-            relax_csr<T>(L, (const T *)L.vb, (const T *)L.vxn, (T *)L.vx, 1, l == 0 ? x64 : nullptr,
-                         (const T *)L.vx, act, s);
+            for (int f = 0; f < fs; ++f, cur ^= 1)
+                relax_csr<T>(L, (const T *)L.vb, bufs[cur], bufs[cur ^ 1], 0, nullptr, nullptr, act, s);
+            relax_csr<T>(L, (const T *)L.vb, bufs[cur], (T *)L.vx, 1, l == 0 ? x64 : nullptr, (const T *)L.vx, act,
+                         s);
         }
     }
     if (NL == 1) {   // single-level hierarchies: x += coarsest solution
@@ -372,10 +381,64 @@ void alloc_cycle_vectors(Hier &h) {
     h.active = dmalloc<int>(h.ndir, h.stream);
 }
 
+namespace {
+// faces with an upwind neighbour of each level-0 row, split by CF, per matrix
+__global__ void k_face_counts(int n, int N, const int8_t *dsign, const int8_t *cf, unsigned long long *out) {
+    int m = blockIdx.y;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    int e = i >> 3;
+    int idx[3] = {e % n, (e / n) % n, e / (n * n)};
+    int f = 0;
+    for (int d = 0; d < 3; ++d) {
+        int sg = dsign[3 * m + d];
+        if (sg != 0 && (sg > 0 ? idx[d] > 0 : idx[d] < n - 1)) ++f;
+    }
+    int8_t c = cf[(long long)m * N + i];
+    // out[m][0] = F rows, [1] = C rows, [2] = faces of F rows, [3] = faces of C rows
+    atomicAdd(&out[4 * m + (c == CF_C ? 1 : 0)], 1ULL);
+    atomicAdd(&out[4 * m + (c == CF_C ? 3 : 2)], (unsigned long long)f);
+}
+}  // namespace
+
+void level0_bytes(Hier &h) {
+    h.bytes_res0.assign(h.ndir, 0.0);
+    h.bytes_relax0.assign(h.ndir, 0.0);
+    if (!h.bsr0) return;
+    cudaStream_t s = h.stream;
+    int N = h.n0[0];
+    unsigned long long *cnt = dmalloc<unsigned long long>(4 * h.ndir, s);
+    PR_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * 4 * h.ndir, s));
+    dim3 grid(blocks_for(N, BS), h.ndir);
+    k_face_counts<<<grid, BS, 0, s>>>(h.hex_n, N, h.dsign, h.lev[0].cf, cnt);
+    PR_LAUNCH();
+    std::vector<unsigned long long> c(4 * h.ndir);
+    PR_CUDA(cudaMemcpyAsync(c.data(), cnt, sizeof(unsigned long long) * c.size(), cudaMemcpyDeviceToHost, s));
+    PR_CUDA(cudaStreamSynchronize(s));
+    dfree(cnt, s);
+    double sT = h.prm.precision == 1 ? 4.0 : 8.0;
+    for (int m = 0; m < h.ndir; ++m) {
+        double nF = (double)c[4 * m], nC = (double)c[4 * m + 1], fF = (double)c[4 * m + 2], fC = (double)c[4 * m + 3];
+        // residual: FP64 face rows (4 values each), b, x read, r written (cycle precision)
+        h.bytes_res0[m] = (fF + fC) * 4 * 8 + (nF + nC) * (8 + 8 + sT);
+        // each F pass: cf, input and output vector for all rows; A rows and b for F rows
+        // C pass: cf, input, x64 (read + write) for all rows; A rows and b for C rows
+        double fpass = fF * 4 * sT + (nF + nC) * (1 + 2 * sT) + nF * sT;
+        h.bytes_relax0[m] = h.prm.f_sweeps * fpass + fC * 4 * sT + (nF + nC) * (1 + sT + 16) + nC * sT;
+    }
+}
+
+void prof_enable(Hier &h) {
+    if (h.prof) return;
+    for (auto &e : h.ev) PR_CUDA(cudaEventCreate(&e));
+    h.prof = true;
+}
+
 void residual0(Hier &h, const double *b, const double *x, double tol, bool update_active) {
     cudaStream_t s = h.stream;
     PR_CUDA(cudaMemsetAsync(h.partials, 0, sizeof(double) * h.maxblk * h.ndir, s));
     int *act = update_active ? h.active : nullptr;
+    if (h.prof) PR_CUDA(cudaEventRecord(h.ev[0], s));
     Level &L = h.lev[0];
     dim3 grid(h.maxblk, h.ndir);
     bool f32 = h.prm.precision == 1;
@@ -396,6 +459,7 @@ void residual0(Hier &h, const double *b, const double *x, double tol, bool updat
                                                    h.partials, h.maxblk, act);
     }
     PR_LAUNCH();
+    if (h.prof) PR_CUDA(cudaEventRecord(h.ev[1], s));
     k_norm_final<<<blocks_for(h.ndir, 128), 128, 0, s>>>(h.ndir, h.partials, h.maxblk, h.rnorm, h.bnorm, tol, act);
     PR_LAUNCH();
 }

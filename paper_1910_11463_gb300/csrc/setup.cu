@@ -599,6 +599,18 @@ void build_hierarchy(Hier &h) {
     char *dcont = dmalloc<char>(ND, s);
     int *dnc = dmalloc<int>(ND, s);
     long long *dnnz = dmalloc<long long>(ND, s);
+    cudaEvent_t ev[4];
+    for (auto &e : ev) PR_CUDA(cudaEventCreate(&e));
+    struct EvFree {
+        cudaEvent_t *e;
+        ~EvFree() { for (int k = 0; k < 4; ++k) cudaEventDestroy(e[k]); }
+    } evfree{ev};
+    auto phase_ms = [&](int a, int b) {
+        float ms = 0;
+        PR_CUDA(cudaEventSynchronize(ev[b]));
+        PR_CUDA(cudaEventElapsedTime(&ms, ev[a], ev[b]));
+        return (double)ms;
+    };
     for (int l = 0;; ++l) {
         Level &L = h.lev[l];
         int n = L.n;
@@ -638,6 +650,7 @@ void build_hierarchy(Hier &h) {
             break;
         }
         PR_CUDA(cudaMemcpyAsync(dwork, work.data(), ND, cudaMemcpyHostToDevice, s));
+        PR_CUDA(cudaEventRecord(ev[0], s));
         long long nnz = L.nnz;
         uint8_t *S = dmalloc<uint8_t>(nnz, s);
         k_strength<<<blocks_for(n, BS), BS, 0, s>>>(n, L.rowptr, L.col, L.val, L.rowdir, dwork, prm.theta,
@@ -670,6 +683,7 @@ void build_hierarchy(Hier &h) {
             d2h(&und, d_count, 1, s);
         }
         L.pmis_rounds = round;
+        PR_CUDA(cudaEventRecord(ev[1], s));
         PR_CUDA(cudaMemsetAsync(dnc, 0, sizeof(int) * ND, s));
         k_count_c<<<blocks_for(n, BS), BS, 0, s>>>(n, L.rowdir, st0, dnc);
         PR_LAUNCH();
@@ -785,6 +799,7 @@ void build_hierarchy(Hier &h) {
         dfree(keep, s); dfree(cand, s); dfree(candptr, s); dfree(ncand, s);
         dfree(S, s);
 
+        PR_CUDA(cudaEventRecord(ev[2], s));
         // ---- RAP ------------------------------------------------------------
         int *aplen = dmalloc<int>(n, s);
         int *apcol = dmalloc<int>(nnz, s);
@@ -862,6 +877,10 @@ void build_hierarchy(Hier &h) {
         }
         C.d_row0 = dmalloc<int>(ND, s);
         PR_CUDA(cudaMemcpyAsync(C.d_row0, C.row0.data(), sizeof(int) * ND, cudaMemcpyHostToDevice, s));
+        PR_CUDA(cudaEventRecord(ev[3], s));
+        h.t_phase[0] += phase_ms(0, 1);
+        h.t_phase[1] += phase_ms(1, 2);
+        h.t_phase[2] += phase_ms(2, 3);
         finish_segments(h, L);
         h.lev.push_back(C);
     }

@@ -92,6 +92,7 @@ static void ensure_graph(Hier &h, const double *b, double *x, double tol) {
     if (h.graph && h.graph_b == b && h.graph_x == x && h.graph_tol == tol) return;
     if (h.graph) { cudaGraphExecDestroy(h.graph); h.graph = nullptr; }
     cudaGraph_t g;
+    long long before = g_launches;
     PR_CUDA(cudaStreamBeginCapture(h.stream, cudaStreamCaptureModeThreadLocal));
     try {
         vcycle_correct(h, x);
@@ -103,6 +104,8 @@ static void ensure_graph(Hier &h, const double *b, double *x, double tol) {
         throw;
     }
     PR_CUDA(cudaStreamEndCapture(h.stream, &g));
+    h.graph_kernels = g_launches - before;
+    g_launches = before;
     PR_CUDA(cudaGraphInstantiate(&h.graph, g, 0));
     cudaGraphDestroy(g);
     h.graph_b = b;
@@ -124,6 +127,24 @@ BatchSolve solve_batch(Hier &h, const double *b, double *x, double tol, int maxi
     PR_CUDA(cudaMemcpyAsync(bn.data(), h.bnorm, sizeof(double) * nd, cudaMemcpyDeviceToHost, s));
     PR_CUDA(cudaMemcpyAsync(act.data(), h.active, sizeof(int) * nd, cudaMemcpyDeviceToHost, s));
     PR_CUDA(cudaStreamSynchronize(s));
+    auto account = [&](const std::vector<int> &was_active, bool relax) {
+        if (!h.prof) return;
+        float ms = 0;
+        PR_CUDA(cudaEventElapsedTime(&ms, h.ev[0], h.ev[1]));
+        h.t_res0 += ms;
+        h.n_res0 += 1;
+        double br = 0, bx = 0;
+        for (int d = 0; d < nd; ++d)
+            if (was_active[d]) { br += h.bytes_res0[d]; bx += h.bytes_relax0[d]; }
+        h.gb_res0 += br * 1e-9;
+        if (relax && h.bsr0) {
+            PR_CUDA(cudaEventElapsedTime(&ms, h.ev[2], h.ev[3]));
+            h.t_relax0 += ms;
+            h.n_relax0 += 1;
+            h.gb_relax0 += bx * 1e-9;
+        }
+    };
+    account(ones, false);
     for (int d = 0; d < nd; ++d)
         if (!std::isfinite(r0[d]) || !std::isfinite(bn[d])) fail(PAIR_ERR_NAN, "NaN/Inf in right-hand side or residual");
     if (use_graph) ensure_graph(h, b, x, tol);
@@ -132,13 +153,16 @@ BatchSolve solve_batch(Hier &h, const double *b, double *x, double tol, int maxi
     while (any && k < maxit) {
         if (use_graph) {
             PR_CUDA(cudaGraphLaunch(h.graph, s));
+            g_launches += h.graph_kernels;
         } else {
             vcycle_correct(h, x);
             residual0(h, b, x, tol, true);
         }
         ++k;
+        std::vector<int> was = act;
         PR_CUDA(cudaMemcpyAsync(act.data(), h.active, sizeof(int) * nd, cudaMemcpyDeviceToHost, s));
         PR_CUDA(cudaStreamSynchronize(s));
+        account(was, true);
         any = false;
         for (int d = 0; d < nd; ++d) {
             if (act[d]) { any = true; itd[d] = k + 1; }
@@ -170,6 +194,8 @@ BatchSolve solve_batch(Hier &h, const double *b, double *x, double tol, int maxi
 
 Hier::~Hier() {
     if (graph) cudaGraphExecDestroy(graph);
+    for (auto &e : ev)
+        if (e) cudaEventDestroy(e);
     if (stream) {
         for (auto &L : lev) free_level(L, stream);
         void *ptrs[] = {bsr64, bsr32, dsign, partials, rnorm, bnorm, rnorm0, active, d_err, d_n0, d_row00};
@@ -264,6 +290,8 @@ void build_batch(HexBatch &B, int n, const double *omega_h, const double *omega_
                  h->d_err, s);
     build_hierarchy(*h);
     alloc_cycle_vectors(*h);
+    level0_bytes(*h);
+    prof_enable(*h);
 }
 
 }  // namespace
@@ -328,6 +356,14 @@ void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t,
     int vcycles = 0, levels_max = 0;
     double max_inner = 0, opc_sum = 0, change = 0;
     int opc_cnt = 0, it = 0;
+    double t_res0 = 0, t_relax0 = 0, gb_res0 = 0, gb_relax0 = 0, tph[4] = {0, 0, 0, 0};
+    long long n_res0 = 0, n_relax0 = 0;
+    auto harvest = [&](Hier &h) {
+        t_res0 += h.t_res0; t_relax0 += h.t_relax0; gb_res0 += h.gb_res0; gb_relax0 += h.gb_relax0;
+        n_res0 += h.n_res0; n_relax0 += h.n_relax0;
+        h.t_res0 = h.t_relax0 = h.gb_res0 = h.gb_relax0 = 0;
+        h.n_res0 = h.n_relax0 = 0;
+    };
     bool converged = false;
     auto elapsed = [&](cudaStream_t st) {
         PR_CUDA(cudaEventRecord(e1, st));
@@ -355,6 +391,7 @@ void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t,
                 PR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
                 t_setup += ms;
                 cudaStreamDestroy(tmp);
+                for (int k = 0; k < 4; ++k) tph[k] += Bt.h->t_phase[k];
                 cudaStream_t hs = Bt.h->stream;
                 Bt.b = dmalloc<double>((size_t)Bt.nd * N, hs);
                 if (!psi) Bt.xown = dmalloc<double>((size_t)Bt.nd * N, hs);
@@ -383,6 +420,7 @@ void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t,
             k_phi_acc<<<blocks_for(N, BS), BS, 0, hs>>>(N, Bt.nd, w_d + Bt.m0, x, phinew);
             PR_LAUNCH();
             t_solve += elapsed(hs);
+            harvest(h);
             if (!resident) {
                 dfree(Bt.b, hs); dfree(Bt.xown, hs);
                 Bt.b = Bt.xown = nullptr;
@@ -414,6 +452,14 @@ void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t,
         info->t_solve_ms = t_solve;
         info->levels_max = levels_max;
         info->op_complexity = opc_cnt ? opc_sum / opc_cnt : 0;
+        info->t_res0_ms = t_res0;
+        info->n_res0 = (int)n_res0;
+        info->gb_res0 = gb_res0;
+        info->t_relax0_ms = t_relax0;
+        info->n_relax0 = (int)n_relax0;
+        info->gb_relax0 = gb_relax0;
+        for (int k = 0; k < 3; ++k) info->t_setup_phase_ms[k] = tph[k];
+        info->t_setup_phase_ms[3] = t_setup - (tph[0] + tph[1] + tph[2]);
     }
     if (!converged && sp.max_iters > 1) {
         char buf[128];

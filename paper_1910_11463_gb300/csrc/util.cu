@@ -6,6 +6,8 @@
 
 namespace pr {
 
+long long g_launches = 0;
+
 void fail(pair_status st, const std::string &msg) { throw Error{st, msg}; }
 
 void cuda_check(cudaError_t e, const char *what, const char *file, int line) {

@@ -28,7 +28,8 @@ class PairError(RuntimeError):
 class air_params(C.Structure):
     _fields_ = [("distance", C.c_int), ("theta", C.c_double), ("eps_R", C.c_double), ("phi_R", C.c_double),
                 ("phi_A", C.c_double), ("max_levels", C.c_int), ("max_coarse", C.c_int),
-                ("coarse_sweeps", C.c_int), ("seed", C.c_uint64), ("precision", C.c_int)]
+                ("coarse_sweeps", C.c_int), ("seed", C.c_uint64), ("precision", C.c_int),
+                ("f_sweeps", C.c_int)]
 
 
 class pair_csr(C.Structure):
@@ -63,7 +64,9 @@ class si_info(C.Structure):
     _fields_ = [("si_iters", C.c_int), ("si_change", C.c_double), ("vcycles", C.c_int),
                 ("max_inner_resid", C.c_double), ("batches", C.c_int), ("rebuilt", C.c_int),
                 ("t_setup_ms", C.c_double), ("t_solve_ms", C.c_double), ("levels_max", C.c_int),
-                ("op_complexity", C.c_double)]
+                ("op_complexity", C.c_double), ("t_res0_ms", C.c_double), ("n_res0", C.c_int),
+                ("gb_res0", C.c_double), ("t_relax0_ms", C.c_double), ("n_relax0", C.c_int),
+                ("gb_relax0", C.c_double), ("t_setup_phase_ms", C.c_double * 4)]
 
 
 _lib = None
@@ -81,6 +84,7 @@ def lib():
             "air_params_default": (None, [C.POINTER(air_params)]),
             "si_params_default": (None, [C.POINTER(si_params)]),
             "pair_last_error": (C.c_char_p, []),
+            "pair_kernel_launches": (C.c_longlong, []),
             "air_setup": (i, [C.POINTER(pair_csr), i, C.POINTER(air_params), vp, C.POINTER(vp)]),
             "air_vcycle": (i, [vp, vp, vp, vp]),
             "air_solve": (i, [vp, vp, vp, d, i, vp, C.POINTER(air_solve_info)]),
@@ -99,6 +103,17 @@ def lib():
             f.argtypes = args
         _lib = L
     return _lib
+
+
+def kernel_source_sha(name: str = "cycle.cu") -> str:
+    """Short hash of a kernel source file (ties stored profiler counters to the code they measured)."""
+    import hashlib
+    with open(os.path.join(_HERE, "csrc", name), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def kernel_launches() -> int:
+    return lib().pair_kernel_launches()
 
 
 def _check(st: int):
@@ -286,7 +301,9 @@ def si_solve(n: int, omega, w, sigma_t, sigma_s, q, air: air_params | None = Non
     rc = lib().si_solve(C.byref(pair_mesh(n)), C.byref(quad), _dptr(st), _dptr(ss), _dptr(qq), C.byref(air),
                         C.byref(si), _dptr(phi), _dptr(psi) if psi is not None else None, _stream(), C.byref(info))
     _check(rc)
-    return phi, psi, {f: getattr(info, f) for f, _ in si_info._fields_}
+    out = {f: getattr(info, f) for f, _ in si_info._fields_}
+    out["t_setup_phase_ms"] = list(info.t_setup_phase_ms)
+    return phi, psi, out
 
 
 def si_solve_problem(prob, **kw):
