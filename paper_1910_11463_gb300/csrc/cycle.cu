@@ -20,6 +20,15 @@ namespace {
 
 constexpr int BS = 256;
 
+// Timing event: a plain record, or an event-record node while the stream is
+// being captured into a graph (so each replay records it).
+void rec_event(cudaEvent_t e, cudaStream_t s) {
+    cudaStreamCaptureStatus cs;
+    PR_CUDA(cudaStreamIsCapturing(s, &cs));
+    if (cs == cudaStreamCaptureStatusActive) PR_CUDA(cudaEventRecordWithFlags(e, s, cudaEventRecordExternal));
+    else PR_CUDA(cudaEventRecord(e, s));
+}
+
 __device__ __forceinline__ int face_node(int d, int o, int t) {
     return d == 0 ? (o | (t << 1)) : d == 1 ? ((t & 1) | (o << 1) | ((t >> 1) << 2)) : (t | (o << 2));
 }
@@ -333,7 +342,7 @@ void vcycle_t(Hier &h, double *x64) {
             int N = h.n0[0];
             dim3 grid(blocks_for(N, BS), h.ndir);
             const T *vals = std::is_same<T, float>::value ? (const T *)h.bsr32 : (const T *)h.bsr64;
-            if (h.prof) PR_CUDA(cudaEventRecordWithFlags(h.ev[2], s, cudaEventRecordExternal));
+            if (h.prof) rec_event(h.ev[2], s);
             for (int f = 0; f < fs; ++f, cur ^= 1) {
                 k_relax_bsr<T><<<grid, BS, 0, s>>>(h.hex_n, N, h.dsign, vals, L.cf, (const T *)L.vb, bufs[cur],
                                                    bufs[cur ^ 1], 0, nullptr, active);
@@ -342,7 +351,7 @@ void vcycle_t(Hier &h, double *x64) {
             k_relax_bsr<T><<<grid, BS, 0, s>>>(h.hex_n, N, h.dsign, vals, L.cf, (const T *)L.vb, bufs[cur], nullptr,
                                                1, x64, active);
             PR_LAUNCH();
-            if (h.prof) PR_CUDA(cudaEventRecordWithFlags(h.ev[3], s, cudaEventRecordExternal));
+            if (h.prof) rec_event(h.ev[3], s);
         } else {
             const int *act = l == 0 ? active : nullptr;
             for (int f = 0; f < fs; ++f, cur ^= 1)
@@ -438,7 +447,7 @@ void residual0(Hier &h, const double *b, const double *x, double tol, bool updat
     cudaStream_t s = h.stream;
     PR_CUDA(cudaMemsetAsync(h.partials, 0, sizeof(double) * h.maxblk * h.ndir, s));
     int *act = update_active ? h.active : nullptr;
-    if (h.prof) PR_CUDA(cudaEventRecordWithFlags(h.ev[0], s, cudaEventRecordExternal));
+    if (h.prof) rec_event(h.ev[0], s);
     Level &L = h.lev[0];
     dim3 grid(h.maxblk, h.ndir);
     bool f32 = h.prm.precision == 1;
@@ -459,7 +468,7 @@ void residual0(Hier &h, const double *b, const double *x, double tol, bool updat
                                                    h.partials, h.maxblk, act);
     }
     PR_LAUNCH();
-    if (h.prof) PR_CUDA(cudaEventRecordWithFlags(h.ev[1], s, cudaEventRecordExternal));
+    if (h.prof) rec_event(h.ev[1], s);
     k_norm_final<<<blocks_for(h.ndir, 128), 128, 0, s>>>(h.ndir, h.partials, h.maxblk, h.rnorm, h.bnorm, tol, act);
     PR_LAUNCH();
 }
