@@ -115,6 +115,7 @@ struct Hier {
     int *d_n0 = nullptr, *d_row00 = nullptr;  // level-0 rows per matrix and first rows
     // instrumentation: CUDA events around the level-0 kernels (also inside graphs)
     bool prof = false;
+    bool relax_timed = false;   // ev[2], ev[3] recorded by the current cycle
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     double t_res0 = 0, t_relax0 = 0, gb_res0 = 0, gb_relax0 = 0;
     long long n_res0 = 0, n_relax0 = 0;

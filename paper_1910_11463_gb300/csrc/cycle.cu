@@ -342,7 +342,7 @@ void vcycle_t(Hier &h, double *x64) {
             int N = h.n0[0];
             dim3 grid(blocks_for(N, BS), h.ndir);
             const T *vals = std::is_same<T, float>::value ? (const T *)h.bsr32 : (const T *)h.bsr64;
-            if (h.prof) rec_event(h.ev[2], s);
+            if (h.prof) { rec_event(h.ev[2], s); h.relax_timed = true; }
             for (int f = 0; f < fs; ++f, cur ^= 1) {
                 k_relax_bsr<T><<<grid, BS, 0, s>>>(h.hex_n, N, h.dsign, vals, L.cf, (const T *)L.vb, bufs[cur],
                                                    bufs[cur ^ 1], 0, nullptr, active);

@@ -137,7 +137,7 @@ BatchSolve solve_batch(Hier &h, const double *b, double *x, double tol, int maxi
         for (int d = 0; d < nd; ++d)
             if (was_active[d]) { br += h.bytes_res0[d]; bx += h.bytes_relax0[d]; }
         h.gb_res0 += br * 1e-9;
-        if (relax && h.bsr0) {
+        if (relax && h.relax_timed) {
             PR_CUDA(cudaEventElapsedTime(&ms, h.ev[2], h.ev[3]));
             h.t_relax0 += ms;
             h.n_relax0 += 1;
