@@ -393,20 +393,26 @@ void alloc_cycle_vectors(Hier &h) {
 namespace {
 // faces with an upwind neighbour of each level-0 row, split by CF, per matrix
 __global__ void k_face_counts(int n, int N, const int8_t *dsign, const int8_t *cf, unsigned long long *out) {
+    // out[m][0] = F rows, [1] = C rows, [2] = faces of F rows, [3] = faces of C rows
+    __shared__ unsigned long long sh[4];
     int m = blockIdx.y;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    int e = i >> 3;
-    int idx[3] = {e % n, (e / n) % n, e / (n * n)};
-    int f = 0;
-    for (int d = 0; d < 3; ++d) {
-        int sg = dsign[3 * m + d];
-        if (sg != 0 && (sg > 0 ? idx[d] > 0 : idx[d] < n - 1)) ++f;
+    if (threadIdx.x < 4) sh[threadIdx.x] = 0;
+    __syncthreads();
+    if (i < N) {
+        int e = i >> 3;
+        int idx[3] = {e % n, (e / n) % n, e / (n * n)};
+        int f = 0;
+        for (int d = 0; d < 3; ++d) {
+            int sg = dsign[3 * m + d];
+            if (sg != 0 && (sg > 0 ? idx[d] > 0 : idx[d] < n - 1)) ++f;
+        }
+        bool isC = cf[(long long)m * N + i] == CF_C;
+        atomicAdd(&sh[isC ? 1 : 0], 1ULL);
+        atomicAdd(&sh[isC ? 3 : 2], (unsigned long long)f);
     }
-    int8_t c = cf[(long long)m * N + i];
-    // out[m][0] = F rows, [1] = C rows, [2] = faces of F rows, [3] = faces of C rows
-    atomicAdd(&out[4 * m + (c == CF_C ? 1 : 0)], 1ULL);
-    atomicAdd(&out[4 * m + (c == CF_C ? 3 : 2)], (unsigned long long)f);
+    __syncthreads();
+    if (threadIdx.x < 4) atomicAdd(&out[4 * m + threadIdx.x], sh[threadIdx.x]);
 }
 }  // namespace
 

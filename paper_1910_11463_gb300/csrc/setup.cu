@@ -136,10 +136,27 @@ __global__ void k_pmis_update(int n, const int *rowptr, const int *col, const ui
     atomicAdd(undecided, 1);
 }
 
+// per-matrix sums: one atomic per warp when its rows share a matrix (the usual case)
+template <class T>
+__device__ __forceinline__ void add_by_dir(T *out, int d, T v, bool valid) {
+    unsigned act = __ballot_sync(0xffffffffu, valid);
+    if (!act) return;
+    int d0 = __shfl_sync(0xffffffffu, d, __ffs(act) - 1);
+    bool same = __all_sync(0xffffffffu, !valid || d == d0);
+    if (same) {
+        T tot = valid ? v : T(0);
+        for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        if ((threadIdx.x & 31) == __ffs(act) - 1 && tot) atomicAdd(&out[d0], tot);
+    } else if (valid && v) {
+        atomicAdd(&out[d], v);
+    }
+}
+
 __global__ void k_count_c(int n, const int *rowdir, const int8_t *state, int *ncdir) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    if (state[i] == ST_C) atomicAdd(&ncdir[rowdir[i]], 1);
+    bool valid = i < n;
+    int d = valid ? rowdir[i] : 0;
+    add_by_dir<int>(ncdir, d, (valid && state[i] == ST_C) ? 1 : 0, valid);
 }
 
 __global__ void k_cf_final(int n, const int *rowdir, const char *cont, const int8_t *state, int8_t *cf, int *isC) {
@@ -225,6 +242,21 @@ __global__ void k_lair_pattern(int nc, const int *cpts, const int *rowptr, const
     npat[ic] = m;
 }
 
+// size class of each lAIR system: 0: n <= 8, 1: <= 16, 2: <= 32, 3: <= 64, 4: larger
+__device__ __forceinline__ int lair_class(int np) { return np <= 8 ? 0 : np <= 16 ? 1 : np <= 32 ? 2 : np <= 64 ? 3 : 4; }
+
+__global__ void k_lair_class_count(int nc, const int *npat, int *cnt) {
+    int ic = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ic < nc) atomicAdd(&cnt[lair_class(npat[ic])], 1);
+}
+
+__global__ void k_lair_class_fill(int nc, const int *npat, const int *start, int *fill, int *list) {
+    int ic = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ic >= nc) return;
+    int c = lair_class(npat[ic]);
+    list[start[c] + atomicAdd(&fill[c], 1)] = ic;
+}
+
 __global__ void k_max_int(const int *v, int n, int *out) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) atomicMax(out, v[i]);
@@ -232,9 +264,20 @@ __global__ void k_max_int(const int *v, int n, int *out) {
 
 // Warp per C row.  Shared memory per warp: M (nmax^2 doubles), y (nmax
 // doubles), pattern (nmax ints), pivots (nmax ints).
-// Small mode (worklist == null): systems of size <= nmax use shared memory;
-// larger ones are counted in *nbig and left for big mode.  Big mode: rows from
-// worklist, workspace in global memory at gbuf + goff[w].
+__device__ __forceinline__ int pat_find(const int *pat, int np, int k) {
+    int lo = 0, hi = np - 1;
+    while (lo <= hi) {
+        int m = (lo + hi) >> 1;
+        int v = pat[m];
+        if (v == k) return m;
+        if (v < k) lo = m + 1; else hi = m - 1;
+    }
+    return -1;
+}
+
+// Warp per C row of the worklist.  Shared-memory mode (gbuf == null): systems
+// of size <= nmax, workspace in shared memory.  Global mode: workspace at
+// gbuf + goff[w] (systems larger than the biggest shared-memory bin).
 __global__ void k_lair_solve(int nwork, const int *worklist, const int *cpts, const int *rowptr, const int *col,
                              const double *val, const int *candptr, const int *cand, const int *npat,
                              const int *zrowptr, int *zcol, double *zval, int *keep, int *nsing_dir,
@@ -248,11 +291,11 @@ __global__ void k_lair_solve(int nwork, const int *worklist, const int *cpts, co
         int i = cpts[ic];
         int np = npat[ic];
         double *M;
-        if (worklist) {
+        if (gbuf) {
             M = gbuf + goff[w];
         } else {
-            if (np > nmax) {
-                if (lane == 0) { keep[ic] = -1; atomicAdd(nbig, 1); }
+            if (np > nmax) {   // cannot happen with the size bins; keep the bound explicit
+                if (lane == 0) { keep[ic] = 0; atomicAdd(nbig, 1); }
                 continue;
             }
             M = smem + (size_t)warp * ((size_t)nmax * nmax + 2 * nmax);
@@ -262,15 +305,26 @@ __global__ void k_lair_solve(int nwork, const int *worklist, const int *cpts, co
         int *piv = pat + np;
         const int *cp = cand + candptr[ic];
         for (int t = lane; t < np; t += 32) pat[t] = cp[t];
+        for (int idx = lane; idx < np * np; idx += 32) M[idx] = 0.0;
+        // absent right-hand-side entries are -0.0: the negation of a stored zero
+        for (int r = lane; r < np; r += 32) y[r] = -0.0;
+        __syncwarp();
+        // M[r][c] = a(pat[c], pat[r]): lane per pattern row, one pass over that row of A,
+        // column positions found by binary search in the (sorted) pattern
+        for (int c = lane; c < np; c += 32) {
+            int j = pat[c];
+            for (int p = rowptr[j]; p < rowptr[j + 1]; ++p) {
+                int r = pat_find(pat, np, col[p]);
+                if (r >= 0) M[r * np + c] = val[p];
+            }
+        }
+        for (int p = rowptr[i] + lane; p < rowptr[i + 1]; p += 32) {
+            int r = pat_find(pat, np, col[p]);
+            if (r >= 0) y[r] = -val[p];
+        }
         __syncwarp();
         double mx = 0.0;
-        for (int idx = lane; idx < np * np; idx += 32) {
-            int r = idx / np, c = idx - r * np;
-            double v = lookup(rowptr, col, val, pat[c], pat[r]);   // transposed block
-            M[idx] = v;
-            mx = fmax(mx, fabs(v));
-        }
-        for (int r = lane; r < np; r += 32) y[r] = -lookup(rowptr, col, val, i, pat[r]);
+        for (int idx = lane; idx < np * np; idx += 32) mx = fmax(mx, fabs(M[idx]));
         for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         double tiny = 1e-14 * mx;
         __syncwarp();
@@ -351,12 +405,14 @@ __global__ void k_lair_solve(int nwork, const int *worklist, const int *cpts, co
     }
 }
 
+// 8 lanes per row: copies the first (newptr[r+1]-newptr[r]) entries of each old row
 __global__ void k_compact_rows(int nrows, const int *oldptr, const int *newptr, const int *col_in,
                                const double *val_in, int *col_out, double *val_out) {
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int r = (int)(tid >> 3), g = (int)(tid & 7);
     if (r >= nrows) return;
     int o = oldptr[r], nn = newptr[r], cnt = newptr[r + 1] - newptr[r];
-    for (int t = 0; t < cnt; ++t) { col_out[nn + t] = col_in[o + t]; val_out[nn + t] = val_in[o + t]; }
+    for (int t = g; t < cnt; t += 8) { col_out[nn + t] = col_in[o + t]; val_out[nn + t] = val_in[o + t]; }
 }
 
 // ---- RAP ---------------------------------------------------------------------
@@ -417,13 +473,14 @@ __global__ void k_rap(int nrows_work, const int *worklist, int nc, const int *cp
             keys = gkeys + off;
             vals = gvals + off;
         } else {
-            cap = hcap;
             vals = smem2 + (size_t)warp * hcap;
             keys = (int *)(smem2 + (size_t)wpb * hcap) + (size_t)warp * hcap;
-            if (2 * U[ic] > cap) {
+            if (2 * U[ic] > hcap) {
                 if (lane == 0) { cnt[ic] = -1; atomicAdd(overflow, 1); }
                 continue;
             }
+            cap = 64;
+            while (cap < 2 * U[ic]) cap <<= 1;   // table sized to this row's bound
         }
         unsigned mask = (unsigned)cap - 1u;
         for (int t = lane; t < cap; t += 32) keys[t] = -1;
@@ -506,9 +563,11 @@ __global__ void k_gather_rowdir(int nc, const int *cpts, const int *rowdir, int 
     if (ic < nc) rowdir_c[ic] = rowdir[cpts[ic]];
 }
 
-__global__ void k_rowlen_dir(int n, const int *rowptr, const int *rowdir, long long *nnzdir) {
+__global__ void k_rowlen_dir(int n, const int *rowptr, const int *rowdir, unsigned long long *nnzdir) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) atomicAdd((unsigned long long *)&nnzdir[rowdir[i]], (unsigned long long)(rowptr[i + 1] - rowptr[i]));
+    bool valid = i < n;
+    int d = valid ? rowdir[i] : 0;
+    add_by_dir<unsigned long long>(nnzdir, d, valid ? (unsigned long long)(rowptr[i + 1] - rowptr[i]) : 0ULL, valid);
 }
 
 __global__ void k_cast(long long n, const double *a, float *b) {
@@ -541,12 +600,10 @@ __global__ void k_overflow_rows(int nc, const int *flag, const int *pos, const i
     capw[w] = c;
 }
 
-__global__ void k_big_rows(int nc, const int *flag, const int *pos, const int *npat, int *list, long long *goff) {
-    int ic = blockIdx.x * blockDim.x + threadIdx.x;
-    if (ic >= nc || !flag[ic]) return;
-    int w = pos[ic];
-    long long np = npat[ic];
-    list[w] = ic;
+__global__ void k_big_rows(int nbig, const int *list, const int *npat, long long *goff) {
+    int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= nbig) return;
+    long long np = npat[list[w]];
     goff[w] = np * np + 2 * np;
 }
 
@@ -622,7 +679,7 @@ void build_hierarchy(Hier &h) {
         L.pmap = dmalloc<int>(n, s);
         // per-matrix stats of this level
         PR_CUDA(cudaMemsetAsync(dnnz, 0, sizeof(long long) * ND, s));
-        k_rowlen_dir<<<blocks_for(n, BS), BS, 0, s>>>(n, L.rowptr, L.rowdir, dnnz);
+        k_rowlen_dir<<<blocks_for(n, BS), BS, 0, s>>>(n, L.rowptr, L.rowdir, (unsigned long long *)dnnz);
         PR_LAUNCH();
         std::vector<long long> nnzd(ND);
         d2h(nnzd.data(), dnnz, ND, s);
@@ -732,11 +789,6 @@ void build_hierarchy(Hier &h) {
         k_lair_pattern<<<blocks_for(nc, BS), BS, 0, s>>>(nc, L.cpts, L.rowptr, L.col, S, L.cf, prm.distance, candptr,
                                                          cand, npat);
         PR_LAUNCH();
-        PR_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int), s));
-        k_max_int<<<blocks_for(nc, BS), BS, 0, s>>>(npat, nc, d_count);
-        PR_LAUNCH();
-        int nmax = 0;
-        d2h(&nmax, d_count, 1, s);
         int *zr = dmalloc<int>(nc + 1, s);
         long long nz = scan_exclusive(npat, zr, nc, s);
         int *zc = dmalloc<int>(nz, s);
@@ -745,29 +797,39 @@ void build_hierarchy(Hier &h) {
         int *dsing = dmalloc<int>(ND, s);
         PR_CUDA(cudaMemsetAsync(dsing, 0, sizeof(int) * ND, s));
         {
-            const int NSMALL = 64;
-            int nm = std::max(1, std::min(nmax, NSMALL));
-            size_t per = ((size_t)nm * nm + 2 * nm) * sizeof(double);
-            int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (200 * 1024) / per));
-            size_t sm = per * wpb;
-            if (sm > 48 * 1024)
-                PR_CUDA(cudaFuncSetAttribute(k_lair_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-            PR_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int), s));
-            unsigned grid = std::min<unsigned>(blocks_for(nc, wpb), 152u * 64u);
-            k_lair_solve<<<grid, 32 * wpb, sm, s>>>(nc, nullptr, L.cpts, L.rowptr, L.col, L.val, candptr, cand, npat,
-                                                    zr, zc, zv, keep, dsing, L.rowdir, prm.phi_R, nm, nullptr,
-                                                    nullptr, d_count);
+            // rows binned by system size; shared memory per warp sized to the bin
+            int *ccount = dmalloc<int>(10, s);
+            PR_CUDA(cudaMemsetAsync(ccount, 0, sizeof(int) * 10, s));
+            k_lair_class_count<<<blocks_for(nc, BS), BS, 0, s>>>(nc, npat, ccount);
             PR_LAUNCH();
-            int nbig = 0;
-            d2h(&nbig, d_count, 1, s);
-            if (nbig > 0) {
-                int *flag = dmalloc<int>(nc, s), *pos = dmalloc<int>(nc + 1, s);
-                k_overflow_list<<<blocks_for(nc, BS), BS, 0, s>>>(nc, keep, flag);
+            int hc[5];
+            d2h(hc, ccount, 5, s);
+            int hstart[5], acc = 0;
+            for (int c = 0; c < 5; ++c) { hstart[c] = acc; acc += hc[c]; }
+            PR_CUDA(cudaMemcpyAsync(ccount, hstart, sizeof(int) * 5, cudaMemcpyHostToDevice, s));
+            PR_CUDA(cudaMemsetAsync(ccount + 5, 0, sizeof(int) * 5, s));
+            int *list = dmalloc<int>(nc, s);
+            k_lair_class_fill<<<blocks_for(nc, BS), BS, 0, s>>>(nc, npat, ccount, ccount + 5, list);
+            PR_LAUNCH();
+            const int cls_n[4] = {8, 16, 32, 64};
+            for (int c = 0; c < 4; ++c) {
+                if (!hc[c]) continue;
+                int nm = cls_n[c];
+                size_t per = ((size_t)nm * nm + 2 * nm) * sizeof(double);
+                int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (200 * 1024) / per));
+                size_t sm = per * wpb;
+                if (sm > 48 * 1024)
+                    PR_CUDA(cudaFuncSetAttribute(k_lair_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+                unsigned grid = std::min<unsigned>(blocks_for(hc[c], wpb), 152u * 64u);
+                k_lair_solve<<<grid, 32 * wpb, sm, s>>>(hc[c], list + hstart[c], L.cpts, L.rowptr, L.col, L.val,
+                                                        candptr, cand, npat, zr, zc, zv, keep, dsing, L.rowdir,
+                                                        prm.phi_R, nm, nullptr, nullptr, d_count);
                 PR_LAUNCH();
-                scan_exclusive(flag, pos, nc, s);
-                int *list = dmalloc<int>(nbig, s);
+            }
+            int nbig = hc[4];
+            if (nbig > 0) {
                 long long *goff = dmalloc<long long>(nbig + 1, s);
-                k_big_rows<<<blocks_for(nc, BS), BS, 0, s>>>(nc, flag, pos, npat, list, goff);
+                k_big_rows<<<blocks_for(nbig, BS), BS, 0, s>>>(nbig, list + hstart[4], npat, goff);
                 PR_LAUNCH();
                 k_prefix_ll<<<1, 1, 0, s>>>(nbig, goff);
                 PR_LAUNCH();
@@ -775,11 +837,12 @@ void build_hierarchy(Hier &h) {
                 d2h(&gtot, goff + nbig, 1, s);
                 double *gbuf = dmalloc<double>(gtot, s);
                 k_lair_solve<<<std::min<unsigned>(nbig, 152u * 16u), 32, 0, s>>>(
-                    nbig, list, L.cpts, L.rowptr, L.col, L.val, candptr, cand, npat, zr, zc, zv, keep, dsing,
-                    L.rowdir, prm.phi_R, nmax, goff, gbuf, d_count);
+                    nbig, list + hstart[4], L.cpts, L.rowptr, L.col, L.val, candptr, cand, npat, zr, zc, zv, keep,
+                    dsing, L.rowdir, prm.phi_R, 0, goff, gbuf, d_count);
                 PR_LAUNCH();
-                dfree(gbuf, s); dfree(goff, s); dfree(list, s); dfree(flag, s); dfree(pos, s);
+                dfree(gbuf, s); dfree(goff, s);
             }
+            dfree(list, s); dfree(ccount, s);
         }
         d2h(L.singular.data(), dsing, ND, s);
         dfree(dsing, s);
@@ -788,7 +851,7 @@ void build_hierarchy(Hier &h) {
         if (nz2 != nz) {
             int *zc2 = dmalloc<int>(nz2, s);
             double *zv2 = dmalloc<double>(nz2, s);
-            k_compact_rows<<<blocks_for(nc, BS), BS, 0, s>>>(nc, zr, zr2, zc, zv, zc2, zv2);
+            k_compact_rows<<<blocks_for(8LL * nc, BS), BS, 0, s>>>(nc, zr, zr2, zc, zv, zc2, zv2);
             PR_LAUNCH();
             dfree(zc, s); dfree(zv, s); dfree(zr, s);
             zc = zc2; zv = zv2;
@@ -854,7 +917,7 @@ void build_hierarchy(Hier &h) {
         C.nnz = scan_exclusive(cnt, C.rowptr, nc, s);
         C.col = dmalloc<int>(C.nnz, s);
         C.val = dmalloc<double>(C.nnz, s);
-        k_compact_rows<<<blocks_for(nc, BS), BS, 0, s>>>(nc, uptr, C.rowptr, ucol, uval, C.col, C.val);
+        k_compact_rows<<<blocks_for(8LL * nc, BS), BS, 0, s>>>(nc, uptr, C.rowptr, ucol, uval, C.col, C.val);
         PR_LAUNCH();
         dfree(ucol, s); dfree(uval, s); dfree(uptr, s); dfree(U, s); dfree(cnt, s);
         dfree(aplen, s); dfree(apcol, s); dfree(apval, s);
