@@ -190,6 +190,7 @@ pair_status air_vcycle(pair_hier hh, const double *b, double *x, void *stream) {
         PR_REQUIRE(hh && b && x, PAIR_ERR_ARG, "air_vcycle: null argument");
         pr::Hier &h = hh->h;
         StreamJoin join((cudaStream_t)stream, h.stream);
+        pr::set_all_active(h);
         pr::residual0(h, b, x, 0.0, false);
         pr::vcycle_correct(h, x);
     });

@@ -140,6 +140,7 @@ void residual0(Hier &h, const double *b, const double *x, double tol, bool updat
 void vcycle_correct(Hier &h, double *x);       // x += V(lev[0].vb), zero initial guess
 void norms0(Hier &h, const double *v, double *out);  // per-matrix 2-norms of a level-0 vector
 void alloc_cycle_vectors(Hier &h);
+void set_all_active(Hier &h);   // every matrix of the batch takes part in the next cycle
 void level0_bytes(Hier &h);   // fills bytes_res0 / bytes_relax0 (hex block form)
 void prof_enable(Hier &h);
 

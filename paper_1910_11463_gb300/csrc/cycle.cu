@@ -388,6 +388,13 @@ void alloc_cycle_vectors(Hier &h) {
     h.rnorm0 = dmalloc<double>(h.ndir, h.stream);
     h.bnorm = dmalloc<double>(h.ndir, h.stream);
     h.active = dmalloc<int>(h.ndir, h.stream);
+    set_all_active(h);
+}
+
+void set_all_active(Hier &h) {
+    std::vector<int> ones(h.ndir, 1);
+    PR_CUDA(cudaMemcpyAsync(h.active, ones.data(), sizeof(int) * h.ndir, cudaMemcpyHostToDevice, h.stream));
+    PR_CUDA(cudaStreamSynchronize(h.stream));   // 'ones' is pageable host memory
 }
 
 namespace {

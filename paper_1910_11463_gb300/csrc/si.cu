@@ -119,7 +119,7 @@ BatchSolve solve_batch(Hier &h, const double *b, double *x, double tol, int maxi
     int nd = h.ndir;
     norms0(h, b, h.bnorm);
     std::vector<int> ones(nd, 1);
-    PR_CUDA(cudaMemcpyAsync(h.active, ones.data(), sizeof(int) * nd, cudaMemcpyHostToDevice, s));
+    set_all_active(h);
     residual0(h, b, x, tol, true);
     std::vector<double> r0(nd), rn(nd), bn(nd);
     std::vector<int> act(nd), itd(nd, 0);
