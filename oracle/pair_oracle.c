@@ -8,8 +8,9 @@
  * and by the benchmark's CPU-baseline leg.  The product library never links,
  * loads or calls it, and it shares no code with the CUDA sources.
  *
- * Build: gcc -O2 -ffp-contract=off -fPIC -shared (no FMA contraction, so every
- * product and sum is rounded exactly as written).
+ * Build: gcc -O2 -ffp-contract=off -fPIC -shared (no implicit FMA contraction,
+ * so every product and sum is rounded exactly as written; the few fused
+ * multiply-adds are explicit fma() calls).
  *
  * Contents (each function cites the passage it follows):
  *   - dense LU with partial pivoting (element blocks, lAIR local systems)
@@ -52,8 +53,9 @@ static const double OR_PI = 3.14159265358979323846;
 /* ------------------------------------------------------------------------- */
 /* Dense LU with partial pivoting (row-major n x n).                          */
 /* Pivot = first row with the largest |entry| in the column; full rows are    */
-/* swapped (LAPACK convention P A = L U); multipliers stored below the        */
-/* diagonal.  Singular if the pivot magnitude is not above 'tiny'.            */
+/* swapped (LAPACK convention P A = L U); multipliers l = a_rk * (1 / a_kk)   */
+/* stored below the diagonal; updates a_rc <- fma(-l, a_kc, a_rc) (one        */
+/* rounding).  Singular if the pivot magnitude is not above 'tiny'.           */
 /* ------------------------------------------------------------------------- */
 static int lu_factor(int n, double *a, int *piv, double tiny)
 {
@@ -71,27 +73,27 @@ static int lu_factor(int n, double *a, int *piv, double tiny)
                 double t = a[k * n + c]; a[k * n + c] = a[p * n + c]; a[p * n + c] = t;
             }
         }
-        double d = a[k * n + k];
+        double rd = 1.0 / a[k * n + k];
         for (int r = k + 1; r < n; ++r) {
-            double l = a[r * n + k] / d;
+            double l = a[r * n + k] * rd;
             a[r * n + k] = l;
-            for (int c = k + 1; c < n; ++c) a[r * n + c] = a[r * n + c] - l * a[k * n + c];
+            for (int c = k + 1; c < n; ++c) a[r * n + c] = fma(-l, a[k * n + c], a[r * n + c]);
         }
     }
     return 0;
 }
 
 /* Solve with the factors: swaps in order, unit-lower forward substitution by
- * columns, upper back substitution by columns. */
+ * columns, upper back substitution by columns (y_k <- y_k * (1 / u_kk)). */
 static void lu_solve(int n, const double *a, const int *piv, double *y)
 {
     for (int k = 0; k < n; ++k)
         if (piv[k] != k) { double t = y[k]; y[k] = y[piv[k]]; y[piv[k]] = t; }
     for (int k = 0; k < n; ++k)
-        for (int r = k + 1; r < n; ++r) y[r] = y[r] - a[r * n + k] * y[k];
+        for (int r = k + 1; r < n; ++r) y[r] = fma(-a[r * n + k], y[k], y[r]);
     for (int k = n - 1; k >= 0; --k) {
-        y[k] = y[k] / a[k * n + k];
-        for (int r = 0; r < k; ++r) y[r] = y[r] - a[r * n + k] * y[k];
+        y[k] = y[k] * (1.0 / a[k * n + k]);
+        for (int r = 0; r < k; ++r) y[r] = fma(-a[r * n + k], y[k], y[r]);
     }
 }
 
@@ -659,7 +661,8 @@ static int lair(olevel *L, const signed char *SR, int distance, double phi_R)
 /* Galerkin coarse operator A_c = R A P (Sec. 1.2; Sec. 4.1.2 stencil growth).
  * (AP)[k,c] = sum_l a_kl over l ascending with pmap(l) = c;
  * (RAP)[ic,c] = sum_k R[ic,k] (AP)[k,c] over the R row in ascending column
- * order, the identity entry (k = C point of ic) included in place.
+ * order, the identity entry (k = C point of ic) included in place, each term
+ * accumulated with one fused multiply-add.
  * Every structural product is kept (exact zeros included). */
 static int rap(const olevel *L, olevel *C, double phi_A)
 {
@@ -711,7 +714,7 @@ static int rap(const olevel *L, olevel *C, double phi_A)
             for (int p = aprow[k]; p < aprow[k + 1]; ++p) {
                 int c = apcol[p];
                 if (where[c] < 0) { where[c] = nl; list[nl++] = c; acc[c] = 0.0; }
-                acc[c] = acc[c] + r * apval[p];
+                acc[c] = fma(r, apval[p], acc[c]);
             }
         }
         qsort(list, nl, sizeof(int), cmp_int);

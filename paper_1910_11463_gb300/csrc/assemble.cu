@@ -1,7 +1,8 @@
 // Upwind DG assembly on the structured hex Q1 mesh with block-inverse scaling
 // (Eq. weak_form_transport; Sec. 1.3).  Compiled with --fmad=false: every
-// product and sum below is rounded as written, in the order written, so the
-// scaled operator is reproducible bit for bit.
+// product and sum below is rounded as written, in the order written (fused
+// multiply-adds only where fma() is written), so the scaled operator is
+// reproducible bit for bit.
 //
 // One thread per (element, direction).  Per element K and direction Omega:
 //   m1[i][j] = (2 or 1) h / 6,  g1[i][j] = -1/2 (i = 0), +1/2 (i = 1)
@@ -17,6 +18,9 @@ namespace pr {
 
 namespace {
 
+// LU with partial pivoting (first maximum), multipliers a_rk * (1 / a_kk),
+// updates fma(-l, a_kc, a_rc); column-oriented substitutions with fma and
+// y_k * (1 / u_kk).  The same operation sequence as every LU in the library.
 __device__ __forceinline__ void lu_factor8(double *a, int *piv, int *singular) {
     const int n = 8;
     for (int k = 0; k < n; ++k) {
@@ -30,11 +34,11 @@ __device__ __forceinline__ void lu_factor8(double *a, int *piv, int *singular) {
         if (!(mx > 0.0)) { *singular = 1; return; }
         if (p != k)
             for (int c = 0; c < n; ++c) { double t = a[k * n + c]; a[k * n + c] = a[p * n + c]; a[p * n + c] = t; }
-        double d = a[k * n + k];
+        double rd = 1.0 / a[k * n + k];
         for (int r = k + 1; r < n; ++r) {
-            double l = a[r * n + k] / d;
+            double l = a[r * n + k] * rd;
             a[r * n + k] = l;
-            for (int c = k + 1; c < n; ++c) a[r * n + c] = a[r * n + c] - l * a[k * n + c];
+            for (int c = k + 1; c < n; ++c) a[r * n + c] = fma(-l, a[k * n + c], a[r * n + c]);
         }
     }
 }
@@ -44,10 +48,10 @@ __device__ __forceinline__ void lu_solve8(const double *a, const int *piv, doubl
     for (int k = 0; k < n; ++k)
         if (piv[k] != k) { double t = y[k]; y[k] = y[piv[k]]; y[piv[k]] = t; }
     for (int k = 0; k < n; ++k)
-        for (int r = k + 1; r < n; ++r) y[r] = y[r] - a[r * n + k] * y[k];
+        for (int r = k + 1; r < n; ++r) y[r] = fma(-a[r * n + k], y[k], y[r]);
     for (int k = n - 1; k >= 0; --k) {
-        y[k] = y[k] / a[k * n + k];
-        for (int r = 0; r < k; ++r) y[r] = y[r] - a[r * n + k] * y[k];
+        y[k] = y[k] * (1.0 / a[k * n + k]);
+        for (int r = 0; r < k; ++r) y[r] = fma(-a[r * n + k], y[k], y[r]);
     }
 }
 

@@ -3,8 +3,8 @@
 // A hierarchy holds a batch of independent matrices; every level of every
 // matrix is processed by one launch per step.  Compiled with --fmad=false and
 // written so that each floating-point result is formed by the same operations
-// in the same order as the plain definitions below, hence reproducible bit for
-// bit:
+// in the same order as the plain definitions below (fused multiply-adds only
+// where fma() is written), hence reproducible bit for bit:
 //   strength   S_i = {j != i : |a_ij| >= theta * max_{k != i} |a_ik|}, empty if the max is 0
 //   PMIS       key_i = (lambda_i, h_i, i), lambda_i = #{k : i in S_k},
 //              h_i = top 32 bits of SplitMix64 at state seed ^ (level << 40) ^ i (local i);
@@ -16,8 +16,10 @@
 //              pivot, full row swaps, column-oriented substitutions); optional phi_R filter
 //   RAP        (AP)[k,c] = sum over l ascending (pmap(l) = c) of a_kl, starting from 0.0;
 //              (RAP)[i,c] = sum over the R row in ascending column order (identity at
-//              its place) of R_ik (AP)[k,c], starting from 0.0; every structural product
-//              kept; optional phi_A filter of off-diagonal entries
+//              its place) of R_ik (AP)[k,c], starting from 0.0, one fma per term; every
+//              structural product kept; optional phi_A filter of off-diagonal entries
+//   LU         multipliers a_rk * (1 / a_kk), updates fma(-l, a_kc, a_rc), substitutions
+//              by columns with fma, y_k * (1 / u_kk)
 #include <algorithm>
 #include <cstdio>
 
@@ -275,6 +277,84 @@ __device__ __forceinline__ int pat_find(const int *pat, int np, int k) {
     return -1;
 }
 
+// Thread per C row of the worklist, systems of size <= 16 (all lanes busy on
+// independent systems; the FP64 pipe is the limit on this part).  Same
+// operation sequence as the warp kernel and the definitions above.
+__global__ void __launch_bounds__(128) k_lair_solve_thread(int nwork, const int *worklist, const int *cpts,
+                                                           const int *rowptr, const int *col, const double *val,
+                                                           const int *candptr, const int *cand, const int *npat,
+                                                           const int *zrowptr, int *zcol, double *zval, int *keep,
+                                                           int *nsing_dir, const int *rowdir, double phi_R) {
+    int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= nwork) return;
+    int ic = worklist[w];
+    int i = cpts[ic];
+    int np = npat[ic];
+    if (np > 16) { keep[ic] = 0; return; }   // excluded by the size bins
+    double M[256], y[16];
+    int pat[16], piv[16];
+    const int *cp = cand + candptr[ic];
+    for (int t = 0; t < np; ++t) { pat[t] = cp[t]; y[t] = -0.0; }
+    for (int t = 0; t < np * np; ++t) M[t] = 0.0;
+    for (int c = 0; c < np; ++c) {
+        int j = pat[c];
+        for (int p = rowptr[j]; p < rowptr[j + 1]; ++p) {
+            int r = pat_find(pat, np, col[p]);
+            if (r >= 0) M[r * np + c] = val[p];
+        }
+    }
+    for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+        int r = pat_find(pat, np, col[p]);
+        if (r >= 0) y[r] = -val[p];
+    }
+    double mx = 0.0;
+    for (int t = 0; t < np * np; ++t) mx = fmax(mx, fabs(M[t]));
+    double tiny = 1e-14 * mx;
+    bool singular = false;
+    for (int k = 0; k < np && !singular; ++k) {
+        int p = k;
+        double pv = fabs(M[k * np + k]);
+        for (int r = k + 1; r < np; ++r) {
+            double v = fabs(M[r * np + k]);
+            if (v > pv) { pv = v; p = r; }
+        }
+        piv[k] = p;
+        if (!(pv > tiny)) { singular = true; break; }
+        if (p != k)
+            for (int c = 0; c < np; ++c) { double t = M[k * np + c]; M[k * np + c] = M[p * np + c]; M[p * np + c] = t; }
+        double rd = 1.0 / M[k * np + k];
+        for (int r = k + 1; r < np; ++r) {
+            double l = M[r * np + k] * rd;
+            M[r * np + k] = l;
+            for (int c = k + 1; c < np; ++c) M[r * np + c] = fma(-l, M[k * np + c], M[r * np + c]);
+        }
+    }
+    int kept = 0;
+    if (singular) {
+        atomicAdd(&nsing_dir[rowdir[i]], 1);
+    } else if (np > 0) {
+        for (int k = 0; k < np; ++k)
+            if (piv[k] != k) { double t = y[k]; y[k] = y[piv[k]]; y[piv[k]] = t; }
+        for (int k = 0; k < np; ++k)
+            for (int r = k + 1; r < np; ++r) y[r] = fma(-M[r * np + k], y[k], y[r]);
+        for (int k = np - 1; k >= 0; --k) {
+            y[k] = y[k] * (1.0 / M[k * np + k]);
+            for (int r = 0; r < k; ++r) y[r] = fma(-M[r * np + k], y[k], y[r]);
+        }
+        double zm = 0.0;
+        for (int t = 0; t < np; ++t) zm = fmax(zm, fabs(y[t]));
+        double thr = phi_R * zm;
+        int base = zrowptr[ic];
+        for (int t = 0; t < np; ++t) {
+            if (phi_R > 0.0 && fabs(y[t]) < thr) continue;
+            zcol[base + kept] = pat[t];
+            zval[base + kept] = y[t];
+            ++kept;
+        }
+    }
+    keep[ic] = kept;
+}
+
 // Warp per C row of the worklist.  Shared-memory mode (gbuf == null): systems
 // of size <= nmax, workspace in shared memory.  Global mode: workspace at
 // gbuf + goff[w] (systems larger than the biggest shared-memory bin).
@@ -351,13 +431,13 @@ __global__ void k_lair_solve(int nwork, const int *worklist, const int *cpts, co
                     M[br * np + c] = t;
                 }
             __syncwarp();
-            double dk = M[k * np + k];
-            for (int r = k + 1 + lane; r < np; r += 32) M[r * np + k] = M[r * np + k] / dk;
+            double rd = 1.0 / M[k * np + k];
+            for (int r = k + 1 + lane; r < np; r += 32) M[r * np + k] = M[r * np + k] * rd;
             __syncwarp();
             int w = np - k - 1;
             for (int idx = lane; idx < w * w; idx += 32) {
                 int r = k + 1 + idx / w, c = k + 1 + idx % w;
-                M[r * np + c] = M[r * np + c] - M[r * np + k] * M[k * np + c];
+                M[r * np + c] = fma(-M[r * np + k], M[k * np + c], M[r * np + c]);
             }
             __syncwarp();
         }
@@ -370,14 +450,14 @@ __global__ void k_lair_solve(int nwork, const int *worklist, const int *cpts, co
             __syncwarp();
             for (int k = 0; k < np; ++k) {
                 double yk = y[k];
-                for (int r = k + 1 + lane; r < np; r += 32) y[r] = y[r] - M[r * np + k] * yk;
+                for (int r = k + 1 + lane; r < np; r += 32) y[r] = fma(-M[r * np + k], yk, y[r]);
                 __syncwarp();
             }
             for (int k = np - 1; k >= 0; --k) {
-                if (lane == 0) y[k] = y[k] / M[k * np + k];
+                if (lane == 0) y[k] = y[k] * (1.0 / M[k * np + k]);
                 __syncwarp();
                 double yk = y[k];
-                for (int r = lane; r < k; r += 32) y[r] = y[r] - M[r * np + k] * yk;
+                for (int r = lane; r < k; r += 32) y[r] = fma(-M[r * np + k], yk, y[r]);
                 __syncwarp();
             }
             double zm = 0.0;
@@ -416,14 +496,40 @@ __global__ void k_compact_rows(int nrows, const int *oldptr, const int *newptr, 
 }
 
 // ---- RAP ---------------------------------------------------------------------
+// Thread per fine row k: (AP)[k,c] accumulated in ascending l order, then
+// sorted by c.  Rows of up to 64 entries work in local arrays, longer rows in
+// their output slots.
 __global__ void k_ap(int n, const int *rowptr, const int *col, const double *val, const int *pmap,
                      const int8_t *cf, int *aplen, int *apcol, double *apval) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     if (cf[k] == CF_COARSEST) { aplen[k] = 0; return; }
-    int s = rowptr[k];
+    int s = rowptr[k], e = rowptr[k + 1];
     int len = 0;
-    for (int p = rowptr[k]; p < rowptr[k + 1]; ++p) {
+    if (e - s <= 64) {
+        int lc[64];
+        double lv[64];
+        for (int p = s; p < e; ++p) {
+            int c = pmap[col[p]];
+            if (c < 0) continue;
+            int t = 0;
+            while (t < len && lc[t] != c) ++t;
+            if (t == len) { lc[t] = c; lv[t] = 0.0; ++len; }
+            lv[t] = lv[t] + val[p];
+        }
+        for (int a = 1; a < len; ++a) {
+            int c = lc[a];
+            double v = lv[a];
+            int b = a;
+            while (b > 0 && lc[b - 1] > c) { lc[b] = lc[b - 1]; lv[b] = lv[b - 1]; --b; }
+            lc[b] = c;
+            lv[b] = v;
+        }
+        for (int t = 0; t < len; ++t) { apcol[s + t] = lc[t]; apval[s + t] = lv[t]; }
+        aplen[k] = len;
+        return;
+    }
+    for (int p = s; p < e; ++p) {
         int c = pmap[col[p]];
         if (c < 0) continue;
         int t = 0;
@@ -455,6 +561,7 @@ __device__ __forceinline__ unsigned hslot(int c, unsigned mask) { return ((unsig
 // Warp per coarse row.  Table: keys (int, -1 empty) and values, in shared
 // memory (cap = hcap) or in global scratch (cap per row given by gcap/gptr).
 // Output: sorted, filtered entries at ucol/uval[uptr[ic]...], count in cnt[ic].
+template <bool GLOBAL_TABLE>
 __global__ void k_rap(int nrows_work, const int *worklist, int nc, const int *cpts, const int *zrowptr,
                       const int *zcol, const double *zval, const int *aprow, const int *aplen, const int *apcol,
                       const double *apval, const int *uptr, const int *U, double phiA, int *cnt, int *ucol,
@@ -467,7 +574,7 @@ __global__ void k_rap(int nrows_work, const int *worklist, int nc, const int *cp
         int *keys;
         double *vals;
         int cap;
-        if (gptr) {
+        if (GLOBAL_TABLE) {
             long long off = gptr[w];
             cap = (int)(gptr[w + 1] - off);
             keys = gkeys + off;
@@ -508,7 +615,7 @@ __global__ void k_rap(int nrows_work, const int *worklist, int nc, const int *cp
                     if (prev == c) { ok = true; break; }
                     hs = (hs + 1) & mask;
                 }
-                if (ok) vals[hs] = vals[hs] + r * v;
+                if (ok) vals[hs] = fma(r, v, vals[hs]);
                 else atomicOr(err, DERR_HASH_OVERFLOW);
             }
             __syncwarp();
@@ -811,8 +918,15 @@ void build_hierarchy(Hier &h) {
             int *list = dmalloc<int>(nc, s);
             k_lair_class_fill<<<blocks_for(nc, BS), BS, 0, s>>>(nc, npat, ccount, ccount + 5, list);
             PR_LAUNCH();
+            int nsmall = hc[0] + hc[1];   // classes 0 and 1 are contiguous in the list
+            if (nsmall) {
+                k_lair_solve_thread<<<blocks_for(nsmall, 128), 128, 0, s>>>(
+                    nsmall, list + hstart[0], L.cpts, L.rowptr, L.col, L.val, candptr, cand, npat, zr, zc, zv, keep,
+                    dsing, L.rowdir, prm.phi_R);
+                PR_LAUNCH();
+            }
             const int cls_n[4] = {8, 16, 32, 64};
-            for (int c = 0; c < 4; ++c) {
+            for (int c = 2; c < 4; ++c) {
                 if (!hc[c]) continue;
                 int nm = cls_n[c];
                 size_t per = ((size_t)nm * nm + 2 * nm) * sizeof(double);
@@ -880,10 +994,10 @@ void build_hierarchy(Hier &h) {
         {
             const int hcap = 2048, wpb = 4;
             size_t sm = (size_t)hcap * wpb * (sizeof(double) + sizeof(int));
-            PR_CUDA(cudaFuncSetAttribute(k_rap, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            PR_CUDA(cudaFuncSetAttribute(k_rap<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
             PR_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int), s));
             unsigned grid = std::min<unsigned>(blocks_for(nc, wpb), 152u * 32u);
-            k_rap<<<grid, 32 * wpb, sm, s>>>(nc, nullptr, nc, L.cpts, L.zrowptr, L.zcol, L.zval, L.rowptr, aplen,
+            k_rap<false><<<grid, 32 * wpb, sm, s>>>(nc, nullptr, nc, L.cpts, L.zrowptr, L.zcol, L.zval, L.rowptr, aplen,
                                              apcol, apval, uptr, U, prm.phi_A, cnt, ucol, uval, hcap, nullptr,
                                              nullptr, nullptr, d_count, h.d_err);
             PR_LAUNCH();
@@ -904,7 +1018,7 @@ void build_hierarchy(Hier &h) {
                 d2h(&gtot, capw + nover, 1, s);
                 int *gk = dmalloc<int>(gtot, s);
                 double *gv = dmalloc<double>(gtot, s);
-                k_rap<<<std::min<unsigned>(nover, 152u * 16u), 32, 0, s>>>(
+                k_rap<true><<<std::min<unsigned>(nover, 152u * 16u), 32, 0, s>>>(
                     nover, list, nc, L.cpts, L.zrowptr, L.zcol, L.zval, L.rowptr, aplen, apcol, apval, uptr, U,
                     prm.phi_A, cnt, ucol, uval, 0, capw, gk, gv, d_count, h.d_err);
                 PR_LAUNCH();
