@@ -277,215 +277,149 @@ __device__ __forceinline__ int pat_find(const int *pat, int np, int k) {
     return -1;
 }
 
-// Thread per C row of the worklist, systems of size <= 16 (all lanes busy on
-// independent systems; the FP64 pipe is the limit on this part).  Same
-// operation sequence as the warp kernel and the definitions above.
-__global__ void __launch_bounds__(128) k_lair_solve_thread(int nwork, const int *worklist, const int *cpts,
-                                                           const int *rowptr, const int *col, const double *val,
-                                                           const int *candptr, const int *cand, const int *npat,
-                                                           const int *zrowptr, int *zcol, double *zval, int *keep,
-                                                           int *nsing_dir, const int *rowdir, double phi_R) {
-    int w = blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= nwork) return;
-    int ic = worklist[w];
-    int i = cpts[ic];
-    int np = npat[ic];
-    if (np > 16) { keep[ic] = 0; return; }   // excluded by the size bins
-    double M[256], y[16];
-    int pat[16], piv[16];
-    const int *cp = cand + candptr[ic];
-    for (int t = 0; t < np; ++t) { pat[t] = cp[t]; y[t] = -0.0; }
-    for (int t = 0; t < np * np; ++t) M[t] = 0.0;
-    for (int c = 0; c < np; ++c) {
-        int j = pat[c];
-        for (int p = rowptr[j]; p < rowptr[j + 1]; ++p) {
-            int r = pat_find(pat, np, col[p]);
-            if (r >= 0) M[r * np + c] = val[p];
-        }
-    }
-    for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) {
-        int r = pat_find(pat, np, col[p]);
-        if (r >= 0) y[r] = -val[p];
-    }
-    double mx = 0.0;
-    for (int t = 0; t < np * np; ++t) mx = fmax(mx, fabs(M[t]));
-    double tiny = 1e-14 * mx;
-    bool singular = false;
-    for (int k = 0; k < np && !singular; ++k) {
-        int p = k;
-        double pv = fabs(M[k * np + k]);
-        for (int r = k + 1; r < np; ++r) {
-            double v = fabs(M[r * np + k]);
-            if (v > pv) { pv = v; p = r; }
-        }
-        piv[k] = p;
-        if (!(pv > tiny)) { singular = true; break; }
-        if (p != k)
-            for (int c = 0; c < np; ++c) { double t = M[k * np + c]; M[k * np + c] = M[p * np + c]; M[p * np + c] = t; }
-        double rd = 1.0 / M[k * np + k];
-        for (int r = k + 1; r < np; ++r) {
-            double l = M[r * np + k] * rd;
-            M[r * np + k] = l;
-            for (int c = k + 1; c < np; ++c) M[r * np + c] = fma(-l, M[k * np + c], M[r * np + c]);
-        }
-    }
-    int kept = 0;
-    if (singular) {
-        atomicAdd(&nsing_dir[rowdir[i]], 1);
-    } else if (np > 0) {
-        for (int k = 0; k < np; ++k)
-            if (piv[k] != k) { double t = y[k]; y[k] = y[piv[k]]; y[piv[k]] = t; }
-        for (int k = 0; k < np; ++k)
-            for (int r = k + 1; r < np; ++r) y[r] = fma(-M[r * np + k], y[k], y[r]);
-        for (int k = np - 1; k >= 0; --k) {
-            y[k] = y[k] * (1.0 / M[k * np + k]);
-            for (int r = 0; r < k; ++r) y[r] = fma(-M[r * np + k], y[k], y[r]);
-        }
-        double zm = 0.0;
-        for (int t = 0; t < np; ++t) zm = fmax(zm, fabs(y[t]));
-        double thr = phi_R * zm;
-        int base = zrowptr[ic];
-        for (int t = 0; t < np; ++t) {
-            if (phi_R > 0.0 && fabs(y[t]) < thr) continue;
-            zcol[base + kept] = pat[t];
-            zval[base + kept] = y[t];
-            ++kept;
-        }
-    }
-    keep[ic] = kept;
-}
-
-// Warp per C row of the worklist.  Shared-memory mode (gbuf == null): systems
-// of size <= nmax, workspace in shared memory.  Global mode: workspace at
-// gbuf + goff[w] (systems larger than the biggest shared-memory bin).
+// G lanes per C row of the worklist (32/G systems per warp).  Shared-memory
+// mode (gbuf == null): systems of size <= nmax, workspace nmax^2 + 2 nmax
+// doubles per group.  Global mode: workspace at gbuf + goff[w].
+template <int G>
 __global__ void k_lair_solve(int nwork, const int *worklist, const int *cpts, const int *rowptr, const int *col,
                              const double *val, const int *candptr, const int *cand, const int *npat,
                              const int *zrowptr, int *zcol, double *zval, int *keep, int *nsing_dir,
-                             const int *rowdir, double phi_R, int nmax, const long long *goff, double *gbuf,
-                             int *nbig) {
+                             const int *rowdir, double phi_R, int nmax, const long long *goff, double *gbuf) {
     extern __shared__ double smem[];
+    const unsigned FULL = 0xffffffffu;
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int g = lane % G, q = lane / G;
     int wpb = blockDim.x >> 5;
-    for (int w = blockIdx.x * wpb + warp; w < nwork; w += gridDim.x * wpb) {
-        int ic = worklist ? worklist[w] : w;
-        int i = cpts[ic];
-        int np = npat[ic];
-        double *M;
-        if (gbuf) {
-            M = gbuf + goff[w];
-        } else {
-            if (np > nmax) {   // cannot happen with the size bins; keep the bound explicit
-                if (lane == 0) { keep[ic] = 0; atomicAdd(nbig, 1); }
-                continue;
-            }
-            M = smem + (size_t)warp * ((size_t)nmax * nmax + 2 * nmax);
-        }
+    constexpr int SPW = 32 / G;   // systems per warp
+    for (int wb = (blockIdx.x * wpb + warp) * SPW; wb < nwork; wb += gridDim.x * wpb * SPW) {
+        int w = wb + q;
+        bool has = w < nwork;
+        int ic = has ? worklist[w] : 0;
+        int i = has ? cpts[ic] : 0;
+        int np = has ? npat[ic] : 0;
+        double *M = gbuf ? gbuf + (has ? goff[w] : 0)
+                         : smem + ((size_t)warp * SPW + q) * ((size_t)nmax * nmax + 2 * nmax);
         double *y = M + (size_t)np * np;
         int *pat = (int *)(y + np);
         int *piv = pat + np;
-        const int *cp = cand + candptr[ic];
-        for (int t = lane; t < np; t += 32) pat[t] = cp[t];
-        for (int idx = lane; idx < np * np; idx += 32) M[idx] = 0.0;
-        // absent right-hand-side entries are -0.0: the negation of a stored zero
-        for (int r = lane; r < np; r += 32) y[r] = -0.0;
-        __syncwarp();
-        // M[r][c] = a(pat[c], pat[r]): lane per pattern row, one pass over that row of A,
-        // column positions found by binary search in the (sorted) pattern
-        for (int c = lane; c < np; c += 32) {
-            int j = pat[c];
-            for (int p = rowptr[j]; p < rowptr[j + 1]; ++p) {
-                int r = pat_find(pat, np, col[p]);
-                if (r >= 0) M[r * np + c] = val[p];
-            }
+        if (has) {
+            const int *cp = cand + candptr[ic];
+            for (int t = g; t < np; t += G) { pat[t] = cp[t]; y[t] = -0.0; }
+            for (int idx = g; idx < np * np; idx += G) M[idx] = 0.0;
         }
-        for (int p = rowptr[i] + lane; p < rowptr[i + 1]; p += 32) {
-            int r = pat_find(pat, np, col[p]);
-            if (r >= 0) y[r] = -val[p];
+        __syncwarp();
+        if (has) {
+            // M[r][c] = a(pat[c], pat[r]): lane per pattern row, one pass over it
+            for (int c = g; c < np; c += G) {
+                int j = pat[c];
+                for (int p = rowptr[j]; p < rowptr[j + 1]; ++p) {
+                    int r = pat_find(pat, np, col[p]);
+                    if (r >= 0) M[r * np + c] = val[p];
+                }
+            }
+            for (int p = rowptr[i] + g; p < rowptr[i + 1]; p += G) {
+                int r = pat_find(pat, np, col[p]);
+                if (r >= 0) y[r] = -val[p];
+            }
         }
         __syncwarp();
         double mx = 0.0;
-        for (int idx = lane; idx < np * np; idx += 32) mx = fmax(mx, fabs(M[idx]));
-        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        for (int idx = g; idx < np * np; idx += G) mx = fmax(mx, fabs(M[idx]));
+        for (int o = G / 2; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(FULL, mx, o, G));
         double tiny = 1e-14 * mx;
-        __syncwarp();
+        int kmax = np;
+        for (int o = 16; o > 0; o >>= 1) kmax = max(kmax, __shfl_xor_sync(FULL, kmax, o));
         bool singular = false;
-        for (int k = 0; k < np; ++k) {
-            // pivot: largest |M[r][k]|, r >= k, smallest r among equals
+        for (int k = 0; k < kmax; ++k) {
+            bool act = k < np && !singular;
             double bv = -1.0;
             int br = k;
-            for (int r = k + lane; r < np; r += 32) {
-                double v = fabs(M[r * np + k]);
-                if (v > bv) { bv = v; br = r; }
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-                int orr = __shfl_xor_sync(0xffffffffu, br, o);
+            if (act)
+                for (int r = k + g; r < np; r += G) {
+                    double v = fabs(M[r * np + k]);
+                    if (v > bv) { bv = v; br = r; }
+                }
+            for (int o = G / 2; o > 0; o >>= 1) {
+                double ov = __shfl_xor_sync(FULL, bv, o, G);
+                int orr = __shfl_xor_sync(FULL, br, o, G);
                 if (ov > bv || (ov == bv && orr < br)) { bv = ov; br = orr; }
             }
-            if (!(bv > tiny)) { singular = true; break; }
-            if (lane == 0) piv[k] = br;
-            if (br != k)
-                for (int c = lane; c < np; c += 32) {
-                    double t = M[k * np + c];
-                    M[k * np + c] = M[br * np + c];
-                    M[br * np + c] = t;
+            if (act && !(bv > tiny)) { singular = true; act = false; }
+            if (act) {
+                if (g == 0) piv[k] = br;
+                if (br != k)
+                    for (int c = g; c < np; c += G) {
+                        double t = M[k * np + c];
+                        M[k * np + c] = M[br * np + c];
+                        M[br * np + c] = t;
+                    }
+            }
+            __syncwarp();
+            if (act) {
+                double rd = 1.0 / M[k * np + k];
+                for (int r = k + 1 + g; r < np; r += G) M[r * np + k] = M[r * np + k] * rd;
+            }
+            __syncwarp();
+            if (act) {
+                int wd = np - k - 1;
+                for (int idx = g; idx < wd * wd; idx += G) {
+                    int r = k + 1 + idx / wd, c = k + 1 + idx % wd;
+                    M[r * np + c] = fma(-M[r * np + k], M[k * np + c], M[r * np + c]);
                 }
-            __syncwarp();
-            double rd = 1.0 / M[k * np + k];
-            for (int r = k + 1 + lane; r < np; r += 32) M[r * np + k] = M[r * np + k] * rd;
-            __syncwarp();
-            int w = np - k - 1;
-            for (int idx = lane; idx < w * w; idx += 32) {
-                int r = k + 1 + idx / w, c = k + 1 + idx % w;
-                M[r * np + c] = fma(-M[r * np + k], M[k * np + c], M[r * np + c]);
             }
             __syncwarp();
         }
+        bool solve = has && !singular && np > 0;
+        if (solve && g == 0)
+            for (int k = 0; k < np; ++k)
+                if (piv[k] != k) { double t = y[k]; y[k] = y[piv[k]]; y[piv[k]] = t; }
+        __syncwarp();
+        for (int k = 0; k < kmax; ++k) {
+            if (solve && k < np) {
+                double yk = y[k];
+                for (int r = k + 1 + g; r < np; r += G) y[r] = fma(-M[r * np + k], yk, y[r]);
+            }
+            __syncwarp();
+        }
+        for (int k = kmax - 1; k >= 0; --k) {
+            if (solve && k < np && g == 0) y[k] = y[k] * (1.0 / M[k * np + k]);
+            __syncwarp();
+            if (solve && k < np) {
+                double yk = y[k];
+                for (int r = g; r < k; r += G) y[r] = fma(-M[r * np + k], yk, y[r]);
+            }
+            __syncwarp();
+        }
+        double zm = 0.0;
+        if (solve)
+            for (int t = g; t < np; t += G) zm = fmax(zm, fabs(y[t]));
+        for (int o = G / 2; o > 0; o >>= 1) zm = fmax(zm, __shfl_xor_sync(FULL, zm, o, G));
+        double thr = phi_R * zm;
         int kept = 0;
-        if (!singular && np > 0) {
-            if (lane == 0) {
-                for (int k = 0; k < np; ++k)
-                    if (piv[k] != k) { double t = y[k]; y[k] = y[piv[k]]; y[piv[k]] = t; }
+        int base = has ? zrowptr[ic] : 0;
+        int tmax = np;
+        for (int o = 16; o > 0; o >>= 1) tmax = max(tmax, __shfl_xor_sync(FULL, tmax, o));
+        // keep in ascending order: ballot-compacted write within the group
+        unsigned gmask = (G == 32) ? FULL : (((1u << G) - 1u) << (q * G));
+        for (int t0 = 0; t0 < tmax; t0 += G) {
+            int t = t0 + g;
+            bool k_ = solve && t < np && !(phi_R > 0.0 && fabs(y[t]) < thr);
+            unsigned msk = __ballot_sync(FULL, k_) & gmask;
+            if (k_) {
+                int off = kept + __popc(msk & ((1u << lane) - 1u));
+                zcol[base + off] = pat[t];
+                zval[base + off] = y[t];
             }
-            __syncwarp();
-            for (int k = 0; k < np; ++k) {
-                double yk = y[k];
-                for (int r = k + 1 + lane; r < np; r += 32) y[r] = fma(-M[r * np + k], yk, y[r]);
-                __syncwarp();
-            }
-            for (int k = np - 1; k >= 0; --k) {
-                if (lane == 0) y[k] = y[k] * (1.0 / M[k * np + k]);
-                __syncwarp();
-                double yk = y[k];
-                for (int r = lane; r < k; r += 32) y[r] = fma(-M[r * np + k], yk, y[r]);
-                __syncwarp();
-            }
-            double zm = 0.0;
-            for (int t = lane; t < np; t += 32) zm = fmax(zm, fabs(y[t]));
-            for (int o = 16; o > 0; o >>= 1) zm = fmax(zm, __shfl_xor_sync(0xffffffffu, zm, o));
-            double thr = phi_R * zm;
-            // keep in ascending order: ballot-compacted write
-            int base = zrowptr[ic];
-            for (int t0 = 0; t0 < np; t0 += 32) {
-                int t = t0 + lane;
-                bool k_ = t < np && !(phi_R > 0.0 && fabs(y[t]) < thr);
-                unsigned msk = __ballot_sync(0xffffffffu, k_);
-                if (k_) {
-                    int off = kept + __popc(msk & ((1u << lane) - 1u));
-                    zcol[base + off] = pat[t];
-                    zval[base + off] = y[t];
-                }
-                kept += __popc(msk);
-            }
-        } else if (singular && lane == 0) {
-            atomicAdd(&nsing_dir[rowdir[i]], 1);
+            kept += __popc(msk);
         }
-        if (lane == 0) keep[ic] = kept;
+        if (has && g == 0) {
+            if (singular) atomicAdd(&nsing_dir[rowdir[i]], 1);
+            keep[ic] = solve ? kept : 0;
+        }
         __syncwarp();
     }
 }
 
-// 8 lanes per row: copies the first (newptr[r+1]-newptr[r]) entries of each old row
 __global__ void k_compact_rows(int nrows, const int *oldptr, const int *newptr, const int *col_in,
                                const double *val_in, int *col_out, double *val_out) {
     long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -690,6 +624,28 @@ __global__ void k_fill_int8(int n, int8_t *a, int8_t v) {
 __global__ void k_fill_int(int n, int *a, int v) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) a[i] = v;
+}
+
+__device__ __forceinline__ int rap_bin(int u) { return 2 * u <= 256 ? 0 : 2 * u <= 1024 ? 1 : 2 * u <= 4096 ? 2 : 3; }
+
+__global__ void k_rap_bin_count(int nc, const int *U, int *cnt) {
+    int ic = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ic < nc) atomicAdd(&cnt[rap_bin(U[ic])], 1);
+}
+
+__global__ void k_rap_bin_fill(int nc, const int *U, const int *start, int *fill, int *list) {
+    int ic = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ic >= nc) return;
+    int c = rap_bin(U[ic]);
+    list[start[c] + atomicAdd(&fill[c], 1)] = ic;
+}
+
+__global__ void k_overflow_caps(int nover, const int *list, const int *U, long long *capw) {
+    int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= nover) return;
+    long long c = 64;
+    while (c < 2LL * U[list[w]]) c <<= 1;
+    capw[w] = c;
 }
 
 __global__ void k_overflow_list(int nc, const int *cnt, int *flag) {
@@ -918,26 +874,29 @@ void build_hierarchy(Hier &h) {
             int *list = dmalloc<int>(nc, s);
             k_lair_class_fill<<<blocks_for(nc, BS), BS, 0, s>>>(nc, npat, ccount, ccount + 5, list);
             PR_LAUNCH();
-            int nsmall = hc[0] + hc[1];   // classes 0 and 1 are contiguous in the list
-            if (nsmall) {
-                k_lair_solve_thread<<<blocks_for(nsmall, 128), 128, 0, s>>>(
-                    nsmall, list + hstart[0], L.cpts, L.rowptr, L.col, L.val, candptr, cand, npat, zr, zc, zv, keep,
-                    dsing, L.rowdir, prm.phi_R);
-                PR_LAUNCH();
-            }
+            // n <= 16: 8 lanes per system; larger: a warp per system
             const int cls_n[4] = {8, 16, 32, 64};
-            for (int c = 2; c < 4; ++c) {
+            for (int c = 0; c < 4; ++c) {
                 if (!hc[c]) continue;
                 int nm = cls_n[c];
-                size_t per = ((size_t)nm * nm + 2 * nm) * sizeof(double);
+                int G = c < 2 ? 8 : 32, spw = 32 / G;
+                size_t per = ((size_t)nm * nm + 2 * nm) * sizeof(double) * spw;   // per warp
                 int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (200 * 1024) / per));
                 size_t sm = per * wpb;
-                if (sm > 48 * 1024)
-                    PR_CUDA(cudaFuncSetAttribute(k_lair_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-                unsigned grid = std::min<unsigned>(blocks_for(hc[c], wpb), 152u * 64u);
-                k_lair_solve<<<grid, 32 * wpb, sm, s>>>(hc[c], list + hstart[c], L.cpts, L.rowptr, L.col, L.val,
-                                                        candptr, cand, npat, zr, zc, zv, keep, dsing, L.rowdir,
-                                                        prm.phi_R, nm, nullptr, nullptr, d_count);
+                unsigned grid = std::min<unsigned>(blocks_for(hc[c], wpb * spw), 152u * 64u);
+                if (G == 8) {
+                    if (sm > 48 * 1024)
+                        PR_CUDA(cudaFuncSetAttribute(k_lair_solve<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+                    k_lair_solve<8><<<grid, 32 * wpb, sm, s>>>(hc[c], list + hstart[c], L.cpts, L.rowptr, L.col, L.val,
+                                                               candptr, cand, npat, zr, zc, zv, keep, dsing, L.rowdir,
+                                                               prm.phi_R, nm, nullptr, nullptr);
+                } else {
+                    if (sm > 48 * 1024)
+                        PR_CUDA(cudaFuncSetAttribute(k_lair_solve<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+                    k_lair_solve<32><<<grid, 32 * wpb, sm, s>>>(hc[c], list + hstart[c], L.cpts, L.rowptr, L.col,
+                                                                L.val, candptr, cand, npat, zr, zc, zv, keep, dsing,
+                                                                L.rowdir, prm.phi_R, nm, nullptr, nullptr);
+                }
                 PR_LAUNCH();
             }
             int nbig = hc[4];
@@ -950,9 +909,9 @@ void build_hierarchy(Hier &h) {
                 long long gtot = 0;
                 d2h(&gtot, goff + nbig, 1, s);
                 double *gbuf = dmalloc<double>(gtot, s);
-                k_lair_solve<<<std::min<unsigned>(nbig, 152u * 16u), 32, 0, s>>>(
+                k_lair_solve<32><<<std::min<unsigned>(nbig, 152u * 16u), 32, 0, s>>>(
                     nbig, list + hstart[4], L.cpts, L.rowptr, L.col, L.val, candptr, cand, npat, zr, zc, zv, keep,
-                    dsing, L.rowdir, prm.phi_R, 0, goff, gbuf, d_count);
+                    dsing, L.rowdir, prm.phi_R, 0, goff, gbuf);
                 PR_LAUNCH();
                 dfree(gbuf, s); dfree(goff, s);
             }
@@ -992,25 +951,40 @@ void build_hierarchy(Hier &h) {
         double *uval = dmalloc<double>(ut, s);
         int *cnt = dmalloc<int>(nc, s);
         {
-            const int hcap = 2048, wpb = 4;
-            size_t sm = (size_t)hcap * wpb * (sizeof(double) + sizeof(int));
-            PR_CUDA(cudaFuncSetAttribute(k_rap<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-            PR_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int), s));
-            unsigned grid = std::min<unsigned>(blocks_for(nc, wpb), 152u * 32u);
-            k_rap<false><<<grid, 32 * wpb, sm, s>>>(nc, nullptr, nc, L.cpts, L.zrowptr, L.zcol, L.zval, L.rowptr, aplen,
-                                             apcol, apval, uptr, U, prm.phi_A, cnt, ucol, uval, hcap, nullptr,
-                                             nullptr, nullptr, d_count, h.d_err);
+            // rows binned by their bound U: tables of 256 / 1024 / 4096 slots in
+            // shared memory, larger rows in global scratch
+            int *bcount = dmalloc<int>(10, s);
+            PR_CUDA(cudaMemsetAsync(bcount, 0, sizeof(int) * 10, s));
+            k_rap_bin_count<<<blocks_for(nc, BS), BS, 0, s>>>(nc, U, bcount);
             PR_LAUNCH();
-            int nover = 0;
-            d2h(&nover, d_count, 1, s);
-            if (nover > 0) {
-                int *flag = dmalloc<int>(nc, s), *pos = dmalloc<int>(nc + 1, s);
-                k_overflow_list<<<blocks_for(nc, BS), BS, 0, s>>>(nc, cnt, flag);
+            int hb[4];
+            d2h(hb, bcount, 4, s);
+            int bstart[4], acc = 0;
+            for (int c = 0; c < 4; ++c) { bstart[c] = acc; acc += hb[c]; }
+            PR_CUDA(cudaMemcpyAsync(bcount, bstart, sizeof(int) * 4, cudaMemcpyHostToDevice, s));
+            PR_CUDA(cudaMemsetAsync(bcount + 4, 0, sizeof(int) * 4, s));
+            int *rlist = dmalloc<int>(nc, s);
+            k_rap_bin_fill<<<blocks_for(nc, BS), BS, 0, s>>>(nc, U, bcount, bcount + 4, rlist);
+            PR_LAUNCH();
+            const int caps[3] = {256, 1024, 4096};
+            PR_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int), s));
+            for (int c = 0; c < 3; ++c) {
+                if (!hb[c]) continue;
+                int hcap = caps[c];
+                int wpb = std::max(1, std::min(16, (200 * 1024) / (hcap * 12)));
+                size_t sm = (size_t)hcap * wpb * (sizeof(double) + sizeof(int));
+                PR_CUDA(cudaFuncSetAttribute(k_rap<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+                unsigned grid = std::min<unsigned>(blocks_for(hb[c], wpb), 152u * 32u);
+                k_rap<false><<<grid, 32 * wpb, sm, s>>>(hb[c], rlist + bstart[c], nc, L.cpts, L.zrowptr, L.zcol, L.zval,
+                                                        L.rowptr, aplen, apcol, apval, uptr, U, prm.phi_A, cnt, ucol,
+                                                        uval, hcap, nullptr, nullptr, nullptr, d_count, h.d_err);
                 PR_LAUNCH();
-                scan_exclusive(flag, pos, nc, s);
-                int *list = dmalloc<int>(nover, s);
+            }
+            int nover = hb[3];
+            if (nover > 0) {
+                int *list = rlist + bstart[3];
                 long long *capw = dmalloc<long long>(nover + 1, s);
-                k_overflow_rows<<<blocks_for(nc, BS), BS, 0, s>>>(nc, flag, pos, U, list, capw);
+                k_overflow_caps<<<blocks_for(nover, BS), BS, 0, s>>>(nover, list, U, capw);
                 PR_LAUNCH();
                 k_prefix_ll<<<1, 1, 0, s>>>(nover, capw);
                 PR_LAUNCH();
@@ -1022,8 +996,12 @@ void build_hierarchy(Hier &h) {
                     nover, list, nc, L.cpts, L.zrowptr, L.zcol, L.zval, L.rowptr, aplen, apcol, apval, uptr, U,
                     prm.phi_A, cnt, ucol, uval, 0, capw, gk, gv, d_count, h.d_err);
                 PR_LAUNCH();
-                dfree(gk, s); dfree(gv, s); dfree(list, s); dfree(capw, s); dfree(flag, s); dfree(pos, s);
+                dfree(gk, s); dfree(gv, s); dfree(capw, s);
             }
+            int nrej = 0;
+            d2h(&nrej, d_count, 1, s);
+            PR_REQUIRE(nrej == 0, PAIR_ERR_DEVICE, "RAP row exceeded its table bin");
+            dfree(rlist, s); dfree(bcount, s);
         }
         Level C;
         C.n = nc;
