@@ -21,20 +21,21 @@ namespace {
 // LU with partial pivoting (first maximum), multipliers a_rk * (1 / a_kk),
 // updates fma(-l, a_kc, a_rc); column-oriented substitutions with fma and
 // y_k * (1 / u_kk).  The same operation sequence as every LU in the library.
-__device__ __forceinline__ void lu_factor8(double *a, int *piv, int *singular) {
+__device__ __forceinline__ void lu_factor8(double *a, int *piv, double *rinv, int *singular) {
     const int n = 8;
     for (int k = 0; k < n; ++k) {
         int p = k;
-        double mx = fabs(a[k * n + k]);
+        long long mx = absbits(a[k * n + k]);
         for (int r = k + 1; r < n; ++r) {
-            double v = fabs(a[r * n + k]);
+            long long v = absbits(a[r * n + k]);
             if (v > mx) { mx = v; p = r; }
         }
         piv[k] = p;
-        if (!(mx > 0.0)) { *singular = 1; return; }
+        if (!(mx > 0)) { *singular = 1; return; }
         if (p != k)
             for (int c = 0; c < n; ++c) { double t = a[k * n + c]; a[k * n + c] = a[p * n + c]; a[p * n + c] = t; }
         double rd = 1.0 / a[k * n + k];
+        rinv[k] = rd;   // row k is final from here on: the back substitution reuses it
         for (int r = k + 1; r < n; ++r) {
             double l = a[r * n + k] * rd;
             a[r * n + k] = l;
@@ -43,14 +44,14 @@ __device__ __forceinline__ void lu_factor8(double *a, int *piv, int *singular) {
     }
 }
 
-__device__ __forceinline__ void lu_solve8(const double *a, const int *piv, double *y) {
+__device__ __forceinline__ void lu_solve8(const double *a, const int *piv, const double *rinv, double *y) {
     const int n = 8;
     for (int k = 0; k < n; ++k)
         if (piv[k] != k) { double t = y[k]; y[k] = y[piv[k]]; y[piv[k]] = t; }
     for (int k = 0; k < n; ++k)
         for (int r = k + 1; r < n; ++r) y[r] = fma(-a[r * n + k], y[k], y[r]);
     for (int k = n - 1; k >= 0; --k) {
-        y[k] = y[k] * (1.0 / a[k * n + k]);
+        y[k] = y[k] * rinv[k];
         for (int r = 0; r < k; ++r) y[r] = fma(-a[r * n + k], y[k], y[r]);
     }
 }
@@ -118,8 +119,9 @@ __global__ void __launch_bounds__(128) k_hex_assemble(int n, int ndir, const dou
         }
     }
     int piv[8];
+    double rinv[8];
     int sing = 0;
-    lu_factor8(D, piv, &sing);
+    lu_factor8(D, piv, rinv, &sing);
     if (sing) { atomicOr(err, 1); return; }
 
     int idx[3] = {e % n, (e / n) % n, e / (n * n)};
@@ -154,7 +156,7 @@ __global__ void __launch_bounds__(128) k_hex_assemble(int n, int ndir, const dou
             if (((b >> d) & 1) != out[d]) continue;
             double *y = Y[d][t];
             for (int a = 0; a < 8; ++a) y[a] = (((a >> d) & 1) != in[d]) ? 0.0 : -(w * face_f(m1, d, a, b));
-            lu_solve8(D, piv, y);
+            lu_solve8(D, piv, rinv, y);
             ++t;
         }
     }
@@ -208,7 +210,7 @@ __global__ void __launch_bounds__(128) k_hex_assemble(int n, int ndir, const dou
             }
             y[a] = acc;
         }
-        lu_solve8(D, piv, y);
+        lu_solve8(D, piv, rinv, y);
         for (int a = 0; a < 8; ++a) Gin[((long long)m * E + e) * 8 + a] = y[a];
     }
     if (W) {
@@ -220,7 +222,7 @@ __global__ void __launch_bounds__(128) k_hex_assemble(int n, int ndir, const dou
                 int ax = a & 1, ay = (a >> 1) & 1, az = (a >> 2) & 1;
                 y[a] = (m1[ax][bx] * m1[ay][by]) * m1[az][bz];
             }
-            lu_solve8(D, piv, y);
+            lu_solve8(D, piv, rinv, y);
             for (int a = 0; a < 8; ++a) We[a * 8 + b] = y[a];
         }
     }

@@ -54,6 +54,13 @@ inline void dfree(void *p, cudaStream_t s) {
 
 inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
+#ifdef __CUDACC__
+// |x| as an ordered integer key: for non-NaN doubles the bit patterns of |x|
+// order exactly as the values, so pivot searches and maxima of magnitudes run
+// on the integer pipe instead of the (narrow) FP64 pipe.
+__device__ __forceinline__ long long absbits(double x) { return __double_as_longlong(x) & 0x7fffffffffffffffLL; }
+#endif
+
 // Exclusive scan of int counts (n entries) into out (n+1 entries, out[n] = total);
 // returns the total (synchronises the stream).
 long long scan_exclusive(const int *in, int *out, int n, cudaStream_t s, bool want_total = true);

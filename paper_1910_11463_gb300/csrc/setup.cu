@@ -244,8 +244,11 @@ __global__ void k_lair_pattern(int nc, const int *cpts, const int *rowptr, const
     npat[ic] = m;
 }
 
-// size class of each lAIR system: 0: n <= 8, 1: <= 16, 2: <= 32, 3: <= 64, 4: larger
-__device__ __forceinline__ int lair_class(int np) { return np <= 8 ? 0 : np <= 16 ? 1 : np <= 32 ? 2 : np <= 64 ? 3 : 4; }
+// size class of each lAIR system: 0: n <= 8, 1: <= 12, 2: <= 16, 3: <= 32, 4: <= 64, 5: larger
+constexpr int LAIR_CLASSES = 6;
+__device__ __forceinline__ int lair_class(int np) {
+    return np <= 8 ? 0 : np <= 12 ? 1 : np <= 16 ? 2 : np <= 32 ? 3 : np <= 64 ? 4 : 5;
+}
 
 __global__ void k_lair_class_count(int nc, const int *npat, int *cnt) {
     int ic = blockIdx.x * blockDim.x + threadIdx.x;
@@ -277,6 +280,120 @@ __device__ __forceinline__ int pat_find(const int *pat, int np, int k) {
     return -1;
 }
 
+// Thread per C row of the worklist for systems of size <= NM: every lane of a
+// warp works on its own system, so each FP64 instruction carries 32 useful
+// operations.  Workspaces live in shared memory interleaved by thread
+// (element e of thread t at [e * T + t]), which keeps accesses conflict-free.
+template <int NM>
+__global__ void __launch_bounds__(64) k_lair_solve_thread(int nwork, const int *worklist, const int *cpts,
+                                                          const int *rowptr, const int *col, const double *val,
+                                                          const int *candptr, const int *cand, const int *npat,
+                                                          const int *zrowptr, int *zcol, double *zval, int *keep,
+                                                          int *nsing_dir, const int *rowdir, double phi_R) {
+    constexpr int T = 64;
+    extern __shared__ double sm3[];
+    const int t = threadIdx.x;
+    double *Ms = sm3;                   // NM*NM
+    double *ys = sm3 + NM * NM * T;     // NM
+    double *rs = ys + NM * T;           // NM
+    int *ps = (int *)(rs + NM * T);     // NM pattern, NM pivots
+#define MM(e) Ms[(e) * T + t]
+#define YY(e) ys[(e) * T + t]
+#define RR(e) rs[(e) * T + t]
+#define PAT(e) ps[(e) * T + t]
+#define PIV(e) ps[(NM + (e)) * T + t]
+    int w = blockIdx.x * T + t;
+    if (w >= nwork) return;
+    int ic = worklist[w];
+    int i = cpts[ic];
+    int np = npat[ic];
+    if (np > NM) { keep[ic] = 0; return; }   // excluded by the size bins
+    const int *cp = cand + candptr[ic];
+    for (int e = 0; e < np; ++e) { PAT(e) = cp[e]; YY(e) = -0.0; }
+    for (int e = 0; e < np * np; ++e) MM(e) = 0.0;
+    for (int c = 0; c < np; ++c) {
+        int j = PAT(c);
+        for (int p = rowptr[j]; p < rowptr[j + 1]; ++p) {
+            int k = col[p], lo = 0, hi = np - 1, r = -1;
+            while (lo <= hi) {
+                int m = (lo + hi) >> 1;
+                int v = PAT(m);
+                if (v == k) { r = m; break; }
+                if (v < k) lo = m + 1; else hi = m - 1;
+            }
+            if (r >= 0) MM(r * np + c) = val[p];
+        }
+    }
+    for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+        int k = col[p], lo = 0, hi = np - 1, r = -1;
+        while (lo <= hi) {
+            int m = (lo + hi) >> 1;
+            int v = PAT(m);
+            if (v == k) { r = m; break; }
+            if (v < k) lo = m + 1; else hi = m - 1;
+        }
+        if (r >= 0) YY(r) = -val[p];
+    }
+    long long mxb = 0;
+    for (int e = 0; e < np * np; ++e) mxb = max(mxb, absbits(MM(e)));
+    long long tinyb = absbits(1e-14 * __longlong_as_double(mxb));
+    bool singular = false;
+    for (int k = 0; k < np; ++k) {
+        int p = k;
+        long long pv = absbits(MM(k * np + k));
+        for (int r = k + 1; r < np; ++r) {
+            long long v = absbits(MM(r * np + k));
+            if (v > pv) { pv = v; p = r; }
+        }
+        PIV(k) = p;
+        if (!(pv > tinyb)) { singular = true; break; }
+        if (p != k)
+            for (int c = 0; c < np; ++c) { double tt = MM(k * np + c); MM(k * np + c) = MM(p * np + c); MM(p * np + c) = tt; }
+        double rd = 1.0 / MM(k * np + k);
+        RR(k) = rd;
+        for (int r = k + 1; r < np; ++r) {
+            double l = MM(r * np + k) * rd;
+            MM(r * np + k) = l;
+            for (int c = k + 1; c < np; ++c) MM(r * np + c) = fma(-l, MM(k * np + c), MM(r * np + c));
+        }
+    }
+    int kept = 0;
+    if (singular) {
+        atomicAdd(&nsing_dir[rowdir[i]], 1);
+    } else if (np > 0) {
+        for (int k = 0; k < np; ++k) {
+            int p = PIV(k);
+            if (p != k) { double tt = YY(k); YY(k) = YY(p); YY(p) = tt; }
+        }
+        for (int k = 0; k < np; ++k) {
+            double yk = YY(k);
+            for (int r = k + 1; r < np; ++r) YY(r) = fma(-MM(r * np + k), yk, YY(r));
+        }
+        for (int k = np - 1; k >= 0; --k) {
+            double yk = YY(k) * RR(k);
+            YY(k) = yk;
+            for (int r = 0; r < k; ++r) YY(r) = fma(-MM(r * np + k), yk, YY(r));
+        }
+        long long zmb = 0;
+        for (int e = 0; e < np; ++e) zmb = max(zmb, absbits(YY(e)));
+        double thr = phi_R * __longlong_as_double(zmb);
+        int base = zrowptr[ic];
+        for (int e = 0; e < np; ++e) {
+            double z = YY(e);
+            if (phi_R > 0.0 && fabs(z) < thr) continue;
+            zcol[base + kept] = PAT(e);
+            zval[base + kept] = z;
+            ++kept;
+        }
+    }
+    keep[ic] = kept;
+#undef MM
+#undef YY
+#undef RR
+#undef PAT
+#undef PIV
+}
+
 // G lanes per C row of the worklist (32/G systems per warp).  Shared-memory
 // mode (gbuf == null): systems of size <= nmax, workspace nmax^2 + 2 nmax
 // doubles per group.  Global mode: workspace at gbuf + goff[w].
@@ -298,9 +415,10 @@ __global__ void k_lair_solve(int nwork, const int *worklist, const int *cpts, co
         int i = has ? cpts[ic] : 0;
         int np = has ? npat[ic] : 0;
         double *M = gbuf ? gbuf + (has ? goff[w] : 0)
-                         : smem + ((size_t)warp * SPW + q) * ((size_t)nmax * nmax + 2 * nmax);
+                         : smem + ((size_t)warp * SPW + q) * ((size_t)nmax * nmax + 3 * nmax);
         double *y = M + (size_t)np * np;
-        int *pat = (int *)(y + np);
+        double *rv = y + np;                  // pivot reciprocals
+        int *pat = (int *)(rv + np);
         int *piv = pat + np;
         if (has) {
             const int *cp = cand + candptr[ic];
@@ -323,28 +441,28 @@ __global__ void k_lair_solve(int nwork, const int *worklist, const int *cpts, co
             }
         }
         __syncwarp();
-        double mx = 0.0;
-        for (int idx = g; idx < np * np; idx += G) mx = fmax(mx, fabs(M[idx]));
-        for (int o = G / 2; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(FULL, mx, o, G));
-        double tiny = 1e-14 * mx;
+        long long mxb = 0;
+        for (int idx = g; idx < np * np; idx += G) mxb = max(mxb, absbits(M[idx]));
+        for (int o = G / 2; o > 0; o >>= 1) mxb = max(mxb, __shfl_xor_sync(FULL, mxb, o, G));
+        long long tinyb = absbits(1e-14 * __longlong_as_double(mxb));
         int kmax = np;
         for (int o = 16; o > 0; o >>= 1) kmax = max(kmax, __shfl_xor_sync(FULL, kmax, o));
         bool singular = false;
         for (int k = 0; k < kmax; ++k) {
             bool act = k < np && !singular;
-            double bv = -1.0;
+            long long bv = -1;
             int br = k;
             if (act)
                 for (int r = k + g; r < np; r += G) {
-                    double v = fabs(M[r * np + k]);
+                    long long v = absbits(M[r * np + k]);
                     if (v > bv) { bv = v; br = r; }
                 }
             for (int o = G / 2; o > 0; o >>= 1) {
-                double ov = __shfl_xor_sync(FULL, bv, o, G);
+                long long ov = __shfl_xor_sync(FULL, bv, o, G);
                 int orr = __shfl_xor_sync(FULL, br, o, G);
                 if (ov > bv || (ov == bv && orr < br)) { bv = ov; br = orr; }
             }
-            if (act && !(bv > tiny)) { singular = true; act = false; }
+            if (act && !(bv > tinyb)) { singular = true; act = false; }
             if (act) {
                 if (g == 0) piv[k] = br;
                 if (br != k)
@@ -357,6 +475,7 @@ __global__ void k_lair_solve(int nwork, const int *worklist, const int *cpts, co
             __syncwarp();
             if (act) {
                 double rd = 1.0 / M[k * np + k];
+                if (g == 0) rv[k] = rd;
                 for (int r = k + 1 + g; r < np; r += G) M[r * np + k] = M[r * np + k] * rd;
             }
             __syncwarp();
@@ -382,7 +501,7 @@ __global__ void k_lair_solve(int nwork, const int *worklist, const int *cpts, co
             __syncwarp();
         }
         for (int k = kmax - 1; k >= 0; --k) {
-            if (solve && k < np && g == 0) y[k] = y[k] * (1.0 / M[k * np + k]);
+            if (solve && k < np && g == 0) y[k] = y[k] * rv[k];
             __syncwarp();
             if (solve && k < np) {
                 double yk = y[k];
@@ -390,11 +509,11 @@ __global__ void k_lair_solve(int nwork, const int *worklist, const int *cpts, co
             }
             __syncwarp();
         }
-        double zm = 0.0;
+        long long zmb = 0;
         if (solve)
-            for (int t = g; t < np; t += G) zm = fmax(zm, fabs(y[t]));
-        for (int o = G / 2; o > 0; o >>= 1) zm = fmax(zm, __shfl_xor_sync(FULL, zm, o, G));
-        double thr = phi_R * zm;
+            for (int t = g; t < np; t += G) zmb = max(zmb, absbits(y[t]));
+        for (int o = G / 2; o > 0; o >>= 1) zmb = max(zmb, __shfl_xor_sync(FULL, zmb, o, G));
+        double thr = phi_R * __longlong_as_double(zmb);
         int kept = 0;
         int base = has ? zrowptr[ic] : 0;
         int tmax = np;
@@ -667,7 +786,7 @@ __global__ void k_big_rows(int nbig, const int *list, const int *npat, long long
     int w = blockIdx.x * blockDim.x + threadIdx.x;
     if (w >= nbig) return;
     long long np = npat[list[w]];
-    goff[w] = np * np + 2 * np;
+    goff[w] = np * np + 3 * np;
 }
 
 __global__ void k_prefix_ll(int n, long long *v) {
@@ -861,48 +980,52 @@ void build_hierarchy(Hier &h) {
         PR_CUDA(cudaMemsetAsync(dsing, 0, sizeof(int) * ND, s));
         {
             // rows binned by system size; shared memory per warp sized to the bin
-            int *ccount = dmalloc<int>(10, s);
-            PR_CUDA(cudaMemsetAsync(ccount, 0, sizeof(int) * 10, s));
+            int *ccount = dmalloc<int>(2 * LAIR_CLASSES, s);
+            PR_CUDA(cudaMemsetAsync(ccount, 0, sizeof(int) * 2 * LAIR_CLASSES, s));
             k_lair_class_count<<<blocks_for(nc, BS), BS, 0, s>>>(nc, npat, ccount);
             PR_LAUNCH();
-            int hc[5];
-            d2h(hc, ccount, 5, s);
-            int hstart[5], acc = 0;
-            for (int c = 0; c < 5; ++c) { hstart[c] = acc; acc += hc[c]; }
-            PR_CUDA(cudaMemcpyAsync(ccount, hstart, sizeof(int) * 5, cudaMemcpyHostToDevice, s));
-            PR_CUDA(cudaMemsetAsync(ccount + 5, 0, sizeof(int) * 5, s));
+            int hc[LAIR_CLASSES];
+            d2h(hc, ccount, LAIR_CLASSES, s);
+            int hstart[LAIR_CLASSES], acc = 0;
+            for (int c = 0; c < LAIR_CLASSES; ++c) { hstart[c] = acc; acc += hc[c]; }
+            PR_CUDA(cudaMemcpyAsync(ccount, hstart, sizeof(int) * LAIR_CLASSES, cudaMemcpyHostToDevice, s));
+            PR_CUDA(cudaMemsetAsync(ccount + LAIR_CLASSES, 0, sizeof(int) * LAIR_CLASSES, s));
             int *list = dmalloc<int>(nc, s);
-            k_lair_class_fill<<<blocks_for(nc, BS), BS, 0, s>>>(nc, npat, ccount, ccount + 5, list);
+            k_lair_class_fill<<<blocks_for(nc, BS), BS, 0, s>>>(nc, npat, ccount, ccount + LAIR_CLASSES, list);
             PR_LAUNCH();
-            // n <= 16: 8 lanes per system; larger: a warp per system
-            const int cls_n[4] = {8, 16, 32, 64};
-            for (int c = 0; c < 4; ++c) {
+            // n <= 16: a thread per system; larger: a warp per system
+            auto thread_bin = [&](int c, auto kern, int nm) {
+                if (!hc[c]) return;
+                size_t sm = (size_t)64 * (nm * nm + 3 * nm) * sizeof(double);
+                if (sm > 48 * 1024)
+                    PR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+                kern<<<blocks_for(hc[c], 64), 64, sm, s>>>(hc[c], list + hstart[c], L.cpts, L.rowptr, L.col, L.val,
+                                                           candptr, cand, npat, zr, zc, zv, keep, dsing, L.rowdir,
+                                                           prm.phi_R);
+                PR_LAUNCH();
+            };
+            thread_bin(0, k_lair_solve_thread<8>, 8);
+            thread_bin(1, k_lair_solve_thread<12>, 12);
+            thread_bin(2, k_lair_solve_thread<16>, 16);
+            const int cls_n[LAIR_CLASSES] = {8, 12, 16, 32, 64, 0};
+            for (int c = 3; c < 5; ++c) {
                 if (!hc[c]) continue;
                 int nm = cls_n[c];
-                int G = c < 2 ? 8 : 32, spw = 32 / G;
-                size_t per = ((size_t)nm * nm + 2 * nm) * sizeof(double) * spw;   // per warp
+                size_t per = ((size_t)nm * nm + 3 * nm) * sizeof(double);   // per warp
                 int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (200 * 1024) / per));
                 size_t sm = per * wpb;
-                unsigned grid = std::min<unsigned>(blocks_for(hc[c], wpb * spw), 152u * 64u);
-                if (G == 8) {
-                    if (sm > 48 * 1024)
-                        PR_CUDA(cudaFuncSetAttribute(k_lair_solve<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-                    k_lair_solve<8><<<grid, 32 * wpb, sm, s>>>(hc[c], list + hstart[c], L.cpts, L.rowptr, L.col, L.val,
-                                                               candptr, cand, npat, zr, zc, zv, keep, dsing, L.rowdir,
-                                                               prm.phi_R, nm, nullptr, nullptr);
-                } else {
-                    if (sm > 48 * 1024)
-                        PR_CUDA(cudaFuncSetAttribute(k_lair_solve<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-                    k_lair_solve<32><<<grid, 32 * wpb, sm, s>>>(hc[c], list + hstart[c], L.cpts, L.rowptr, L.col,
-                                                                L.val, candptr, cand, npat, zr, zc, zv, keep, dsing,
-                                                                L.rowdir, prm.phi_R, nm, nullptr, nullptr);
-                }
+                unsigned grid = std::min<unsigned>(blocks_for(hc[c], wpb), 152u * 64u);
+                if (sm > 48 * 1024)
+                    PR_CUDA(cudaFuncSetAttribute(k_lair_solve<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+                k_lair_solve<32><<<grid, 32 * wpb, sm, s>>>(hc[c], list + hstart[c], L.cpts, L.rowptr, L.col, L.val,
+                                                            candptr, cand, npat, zr, zc, zv, keep, dsing, L.rowdir,
+                                                            prm.phi_R, nm, nullptr, nullptr);
                 PR_LAUNCH();
             }
-            int nbig = hc[4];
+            int nbig = hc[5];
             if (nbig > 0) {
                 long long *goff = dmalloc<long long>(nbig + 1, s);
-                k_big_rows<<<blocks_for(nbig, BS), BS, 0, s>>>(nbig, list + hstart[4], npat, goff);
+                k_big_rows<<<blocks_for(nbig, BS), BS, 0, s>>>(nbig, list + hstart[5], npat, goff);
                 PR_LAUNCH();
                 k_prefix_ll<<<1, 1, 0, s>>>(nbig, goff);
                 PR_LAUNCH();
@@ -910,7 +1033,7 @@ void build_hierarchy(Hier &h) {
                 d2h(&gtot, goff + nbig, 1, s);
                 double *gbuf = dmalloc<double>(gtot, s);
                 k_lair_solve<32><<<std::min<unsigned>(nbig, 152u * 16u), 32, 0, s>>>(
-                    nbig, list + hstart[4], L.cpts, L.rowptr, L.col, L.val, candptr, cand, npat, zr, zc, zv, keep,
+                    nbig, list + hstart[5], L.cpts, L.rowptr, L.col, L.val, candptr, cand, npat, zr, zc, zv, keep,
                     dsing, L.rowdir, prm.phi_R, 0, goff, gbuf);
                 PR_LAUNCH();
                 dfree(gbuf, s); dfree(goff, s);
