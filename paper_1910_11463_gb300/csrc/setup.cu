@@ -250,17 +250,7 @@ __device__ __forceinline__ int lair_class(int np) {
     return np <= 8 ? 0 : np <= 12 ? 1 : np <= 16 ? 2 : np <= 32 ? 3 : np <= 64 ? 4 : 5;
 }
 
-__global__ void k_lair_class_count(int nc, const int *npat, int *cnt) {
-    int ic = blockIdx.x * blockDim.x + threadIdx.x;
-    if (ic < nc) atomicAdd(&cnt[lair_class(npat[ic])], 1);
-}
 
-__global__ void k_lair_class_fill(int nc, const int *npat, const int *start, int *fill, int *list) {
-    int ic = blockIdx.x * blockDim.x + threadIdx.x;
-    if (ic >= nc) return;
-    int c = lair_class(npat[ic]);
-    list[start[c] + atomicAdd(&fill[c], 1)] = ic;
-}
 
 __global__ void k_max_int(const int *v, int n, int *out) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -611,84 +601,102 @@ __global__ void k_rap_bound(int nc, const int *cpts, const int *zrowptr, const i
 
 __device__ __forceinline__ unsigned hslot(int c, unsigned mask) { return ((unsigned)c * 2654435761u) & mask; }
 
-// Warp per coarse row.  Table: keys (int, -1 empty) and values, in shared
-// memory (cap = hcap) or in global scratch (cap per row given by gcap/gptr).
-// Output: sorted, filtered entries at ucol/uval[uptr[ic]...], count in cnt[ic].
-template <bool GLOBAL_TABLE>
-__global__ void k_rap(int nrows_work, const int *worklist, int nc, const int *cpts, const int *zrowptr,
-                      const int *zcol, const double *zval, const int *aprow, const int *aplen, const int *apcol,
-                      const double *apval, const int *uptr, const int *U, double phiA, int *cnt, int *ucol,
-                      double *uval, int hcap, const long long *gptr, int *gkeys, double *gvals, int *overflow, int *err) {
+// G lanes per coarse row (32/G rows per warp).  Table: keys (int, -1 empty)
+// and values, in shared memory (hcap slots per row, sized to the row's bin) or
+// in global scratch (cap per row given by gptr).  Output: sorted, filtered
+// entries at ucol/uval[uptr[ic]...], count in cnt[ic].  Magnitude maxima use
+// integer keys; the phi_A filter costs nothing when it is off (filt == 0).
+template <int G, bool GLOBAL_TABLE>
+__global__ void k_rap(int nrows_work, const int *worklist, const int *cpts, const int *zrowptr, const int *zcol,
+                      const double *zval, const int *aprow, const int *aplen, const int *apcol, const double *apval,
+                      const int *uptr, const int *U, int filt, double phiA, int *cnt, int *ucol, double *uval, int hcap,
+                      const long long *gptr, int *gkeys, double *gvals, int *overflow, int *err) {
     extern __shared__ double smem2[];
+    const unsigned FULL = 0xffffffffu;
+    constexpr int SPW = 32 / G;
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int g = lane % G, q = lane / G;
     int wpb = blockDim.x >> 5;
-    for (int w = blockIdx.x * wpb + warp; w < nrows_work; w += gridDim.x * wpb) {
-        int ic = worklist ? worklist[w] : w;
-        int *keys;
-        double *vals;
-        int cap;
-        if (GLOBAL_TABLE) {
-            long long off = gptr[w];
-            cap = (int)(gptr[w + 1] - off);
-            keys = gkeys + off;
-            vals = gvals + off;
-        } else {
-            vals = smem2 + (size_t)warp * hcap;
-            keys = (int *)(smem2 + (size_t)wpb * hcap) + (size_t)warp * hcap;
-            if (2 * U[ic] > hcap) {
-                if (lane == 0) { cnt[ic] = -1; atomicAdd(overflow, 1); }
-                continue;
+    unsigned gmask = (G == 32) ? FULL : (((1u << (G & 31)) - 1u) << (q * G));
+    for (int wb = (blockIdx.x * wpb + warp) * SPW; wb < nrows_work; wb += gridDim.x * wpb * SPW) {
+        int w = wb + q;
+        bool has = w < nrows_work;
+        int ic = has ? worklist[w] : 0;
+        int *keys = nullptr;
+        double *vals = nullptr;
+        int cap = 0;
+        if (has) {
+            if (GLOBAL_TABLE) {
+                long long off = gptr[w];
+                cap = (int)(gptr[w + 1] - off);
+                keys = gkeys + off;
+                vals = gvals + off;
+            } else {
+                int slot = warp * SPW + q;
+                vals = smem2 + (size_t)slot * hcap;
+                keys = (int *)(smem2 + (size_t)wpb * SPW * hcap) + (size_t)slot * hcap;
+                if (2 * U[ic] > hcap) {
+                    if (g == 0) { cnt[ic] = -1; atomicAdd(overflow, 1); }
+                    has = false;
+                } else {
+                    cap = 64;
+                    while (cap < 2 * U[ic]) cap <<= 1;
+                }
             }
-            cap = 64;
-            while (cap < 2 * U[ic]) cap <<= 1;   // table sized to this row's bound
         }
         unsigned mask = (unsigned)cap - 1u;
-        for (int t = lane; t < cap; t += 32) keys[t] = -1;
+        for (int t = g; t < cap; t += G) keys[t] = -1;
         __syncwarp();
-        int i = cpts[ic];
-        int z0 = zrowptr[ic], z1 = zrowptr[ic + 1];
+        int i = has ? cpts[ic] : 0;
+        int z0 = has ? zrowptr[ic] : 0, z1 = has ? zrowptr[ic + 1] : 0;
+        int nr = has ? z1 - z0 + 1 : 0;   // R row entries, identity included
+        int nrmax = nr;
+        for (int o = 16; o > 0; o >>= 1) nrmax = max(nrmax, __shfl_xor_sync(FULL, nrmax, o));
         bool placed = false;
         int t = z0;
-        while (true) {
-            int k;
-            double r;
-            if (!placed && (t == z1 || zcol[t] > i)) { k = i; r = 1.0; placed = true; }
-            else if (t < z1) { k = zcol[t]; r = zval[t]; ++t; }
-            else break;
-            int a0 = aprow[k], al = aplen[k];
-            for (int q = lane; q < al; q += 32) {
-                int c = apcol[a0 + q];
-                double v = apval[a0 + q];
-                unsigned hs = hslot(c, mask);
-                int probes = 0;
-                bool ok = false;
-                while (probes++ < cap) {
-                    int prev = atomicCAS(&keys[hs], -1, c);
-                    if (prev == -1) { vals[hs] = 0.0; ok = true; break; }
-                    if (prev == c) { ok = true; break; }
-                    hs = (hs + 1) & mask;
+        for (int step = 0; step < nrmax; ++step) {
+            if (step < nr) {
+                int k;
+                double r;
+                if (!placed && (t == z1 || zcol[t] > i)) { k = i; r = 1.0; placed = true; }
+                else { k = zcol[t]; r = zval[t]; ++t; }
+                int a0 = aprow[k], al = aplen[k];
+                for (int qq = g; qq < al; qq += G) {
+                    int c = apcol[a0 + qq];
+                    double v = apval[a0 + qq];
+                    unsigned hs = hslot(c, mask);
+                    int probes = 0;
+                    bool ok = false;
+                    while (probes++ < cap) {
+                        int prev = atomicCAS(&keys[hs], -1, c);
+                        if (prev == -1) { vals[hs] = 0.0; ok = true; break; }
+                        if (prev == c) { ok = true; break; }
+                        hs = (hs + 1) & mask;
+                    }
+                    if (ok) vals[hs] = fma(r, v, vals[hs]);
+                    else atomicOr(err, DERR_HASH_OVERFLOW);
                 }
-                if (ok) vals[hs] = fma(r, v, vals[hs]);
-                else atomicOr(err, DERR_HASH_OVERFLOW);
             }
             __syncwarp();
         }
         // compact to the scratch output (unsorted), then rank-sort back into the table
-        int base = uptr[ic];
+        int base = has ? uptr[ic] : 0;
         int m = 0;
-        for (int s0 = 0; s0 < cap; s0 += 32) {
-            int s = s0 + lane;
-            bool occ = s < cap && keys[s] >= 0;
-            unsigned msk = __ballot_sync(0xffffffffu, occ);
+        int capmax = cap;
+        for (int o = 16; o > 0; o >>= 1) capmax = max(capmax, __shfl_xor_sync(FULL, capmax, o));
+        for (int s0 = 0; s0 < capmax; s0 += G) {
+            int sl = s0 + g;
+            bool occ = sl < cap && keys[sl] >= 0;
+            unsigned msk = __ballot_sync(FULL, occ) & gmask;
             if (occ) {
                 int off = m + __popc(msk & ((1u << lane) - 1u));
-                ucol[base + off] = keys[s];
-                uval[base + off] = vals[s];
+                ucol[base + off] = keys[sl];
+                uval[base + off] = vals[sl];
             }
             m += __popc(msk);
         }
         __syncwarp();
-        for (int e = lane; e < m; e += 32) {
+        for (int e = g; e < m; e += G) {
             int ce = ucol[base + e];
             int rank = 0;
             for (int f = 0; f < m; ++f) rank += ucol[base + f] < ce;
@@ -696,16 +704,21 @@ __global__ void k_rap(int nrows_work, const int *worklist, int nc, const int *cp
             vals[rank] = uval[base + e];
         }
         __syncwarp();
-        double mx = 0.0;
-        for (int e = lane; e < m; e += 32)
-            if (keys[e] != ic) mx = fmax(mx, fabs(vals[e]));
-        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        double thr = phiA * mx;
+        int mmax = m;
+        for (int o = 16; o > 0; o >>= 1) mmax = max(mmax, __shfl_xor_sync(FULL, mmax, o));
+        double thr = 0.0;
+        if (filt) {
+            long long mxb = 0;
+            for (int e = g; e < m; e += G)
+                if (keys[e] != ic) mxb = max(mxb, absbits(vals[e]));
+            for (int o = G / 2; o > 0; o >>= 1) mxb = max(mxb, __shfl_xor_sync(FULL, mxb, o, G));
+            thr = phiA * __longlong_as_double(mxb);
+        }
         int kept = 0;
-        for (int e0 = 0; e0 < m; e0 += 32) {
-            int e = e0 + lane;
-            bool k_ = e < m && !(phiA > 0.0 && keys[e] != ic && fabs(vals[e]) < thr);
-            unsigned msk = __ballot_sync(0xffffffffu, k_);
+        for (int e0 = 0; e0 < mmax; e0 += G) {
+            int e = e0 + g;
+            bool k_ = e < m && !(filt && keys[e] != ic && fabs(vals[e]) < thr);
+            unsigned msk = __ballot_sync(FULL, k_) & gmask;
             if (k_) {
                 int off = kept + __popc(msk & ((1u << lane) - 1u));
                 ucol[base + off] = keys[e];
@@ -713,7 +726,7 @@ __global__ void k_rap(int nrows_work, const int *worklist, int nc, const int *cp
             }
             kept += __popc(msk);
         }
-        if (lane == 0) cnt[ic] = kept;
+        if (has && g == 0) cnt[ic] = kept;
         __syncwarp();
     }
 }
@@ -747,17 +760,7 @@ __global__ void k_fill_int(int n, int *a, int v) {
 
 __device__ __forceinline__ int rap_bin(int u) { return 2 * u <= 256 ? 0 : 2 * u <= 1024 ? 1 : 2 * u <= 4096 ? 2 : 3; }
 
-__global__ void k_rap_bin_count(int nc, const int *U, int *cnt) {
-    int ic = blockIdx.x * blockDim.x + threadIdx.x;
-    if (ic < nc) atomicAdd(&cnt[rap_bin(U[ic])], 1);
-}
 
-__global__ void k_rap_bin_fill(int nc, const int *U, const int *start, int *fill, int *list) {
-    int ic = blockIdx.x * blockDim.x + threadIdx.x;
-    if (ic >= nc) return;
-    int c = rap_bin(U[ic]);
-    list[start[c] + atomicAdd(&fill[c], 1)] = ic;
-}
 
 __global__ void k_overflow_caps(int nover, const int *list, const int *U, long long *capw) {
     int w = blockIdx.x * blockDim.x + threadIdx.x;
@@ -797,10 +800,51 @@ __global__ void k_prefix_ll(int n, long long *v) {
     v[n] = s;
 }
 
+__global__ void k_flag_eq(int n, const int8_t *cls, int c, int *flag) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) flag[i] = cls[i] == c ? 1 : 0;
+}
+
+__global__ void k_scatter_eq(int n, const int8_t *cls, int c, const int *pos, int start, int *list) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && cls[i] == c) list[start + pos[i]] = i;
+}
+
+__global__ void k_lair_classes(int nc, const int *npat, int8_t *cls) {
+    int ic = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ic < nc) cls[ic] = (int8_t)lair_class(npat[ic]);
+}
+
+__global__ void k_rap_classes(int nc, const int *U, int8_t *cls) {
+    int ic = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ic < nc) cls[ic] = (int8_t)rap_bin(U[ic]);
+}
+
 template <class T>
 void d2h(T *h, const T *d, size_t count, cudaStream_t s) {
     PR_CUDA(cudaMemcpyAsync(h, d, count * sizeof(T), cudaMemcpyDeviceToHost, s));
     PR_CUDA(cudaStreamSynchronize(s));
+}
+
+// Rows 0..n-1 grouped by class (ascending row order inside each class):
+// list[start[c] .. start[c] + count[c]).  Deterministic.
+void partition_by_class(const int8_t *cls, int n, int nclass, int *list, int *start, int *count, cudaStream_t s) {
+    const int BS = 256;
+    int *flag = dmalloc<int>(n, s), *pos = dmalloc<int>(n + 1, s);
+    int acc = 0;
+    for (int c = 0; c < nclass; ++c) {
+        k_flag_eq<<<blocks_for(n, BS), BS, 0, s>>>(n, cls, c, flag);
+        PR_LAUNCH();
+        count[c] = (int)scan_exclusive(flag, pos, n, s);
+        start[c] = acc;
+        if (count[c]) {
+            k_scatter_eq<<<blocks_for(n, BS), BS, 0, s>>>(n, cls, c, pos, acc, list);
+            PR_LAUNCH();
+        }
+        acc += count[c];
+    }
+    dfree(flag, s);
+    dfree(pos, s);
 }
 
 }  // namespace
@@ -980,19 +1024,13 @@ void build_hierarchy(Hier &h) {
         PR_CUDA(cudaMemsetAsync(dsing, 0, sizeof(int) * ND, s));
         {
             // rows binned by system size; shared memory per warp sized to the bin
-            int *ccount = dmalloc<int>(2 * LAIR_CLASSES, s);
-            PR_CUDA(cudaMemsetAsync(ccount, 0, sizeof(int) * 2 * LAIR_CLASSES, s));
-            k_lair_class_count<<<blocks_for(nc, BS), BS, 0, s>>>(nc, npat, ccount);
+            int8_t *ccls = dmalloc<int8_t>(nc, s);
+            k_lair_classes<<<blocks_for(nc, BS), BS, 0, s>>>(nc, npat, ccls);
             PR_LAUNCH();
-            int hc[LAIR_CLASSES];
-            d2h(hc, ccount, LAIR_CLASSES, s);
-            int hstart[LAIR_CLASSES], acc = 0;
-            for (int c = 0; c < LAIR_CLASSES; ++c) { hstart[c] = acc; acc += hc[c]; }
-            PR_CUDA(cudaMemcpyAsync(ccount, hstart, sizeof(int) * LAIR_CLASSES, cudaMemcpyHostToDevice, s));
-            PR_CUDA(cudaMemsetAsync(ccount + LAIR_CLASSES, 0, sizeof(int) * LAIR_CLASSES, s));
+            int hc[LAIR_CLASSES], hstart[LAIR_CLASSES];
             int *list = dmalloc<int>(nc, s);
-            k_lair_class_fill<<<blocks_for(nc, BS), BS, 0, s>>>(nc, npat, ccount, ccount + LAIR_CLASSES, list);
-            PR_LAUNCH();
+            partition_by_class(ccls, nc, LAIR_CLASSES, list, hstart, hc, s);
+            dfree(ccls, s);
             // n <= 16: a thread per system; larger: a warp per system
             auto thread_bin = [&](int c, auto kern, int nm) {
                 if (!hc[c]) return;
@@ -1038,7 +1076,7 @@ void build_hierarchy(Hier &h) {
                 PR_LAUNCH();
                 dfree(gbuf, s); dfree(goff, s);
             }
-            dfree(list, s); dfree(ccount, s);
+            dfree(list, s);
         }
         d2h(L.singular.data(), dsing, ND, s);
         dfree(dsing, s);
@@ -1076,31 +1114,37 @@ void build_hierarchy(Hier &h) {
         {
             // rows binned by their bound U: tables of 256 / 1024 / 4096 slots in
             // shared memory, larger rows in global scratch
-            int *bcount = dmalloc<int>(10, s);
-            PR_CUDA(cudaMemsetAsync(bcount, 0, sizeof(int) * 10, s));
-            k_rap_bin_count<<<blocks_for(nc, BS), BS, 0, s>>>(nc, U, bcount);
+            int8_t *rcls = dmalloc<int8_t>(nc, s);
+            k_rap_classes<<<blocks_for(nc, BS), BS, 0, s>>>(nc, U, rcls);
             PR_LAUNCH();
-            int hb[4];
-            d2h(hb, bcount, 4, s);
-            int bstart[4], acc = 0;
-            for (int c = 0; c < 4; ++c) { bstart[c] = acc; acc += hb[c]; }
-            PR_CUDA(cudaMemcpyAsync(bcount, bstart, sizeof(int) * 4, cudaMemcpyHostToDevice, s));
-            PR_CUDA(cudaMemsetAsync(bcount + 4, 0, sizeof(int) * 4, s));
+            int hb[4], bstart[4];
             int *rlist = dmalloc<int>(nc, s);
-            k_rap_bin_fill<<<blocks_for(nc, BS), BS, 0, s>>>(nc, U, bcount, bcount + 4, rlist);
-            PR_LAUNCH();
+            partition_by_class(rcls, nc, 4, rlist, bstart, hb, s);
+            dfree(rcls, s);
             const int caps[3] = {256, 1024, 4096};
+            int filt = prm.phi_A > 0.0 ? 1 : 0;
             PR_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int), s));
             for (int c = 0; c < 3; ++c) {
                 if (!hb[c]) continue;
                 int hcap = caps[c];
-                int wpb = std::max(1, std::min(16, (200 * 1024) / (hcap * 12)));
-                size_t sm = (size_t)hcap * wpb * (sizeof(double) + sizeof(int));
-                PR_CUDA(cudaFuncSetAttribute(k_rap<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-                unsigned grid = std::min<unsigned>(blocks_for(hb[c], wpb), 152u * 32u);
-                k_rap<false><<<grid, 32 * wpb, sm, s>>>(hb[c], rlist + bstart[c], nc, L.cpts, L.zrowptr, L.zcol, L.zval,
-                                                        L.rowptr, aplen, apcol, apval, uptr, U, prm.phi_A, cnt, ucol,
-                                                        uval, hcap, nullptr, nullptr, nullptr, d_count, h.d_err);
+                bool grp = c == 0;   // small rows: 8 lanes per row, 4 rows per warp
+                int spw = grp ? 4 : 1;
+                int wpb = std::max(1, std::min(16, (200 * 1024) / (hcap * 12 * spw)));
+                size_t sm = (size_t)hcap * wpb * spw * (sizeof(double) + sizeof(int));
+                unsigned grid = std::min<unsigned>(blocks_for(hb[c], wpb * spw), 152u * 32u);
+                if (grp) {
+                    PR_CUDA(cudaFuncSetAttribute(k_rap<8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+                    k_rap<8, false><<<grid, 32 * wpb, sm, s>>>(hb[c], rlist + bstart[c], L.cpts, L.zrowptr, L.zcol,
+                                                               L.zval, L.rowptr, aplen, apcol, apval, uptr, U, filt,
+                                                               prm.phi_A, cnt, ucol, uval, hcap, nullptr, nullptr,
+                                                               nullptr, d_count, h.d_err);
+                } else {
+                    PR_CUDA(cudaFuncSetAttribute(k_rap<32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+                    k_rap<32, false><<<grid, 32 * wpb, sm, s>>>(hb[c], rlist + bstart[c], L.cpts, L.zrowptr, L.zcol,
+                                                                L.zval, L.rowptr, aplen, apcol, apval, uptr, U, filt,
+                                                                prm.phi_A, cnt, ucol, uval, hcap, nullptr, nullptr,
+                                                                nullptr, d_count, h.d_err);
+                }
                 PR_LAUNCH();
             }
             int nover = hb[3];
@@ -1115,8 +1159,8 @@ void build_hierarchy(Hier &h) {
                 d2h(&gtot, capw + nover, 1, s);
                 int *gk = dmalloc<int>(gtot, s);
                 double *gv = dmalloc<double>(gtot, s);
-                k_rap<true><<<std::min<unsigned>(nover, 152u * 16u), 32, 0, s>>>(
-                    nover, list, nc, L.cpts, L.zrowptr, L.zcol, L.zval, L.rowptr, aplen, apcol, apval, uptr, U,
+                k_rap<32, true><<<std::min<unsigned>(nover, 152u * 16u), 32, 0, s>>>(
+                    nover, list, L.cpts, L.zrowptr, L.zcol, L.zval, L.rowptr, aplen, apcol, apval, uptr, U, filt,
                     prm.phi_A, cnt, ucol, uval, 0, capw, gk, gv, d_count, h.d_err);
                 PR_LAUNCH();
                 dfree(gk, s); dfree(gv, s); dfree(capw, s);
@@ -1124,7 +1168,7 @@ void build_hierarchy(Hier &h) {
             int nrej = 0;
             d2h(&nrej, d_count, 1, s);
             PR_REQUIRE(nrej == 0, PAIR_ERR_DEVICE, "RAP row exceeded its table bin");
-            dfree(rlist, s); dfree(bcount, s);
+            dfree(rlist, s);
         }
         Level C;
         C.n = nc;
