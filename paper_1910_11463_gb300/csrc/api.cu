@@ -1,6 +1,7 @@
 // extern "C" boundary of libpair (declared in include/pair.h).  Every entry
 // point converts internal errors into a pair_status and a per-thread message.
 #include <algorithm>
+#include <cstdio>
 #include <cmath>
 #include <cstring>
 
@@ -202,23 +203,19 @@ pair_status air_solve(pair_hier hh, const double *b, double *x, double tol, int 
         PR_REQUIRE(hh && b && x && tol >= 0 && maxit >= 0, PAIR_ERR_ARG, "air_solve: bad argument");
         pr::Hier &h = hh->h;
         PR_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
-        pr::BatchSolve bs;
-        pair_status st = PAIR_OK;
-        std::string msg;
-        try {
-            bs = pr::solve_batch(h, b, x, tol, maxit, false);
-        } catch (const pr::Error &e) {
-            if (e.st != PAIR_ERR_NOT_CONVERGED) throw;
-            st = e.st;
-            msg = e.msg;
-        }
+        pr::BatchSolve bs = pr::solve_batch(h, b, x, tol, maxit, false);
         PR_CUDA(cudaStreamSynchronize(h.stream));
         if (info) {
             info->iters = bs.iters;
             info->rel_resid = bs.max_rel;
             info->rho = bs.rho_cnt ? bs.rho_sum / bs.rho_cnt : 0.0;
         }
-        if (st != PAIR_OK) pr::fail(st, msg);
+        if (!bs.converged) {
+            char buf[160];
+            snprintf(buf, sizeof buf, "air_solve: %d cycles, relative residual %.3e > %.3e", bs.iters, bs.max_rel,
+                     tol);
+            pr::fail(PAIR_ERR_NOT_CONVERGED, buf);
+        }
     });
 }
 

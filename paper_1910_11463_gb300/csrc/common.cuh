@@ -158,6 +158,7 @@ long long hex_nnz(int n, const double *omega_h);
 
 // si.cu
 struct BatchSolve {
+    bool converged = true;
     int iters = 0;
     double max_rel = 0;
     double rho_sum = 0;

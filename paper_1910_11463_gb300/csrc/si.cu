@@ -183,12 +183,7 @@ BatchSolve solve_batch(Hier &h, const double *b, double *x, double tol, int maxi
             out.rho_cnt++;
         }
     }
-    if (any) {
-        char buf[160];
-        snprintf(buf, sizeof buf, "AIR solve reached %d cycles with relative residual %.3e > %.3e", k, out.max_rel,
-                 tol);
-        fail(PAIR_ERR_NOT_CONVERGED, buf);
-    }
+    out.converged = !any;
     return out;
 }
 
@@ -415,6 +410,12 @@ void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t,
             PR_LAUNCH();
             PR_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * Bt.nd * N, hs));
             BatchSolve bs = solve_batch(h, Bt.b, x, sp.inner_tol, sp.inner_maxit, sp.use_graphs != 0);
+            if (!bs.converged) {
+                char buf[160];
+                snprintf(buf, sizeof buf, "AIR solve reached %d cycles with relative residual %.3e > %.3e", bs.iters,
+                         bs.max_rel, sp.inner_tol);
+                fail(PAIR_ERR_NOT_CONVERGED, buf);
+            }
             vcycles += bs.iters * Bt.nd;
             max_inner = std::max(max_inner, bs.max_rel);
             k_phi_acc<<<blocks_for(N, BS), BS, 0, hs>>>(N, Bt.nd, w_d + Bt.m0, x, phinew);

@@ -152,6 +152,20 @@ def test_air_solve_equals_sweep(pair, precision, tol):
         assert np.linalg.norm(x[sl] - xs) <= 1e-9 * np.linalg.norm(xs)
 
 
+def test_air_solve_reports_residual_when_not_converged(pair):
+    """Stopping at maxit still fills the info: the residual and the cycle count."""
+    prob = I.small_hex(6, order=2, seed=3)
+    mats = [_gpu_csr(pair, prob.n, prob.omega[m], prob.sigma_t) for m in range(2)]
+    H = pair.Hierarchy(mats, pair.default_air_params(precision=0))
+    b = torch.ones(2 * prob.N, dtype=torch.float64, device="cuda")
+    x, info = H.solve(b, tol=1e-14, maxit=2, raise_on_fail=False)
+    assert info["status"] == -4 and info["iters"] == 2
+    assert 1e-14 < info["rel_resid"] < 1.0
+    x0 = torch.zeros_like(b)
+    _, info0 = H.solve(b, x0, tol=1e-14, maxit=0, raise_on_fail=False)
+    assert info0["iters"] == 0 and abs(info0["rel_resid"] - 1.0) < 1e-14   # x = 0: ||b - A 0|| / ||b|| = 1
+
+
 def test_si_fp64_matches_oracle_c1(pair):
     prob = I.config("hex8_s2")
     ref, _, info_o = O.si_hex(prob, tol=1e-8, inner_tol=1e-10)
