@@ -232,6 +232,31 @@ PAIR_API pair_status si_solve(const pair_mesh *mesh, const pair_quad *quad, cons
 
 PAIR_API const char *pair_last_error(void);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free residual.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory when they need a
+ * residual, for example code running inside a memory arena or pool that
+ * forbids cudaMalloc/cudaFree (an allocation there would synchronise the
+ * device or bypass the arena's accounting), or an application that has
+ * already reserved all device memory for its own buffers.
+ *
+ * r = b - A x and rnorm[0] = ||r||_2 (FP64, deterministic), for one CSR
+ * matrix.  All arrays are caller-owned device memory: A's arrays, b, x, r (n
+ * doubles each) and rnorm (one double).  The call allocates nothing: its only
+ * scratch, one partial sum per 256 rows, lives in a static device array of
+ * PAIR_NOALLOC_MAX_ROWS / 256 doubles (512 KiB) that every GPU which loads the
+ * library holds until the process exits.  Matrices with more than
+ * PAIR_NOALLOC_MAX_ROWS rows are rejected with PAIR_ERR_UNSUPPORTED.
+ * The first call on a device looks up the array's device address; make that
+ * first call before any stream capture.  All calls share the one array, so
+ * calls whose work overlaps on the GPU (different streams, no ordering) race
+ * and must not be issued; each call writes every scratch entry it reads, so
+ * nothing needs clearing between calls.  Ordered on 'stream'.
+ * ------------------------------------------------------------------------- */
+#define PAIR_NOALLOC_MAX_ROWS (1 << 24)
+PAIR_API pair_status pair_residual_norm_noalloc(const pair_csr *A, const double *b, const double *x, double *r,
+                                                double *rnorm, void *stream);
+
 /* Library kernels launched so far by this process (graph replays count each
  * captured kernel once per replay).  Instrumentation for benchmarks; not
  * thread-safe with concurrent library calls. */

@@ -81,6 +81,8 @@ struct StreamJoin {
 
 }  // namespace
 
+void pr::set_last_error(const std::string &msg) { g_last_error = msg; }
+
 extern "C" {
 
 void air_params_default(air_params *p) {

@@ -16,6 +16,7 @@ struct Error {
 };
 
 [[noreturn]] void fail(pair_status st, const std::string &msg);
+void set_last_error(const std::string &msg);   // the message pair_last_error() returns
 void cuda_check(cudaError_t e, const char *what, const char *file, int line);
 
 #define PR_CUDA(call) ::pr::cuda_check((call), #call, __FILE__, __LINE__)

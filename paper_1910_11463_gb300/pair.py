@@ -85,6 +85,7 @@ def lib():
             "si_params_default": (None, [C.POINTER(si_params)]),
             "pair_last_error": (C.c_char_p, []),
             "pair_kernel_launches": (C.c_longlong, []),
+            "pair_residual_norm_noalloc": (i, [C.POINTER(pair_csr), vp, vp, vp, vp, vp]),
             "air_setup": (i, [C.POINTER(pair_csr), i, C.POINTER(air_params), vp, C.POINTER(vp)]),
             "air_vcycle": (i, [vp, vp, vp, vp]),
             "air_solve": (i, [vp, vp, vp, d, i, vp, C.POINTER(air_solve_info)]),
@@ -249,6 +250,20 @@ class Hierarchy:
         if raise_on_fail or st not in (PAIR_OK, -4):
             _check(st)
         return x, {"iters": info.iters, "rel_resid": info.rel_resid, "rho": info.rho, "status": st}
+
+
+def residual_norm_noalloc(rowptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor, b: torch.Tensor,
+                          x: torch.Tensor, r: torch.Tensor | None = None, rnorm: torch.Tensor | None = None):
+    """r = b - A x and ||r||_2 through the allocation-free entry point (the
+    library allocates nothing; r and rnorm are allocated here by PyTorch unless
+    given).  Returns (r, rnorm) as device tensors."""
+    if r is None:
+        r = torch.empty_like(b)
+    if rnorm is None:
+        rnorm = torch.empty(1, dtype=torch.float64, device=b.device)
+    desc = pair_csr(rowptr.numel() - 1, col.numel(), rowptr.data_ptr(), col.data_ptr(), val.data_ptr())
+    _check(lib().pair_residual_norm_noalloc(C.byref(desc), _dptr(b), _dptr(x), _dptr(r), _dptr(rnorm), _stream()))
+    return r, rnorm
 
 
 # ---------------------------------------------------------------------------
