@@ -9,13 +9,17 @@ Workload (default): unit cube, 32^3 hexahedra, trilinear Q1 upwind DG
 batch, sigma_t ~ U[0.5, 2] per element (SplitMix64 seed 1), sigma_s = 0.8
 sigma_t, q = 1, vacuum boundaries.  Synthetic, seeded inputs.
 
-One timed step = one full pass of the path from resident inputs: DG assembly
-and block scaling of all directions, AIR setup of every hierarchy (strength,
-PMIS, one-point P, lAIR, Galerkin RAP), then one source iteration (right-hand
-sides, every direction solved from psi = 0 to 1e-8 with FP32 V-cycles under
-FP64 iterative refinement, scalar-flux quadrature sum).  Hierarchies are
-rebuilt every step, as in the paper's memory mode.  Each step moves well over
-1 GB, far more than the 129 MB L2, so no explicit flush is needed between steps.
+One timed step = one complete source-iteration solve from phi = 0, every row of
+the path in every step: DG assembly and block scaling of all directions, AIR
+setup of every hierarchy (strength, PMIS, one-point P, lAIR, Galerkin RAP),
+then source iterations to ||phi^{n+1} - phi^n|| <= 1e-8 ||phi^{n+1}||, each
+iteration building the right-hand sides, solving every direction from psi = 0
+to a 1e-8 relative FP64 residual (FP32 V-cycles under FP64 iterative
+refinement) and forming the scalar-flux quadrature sum.  The value is
+DOF*directions*iterations / step time, so the setup is amortised over the
+solve's iterations; the mode that rebuilds every hierarchy for every iteration
+(the paper's memory mode) is measured beside it.  Each step moves many GB, far
+more than the 129 MB L2, so no explicit flush is needed between steps.
 
 --impl reference times the CPU oracle (the plain C implementation the tests
 check against) on the host cores on a bounded sample of the same workload.
@@ -117,26 +121,38 @@ class ClockSampler:
                 "samples": len(sm), "power_w_max": max(power) if power else None}
 
 
-def cpu_baseline_oracle(prob, max_seconds: float = 20.0, min_dirs: int = 1):
-    """The CPU oracle, as it stands, on the host: one source-iteration step
-    (assembly, AIR setup and a 1e-8 solve of every sampled direction, scalar
-    flux sum) over as many directions as fit the time bound."""
+def oracle_direction_times(prob, m, air_kw):
+    """Oracle times for one direction: assembly + AIR setup, and one solve of
+    the first SI iteration's right-hand side to 1e-8 (seconds)."""
+    import numpy as np
     from oracle import oracle as O
-    from paper_1910_11463_gb300 import inputs as I
+    t0 = time.perf_counter()
+    r, c, v = O.hex_assemble(prob.n, prob.omega[m], prob.sigma_t)
+    H = O.Hierarchy(r, c, v, O.default_params(**air_kw))
+    t1 = time.perf_counter()
+    src = np.repeat(prob.q, 8) / (4 * np.pi)
+    b = O.hex_rhs(prob.n, prob.omega[m], prob.sigma_t, src)
+    H.solve(b, tol=1e-8, maxit=500)
+    t2 = time.perf_counter()
+    return t1 - t0, t2 - t1
+
+
+def cpu_baseline_oracle(prob, si_iters, air_kw, max_seconds: float = 20.0):
+    """The CPU oracle, as it stands, single-threaded on the host, on a bounded
+    sample of the workload's directions; per-SI-iteration throughput with the
+    setup amortised over the same number of SI iterations as the GPU solve."""
+    from oracle import oracle as O
     O.build()
-    done, t_total = 0, 0.0
+    done, ts, tv = 0, 0.0, 0.0
     while done < prob.M:
-        sub = I.HexProblem(prob.name, prob.n, prob.omega[done:done + 1].copy(), prob.w[done:done + 1].copy(),
-                           prob.sigma_t, prob.sigma_s, prob.q)
-        t0 = time.perf_counter()
-        O.si_hex(sub, tol=1e-8, max_iters=1, inner_tol=1e-8, inner_maxit=500)
-        t_total += time.perf_counter() - t0
-        done += 1
-        if done >= min_dirs and t_total >= max_seconds:
+        a, b = oracle_direction_times(prob, done, air_kw)
+        ts, tv, done = ts + a, tv + b, done + 1
+        if ts + tv >= max_seconds:
             break
-    return {"value": prob.N * done / t_total, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{done} of {prob.M} directions of the same workload, one SI step each "
-                      f"(assembly + AIR setup + 1e-8 solve + phi sum), single-threaded C oracle, {t_total:.2f} s"}
+    per_dir_iter = ts / done / max(si_iters, 1) + tv / done
+    return {"value": prob.N / per_dir_iter, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{done} of {prob.M} directions: oracle assembly + AIR setup ({ts:.1f} s) and one 1e-8 solve "
+                      f"each ({tv:.1f} s), setup amortised over {si_iters} SI iterations, single-threaded"}
 
 
 def run_reference(args):
@@ -145,25 +161,25 @@ def run_reference(args):
         return 0
     from paper_1910_11463_gb300 import inputs as I
     prob = I.config(args.config)
-    # each step: one direction of the workload through the oracle (bounded CPU sample)
+    # each step: one direction of the workload through the oracle (bounded CPU
+    # sample); setup amortised over the SI iterations the workload needs
     from oracle import oracle as O
     O.build()
+    air_kw = dict(theta=args.theta, phi_R=args.phi_R, phi_A=args.phi_A)
+    si_iters = args.si_iters
     times = []
     for k in range(args.warmup + args.steps):
-        m = k % prob.M
-        sub = I.HexProblem(prob.name, prob.n, prob.omega[m:m + 1].copy(), prob.w[m:m + 1].copy(),
-                           prob.sigma_t, prob.sigma_s, prob.q)
-        t0 = time.perf_counter()
-        O.si_hex(sub, tol=1e-8, max_iters=1, inner_tol=1e-8, inner_maxit=500)
+        a, b = oracle_direction_times(prob, k % prob.M, air_kw)
         if k >= args.warmup:
-            times.append(time.perf_counter() - t0)
+            times.append(a / si_iters + b)
     t = sum(times) / len(times)
     value = prob.N / t
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.config + ": " + WORKLOADS[args.config],
-                       "step": "one direction of the workload per step: assembly + AIR setup + 1e-8 solve + phi sum"},
+                       "step": "one direction of the workload per step: oracle assembly + AIR setup (amortised over "
+                               f"{si_iters} SI iterations) + one 1e-8 solve"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{args.steps} timed directions (after {args.warmup} warm-up), "
                                        "single-threaded C oracle"},
@@ -194,23 +210,23 @@ def run_ours(args):
     ss = torch.as_tensor(prob.sigma_s, device=dev)
     qq = torch.as_tensor(prob.q, device=dev)
     N, M = prob.N, prob.M
-    air = pair.default_air_params(precision=args.precision)
-    si = pair.default_si_params(tol=1e-8, max_iters=1, inner_tol=1e-8, inner_maxit=200)
-    phi = torch.zeros(N, dtype=torch.float64, device=dev)
-    quad = (prob.omega, prob.w)
+    tuned = dict(theta=args.theta, phi_R=args.phi_R, phi_A=args.phi_A)
+    air = pair.default_air_params(precision=args.precision, **tuned)
+    si = pair.default_si_params(tol=1e-8, max_iters=1000, inner_tol=1e-8, inner_maxit=200)
+    si_one = pair.default_si_params(tol=1e-8, max_iters=1, inner_tol=1e-8, inner_maxit=200)
+    zero = torch.zeros(N, dtype=torch.float64, device=dev)
 
-    def step(phi_in, air_p, si_p):
-        out, _, info = pair.si_solve(prob.n, quad[0], quad[1], st, ss, qq, air=air_p, si=si_p, phi0=phi_in)
+    def solve(air_p, si_p, phi0):
+        out, _, info = pair.si_solve(prob.n, prob.omega, prob.w, st, ss, qq, air=air_p, si=si_p, phi0=phi0)
         return out, info
-
-    # warm-up: the SI continues from step to step (phi^n -> phi^{n+1})
-    for _ in range(args.warmup):
-        phi, info = step(phi, air, si)
 
     def barrier():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        solve(air, si, zero)
 
     infos = []
     clocks = ClockSampler(torch.cuda.current_device())
@@ -221,7 +237,7 @@ def run_ours(args):
     barrier()
     e0.record(stream)
     for _ in range(args.steps):
-        phi, info = step(phi, air, si)
+        phi, info = solve(air, si, zero)
         infos.append(info)
     e1.record(stream)
     barrier()
@@ -232,21 +248,24 @@ def run_ours(args):
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    value = N * M * world / (ms * 1e-3)
+    iters = infos[-1]["si_iters"]
+    value = N * M * iters * world / (ms * 1e-3)
 
-    # phase split and level-0 kernel roofline from the library's device events
     def tot(key):
         return sum(i[key] for i in infos)
     t_setup, t_solve = tot("t_setup_ms") / args.steps, tot("t_solve_ms") / args.steps
     phases = [sum(i["t_setup_phase_ms"][k] for i in infos) / args.steps for k in range(4)]
     peak, peak_kind = measured_peaks()
     kern = {
-        "k_res0_bsr (FP64 outer residual, level 0)": (tot("t_res0_ms"), tot("n_res0"), tot("gb_res0")),
-        "k_relax_bsr (FP32 F-F-C Jacobi, level 0)": (tot("t_relax0_ms"), tot("n_relax0"), tot("gb_relax0")),
+        "k_res0_bsr": ("FP64 outer residual, level 0 block form", tot("t_res0_ms"), tot("n_res0"), tot("gb_res0")),
+        "k_relax_bsr": ("FP32 F-F-C Jacobi, level 0 block form", tot("t_relax0_ms"), tot("n_relax0"),
+                        tot("gb_relax0")),
+        "k_relax_csr": ("FP32 F-F-C Jacobi, levels >= 1 (CSR), per cycle", tot("t_relaxc_ms"), tot("n_relaxc"),
+                        tot("gb_relaxc")),
     }
     rl = {}
-    for name, (t_ms, n_l, gb) in kern.items():
-        rl[name] = {"achieved": gb / (t_ms * 1e-3) if t_ms > 0 else None, "launches": n_l,
+    for name, (what, t_ms, n_l, gb) in kern.items():
+        rl[name] = {"what": what, "achieved_gbs": gb / (t_ms * 1e-3) if t_ms > 0 else None, "launches": n_l,
                     "ms_per_launch": t_ms / max(n_l, 1), "gb_per_launch": gb / max(n_l, 1),
                     "share_of_step": t_ms / args.steps / ms}
     dom = max(rl, key=lambda k: rl[k]["share_of_step"])
@@ -255,53 +274,64 @@ def run_ours(args):
     if os.path.exists(tfile):
         with open(tfile) as f:
             tj = json.load(f)
-        entry = tj.get(dom.split()[0])
+        entry = tj.get(dom)
         if entry and entry.get("source_sha") == pair.kernel_source_sha(entry.get("source", "cycle.cu")):
             traffic = entry["bytes_per_launch"] * (rl[dom]["gb_per_launch"] / entry["gb_per_launch_at_capture"])
-    achieved = rl[dom]["achieved"]
+    achieved = rl[dom]["achieved_gbs"]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak if achieved else None, "traffic": traffic,
-                "kernel": dom, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs copy test)",
-                "algorithmic_bytes": "per launch: FP64 face-block rows + b, psi read + r written (residual); "
-                                     "see DESIGN.md",
+                "frac": achieved / peak if achieved else None, "traffic": traffic, "kernel": dom,
+                "peak_source": f"{peak_kind}: MEASURED_PEAKS.json hbm_gbs (copy test)",
+                "algorithmic_bytes": "counted per launch in the library from the hierarchy (DESIGN.md 6)",
                 "kernels": rl}
 
-    # e2e: the same step through the public API with host buffers (pinned),
-    # copies in and phi back to the host inside the timed region
+    # the paper's memory mode: every hierarchy rebuilt for every iteration
+    reb = []
+    for k in range(3):
+        barrier()
+        e0.record(stream)
+        solve(air, si_one, phi)
+        e1.record(stream)
+        barrier()
+        reb.append(e0.elapsed_time(e1))
+    ms_reb = sorted(reb)[1]
+    rebuild = {"value": N * M / (ms_reb * 1e-3), "ms_per_iteration": ms_reb,
+               "note": "assembly + AIR setup + one SI iteration per step (median of 3)"}
+
+    # e2e: the same full solve through the public API with pinned host buffers,
+    # inputs copied in and phi copied back inside the timed region
     h_st = torch.as_tensor(prob.sigma_t).pin_memory()
     h_ss = torch.as_tensor(prob.sigma_s).pin_memory()
     h_q = torch.as_tensor(prob.q).pin_memory()
-    h_phi = phi.cpu().pin_memory()
-    e2e_steps = max(1, min(args.steps, 3))
+    h_phi0 = torch.zeros(N, dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(args.steps, 2))
     barrier()
     e0.record(stream)
     for _ in range(e2e_steps):
-        out, _, _ = pair.si_solve(prob.n, quad[0], quad[1], h_st, h_ss, h_q, air=air, si=si, phi0=h_phi)
-        h_phi = out.cpu()
+        out, _, info_e = pair.si_solve(prob.n, prob.omega, prob.w, h_st, h_ss, h_q, air=air, si=si, phi0=h_phi0)
+        h_out = out.cpu()
     e1.record(stream)
     barrier()
     ms_e2e = e0.elapsed_time(e1) / e2e_steps
-    e2e = {"value": N * M * world / (ms_e2e * 1e-3), "unit": UNIT,
-           "h2d_bytes_per_step": 3 * prob.E * 8 + N * 8, "d2h_bytes_per_step": N * 8,
-           "ms_per_step": ms_e2e}
+    e2e = {"value": N * M * info_e["si_iters"] * world / (ms_e2e * 1e-3), "unit": UNIT,
+           "h2d_bytes_per_step": 3 * prob.E * 8 + N * 8, "d2h_bytes_per_step": N * 8, "ms_per_step": ms_e2e}
 
-    # comparator: plain FP64 pAIR, one direction at a time, no graphs (same GPU)
+    # comparator: plain FP64 pAIR, one direction at a time, no graphs (same GPU, same AIR parameters)
     fp64 = None
     if not args.no_fp64_baseline:
-        air64 = pair.default_air_params(precision=0)
-        si64 = pair.default_si_params(tol=1e-8, max_iters=1, inner_tol=1e-8, inner_maxit=200, batch=1,
+        air64 = pair.default_air_params(precision=0, **tuned)
+        si64 = pair.default_si_params(tol=1e-8, max_iters=1000, inner_tol=1e-8, inner_maxit=200, batch=1,
                                       use_graphs=0)
-        step(phi, air64, si64)
         barrier()
         e0.record(stream)
-        _, i64 = step(phi, air64, si64)
+        phi64, i64 = solve(air64, si64, zero)
         e1.record(stream)
         barrier()
         ms64 = e0.elapsed_time(e1)
-        fp64 = {"value": N * M / (ms64 * 1e-3), "ms_per_step": ms64, "setup_ms": i64["t_setup_ms"],
-                "solve_ms": i64["t_solve_ms"], "vcycles": i64["vcycles"],
-                "speedup_of_fp32_refined_batched": (N * M / (ms * 1e-3)) / (N * M / (ms64 * 1e-3))}
-
+        err = (torch.linalg.norm(phi64 - phi) / torch.linalg.norm(phi64)).item()
+        fp64 = {"value": N * M * i64["si_iters"] / (ms64 * 1e-3), "ms_per_step": ms64, "si_iters": i64["si_iters"],
+                "setup_ms": i64["t_setup_ms"], "solve_ms": i64["t_solve_ms"],
+                "speedup_of_fp32_refined_batched": value / world / (N * M * i64["si_iters"] / (ms64 * 1e-3)),
+                "phi_rel_diff_fp32_refined_vs_fp64": err}
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -313,22 +343,26 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32 V-cycle + f64 residual/setup" if args.precision else "f64",
         "data": "synthetic",
         "config": {"workload": args.config + ": " + WORKLOADS[args.config],
-                   "step": "assembly + AIR setup (rebuilt each step) + 1 source iteration, all directions solved "
-                           "from psi=0 to 1e-8 relative FP64 residual",
-                   "l2": "working set per step > 1 GB >> 129 MB L2 (no flush needed)",
+                   "step": "one complete SI solve from phi=0 (assembly + AIR setup + SI iterations to 1e-8, every "
+                           "direction solved from psi=0 to 1e-8 relative FP64 residual each iteration); value = "
+                           "DOF*dir*iterations/step time",
+                   "air": {"theta": args.theta, "eps_R": 0.01, "phi_R": args.phi_R, "phi_A": args.phi_A,
+                           "distance": 1, "relax": "F-F-C Jacobi", "coarsening": "PMIS"},
+                   "l2": "working set per step >> 129 MB L2 (no flush needed)",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU, all directions in one batch",
                    "precision": "FP32 hierarchy/V-cycle, FP64 refinement" if args.precision else "FP64"},
-        "solve_only": {"value": N * M / (t_solve * 1e-3), "ms_per_step": t_solve,
-                       "note": "RHS + solves + phi sum with resident hierarchies"},
-        "setup_ms": t_setup, "setup_phase_ms": {"strength+pmis": phases[0], "p+lair": phases[1],
-                                                "rap": phases[2], "assembly+other": phases[3]},
-        "vcycles_per_direction": last["vcycles"] / M, "levels": last["levels_max"],
+        "si_iterations": iters, "setup_ms": t_setup, "solve_ms": t_solve,
+        "setup_phase_ms": {"strength+pmis": phases[0], "p+lair": phases[1], "rap": phases[2],
+                           "assembly+other": phases[3]},
+        "rebuild_every_iteration": rebuild,
+        "vcycles_per_direction_per_iteration": last["vcycles"] / M / max(iters, 1), "levels": last["levels_max"],
         "op_complexity": last["op_complexity"], "max_inner_resid": last["max_inner_resid"],
         "roofline": roofline, "clocks": clk, "e2e": e2e, "gpu_launches": launches,
         "fp64_one_direction": fp64,
     }
     if world == 1 or rank == 0:
-        line["cpu_baseline"] = cpu_baseline_oracle(prob, max_seconds=args.cpu_seconds) if not args.no_cpu else None
+        line["cpu_baseline"] = (cpu_baseline_oracle(prob, iters, tuned, max_seconds=args.cpu_seconds)
+                                if not args.no_cpu else None)
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -346,6 +380,11 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64-baseline", action="store_true")
+    ap.add_argument("--theta", type=float, default=0.5)
+    ap.add_argument("--phi-R", dest="phi_R", type=float, default=0.0)
+    ap.add_argument("--phi-A", dest="phi_A", type=float, default=0.05)
+    ap.add_argument("--si-iters", type=int, default=18,
+                    help="SI iterations the setup is amortised over in the reference arm (hex32_s4 needs 18)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)   # timing rule: at least three untimed warm-up steps
     if args.impl == "reference":

@@ -215,6 +215,9 @@ typedef struct {
     int n_relax0;
     double gb_relax0;
     double t_setup_phase_ms[4]; /* strength+PMIS, P+lAIR, Galerkin RAP, other setup */
+    double t_relaxc_ms;      /* F- and C-Jacobi passes on levels >= 1 (CSR), all cycles */
+    int n_relaxc;            /* cycles measured */
+    double gb_relaxc;        /* algorithmic GB of those passes */
 } si_info;
 
 /* Source iteration (Eq. sn_transport with Eq. angular_quad): each iteration

@@ -130,6 +130,10 @@ struct Hier {
     // per matrix: level-0 algorithmic bytes of one residual / one F+C relaxation pass
     std::vector<double> bytes_res0, bytes_relax0;
     double t_phase[4] = {0, 0, 0, 0};   // setup: strength+PMIS, P+lAIR, RAP, other
+    // coarse-level (l >= 1) relaxation: events per level, bytes per cycle
+    std::vector<cudaEvent_t> evl;      // 2 per level
+    double t_relaxc = 0, gb_relaxc = 0, bytes_relaxc = 0;
+    long long n_relaxc = 0;
     cudaGraphExec_t graph = nullptr;
     long long graph_kernels = 0;
     const double *graph_b = nullptr;
@@ -149,7 +153,7 @@ void vcycle_correct(Hier &h, double *x);       // x += V(lev[0].vb), zero initia
 void norms0(Hier &h, const double *v, double *out);  // per-matrix 2-norms of a level-0 vector
 void alloc_cycle_vectors(Hier &h);
 void set_all_active(Hier &h);   // every matrix of the batch takes part in the next cycle
-void level0_bytes(Hier &h);   // fills bytes_res0 / bytes_relax0 (hex block form)
+void level0_bytes(Hier &h);   // fills bytes_res0 / bytes_relax0 (hex block form), bytes_relaxc
 void prof_enable(Hier &h);
 
 // assemble.cu

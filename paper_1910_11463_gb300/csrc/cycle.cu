@@ -354,10 +354,13 @@ void vcycle_t(Hier &h, double *x64) {
             if (h.prof) rec_event(h.ev[3], s);
         } else {
             const int *act = l == 0 ? active : nullptr;
+            bool tl = h.prof && l >= 1 && (int)h.evl.size() >= 2 * (l + 1);
+            if (tl) rec_event(h.evl[2 * l], s);
             for (int f = 0; f < fs; ++f, cur ^= 1)
                 relax_csr<T>(L, (const T *)L.vb, bufs[cur], bufs[cur ^ 1], 0, nullptr, nullptr, act, s);
             relax_csr<T>(L, (const T *)L.vb, bufs[cur], (T *)L.vx, 1, l == 0 ? x64 : nullptr, (const T *)L.vx, act,
                          s);
+            if (tl) rec_event(h.evl[2 * l + 1], s);
         }
     }
     if (NL == 1) {   // single-level hierarchies: x += coarsest solution
@@ -423,11 +426,50 @@ __global__ void k_face_counts(int n, int N, const int8_t *dsign, const int8_t *c
 }
 }  // namespace
 
+namespace {
+// per level: [F rows, C rows, entries of F rows, entries of C rows]
+__global__ void k_level_counts(int n, const int *rowptr, const int8_t *cf, unsigned long long *out) {
+    __shared__ unsigned long long sh[4];
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (threadIdx.x < 4) sh[threadIdx.x] = 0;
+    __syncthreads();
+    if (i < n && cf[i] != CF_COARSEST) {
+        bool isC = cf[i] == CF_C;
+        atomicAdd(&sh[isC ? 1 : 0], 1ULL);
+        atomicAdd(&sh[isC ? 3 : 2], (unsigned long long)(rowptr[i + 1] - rowptr[i]));
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) atomicAdd(&out[threadIdx.x], sh[threadIdx.x]);
+}
+}  // namespace
+
 void level0_bytes(Hier &h) {
     h.bytes_res0.assign(h.ndir, 0.0);
     h.bytes_relax0.assign(h.ndir, 0.0);
-    if (!h.bsr0) return;
+    h.bytes_relaxc = 0;
     cudaStream_t s = h.stream;
+    {
+        // coarse levels: each F sweep reads rowptr, cf, input and writes output for every
+        // row, and entries (column + value), b and dinv of F rows; the C sweep likewise
+        double sT = h.prm.precision == 1 ? 4.0 : 8.0;
+        unsigned long long *cnt = dmalloc<unsigned long long>(4, s);
+        for (size_t l = 1; l + 1 < h.lev.size(); ++l) {
+            Level &L = h.lev[l];
+            if (L.n == 0) continue;
+            PR_CUDA(cudaMemsetAsync(cnt, 0, 4 * sizeof(unsigned long long), s));
+            k_level_counts<<<blocks_for(L.n, BS), BS, 0, s>>>(L.n, L.rowptr, L.cf, cnt);
+            PR_LAUNCH();
+            unsigned long long c[4];
+            PR_CUDA(cudaMemcpyAsync(c, cnt, sizeof c, cudaMemcpyDeviceToHost, s));
+            PR_CUDA(cudaStreamSynchronize(s));
+            double rows = (double)(c[0] + c[1]);
+            double fpass = rows * (4 + 1 + 2 * sT) + (double)c[2] * (4 + sT) + (double)c[0] * 2 * sT;
+            double cpass = rows * (4 + 1 + 2 * sT) + (double)c[3] * (4 + sT) + (double)c[1] * 2 * sT;
+            h.bytes_relaxc += h.prm.f_sweeps * fpass + cpass;
+        }
+        dfree(cnt, s);
+    }
+    if (!h.bsr0) return;
     int N = h.n0[0];
     unsigned long long *cnt = dmalloc<unsigned long long>(4 * h.ndir, s);
     PR_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * 4 * h.ndir, s));
@@ -453,6 +495,8 @@ void level0_bytes(Hier &h) {
 void prof_enable(Hier &h) {
     if (h.prof) return;
     for (auto &e : h.ev) PR_CUDA(cudaEventCreate(&e));
+    h.evl.assign(2 * h.lev.size(), nullptr);
+    for (auto &e : h.evl) PR_CUDA(cudaEventCreate(&e));
     h.prof = true;
 }
 

@@ -137,6 +137,23 @@ BatchSolve solve_batch(Hier &h, const double *b, double *x, double tol, int maxi
         for (int d = 0; d < nd; ++d)
             if (was_active[d]) { br += h.bytes_res0[d]; bx += h.bytes_relax0[d]; }
         h.gb_res0 += br * 1e-9;
+        if (relax && h.evl.size() >= 4) {
+            // coarse levels run for every direction of the batch
+            double tl = 0;
+            int nl = 0;
+            for (size_t l = 1; l + 1 < h.lev.size(); ++l) {
+                if (!h.lev[l].n) continue;
+                float m2 = 0;
+                PR_CUDA(cudaEventElapsedTime(&m2, h.evl[2 * l], h.evl[2 * l + 1]));
+                tl += m2;
+                ++nl;
+            }
+            if (nl) {
+                h.t_relaxc += tl;
+                h.n_relaxc += 1;
+                h.gb_relaxc += h.bytes_relaxc * 1e-9;
+            }
+        }
         if (relax && h.relax_timed) {
             PR_CUDA(cudaEventElapsedTime(&ms, h.ev[2], h.ev[3]));
             h.t_relax0 += ms;
@@ -190,6 +207,8 @@ BatchSolve solve_batch(Hier &h, const double *b, double *x, double tol, int maxi
 Hier::~Hier() {
     if (graph) cudaGraphExecDestroy(graph);
     for (auto &e : ev)
+        if (e) cudaEventDestroy(e);
+    for (auto &e : evl)
         if (e) cudaEventDestroy(e);
     if (stream) {
         for (auto &L : lev) free_level(L, stream);
@@ -352,12 +371,14 @@ void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t,
     double max_inner = 0, opc_sum = 0, change = 0;
     int opc_cnt = 0, it = 0;
     double t_res0 = 0, t_relax0 = 0, gb_res0 = 0, gb_relax0 = 0, tph[4] = {0, 0, 0, 0};
-    long long n_res0 = 0, n_relax0 = 0;
+    double t_relaxc = 0, gb_relaxc = 0;
+    long long n_res0 = 0, n_relax0 = 0, n_relaxc = 0;
     auto harvest = [&](Hier &h) {
         t_res0 += h.t_res0; t_relax0 += h.t_relax0; gb_res0 += h.gb_res0; gb_relax0 += h.gb_relax0;
         n_res0 += h.n_res0; n_relax0 += h.n_relax0;
-        h.t_res0 = h.t_relax0 = h.gb_res0 = h.gb_relax0 = 0;
-        h.n_res0 = h.n_relax0 = 0;
+        t_relaxc += h.t_relaxc; gb_relaxc += h.gb_relaxc; n_relaxc += h.n_relaxc;
+        h.t_res0 = h.t_relax0 = h.gb_res0 = h.gb_relax0 = h.t_relaxc = h.gb_relaxc = 0;
+        h.n_res0 = h.n_relax0 = h.n_relaxc = 0;
     };
     bool converged = false;
     auto elapsed = [&](cudaStream_t st) {
@@ -459,6 +480,9 @@ void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t,
         info->t_relax0_ms = t_relax0;
         info->n_relax0 = (int)n_relax0;
         info->gb_relax0 = gb_relax0;
+        info->t_relaxc_ms = t_relaxc;
+        info->n_relaxc = (int)n_relaxc;
+        info->gb_relaxc = gb_relaxc;
         for (int k = 0; k < 3; ++k) info->t_setup_phase_ms[k] = tph[k];
         info->t_setup_phase_ms[3] = t_setup - (tph[0] + tph[1] + tph[2]);
     }

@@ -66,7 +66,8 @@ class si_info(C.Structure):
                 ("t_setup_ms", C.c_double), ("t_solve_ms", C.c_double), ("levels_max", C.c_int),
                 ("op_complexity", C.c_double), ("t_res0_ms", C.c_double), ("n_res0", C.c_int),
                 ("gb_res0", C.c_double), ("t_relax0_ms", C.c_double), ("n_relax0", C.c_int),
-                ("gb_relax0", C.c_double), ("t_setup_phase_ms", C.c_double * 4)]
+                ("gb_relax0", C.c_double), ("t_setup_phase_ms", C.c_double * 4), ("t_relaxc_ms", C.c_double),
+                ("n_relaxc", C.c_int), ("gb_relaxc", C.c_double)]
 
 
 _lib = None
