@@ -239,3 +239,41 @@ def si_hex(prob, tol=1e-8, max_iters=500, inner_tol=1e-10, inner_maxit=200, use_
                          C.byref(sp), C.byref(prm), _p(phi), _p(psi), _p(info))
     return phi, psi, {"rc": rc, "si_iters": int(info[0]), "si_change": info[1],
                       "inner_iters": int(info[2]), "max_inner_resid": info[3]}
+
+
+def csr_transpose(rowptr, col, val):
+    N = len(rowptr) - 1
+    tr = np.zeros(N + 1, np.int32)
+    tc = np.zeros(len(col), np.int32)
+    tv = np.zeros(len(col))
+    rc = lib().or_csr_transpose(C.c_int(N), _p(_i32(rowptr)), _p(_i32(col)), _p(_f64(val)), _p(tr), _p(tc), _p(tv))
+    if rc != OR_OK:
+        raise RuntimeError(f"or_csr_transpose failed: {rc}")
+    return tr, tc, tv
+
+
+def si_adjoint_hex(prob, psi, g, tol=1e-8, max_iters=500, inner_tol=1e-10, inner_maxit=200, use_sweep=False,
+                   params: or_params | None = None):
+    """Adjoint SI and gradients of J = g^T phi w.r.t. sigma_t, sigma_s, q per element.
+    Returns (dJ/dsigma_t, dJ/dsigma_s, dJ/dq, phi_adjoint, info)."""
+    n, M, N, E = prob.n, prob.M, prob.N, prob.E
+    sp = or_si_params(tol, max_iters, inner_tol, inner_maxit, int(use_sweep), 0.0)
+    prm = params or default_params()
+    dst, dss, dq = np.zeros(E), np.zeros(E), np.zeros(E)
+    phis = np.zeros(N)
+    info = np.zeros(2)
+    rc = lib().or_si_adjoint_hex(C.c_int(n), C.c_int(M), _p(_f64(prob.omega)), _p(_f64(prob.w)),
+                                 _p(_f64(prob.sigma_t)), _p(_f64(prob.sigma_s)), _p(_f64(prob.q)),
+                                 _p(_f64(np.ascontiguousarray(psi).reshape(-1))), _p(_f64(g)), C.byref(sp),
+                                 C.byref(prm), _p(dst), _p(dss), _p(dq), _p(phis), _p(info))
+    return dst, dss, dq, phis, {"rc": rc, "iters": int(info[0]), "change": info[1]}
+
+
+def detector_weights(prob, mask):
+    """g with J = g^T phi = integral of phi_h over the elements in mask: g_K = M_K 1."""
+    h = 1.0 / prob.n
+    # row sums of the Q1 mass matrix: h^3 / 8 for every node
+    g = np.zeros(prob.N)
+    for e in np.nonzero(mask)[0]:
+        g[8 * e: 8 * e + 8] = h ** 3 / 8.0
+    return g

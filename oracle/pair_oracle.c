@@ -83,6 +83,24 @@ static int lu_factor(int n, double *a, int *piv, double tiny)
     return 0;
 }
 
+/* Transposed solve with the factors of P A = L U: A^T x = y is
+ * U^T w = y, L^T v = w, x = P^T v (swaps undone in reverse order). */
+static void lu_solve_transpose(int n, const double *a, const int *piv, double *y)
+{
+    for (int k = 0; k < n; ++k) {
+        double s = y[k];
+        for (int r = 0; r < k; ++r) s = s - a[r * n + k] * y[r];
+        y[k] = s / a[k * n + k];
+    }
+    for (int k = n - 1; k >= 0; --k) {
+        double s = y[k];
+        for (int r = k + 1; r < n; ++r) s = s - a[r * n + k] * y[r];
+        y[k] = s;
+    }
+    for (int k = n - 1; k >= 0; --k)
+        if (piv[k] != k) { double t = y[k]; y[k] = y[piv[k]]; y[piv[k]] = t; }
+}
+
 /* Solve with the factors: swaps in order, unit-lower forward substitution by
  * columns, upper back substitution by columns (y_k <- y_k * (1 / u_kk)). */
 static void lu_solve(int n, const double *a, const int *piv, double *y)
@@ -331,6 +349,39 @@ static void odg_rhs(const odg *g, const double *src, const double *ginflow, int 
         }
         if (scaled) lu_solve(nb, g->D + (size_t)e * nb * nb, g->piv + (size_t)e * nb, be);
     }
+}
+
+/* CSR transpose with ascending columns (counting sort by column). */
+static int csr_transpose(int n, const int *rp, const int *ci, const double *v, int **trp, int **tci, double **tv)
+{
+    int nnz = rp[n];
+    int *r = calloc(n + 1, sizeof(int));
+    int *c = malloc(sizeof(int) * (size_t)(nnz > 0 ? nnz : 1));
+    double *x = malloc(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
+    int *fill = calloc(n, sizeof(int));
+    if (!r || !c || !x || !fill) { free(r); free(c); free(x); free(fill); return OR_ERR_OOM; }
+    for (int p = 0; p < nnz; ++p) r[ci[p] + 1]++;
+    for (int i = 0; i < n; ++i) r[i + 1] += r[i];
+    for (int i = 0; i < n; ++i)
+        for (int p = rp[i]; p < rp[i + 1]; ++p) {
+            int j = ci[p], q = r[j] + fill[j]++;
+            c[q] = i; x[q] = v[p];
+        }
+    free(fill);
+    *trp = r; *tci = c; *tv = x;
+    return OR_OK;
+}
+
+int or_csr_transpose(int n, const int *rp, const int *ci, const double *v, int *trp, int *tci, double *tv)
+{
+    int *r, *c; double *x;
+    int rc = csr_transpose(n, rp, ci, v, &r, &c, &x);
+    if (rc) return rc;
+    memcpy(trp, r, sizeof(int) * (size_t)(n + 1));
+    memcpy(tci, c, sizeof(int) * (size_t)rp[n]);
+    memcpy(tv, x, sizeof(double) * (size_t)rp[n]);
+    free(r); free(c); free(x);
+    return OR_OK;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -1060,5 +1111,122 @@ int or_si_hex(int n, int M, const double *omega, const double *w, const double *
 done:
     if (dirs) for (int m = 0; m < M; ++m) odir_free(&dirs[m]);
     free(dirs); free(src); free(b); free(ginfl); free(phinew); free(hist);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Adjoint source iteration and cross-section gradients (not in the paper).  */
+/* Forward: L_m psi_m = M (sigma_s phi + q) / (4 pi), phi = sum_m w_m psi_m,  */
+/* J = g^T phi.  Adjoint: L_m^T c_m = phis, phis = g + sigma_s M sum_m w_m    */
+/* c_m / (4 pi); with A_m = D_m^{-1} L_m this is A_m^T y_m = phis,            */
+/* c_m = D_m^{-T} y_m.  Gradients per element K:                              */
+/*   dJ/dsigma_t,K = - sum_m w_m c_{m,K}^T M_K psi_{m,K}                       */
+/*   dJ/dsigma_s,K =   sum_m w_m c_{m,K}^T M_K phi_K / (4 pi)                  */
+/*   dJ/dq_K       =   sum_m w_m c_{m,K}^T M_K 1 / (4 pi)                      */
+/* psi is the converged forward solution (N*M, direction-major).             */
+/* info[0] = adjoint SI iterations, info[1] = last relative change.          */
+/* ------------------------------------------------------------------------- */
+int or_si_adjoint_hex(int n, int M, const double *omega, const double *w, const double *sigma_t,
+                      const double *sigma_s, const double *q, const double *psi, const double *g,
+                      const or_si_params *sp, const or_params *prm, double *dst, double *dss, double *dq,
+                      double *phis, double *info)
+{
+    int E = n * n * n, N = 8 * E;
+    double fourpi = 4.0 * OR_PI;
+    odir *dirs = calloc(M, sizeof(odir));
+    int **trp = calloc(M, sizeof(int *)), **tci = calloc(M, sizeof(int *));
+    double **tv = calloc(M, sizeof(double *));
+    void **th = calloc(M, sizeof(void *));
+    double *C = malloc(sizeof(double) * (size_t)N * M);   /* c_m = D^{-T} y_m */
+    double *acc = malloc(sizeof(double) * (size_t)N);
+    double *pnew = malloc(sizeof(double) * (size_t)N);
+    double *y = malloc(sizeof(double) * (size_t)N);
+    double *phi = calloc(N, sizeof(double));
+    double *hist = malloc(sizeof(double) * (size_t)(sp->inner_maxit + 1));
+    int rc = OR_OK;
+    if (!dirs || !trp || !tci || !tv || !th || !C || !acc || !pnew || !y || !phi || !hist) { rc = OR_ERR_OOM; goto done; }
+    for (int m = 0; m < M; ++m) {
+        rc = odir_build(&dirs[m], n, omega + 3 * m, sigma_t, prm, 0);
+        if (rc) goto done;
+        rc = csr_transpose(N, dirs[m].rowptr, dirs[m].col, dirs[m].val, &trp[m], &tci[m], &tv[m]);
+        if (rc) goto done;
+        if (!sp->use_sweep) {
+            th[m] = or_air_setup(N, trp[m], tci[m], tv[m], prm, &rc);
+            if (rc) goto done;
+        }
+        for (int i = 0; i < N; ++i) phi[i] = phi[i] + w[m] * psi[(size_t)m * N + i];
+    }
+    for (int i = 0; i < N; ++i) phis[i] = 0.0;
+    info[0] = 0; info[1] = 0;
+    for (int it = 0; it < sp->max_iters; ++it) {
+        for (int i = 0; i < N; ++i) acc[i] = 0.0;
+        for (int m = 0; m < M; ++m) {
+            odg *gd = &dirs[m].g;
+            if (sp->use_sweep) {
+                rc = or_sweep(N, 8, trp[m], tci[m], tv[m], phis, y, NULL);
+                if (rc) goto done;
+            } else {
+                for (int i = 0; i < N; ++i) y[i] = 0.0;
+                int iters = 0;
+                rc = or_air_solve(th[m], phis, y, sp->inner_tol, sp->inner_maxit, &iters, hist);
+                if (rc && rc != OR_ERR_NOT_CONVERGED) goto done;
+                rc = OR_OK;
+            }
+            double *c = C + (size_t)m * N;
+            for (int e = 0; e < E; ++e) {
+                memcpy(c + 8 * e, y + 8 * e, sizeof(double) * 8);
+                lu_solve_transpose(8, gd->D + (size_t)e * 64, gd->piv + (size_t)e * 8, c + 8 * e);
+                const double *Mk = gd->Mass + (size_t)e * 64;
+                for (int a = 0; a < 8; ++a) {
+                    double s = 0.0;
+                    for (int b = 0; b < 8; ++b) s = s + Mk[a * 8 + b] * c[8 * e + b];
+                    acc[8 * e + a] = acc[8 * e + a] + w[m] * s;
+                }
+            }
+        }
+        double dn = 0.0, pn = 0.0;
+        for (int e = 0; e < E; ++e)
+            for (int a = 0; a < 8; ++a) {
+                int i = 8 * e + a;
+                pnew[i] = g[i] + sigma_s[e] * acc[i] / fourpi;
+                double t = pnew[i] - phis[i];
+                dn = dn + t * t;
+                pn = pn + pnew[i] * pnew[i];
+            }
+        memcpy(phis, pnew, sizeof(double) * (size_t)N);
+        info[0] = it + 1;
+        info[1] = pn > 0 ? sqrt(dn) / sqrt(pn) : 0.0;
+        if (info[1] <= sp->tol) break;
+    }
+    /* gradients with the last adjoint solutions */
+    for (int e = 0; e < E; ++e) { dst[e] = 0.0; dss[e] = 0.0; dq[e] = 0.0; }
+    for (int m = 0; m < M; ++m) {
+        const double *c = C + (size_t)m * N;
+        const double *ps = psi + (size_t)m * N;
+        odg *gd = &dirs[m].g;
+        for (int e = 0; e < E; ++e) {
+            const double *Mk = gd->Mass + (size_t)e * 64;
+            double t_psi = 0.0, t_phi = 0.0, t_one = 0.0;
+            for (int a = 0; a < 8; ++a) {
+                double mp = 0.0, mf = 0.0, m1 = 0.0;
+                for (int b = 0; b < 8; ++b) {
+                    mp = mp + Mk[a * 8 + b] * ps[8 * e + b];
+                    mf = mf + Mk[a * 8 + b] * phi[8 * e + b];
+                    m1 = m1 + Mk[a * 8 + b];
+                }
+                t_psi = t_psi + c[8 * e + a] * mp;
+                t_phi = t_phi + c[8 * e + a] * mf;
+                t_one = t_one + c[8 * e + a] * m1;
+            }
+            dst[e] = dst[e] - w[m] * t_psi;
+            dss[e] = dss[e] + w[m] * t_phi / fourpi;
+            dq[e] = dq[e] + w[m] * t_one / fourpi;
+        }
+    }
+    if (info[1] > sp->tol && sp->max_iters > 1) rc = OR_ERR_NOT_CONVERGED;
+done:
+    if (dirs) for (int m = 0; m < M; ++m) odir_free(&dirs[m]);
+    if (trp) for (int m = 0; m < M; ++m) { free(trp[m]); free(tci[m]); free(tv[m]); if (th[m]) or_hier_free(th[m]); }
+    free(dirs); free(trp); free(tci); free(tv); free(th); free(C); free(acc); free(pnew); free(y); free(phi); free(hist);
     return rc;
 }

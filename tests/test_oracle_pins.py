@@ -359,3 +359,58 @@ def test_si_air_equals_si_sweep_and_contracts_like_scattering_ratio():
     # spectral radius of SI is at most sigma_s / sigma_t = 0.5
     it = info_s["si_iters"]
     assert it <= math.ceil(math.log(1e-10) / math.log(0.5)) + 3
+
+
+# ---------------------------------------------------------------------------
+# Adjoint (gradients of a detector response J = g^T phi)
+# ---------------------------------------------------------------------------
+
+def _adjoint_problem():
+    prob = I.hex_random(3, 2, 0.7, seed=5, source_block=(1, 3))
+    ix, iy, iz = I.element_index_grid(prob.n)
+    det = (ix == 0) & (iy == 0) & (iz <= 1)
+    return prob, O.detector_weights(prob, det)
+
+
+def _J(prob, g, **over):
+    import copy
+    p = copy.copy(prob)
+    for k, v in over.items():
+        setattr(p, k, v)
+    phi, psi, info = O.si_hex(p, tol=1e-15, max_iters=400, use_sweep=True)
+    return float(g @ phi), phi, psi
+
+
+def test_adjoint_reproduces_response_and_solvers_agree():
+    """J is linear in q, so sum_K q_K dJ/dq_K must equal J itself; the AIR-based
+    and the sweep-based adjoints must agree."""
+    prob, g = _adjoint_problem()
+    J, phi, psi = _J(prob, g)
+    st_s, ss_s, q_s, phis_s, info_s = O.si_adjoint_hex(prob, psi, g, tol=1e-15, max_iters=400, use_sweep=True)
+    st_a, ss_a, q_a, phis_a, info_a = O.si_adjoint_hex(prob, psi, g, tol=1e-14, max_iters=400, inner_tol=1e-14)
+    assert info_s["rc"] == 0 and info_a["rc"] == 0
+    assert abs(np.dot(prob.q, q_s) - J) <= 1e-12 * abs(J)
+    for a, b in ((st_s, st_a), (ss_s, ss_a), (q_s, q_a)):
+        assert np.abs(a - b).max() <= 1e-10 * np.abs(a).max()
+
+
+def test_adjoint_gradients_match_central_differences():
+    prob, g = _adjoint_problem()
+    J, phi, psi = _J(prob, g)
+    dst, dss, dq, _, info = O.si_adjoint_hex(prob, psi, g, tol=1e-15, max_iters=400, use_sweep=True)
+    rng = np.random.default_rng(2)
+    for name, grad in (("sigma_t", dst), ("sigma_s", dss), ("q", dq)):
+        base = getattr(prob, name)
+        for K in rng.choice(prob.E, 6, replace=False):
+            h = 1e-6 * max(1.0, abs(base[K]))
+            vp, vm = base.copy(), base.copy()
+            vp[K] += h
+            vm[K] -= h
+            if name == "sigma_t":   # keep sigma_s fixed when sigma_t moves
+                fd = (_J(prob, g, sigma_t=vp)[0] - _J(prob, g, sigma_t=vm)[0]) / (2 * h)
+            elif name == "sigma_s":
+                fd = (_J(prob, g, sigma_s=vp)[0] - _J(prob, g, sigma_s=vm)[0]) / (2 * h)
+            else:
+                fd = (_J(prob, g, q=vp)[0] - _J(prob, g, q=vm)[0]) / (2 * h)
+            scale = max(abs(fd), 1e-3 * np.abs(grad).max())
+            assert abs(grad[K] - fd) <= 1e-5 * scale, (name, K, grad[K], fd)
