@@ -131,17 +131,22 @@ __global__ void __launch_bounds__(BS) k_res0_csr(const int *row0, const int *nro
     if (threadIdx.x == 0) partials[(long long)m * maxblk + blockIdx.x] = tot;
 }
 
-// per-matrix norm from the partials in fixed block order (deterministic)
+// per-matrix norm from the partials: a warp per matrix, lane k sums partials
+// k, k+32, ... in order, then a fixed shuffle tree (deterministic)
 __global__ void k_norm_final(int ndir, const double *partials, int maxblk, double *out, const double *bnorm,
                              double tol, int *active) {
-    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    int m = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    int lane = threadIdx.x & 31;
     if (m >= ndir) return;
     if (active && !active[m]) return;
     double s = 0.0;
-    for (int k = 0; k < maxblk; ++k) s += partials[(long long)m * maxblk + k];
-    double nr = sqrt(s);
-    out[m] = nr;
-    if (active && bnorm) active[m] = nr > tol * bnorm[m] ? 1 : 0;
+    for (int k = lane; k < maxblk; k += 32) s += partials[(long long)m * maxblk + k];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+        double nr = sqrt(s);
+        out[m] = nr;
+        if (active && bnorm) active[m] = nr > tol * bnorm[m] ? 1 : 0;
+    }
 }
 
 __global__ void k_sumsq_rows(const int *row0, const int *nrow, const double *v, double *partials, int maxblk) {
@@ -526,7 +531,8 @@ void residual0(Hier &h, const double *b, const double *x, double tol, bool updat
     }
     PR_LAUNCH();
     if (h.prof) rec_event(h.ev[1], s);
-    k_norm_final<<<blocks_for(h.ndir, 128), 128, 0, s>>>(h.ndir, h.partials, h.maxblk, h.rnorm, h.bnorm, tol, act);
+    k_norm_final<<<blocks_for(32LL * h.ndir, 128), 128, 0, s>>>(h.ndir, h.partials, h.maxblk, h.rnorm, h.bnorm, tol,
+                                                                 act);
     PR_LAUNCH();
 }
 
@@ -536,7 +542,8 @@ void norms0(Hier &h, const double *v, double *out) {
     dim3 grid(h.maxblk, h.ndir);
     k_sumsq_rows<<<grid, BS, 0, s>>>(h.d_row00, h.d_n0, v, h.partials, h.maxblk);
     PR_LAUNCH();
-    k_norm_final<<<blocks_for(h.ndir, 128), 128, 0, s>>>(h.ndir, h.partials, h.maxblk, out, nullptr, 0.0, nullptr);
+    k_norm_final<<<blocks_for(32LL * h.ndir, 128), 128, 0, s>>>(h.ndir, h.partials, h.maxblk, out, nullptr, 0.0,
+                                                                 nullptr);
     PR_LAUNCH();
 }
 
