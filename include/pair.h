@@ -233,6 +233,30 @@ PAIR_API pair_status si_solve(const pair_mesh *mesh, const pair_quad *quad, cons
                      const double *q, const air_params *air, const si_params *sp, double *phi, double *psi,
                      void *stream, si_info *info);
 
+/* Adjoint source iteration and cross-section gradients of J = g^T phi, the
+ * discrete adjoint of si_solve's fixed point (the paper has no adjoint; the
+ * forward equations are Eq. sn_transport and Eq. angular_quad):
+ *   A_m^T y_m = phis,  phis <- g + sigma_s (sum_m w_m W_m^T y_m) / (4 pi),
+ *   W_m = D_m^{-1} M (so W_m^T y_m = M D_m^{-T} y_m, M symmetric);
+ *   dJ/dsigma_t,K = -sum_m w_m y_{m,K}^T W_{m,K} psi_{m,K}
+ *   dJ/dsigma_s,K =  sum_m w_m y_{m,K}^T W_{m,K} phi_K / (4 pi)
+ *   dJ/dq_K       =  sum_m w_m y_{m,K}^T W_{m,K} 1 / (4 pi)
+ * Each A_m^T gets its own AIR hierarchy (all directions batched).
+ *   psi            device N*M, the converged forward angular fluxes (si_solve's psi)
+ *   g              device N, dJ/dphi (e.g. detector weights)
+ *   dJ_dsigma_t, dJ_dsigma_s, dJ_dq   device n^3 outputs
+ *   phi_adjoint    device N output (adjoint scalar flux) or NULL
+ * Every direction's hierarchy must fit the memory budget (PAIR_ERR_OOM otherwise). */
+PAIR_API pair_status si_adjoint(const pair_mesh *mesh, const pair_quad *quad, const double *sigma_t,
+                                const double *sigma_s, const double *q, const double *psi, const double *g,
+                                const air_params *air, const si_params *sp, double *dJ_dsigma_t,
+                                double *dJ_dsigma_s, double *dJ_dq, double *phi_adjoint, void *stream,
+                                si_info *info);
+
+/* Transpose of a device CSR matrix into caller-allocated device arrays
+ * (trowptr n+1, tcol and tval nnz), columns ascending in every row. */
+PAIR_API pair_status pair_csr_transpose(const pair_csr *A, int *trowptr, int *tcol, double *tval, void *stream);
+
 PAIR_API const char *pair_last_error(void);
 
 /* ---------------------------------------------------------------------------

@@ -350,4 +350,32 @@ pair_status si_solve(const pair_mesh *mesh, const pair_quad *quad, const double 
     });
 }
 
+pair_status si_adjoint(const pair_mesh *mesh, const pair_quad *quad, const double *sigma_t, const double *sigma_s,
+                       const double *q, const double *psi, const double *g, const air_params *air,
+                       const si_params *sp, double *dJ_dsigma_t, double *dJ_dsigma_s, double *dJ_dq,
+                       double *phi_adjoint, void *stream, si_info *info) {
+    return guarded([&] {
+        PR_REQUIRE(mesh && quad && sigma_t && sigma_s && q && psi && g && sp && dJ_dsigma_t && dJ_dsigma_s &&
+                       dJ_dq && mesh->n >= 1,
+                   PAIR_ERR_ARG, "si_adjoint: null argument or n < 1");
+        PR_REQUIRE(quad->M >= 1 && quad->omega && quad->w, PAIR_ERR_ARG, "si_adjoint: empty quadrature");
+        check_params(air);
+        PR_REQUIRE(sp->tol >= 0 && sp->max_iters >= 1 && sp->inner_tol > 0 && sp->inner_maxit >= 1, PAIR_ERR_ARG,
+                   "si_adjoint: bad si_params");
+        pr::si_adjoint_run(*mesh, *quad, sigma_t, sigma_s, psi, g, *air, *sp, dJ_dsigma_t, dJ_dsigma_s, dJ_dq,
+                           phi_adjoint, (cudaStream_t)stream, info);
+    });
+}
+
+pair_status pair_csr_transpose(const pair_csr *A, int *trowptr, int *tcol, double *tval, void *stream) {
+    return guarded([&] {
+        PR_REQUIRE(A && A->rowptr && trowptr && A->n >= 1 && A->nnz >= 0 &&
+                       (A->nnz == 0 || (A->col && A->val && tcol && tval)),
+                   PAIR_ERR_ARG, "pair_csr_transpose: bad argument");
+        cudaStream_t s = (cudaStream_t)stream;
+        pr::csr_transpose_dev(A->n, A->nnz, A->rowptr, A->col, A->val, trowptr, tcol, tval, s);
+        PR_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
 }  // extern "C"

@@ -173,5 +173,10 @@ BatchSolve solve_batch(Hier &h, const double *b, double *x, double tol, int maxi
 void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t, const double *sigma_s,
             const double *q, const air_params &prm, const si_params &sp, double *phi, double *psi,
             cudaStream_t user, si_info *info);
+void si_adjoint_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t, const double *sigma_s,
+                    const double *psi, const double *g, const air_params &prm, const si_params &sp, double *dst,
+                    double *dss, double *dq, double *phis_out, cudaStream_t user, si_info *info);
+void csr_transpose_dev(int n, long long nnz, const int *rowptr, const int *col, const double *val, int *trp,
+                       int *tcol, double *tval, cudaStream_t s);
 
 }  // namespace pr

@@ -204,6 +204,123 @@ BatchSolve solve_batch(Hier &h, const double *b, double *x, double tol, int maxi
     return out;
 }
 
+namespace {
+
+__global__ void k_col_count(long long nnz, const int *col, int *cnt) {
+    long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < nnz) atomicAdd(&cnt[col[p]], 1);
+}
+
+__global__ void k_transpose_scatter(int n, const int *rowptr, const int *col, const double *val, const int *trp,
+                                    int *fill, int *tcol, double *tval) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+        int j = col[p];
+        int q = trp[j] + atomicAdd(&fill[j], 1);
+        tcol[q] = i;
+        tval[q] = val[p];
+    }
+}
+
+// rows of the transpose sorted by column (the scatter order is arbitrary)
+__global__ void k_sort_rows(int n, const int *rowptr, int *col, double *val) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int s = rowptr[i], e = rowptr[i + 1];
+    for (int a = s + 1; a < e; ++a) {
+        int c = col[a];
+        double v = val[a];
+        int b = a;
+        while (b > s && col[b - 1] > c) { col[b] = col[b - 1]; val[b] = val[b - 1]; --b; }
+        col[b] = c;
+        val[b] = v;
+    }
+}
+
+// right-hand side of every adjoint direction: the adjoint flux itself
+__global__ void k_broadcast(long long N, int nd, const double *v, double *out) {
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < N * nd) out[t] = v[t % N];
+}
+
+// acc += sum_m w_m (W_m^T y_m)  (M c_m with c_m = D_m^{-T} y_m, since M is symmetric)
+__global__ void k_wty_acc(long long E, int nd, const double *W, const double *w, const double *y, double *acc) {
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 8 * E) return;
+    long long e = t >> 3;
+    int a = (int)(t & 7);
+    double s = acc[t];
+    for (int m = 0; m < nd; ++m) {
+        const double *We = W + ((long long)m * E + e) * 64;
+        const double *ye = y + (long long)m * 8 * E + 8 * e;
+        double u = 0.0;
+        for (int b = 0; b < 8; ++b) u += We[b * 8 + a] * ye[b];
+        s += w[m] * u;
+    }
+    acc[t] = s;
+}
+
+// phis_new = g + sigma_s acc / (4 pi)
+__global__ void k_adj_update(long long N, const double *g, const double *sigma_s, const double *acc, double *out) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double inv4pi = 1.0 / (4.0 * 3.14159265358979323846);
+    out[i] = g[i] + sigma_s[i >> 3] * acc[i] * inv4pi;
+}
+
+// per element: dst -= sum_m w_m y^T W psi, dss += sum_m w_m y^T W phi / 4pi, dq += sum_m w_m y^T W 1 / 4pi
+__global__ void k_adj_grad(long long E, int nd, const double *W, const double *w, const double *y, const double *psi,
+                           const double *phi, double *dst, double *dss, double *dq) {
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= E) return;
+    const double inv4pi = 1.0 / (4.0 * 3.14159265358979323846);
+    double gs = dst[e], gss = dss[e], gq = dq[e];
+    for (int m = 0; m < nd; ++m) {
+        const double *We = W + ((long long)m * E + e) * 64;
+        const double *ye = y + (long long)m * 8 * E + 8 * e;
+        const double *pe = psi + (long long)m * 8 * E + 8 * e;
+        const double *fe = phi + 8 * e;
+        double tp = 0.0, tf = 0.0, t1 = 0.0;
+        for (int a = 0; a < 8; ++a) {
+            double mp = 0.0, mf = 0.0, m1 = 0.0;
+            for (int b = 0; b < 8; ++b) {
+                double wab = We[a * 8 + b];
+                mp += wab * pe[b];
+                mf += wab * fe[b];
+                m1 += wab;
+            }
+            tp += ye[a] * mp;
+            tf += ye[a] * mf;
+            t1 += ye[a] * m1;
+        }
+        gs -= w[m] * tp;
+        gss += w[m] * tf * inv4pi;
+        gq += w[m] * t1 * inv4pi;
+    }
+    dst[e] = gs;
+    dss[e] = gss;
+    dq[e] = gq;
+}
+
+}  // namespace
+
+// Transpose of a CSR matrix (rows sorted by column), on stream s.
+void csr_transpose_dev(int n, long long nnz, const int *rowptr, const int *col, const double *val, int *trp,
+                       int *tcol, double *tval, cudaStream_t s) {
+    int *cnt = dmalloc<int>(n, s);
+    PR_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * n, s));
+    k_col_count<<<blocks_for(nnz, BS), BS, 0, s>>>(nnz, col, cnt);
+    PR_LAUNCH();
+    scan_exclusive(cnt, trp, n, s, false);
+    PR_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * n, s));
+    k_transpose_scatter<<<blocks_for(n, BS), BS, 0, s>>>(n, rowptr, col, val, trp, cnt, tcol, tval);
+    PR_LAUNCH();
+    k_sort_rows<<<blocks_for(n, BS), BS, 0, s>>>(n, trp, tcol, tval);
+    PR_LAUNCH();
+    dfree(cnt, s);
+}
+
 Hier::~Hier() {
     if (graph) cudaGraphExecDestroy(graph);
     for (auto &e : ev)
@@ -253,7 +370,7 @@ void free_batch_ops(HexBatch &B) {
 }
 
 void build_batch(HexBatch &B, int n, const double *omega_h, const double *omega_d, const double *sigma_t,
-                 const air_params &prm, bool gin) {
+                 const air_params &prm, bool gin, bool adjoint = false) {
     Hier *h = new Hier;
     B.h = h;
     PR_CUDA(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
@@ -296,12 +413,24 @@ void build_batch(HexBatch &B, int n, const double *omega_h, const double *omega_
     k_iota_dirs<<<blocks_for(nd, 64), 64, 0, s>>>(nd, N, L.d_row0, h->d_n0);
     PR_LAUNCH();
     PR_CUDA(cudaMemcpyAsync(h->d_row00, L.d_row0, sizeof(int) * nd, cudaMemcpyDeviceToDevice, s));
-    h->bsr64 = dmalloc<double>((size_t)nd * E * 96, s);
-    if (prm.precision == 1) h->bsr32 = dmalloc<float>((size_t)nd * E * 96, s);
+    if (!adjoint) {
+        h->bsr64 = dmalloc<double>((size_t)nd * E * 96, s);
+        if (prm.precision == 1) h->bsr32 = dmalloc<float>((size_t)nd * E * 96, s);
+    } else {
+        h->bsr0 = false;
+    }
     B.W = dmalloc<double>((size_t)nd * E * 64, s);
     if (gin) B.Gin = dmalloc<double>((size_t)nd * N, s);
     hex_assemble(n, nd, omega_d + 3 * B.m0, sigma_t, L.rowptr, L.col, L.val, h->bsr64, h->bsr32, B.W, B.Gin,
                  h->d_err, s);
+    if (adjoint) {
+        // A_m^T: rows of the transpose of the (block-diagonal) batch operator
+        int *trp = dmalloc<int>(L.n + 1, s), *tcol = dmalloc<int>(nnz, s);
+        double *tval = dmalloc<double>(nnz, s);
+        csr_transpose_dev(L.n, nnz, L.rowptr, L.col, L.val, trp, tcol, tval, s);
+        dfree(L.rowptr, s); dfree(L.col, s); dfree(L.val, s);
+        L.rowptr = trp; L.col = tcol; L.val = tval;
+    }
     build_hierarchy(*h);
     alloc_cycle_vectors(*h);
     level0_bytes(*h);
@@ -490,6 +619,149 @@ void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t,
         char buf[128];
         snprintf(buf, sizeof buf, "source iteration: %d iterations, change %.3e > %.3e", sp.max_iters, change, sp.tol);
         fail(PAIR_ERR_NOT_CONVERGED, buf);
+    }
+}
+
+void si_adjoint_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t, const double *sigma_s,
+                    const double *psi, const double *g, const air_params &prm, const si_params &sp, double *dst,
+                    double *dss, double *dq, double *phis_out, cudaStream_t user, si_info *info) {
+    int n = mesh.n, M = quad.M;
+    long long E = (long long)n * n * n, N = 8 * E;
+    PR_CUDA(cudaStreamSynchronize(user));
+    size_t per = bytes_per_dir(n, prm.precision, false) + (size_t)N * 16;
+    size_t freeb = 0, totb = 0;
+    PR_CUDA(cudaMemGetInfo(&freeb, &totb));
+    double budget = sp.mem_budget_gb > 0 ? sp.mem_budget_gb * 1e9 : 0.6 * (double)freeb;
+    int B = sp.batch > 0 ? std::min(sp.batch, M) : M;
+    B = std::min<long long>(B, std::max<long long>(1, (long long)(budget / (double)per)));
+    B = (int)std::min<long long>(B, std::max<long long>(1, (0x7fffffffLL / 64) / N));
+    int nb = (M + B - 1) / B;
+    bool resident = (double)per * M <= budget;
+    PR_REQUIRE(resident, PAIR_ERR_OOM, "si_adjoint: all direction hierarchies must fit the memory budget");
+    cudaStream_t s;
+    PR_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    std::vector<HexBatch> batches(nb);
+    struct Cleanup {
+        cudaStream_t s;
+        std::vector<HexBatch> *bs;
+        std::vector<void *> bufs;
+        ~Cleanup() {
+            for (auto &b : *bs) {
+                if (b.h) { dfree(b.b, b.h->stream); dfree(b.xown, b.h->stream); }
+                free_batch_ops(b);
+            }
+            for (void *p : bufs) cudaFreeAsync(p, s);
+            cudaStreamSynchronize(s);
+            cudaStreamDestroy(s);
+        }
+    } cl{s, &batches, {}};
+    auto buf = [&](size_t cnt) { double *p = dmalloc<double>(cnt, s); cl.bufs.push_back(p); return p; };
+    double *omega_d = buf(3 * M), *w_d = buf(M), *phi = buf(N), *phis = buf(N), *pnew = buf(N), *acc = buf(N);
+    int nbk = (int)blocks_for(N, BS);
+    double *part = buf(2 * (size_t)nbk), *dres = buf(2);
+    PR_CUDA(cudaMemcpyAsync(omega_d, quad.omega, sizeof(double) * 3 * M, cudaMemcpyHostToDevice, s));
+    PR_CUDA(cudaMemcpyAsync(w_d, quad.w, sizeof(double) * M, cudaMemcpyHostToDevice, s));
+    PR_CUDA(cudaMemsetAsync(phi, 0, sizeof(double) * N, s));
+    PR_CUDA(cudaMemsetAsync(phis, 0, sizeof(double) * N, s));
+    // forward scalar flux from the given angular fluxes
+    k_phi_acc<<<blocks_for(N, BS), BS, 0, s>>>(N, M, w_d, psi, phi);
+    PR_LAUNCH();
+    PR_CUDA(cudaStreamSynchronize(s));
+    cudaEvent_t e0, e1;
+    PR_CUDA(cudaEventCreate(&e0));
+    PR_CUDA(cudaEventCreate(&e1));
+    double t_setup = 0, t_solve = 0, change = 0, max_inner = 0;
+    int vcycles = 0, it = 0;
+    bool converged = false;
+    for (int b = 0; b < nb; ++b) {
+        HexBatch &Bt = batches[b];
+        Bt.m0 = b * B;
+        Bt.nd = std::min(B, M - b * B);
+        PR_CUDA(cudaEventRecord(e0, s));
+        PR_CUDA(cudaStreamSynchronize(s));
+        build_batch(Bt, n, quad.omega, omega_d, sigma_t, prm, false, true);
+        cudaStream_t hs = Bt.h->stream;
+        Bt.b = dmalloc<double>((size_t)Bt.nd * N, hs);
+        Bt.xown = dmalloc<double>((size_t)Bt.nd * N, hs);
+        PR_CUDA(cudaStreamSynchronize(hs));
+        PR_CUDA(cudaEventRecord(e1, s));
+        PR_CUDA(cudaEventSynchronize(e1));
+        float ms = 0;
+        PR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        t_setup += ms;
+    }
+    for (it = 0; it < sp.max_iters; ++it) {
+        PR_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * N, s));
+        PR_CUDA(cudaStreamSynchronize(s));
+        for (int b = 0; b < nb; ++b) {
+            HexBatch &Bt = batches[b];
+            Hier &h = *Bt.h;
+            cudaStream_t hs = h.stream;
+            PR_CUDA(cudaEventRecord(e0, hs));
+            k_broadcast<<<blocks_for((long long)Bt.nd * N, BS), BS, 0, hs>>>(N, Bt.nd, phis, Bt.b);
+            PR_LAUNCH();
+            PR_CUDA(cudaMemsetAsync(Bt.xown, 0, sizeof(double) * Bt.nd * N, hs));
+            BatchSolve bs = solve_batch(h, Bt.b, Bt.xown, sp.inner_tol, sp.inner_maxit, sp.use_graphs != 0);
+            if (!bs.converged && it > 0) {   // the first right-hand side is zero
+                char buf2[160];
+                snprintf(buf2, sizeof buf2, "adjoint AIR solve reached %d cycles with relative residual %.3e",
+                         bs.iters, bs.max_rel);
+                fail(PAIR_ERR_NOT_CONVERGED, buf2);
+            }
+            vcycles += bs.iters * Bt.nd;
+            max_inner = std::max(max_inner, bs.max_rel);
+            k_wty_acc<<<blocks_for(N, BS), BS, 0, hs>>>(E, Bt.nd, Bt.W, w_d + Bt.m0, Bt.xown, acc);
+            PR_LAUNCH();
+            PR_CUDA(cudaEventRecord(e1, hs));
+            PR_CUDA(cudaEventSynchronize(e1));
+            float ms = 0;
+            PR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            t_solve += ms;
+        }
+        k_adj_update<<<blocks_for(N, BS), BS, 0, s>>>(N, g, sigma_s, acc, pnew);
+        PR_LAUNCH();
+        k_diff_partials<<<nbk, BS, 0, s>>>(N, pnew, phis, part);
+        PR_LAUNCH();
+        k_diff_final<<<1, 1, 0, s>>>(nbk, part, dres);
+        PR_LAUNCH();
+        double hr[2];
+        PR_CUDA(cudaMemcpyAsync(hr, dres, sizeof hr, cudaMemcpyDeviceToHost, s));
+        PR_CUDA(cudaMemcpyAsync(phis, pnew, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+        PR_CUDA(cudaStreamSynchronize(s));
+        change = hr[1] > 0 ? hr[0] / hr[1] : 0.0;
+        if (!std::isfinite(change)) fail(PAIR_ERR_NAN, "NaN/Inf in the adjoint flux");
+        if (change <= sp.tol) { converged = true; ++it; break; }
+    }
+    // gradients from the last adjoint solutions
+    PR_CUDA(cudaMemsetAsync(dst, 0, sizeof(double) * E, s));
+    PR_CUDA(cudaMemsetAsync(dss, 0, sizeof(double) * E, s));
+    PR_CUDA(cudaMemsetAsync(dq, 0, sizeof(double) * E, s));
+    PR_CUDA(cudaStreamSynchronize(s));
+    for (int b = 0; b < nb; ++b) {
+        HexBatch &Bt = batches[b];
+        k_adj_grad<<<blocks_for(E, 128), 128, 0, s>>>(E, Bt.nd, Bt.W, w_d + Bt.m0, Bt.xown, psi + (size_t)Bt.m0 * N,
+                                                      phi, dst, dss, dq);
+        PR_LAUNCH();
+    }
+    if (phis_out) PR_CUDA(cudaMemcpyAsync(phis_out, phis, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+    PR_CUDA(cudaStreamSynchronize(s));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (info) {
+        memset(info, 0, sizeof(*info));
+        info->si_iters = std::min(it, sp.max_iters);
+        info->si_change = change;
+        info->vcycles = vcycles;
+        info->max_inner_resid = max_inner;
+        info->batches = nb;
+        info->t_setup_ms = t_setup;
+        info->t_solve_ms = t_solve;
+    }
+    if (!converged && sp.max_iters > 1) {
+        char buf2[128];
+        snprintf(buf2, sizeof buf2, "adjoint source iteration: %d iterations, change %.3e > %.3e", sp.max_iters,
+                 change, sp.tol);
+        fail(PAIR_ERR_NOT_CONVERGED, buf2);
     }
 }
 

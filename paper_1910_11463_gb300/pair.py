@@ -87,6 +87,9 @@ def lib():
             "pair_last_error": (C.c_char_p, []),
             "pair_kernel_launches": (C.c_longlong, []),
             "pair_residual_norm_noalloc": (i, [C.POINTER(pair_csr), vp, vp, vp, vp, vp]),
+            "pair_csr_transpose": (i, [C.POINTER(pair_csr), vp, vp, vp, vp]),
+            "si_adjoint": (i, [C.POINTER(pair_mesh), C.POINTER(pair_quad), vp, vp, vp, vp, vp, C.POINTER(air_params),
+                               C.POINTER(si_params), vp, vp, vp, vp, vp, C.POINTER(si_info)]),
             "air_setup": (i, [C.POINTER(pair_csr), i, C.POINTER(air_params), vp, C.POINTER(vp)]),
             "air_vcycle": (i, [vp, vp, vp, vp]),
             "air_solve": (i, [vp, vp, vp, d, i, vp, C.POINTER(air_solve_info)]),
@@ -325,3 +328,64 @@ def si_solve(n: int, omega, w, sigma_t, sigma_s, q, air: air_params | None = Non
 def si_solve_problem(prob, **kw):
     """si_solve on an inputs.HexProblem."""
     return si_solve(prob.n, prob.omega, prob.w, prob.sigma_t, prob.sigma_s, prob.q, **kw)
+
+
+def csr_transpose(rowptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor):
+    """Transpose of a device CSR matrix (columns ascending in every row)."""
+    n = rowptr.numel() - 1
+    trp = torch.empty_like(rowptr)
+    tc = torch.empty_like(col)
+    tv = torch.empty_like(val)
+    desc = pair_csr(n, col.numel(), rowptr.data_ptr(), col.data_ptr(), val.data_ptr())
+    _check(lib().pair_csr_transpose(C.byref(desc), _dptr(trp), _dptr(tc), _dptr(tv), _stream()))
+    return trp, tc, tv
+
+
+def si_adjoint(n: int, omega, w, sigma_t, sigma_s, q, psi: torch.Tensor, g: torch.Tensor,
+               air: air_params | None = None, si: si_params | None = None, device="cuda"):
+    """Gradients of J = g^T phi w.r.t. sigma_t, sigma_s and q per element, by
+    adjoint source iteration on the transposed direction operators.
+    psi: converged forward angular fluxes (M, N) on the device.
+    Returns (dJ/dsigma_t, dJ/dsigma_s, dJ/dq, adjoint scalar flux, info)."""
+    air = air or default_air_params()
+    si = si or default_si_params()
+    om = np.ascontiguousarray(omega, dtype=np.float64)
+    ww = np.ascontiguousarray(w, dtype=np.float64)
+    M, E, N = om.shape[0], n ** 3, 8 * n ** 3
+
+    def dev_t(t):
+        return torch.as_tensor(t, dtype=torch.float64).to(device).contiguous()
+
+    st, ss, qq, gg = dev_t(sigma_t), dev_t(sigma_s), dev_t(q), dev_t(g)
+    psi = dev_t(psi).reshape(M, N)
+    dst = torch.empty(E, dtype=torch.float64, device=device)
+    dss = torch.empty_like(dst)
+    dq = torch.empty_like(dst)
+    phis = torch.empty(N, dtype=torch.float64, device=device)
+    info = si_info()
+    quad = pair_quad(M, om.ctypes.data, ww.ctypes.data)
+    _check(lib().si_adjoint(C.byref(pair_mesh(n)), C.byref(quad), _dptr(st), _dptr(ss), _dptr(qq), _dptr(psi),
+                            _dptr(gg), C.byref(air), C.byref(si), _dptr(dst), _dptr(dss), _dptr(dq), _dptr(phis),
+                            _stream(), C.byref(info)))
+    return dst, dss, dq, phis, {f: getattr(info, f) for f, _ in si_info._fields_ if f != "t_setup_phase_ms"}
+
+
+class SIFunction(torch.autograd.Function):
+    """phi = SI(sigma_t, sigma_s, q) on the n^3 hex mesh with a fixed quadrature;
+    backward runs the adjoint source iteration (si_adjoint) with g = dL/dphi."""
+
+    @staticmethod
+    def forward(ctx, sigma_t, sigma_s, q, n, omega, w, air=None, si=None):
+        phi, psi, _ = si_solve(n, omega, w, sigma_t.detach(), sigma_s.detach(), q.detach(), air=air, si=si,
+                               want_psi=True, device=sigma_t.device)
+        ctx.save_for_backward(sigma_t, sigma_s, q, psi)
+        ctx.cfg = (n, omega, w, air, si)
+        return phi
+
+    @staticmethod
+    def backward(ctx, grad_phi):
+        sigma_t, sigma_s, q, psi = ctx.saved_tensors
+        n, omega, w, air, si = ctx.cfg
+        dst, dss, dq, _, _ = si_adjoint(n, omega, w, sigma_t.detach(), sigma_s.detach(), q.detach(), psi,
+                                        grad_phi.detach().contiguous(), air=air, si=si, device=sigma_t.device)
+        return dst, dss, dq, None, None, None, None, None
