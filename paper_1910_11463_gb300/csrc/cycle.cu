@@ -50,10 +50,30 @@ __device__ __forceinline__ V4<double> load4(const double *p) {
 
 // Off-diagonal part of row (m, e, a) of the hex block operator applied to v
 // (v points at direction m's vector).  Returns sum_faces sum_t A v.
+// Level-0 block kernels run on a 3-D grid: x = tiles of 32 elements along a
+// mesh row (8 rows each, 256 threads), y = iy + n iz, z = direction, so the
+// element coordinates come from block indices.
+struct HexRow {
+    int m, e, a, idx[3];
+    bool valid;
+};
+
+__device__ __forceinline__ HexRow hex_row(int n) {
+    HexRow r;
+    r.m = blockIdx.z;
+    int ix = blockIdx.x * 32 + (threadIdx.x >> 3);
+    r.a = threadIdx.x & 7;
+    r.idx[0] = ix;
+    r.idx[1] = blockIdx.y % n;
+    r.idx[2] = blockIdx.y / n;
+    r.valid = ix < n;
+    r.e = ix + n * (int)blockIdx.y;
+    return r;
+}
+
 template <class T, class TV>
-__device__ __forceinline__ T bsr_offdiag(int n, long long E, int m, int e, int a, const int8_t *dsign, const T *vals,
-                                         const TV *v) {
-    int idx[3] = {e % n, (e / n) % n, e / (n * n)};
+__device__ __forceinline__ T bsr_offdiag(int n, long long E, int m, int e, int a, const int *idx, const int8_t *dsign,
+                                         const T *vals, const TV *v) {
     const int stride[3] = {1, n, n * n};
     T acc = T(0);
     const T *base = vals + (((long long)m * E + e) * 3) * 32 + a * 4;
@@ -95,20 +115,19 @@ template <class T>
 __global__ void __launch_bounds__(BS) k_res0_bsr(int n, int N, const int8_t *dsign, const double *bsr64,
                                                  const double *b, const double *x, T *r, double *partials,
                                                  int maxblk, const int *active) {
-    int m = blockIdx.y;
-    if (active && !active[m]) return;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    HexRow q = hex_row(n);
+    if (active && !active[q.m]) return;
     double s2 = 0.0;
     long long E = (long long)N / 8;
-    if (i < N) {
-        long long gi = (long long)m * N + i;
+    if (q.valid) {
+        long long gi = (long long)q.m * N + 8LL * q.e + q.a;
         double acc = b[gi] - x[gi];
-        acc -= bsr_offdiag<double, double>(n, E, m, i >> 3, i & 7, dsign, bsr64, x + (long long)m * N);
+        acc -= bsr_offdiag<double, double>(n, E, q.m, q.e, q.a, q.idx, dsign, bsr64, x + (long long)q.m * N);
         r[gi] = (T)acc;
         s2 = acc * acc;
     }
     double tot = block_sum(s2);
-    if (threadIdx.x == 0) partials[(long long)m * maxblk + blockIdx.x] = tot;
+    if (threadIdx.x == 0) partials[(long long)q.m * maxblk + blockIdx.y * gridDim.x + blockIdx.x] = tot;
 }
 
 template <class T>
@@ -224,15 +243,14 @@ template <class T>
 __global__ void __launch_bounds__(BS) k_relax_bsr(int n, int N, const int8_t *dsign, const T *vals, const int8_t *cf,
                                                   const T *b, const T *in, T *out, int phase, double *x64,
                                                   const int *active) {
-    int m = blockIdx.y;
-    if (active && !active[m]) return;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    long long gi = (long long)m * N + i;
+    HexRow q = hex_row(n);
+    if (active && !active[q.m]) return;
+    if (!q.valid) return;
+    long long gi = (long long)q.m * N + 8LL * q.e + q.a;
     int8_t c = cf[gi];
     T v = in[gi];
     if (c == (phase == 0 ? CF_F : CF_C)) {
-        T acc = bsr_offdiag<T, T>(n, (long long)N / 8, m, i >> 3, i & 7, dsign, vals, in + (long long)m * N);
+        T acc = bsr_offdiag<T, T>(n, (long long)N / 8, q.m, q.e, q.a, q.idx, dsign, vals, in + (long long)q.m * N);
         v = v + (b[gi] - (acc + v));
     }
     if (phase == 1) x64[gi] += (double)v;
@@ -345,7 +363,7 @@ void vcycle_t(Hier &h, double *x64) {
         int cur = 0;
         if (l == 0 && h.bsr0) {
             int N = h.n0[0];
-            dim3 grid(blocks_for(N, BS), h.ndir);
+            dim3 grid(blocks_for(h.hex_n, 32), h.hex_n * h.hex_n, h.ndir);
             const T *vals = std::is_same<T, float>::value ? (const T *)h.bsr32 : (const T *)h.bsr64;
             if (h.prof) { rec_event(h.ev[2], s); h.relax_timed = true; }
             for (int f = 0; f < fs; ++f, cur ^= 1) {
@@ -390,6 +408,7 @@ void alloc_cycle_vectors(Hier &h) {
     }
     int mb = 1;
     for (int d = 0; d < h.ndir; ++d) mb = std::max<int>(mb, (int)blocks_for(h.n0[d], BS));
+    if (h.bsr0) mb = std::max<int>(mb, (int)blocks_for(h.hex_n, 32) * h.hex_n * h.hex_n);
     h.maxblk = mb;
     h.partials = dmalloc<double>((size_t)mb * h.ndir, h.stream);
     h.rnorm = dmalloc<double>(h.ndir, h.stream);
@@ -515,11 +534,12 @@ void residual0(Hier &h, const double *b, const double *x, double tol, bool updat
     bool f32 = h.prm.precision == 1;
     if (h.bsr0) {
         int N = h.n0[0];
+        dim3 g3(blocks_for(h.hex_n, 32), h.hex_n * h.hex_n, h.ndir);
         if (f32)
-            k_res0_bsr<float><<<grid, BS, 0, s>>>(h.hex_n, N, h.dsign, h.bsr64, b, x, (float *)L.vb, h.partials,
+            k_res0_bsr<float><<<g3, BS, 0, s>>>(h.hex_n, N, h.dsign, h.bsr64, b, x, (float *)L.vb, h.partials,
                                                   h.maxblk, act);
         else
-            k_res0_bsr<double><<<grid, BS, 0, s>>>(h.hex_n, N, h.dsign, h.bsr64, b, x, (double *)L.vb, h.partials,
+            k_res0_bsr<double><<<g3, BS, 0, s>>>(h.hex_n, N, h.dsign, h.bsr64, b, x, (double *)L.vb, h.partials,
                                                    h.maxblk, act);
     } else {
         if (f32)
