@@ -277,3 +277,65 @@ def detector_weights(prob, mask):
     for e in np.nonzero(mask)[0]:
         g[8 * e: 8 * e + 8] = h ** 3 / 8.0
     return g
+
+
+# ---------------------------------------------------------------------------
+# Tetrahedra
+# ---------------------------------------------------------------------------
+
+def _tet_args(prob):
+    return (C.c_int(prob.E), _p(_f64(prob.verts)), _p(_i32(prob.tets)), _p(_i32(prob.nbr)))
+
+
+def tet_assemble(prob, omega, sigma_t=None, scaled: bool = True):
+    """CSR of A = D^{-1} L (or L) for one direction on a TetProblem's mesh."""
+    st = _f64(prob.sigma_t if sigma_t is None else sigma_t)
+    om = _f64(omega)
+    nnz = lib().or_tet_nnz(*_tet_args(prob), _p(om), C.c_int(int(scaled)))
+    if nnz < 0:
+        raise RuntimeError(f"or_tet_nnz failed: {nnz}")
+    rowptr = np.zeros(prob.N + 1, np.int32)
+    col = np.zeros(nnz, np.int32)
+    val = np.zeros(nnz)
+    rc = lib().or_tet_assemble(*_tet_args(prob), _p(om), _p(st), C.c_int(int(scaled)), _p(rowptr), _p(col), _p(val))
+    if rc != OR_OK:
+        raise RuntimeError(f"or_tet_assemble failed: {rc}")
+    return rowptr, col, val
+
+
+def tet_rhs(prob, omega, src, ginflow=None, scaled: bool = True, sigma_t=None):
+    b = np.zeros(prob.N)
+    st = _f64(prob.sigma_t if sigma_t is None else sigma_t)
+    g = None if ginflow is None else _f64(ginflow)
+    rc = lib().or_tet_rhs(*_tet_args(prob), _p(_f64(omega)), _p(st), _p(_f64(src)), _p(g), C.c_int(int(scaled)),
+                          _p(b))
+    if rc != OR_OK:
+        raise RuntimeError(f"or_tet_rhs failed: {rc}")
+    return b
+
+
+def sweep_scc(rowptr, col, val, b, nb):
+    """Exact block solve by strongly connected components; returns (x, number of cycles)."""
+    N = len(rowptr) - 1
+    x = np.zeros(N)
+    ncyc = C.c_int(0)
+    rc = lib().or_sweep_scc(C.c_int(N), C.c_int(nb), _p(_i32(rowptr)), _p(_i32(col)), _p(_f64(val)), _p(_f64(b)),
+                            _p(x), None, C.byref(ncyc))
+    if rc != OR_OK:
+        raise RuntimeError(f"or_sweep_scc failed: {rc}")
+    return x, ncyc.value
+
+
+def si_tet(prob, tol=1e-8, max_iters=500, inner_tol=1e-10, inner_maxit=200, use_sweep=False, g_inflow=0.0,
+           params: or_params | None = None):
+    M, N = prob.M, prob.N
+    sp = or_si_params(tol, max_iters, inner_tol, inner_maxit, int(use_sweep), g_inflow)
+    prm = params or default_params()
+    phi = np.zeros(N)
+    psi = np.zeros((M, N))
+    info = np.zeros(4)
+    rc = lib().or_si_tet(*_tet_args(prob), C.c_int(M), _p(_f64(prob.omega)), _p(_f64(prob.w)),
+                         _p(_f64(prob.sigma_t)), _p(_f64(prob.sigma_s)), _p(_f64(prob.q)), C.byref(sp), C.byref(prm),
+                         _p(phi), _p(psi), _p(info))
+    return phi, psi, {"rc": rc, "si_iters": int(info[0]), "si_change": info[1], "inner_iters": int(info[2]),
+                      "max_inner_resid": info[3]}

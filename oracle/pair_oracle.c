@@ -258,6 +258,92 @@ static int hex_build(int n, const double *om, const double *sigma_t, odg *g)
     return odg_factor(g);
 }
 
+/* ---- tetrahedra, P1 (linear) DG --------------------------------------------- */
+/* Local node a = tet vertex a; face f = the triangle without vertex f.
+ * Geometry: e_k = x_k - x_0, c23 = e2 x e3, c31 = e3 x e1, c12 = e1 x e2,
+ * det = e1 . c23, grad l1 = c23/det, grad l2 = c31/det, grad l3 = c12/det,
+ * grad l0 = -((grad l1 + grad l2) + grad l3), |K| = |det| / 6.
+ * od_a = Omega . grad l_a.  Mass (|K|/20)(1 + d_ab); advection (phi_b, Omega.grad phi_a)
+ * = od_a |K| / 4; face f: (Omega.n)|F| = -(od_f (3 |K|)), face mass (1 + d_ab)/12 of it. */
+static void cross3(const double *a, const double *b, double *c)
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+static double dot3(const double *a, const double *b) { return (a[0] * b[0] + a[1] * b[1]) + a[2] * b[2]; }
+
+static int tet_build(int T, const double *verts, const int *tets, const int *nbrs, const double *om,
+                     const double *sigma_t, odg *g)
+{
+    int rc = odg_alloc(g, T, 4, 4, 3);
+    if (rc) return rc;
+    for (int t = 0; t < T; ++t) {
+        const int *tv = tets + 4 * t;
+        double x[4][3], e[3][3], gr[4][3], od[4], c23[3], c31[3], c12[3];
+        for (int a = 0; a < 4; ++a)
+            for (int k = 0; k < 3; ++k) x[a][k] = verts[3 * tv[a] + k];
+        for (int j = 0; j < 3; ++j)
+            for (int k = 0; k < 3; ++k) e[j][k] = x[j + 1][k] - x[0][k];
+        cross3(e[1], e[2], c23);
+        cross3(e[2], e[0], c31);
+        cross3(e[0], e[1], c12);
+        double det = dot3(e[0], c23);
+        if (det == 0.0) { odg_free(g); return OR_ERR_SINGULAR; }
+        for (int k = 0; k < 3; ++k) {
+            gr[1][k] = c23[k] / det;
+            gr[2][k] = c31[k] / det;
+            gr[3][k] = c12[k] / det;
+            gr[0][k] = -((gr[1][k] + gr[2][k]) + gr[3][k]);
+        }
+        double vol = fabs(det) / 6.0;
+        for (int a = 0; a < 4; ++a) od[a] = dot3(om, gr[a]);
+        double fl[4];
+        for (int f = 0; f < 4; ++f) fl[f] = -(od[f] * (3.0 * vol));
+        double st = sigma_t[t];
+        double *Dk = g->D0 + (size_t)t * 16, *Mk = g->Mass + (size_t)t * 16;
+        for (int a = 0; a < 4; ++a)
+            for (int b = 0; b < 4; ++b) {
+                double mass = ((a == b) ? 2.0 : 1.0) * vol / 20.0;
+                double v = st * mass - od[a] * vol / 4.0;
+                for (int f = 0; f < 4; ++f) {
+                    if (!(fl[f] > 0.0) || a == f || b == f) continue;   /* outflow faces holding a and b */
+                    v = v + fl[f] * ((a == b) ? 2.0 : 1.0) / 12.0;
+                }
+                Dk[a * 4 + b] = v;
+                Mk[a * 4 + b] = mass;
+            }
+        for (int f = 0; f < 4; ++f) {
+            if (!(fl[f] < 0.0)) continue;   /* inflow faces only (Omega.n == 0: no flux) */
+            int slot = t * 4 + f, up = nbrs[4 * t + f];
+            if (up >= 0) {
+                g->nbr[slot] = up;
+                const int *uv = tets + 4 * up;
+                int u = 0;
+                for (int b = 0; b < 4; ++b) {
+                    int onface = 0;
+                    for (int a = 0; a < 4; ++a) if (a != f && tv[a] == uv[b]) onface = 1;
+                    if (!onface) continue;
+                    g->fnodes[(size_t)slot * 3 + u] = b;
+                    double *col = g->Bcol + ((size_t)slot * 3 + u) * 4;
+                    for (int a = 0; a < 4; ++a)
+                        col[a] = (a == f) ? 0.0 : fl[f] * ((tv[a] == uv[b]) ? 2.0 : 1.0) / 12.0;
+                    ++u;
+                }
+                if (u != 3) { odg_free(g); return OR_ERR_ARG; }
+            } else {
+                g->bnd[slot] = 1;
+                double *G = g->Gb + (size_t)slot * 16;
+                for (int a = 0; a < 4; ++a)
+                    for (int b = 0; b < 4; ++b)
+                        G[a * 4 + b] = (a == f || b == f) ? 0.0 : -(fl[f] * ((a == b) ? 2.0 : 1.0) / 12.0);
+            }
+        }
+    }
+    return odg_factor(g);
+}
+
 /* Row entries of the scaled operator A = D^{-1} L for element e, or of L itself.
  * Columns ascending: the element blocks are visited in increasing element
  * index (the upwind neighbours and e itself). */
@@ -389,76 +475,113 @@ int or_csr_transpose(int n, const int *rp, const int *ci, const double *v, int *
 /* and is block lower triangular in upwind order, so x_K = b_K - sum A_KK' x_K' */
 /* visiting elements in topological order (Kahn, smallest index first).      */
 /* ------------------------------------------------------------------------- */
-static void heap_push(int *hp, int *hn, int v)
+/* Exact block solve of the scaled system (identity diagonal blocks) by
+ * strongly connected components of the element dependency graph, visited in
+ * dependency order (Tarjan: a component is emitted after every component it
+ * depends on).  A component of one element is x_K = b_K - sum A_KK' x_K'; a
+ * cycle (possible on tetrahedra) is solved as one dense system by LU.
+ * order_out (optional): elements in the visiting order.  Returns the number of
+ * components with more than one element in *ncyc (optional). */
+int or_sweep_scc(int nrows, int nb, const int *rowptr, const int *col, const double *val, const double *b,
+                 double *x, int *order_out, int *ncyc)
 {
-    int i = (*hn)++;
-    hp[i] = v;
-    while (i > 0) { int p = (i - 1) / 2; if (hp[p] <= hp[i]) break; int t = hp[p]; hp[p] = hp[i]; hp[i] = t; i = p; }
-}
-static int heap_pop(int *hp, int *hn)
-{
-    int top = hp[0];
-    hp[0] = hp[--(*hn)];
-    int i = 0;
-    for (;;) {
-        int l = 2 * i + 1, r = l + 1, m = i;
-        if (l < *hn && hp[l] < hp[m]) m = l;
-        if (r < *hn && hp[r] < hp[m]) m = r;
-        if (m == i) break;
-        int t = hp[m]; hp[m] = hp[i]; hp[i] = t; i = m;
+    if (nrows % nb) return OR_ERR_ARG;
+    int E = nrows / nb;
+    /* adjacency e -> elements it references (its upwind elements) */
+    int *cnt = calloc(E + 1, sizeof(int));
+    if (!cnt) return OR_ERR_OOM;
+    for (int e = 0; e < E; ++e)
+        for (int r = e * nb; r < (e + 1) * nb; ++r)
+            for (int p = rowptr[r]; p < rowptr[r + 1]; ++p) if (col[p] / nb != e) cnt[e + 1]++;
+    for (int e = 0; e < E; ++e) cnt[e + 1] += cnt[e];
+    int *adj = malloc(sizeof(int) * (size_t)(cnt[E] > 0 ? cnt[E] : 1));
+    int *fill = calloc(E, sizeof(int));
+    int *idx = malloc(sizeof(int) * (size_t)E), *low = malloc(sizeof(int) * (size_t)E);
+    int *onst = calloc(E, sizeof(int)), *stk = malloc(sizeof(int) * (size_t)E);
+    int *cs = malloc(sizeof(int) * (size_t)E), *ci = malloc(sizeof(int) * (size_t)E);
+    int *comp = malloc(sizeof(int) * (size_t)E);
+    if (!adj || !fill || !idx || !low || !onst || !stk || !cs || !ci || !comp) return OR_ERR_OOM;
+    for (int e = 0; e < E; ++e)
+        for (int r = e * nb; r < (e + 1) * nb; ++r)
+            for (int p = rowptr[r]; p < rowptr[r + 1]; ++p) {
+                int u = col[p] / nb;
+                if (u != e) adj[cnt[e] + fill[e]++] = u;
+            }
+    for (int e = 0; e < E; ++e) idx[e] = -1;
+    int counter = 0, sp = 0, done = 0, cyc = 0, rc = OR_OK;
+    for (int s0 = 0; s0 < E && rc == OR_OK; ++s0) {
+        if (idx[s0] >= 0) continue;
+        int cd = 0;
+        cs[cd] = s0; ci[cd] = cnt[s0]; cd++;
+        idx[s0] = low[s0] = counter++; stk[sp++] = s0; onst[s0] = 1;
+        while (cd > 0 && rc == OR_OK) {
+            int v = cs[cd - 1];
+            if (ci[cd - 1] < cnt[v + 1]) {
+                int u = adj[ci[cd - 1]++];
+                if (idx[u] < 0) {
+                    idx[u] = low[u] = counter++; stk[sp++] = u; onst[u] = 1;
+                    cs[cd] = u; ci[cd] = cnt[u]; cd++;
+                } else if (onst[u] && idx[u] < low[v]) low[v] = idx[u];
+                continue;
+            }
+            --cd;
+            if (cd > 0 && low[v] < low[cs[cd - 1]]) low[cs[cd - 1]] = low[v];
+            if (low[v] != idx[v]) continue;
+            /* pop one component */
+            int k = 0;
+            for (;;) { int u = stk[--sp]; onst[u] = 0; comp[k++] = u; if (u == v) break; }
+            for (int i = 0; i < k; ++i) if (order_out) order_out[done + i] = comp[i];
+            done += k;
+            if (k == 1) {
+                int e = comp[0];
+                for (int r = e * nb; r < (e + 1) * nb; ++r) {
+                    double sacc = b[r];
+                    for (int p = rowptr[r]; p < rowptr[r + 1]; ++p) {
+                        int c = col[p];
+                        if (c / nb == e) continue;
+                        sacc = sacc - val[p] * x[c];
+                    }
+                    x[r] = sacc;
+                }
+                continue;
+            }
+            /* dense solve of the component */
+            ++cyc;
+            int m = k * nb;
+            double *Ad = calloc((size_t)m * m, sizeof(double)), *y = malloc(sizeof(double) * (size_t)m);
+            int *pv = malloc(sizeof(int) * (size_t)m), *pos = malloc(sizeof(int) * (size_t)E);
+            if (!Ad || !y || !pv || !pos) { rc = OR_ERR_OOM; break; }
+            for (int i = 0; i < E; ++i) pos[i] = -1;
+            for (int i = 0; i < k; ++i) pos[comp[i]] = i;
+            for (int i = 0; i < k; ++i)
+                for (int a = 0; a < nb; ++a) {
+                    int r = comp[i] * nb + a, rr = i * nb + a;
+                    double sacc = b[r];
+                    for (int p = rowptr[r]; p < rowptr[r + 1]; ++p) {
+                        int c = col[p], pe = pos[c / nb];
+                        if (pe >= 0) Ad[(size_t)rr * m + pe * nb + c % nb] = val[p];
+                        else sacc = sacc - val[p] * x[c];
+                    }
+                    y[rr] = sacc;
+                }
+            if (lu_factor(m, Ad, pv, 0.0)) rc = OR_ERR_SINGULAR;
+            else {
+                lu_solve(m, Ad, pv, y);
+                for (int i = 0; i < k; ++i)
+                    for (int a = 0; a < nb; ++a) x[comp[i] * nb + a] = y[i * nb + a];
+            }
+            free(Ad); free(y); free(pv); free(pos);
+        }
     }
-    return top;
+    free(cnt); free(adj); free(fill); free(idx); free(low); free(onst); free(stk); free(cs); free(ci); free(comp);
+    if (ncyc) *ncyc = cyc;
+    return rc;
 }
 
 int or_sweep(int nrows, int nb, const int *rowptr, const int *col, const double *val,
              const double *b, double *x, int *order_out)
 {
-    if (nrows % nb) return OR_ERR_ARG;
-    int E = nrows / nb;
-    int *indeg = calloc(E, sizeof(int));
-    int *cnt = calloc(E + 1, sizeof(int));
-    int *heap = malloc(sizeof(int) * (size_t)(E > 0 ? E : 1));
-    if (!indeg || !cnt || !heap) { free(indeg); free(cnt); free(heap); return OR_ERR_OOM; }
-    /* element dependency graph: e depends on every element its rows reference */
-    for (int e = 0; e < E; ++e) {
-        for (int r = e * nb; r < (e + 1) * nb; ++r)
-            for (int p = rowptr[r]; p < rowptr[r + 1]; ++p) {
-                int u = col[p] / nb;
-                if (u != e) cnt[u + 1]++;   /* edge u -> e, counted per entry */
-            }
-    }
-    for (int u = 0; u < E; ++u) cnt[u + 1] += cnt[u];
-    int *adj = malloc(sizeof(int) * (size_t)(cnt[E] > 0 ? cnt[E] : 1));
-    int *fill = calloc(E, sizeof(int));
-    if (!adj || !fill) { free(indeg); free(cnt); free(heap); free(adj); free(fill); return OR_ERR_OOM; }
-    for (int e = 0; e < E; ++e)
-        for (int r = e * nb; r < (e + 1) * nb; ++r)
-            for (int p = rowptr[r]; p < rowptr[r + 1]; ++p) {
-                int u = col[p] / nb;
-                if (u != e) { adj[cnt[u] + fill[u]++] = e; indeg[e]++; }
-            }
-    int hn = 0, done = 0;
-    for (int e = 0; e < E; ++e) if (indeg[e] == 0) heap_push(heap, &hn, e);
-    while (hn > 0) {
-        int e = heap_pop(heap, &hn);
-        if (order_out) order_out[done] = e;
-        ++done;
-        for (int r = e * nb; r < (e + 1) * nb; ++r) {
-            double s = b[r];
-            for (int p = rowptr[r]; p < rowptr[r + 1]; ++p) {
-                int c = col[p];
-                if (c / nb == e) continue;   /* identity diagonal block */
-                s = s - val[p] * x[c];
-            }
-            x[r] = s;
-        }
-        for (int k = cnt[e]; k < cnt[e + 1]; ++k) {
-            int v = adj[k];
-            if (--indeg[v] == 0) heap_push(heap, &hn, v);
-        }
-    }
-    free(indeg); free(cnt); free(heap); free(adj); free(fill);
-    return done == E ? OR_OK : OR_ERR_CYCLE;
+    return or_sweep_scc(nrows, nb, rowptr, col, val, b, x, order_out, NULL);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -496,6 +619,43 @@ int or_hex_rhs(int n, const double *om, const double *sigma_t, const double *src
 {
     odg g;
     int rc = hex_build(n, om, sigma_t, &g);
+    if (rc) return rc;
+    odg_rhs(&g, src, ginflow, scaled, b);
+    odg_free(&g);
+    return OR_OK;
+}
+
+int or_tet_nnz(int T, const double *verts, const int *tets, const int *nbrs, const double *om, int scaled)
+{
+    odg g;
+    double *st = malloc(sizeof(double) * (size_t)T);
+    if (!st) return OR_ERR_OOM;
+    for (int i = 0; i < T; ++i) st[i] = 1.0;
+    int rc = tet_build(T, verts, tets, nbrs, om, st, &g);
+    free(st);
+    if (rc) return rc;
+    int nnz = 0;
+    for (int e = 0; e < T; ++e) nnz += 4 * ((scaled ? 1 : 4) + odg_row_count(&g, e));
+    odg_free(&g);
+    return nnz;
+}
+
+int or_tet_assemble(int T, const double *verts, const int *tets, const int *nbrs, const double *om,
+                    const double *sigma_t, int scaled, int *rowptr, int *col, double *val)
+{
+    odg g;
+    int rc = tet_build(T, verts, tets, nbrs, om, sigma_t, &g);
+    if (rc) return rc;
+    rc = odg_csr(&g, scaled, rowptr, col, val);
+    odg_free(&g);
+    return rc;
+}
+
+int or_tet_rhs(int T, const double *verts, const int *tets, const int *nbrs, const double *om, const double *sigma_t,
+               const double *src, const double *ginflow, int scaled, double *b)
+{
+    odg g;
+    int rc = tet_build(T, verts, tets, nbrs, om, sigma_t, &g);
     if (rc) return rc;
     odg_rhs(&g, src, ginflow, scaled, b);
     odg_free(&g);
@@ -1007,6 +1167,20 @@ typedef struct {
     double g_inflow;    /* isotropic inflow angular flux on the inflow boundary */
 } or_si_params;
 
+/* Mesh descriptor: kind 0 = n^3 hexahedra (Q1), kind 1 = tetrahedra (P1). */
+typedef struct {
+    int kind, n, T;
+    const double *verts;
+    const int *tets, *nbr;
+} or_mesh;
+
+static int mesh_build(const or_mesh *mesh, const double *om, const double *sigma_t, odg *g)
+{
+    if (mesh->kind == 0) return hex_build(mesh->n, om, sigma_t, g);
+    if (mesh->kind == 1) return tet_build(mesh->T, mesh->verts, mesh->tets, mesh->nbr, om, sigma_t, g);
+    return OR_ERR_ARG;
+}
+
 typedef struct {
     odg g;
     int nnz;
@@ -1021,13 +1195,15 @@ static void odir_free(odir *d)
     if (d->hier) or_hier_free(d->hier);
 }
 
-static int odir_build(odir *d, int n, const double *om, const double *sigma_t, const or_params *prm, int with_air)
+static int odir_build(odir *d, const or_mesh *mesh, const double *om, const double *sigma_t, const or_params *prm,
+                      int with_air)
 {
     memset(d, 0, sizeof(*d));
-    int rc = hex_build(n, om, sigma_t, &d->g);
+    int rc = mesh_build(mesh, om, sigma_t, &d->g);
     if (rc) return rc;
     int N = d->g.E * d->g.nb, nnz = 0;
     for (int e = 0; e < d->g.E; ++e) nnz += d->g.nb * (1 + odg_row_count(&d->g, e));
+
     d->nnz = nnz;
     d->rowptr = malloc(sizeof(int) * (size_t)(N + 1));
     d->col = malloc(sizeof(int) * (size_t)nnz);
@@ -1055,11 +1231,12 @@ static void si_source(int E, int nb, const double *sigma_s, const double *q, con
 
 /* info[0] = SI iterations, info[1] = last relative phi change, info[2] = total
  * inner iterations (V-cycles), info[3] = max final relative inner residual. */
-int or_si_hex(int n, int M, const double *omega, const double *w, const double *sigma_t,
-              const double *sigma_s, const double *q, const or_si_params *sp, const or_params *prm,
-              double *phi, double *psi, double *info)
+int or_si(const or_mesh *mesh, int M, const double *omega, const double *w, const double *sigma_t,
+          const double *sigma_s, const double *q, const or_si_params *sp, const or_params *prm,
+          double *phi, double *psi, double *info)
 {
-    int E = n * n * n, N = 8 * E;
+    int nb = mesh->kind == 0 ? 8 : 4;
+    int E = mesh->kind == 0 ? mesh->n * mesh->n * mesh->n : mesh->T, N = nb * E;
     odir *dirs = calloc(M, sizeof(odir));
     double *src = malloc(sizeof(double) * (size_t)N);
     double *b = malloc(sizeof(double) * (size_t)N);
@@ -1070,19 +1247,19 @@ int or_si_hex(int n, int M, const double *omega, const double *w, const double *
     if (!dirs || !src || !b || !ginfl || !phinew || !hist) { rc = OR_ERR_OOM; goto done; }
     for (int i = 0; i < N; ++i) ginfl[i] = sp->g_inflow;
     for (int m = 0; m < M; ++m) {
-        rc = odir_build(&dirs[m], n, omega + 3 * m, sigma_t, prm, !sp->use_sweep);
+        rc = odir_build(&dirs[m], mesh, omega + 3 * m, sigma_t, prm, !sp->use_sweep);
         if (rc) goto done;
     }
     info[0] = 0; info[1] = 0; info[2] = 0; info[3] = 0;
     for (int it = 0; it < sp->max_iters; ++it) {
-        si_source(E, 8, sigma_s, q, phi, src);
+        si_source(E, nb, sigma_s, q, phi, src);
         for (int i = 0; i < N; ++i) phinew[i] = 0.0;
         for (int m = 0; m < M; ++m) {
             odir *d = &dirs[m];
             odg_rhs(&d->g, src, sp->g_inflow != 0.0 ? ginfl : NULL, 1, b);
             double *x = psi + (size_t)m * N;
             if (sp->use_sweep) {
-                rc = or_sweep(N, 8, d->rowptr, d->col, d->val, b, x, NULL);
+                rc = or_sweep(N, nb, d->rowptr, d->col, d->val, b, x, NULL);
                 if (rc) goto done;
             } else {
                 for (int i = 0; i < N; ++i) x[i] = 0.0;
@@ -1112,6 +1289,22 @@ done:
     if (dirs) for (int m = 0; m < M; ++m) odir_free(&dirs[m]);
     free(dirs); free(src); free(b); free(ginfl); free(phinew); free(hist);
     return rc;
+}
+
+int or_si_hex(int n, int M, const double *omega, const double *w, const double *sigma_t,
+              const double *sigma_s, const double *q, const or_si_params *sp, const or_params *prm,
+              double *phi, double *psi, double *info)
+{
+    or_mesh mesh = {0, n, 0, NULL, NULL, NULL};
+    return or_si(&mesh, M, omega, w, sigma_t, sigma_s, q, sp, prm, phi, psi, info);
+}
+
+int or_si_tet(int T, const double *verts, const int *tets, const int *nbr, int M, const double *omega,
+              const double *w, const double *sigma_t, const double *sigma_s, const double *q,
+              const or_si_params *sp, const or_params *prm, double *phi, double *psi, double *info)
+{
+    or_mesh mesh = {1, 0, T, verts, tets, nbr};
+    return or_si(&mesh, M, omega, w, sigma_t, sigma_s, q, sp, prm, phi, psi, info);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -1146,7 +1339,8 @@ int or_si_adjoint_hex(int n, int M, const double *omega, const double *w, const 
     int rc = OR_OK;
     if (!dirs || !trp || !tci || !tv || !th || !C || !acc || !pnew || !y || !phi || !hist) { rc = OR_ERR_OOM; goto done; }
     for (int m = 0; m < M; ++m) {
-        rc = odir_build(&dirs[m], n, omega + 3 * m, sigma_t, prm, 0);
+        or_mesh mesh = {0, n, 0, NULL, NULL, NULL};
+        rc = odir_build(&dirs[m], &mesh, omega + 3 * m, sigma_t, prm, 0);
         if (rc) goto done;
         rc = csr_transpose(N, dirs[m].rowptr, dirs[m].col, dirs[m].val, &trp[m], &tci[m], &tv[m]);
         if (rc) goto done;

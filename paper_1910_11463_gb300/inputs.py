@@ -197,7 +197,112 @@ def config(name: str) -> HexProblem:
         return hex_random(24, 4, 0.7, seed=1, source_block=(8, 16), name=name)
     if name == "hex64_s8":
         return hex_random(64, 8, 0.95, seed=1, lo=0.1, hi=100.0, log_uniform=True, name=name)
+    if name == "tet40_s8":
+        return tet_checkerboard(40, 8, 4, 0.9, 0.2, 1, name)
     raise KeyError(name)
+
+
+# ---------------------------------------------------------------------------
+# Unstructured tetrahedra: Kuhn split of a jittered cube grid
+# ---------------------------------------------------------------------------
+
+# the six permutations of (x, y, z) in lexicographic order
+_KUHN = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
+
+
+@dataclass
+class TetProblem:
+    """Tetrahedral mesh of the unit cube, P1 upwind DG (4 DOFs per tet, DOF = 4 t + a)."""
+    name: str
+    n: int                     # cubes per axis
+    verts: np.ndarray          # (V, 3) coordinates
+    tets: np.ndarray           # (T, 4) vertex ids, local node a = column a
+    nbr: np.ndarray            # (T, 4) tet across the face opposite local vertex f, -1 on the boundary
+    omega: np.ndarray
+    w: np.ndarray
+    sigma_t: np.ndarray        # (T,)
+    sigma_s: np.ndarray
+    q: np.ndarray
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def E(self) -> int:
+        return self.tets.shape[0]
+
+    @property
+    def N(self) -> int:
+        return 4 * self.tets.shape[0]
+
+    @property
+    def M(self) -> int:
+        return self.omega.shape[0]
+
+
+def kuhn_mesh(n: int, jitter: float = 0.2, seed: int = 1):
+    """Vertices of the (n+1)^3 grid (v = vx + (n+1)(vy + (n+1) vz)); interior
+    vertices moved by U[-jitter h, jitter h] per coordinate, three draws per
+    vertex in vertex order (boundary vertices draw but do not move).  Cube
+    c = cx + n (cy + n cz) is split into 6 tets, tet 6c + k = {v000,
+    v000 + e_p0, v000 + e_p0 + e_p1, v111} for the k-th permutation p.
+    Returns (verts, tets, nbr, cube_of_tet)."""
+    h = 1.0 / n
+    n1 = n + 1
+    v = np.arange(n1 ** 3)
+    vx, vy, vz = v % n1, (v // n1) % n1, v // (n1 * n1)
+    verts = np.stack([vx, vy, vz], 1).astype(np.float64) * h
+    if jitter > 0:
+        u = uniform01(seed, 3 * n1 ** 3).reshape(-1, 3)
+        interior = (vx > 0) & (vx < n) & (vy > 0) & (vy < n) & (vz > 0) & (vz < n)
+        verts[interior] += (2.0 * u[interior] - 1.0) * (jitter * h)
+    c = np.arange(n ** 3)
+    cx, cy, cz = c % n, (c // n) % n, c // (n * n)
+    base = np.stack([cx, cy, cz], 1)
+    tets = np.zeros((6 * n ** 3, 4), np.int64)
+    vid = lambda p: p[:, 0] + n1 * (p[:, 1] + n1 * p[:, 2])
+    for k, perm in enumerate(_KUHN):
+        p0 = base.copy()
+        p1 = p0.copy(); p1[:, perm[0]] += 1
+        p2 = p1.copy(); p2[:, perm[1]] += 1
+        p3 = base + 1
+        tets[k::6] = np.stack([vid(p0), vid(p1), vid(p2), vid(p3)], 1)
+    # face neighbours: face f of tet t is the triangle without local vertex f
+    T = tets.shape[0]
+    faces = np.stack([np.delete(tets, f, axis=1) for f in range(4)], 1)   # (T, 4, 3)
+    key = np.sort(faces, axis=2).reshape(-1, 3)
+    order = np.lexsort((key[:, 2], key[:, 1], key[:, 0]))
+    ks = key[order]
+    same = np.all(ks[1:] == ks[:-1], axis=1)
+    nbr = -np.ones(4 * T, np.int64)
+    i = np.nonzero(same)[0]
+    a, b = order[i], order[i + 1]
+    nbr[a] = b // 4
+    nbr[b] = a // 4
+    return verts, tets.astype(np.int32), nbr.reshape(T, 4).astype(np.int32), np.repeat(c, 6)
+
+
+def tet_checkerboard(n: int = 40, order: int = 8, regions: int = 4, ratio: float = 0.9, jitter: float = 0.2,
+                     seed: int = 1, name: str = "tet40_s8") -> TetProblem:
+    """Checkerboard of regions^3 blocks of cubes: sigma_t = 1 where the block
+    parity (rx + ry + rz) is even, 100 where odd; sigma_s = ratio sigma_t; q = 1
+    only where sigma_t = 1."""
+    verts, tets, nbr, cube = kuhn_mesh(n, jitter, seed)
+    omega, w = level_symmetric(order)
+    per = n // regions
+    cx, cy, cz = cube % n, (cube // n) % n, cube // (n * n)
+    odd = ((cx // per + cy // per + cz // per) % 2) == 1
+    st = np.where(odd, 100.0, 1.0)
+    q = np.where(odd, 0.0, 1.0)
+    return TetProblem(name, n, verts, tets, nbr, omega, w, st, st * ratio, q,
+                      {"order": order, "regions": regions, "jitter": jitter, "seed": seed})
+
+
+def small_tet(n: int = 3, order: int = 2, seed: int = 4, ratio: float = 0.5, jitter: float = 0.2) -> TetProblem:
+    verts, tets, nbr, cube = kuhn_mesh(n, jitter, seed)
+    omega, w = level_symmetric(order)
+    u = uniform01(seed + 100, tets.shape[0])
+    st = 0.5 + 1.5 * u
+    return TetProblem(f"tet{n}_s{order}_seed{seed}", n, verts, tets, nbr, omega, w, st, st * ratio,
+                      np.ones(tets.shape[0]), {"order": order, "seed": seed})
 
 
 def small_hex(n: int, order: int = 2, seed: int = 7, ratio: float = 0.5) -> HexProblem:

@@ -414,3 +414,64 @@ def test_adjoint_gradients_match_central_differences():
                 fd = (_J(prob, g, q=vp)[0] - _J(prob, g, q=vm)[0]) / (2 * h)
             scale = max(abs(fd), 1e-3 * np.abs(grad).max())
             assert abs(grad[K] - fd) <= 1e-5 * scale, (name, K, grad[K], fd)
+
+
+# ---------------------------------------------------------------------------
+# Tetrahedra (P1 upwind DG on a jittered Kuhn mesh)
+# ---------------------------------------------------------------------------
+
+def _tet_nodes(prob):
+    return prob.verts[prob.tets.reshape(-1)]
+
+
+@pytest.mark.parametrize("order,dirn", [(2, 0), (4, 11), (8, 37), (8, 66)])
+def test_tet_dg_reproduces_linear_solution(order, dirn):
+    prob = I.small_tet(3, order=order, seed=4)
+    om = prob.omega[dirn]
+    rng = np.random.default_rng(dirn)
+    c0, c = rng.standard_normal(), rng.standard_normal(3)
+    X = _tet_nodes(prob)
+    psi = c0 + X @ c
+    f = np.dot(om, c) + np.repeat(prob.sigma_t, 4) * psi
+    for scaled in (True, False):
+        r, cc, v = O.tet_assemble(prob, om, scaled=scaled)
+        b = O.tet_rhs(prob, om, f, psi, scaled=scaled)
+        sol = spl.spsolve(sp.csr_matrix((v, cc, r), shape=(prob.N, prob.N)).tocsc(), b)
+        assert np.abs(sol - psi).max() < 1e-11
+
+
+def test_tet_sweep_with_cycles_equals_dense_solve():
+    prob = I.small_tet(4, order=8, seed=9)
+    rng = np.random.default_rng(3)
+    cycles = 0
+    for m in range(0, prob.M, 7):
+        om = prob.omega[m]
+        src = rng.random(prob.N)
+        rL, cL, vL = O.tet_assemble(prob, om, scaled=False)
+        ref = np.linalg.solve(csr_dense(rL, cL, vL, prob.N), O.tet_rhs(prob, om, src, scaled=False))
+        r, c, v = O.tet_assemble(prob, om)
+        x, ncyc = O.sweep_scc(r, c, v, O.tet_rhs(prob, om, src), nb=4)
+        cycles += ncyc
+        assert np.abs(x - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_tet_air_distance2_equals_sweep_and_si_fixed_point():
+    prob = I.small_tet(4, order=4, seed=2, ratio=0.6)
+    rng = np.random.default_rng(5)
+    for m in (0, 13):
+        r, c, v = O.tet_assemble(prob, prob.omega[m])
+        b = rng.random(prob.N)
+        H = O.Hierarchy(r, c, v, O.default_params(distance=2))
+        x, hist, rc = H.solve(b, tol=1e-12, maxit=200)
+        assert rc == 0
+        xs, _ = O.sweep_scc(r, c, v, b, nb=4)
+        assert np.linalg.norm(x - xs) <= 1e-10 * np.linalg.norm(xs)
+    # constant inflow q / (4 pi (sigma_t - sigma_s)) with uniform cross sections: phi = q / (sigma_t - sigma_s)
+    import copy
+    pu = copy.copy(prob)
+    pu.sigma_t = np.full(prob.E, 2.0)
+    pu.sigma_s = np.full(prob.E, 1.2)
+    phi, psi, info = O.si_tet(pu, tol=1e-12, inner_tol=1e-12, g_inflow=1.0 / (0.8 * 4 * math.pi),
+                              params=O.default_params(distance=2))
+    assert info["rc"] == 0
+    assert np.abs(phi - 1.0 / 0.8).max() < 1e-9
