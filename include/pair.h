@@ -153,12 +153,22 @@ PAIR_API pair_status air_level_export(pair_hier h, int mat, int level, int *rowp
 PAIR_API void air_free(pair_hier h);
 
 /* ---------------------------------------------------------------------------
- * Upwind DG transport on the unit cube split into n^3 hexahedra, Q1 elements
- * (Eq. weak_form_transport), element e = ix + n (iy + n iz), DOF 8 e + a with
- * local node a = ax + 2 ay + 4 az.  Vacuum boundaries unless g_inflow != 0.
+ * Upwind DG transport (Eq. weak_form_transport) on two mesh kinds:
+ *  PAIR_MESH_HEX: the unit cube split into n^3 hexahedra, Q1 elements, element
+ *    e = ix + n (iy + n iz), DOF 8 e + a, local node a = ax + 2 ay + 4 az;
+ *  PAIR_MESH_TET: tetrahedra, P1 elements, DOF 4 t + a, local node a = vertex
+ *    tets[4t + a]; face f of a tet is the triangle without its vertex f.
+ * Vacuum boundaries unless g_inflow != 0.
  * ------------------------------------------------------------------------- */
+#define PAIR_MESH_HEX 0
+#define PAIR_MESH_TET 1
 typedef struct {
-    int n;              /* elements per axis */
+    int kind;              /* PAIR_MESH_HEX or PAIR_MESH_TET */
+    int n;                 /* hex: elements per axis */
+    int ntet;              /* tet: number of tetrahedra */
+    const double *verts;   /* tet: device, vertex coordinates, 3 per vertex */
+    const int *tets;       /* tet: device, 4 vertex ids per tetrahedron */
+    const int *nbr;        /* tet: device, 4 per tetrahedron: the tet across face f, -1 on the boundary */
 } pair_mesh;
 
 typedef struct {
@@ -180,6 +190,15 @@ PAIR_API pair_status dg_hex_nnz(const pair_mesh *mesh, const double *omega, int 
  *   sigma_t  device, n^3 values. */
 PAIR_API pair_status dg_assemble_hex(const pair_mesh *mesh, const double *omega, const double *sigma_t,
                             int *rowptr, int *col, double *val, void *stream);
+
+/* Tetrahedral counterpart of dg_assemble_hex (P1, block size 4, coupling
+ * blocks 4 x 3).  The row pointer (N + 1 = 4 ntet + 1 entries) is always
+ * written and *nnz receives the entry count; col and val (capacity entries)
+ * are written only when non-NULL and capacity >= *nnz, so a first call with
+ * col = val = NULL sizes the arrays.  Tetrahedra are tested for zero volume
+ * (PAIR_ERR_SINGULAR). */
+PAIR_API pair_status dg_assemble_tet(const pair_mesh *mesh, const double *omega, const double *sigma_t, int *rowptr,
+                                     int *col, double *val, int capacity, int *nnz, void *stream);
 
 /* Source-iteration controls. */
 typedef struct {
@@ -224,8 +243,8 @@ typedef struct {
  * solves every direction m with AIR, A_m psi_m = D_m^{-1} M (sigma_s phi^n + q)/(4 pi),
  * from psi = 0 to inner_tol, then phi^{n+1} = sum_m w_m psi_m (FP64, fixed m
  * order).
- *   sigma_t, sigma_s, q   device, n^3 per-element values
- *   phi      device, N = 8 n^3: in = initial guess, out = result
+ *   sigma_t, sigma_s, q   device, per-element values (n^3 or ntet)
+ *   phi      device, N DOFs (8 n^3 or 4 ntet): in = initial guess, out = result
  *   psi      device N*M (direction-major) or NULL
  *   air      AIR parameters (precision selects FP64 or FP32-refined)
  *   info     host, may be NULL. */
@@ -246,7 +265,8 @@ PAIR_API pair_status si_solve(const pair_mesh *mesh, const pair_quad *quad, cons
  *   g              device N, dJ/dphi (e.g. detector weights)
  *   dJ_dsigma_t, dJ_dsigma_s, dJ_dq   device n^3 outputs
  *   phi_adjoint    device N output (adjoint scalar flux) or NULL
- * Every direction's hierarchy must fit the memory budget (PAIR_ERR_OOM otherwise). */
+ * Every direction's hierarchy must fit the memory budget (PAIR_ERR_OOM otherwise).
+ * Hexahedral meshes only (PAIR_ERR_UNSUPPORTED for tetrahedra). */
 PAIR_API pair_status si_adjoint(const pair_mesh *mesh, const pair_quad *quad, const double *sigma_t,
                                 const double *sigma_s, const double *q, const double *psi, const double *g,
                                 const air_params *air, const si_params *sp, double *dJ_dsigma_t,

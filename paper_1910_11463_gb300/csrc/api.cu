@@ -301,9 +301,46 @@ pair_status air_level_export(pair_hier hh, int mat, int level, int *rowptr, int 
 
 void air_free(pair_hier hh) { delete hh; }
 
+static void check_mesh(const pair_mesh *mesh, const char *who) {
+    PR_REQUIRE(mesh, PAIR_ERR_ARG, std::string(who) + ": null mesh");
+    if (mesh->kind == PAIR_MESH_HEX) {
+        PR_REQUIRE(mesh->n >= 1, PAIR_ERR_ARG, std::string(who) + ": hex mesh needs n >= 1");
+    } else {
+        PR_REQUIRE(mesh->kind == PAIR_MESH_TET && mesh->ntet >= 1 && mesh->verts && mesh->tets && mesh->nbr,
+                   PAIR_ERR_ARG, std::string(who) + ": tet mesh needs ntet >= 1 and verts, tets, nbr");
+    }
+}
+
+pair_status dg_assemble_tet(const pair_mesh *mesh, const double *omega, const double *sigma_t, int *rowptr, int *col,
+                            double *val, int capacity, int *nnz, void *stream) {
+    return guarded([&] {
+        check_mesh(mesh, "dg_assemble_tet");
+        PR_REQUIRE(mesh->kind == PAIR_MESH_TET && omega && sigma_t && rowptr && nnz, PAIR_ERR_ARG,
+                   "dg_assemble_tet: bad argument");
+        cudaStream_t s = (cudaStream_t)stream;
+        double *om = pr::dmalloc<double>(3, s);
+        int *err = pr::dmalloc<int>(1, s);
+        PR_CUDA(cudaMemcpyAsync(om, omega, 3 * sizeof(double), cudaMemcpyHostToDevice, s));
+        PR_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+        long long z = pr::tet_assemble(mesh->ntet, 1, om, mesh->verts, mesh->tets, mesh->nbr, sigma_t, rowptr,
+                                       nullptr, nullptr, nullptr, nullptr, err, s, true);
+        *nnz = (int)z;
+        if (col && val && capacity >= z)
+            pr::tet_assemble(mesh->ntet, 1, om, mesh->verts, mesh->tets, mesh->nbr, sigma_t, rowptr, col, val,
+                             nullptr, nullptr, err, s, false);
+        int herr = 0;
+        PR_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+        PR_CUDA(cudaStreamSynchronize(s));
+        pr::dfree(om, s);
+        pr::dfree(err, s);
+        PR_REQUIRE(herr == 0, PAIR_ERR_SINGULAR, "dg_assemble_tet: degenerate tetrahedron or face mismatch");
+    });
+}
+
 pair_status dg_hex_nnz(const pair_mesh *mesh, const double *omega, int *nnz) {
     return guarded([&] {
-        PR_REQUIRE(mesh && omega && nnz && mesh->n >= 1, PAIR_ERR_ARG, "dg_hex_nnz: bad argument");
+        PR_REQUIRE(mesh && omega && nnz && mesh->kind == PAIR_MESH_HEX && mesh->n >= 1, PAIR_ERR_ARG,
+                   "dg_hex_nnz: bad argument");
         long long v = pr::hex_nnz(mesh->n, omega);
         PR_REQUIRE(v < 0x7fffffffLL, PAIR_ERR_UNSUPPORTED, "dg_hex_nnz: more than 2^31 entries");
         *nnz = (int)v;
@@ -313,8 +350,8 @@ pair_status dg_hex_nnz(const pair_mesh *mesh, const double *omega, int *nnz) {
 pair_status dg_assemble_hex(const pair_mesh *mesh, const double *omega, const double *sigma_t, int *rowptr, int *col,
                             double *val, void *stream) {
     return guarded([&] {
-        PR_REQUIRE(mesh && omega && sigma_t && rowptr && col && val && mesh->n >= 1, PAIR_ERR_ARG,
-                   "dg_assemble_hex: bad argument");
+        PR_REQUIRE(mesh && omega && sigma_t && rowptr && col && val && mesh->kind == PAIR_MESH_HEX && mesh->n >= 1,
+                   PAIR_ERR_ARG, "dg_assemble_hex: bad argument");
         PR_REQUIRE(std::isfinite(omega[0]) && std::isfinite(omega[1]) && std::isfinite(omega[2]), PAIR_ERR_ARG,
                    "dg_assemble_hex: non-finite direction");
         cudaStream_t s = (cudaStream_t)stream;
@@ -336,8 +373,8 @@ pair_status si_solve(const pair_mesh *mesh, const pair_quad *quad, const double 
                      const double *q, const air_params *air, const si_params *sp, double *phi, double *psi,
                      void *stream, si_info *info) {
     return guarded([&] {
-        PR_REQUIRE(mesh && quad && sigma_t && sigma_s && q && sp && phi && mesh->n >= 1, PAIR_ERR_ARG,
-                   "si_solve: null argument or n < 1");
+        PR_REQUIRE(quad && sigma_t && sigma_s && q && sp && phi, PAIR_ERR_ARG, "si_solve: null argument");
+        check_mesh(mesh, "si_solve");
         PR_REQUIRE(quad->M >= 1 && quad->omega && quad->w, PAIR_ERR_ARG, "si_solve: empty quadrature");
         check_params(air);
         PR_REQUIRE(sp->tol >= 0 && sp->max_iters >= 1 && sp->inner_tol > 0 && sp->inner_maxit >= 1, PAIR_ERR_ARG,
@@ -355,9 +392,9 @@ pair_status si_adjoint(const pair_mesh *mesh, const pair_quad *quad, const doubl
                        const si_params *sp, double *dJ_dsigma_t, double *dJ_dsigma_s, double *dJ_dq,
                        double *phi_adjoint, void *stream, si_info *info) {
     return guarded([&] {
-        PR_REQUIRE(mesh && quad && sigma_t && sigma_s && q && psi && g && sp && dJ_dsigma_t && dJ_dsigma_s &&
-                       dJ_dq && mesh->n >= 1,
-                   PAIR_ERR_ARG, "si_adjoint: null argument or n < 1");
+        PR_REQUIRE(quad && sigma_t && sigma_s && q && psi && g && sp && dJ_dsigma_t && dJ_dsigma_s && dJ_dq,
+                   PAIR_ERR_ARG, "si_adjoint: null argument");
+        check_mesh(mesh, "si_adjoint");
         PR_REQUIRE(quad->M >= 1 && quad->omega && quad->w, PAIR_ERR_ARG, "si_adjoint: empty quadrature");
         check_params(air);
         PR_REQUIRE(sp->tol >= 0 && sp->max_iters >= 1 && sp->inner_tol > 0 && sp->inner_maxit >= 1, PAIR_ERR_ARG,

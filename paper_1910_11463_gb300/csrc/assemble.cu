@@ -21,8 +21,8 @@ namespace {
 // LU with partial pivoting (first maximum), multipliers a_rk * (1 / a_kk),
 // updates fma(-l, a_kc, a_rc); column-oriented substitutions with fma and
 // y_k * (1 / u_kk).  The same operation sequence as every LU in the library.
-__device__ __forceinline__ void lu_factor8(double *a, int *piv, double *rinv, int *singular) {
-    const int n = 8;
+template <int n>
+__device__ __forceinline__ void lu_factorN(double *a, int *piv, double *rinv, int *singular) {
     for (int k = 0; k < n; ++k) {
         int p = k;
         long long mx = absbits(a[k * n + k]);
@@ -44,8 +44,8 @@ __device__ __forceinline__ void lu_factor8(double *a, int *piv, double *rinv, in
     }
 }
 
-__device__ __forceinline__ void lu_solve8(const double *a, const int *piv, const double *rinv, double *y) {
-    const int n = 8;
+template <int n>
+__device__ __forceinline__ void lu_solveN(const double *a, const int *piv, const double *rinv, double *y) {
     for (int k = 0; k < n; ++k)
         if (piv[k] != k) { double t = y[k]; y[k] = y[piv[k]]; y[piv[k]] = t; }
     for (int k = 0; k < n; ++k)
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(128) k_hex_assemble(int n, int ndir, const dou
     int piv[8];
     double rinv[8];
     int sing = 0;
-    lu_factor8(D, piv, rinv, &sing);
+    lu_factorN<8>(D, piv, rinv, &sing);
     if (sing) { atomicOr(err, 1); return; }
 
     int idx[3] = {e % n, (e / n) % n, e / (n * n)};
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(128) k_hex_assemble(int n, int ndir, const dou
             if (((b >> d) & 1) != out[d]) continue;
             double *y = Y[d][t];
             for (int a = 0; a < 8; ++a) y[a] = (((a >> d) & 1) != in[d]) ? 0.0 : -(w * face_f(m1, d, a, b));
-            lu_solve8(D, piv, rinv, y);
+            lu_solveN<8>(D, piv, rinv, y);
             ++t;
         }
     }
@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(128) k_hex_assemble(int n, int ndir, const dou
             }
             y[a] = acc;
         }
-        lu_solve8(D, piv, rinv, y);
+        lu_solveN<8>(D, piv, rinv, y);
         for (int a = 0; a < 8; ++a) Gin[((long long)m * E + e) * 8 + a] = y[a];
     }
     if (W) {
@@ -222,8 +222,169 @@ __global__ void __launch_bounds__(128) k_hex_assemble(int n, int ndir, const dou
                 int ax = a & 1, ay = (a >> 1) & 1, az = (a >> 2) & 1;
                 y[a] = (m1[ax][bx] * m1[ay][by]) * m1[az][bz];
             }
-            lu_solve8(D, piv, rinv, y);
+            lu_solveN<8>(D, piv, rinv, y);
             for (int a = 0; a < 8; ++a) We[a * 8 + b] = y[a];
+        }
+    }
+}
+
+
+// ---- tetrahedra, P1 -----------------------------------------------------------
+// Local node a = tet vertex a; face f = the triangle without vertex f.
+// e_k = x_k - x_0; c23 = e2 x e3, c31 = e3 x e1, c12 = e1 x e2; det = e1 . c23;
+// grad l1 = c23 / det, grad l2 = c31 / det, grad l3 = c12 / det,
+// grad l0 = -((grad l1 + grad l2) + grad l3); |K| = |det| / 6; od_a = Omega . grad l_a;
+// face flux (Omega.n)|F| = -(od_f (3 |K|)).
+// L_KK[a][b] = sigma_t (c_ab |K| / 20) - (od_a |K|) / 4 + sum_{outflow f, a,b != f} (fl_f c_ab) / 12
+// L_KK'[a][b'] = (fl_f c) / 12 on the inflow face f (c = 2 on the same vertex, else 1).
+struct TetGeom {
+    double od[4], fl[4], vol;
+};
+
+__device__ __forceinline__ void cross3(const double *a, const double *b, double *c) {
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+__device__ __forceinline__ double dot3(const double *a, const double *b) { return (a[0] * b[0] + a[1] * b[1]) + a[2] * b[2]; }
+
+__device__ __forceinline__ bool tet_geom(const double *verts, const int *tv, const double *om, TetGeom &g) {
+    double x[4][3], e[3][3], gr[4][3], c23[3], c31[3], c12[3];
+    for (int a = 0; a < 4; ++a)
+        for (int k = 0; k < 3; ++k) x[a][k] = verts[3 * tv[a] + k];
+    for (int j = 0; j < 3; ++j)
+        for (int k = 0; k < 3; ++k) e[j][k] = x[j + 1][k] - x[0][k];
+    cross3(e[1], e[2], c23);
+    cross3(e[2], e[0], c31);
+    cross3(e[0], e[1], c12);
+    double det = dot3(e[0], c23);
+    if (det == 0.0) return false;
+    for (int k = 0; k < 3; ++k) {
+        gr[1][k] = c23[k] / det;
+        gr[2][k] = c31[k] / det;
+        gr[3][k] = c12[k] / det;
+        gr[0][k] = -((gr[1][k] + gr[2][k]) + gr[3][k]);
+    }
+    g.vol = fabs(det) / 6.0;
+    for (int a = 0; a < 4; ++a) g.od[a] = dot3(om, gr[a]);
+    for (int f = 0; f < 4; ++f) g.fl[f] = -(g.od[f] * (3.0 * g.vol));
+    return true;
+}
+
+__global__ void k_tet_rowcounts(int T, int ndir, const double *omega, const double *verts, const int *tets,
+                                const int *nbr, int *counts) {
+    long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= (long long)T * ndir) return;
+    int m = (int)(tid / T), t = (int)(tid % T);
+    const double om[3] = {omega[3 * m], omega[3 * m + 1], omega[3 * m + 2]};
+    TetGeom g;
+    int c = 1;
+    if (tet_geom(verts, tets + 4 * t, om, g))
+        for (int f = 0; f < 4; ++f)
+            if (g.fl[f] < 0.0 && nbr[4 * t + f] >= 0) c += 3;
+    long long r0 = ((long long)m * T + t) * 4;
+    for (int a = 0; a < 4; ++a) counts[r0 + a] = c;
+}
+
+__global__ void __launch_bounds__(128) k_tet_assemble(int T, int ndir, const double *omega, const double *verts,
+                                                      const int *tets, const int *nbr, const double *sigma_t,
+                                                      const int *rowptr, int *col, double *val, double *W,
+                                                      double *Gin, int *err) {
+    long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= (long long)T * ndir) return;
+    int m = (int)(tid / T), t = (int)(tid % T);
+    const double om[3] = {omega[3 * m], omega[3 * m + 1], omega[3 * m + 2]};
+    const int *tv = tets + 4 * t;
+    TetGeom g;
+    if (!tet_geom(verts, tv, om, g)) { atomicOr(err, 1); return; }
+    double st = sigma_t[t], vol = g.vol;
+    double D[16];
+    for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) {
+            double mass = ((a == b) ? 2.0 : 1.0) * vol / 20.0;
+            double v = st * mass - g.od[a] * vol / 4.0;
+            for (int f = 0; f < 4; ++f) {
+                if (!(g.fl[f] > 0.0) || a == f || b == f) continue;
+                v = v + g.fl[f] * ((a == b) ? 2.0 : 1.0) / 12.0;
+            }
+            D[a * 4 + b] = v;
+        }
+    int piv[4], sing = 0;
+    double rinv[4];
+    lu_factorN<4>(D, piv, rinv, &sing);
+    if (sing) { atomicOr(err, 1); return; }
+    // inflow faces with an upwind neighbour, sorted by neighbour index with t itself
+    int nb_e[5], nb_f[5], cnt = 0;
+    for (int f = 0; f < 4; ++f)
+        if (g.fl[f] < 0.0 && nbr[4 * t + f] >= 0) { nb_e[cnt] = nbr[4 * t + f]; nb_f[cnt] = f; ++cnt; }
+    nb_e[cnt] = t;
+    nb_f[cnt] = -1;
+    int tot = cnt + 1;
+    for (int i = 1; i < tot; ++i)
+        for (int j = i; j > 0 && nb_e[j - 1] > nb_e[j]; --j) {
+            int x = nb_e[j]; nb_e[j] = nb_e[j - 1]; nb_e[j - 1] = x;
+            x = nb_f[j]; nb_f[j] = nb_f[j - 1]; nb_f[j - 1] = x;
+        }
+    double Y[4][3][4];   // [face][face node][row]
+    int Ynode[4][3];
+    for (int k = 0; k < tot; ++k) {
+        int f = nb_f[k];
+        if (f < 0) continue;
+        const int *uv = tets + 4 * nb_e[k];
+        int u = 0;
+        for (int b = 0; b < 4 && u < 3; ++b) {
+            bool onface = false;
+            for (int a = 0; a < 4; ++a)
+                if (a != f && tv[a] == uv[b]) onface = true;
+            if (!onface) continue;
+            Ynode[f][u] = b;
+            double *y = Y[f][u];
+            for (int a = 0; a < 4; ++a) y[a] = (a == f) ? 0.0 : g.fl[f] * ((tv[a] == uv[b]) ? 2.0 : 1.0) / 12.0;
+            lu_solveN<4>(D, piv, rinv, y);
+            ++u;
+        }
+        if (u != 3) atomicOr(err, 2);
+    }
+    long long N = 4LL * T;
+    long long rowbase = (long long)m * N + 4LL * t;
+    if (col) {
+        for (int a = 0; a < 4; ++a) {
+            long long p = rowptr[rowbase + a];
+            for (int k = 0; k < tot; ++k) {
+                int f = nb_f[k];
+                if (f < 0) { col[p] = (int)(rowbase + a); val[p] = 1.0; ++p; continue; }
+                for (int u = 0; u < 3; ++u) {
+                    col[p] = (int)((long long)m * N + 4LL * nb_e[k] + Ynode[f][u]);
+                    val[p] = Y[f][u][a];
+                    ++p;
+                }
+            }
+        }
+    }
+    if (Gin) {
+        // D^{-1} (boundary inflow faces: sum_b |fl_f| c_ab / 12, unit inflow)
+        double y[4];
+        for (int a = 0; a < 4; ++a) {
+            double acc = 0.0;
+            for (int f = 0; f < 4; ++f) {
+                if (!(g.fl[f] < 0.0) || nbr[4 * t + f] >= 0 || a == f) continue;
+                double s2 = 0.0;
+                for (int b = 0; b < 4; ++b)
+                    if (b != f) s2 = s2 + -(g.fl[f] * ((a == b) ? 2.0 : 1.0) / 12.0);
+                acc = acc + s2;
+            }
+            y[a] = acc;
+        }
+        lu_solveN<4>(D, piv, rinv, y);
+        for (int a = 0; a < 4; ++a) Gin[((long long)m * T + t) * 4 + a] = y[a];
+    }
+    if (W) {
+        double *We = W + ((long long)m * T + t) * 16;
+        for (int b = 0; b < 4; ++b) {
+            double y[4];
+            for (int a = 0; a < 4; ++a) y[a] = ((a == b) ? 2.0 : 1.0) * vol / 20.0;
+            lu_solveN<4>(D, piv, rinv, y);
+            for (int a = 0; a < 4; ++a) We[a * 4 + b] = y[a];
         }
     }
 }
@@ -249,6 +410,25 @@ void hex_assemble(int n, int ndir, const double *omega_d, const double *sigma_t,
     k_hex_assemble<<<blocks_for(E * ndir, 128), 128, 0, s>>>(n, ndir, omega_d, sigma_t, rowptr, col, val, bsr64,
                                                               bsr32, W, Gin, d_err);
     PR_LAUNCH();
+}
+
+// Tetrahedral mesh, 'ndir' directions: CSR (rows/cols offset by m * 4T), W
+// [dir][tet][4][4] = D^{-1} M, Gin [dir][4T].  Computes rowptr; returns nnz.
+long long tet_assemble(int T, int ndir, const double *omega_d, const double *verts, const int *tets, const int *nbr,
+                       const double *sigma_t, int *rowptr, int *col, double *val, double *W, double *Gin, int *d_err,
+                       cudaStream_t s, bool rowptr_only) {
+    long long rows = 4LL * T * ndir;
+    PR_REQUIRE(rows < 0x7fffffffLL, PAIR_ERR_UNSUPPORTED, "tet batch has more than 2^31 rows");
+    int *counts = dmalloc<int>(rows, s);
+    k_tet_rowcounts<<<blocks_for((long long)T * ndir, 256), 256, 0, s>>>(T, ndir, omega_d, verts, tets, nbr, counts);
+    PR_LAUNCH();
+    long long nnz = scan_exclusive(counts, rowptr, (int)rows, s);
+    dfree(counts, s);
+    if (rowptr_only) return nnz;
+    k_tet_assemble<<<blocks_for((long long)T * ndir, 128), 128, 0, s>>>(T, ndir, omega_d, verts, tets, nbr, sigma_t,
+                                                                        rowptr, col, val, W, Gin, d_err);
+    PR_LAUNCH();
+    return nnz;
 }
 
 // Stored entries of the scaled operator of one direction (closed form).

@@ -160,6 +160,9 @@ void prof_enable(Hier &h);
 void hex_assemble(int n, int ndir, const double *omega_d, const double *sigma_t, int *rowptr, int *col,
                   double *val, double *bsr64, float *bsr32, double *W, double *Gin, int *d_err, cudaStream_t s);
 long long hex_nnz(int n, const double *omega_h);
+long long tet_assemble(int T, int ndir, const double *omega_d, const double *verts, const int *tets, const int *nbr,
+                       const double *sigma_t, int *rowptr, int *col, double *val, double *W, double *Gin, int *d_err,
+                       cudaStream_t s, bool rowptr_only);
 
 // si.cu
 struct BatchSolve {

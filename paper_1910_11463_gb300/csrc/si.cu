@@ -19,22 +19,22 @@ namespace {
 
 constexpr int BS = 256;
 
-__global__ void k_rhs(int n, int ndir, const double *W, const double *Gin, double g, const double *sigma_s,
+template <int NB>
+__global__ void k_rhs(long long E, int ndir, const double *W, const double *Gin, double g, const double *sigma_s,
                       const double *q, const double *phi, double *b) {
-    long long E = (long long)n * n * n;
     long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (tid >= 8 * E * ndir) return;
-    long long m = tid / (8 * E);
-    long long r = tid % (8 * E);
-    long long e = r >> 3;
-    int a = (int)(r & 7);
+    if (tid >= NB * E * ndir) return;
+    long long m = tid / (NB * E);
+    long long r = tid % (NB * E);
+    long long e = r / NB;
+    int a = (int)(r % NB);
     const double inv4pi = 1.0 / (4.0 * 3.14159265358979323846);
     double ss = sigma_s[e], qq = q[e];
-    const double *w = W + ((m * E + e) * 8 + a) * 8;
-    const double *ph = phi + 8 * e;
+    const double *w = W + ((m * E + e) * NB + a) * NB;
+    const double *ph = phi + NB * e;
     double acc = 0.0;
 #pragma unroll
-    for (int c = 0; c < 8; ++c) acc += w[c] * ((ss * ph[c] + qq) * inv4pi);
+    for (int c = 0; c < NB; ++c) acc += w[c] * ((ss * ph[c] + qq) * inv4pi);
     if (Gin) acc += g * Gin[tid];
     b[tid] = acc;
 }
@@ -344,11 +344,13 @@ __global__ void k_iota_dirs(int nd, long long N, int *row0, int *n0) {
     if (d < nd) { row0[d] = (int)(d * N); n0[d] = (int)N; }
 }
 
-size_t bytes_per_dir(int n, int precision, bool gin) {
-    size_t E = (size_t)n * n * n, N = 8 * E;
+size_t bytes_per_dir(const pair_mesh &mesh, int precision, bool gin) {
+    bool hex = mesh.kind == PAIR_MESH_HEX;
+    size_t nb = hex ? 8 : 4;
+    size_t E = hex ? (size_t)mesh.n * mesh.n * mesh.n : (size_t)mesh.ntet, N = nb * E;
     double om[3] = {1, 1, 1};
-    size_t nnz0 = (size_t)hex_nnz(n, om);
-    size_t lvl0 = nnz0 * 12 + N * 96 + (precision ? N * 48 : 0) + E * 512 + (gin ? N * 8 : 0);
+    size_t nnz0 = hex ? (size_t)hex_nnz(mesh.n, om) : N * 13;
+    size_t lvl0 = nnz0 * 12 + (hex ? N * 96 + (precision ? N * 48 : 0) : 0) + E * nb * nb * 8 + (gin ? N * 8 : 0);
     size_t coarse = nnz0 * 12 * 3 / 2 + nnz0 * 8;   // coarse operators, Z, setup scratch
     size_t vec = N * (8 * 3 + 4 * 8);
     return lvl0 + coarse + vec;
@@ -369,18 +371,20 @@ void free_batch_ops(HexBatch &B) {
     B.h = nullptr;
 }
 
-void build_batch(HexBatch &B, int n, const double *omega_h, const double *omega_d, const double *sigma_t,
-                 const air_params &prm, bool gin, bool adjoint = false) {
+void build_batch(HexBatch &B, const pair_mesh &mesh, const double *omega_h, const double *omega_d,
+                 const double *sigma_t, const air_params &prm, bool gin, bool adjoint = false) {
+    const int n = mesh.n;
+    const bool hex = mesh.kind == PAIR_MESH_HEX;
     Hier *h = new Hier;
     B.h = h;
     PR_CUDA(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
     cudaStream_t s = h->stream;
     int nd = B.nd;
-    long long E = (long long)n * n * n, N = 8 * E;
+    long long E = hex ? (long long)n * n * n : (long long)mesh.ntet, N = (hex ? 8 : 4) * E;
     h->ndir = nd;
     h->prm = prm;
-    h->bsr0 = true;
-    h->hex_n = n;
+    h->bsr0 = hex;
+    h->hex_n = hex ? n : 0;
     h->n0.assign(nd, (int)N);
     h->d_err = dmalloc<int>(1, s);
     PR_CUDA(cudaMemsetAsync(h->d_err, 0, sizeof(int), s));
@@ -389,16 +393,19 @@ void build_batch(HexBatch &B, int n, const double *omega_h, const double *omega_
     for (int d = 0; d < nd; ++d) {
         const double *om = omega_h + 3 * (B.m0 + d);
         for (int k = 0; k < 3; ++k) sg[3 * d + k] = om[k] > 0 ? 1 : (om[k] < 0 ? -1 : 0);
-        nnz += hex_nnz(n, om);
+        if (hex) nnz += hex_nnz(n, om);
     }
-    PR_REQUIRE(nnz < 0x7fffffffLL, PAIR_ERR_UNSUPPORTED, "direction batch exceeds 2^31 stored entries");
     h->dsign = dmalloc<int8_t>(3 * nd, s);
     PR_CUDA(cudaMemcpyAsync(h->dsign, sg.data(), 3 * nd, cudaMemcpyHostToDevice, s));
     h->lev.resize(1);
     Level &L = h->lev[0];
     L.n = (int)(N * nd);
-    L.nnz = nnz;
     L.rowptr = dmalloc<int>(L.n + 1, s);
+    if (!hex)   // entry count depends on the sign of Omega.n on every face
+        nnz = tet_assemble(mesh.ntet, nd, omega_d + 3 * B.m0, mesh.verts, mesh.tets, mesh.nbr, sigma_t, L.rowptr,
+                           nullptr, nullptr, nullptr, nullptr, h->d_err, s, true);
+    PR_REQUIRE(nnz < 0x7fffffffLL, PAIR_ERR_UNSUPPORTED, "direction batch exceeds 2^31 stored entries");
+    L.nnz = nnz;
     L.col = dmalloc<int>(nnz, s);
     L.val = dmalloc<double>(nnz, s);
     L.rowdir = dmalloc<int>(L.n, s);
@@ -413,16 +420,21 @@ void build_batch(HexBatch &B, int n, const double *omega_h, const double *omega_
     k_iota_dirs<<<blocks_for(nd, 64), 64, 0, s>>>(nd, N, L.d_row0, h->d_n0);
     PR_LAUNCH();
     PR_CUDA(cudaMemcpyAsync(h->d_row00, L.d_row0, sizeof(int) * nd, cudaMemcpyDeviceToDevice, s));
-    if (!adjoint) {
+    if (hex && !adjoint) {
         h->bsr64 = dmalloc<double>((size_t)nd * E * 96, s);
         if (prm.precision == 1) h->bsr32 = dmalloc<float>((size_t)nd * E * 96, s);
     } else {
         h->bsr0 = false;
     }
-    B.W = dmalloc<double>((size_t)nd * E * 64, s);
+    const int nb = hex ? 8 : 4;
+    B.W = dmalloc<double>((size_t)nd * E * nb * nb, s);
     if (gin) B.Gin = dmalloc<double>((size_t)nd * N, s);
-    hex_assemble(n, nd, omega_d + 3 * B.m0, sigma_t, L.rowptr, L.col, L.val, h->bsr64, h->bsr32, B.W, B.Gin,
-                 h->d_err, s);
+    if (hex)
+        hex_assemble(n, nd, omega_d + 3 * B.m0, sigma_t, L.rowptr, L.col, L.val, h->bsr64, h->bsr32, B.W, B.Gin,
+                     h->d_err, s);
+    else
+        tet_assemble(mesh.ntet, nd, omega_d + 3 * B.m0, mesh.verts, mesh.tets, mesh.nbr, sigma_t, L.rowptr, L.col,
+                     L.val, B.W, B.Gin, h->d_err, s, false);
     if (adjoint) {
         // A_m^T: rows of the transpose of the (block-diagonal) batch operator
         int *trp = dmalloc<int>(L.n + 1, s), *tcol = dmalloc<int>(nnz, s);
@@ -443,11 +455,13 @@ void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t,
             const double *q, const air_params &prm, const si_params &sp, double *phi, double *psi,
             cudaStream_t user, si_info *info) {
     int n = mesh.n, M = quad.M;
-    long long E = (long long)n * n * n, N = 8 * E;
+    const bool hex = mesh.kind == PAIR_MESH_HEX;
+    const int nbk0 = hex ? 8 : 4;
+    long long E = hex ? (long long)n * n * n : (long long)mesh.ntet, N = nbk0 * E;
     PR_CUDA(cudaStreamSynchronize(user));
     bool gin = sp.g_inflow != 0.0;
     // direction batches admitted by memory
-    size_t per = bytes_per_dir(n, prm.precision, gin);
+    size_t per = bytes_per_dir(mesh, prm.precision, gin);
     size_t freeb = 0, totb = 0;
     PR_CUDA(cudaMemGetInfo(&freeb, &totb));
     double budget = sp.mem_budget_gb > 0 ? sp.mem_budget_gb * 1e9 : 0.6 * (double)freeb;
@@ -528,7 +542,7 @@ void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t,
                 PR_CUDA(cudaStreamCreateWithFlags(&tmp, cudaStreamNonBlocking));
                 PR_CUDA(cudaEventRecord(e0, tmp));
                 PR_CUDA(cudaStreamSynchronize(tmp));
-                build_batch(Bt, n, quad.omega, omega_d, sigma_t, prm, gin);
+                build_batch(Bt, mesh, quad.omega, omega_d, sigma_t, prm, gin);
                 PR_CUDA(cudaStreamSynchronize(Bt.h->stream));
                 PR_CUDA(cudaEventRecord(e1, tmp));
                 PR_CUDA(cudaEventSynchronize(e1));
@@ -555,8 +569,12 @@ void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t,
             cudaStream_t hs = h.stream;
             double *x = psi ? psi + (size_t)Bt.m0 * N : Bt.xown;
             PR_CUDA(cudaEventRecord(e0, hs));
-            k_rhs<<<blocks_for((long long)Bt.nd * N, BS), BS, 0, hs>>>(n, Bt.nd, Bt.W, Bt.Gin, sp.g_inflow, sigma_s, q,
-                                                                      phi, Bt.b);
+            if (hex)
+                k_rhs<8><<<blocks_for((long long)Bt.nd * N, BS), BS, 0, hs>>>(E, Bt.nd, Bt.W, Bt.Gin, sp.g_inflow,
+                                                                           sigma_s, q, phi, Bt.b);
+            else
+                k_rhs<4><<<blocks_for((long long)Bt.nd * N, BS), BS, 0, hs>>>(E, Bt.nd, Bt.W, Bt.Gin, sp.g_inflow,
+                                                                           sigma_s, q, phi, Bt.b);
             PR_LAUNCH();
             PR_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * Bt.nd * N, hs));
             BatchSolve bs = solve_batch(h, Bt.b, x, sp.inner_tol, sp.inner_maxit, sp.use_graphs != 0);
@@ -625,10 +643,11 @@ void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t,
 void si_adjoint_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t, const double *sigma_s,
                     const double *psi, const double *g, const air_params &prm, const si_params &sp, double *dst,
                     double *dss, double *dq, double *phis_out, cudaStream_t user, si_info *info) {
+    PR_REQUIRE(mesh.kind == PAIR_MESH_HEX, PAIR_ERR_UNSUPPORTED, "si_adjoint: hexahedral meshes only");
     int n = mesh.n, M = quad.M;
     long long E = (long long)n * n * n, N = 8 * E;
     PR_CUDA(cudaStreamSynchronize(user));
-    size_t per = bytes_per_dir(n, prm.precision, false) + (size_t)N * 16;
+    size_t per = bytes_per_dir(mesh, prm.precision, false) + (size_t)N * 16;
     size_t freeb = 0, totb = 0;
     PR_CUDA(cudaMemGetInfo(&freeb, &totb));
     double budget = sp.mem_budget_gb > 0 ? sp.mem_budget_gb * 1e9 : 0.6 * (double)freeb;
@@ -679,7 +698,7 @@ void si_adjoint_run(const pair_mesh &mesh, const pair_quad &quad, const double *
         Bt.nd = std::min(B, M - b * B);
         PR_CUDA(cudaEventRecord(e0, s));
         PR_CUDA(cudaStreamSynchronize(s));
-        build_batch(Bt, n, quad.omega, omega_d, sigma_t, prm, false, true);
+        build_batch(Bt, mesh, quad.omega, omega_d, sigma_t, prm, false, true);
         cudaStream_t hs = Bt.h->stream;
         Bt.b = dmalloc<double>((size_t)Bt.nd * N, hs);
         Bt.xown = dmalloc<double>((size_t)Bt.nd * N, hs);

@@ -46,8 +46,43 @@ class air_solve_info(C.Structure):
     _fields_ = [("iters", C.c_int), ("rel_resid", C.c_double), ("rho", C.c_double)]
 
 
+PAIR_MESH_HEX, PAIR_MESH_TET = 0, 1
+
+
 class pair_mesh(C.Structure):
-    _fields_ = [("n", C.c_int)]
+    _fields_ = [("kind", C.c_int), ("n", C.c_int), ("ntet", C.c_int), ("verts", C.c_void_p), ("tets", C.c_void_p),
+                ("nbr", C.c_void_p)]
+
+
+def hex_mesh(n: int) -> pair_mesh:
+    return pair_mesh(PAIR_MESH_HEX, n, 0, None, None, None)
+
+
+class TetMesh:
+    """Device copy of a tetrahedral mesh (vertex coordinates, tets, face neighbours)."""
+
+    def __init__(self, verts, tets, nbr, device="cuda"):
+        self.verts = torch.as_tensor(np.ascontiguousarray(verts, np.float64), device=device).contiguous()
+        self.tets = torch.as_tensor(np.ascontiguousarray(tets, np.int32), device=device).contiguous()
+        self.nbr = torch.as_tensor(np.ascontiguousarray(nbr, np.int32), device=device).contiguous()
+        self.ntet = self.tets.shape[0]
+        self.struct = pair_mesh(PAIR_MESH_TET, 0, self.ntet, self.verts.data_ptr(), self.tets.data_ptr(),
+                                self.nbr.data_ptr())
+
+    @property
+    def E(self) -> int:
+        return self.ntet
+
+    @property
+    def N(self) -> int:
+        return 4 * self.ntet
+
+
+def _mesh_struct(mesh):
+    if isinstance(mesh, TetMesh):
+        return mesh.struct, mesh.ntet, 4 * mesh.ntet
+    n = int(mesh)
+    return hex_mesh(n), n ** 3, 8 * n ** 3
 
 
 class pair_quad(C.Structure):
@@ -99,6 +134,7 @@ def lib():
             "air_free": (None, [vp]),
             "dg_hex_nnz": (i, [C.POINTER(pair_mesh), vp, C.POINTER(i)]),
             "dg_assemble_hex": (i, [C.POINTER(pair_mesh), vp, vp, vp, vp, vp, vp]),
+            "dg_assemble_tet": (i, [C.POINTER(pair_mesh), vp, vp, vp, vp, vp, i, C.POINTER(i), vp]),
             "si_solve": (i, [C.POINTER(pair_mesh), C.POINTER(pair_quad), vp, vp, vp, C.POINTER(air_params),
                              C.POINTER(si_params), vp, vp, vp, C.POINTER(si_info)]),
         }
@@ -277,7 +313,7 @@ def residual_norm_noalloc(rowptr: torch.Tensor, col: torch.Tensor, val: torch.Te
 def dg_hex_nnz(n: int, omega) -> int:
     om = np.ascontiguousarray(omega, dtype=np.float64)
     v = C.c_int()
-    _check(lib().dg_hex_nnz(C.byref(pair_mesh(n)), _np_ptr(om), C.byref(v)))
+    _check(lib().dg_hex_nnz(C.byref(hex_mesh(n)), _np_ptr(om), C.byref(v)))
     return v.value
 
 
@@ -291,22 +327,37 @@ def dg_assemble_hex(n: int, omega, sigma_t: torch.Tensor):
     col = torch.empty(nnz, dtype=torch.int32, device=dev)
     val = torch.empty(nnz, dtype=torch.float64, device=dev)
     st = sigma_t.to(torch.float64).contiguous()
-    _check(lib().dg_assemble_hex(C.byref(pair_mesh(n)), _np_ptr(om), _dptr(st), _dptr(rowptr), _dptr(col),
+    _check(lib().dg_assemble_hex(C.byref(hex_mesh(n)), _np_ptr(om), _dptr(st), _dptr(rowptr), _dptr(col),
                                  _dptr(val), _stream()))
     return rowptr, col, val
 
 
-def si_solve(n: int, omega, w, sigma_t, sigma_s, q, air: air_params | None = None, si: si_params | None = None,
+def dg_assemble_tet(mesh: "TetMesh", omega, sigma_t: torch.Tensor):
+    """Block-scaled upwind P1 DG operator of one direction on a tetrahedral mesh."""
+    om = np.ascontiguousarray(omega, dtype=np.float64)
+    st = sigma_t.to(torch.float64).contiguous()
+    rowptr = torch.empty(mesh.N + 1, dtype=torch.int32, device=st.device)
+    nnz = C.c_int()
+    _check(lib().dg_assemble_tet(C.byref(mesh.struct), _np_ptr(om), _dptr(st), _dptr(rowptr), None, None, 0,
+                                 C.byref(nnz), _stream()))
+    col = torch.empty(nnz.value, dtype=torch.int32, device=st.device)
+    val = torch.empty(nnz.value, dtype=torch.float64, device=st.device)
+    _check(lib().dg_assemble_tet(C.byref(mesh.struct), _np_ptr(om), _dptr(st), _dptr(rowptr), _dptr(col), _dptr(val),
+                                 nnz.value, C.byref(nnz), _stream()))
+    return rowptr, col, val
+
+
+def si_solve(n, omega, w, sigma_t, sigma_s, q, air: air_params | None = None, si: si_params | None = None,
              phi0=None, want_psi: bool = False, device="cuda"):
-    """Source iteration on the n^3 hex mesh.  Cross sections may be CPU or CUDA
-    tensors (CPU inputs are copied to the device and phi is returned on the
-    device).  Returns (phi, psi or None, info dict)."""
+    """Source iteration on the n^3 hex mesh (n an int) or on a TetMesh.  Cross
+    sections may be CPU or CUDA tensors (CPU inputs are copied to the device and
+    phi is returned on the device).  Returns (phi, psi or None, info dict)."""
     air = air or default_air_params()
     si = si or default_si_params()
     om = np.ascontiguousarray(omega, dtype=np.float64)
     ww = np.ascontiguousarray(w, dtype=np.float64)
     M = om.shape[0]
-    N = 8 * n ** 3
+    mstruct, _, N = _mesh_struct(n)
 
     def dev_t(t):
         t = torch.as_tensor(t, dtype=torch.float64)
@@ -317,7 +368,7 @@ def si_solve(n: int, omega, w, sigma_t, sigma_s, q, air: air_params | None = Non
     psi = torch.empty((M, N), dtype=torch.float64, device=device) if want_psi else None
     info = si_info()
     quad = pair_quad(M, om.ctypes.data, ww.ctypes.data)
-    rc = lib().si_solve(C.byref(pair_mesh(n)), C.byref(quad), _dptr(st), _dptr(ss), _dptr(qq), C.byref(air),
+    rc = lib().si_solve(C.byref(mstruct), C.byref(quad), _dptr(st), _dptr(ss), _dptr(qq), C.byref(air),
                         C.byref(si), _dptr(phi), _dptr(psi) if psi is not None else None, _stream(), C.byref(info))
     _check(rc)
     out = {f: getattr(info, f) for f, _ in si_info._fields_}
@@ -325,8 +376,11 @@ def si_solve(n: int, omega, w, sigma_t, sigma_s, q, air: air_params | None = Non
     return phi, psi, out
 
 
-def si_solve_problem(prob, **kw):
-    """si_solve on an inputs.HexProblem."""
+def si_solve_problem(prob, mesh=None, **kw):
+    """si_solve on an inputs.HexProblem or inputs.TetProblem (mesh: a TetMesh to reuse)."""
+    if hasattr(prob, "tets"):
+        mesh = mesh or TetMesh(prob.verts, prob.tets, prob.nbr)
+        return si_solve(mesh, prob.omega, prob.w, prob.sigma_t, prob.sigma_s, prob.q, **kw)
     return si_solve(prob.n, prob.omega, prob.w, prob.sigma_t, prob.sigma_s, prob.q, **kw)
 
 
@@ -364,7 +418,7 @@ def si_adjoint(n: int, omega, w, sigma_t, sigma_s, q, psi: torch.Tensor, g: torc
     phis = torch.empty(N, dtype=torch.float64, device=device)
     info = si_info()
     quad = pair_quad(M, om.ctypes.data, ww.ctypes.data)
-    _check(lib().si_adjoint(C.byref(pair_mesh(n)), C.byref(quad), _dptr(st), _dptr(ss), _dptr(qq), _dptr(psi),
+    _check(lib().si_adjoint(C.byref(hex_mesh(n)), C.byref(quad), _dptr(st), _dptr(ss), _dptr(qq), _dptr(psi),
                             _dptr(gg), C.byref(air), C.byref(si), _dptr(dst), _dptr(dss), _dptr(dq), _dptr(phis),
                             _stream(), C.byref(info)))
     return dst, dss, dq, phis, {f: getattr(info, f) for f, _ in si_info._fields_ if f != "t_setup_phase_ms"}
