@@ -95,6 +95,23 @@ __device__ __forceinline__ T bsr_offdiag(int n, long long E, int m, int e, int a
     return acc;
 }
 
+// Block sum of per-thread FP32 squares: FP32 inside each warp, one conversion
+// per warp, FP64 across warps (fixed order).
+__device__ __forceinline__ double block_sum_f(float v) {
+    __shared__ double shf[32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) shf[w] = (double)v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0) {
+        int nw = (blockDim.x + 31) >> 5;
+        for (int k = 0; k < nw; ++k) s += shf[k];
+    }
+    __syncthreads();
+    return s;
+}
+
 __device__ __forceinline__ double block_sum(double v) {
     __shared__ double sh[32];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -117,16 +134,22 @@ __global__ void __launch_bounds__(BS) k_res0_bsr(int n, int N, const int8_t *dsi
                                                  int maxblk, const int *active) {
     HexRow q = hex_row(n);
     if (active && !active[q.m]) return;
+    constexpr bool F32 = std::is_same<T, float>::value;
     double s2 = 0.0;
+    float s2f = 0.0f;
     long long E = (long long)N / 8;
     if (q.valid) {
         long long gi = (long long)q.m * N + 8LL * q.e + q.a;
         double acc = b[gi] - x[gi];
         acc -= bsr_offdiag<double, double>(n, E, q.m, q.e, q.a, q.idx, dsign, bsr64, x + (long long)q.m * N);
-        r[gi] = (T)acc;
-        s2 = acc * acc;
+        T rt = (T)acc;
+        r[gi] = rt;
+        // the stopping test needs ||r|| to a few digits: with an FP32 cycle the
+        // square of the cast value is summed in FP32 inside each warp
+        if (F32) s2f = (float)rt * (float)rt;
+        else s2 = acc * acc;
     }
-    double tot = block_sum(s2);
+    double tot = F32 ? block_sum_f(s2f) : block_sum(s2);
     if (threadIdx.x == 0) partials[(long long)q.m * maxblk + blockIdx.y * gridDim.x + blockIdx.x] = tot;
 }
 
@@ -210,7 +233,10 @@ __global__ void k_prolong(int n, const int8_t *cf, const int *pmap, const T *xc,
 // phase 0 (F): xn = y + dinv (b - A y) on F rows, xn = y on C rows
 // phase 1 (C): out = xn + dinv (b - A xn) on C rows, out = xn on F rows;
 //              level 0 (x64 != null): x64 += out, coarsest rows x64 += xco
-template <class T, int G>
+// FINAL: the last sweep on level 0, which adds the correction into the FP64
+// iterate; every other instance is FP64-free (on this GPU even an unused FP64
+// conversion occupies the narrow FP64 pipe).
+template <class T, int G, bool FINAL>
 __global__ void __launch_bounds__(BS) k_relax_csr(int n, const int *rowptr, const int *col, const T *val,
                                                   const T *dinv, const int8_t *cf, const T *b, const T *in, T *out,
                                                   int phase, double *x64, const T *xco, const int *active,
@@ -230,16 +256,16 @@ __global__ void __launch_bounds__(BS) k_relax_csr(int n, const int *rowptr, cons
     if (!valid || g != 0) return;
     T v;
     if (c == CF_COARSEST) {
-        if (x64 && phase == 1) x64[i] += (double)xco[i];
+        if (FINAL) x64[i] += (double)xco[i];
         return;
     }
     v = work ? in[i] + dinv[i] * (b[i] - acc) : in[i];
-    if (phase == 1 && x64) x64[i] += (double)v;
+    if (FINAL) x64[i] += (double)v;
     else out[i] = v;
 }
 
 // ---- BSR (hex level 0) relaxation, unit diagonal ------------------------------
-template <class T>
+template <class T, bool FINAL>
 __global__ void __launch_bounds__(BS) k_relax_bsr(int n, int N, const int8_t *dsign, const T *vals, const int8_t *cf,
                                                   const T *b, const T *in, T *out, int phase, double *x64,
                                                   const int *active) {
@@ -253,7 +279,7 @@ __global__ void __launch_bounds__(BS) k_relax_bsr(int n, int N, const int8_t *ds
         T acc = bsr_offdiag<T, T>(n, (long long)N / 8, q.m, q.e, q.a, q.idx, dsign, vals, in + (long long)q.m * N);
         v = v + (b[gi] - (acc + v));
     }
-    if (phase == 1) x64[gi] += (double)v;
+    if (FINAL) x64[gi] += (double)v;
     else out[gi] = v;
 }
 
@@ -309,8 +335,13 @@ int pick_group(long long nnz, int n) {
 template <class T, int G>
 void launch_relax(const Level &L, const T *b, const T *in, T *out, int phase, double *x64, const T *xco,
                   const int *active, cudaStream_t s) {
-    k_relax_csr<T, G><<<blocks_for((long long)L.n * G, BS), BS, 0, s>>>(
-        L.n, L.rowptr, L.col, lv_val<T>(L), lv_dinv<T>(L), L.cf, b, in, out, phase, x64, xco, active, L.rowdir);
+    if (x64 && phase == 1)
+        k_relax_csr<T, G, true><<<blocks_for((long long)L.n * G, BS), BS, 0, s>>>(
+            L.n, L.rowptr, L.col, lv_val<T>(L), lv_dinv<T>(L), L.cf, b, in, out, phase, x64, xco, active, L.rowdir);
+    else
+        k_relax_csr<T, G, false><<<blocks_for((long long)L.n * G, BS), BS, 0, s>>>(
+            L.n, L.rowptr, L.col, lv_val<T>(L), lv_dinv<T>(L), L.cf, b, in, out, phase, nullptr, xco, active,
+            L.rowdir);
 }
 
 template <class T>
@@ -367,12 +398,12 @@ void vcycle_t(Hier &h, double *x64) {
             const T *vals = std::is_same<T, float>::value ? (const T *)h.bsr32 : (const T *)h.bsr64;
             if (h.prof) { rec_event(h.ev[2], s); h.relax_timed = true; }
             for (int f = 0; f < fs; ++f, cur ^= 1) {
-                k_relax_bsr<T><<<grid, BS, 0, s>>>(h.hex_n, N, h.dsign, vals, L.cf, (const T *)L.vb, bufs[cur],
-                                                   bufs[cur ^ 1], 0, nullptr, active);
+                k_relax_bsr<T, false><<<grid, BS, 0, s>>>(h.hex_n, N, h.dsign, vals, L.cf, (const T *)L.vb, bufs[cur],
+                                                          bufs[cur ^ 1], 0, nullptr, active);
                 PR_LAUNCH();
             }
-            k_relax_bsr<T><<<grid, BS, 0, s>>>(h.hex_n, N, h.dsign, vals, L.cf, (const T *)L.vb, bufs[cur], nullptr,
-                                               1, x64, active);
+            k_relax_bsr<T, true><<<grid, BS, 0, s>>>(h.hex_n, N, h.dsign, vals, L.cf, (const T *)L.vb, bufs[cur],
+                                                     nullptr, 1, x64, active);
             PR_LAUNCH();
             if (h.prof) rec_event(h.ev[3], s);
         } else {
