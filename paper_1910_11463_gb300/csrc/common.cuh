@@ -78,7 +78,6 @@ struct Level {
     long long nnz = 0;
     int *rowptr = nullptr, *col = nullptr;
     double *val = nullptr;
-    float *val32 = nullptr;
     double *dinv = nullptr;
     float *dinv32 = nullptr;
     int8_t *cf = nullptr;     // CF_F / CF_C / CF_COARSEST
@@ -98,8 +97,18 @@ struct Level {
     // coarsest segments (device): first row and rows of each matrix that ends here
     int n_cseg = 0;
     int *d_cseg_row0 = nullptr, *d_cseg_n = nullptr;
-    // V-cycle work vectors (precision of the hierarchy)
+    // CF-split copy of the rows for relaxation: rows in the order [F | C | coarsest],
+    // ascending within each group, with their entries stored contiguously in that
+    // order in the V-cycle's precision (sptr indexes the split order)
+    int nF = 0, nC = 0;
+    long long eF = 0, eC = 0;                  // entries of the F and C groups
+    int *srow = nullptr, *sptr = nullptr, *scol = nullptr;
+    void *sval = nullptr;
+    int *d_cseg_s0 = nullptr;                  // split position of each coarsest segment
+    // V-cycle work vectors (precision of the hierarchy); vF is the buffer (vy or vxn)
+    // that holds the F rows after the last F sweep, C rows are then in vx
     void *vb = nullptr, *vx = nullptr, *vxn = nullptr, *vy = nullptr;
+    void *vF = nullptr;
 };
 
 struct Hier {

@@ -38,13 +38,15 @@ struct V4 {
     T x, y, z, w;
 };
 
+// block values are read once per sweep: streaming loads (evict-first), so the
+// vectors gathered by the face terms stay in L2
 __device__ __forceinline__ V4<float> load4(const float *p) {
-    float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+    float4 v = __ldcs(reinterpret_cast<const float4 *>(p));
     return {v.x, v.y, v.z, v.w};
 }
 __device__ __forceinline__ V4<double> load4(const double *p) {
-    double2 a = __ldg(reinterpret_cast<const double2 *>(p));
-    double2 b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+    double2 a = __ldcs(reinterpret_cast<const double2 *>(p));
+    double2 b = __ldcs(reinterpret_cast<const double2 *>(p) + 1);
     return {a.x, a.y, b.x, b.y};
 }
 
@@ -203,6 +205,25 @@ __global__ void k_sumsq_rows(const int *row0, const int *nrow, const double *v, 
     if (threadIdx.x == 0) partials[(long long)m * maxblk + blockIdx.x] = tot;
 }
 
+// ---- sparse row dot products ----------------------------------------------------
+// Row k of a CSR-like store (ptr, col, val) times the vector in, lanes g, g+G, ...
+// of a G-lane group, two entries in flight per lane; entries are streamed
+// (evict-first) so the gathered vector stays in L2.  Per lane the terms are added
+// in ascending entry order.
+template <class T, int G>
+__device__ __forceinline__ T row_dot(int k, int g, const int *sptr, const int *scol, const T *sval, const T *in) {
+    int p = sptr[k] + g, e = sptr[k + 1];
+    T acc = T(0);
+    for (; p + G < e; p += 2 * G) {
+        int c0 = __ldcs(scol + p), c1 = __ldcs(scol + p + G);
+        T v0 = __ldcs(sval + p), v1 = __ldcs(sval + p + G);
+        acc += v0 * in[c0];
+        acc += v1 * in[c1];
+    }
+    if (p < e) acc += __ldcs(sval + p) * in[__ldcs(scol + p)];
+    return acc;
+}
+
 // ---- restriction ---------------------------------------------------------------
 template <class T, int G>
 __global__ void __launch_bounds__(BS) k_restrict(int nc, const int *cpts, const int *zrowptr, const int *zcol,
@@ -210,70 +231,100 @@ __global__ void __launch_bounds__(BS) k_restrict(int nc, const int *cpts, const 
     long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     int ic = (int)(tid / G);
     int g = threadIdx.x % G;
-    T acc = T(0);
-    if (ic < nc) {
-        for (int p = zrowptr[ic] + g; p < zrowptr[ic + 1]; p += G) acc += zval[p] * bf[zcol[p]];
-    }
+    T acc = ic < nc ? row_dot<T, G>(ic, g, zrowptr, zcol, zval, bf) : T(0);
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, G);
     if (ic < nc && g == 0) bc[ic] = acc + bf[cpts[ic]];
 }
 
 // ---- prolongation y = P x_c --------------------------------------------------
+// The coarse vector of level l+1 lives in two buffers after its relaxation: F rows
+// in xcF, C and coarsest rows in xc.  C rows of y are also written to y2 (the other
+// ping-pong buffer of the F sweeps), so the F sweeps never copy C rows.
 template <class T>
-__global__ void k_prolong(int n, const int8_t *cf, const int *pmap, const T *xc, T *y) {
+__global__ void k_prolong(int n, const int8_t *cf, const int *pmap, const int8_t *cfc, const T *xcF, const T *xc,
+                          T *y, T *y2) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    if (cf[i] == CF_COARSEST) return;
+    int8_t c = cf[i];
+    if (c == CF_COARSEST) return;
     int p = pmap[i];
-    y[i] = p >= 0 ? xc[p] : T(0);
+    T v = T(0);
+    if (p >= 0) v = cfc[p] == CF_F ? xcF[p] : xc[p];
+    y[i] = v;
+    if (y2 && c == CF_C) y2[i] = v;
 }
 
-// ---- CSR relaxation ------------------------------------------------------------
-// phase 0 (F): xn = y + dinv (b - A y) on F rows, xn = y on C rows
-// phase 1 (C): out = xn + dinv (b - A xn) on C rows, out = xn on F rows;
-//              level 0 (x64 != null): x64 += out, coarsest rows x64 += xco
-// FINAL: the last sweep on level 0, which adds the correction into the FP64
-// iterate; every other instance is FP64-free (on this GPU even an unused FP64
-// conversion occupies the narrow FP64 pipe).
-template <class T, int G, bool FINAL>
-__global__ void __launch_bounds__(BS) k_relax_csr(int n, const int *rowptr, const int *col, const T *val,
-                                                  const T *dinv, const int8_t *cf, const T *b, const T *in, T *out,
-                                                  int phase, double *x64, const T *xco, const int *active,
-                                                  const int *rowdir) {
+// F sweep over split positions [0, nF): out = in + dinv (b - A in) on F rows; with
+// fold (the last F sweep of a level-0 correction) x64 += the new F values as well
+template <class T, int G>
+__global__ void __launch_bounds__(BS) k_relax_f(int nF, const int *srow, const int *sptr, const int *scol,
+                                                const T *sval, const T *dinv, const T *b, const T *in, T *out,
+                                                double *fold, const int *active, const int *rowdir) {
     long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    int i = (int)(tid / G);
+    int k = (int)(tid / G);
     int g = threadIdx.x % G;
-    bool valid = i < n;
-    int8_t c = valid ? cf[i] : CF_COARSEST;
+    bool valid = k < nF;
+    int i = valid ? srow[k] : 0;
     if (valid && active && !active[rowdir[i]]) valid = false;
-    bool work = valid && c == (phase == 0 ? CF_F : CF_C);
-    T acc = T(0);
-    if (work)
-        for (int p = rowptr[i] + g; p < rowptr[i + 1]; p += G) acc += val[p] * in[col[p]];
+    T acc = valid ? row_dot<T, G>(k, g, sptr, scol, sval, in) : T(0);
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, G);
     if (!valid || g != 0) return;
-    T v;
-    if (c == CF_COARSEST) {
+    T v = in[i] + dinv[i] * (b[i] - acc);
+    out[i] = v;
+    if (fold) fold[i] += (double)v;
+}
+
+// C sweep over split positions [k0, k1): C rows relax into out (non-final) or into
+// x64 (final); coarsest rows (final only) add the coarsest solution xco
+template <class T, int G, bool FINAL>
+__global__ void __launch_bounds__(BS) k_relax_c(int k0, int k1, int kX, const int *srow, const int *sptr,
+                                                const int *scol, const T *sval, const T *dinv, const T *b,
+                                                const T *in, T *out, double *x64, const T *xco, const int *active,
+                                                const int *rowdir) {
+    long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int k = k0 + (int)(tid / G);
+    int g = threadIdx.x % G;
+    bool valid = k < k1;
+    int i = valid ? srow[k] : 0;
+    if (valid && active && !active[rowdir[i]]) valid = false;
+    bool work = valid && k < kX;
+    T acc = work ? row_dot<T, G>(k, g, sptr, scol, sval, in) : T(0);
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, G);
+    if (!valid || g != 0) return;
+    if (!work) {
         if (FINAL) x64[i] += (double)xco[i];
         return;
     }
-    v = work ? in[i] + dinv[i] * (b[i] - acc) : in[i];
+    T v = in[i] + dinv[i] * (b[i] - acc);
     if (FINAL) x64[i] += (double)v;
     else out[i] = v;
+}
+
+// single-level hierarchies: x64 += the coarsest solution on active rows
+template <class T>
+__global__ void k_fold_coarsest(int n, const T *xco, double *x64, const int *active, const int *rowdir) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || (active && !active[rowdir[i]])) return;
+    x64[i] += (double)xco[i];
 }
 
 // ---- BSR (hex level 0) relaxation, unit diagonal ------------------------------
 template <class T, bool FINAL>
 __global__ void __launch_bounds__(BS) k_relax_bsr(int n, int N, const int8_t *dsign, const T *vals, const int8_t *cf,
                                                   const T *b, const T *in, T *out, int phase, double *x64,
-                                                  const int *active) {
+                                                  const T *xco, const int *active) {
     HexRow q = hex_row(n);
     if (active && !active[q.m]) return;
     if (!q.valid) return;
     long long gi = (long long)q.m * N + 8LL * q.e + q.a;
     int8_t c = cf[gi];
+    if (c == CF_COARSEST) {   // a matrix whose hierarchy ends at level 0
+        if (FINAL) x64[gi] += (double)xco[gi];
+        return;
+    }
     T v = in[gi];
     if (c == (phase == 0 ? CF_F : CF_C)) {
         T acc = bsr_offdiag<T, T>(n, (long long)N / 8, q.m, q.e, q.a, q.idx, dsign, vals, in + (long long)q.m * N);
@@ -284,18 +335,19 @@ __global__ void __launch_bounds__(BS) k_relax_bsr(int n, int N, const int8_t *ds
 }
 
 // ---- coarsest level: Jacobi sweeps, one CTA per matrix segment ---------------
+// segment rows r0.. sit at split positions s0.. (the coarsest group of the split)
 template <class T>
-__global__ void k_coarsest(const int *seg_row0, const int *seg_n, const int *rowptr, const int *col, const T *val,
-                           const T *dinv, const T *b, T *x, T *xt, int sweeps) {
-    int r0 = seg_row0[blockIdx.x], nr = seg_n[blockIdx.x];
+__global__ void k_coarsest(const int *seg_row0, const int *seg_n, const int *seg_s0, const int *sptr,
+                           const int *scol, const T *sval, const T *dinv, const T *b, T *x, T *xt, int sweeps) {
+    int r0 = seg_row0[blockIdx.x], nr = seg_n[blockIdx.x], s0 = seg_s0[blockIdx.x];
     for (int i = threadIdx.x; i < nr; i += blockDim.x) x[r0 + i] = T(0);
     __syncthreads();
     T *cur = x, *nxt = xt;
     for (int s = 0; s < sweeps; ++s) {
         for (int li = threadIdx.x; li < nr; li += blockDim.x) {
-            int i = r0 + li;
+            int i = r0 + li, k = s0 + li;
             T acc = T(0);
-            for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) acc += val[p] * cur[col[p]];
+            for (int p = sptr[k]; p < sptr[k + 1]; ++p) acc += sval[p] * cur[scol[p]];
             nxt[i] = cur[i] + dinv[i] * (b[i] - acc);
         }
         __syncthreads();
@@ -305,12 +357,6 @@ __global__ void k_coarsest(const int *seg_row0, const int *seg_n, const int *row
         for (int li = threadIdx.x; li < nr; li += blockDim.x) x[r0 + li] = cur[r0 + li];
 }
 
-template <class T>
-const T *lv_val(const Level &L);
-template <>
-const float *lv_val<float>(const Level &L) { return L.val32; }
-template <>
-const double *lv_val<double>(const Level &L) { return L.val; }
 template <class T>
 const T *lv_dinv(const Level &L);
 template <>
@@ -332,27 +378,49 @@ int pick_group(long long nnz, int n) {
     return 16;
 }
 
-template <class T, int G>
-void launch_relax(const Level &L, const T *b, const T *in, T *out, int phase, double *x64, const T *xco,
-                  const int *active, cudaStream_t s) {
-    if (x64 && phase == 1)
-        k_relax_csr<T, G, true><<<blocks_for((long long)L.n * G, BS), BS, 0, s>>>(
-            L.n, L.rowptr, L.col, lv_val<T>(L), lv_dinv<T>(L), L.cf, b, in, out, phase, x64, xco, active, L.rowdir);
-    else
-        k_relax_csr<T, G, false><<<blocks_for((long long)L.n * G, BS), BS, 0, s>>>(
-            L.n, L.rowptr, L.col, lv_val<T>(L), lv_dinv<T>(L), L.cf, b, in, out, phase, nullptr, xco, active,
-            L.rowdir);
+// F sweep (fold: x64 on the last level-0 sweep) and C sweep (final: into x64)
+template <class T>
+void relax_f(const Level &L, const T *b, const T *in, T *out, double *fold, const int *active, cudaStream_t s) {
+    if (L.nF == 0) return;
+    const T *sv = (const T *)L.sval;
+    const T *dv = lv_dinv<T>(L);
+#define PR_RELAX_F(G)                                                                                       \
+    k_relax_f<T, G><<<blocks_for((long long)L.nF * G, BS), BS, 0, s>>>(L.nF, L.srow, L.sptr, L.scol, sv, dv, b, \
+                                                                       in, out, fold, active, L.rowdir)
+    switch (pick_group(L.eF, L.nF)) {
+        case 1: PR_RELAX_F(1); break;
+        case 4: PR_RELAX_F(4); break;
+        case 8: PR_RELAX_F(8); break;
+        default: PR_RELAX_F(16); break;
+    }
+#undef PR_RELAX_F
+    PR_LAUNCH();
 }
 
 template <class T>
-void relax_csr(const Level &L, const T *b, const T *in, T *out, int phase, double *x64, const T *xco,
-               const int *active, cudaStream_t s) {
-    switch (pick_group(L.nnz, L.n)) {
-        case 1: launch_relax<T, 1>(L, b, in, out, phase, x64, xco, active, s); break;
-        case 4: launch_relax<T, 4>(L, b, in, out, phase, x64, xco, active, s); break;
-        case 8: launch_relax<T, 8>(L, b, in, out, phase, x64, xco, active, s); break;
-        default: launch_relax<T, 16>(L, b, in, out, phase, x64, xco, active, s); break;
+void relax_c(const Level &L, const T *b, const T *in, T *out, double *x64, const T *xco, const int *active,
+             cudaStream_t s) {
+    const int k0 = L.nF, kX = L.nF + L.nC, k1 = x64 ? L.n : kX;
+    if (k1 <= k0) return;
+    const T *sv = (const T *)L.sval;
+    const T *dv = lv_dinv<T>(L);
+#define PR_RELAX_C(G)                                                                                          \
+    do {                                                                                                      \
+        long long nb = blocks_for((long long)(k1 - k0) * G, BS);                                              \
+        if (x64)                                                                                              \
+            k_relax_c<T, G, true><<<nb, BS, 0, s>>>(k0, k1, kX, L.srow, L.sptr, L.scol, sv, dv, b, in, nullptr, \
+                                                    x64, xco, active, L.rowdir);                              \
+        else                                                                                                  \
+            k_relax_c<T, G, false><<<nb, BS, 0, s>>>(k0, k1, kX, L.srow, L.sptr, L.scol, sv, dv, b, in, out,    \
+                                                     nullptr, xco, active, L.rowdir);                         \
+    } while (0)
+    switch (pick_group(L.eC, L.nC)) {
+        case 1: PR_RELAX_C(1); break;
+        case 4: PR_RELAX_C(4); break;
+        case 8: PR_RELAX_C(8); break;
+        default: PR_RELAX_C(16); break;
     }
+#undef PR_RELAX_C
     PR_LAUNCH();
 }
 
@@ -375,11 +443,12 @@ void vcycle_t(Hier &h, double *x64) {
     const int *active = h.active;
     for (int l = 0; l < NL; ++l) {
         Level &L = h.lev[l];
+        L.vF = L.vx;   // replaced by the F sweeps' buffer once the level relaxes
         if (l + 1 < NL) restrict_<T>(L, (const T *)L.vb, (T *)h.lev[l + 1].vb, s);
         if (L.n_cseg) {
-            k_coarsest<T><<<L.n_cseg, 256, 0, s>>>(L.d_cseg_row0, L.d_cseg_n, L.rowptr, L.col, lv_val<T>(L),
-                                                   lv_dinv<T>(L), (const T *)L.vb, (T *)L.vx, (T *)L.vxn,
-                                                   h.prm.coarse_sweeps);
+            k_coarsest<T><<<L.n_cseg, 256, 0, s>>>(L.d_cseg_row0, L.d_cseg_n, L.d_cseg_s0, L.sptr, L.scol,
+                                                   (const T *)L.sval, lv_dinv<T>(L), (const T *)L.vb, (T *)L.vx,
+                                                   (T *)L.vxn, h.prm.coarse_sweeps);
             PR_LAUNCH();
         }
     }
@@ -387,39 +456,45 @@ void vcycle_t(Hier &h, double *x64) {
     for (int l = NL - 2; l >= 0; --l) {
         Level &L = h.lev[l];
         const Level &C = h.lev[l + 1];
-        k_prolong<T><<<blocks_for(L.n, BS), BS, 0, s>>>(L.n, L.cf, L.pmap, (const T *)C.vx, (T *)L.vy);
-        PR_LAUNCH();
+        const bool bsr = l == 0 && h.bsr0;
         // F sweeps ping-pong between vy and vxn; the C sweep reads the last one
         T *bufs[2] = {(T *)L.vy, (T *)L.vxn};
+        k_prolong<T><<<blocks_for(L.n, BS), BS, 0, s>>>(L.n, L.cf, L.pmap, C.cf, (const T *)C.vF, (const T *)C.vx,
+                                                        bufs[0], bsr ? nullptr : bufs[1]);
+        PR_LAUNCH();
         int cur = 0;
-        if (l == 0 && h.bsr0) {
+        if (bsr) {
             int N = h.n0[0];
             dim3 grid(blocks_for(h.hex_n, 32), h.hex_n * h.hex_n, h.ndir);
             const T *vals = std::is_same<T, float>::value ? (const T *)h.bsr32 : (const T *)h.bsr64;
             if (h.prof) { rec_event(h.ev[2], s); h.relax_timed = true; }
             for (int f = 0; f < fs; ++f, cur ^= 1) {
                 k_relax_bsr<T, false><<<grid, BS, 0, s>>>(h.hex_n, N, h.dsign, vals, L.cf, (const T *)L.vb, bufs[cur],
-                                                          bufs[cur ^ 1], 0, nullptr, active);
+                                                          bufs[cur ^ 1], 0, nullptr, nullptr, active);
                 PR_LAUNCH();
             }
             k_relax_bsr<T, true><<<grid, BS, 0, s>>>(h.hex_n, N, h.dsign, vals, L.cf, (const T *)L.vb, bufs[cur],
-                                                     nullptr, 1, x64, active);
+                                                     nullptr, 1, x64, (const T *)L.vx, active);
             PR_LAUNCH();
             if (h.prof) rec_event(h.ev[3], s);
         } else {
+            // C rows stay where the prolongation put them (both buffers); F rows end in
+            // bufs[cur], C rows in vx (level 0: both folded into x64 instead)
             const int *act = l == 0 ? active : nullptr;
             bool tl = h.prof && l >= 1 && (int)h.evl.size() >= 2 * (l + 1);
             if (tl) rec_event(h.evl[2 * l], s);
             for (int f = 0; f < fs; ++f, cur ^= 1)
-                relax_csr<T>(L, (const T *)L.vb, bufs[cur], bufs[cur ^ 1], 0, nullptr, nullptr, act, s);
-            relax_csr<T>(L, (const T *)L.vb, bufs[cur], (T *)L.vx, 1, l == 0 ? x64 : nullptr, (const T *)L.vx, act,
-                         s);
+                relax_f<T>(L, (const T *)L.vb, bufs[cur], bufs[cur ^ 1], l == 0 && f == fs - 1 ? x64 : nullptr, act,
+                           s);
+            relax_c<T>(L, (const T *)L.vb, bufs[cur], (T *)L.vx, l == 0 ? x64 : nullptr, (const T *)L.vx, act, s);
             if (tl) rec_event(h.evl[2 * l + 1], s);
         }
+        L.vF = bufs[cur];
     }
     if (NL == 1) {   // single-level hierarchies: x += coarsest solution
         Level &L = h.lev[0];
-        relax_csr<T>(L, (const T *)L.vb, (const T *)L.vx, (T *)L.vxn, 1, x64, (const T *)L.vx, active, s);
+        k_fold_coarsest<T><<<blocks_for(L.n, BS), BS, 0, s>>>(L.n, (const T *)L.vx, x64, active, L.rowdir);
+        PR_LAUNCH();
     }
 }
 
@@ -504,8 +579,10 @@ void level0_bytes(Hier &h) {
     h.bytes_relaxc = 0;
     cudaStream_t s = h.stream;
     {
-        // coarse levels: each F sweep reads rowptr, cf, input and writes output for every
-        // row, and entries (column + value), b and dinv of F rows; the C sweep likewise
+        // coarse levels: each F sweep reads, per F row, its split position (row index and
+        // entry offset), b, dinv and its input value, writes its output value, and reads
+        // its entries (column + value); the C sweep likewise over the C rows.  Gathered
+        // neighbour values are taken as cached (the vector is far smaller than L2).
         double sT = h.prm.precision == 1 ? 4.0 : 8.0;
         unsigned long long *cnt = dmalloc<unsigned long long>(4, s);
         for (size_t l = 1; l + 1 < h.lev.size(); ++l) {
@@ -517,9 +594,8 @@ void level0_bytes(Hier &h) {
             unsigned long long c[4];
             PR_CUDA(cudaMemcpyAsync(c, cnt, sizeof c, cudaMemcpyDeviceToHost, s));
             PR_CUDA(cudaStreamSynchronize(s));
-            double rows = (double)(c[0] + c[1]);
-            double fpass = rows * (4 + 1 + 2 * sT) + (double)c[2] * (4 + sT) + (double)c[0] * 2 * sT;
-            double cpass = rows * (4 + 1 + 2 * sT) + (double)c[3] * (4 + sT) + (double)c[1] * 2 * sT;
+            double fpass = (double)c[0] * (8 + 4 * sT) + (double)c[2] * (4 + sT);
+            double cpass = (double)c[1] * (8 + 4 * sT) + (double)c[3] * (4 + sT);
             h.bytes_relaxc += h.prm.f_sweeps * fpass + cpass;
         }
         dfree(cnt, s);

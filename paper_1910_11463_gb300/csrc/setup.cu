@@ -847,11 +847,92 @@ void partition_by_class(const int8_t *cls, int n, int nclass, int *list, int *st
     dfree(pos, s);
 }
 
+__global__ void k_split_len(int n, const int *srow, const int *rowptr, int *len) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) {
+        int i = srow[k];
+        len[k] = rowptr[i + 1] - rowptr[i];
+    }
+}
+
+// entries of split row k (row srow[k]) copied to sptr[k].., eight lanes per row
+template <class T>
+__global__ void k_split_copy(int n, const int *srow, const int *rowptr, const int *col, const double *val,
+                             const int *sptr, int *scol, T *sval) {
+    long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int k = (int)(tid >> 3), g = (int)(tid & 7);
+    if (k >= n) return;
+    int i = srow[k];
+    int a = rowptr[i], len = rowptr[i + 1] - a, d = sptr[k];
+    for (int q = g; q < len; q += 8) {
+        scol[d + q] = col[a + q];
+        sval[d + q] = (T)val[a + q];
+    }
+}
+
+// CF-split row storage of one level (see Level): F rows, then C rows, then the rows of
+// matrices that end at this level, with the coarsest segments' split positions
+void build_split(Hier &h, Level &L) {
+    cudaStream_t s = h.stream;
+    const int BS = 256;
+    const int n = L.n;
+    const size_t es = h.prm.precision == 1 ? sizeof(float) : sizeof(double);
+    int st[3] = {0, 0, 0}, cnt[3] = {0, 0, 0};
+    L.srow = dmalloc<int>(std::max(n, 1), s);
+    partition_by_class(L.cf, n, 3, L.srow, st, cnt, s);
+    PR_REQUIRE(cnt[0] + cnt[1] + cnt[2] == n, PAIR_ERR_DEVICE, "CF split does not cover the level's rows");
+    L.nF = cnt[0];
+    L.nC = cnt[1];
+    int *len = dmalloc<int>(std::max(n, 1), s);
+    k_split_len<<<blocks_for(std::max(n, 1), BS), BS, 0, s>>>(n, L.srow, L.rowptr, len);
+    PR_LAUNCH();
+    L.sptr = dmalloc<int>(n + 1, s);
+    long long tot = scan_exclusive(len, L.sptr, n, s);
+    dfree(len, s);
+    PR_REQUIRE(tot == L.nnz, PAIR_ERR_DEVICE, "CF split entry count differs from the level's");
+    int b[2] = {0, 0};
+    PR_CUDA(cudaMemcpyAsync(&b[0], L.sptr + L.nF, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PR_CUDA(cudaMemcpyAsync(&b[1], L.sptr + L.nF + L.nC, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PR_CUDA(cudaStreamSynchronize(s));
+    L.eF = b[0];
+    L.eC = (long long)b[1] - b[0];
+    L.scol = dmalloc<int>(std::max<long long>(L.nnz, 1), s);
+    L.sval = dmalloc<char>(std::max<long long>(L.nnz, 1) * es, s);
+    if (n) {
+        if (h.prm.precision == 1)
+            k_split_copy<float><<<blocks_for((long long)n * 8, BS), BS, 0, s>>>(n, L.srow, L.rowptr, L.col, L.val,
+                                                                               L.sptr, L.scol, (float *)L.sval);
+        else
+            k_split_copy<double><<<blocks_for((long long)n * 8, BS), BS, 0, s>>>(n, L.srow, L.rowptr, L.col, L.val,
+                                                                                L.sptr, L.scol, (double *)L.sval);
+        PR_LAUNCH();
+    }
+    // coarsest segments are whole matrices, ascending in row order, so each one is a
+    // contiguous run of the coarsest group
+    std::vector<int> s0;
+    long long pos = (long long)L.nF + L.nC, prev = -1;
+    for (int d = 0; d < h.ndir; ++d)
+        if (L.nrows[d] > 0 && L.coarsest[d]) {
+            PR_REQUIRE(L.row0[d] > prev, PAIR_ERR_DEVICE, "coarsest segments out of row order");
+            prev = L.row0[d];
+            s0.push_back((int)pos);
+            pos += L.nrows[d];
+        }
+    PR_REQUIRE(pos == n, PAIR_ERR_DEVICE, "coarsest rows differ from the coarsest segments");
+    PR_REQUIRE((int)s0.size() == L.n_cseg, PAIR_ERR_DEVICE, "coarsest segment count mismatch");
+    if (!s0.empty()) {
+        L.d_cseg_s0 = dmalloc<int>(s0.size(), s);
+        PR_CUDA(cudaMemcpyAsync(L.d_cseg_s0, s0.data(), sizeof(int) * s0.size(), cudaMemcpyHostToDevice, s));
+        PR_CUDA(cudaStreamSynchronize(s));
+    }
+}
+
 }  // namespace
 
 void free_level(Level &L, cudaStream_t s) {
-    void *ptrs[] = {L.rowptr, L.col, L.val, L.val32, L.dinv, L.dinv32, L.cf, L.pmap, L.rowdir, L.cpts,
+    void *ptrs[] = {L.rowptr, L.col, L.val, L.dinv, L.dinv32, L.cf, L.pmap, L.rowdir, L.cpts,
                     L.zrowptr, L.zcol, L.zval, L.zval32, L.d_row0, L.d_cseg_row0, L.d_cseg_n,
+                    L.srow, L.sptr, L.scol, L.sval, L.d_cseg_s0,
                     L.vb, L.vx, L.vxn, L.vy};
     for (void *p : ptrs) dfree(p, s);
     L = Level();
@@ -1210,15 +1291,13 @@ void build_hierarchy(Hier &h) {
     d2h(&err, h.d_err, 1, s);
     dfree(d_count, s); dfree(dwork, s); dfree(dcont, s); dfree(dnc, s); dfree(dnnz, s);
     PR_REQUIRE(err == 0, PAIR_ERR_DEVICE, "setup kernel reported device error bits " + std::to_string(err));
-    // FP32 copies for the inner V-cycle
+    // relaxation storage (CF split, cycle precision) and FP32 copies of Z
+    // (the block-form level 0 relaxes without it; it needs it only for coarsest sweeps)
+    for (size_t l = 0; l < h.lev.size(); ++l)
+        if (!(l == 0 && h.bsr0) || h.lev[l].n_cseg > 0) build_split(h, h.lev[l]);
     if (prm.precision == 1) {
         for (size_t l = 0; l < h.lev.size(); ++l) {
             Level &L = h.lev[l];
-            if (!(l == 0 && h.bsr0)) {
-                L.val32 = dmalloc<float>(L.nnz, s);
-                k_cast<<<blocks_for(L.nnz, BS), BS, 0, s>>>(L.nnz, L.val, L.val32);
-                PR_LAUNCH();
-            }
             if (L.nnzZ) {
                 L.zval32 = dmalloc<float>(L.nnzZ, s);
                 k_cast<<<blocks_for(L.nnzZ, BS), BS, 0, s>>>(L.nnzZ, L.zval, L.zval32);

@@ -103,9 +103,11 @@ def test_adjoint_gradients_vs_central_differences_hex24(pair):
     elems = rng.choice(prob.E, 50, replace=False)
 
     def J(**over):
+        # perturbed solves start from the unperturbed flux (fewer iterations, alike errors)
         kw = {k: getattr(prob, k).copy() for k in ("sigma_t", "sigma_s", "q")}
         kw.update(over)
-        p, _, _ = pair.si_solve(prob.n, prob.omega, prob.w, kw["sigma_t"], kw["sigma_s"], kw["q"], air=air, si=si)
+        p, _, _ = pair.si_solve(prob.n, prob.omega, prob.w, kw["sigma_t"], kw["sigma_s"], kw["q"], air=air, si=si,
+                                phi0=phi)
         return float(torch.dot(gd, p).item())
 
     worst = {}
@@ -114,7 +116,11 @@ def test_adjoint_gradients_vs_central_differences_hex24(pair):
         gmax = np.abs(grads[name]).max()
         errs = []
         for K in elems[:10] if name != "sigma_t" else elems:
-            h = 1e-6 * max(1.0, abs(base[K]))
+            # error model of the central difference: truncation ~ h^2 |J'''|/6 (J is a
+            # rational function of the element's cross sections, so ~h^2/6 relative) plus
+            # round-off ~ eps_J |J| / h with eps_J ~ 1e-14 from the solve's stopping test;
+            # one element's derivative is ~|J|/E, so h = 1e-3 keeps both near 1e-7
+            h = 1e-3 * max(1.0, abs(base[K]))
             vp, vm = base.copy(), base.copy()
             vp[K] += h
             vm[K] -= h
