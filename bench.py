@@ -47,7 +47,13 @@ WORKLOADS = {
                     "q=1 in central 8^3",
     "hex64_s8": "unit cube 64^3 hex Q1 (2,097,152 DOFs/dir), S8 (80 dirs) in HBM-admitted batches, "
                 "sigma_t~logU[0.1,100], sigma_s=0.95 sigma_t, q=1",
+    "tet40_s8": "unit cube 40^3 cubes x 6 Kuhn tets jittered 0.2h (1,536,000 P1 DOFs/dir), S8 (80 dirs), sigma_t "
+                "checkerboard {1,100} over 4^3 regions, sigma_s=0.9 sigma_t, q=1 where sigma_t=1, distance-2 AIR",
 }
+# workloads whose scattering ratio needs hundreds of SI iterations: a step runs a
+# fixed number of iterations instead of the whole solve
+FIXED_SI = {"hex64_s8": 2, "tet40_s8": 2}
+DISTANCE = {"tet40_s8": 2}
 
 
 def dist_env():
@@ -137,12 +143,16 @@ def oracle_direction_times(prob, m, air_kw):
     the first SI iteration's right-hand side to 1e-8 (seconds)."""
     import numpy as np
     from oracle import oracle as O
+    tet = hasattr(prob, "tets")
     t0 = time.perf_counter()
-    r, c, v = O.hex_assemble(prob.n, prob.omega[m], prob.sigma_t)
+    if tet:
+        r, c, v = O.tet_assemble(prob, prob.omega[m])
+    else:
+        r, c, v = O.hex_assemble(prob.n, prob.omega[m], prob.sigma_t)
     H = O.Hierarchy(r, c, v, O.default_params(**air_kw))
     t1 = time.perf_counter()
-    src = np.repeat(prob.q, 8) / (4 * np.pi)
-    b = O.hex_rhs(prob.n, prob.omega[m], prob.sigma_t, src)
+    src = np.repeat(prob.q, 4 if tet else 8) / (4 * np.pi)
+    b = O.tet_rhs(prob, prob.omega[m], src) if tet else O.hex_rhs(prob.n, prob.omega[m], prob.sigma_t, src)
     H.solve(b, tol=1e-8, maxit=500)
     t2 = time.perf_counter()
     return t1 - t0, t2 - t1
@@ -176,8 +186,9 @@ def run_reference(args):
     # sample); setup amortised over the SI iterations the workload needs
     from oracle import oracle as O
     O.build()
-    air_kw = dict(theta=args.theta, phi_R=args.phi_R, phi_A=args.phi_A)
-    si_iters = args.si_iters
+    air_kw = dict(theta=args.theta, phi_R=args.phi_R, phi_A=args.phi_A, distance=args.distance)
+    fixed = args.si_fixed if args.si_fixed is not None else FIXED_SI.get(args.config, 0)
+    si_iters = fixed or args.si_iters
     times = []
     for k in range(args.warmup + args.steps):
         a, b = oracle_direction_times(prob, k % prob.M, air_kw)
@@ -221,14 +232,19 @@ def run_ours(args):
     ss = torch.as_tensor(prob.sigma_s, device=dev)
     qq = torch.as_tensor(prob.q, device=dev)
     N, M = prob.N, prob.M
-    tuned = dict(theta=args.theta, phi_R=args.phi_R, phi_A=args.phi_A)
+    geom = pair.TetMesh(prob.verts, prob.tets, prob.nbr) if hasattr(prob, "tets") else prob.n
+    fixed = args.si_fixed if args.si_fixed is not None else FIXED_SI.get(args.config, 0)
+    tuned = dict(theta=args.theta, phi_R=args.phi_R, phi_A=args.phi_A, distance=args.distance)
     air = pair.default_air_params(precision=args.precision, **tuned)
-    si = pair.default_si_params(tol=1e-8, max_iters=1000, inner_tol=1e-8, inner_maxit=200)
+    if fixed:
+        si = pair.default_si_params(tol=1e-8, max_iters=fixed, fixed_iters=1, inner_tol=1e-8, inner_maxit=200)
+    else:
+        si = pair.default_si_params(tol=1e-8, max_iters=1000, inner_tol=1e-8, inner_maxit=200)
     si_one = pair.default_si_params(tol=1e-8, max_iters=1, inner_tol=1e-8, inner_maxit=200)
     zero = torch.zeros(N, dtype=torch.float64, device=dev)
 
     def solve(air_p, si_p, phi0):
-        out, _, info = pair.si_solve(prob.n, prob.omega, prob.w, st, ss, qq, air=air_p, si=si_p, phi0=phi0)
+        out, _, info = pair.si_solve(geom, prob.omega, prob.w, st, ss, qq, air=air_p, si=si_p, phi0=phi0)
         return out, info
 
     def barrier():
@@ -267,8 +283,8 @@ def run_ours(args):
         "k_res0_bsr": ("FP64 outer residual, level 0 block form", tot("t_res0_ms"), tot("n_res0"), tot("gb_res0")),
         "k_relax_bsr": ("FP32 F-F-C Jacobi, level 0 block form", tot("t_relax0_ms"), tot("n_relax0"),
                         tot("gb_relax0")),
-        "k_relax_csr": ("FP32 F-F-C Jacobi, levels >= 1 (CSR), per cycle", tot("t_relaxc_ms"), tot("n_relaxc"),
-                        tot("gb_relaxc")),
+        "k_relax_f+k_relax_c": ("FP32 F-F-C Jacobi, levels >= 1 (CF-split CSR); one unit = every coarse "
+                                "level's sweeps of one V-cycle", tot("t_relaxc_ms"), tot("n_relaxc"), tot("gb_relaxc")),
     }
     rl = {}
     for name, (what, t_ms, n_l, gb) in kern.items():
@@ -288,7 +304,7 @@ def run_ours(args):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic, "kernel": dom,
                 "peak_source": f"{peak_kind}: MEASURED_PEAKS.json hbm_gbs (copy test)",
-                "algorithmic_bytes": "counted per launch in the library from the hierarchy (DESIGN.md 6)",
+                "algorithmic_bytes": "counted in the library from the hierarchy: per launch (level-0 kernels) or per V-cycle (all coarse levels' F, F and C sweeps)",
                 "kernels": rl}
 
     # the paper's memory mode: every hierarchy rebuilt for every iteration
@@ -314,7 +330,7 @@ def run_ours(args):
     barrier()
     e0.record(stream)
     for _ in range(e2e_steps):
-        out, _, info_e = pair.si_solve(prob.n, prob.omega, prob.w, h_st, h_ss, h_q, air=air, si=si, phi0=h_phi0)
+        out, _, info_e = pair.si_solve(geom, prob.omega, prob.w, h_st, h_ss, h_q, air=air, si=si, phi0=h_phi0)
         h_out = out.cpu()
     e1.record(stream)
     barrier()
@@ -326,8 +342,8 @@ def run_ours(args):
     fp64 = None
     if not args.no_fp64_baseline:
         air64 = pair.default_air_params(precision=0, **tuned)
-        si64 = pair.default_si_params(tol=1e-8, max_iters=1000, inner_tol=1e-8, inner_maxit=200, batch=1,
-                                      use_graphs=0)
+        si64 = pair.default_si_params(tol=1e-8, max_iters=fixed or 1000, fixed_iters=int(bool(fixed)),
+                                      inner_tol=1e-8, inner_maxit=200, batch=1, use_graphs=0)
         barrier()
         e0.record(stream)
         phi64, i64 = solve(air64, si64, zero)
@@ -350,15 +366,19 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32 V-cycle + f64 residual/setup" if args.precision else "f64",
         "data": "synthetic",
         "config": {"workload": args.config + ": " + WORKLOADS[args.config],
-                   "step": "one complete SI solve from phi=0 (assembly + AIR setup + SI iterations to 1e-8, every "
-                           "direction solved from psi=0 to 1e-8 relative FP64 residual each iteration); value = "
-                           "DOF*dir*iterations/step time",
+                   "step": ("one complete SI solve from phi=0 (assembly + AIR setup + SI iterations to 1e-8, every "
+                            "direction solved from psi=0 to 1e-8 relative FP64 residual each iteration); value = "
+                            "DOF*dir*iterations/step time") if not fixed else
+                           (f"assembly + AIR setup + {fixed} SI iterations from phi=0 (every direction solved from "
+                            "psi=0 to 1e-8 relative FP64 residual each iteration); value = DOF*dir*iterations/step "
+                            "time (setup included); solve_only_value excludes the setup"),
                    "air": {"theta": args.theta, "eps_R": 0.01, "phi_R": args.phi_R, "phi_A": args.phi_A,
-                           "distance": 1, "relax": "F-F-C Jacobi", "coarsening": "PMIS"},
+                           "distance": args.distance, "relax": "F-F-C Jacobi", "coarsening": "PMIS"},
                    "l2": "working set per step >> 129 MB L2 (no flush needed)",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU, all directions in one batch",
                    "precision": "FP32 hierarchy/V-cycle, FP64 refinement" if args.precision else "FP64"},
         "si_iterations": iters, "setup_ms": t_setup, "solve_ms": t_solve,
+        "solve_only_value": N * M * iters * world / (t_solve * 1e-3) if t_solve > 0 else None,
         "setup_phase_ms": {"strength+pmis": phases[0], "p+lair": phases[1], "rap": phases[2],
                            "assembly+other": phases[3]},
         "rebuild_every_iteration": rebuild,
@@ -390,10 +410,17 @@ def main():
     ap.add_argument("--theta", type=float, default=0.5)
     ap.add_argument("--phi-R", dest="phi_R", type=float, default=0.0)
     ap.add_argument("--phi-A", dest="phi_A", type=float, default=0.05)
+    ap.add_argument("--distance", type=int, default=None, choices=[1, 2],
+                    help="lAIR distance (default: 2 for tet40_s8, else 1)")
+    ap.add_argument("--si-fixed", dest="si_fixed", type=int, default=None,
+                    help="run exactly this many SI iterations per step (default: 2 for hex64_s8 and tet40_s8, "
+                         "0 = solve to 1e-8 for the others)")
     ap.add_argument("--si-iters", type=int, default=18,
                     help="SI iterations the setup is amortised over in the reference arm (hex32_s4 needs 18)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)   # timing rule: at least three untimed warm-up steps
+    if args.distance is None:
+        args.distance = DISTANCE.get(args.config, 1)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -210,9 +210,12 @@ typedef struct {
     double mem_budget_gb;/* device memory for hierarchies (0: 60% of free memory) */
     double g_inflow;     /* isotropic inflow angular flux on the inflow boundary (0: vacuum) */
     int use_graphs;      /* capture the V-cycle of a batch in a CUDA graph */
+    int fixed_iters;     /* 1: run exactly max_iters SI iterations (stop early only at tol)
+                          * and return PAIR_OK with the last change in info; 0: missing
+                          * tol after max_iters > 1 iterations is PAIR_ERR_NOT_CONVERGED */
 } si_params;
 
-PAIR_API void si_params_default(si_params *p);   /* 1e-8, 500, 1e-8, 100, 0, 0, 0, 1 */
+PAIR_API void si_params_default(si_params *p);   /* 1e-8, 500, 1e-8, 100, 0, 0, 0, 1, 0 */
 
 typedef struct {
     int si_iters;

@@ -110,6 +110,7 @@ void si_params_default(si_params *p) {
     p->mem_budget_gb = 0;
     p->g_inflow = 0;
     p->use_graphs = 1;
+    p->fixed_iters = 0;
 }
 
 const char *pair_last_error(void) { return g_last_error.c_str(); }

@@ -636,7 +636,7 @@ void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t,
         for (int k = 0; k < 3; ++k) info->t_setup_phase_ms[k] = tph[k];
         info->t_setup_phase_ms[3] = t_setup - (tph[0] + tph[1] + tph[2]);
     }
-    if (!converged && sp.max_iters > 1) {
+    if (!converged && sp.max_iters > 1 && !sp.fixed_iters) {
         char buf[128];
         snprintf(buf, sizeof buf, "source iteration: %d iterations, change %.3e > %.3e", sp.max_iters, change, sp.tol);
         fail(PAIR_ERR_NOT_CONVERGED, buf);

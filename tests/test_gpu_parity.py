@@ -207,6 +207,22 @@ def test_si_tiny_meshes(pair, n):
     assert np.linalg.norm(_cpu(phi) - ref) <= 1e-9 * np.linalg.norm(ref)
 
 
+def test_si_fixed_iterations(pair):
+    """fixed_iters: exactly max_iters SI iterations, no error although the change is
+    above tol, and the flux equals the oracle's after the same number of iterations;
+    without the flag the same call reports PAIR_ERR_NOT_CONVERGED."""
+    prob = I.small_hex(5, order=4, seed=21)
+    a = pair.default_air_params(precision=0)
+    ref, _, oinfo = O.si_hex(prob, tol=1e-300, max_iters=3, inner_tol=1e-12)
+    phi, _, info = pair.si_solve_problem(prob, air=a, si=pair.default_si_params(tol=1e-300, max_iters=3, fixed_iters=1,
+                                                                                 inner_tol=1e-12))
+    assert info["si_iters"] == 3 and info["si_change"] > 0
+    assert np.linalg.norm(_cpu(phi) - ref) <= 1e-10 * np.linalg.norm(ref)
+    with pytest.raises(pair.PairError) as e:
+        pair.si_solve_problem(prob, air=a, si=pair.default_si_params(tol=1e-300, max_iters=3, inner_tol=1e-12))
+    assert e.value.status == -4
+
+
 def test_batched_si_equals_unbatched(pair):
     prob = I.small_hex(6, order=4, seed=12)
     a = pair.default_air_params(precision=0)
