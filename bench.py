@@ -279,10 +279,14 @@ def run_ours(args):
     t_setup, t_solve = tot("t_setup_ms") / args.steps, tot("t_solve_ms") / args.steps
     phases = [sum(i["t_setup_phase_ms"][k] for i in infos) / args.steps for k in range(4)]
     peak, peak_kind = measured_peaks()
+    tet = hasattr(prob, "tets")
     kern = {
-        "k_res0_bsr": ("FP64 outer residual, level 0 block form", tot("t_res0_ms"), tot("n_res0"), tot("gb_res0")),
-        "k_relax_bsr": ("FP32 F-F-C Jacobi, level 0 block form", tot("t_relax0_ms"), tot("n_relax0"),
-                        tot("gb_relax0")),
+        ("k_res0_csr" if tet else "k_res0_bsr"): ("FP64 outer residual, level 0 " + ("CSR" if tet else "block form"),
+                                                  tot("t_res0_ms"), tot("n_res0"), tot("gb_res0")),
+        ("k_relax_f+k_relax_c level 0" if tet else "k_relax_bsr"): (
+            "FP32 F-F-C Jacobi, level 0 " + ("CF-split CSR; one unit = one V-cycle's three sweeps" if tet
+                                             else "block form; one unit = one V-cycle's three sweeps"),
+            tot("t_relax0_ms"), tot("n_relax0"), tot("gb_relax0")),
         "k_relax_f+k_relax_c": ("FP32 F-F-C Jacobi, levels >= 1 (CF-split CSR); one unit = every coarse "
                                 "level's sweeps of one V-cycle", tot("t_relaxc_ms"), tot("n_relaxc"), tot("gb_relaxc")),
     }

@@ -483,11 +483,13 @@ void vcycle_t(Hier &h, double *x64) {
             const int *act = l == 0 ? active : nullptr;
             bool tl = h.prof && l >= 1 && (int)h.evl.size() >= 2 * (l + 1);
             if (tl) rec_event(h.evl[2 * l], s);
+            if (h.prof && l == 0) { rec_event(h.ev[2], s); h.relax_timed = true; }
             for (int f = 0; f < fs; ++f, cur ^= 1)
                 relax_f<T>(L, (const T *)L.vb, bufs[cur], bufs[cur ^ 1], l == 0 && f == fs - 1 ? x64 : nullptr, act,
                            s);
             relax_c<T>(L, (const T *)L.vb, bufs[cur], (T *)L.vx, l == 0 ? x64 : nullptr, (const T *)L.vx, act, s);
             if (tl) rec_event(h.evl[2 * l + 1], s);
+            if (h.prof && l == 0) rec_event(h.ev[3], s);
         }
         L.vF = bufs[cur];
     }
@@ -571,6 +573,16 @@ __global__ void k_level_counts(int n, const int *rowptr, const int8_t *cf, unsig
     __syncthreads();
     if (threadIdx.x < 4) atomicAdd(&out[threadIdx.x], sh[threadIdx.x]);
 }
+// level 0 in CSR form, per matrix: [F rows, C rows, entries of F rows, entries of C rows]
+__global__ void k_level_counts_dir(int n, const int *rowptr, const int8_t *cf, const int *rowdir,
+                                   unsigned long long *out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || cf[i] == CF_COARSEST) return;
+    bool isC = cf[i] == CF_C;
+    unsigned long long *o = out + 4LL * rowdir[i];
+    atomicAdd(&o[isC ? 1 : 0], 1ULL);
+    atomicAdd(&o[isC ? 3 : 2], (unsigned long long)(rowptr[i + 1] - rowptr[i]));
+}
 }  // namespace
 
 void level0_bytes(Hier &h) {
@@ -600,7 +612,30 @@ void level0_bytes(Hier &h) {
         }
         dfree(cnt, s);
     }
-    if (!h.bsr0) return;
+    if (!h.bsr0) {
+        // CSR level 0 (tetrahedra): residual reads every entry (column + FP64 value), b
+        // and x, writes r; the relaxation counts as on coarse levels, except that the
+        // last F sweep and the C sweep add into x64 (read + write) instead of writing
+        Level &L = h.lev[0];
+        double sT = h.prm.precision == 1 ? 4.0 : 8.0;
+        unsigned long long *cnt = dmalloc<unsigned long long>(4 * h.ndir, s);
+        PR_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * 4 * h.ndir, s));
+        k_level_counts_dir<<<blocks_for(std::max(L.n, 1), BS), BS, 0, s>>>(L.n, L.rowptr, L.cf, L.rowdir, cnt);
+        PR_LAUNCH();
+        std::vector<unsigned long long> c(4 * h.ndir);
+        PR_CUDA(cudaMemcpyAsync(c.data(), cnt, sizeof(unsigned long long) * c.size(), cudaMemcpyDeviceToHost, s));
+        PR_CUDA(cudaStreamSynchronize(s));
+        dfree(cnt, s);
+        for (int m = 0; m < h.ndir; ++m) {
+            double nF = (double)c[4 * m], nC = (double)c[4 * m + 1], eF = (double)c[4 * m + 2],
+                   eC = (double)c[4 * m + 3];
+            h.bytes_res0[m] = (eF + eC) * 12 + (nF + nC) * (16 + sT);
+            double fpass = nF * (8 + 4 * sT) + eF * (4 + sT);
+            double cpass = nC * (8 + 3 * sT + 16) + eC * (4 + sT);
+            h.bytes_relax0[m] = h.prm.f_sweeps * fpass + nF * 16 + cpass;
+        }
+        return;
+    }
     int N = h.n0[0];
     unsigned long long *cnt = dmalloc<unsigned long long>(4 * h.ndir, s);
     PR_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * 4 * h.ndir, s));
