@@ -143,14 +143,6 @@ struct Hier {
     std::vector<cudaEvent_t> evl;      // 2 per level
     double t_relaxc = 0, gb_relaxc = 0, bytes_relaxc = 0;
     long long n_relaxc = 0;
-    // bottom of the V-cycle (levels >= lb, one cluster per matrix; lb = levels: none)
-    int lb = 0;
-    int n_bdirs = 0;
-    void *d_blev = nullptr, *d_bdir = nullptr;
-    int *d_bdirs = nullptr;
-    cudaEvent_t evb[2] = {nullptr, nullptr};
-    double t_bottom = 0;
-    long long n_bottom = 0;
     cudaGraphExec_t graph = nullptr;
     long long graph_kernels = 0;
     const double *graph_b = nullptr;
@@ -172,10 +164,6 @@ void alloc_cycle_vectors(Hier &h);
 void set_all_active(Hier &h);   // every matrix of the batch takes part in the next cycle
 void level0_bytes(Hier &h);   // fills bytes_res0 / bytes_relax0 (hex block form), bytes_relaxc
 void prof_enable(Hier &h);
-
-// bottom.cu
-void bottom_prepare(Hier &h);   // chooses h.lb, uploads per-level pointers and row ranges
-void bottom_cycle(Hier &h);     // levels >= lb of one V-cycle (vb of level lb given), on h.stream
 
 // assemble.cu
 void hex_assemble(int n, int ndir, const double *omega_d, const double *sigma_t, int *rowptr, int *col,

@@ -441,8 +441,7 @@ void vcycle_t(Hier &h, double *x64) {
     cudaStream_t s = h.stream;
     int NL = (int)h.lev.size();
     const int *active = h.active;
-    const int lb = std::min(h.lb, NL);   // levels >= lb run in the bottom kernel
-    for (int l = 0; l < lb; ++l) {
+    for (int l = 0; l < NL; ++l) {
         Level &L = h.lev[l];
         L.vF = L.vx;   // replaced by the F sweeps' buffer once the level relaxes
         if (l + 1 < NL) restrict_<T>(L, (const T *)L.vb, (T *)h.lev[l + 1].vb, s);
@@ -454,13 +453,7 @@ void vcycle_t(Hier &h, double *x64) {
         }
     }
     const int fs = h.prm.f_sweeps;
-    if (lb < NL) {
-        if (h.prof) rec_event(h.evb[0], s);
-        bottom_cycle(h);
-        if (h.prof) rec_event(h.evb[1], s);
-        for (int l = lb; l < NL; ++l) h.lev[l].vF = (fs & 1) ? h.lev[l].vxn : h.lev[l].vy;
-    }
-    for (int l = std::min(lb, NL - 1) - 1; l >= 0; --l) {
+    for (int l = NL - 2; l >= 0; --l) {
         Level &L = h.lev[l];
         const Level &C = h.lev[l + 1];
         const bool bsr = l == 0 && h.bsr0;
@@ -531,7 +524,6 @@ void alloc_cycle_vectors(Hier &h) {
     h.bnorm = dmalloc<double>(h.ndir, h.stream);
     h.active = dmalloc<int>(h.ndir, h.stream);
     set_all_active(h);
-    bottom_prepare(h);
 }
 
 void set_all_active(Hier &h) {
@@ -605,7 +597,7 @@ void level0_bytes(Hier &h) {
         // neighbour values are taken as cached (the vector is far smaller than L2).
         double sT = h.prm.precision == 1 ? 4.0 : 8.0;
         unsigned long long *cnt = dmalloc<unsigned long long>(4, s);
-        for (size_t l = 1; l + 1 < h.lev.size() && (int)l < h.lb; ++l) {
+        for (size_t l = 1; l + 1 < h.lev.size(); ++l) {
             Level &L = h.lev[l];
             if (L.n == 0) continue;
             PR_CUDA(cudaMemsetAsync(cnt, 0, 4 * sizeof(unsigned long long), s));
@@ -671,7 +663,6 @@ void prof_enable(Hier &h) {
     for (auto &e : h.ev) PR_CUDA(cudaEventCreate(&e));
     h.evl.assign(2 * h.lev.size(), nullptr);
     for (auto &e : h.evl) PR_CUDA(cudaEventCreate(&e));
-    for (auto &e : h.evb) PR_CUDA(cudaEventCreate(&e));
     h.prof = true;
 }
 

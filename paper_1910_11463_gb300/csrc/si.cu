@@ -141,7 +141,7 @@ BatchSolve solve_batch(Hier &h, const double *b, double *x, double tol, int maxi
             // coarse levels run for every direction of the batch
             double tl = 0;
             int nl = 0;
-            for (size_t l = 1; l + 1 < h.lev.size() && (int)l < h.lb; ++l) {
+            for (size_t l = 1; l + 1 < h.lev.size(); ++l) {
                 if (!h.lev[l].n) continue;
                 float m2 = 0;
                 PR_CUDA(cudaEventElapsedTime(&m2, h.evl[2 * l], h.evl[2 * l + 1]));
@@ -153,11 +153,6 @@ BatchSolve solve_batch(Hier &h, const double *b, double *x, double tol, int maxi
                 h.n_relaxc += 1;
                 h.gb_relaxc += h.bytes_relaxc * 1e-9;
             }
-        }
-        if (relax && h.lb < (int)h.lev.size()) {
-            PR_CUDA(cudaEventElapsedTime(&ms, h.evb[0], h.evb[1]));
-            h.t_bottom += ms;
-            h.n_bottom += 1;
         }
         if (relax && h.relax_timed) {
             PR_CUDA(cudaEventElapsedTime(&ms, h.ev[2], h.ev[3]));
@@ -332,12 +327,9 @@ Hier::~Hier() {
         if (e) cudaEventDestroy(e);
     for (auto &e : evl)
         if (e) cudaEventDestroy(e);
-    for (auto &e : evb)
-        if (e) cudaEventDestroy(e);
     if (stream) {
         for (auto &L : lev) free_level(L, stream);
-        void *ptrs[] = {bsr64, bsr32, dsign, partials, rnorm, bnorm, rnorm0, active, d_err, d_n0, d_row00,
-                        d_blev, d_bdir, d_bdirs};
+        void *ptrs[] = {bsr64, bsr32, dsign, partials, rnorm, bnorm, rnorm0, active, d_err, d_n0, d_row00};
         for (void *p : ptrs) dfree(p, stream);
         cudaStreamSynchronize(stream);
         cudaStreamDestroy(stream);
