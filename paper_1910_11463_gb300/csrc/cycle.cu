@@ -13,7 +13,6 @@
 #include <type_traits>
 
 #include "common.cuh"
-#include "tile_dot.cuh"
 
 namespace pr {
 
@@ -206,6 +205,38 @@ __global__ void k_sumsq_rows(const int *row0, const int *nrow, const double *v, 
     if (threadIdx.x == 0) partials[(long long)m * maxblk + blockIdx.x] = tot;
 }
 
+// ---- sparse row dot products ----------------------------------------------------
+// Row k of a CSR-like store (ptr, col, val) times the vector in, lanes g, g+G, ...
+// of a G-lane group, two entries in flight per lane; entries are streamed
+// (evict-first) so the gathered vector stays in L2.  Per lane the terms are added
+// in ascending entry order.
+template <class T, int G>
+__device__ __forceinline__ T row_dot(int k, int g, const int *sptr, const int *scol, const T *sval, const T *in) {
+    int p = sptr[k] + g, e = sptr[k + 1];
+    T acc = T(0);
+    for (; p + G < e; p += 2 * G) {
+        int c0 = __ldcs(scol + p), c1 = __ldcs(scol + p + G);
+        T v0 = __ldcs(sval + p), v1 = __ldcs(sval + p + G);
+        acc += v0 * in[c0];
+        acc += v1 * in[c1];
+    }
+    if (p < e) acc += __ldcs(sval + p) * in[__ldcs(scol + p)];
+    return acc;
+}
+
+// ---- restriction ---------------------------------------------------------------
+template <class T, int G>
+__global__ void __launch_bounds__(BS) k_restrict(int nc, const int *cpts, const int *zrowptr, const int *zcol,
+                                                 const T *zval, const T *bf, T *bc) {
+    long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int ic = (int)(tid / G);
+    int g = threadIdx.x % G;
+    T acc = ic < nc ? row_dot<T, G>(ic, g, zrowptr, zcol, zval, bf) : T(0);
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, G);
+    if (ic < nc && g == 0) bc[ic] = acc + bf[cpts[ic]];
+}
+
 // ---- prolongation y = P x_c --------------------------------------------------
 // The coarse vector of level l+1 lives in two buffers after its relaxation: F rows
 // in xcF, C and coarsest rows in xc.  C rows of y are also written to y2 (the other
@@ -224,23 +255,59 @@ __global__ void k_prolong(int n, const int8_t *cf, const int *pmap, const int8_t
     if (y2 && c == CF_C) y2[i] = v;
 }
 
+// F sweep over split positions [0, nF): out = in + dinv (b - A in) on F rows; with
+// fold (the last F sweep of a level-0 correction) x64 += the new F values as well
+template <class T, int G>
+__global__ void __launch_bounds__(BS) k_relax_f(int nF, const int *srow, const int *sptr, const int *scol,
+                                                const T *sval, const T *dinv, const T *b, const T *in, T *out,
+                                                double *fold, const int *active, const int *rowdir) {
+    long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int k = (int)(tid / G);
+    int g = threadIdx.x % G;
+    bool valid = k < nF;
+    int i = valid ? srow[k] : 0;
+    if (valid && active && !active[rowdir[i]]) valid = false;
+    T acc = valid ? row_dot<T, G>(k, g, sptr, scol, sval, in) : T(0);
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, G);
+    if (!valid || g != 0) return;
+    T v = in[i] + dinv[i] * (b[i] - acc);
+    out[i] = v;
+    if (fold) fold[i] += (double)v;
+}
+
+// C sweep over split positions [k0, k1): C rows relax into out (non-final) or into
+// x64 (final); coarsest rows (final only) add the coarsest solution xco
+template <class T, int G, bool FINAL>
+__global__ void __launch_bounds__(BS) k_relax_c(int k0, int k1, int kX, const int *srow, const int *sptr,
+                                                const int *scol, const T *sval, const T *dinv, const T *b,
+                                                const T *in, T *out, double *x64, const T *xco, const int *active,
+                                                const int *rowdir) {
+    long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int k = k0 + (int)(tid / G);
+    int g = threadIdx.x % G;
+    bool valid = k < k1;
+    int i = valid ? srow[k] : 0;
+    if (valid && active && !active[rowdir[i]]) valid = false;
+    bool work = valid && k < kX;
+    T acc = work ? row_dot<T, G>(k, g, sptr, scol, sval, in) : T(0);
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, G);
+    if (!valid || g != 0) return;
+    if (!work) {
+        if (FINAL) x64[i] += (double)xco[i];
+        return;
+    }
+    T v = in[i] + dinv[i] * (b[i] - acc);
+    if (FINAL) x64[i] += (double)v;
+    else out[i] = v;
+}
+
 // single-level hierarchies: x64 += the coarsest solution on active rows
 template <class T>
 __global__ void k_fold_coarsest(int n, const T *xco, double *x64, const int *active, const int *rowdir) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || (active && !active[rowdir[i]])) return;
-    x64[i] += (double)xco[i];
-}
-
-// final correction at a CSR level 0: x64 += the coarsest solution on the rows of
-// matrices that end there (split positions [kX, n))
-template <class T>
-__global__ void k_fold_split(int kX, int n, const int *srow, const T *xco, double *x64, const int *active,
-                             const int *rowdir) {
-    int k = kX + blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    int i = srow[k];
-    if (active && !active[rowdir[i]]) return;
     x64[i] += (double)xco[i];
 }
 
@@ -311,92 +378,62 @@ int pick_group(long long nnz, int n) {
     return 16;
 }
 
-template <class T, int G, int MODE>
-void launch_tile_g(const tile::Job<T> &j, int sms, cudaStream_t s) {
-    const int rows = j.k1 - j.k0;
-    const int ntiles = (rows + tile::BS / G - 1) / (tile::BS / G);
-    const int grid = std::min(ntiles, sms * tile::CTAS_PER_SM);
-    tile::k_tile_dot<T, G, MODE><<<grid, tile::BS, 0, s>>>(j, ntiles);
+// F sweep (fold: x64 on the last level-0 sweep) and C sweep (final: into x64)
+template <class T>
+void relax_f(const Level &L, const T *b, const T *in, T *out, double *fold, const int *active, cudaStream_t s) {
+    if (L.nF == 0) return;
+    const T *sv = (const T *)L.sval;
+    const T *dv = lv_dinv<T>(L);
+#define PR_RELAX_F(G)                                                                                       \
+    k_relax_f<T, G><<<blocks_for((long long)L.nF * G, BS), BS, 0, s>>>(L.nF, L.srow, L.sptr, L.scol, sv, dv, b, \
+                                                                       in, out, fold, active, L.rowdir)
+    switch (pick_group(L.eF, L.nF)) {
+        case 1: PR_RELAX_F(1); break;
+        case 4: PR_RELAX_F(4); break;
+        case 8: PR_RELAX_F(8); break;
+        default: PR_RELAX_F(16); break;
+    }
+#undef PR_RELAX_F
     PR_LAUNCH();
 }
 
-// G lanes per row from the rows' mean length
-template <class T, int MODE>
-void launch_tile(const tile::Job<T> &j, long long entries, int sms, cudaStream_t s) {
-    if (j.k1 <= j.k0) return;
-    switch (pick_group(entries, j.k1 - j.k0)) {
-        case 1: launch_tile_g<T, 1, MODE>(j, sms, s); break;
-        case 4: launch_tile_g<T, 4, MODE>(j, sms, s); break;
-        case 8: launch_tile_g<T, 8, MODE>(j, sms, s); break;
-        default: launch_tile_g<T, 16, MODE>(j, sms, s); break;
-    }
-}
-
 template <class T>
-tile::Job<T> sweep_job(const Hier &h, const Level &L, const T *b, const T *in, int k0, int k1) {
-    tile::Job<T> j{};
-    j.k0 = k0;
-    j.k1 = k1;
-    j.nnz = L.nnz;
-    j.ptr = L.sptr;
-    j.col = L.scol;
-    j.val = (const T *)L.sval;
-    j.in = in;
-    j.srow = L.srow;
-    j.dinv = lv_dinv<T>(L);
-    j.b = b;
-    j.rowdir = L.rowdir;
-    j.err = h.d_err;
-    return j;
-}
-
-// F sweep over the F rows (fold: x64 += the new values, the last level-0 sweep)
-template <class T>
-void relax_f(const Hier &h, const Level &L, const T *b, const T *in, T *out, double *fold, const int *active,
+void relax_c(const Level &L, const T *b, const T *in, T *out, double *x64, const T *xco, const int *active,
              cudaStream_t s) {
-    tile::Job<T> j = sweep_job<T>(h, L, b, in, 0, L.nF);
-    j.out = out;
-    j.x64 = fold;
-    j.active = active;
-    launch_tile<T, tile::F_SWEEP>(j, L.eF, h.sms, s);
-}
-
-// C sweep over the C rows into out, or (final) into x64 together with the
-// coarsest rows of matrices that end on this level
-template <class T>
-void relax_c(const Hier &h, const Level &L, const T *b, const T *in, T *out, double *x64, const T *xco,
-             const int *active, cudaStream_t s) {
-    const int kX = L.nF + L.nC;
-    tile::Job<T> j = sweep_job<T>(h, L, b, in, L.nF, kX);
-    j.out = out;
-    j.x64 = x64;
-    j.active = active;
-    if (x64) {
-        launch_tile<T, tile::C_SWEEP_FINAL>(j, L.eC, h.sms, s);
-        if (L.n > kX) {
-            k_fold_split<T><<<blocks_for(L.n - kX, BS), BS, 0, s>>>(kX, L.n, L.srow, xco, x64, active, L.rowdir);
-            PR_LAUNCH();
-        }
-    } else {
-        launch_tile<T, tile::C_SWEEP>(j, L.eC, h.sms, s);
+    const int k0 = L.nF, kX = L.nF + L.nC, k1 = x64 ? L.n : kX;
+    if (k1 <= k0) return;
+    const T *sv = (const T *)L.sval;
+    const T *dv = lv_dinv<T>(L);
+#define PR_RELAX_C(G)                                                                                          \
+    do {                                                                                                      \
+        long long nb = blocks_for((long long)(k1 - k0) * G, BS);                                              \
+        if (x64)                                                                                              \
+            k_relax_c<T, G, true><<<nb, BS, 0, s>>>(k0, k1, kX, L.srow, L.sptr, L.scol, sv, dv, b, in, nullptr, \
+                                                    x64, xco, active, L.rowdir);                              \
+        else                                                                                                  \
+            k_relax_c<T, G, false><<<nb, BS, 0, s>>>(k0, k1, kX, L.srow, L.sptr, L.scol, sv, dv, b, in, out,    \
+                                                     nullptr, xco, active, L.rowdir);                         \
+    } while (0)
+    switch (pick_group(L.eC, L.nC)) {
+        case 1: PR_RELAX_C(1); break;
+        case 4: PR_RELAX_C(4); break;
+        case 8: PR_RELAX_C(8); break;
+        default: PR_RELAX_C(16); break;
     }
+#undef PR_RELAX_C
+    PR_LAUNCH();
 }
 
-// b_c = Z b_F + b_C: one row of Z per coarse point
 template <class T>
-void restrict_(const Hier &h, const Level &L, const T *bf, T *bc, cudaStream_t s) {
-    tile::Job<T> j{};
-    j.k0 = 0;
-    j.k1 = L.nc;
-    j.nnz = L.nnzZ;
-    j.ptr = L.zrowptr;
-    j.col = L.zcol;
-    j.val = lv_zval<T>(L);
-    j.in = bf;
-    j.out = bc;
-    j.cpts = L.cpts;
-    j.err = h.d_err;
-    launch_tile<T, tile::RESTRICT>(j, L.nnzZ, h.sms, s);
+void restrict_(const Level &L, const T *bf, T *bc, cudaStream_t s) {
+    int G = pick_group(L.nnzZ, L.nc);
+    switch (G) {
+        case 1: k_restrict<T, 1><<<blocks_for((long long)L.nc, BS), BS, 0, s>>>(L.nc, L.cpts, L.zrowptr, L.zcol, lv_zval<T>(L), bf, bc); break;
+        case 4: k_restrict<T, 4><<<blocks_for((long long)L.nc * 4, BS), BS, 0, s>>>(L.nc, L.cpts, L.zrowptr, L.zcol, lv_zval<T>(L), bf, bc); break;
+        case 8: k_restrict<T, 8><<<blocks_for((long long)L.nc * 8, BS), BS, 0, s>>>(L.nc, L.cpts, L.zrowptr, L.zcol, lv_zval<T>(L), bf, bc); break;
+        default: k_restrict<T, 16><<<blocks_for((long long)L.nc * 16, BS), BS, 0, s>>>(L.nc, L.cpts, L.zrowptr, L.zcol, lv_zval<T>(L), bf, bc); break;
+    }
+    PR_LAUNCH();
 }
 
 template <class T>
@@ -407,7 +444,7 @@ void vcycle_t(Hier &h, double *x64) {
     for (int l = 0; l < NL; ++l) {
         Level &L = h.lev[l];
         L.vF = L.vx;   // replaced by the F sweeps' buffer once the level relaxes
-        if (l + 1 < NL) restrict_<T>(h, L, (const T *)L.vb, (T *)h.lev[l + 1].vb, s);
+        if (l + 1 < NL) restrict_<T>(L, (const T *)L.vb, (T *)h.lev[l + 1].vb, s);
         if (L.n_cseg) {
             k_coarsest<T><<<L.n_cseg, 256, 0, s>>>(L.d_cseg_row0, L.d_cseg_n, L.d_cseg_s0, L.sptr, L.scol,
                                                    (const T *)L.sval, lv_dinv<T>(L), (const T *)L.vb, (T *)L.vx,
@@ -448,10 +485,9 @@ void vcycle_t(Hier &h, double *x64) {
             if (tl) rec_event(h.evl[2 * l], s);
             if (h.prof && l == 0) { rec_event(h.ev[2], s); h.relax_timed = true; }
             for (int f = 0; f < fs; ++f, cur ^= 1)
-                relax_f<T>(h, L, (const T *)L.vb, bufs[cur], bufs[cur ^ 1], l == 0 && f == fs - 1 ? x64 : nullptr,
-                           act, s);
-            relax_c<T>(h, L, (const T *)L.vb, bufs[cur], (T *)L.vx, l == 0 ? x64 : nullptr, (const T *)L.vx, act,
-                       s);
+                relax_f<T>(L, (const T *)L.vb, bufs[cur], bufs[cur ^ 1], l == 0 && f == fs - 1 ? x64 : nullptr, act,
+                           s);
+            relax_c<T>(L, (const T *)L.vb, bufs[cur], (T *)L.vx, l == 0 ? x64 : nullptr, (const T *)L.vx, act, s);
             if (tl) rec_event(h.evl[2 * l + 1], s);
             if (h.prof && l == 0) rec_event(h.ev[3], s);
         }
@@ -488,9 +524,6 @@ void alloc_cycle_vectors(Hier &h) {
     h.bnorm = dmalloc<double>(h.ndir, h.stream);
     h.active = dmalloc<int>(h.ndir, h.stream);
     set_all_active(h);
-    int dev = 0;
-    PR_CUDA(cudaGetDevice(&dev));
-    PR_CUDA(cudaDeviceGetAttribute(&h.sms, cudaDevAttrMultiProcessorCount, dev));
 }
 
 void set_all_active(Hier &h) {

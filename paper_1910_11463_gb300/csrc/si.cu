@@ -187,10 +187,7 @@ BatchSolve solve_batch(Hier &h, const double *b, double *x, double tol, int maxi
         }
     }
     PR_CUDA(cudaMemcpyAsync(rn.data(), h.rnorm, sizeof(double) * nd, cudaMemcpyDeviceToHost, s));
-    int derr = 0;
-    PR_CUDA(cudaMemcpyAsync(&derr, h.d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     PR_CUDA(cudaStreamSynchronize(s));
-    if (derr & DERR_TIMEOUT) fail(PAIR_ERR_DEVICE_TIMEOUT, "a V-cycle kernel gave up waiting for its tile copies");
     BatchSolve out;
     out.iters = k;
     for (int d = 0; d < nd; ++d) {
