@@ -206,23 +206,34 @@ __global__ void k_sumsq_rows(const int *row0, const int *nrow, const double *v, 
 }
 
 // ---- sparse row dot products ----------------------------------------------------
-// Row k of a CSR-like store (ptr, col, val) times the vector in, lanes g, g+G, ...
-// of a G-lane group, two entries in flight per lane; entries are streamed
+// Row [p0, p1) of a CSR-like store (col, val) times the vector in, lanes g, g+G, ...
+// of a G-lane group.  The coarse sweeps are latency-bound (a chain of dependent
+// loads per thread: row offsets -> entries -> gathered values), so each lane
+// issues its first U entries' loads together, then their U gathers together, and
+// only then adds; longer rows continue in a loop.  Entries are streamed
 // (evict-first) so the gathered vector stays in L2.  Per lane the terms are added
 // in ascending entry order.
-template <class T, int G>
-__device__ __forceinline__ T row_dot(int k, int g, const int *sptr, const int *scol, const T *sval, const T *in) {
-    int p = sptr[k] + g, e = sptr[k + 1];
-    T acc = T(0);
-    for (; p + G < e; p += 2 * G) {
-        int c0 = __ldcs(scol + p), c1 = __ldcs(scol + p + G);
-        T v0 = __ldcs(sval + p), v1 = __ldcs(sval + p + G);
-        acc += v0 * in[c0];
-        acc += v1 * in[c1];
+template <class T, int G, int U>
+__device__ __forceinline__ T row_dot(int p0, int p1, int g, const int *col, const T *val, const T *in) {
+    int c[U];
+    T v[U], x[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int p = p0 + g + u * G;
+        c[u] = p < p1 ? __ldcs(col + p) : 0;
+        v[u] = p < p1 ? __ldcs(val + p) : T(0);
     }
-    if (p < e) acc += __ldcs(sval + p) * in[__ldcs(scol + p)];
+#pragma unroll
+    for (int u = 0; u < U; ++u) x[u] = p0 + g + u * G < p1 ? in[c[u]] : T(0);
+    T acc = T(0);
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+        if (p0 + g + u * G < p1) acc += v[u] * x[u];
+    for (int p = p0 + g + U * G; p < p1; p += G) acc += __ldcs(val + p) * in[__ldcs(col + p)];
     return acc;
 }
+
+constexpr int ROW_U = 4;   // entries per lane issued together
 
 // ---- restriction ---------------------------------------------------------------
 template <class T, int G>
@@ -231,10 +242,12 @@ __global__ void __launch_bounds__(BS) k_restrict(int nc, const int *cpts, const 
     long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     int ic = (int)(tid / G);
     int g = threadIdx.x % G;
-    T acc = ic < nc ? row_dot<T, G>(ic, g, zrowptr, zcol, zval, bf) : T(0);
+    const bool ok = ic < nc;
+    const T bself = ok && g == 0 ? bf[cpts[ic]] : T(0);   // issued before the dot product
+    T acc = ok ? row_dot<T, G, ROW_U>(zrowptr[ic], zrowptr[ic + 1], g, zcol, zval, bf) : T(0);
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, G);
-    if (ic < nc && g == 0) bc[ic] = acc + bf[cpts[ic]];
+    if (ok && g == 0) bc[ic] = acc + bself;
 }
 
 // ---- prolongation y = P x_c --------------------------------------------------
@@ -267,11 +280,14 @@ __global__ void __launch_bounds__(BS) k_relax_f(int nF, const int *srow, const i
     bool valid = k < nF;
     int i = valid ? srow[k] : 0;
     if (valid && active && !active[rowdir[i]]) valid = false;
-    T acc = valid ? row_dot<T, G>(k, g, sptr, scol, sval, in) : T(0);
+    // the row's own operands are loaded before the dot product (shorter chain)
+    T xi = T(0), di = T(0), bi = T(0);
+    if (valid && g == 0) { xi = in[i]; di = dinv[i]; bi = b[i]; }
+    T acc = valid ? row_dot<T, G, ROW_U>(sptr[k], sptr[k + 1], g, scol, sval, in) : T(0);
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, G);
     if (!valid || g != 0) return;
-    T v = in[i] + dinv[i] * (b[i] - acc);
+    T v = xi + di * (bi - acc);
     out[i] = v;
     if (fold) fold[i] += (double)v;
 }
@@ -290,7 +306,9 @@ __global__ void __launch_bounds__(BS) k_relax_c(int k0, int k1, int kX, const in
     int i = valid ? srow[k] : 0;
     if (valid && active && !active[rowdir[i]]) valid = false;
     bool work = valid && k < kX;
-    T acc = work ? row_dot<T, G>(k, g, sptr, scol, sval, in) : T(0);
+    T xi = T(0), di = T(0), bi = T(0);
+    if (work && g == 0) { xi = in[i]; di = dinv[i]; bi = b[i]; }
+    T acc = work ? row_dot<T, G, ROW_U>(sptr[k], sptr[k + 1], g, scol, sval, in) : T(0);
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, G);
     if (!valid || g != 0) return;
@@ -298,7 +316,7 @@ __global__ void __launch_bounds__(BS) k_relax_c(int k0, int k1, int kX, const in
         if (FINAL) x64[i] += (double)xco[i];
         return;
     }
-    T v = in[i] + dinv[i] * (b[i] - acc);
+    T v = xi + di * (bi - acc);
     if (FINAL) x64[i] += (double)v;
     else out[i] = v;
 }
@@ -370,11 +388,12 @@ const float *lv_zval<float>(const Level &L) { return L.zval32; }
 template <>
 const double *lv_zval<double>(const Level &L) { return L.zval; }
 
+// G lanes per row so that a mean row fits in the G*ROW_U entries a group issues at once
 int pick_group(long long nnz, int n) {
     double avg = n > 0 ? (double)nnz / n : 0;
-    if (avg <= 6) return 1;
-    if (avg <= 14) return 4;
-    if (avg <= 40) return 8;
+    if (avg <= 1 * ROW_U) return 1;
+    if (avg <= 4 * ROW_U) return 4;
+    if (avg <= 8 * ROW_U) return 8;
     return 16;
 }
 
