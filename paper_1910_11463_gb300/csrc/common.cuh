@@ -73,6 +73,16 @@ long long scan_exclusive(const int *in, int *out, int n, cudaStream_t s, bool wa
 // ---------------------------------------------------------------------------
 enum : int8_t { CF_F = 0, CF_C = 1, CF_COARSEST = 2 };
 
+// Sliced ELL copy of a set of rows (32 rows per slice, rows ordered by decreasing
+// length inside windows of 256): position q holds row[q] (-1: empty) with len[q]
+// entries at ptr[q / 32] + (q % 32) + 32 j, j < len[q]
+struct Sell {
+    int nrows = 0, npos = 0;
+    long long nnz = 0;   // stored slots including padding
+    int *ptr = nullptr, *row = nullptr, *len = nullptr, *col = nullptr;
+    void *val = nullptr;
+};
+
 struct Level {
     int n = 0;
     long long nnz = 0;
@@ -87,7 +97,6 @@ struct Level {
     int *cpts = nullptr;      // fine row of every coarse point
     int *zrowptr = nullptr, *zcol = nullptr;
     double *zval = nullptr;
-    float *zval32 = nullptr;
     long long nnzZ = 0;
     // per matrix slot (host): first row, rows, coarse points, coarsest flag, stats
     std::vector<int> row0, nrows, ncdir, nnzdir, nnzZdir, singular;
@@ -97,14 +106,15 @@ struct Level {
     // coarsest segments (device): first row and rows of each matrix that ends here
     int n_cseg = 0;
     int *d_cseg_row0 = nullptr, *d_cseg_n = nullptr;
-    // CF-split copy of the rows for relaxation: rows in the order [F | C | coarsest],
-    // ascending within each group, with their entries stored contiguously in that
-    // order in the V-cycle's precision (sptr indexes the split order)
+    // CF split for the V-cycle: srow lists the rows in the order [F | C | coarsest],
+    // ascending within each group; sF, sC: SELL copies of the F and C rows, sZ of Z
+    // (values in the cycle precision); sptr/scol/sval: CSR copy of the coarsest rows
+    // in split order, d_cseg_s0: each coarsest segment's first position in it
     int nF = 0, nC = 0;
-    long long eF = 0, eC = 0;                  // entries of the F and C groups
     int *srow = nullptr, *sptr = nullptr, *scol = nullptr;
     void *sval = nullptr;
-    int *d_cseg_s0 = nullptr;                  // split position of each coarsest segment
+    int *d_cseg_s0 = nullptr;
+    Sell sF, sC, sZ;
     // V-cycle work vectors (precision of the hierarchy); vF is the buffer (vy or vxn)
     // that holds the F rows after the last F sweep, C rows are then in vx
     void *vb = nullptr, *vx = nullptr, *vxn = nullptr, *vy = nullptr;

@@ -205,49 +205,84 @@ __global__ void k_sumsq_rows(const int *row0, const int *nrow, const double *v, 
     if (threadIdx.x == 0) partials[(long long)m * maxblk + blockIdx.x] = tot;
 }
 
-// ---- sparse row dot products ----------------------------------------------------
-// Row [p0, p1) of a CSR-like store (col, val) times the vector in, lanes g, g+G, ...
-// of a G-lane group.  The coarse sweeps are latency-bound (a chain of dependent
-// loads per thread: row offsets -> entries -> gathered values), so each lane
-// issues its first U entries' loads together, then their U gathers together, and
-// only then adds; longer rows continue in a loop.  Entries are streamed
-// (evict-first) so the gathered vector stays in L2.  Per lane the terms are added
-// in ascending entry order.
-template <class T, int G, int U>
-__device__ __forceinline__ T row_dot(int p0, int p1, int g, const int *col, const T *val, const T *in) {
-    int c[U];
-    T v[U], x[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-        const int p = p0 + g + u * G;
-        c[u] = p < p1 ? __ldcs(col + p) : 0;
-        v[u] = p < p1 ? __ldcs(val + p) : T(0);
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) x[u] = p0 + g + u * G < p1 ? in[c[u]] : T(0);
+// ---- sparse row dot products on SELL copies --------------------------------------
+// One thread per row.  The coarse sweeps are latency-bound (dependent loads per
+// thread), so a thread issues the loads of SELL_U entries together, then their
+// SELL_U gathers, and only then adds; entry addresses need nothing but the slice
+// offset, and a warp's loads of one entry index are one contiguous 128-byte line.
+// Entries are streamed (evict-first) so the gathered vector stays in L2.  Terms are
+// added in ascending entry order.
+constexpr int SELL_U = 8;
+
+template <class T>
+__device__ __forceinline__ T sell_dot(int base, int len, const int *col, const T *val, const T *in) {
     T acc = T(0);
+    for (int j0 = 0; j0 < len; j0 += SELL_U) {
+        int c[SELL_U];
+        T v[SELL_U], x[SELL_U];
 #pragma unroll
-    for (int u = 0; u < U; ++u)
-        if (p0 + g + u * G < p1) acc += v[u] * x[u];
-    for (int p = p0 + g + U * G; p < p1; p += G) acc += __ldcs(val + p) * in[__ldcs(col + p)];
+        for (int u = 0; u < SELL_U; ++u) {
+            const bool ok = j0 + u < len;
+            c[u] = ok ? __ldcs(col + base + 32 * (j0 + u)) : 0;
+            v[u] = ok ? __ldcs(val + base + 32 * (j0 + u)) : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < SELL_U; ++u) x[u] = j0 + u < len ? in[c[u]] : T(0);
+#pragma unroll
+        for (int u = 0; u < SELL_U; ++u)
+            if (j0 + u < len) acc += v[u] * x[u];
+    }
     return acc;
 }
 
-constexpr int ROW_U = 4;   // entries per lane issued together
+enum SellMode : int { SM_F = 0, SM_C = 1, SM_C_FINAL = 2, SM_RESTRICT = 3 };
 
-// ---- restriction ---------------------------------------------------------------
-template <class T, int G>
-__global__ void __launch_bounds__(BS) k_restrict(int nc, const int *cpts, const int *zrowptr, const int *zcol,
-                                                 const T *zval, const T *bf, T *bc) {
-    long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    int ic = (int)(tid / G);
-    int g = threadIdx.x % G;
-    const bool ok = ic < nc;
-    const T bself = ok && g == 0 ? bf[cpts[ic]] : T(0);   // issued before the dot product
-    T acc = ok ? row_dot<T, G, ROW_U>(zrowptr[ic], zrowptr[ic + 1], g, zcol, zval, bf) : T(0);
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, G);
-    if (ok && g == 0) bc[ic] = acc + bself;
+template <class T>
+struct SellJob {
+    int npos;
+    const int *ptr, *row, *len, *col;
+    const T *val;
+    const T *in;          // vector the rows multiply
+    const T *dinv, *b;    // sweeps
+    T *out;
+    double *x64;          // F sweep: optional fold; final C sweep: target
+    const int *cpts;      // restriction: fine row of each coarse point
+    const int *active, *rowdir;
+};
+
+// F sweep:   out[i] = in[i] + dinv[i] (b[i] - A_i in)        (x64[i] += it, if given)
+// C sweep:   same into out, or (final) x64[i] += it
+// restrict:  out[ic] = Z_ic in + in[cpts[ic]]
+template <class T, int MODE>
+__global__ void __launch_bounds__(BS) k_sell(SellJob<T> j) {
+    const int q = blockIdx.x * BS + threadIdx.x;
+    if (q >= j.npos) return;
+    const int r = j.row[q];
+    if (r < 0) return;
+    if (MODE != SM_RESTRICT && j.active && !j.active[j.rowdir[r]]) return;
+    const int len = j.len[q];
+    const int base = j.ptr[q >> 5] + (q & 31);
+    // the row's own operands are loaded before the dot product (shorter chain)
+    T own, di = T(0), bi = T(0);
+    if (MODE == SM_RESTRICT) {
+        own = j.in[j.cpts[r]];
+    } else {
+        own = j.in[r];
+        di = j.dinv[r];
+        bi = j.b[r];
+    }
+    const T acc = sell_dot<T>(base, len, j.col, j.val, j.in);
+    if (MODE == SM_RESTRICT) {
+        j.out[r] = acc + own;
+        return;
+    }
+    const T v = own + di * (bi - acc);
+    if (MODE == SM_C_FINAL) {
+        j.x64[r] += (double)v;
+    } else {
+        j.out[r] = v;
+        if (MODE == SM_F && j.x64) j.x64[r] += (double)v;
+    }
 }
 
 // ---- prolongation y = P x_c --------------------------------------------------
@@ -268,64 +303,23 @@ __global__ void k_prolong(int n, const int8_t *cf, const int *pmap, const int8_t
     if (y2 && c == CF_C) y2[i] = v;
 }
 
-// F sweep over split positions [0, nF): out = in + dinv (b - A in) on F rows; with
-// fold (the last F sweep of a level-0 correction) x64 += the new F values as well
-template <class T, int G>
-__global__ void __launch_bounds__(BS) k_relax_f(int nF, const int *srow, const int *sptr, const int *scol,
-                                                const T *sval, const T *dinv, const T *b, const T *in, T *out,
-                                                double *fold, const int *active, const int *rowdir) {
-    long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    int k = (int)(tid / G);
-    int g = threadIdx.x % G;
-    bool valid = k < nF;
-    int i = valid ? srow[k] : 0;
-    if (valid && active && !active[rowdir[i]]) valid = false;
-    // the row's own operands are loaded before the dot product (shorter chain)
-    T xi = T(0), di = T(0), bi = T(0);
-    if (valid && g == 0) { xi = in[i]; di = dinv[i]; bi = b[i]; }
-    T acc = valid ? row_dot<T, G, ROW_U>(sptr[k], sptr[k + 1], g, scol, sval, in) : T(0);
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, G);
-    if (!valid || g != 0) return;
-    T v = xi + di * (bi - acc);
-    out[i] = v;
-    if (fold) fold[i] += (double)v;
-}
-
-// C sweep over split positions [k0, k1): C rows relax into out (non-final) or into
-// x64 (final); coarsest rows (final only) add the coarsest solution xco
-template <class T, int G, bool FINAL>
-__global__ void __launch_bounds__(BS) k_relax_c(int k0, int k1, int kX, const int *srow, const int *sptr,
-                                                const int *scol, const T *sval, const T *dinv, const T *b,
-                                                const T *in, T *out, double *x64, const T *xco, const int *active,
-                                                const int *rowdir) {
-    long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    int k = k0 + (int)(tid / G);
-    int g = threadIdx.x % G;
-    bool valid = k < k1;
-    int i = valid ? srow[k] : 0;
-    if (valid && active && !active[rowdir[i]]) valid = false;
-    bool work = valid && k < kX;
-    T xi = T(0), di = T(0), bi = T(0);
-    if (work && g == 0) { xi = in[i]; di = dinv[i]; bi = b[i]; }
-    T acc = work ? row_dot<T, G, ROW_U>(sptr[k], sptr[k + 1], g, scol, sval, in) : T(0);
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, G);
-    if (!valid || g != 0) return;
-    if (!work) {
-        if (FINAL) x64[i] += (double)xco[i];
-        return;
-    }
-    T v = xi + di * (bi - acc);
-    if (FINAL) x64[i] += (double)v;
-    else out[i] = v;
-}
-
 // single-level hierarchies: x64 += the coarsest solution on active rows
 template <class T>
 __global__ void k_fold_coarsest(int n, const T *xco, double *x64, const int *active, const int *rowdir) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || (active && !active[rowdir[i]])) return;
+    x64[i] += (double)xco[i];
+}
+
+// final correction at a CSR level 0: x64 += the coarsest solution on the rows of
+// matrices that end there (split positions [kX, n))
+template <class T>
+__global__ void k_fold_split(int kX, int n, const int *srow, const T *xco, double *x64, const int *active,
+                             const int *rowdir) {
+    int k = kX + blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int i = srow[k];
+    if (active && !active[rowdir[i]]) return;
     x64[i] += (double)xco[i];
 }
 
@@ -381,78 +375,66 @@ template <>
 const float *lv_dinv<float>(const Level &L) { return L.dinv32; }
 template <>
 const double *lv_dinv<double>(const Level &L) { return L.dinv; }
-template <class T>
-const T *lv_zval(const Level &L);
-template <>
-const float *lv_zval<float>(const Level &L) { return L.zval32; }
-template <>
-const double *lv_zval<double>(const Level &L) { return L.zval; }
-
-// G lanes per row so that a mean row fits in the G*ROW_U entries a group issues at once
-int pick_group(long long nnz, int n) {
-    double avg = n > 0 ? (double)nnz / n : 0;
-    if (avg <= 1 * ROW_U) return 1;
-    if (avg <= 4 * ROW_U) return 4;
-    if (avg <= 8 * ROW_U) return 8;
-    return 16;
-}
-
-// F sweep (fold: x64 on the last level-0 sweep) and C sweep (final: into x64)
-template <class T>
-void relax_f(const Level &L, const T *b, const T *in, T *out, double *fold, const int *active, cudaStream_t s) {
-    if (L.nF == 0) return;
-    const T *sv = (const T *)L.sval;
-    const T *dv = lv_dinv<T>(L);
-#define PR_RELAX_F(G)                                                                                       \
-    k_relax_f<T, G><<<blocks_for((long long)L.nF * G, BS), BS, 0, s>>>(L.nF, L.srow, L.sptr, L.scol, sv, dv, b, \
-                                                                       in, out, fold, active, L.rowdir)
-    switch (pick_group(L.eF, L.nF)) {
-        case 1: PR_RELAX_F(1); break;
-        case 4: PR_RELAX_F(4); break;
-        case 8: PR_RELAX_F(8); break;
-        default: PR_RELAX_F(16); break;
-    }
-#undef PR_RELAX_F
+template <class T, int MODE>
+void launch_sell(const Sell &S, SellJob<T> j, cudaStream_t s) {
+    if (S.nrows <= 0) return;
+    j.npos = S.npos;
+    j.ptr = S.ptr;
+    j.row = S.row;
+    j.len = S.len;
+    j.col = S.col;
+    j.val = (const T *)S.val;
+    k_sell<T, MODE><<<blocks_for(S.npos, BS), BS, 0, s>>>(j);
     PR_LAUNCH();
 }
 
+// F sweep over the F rows (fold: x64 += the new values, the last level-0 sweep)
+template <class T>
+void relax_f(const Level &L, const T *b, const T *in, T *out, double *fold, const int *active, cudaStream_t s) {
+    SellJob<T> j{};
+    j.in = in;
+    j.dinv = lv_dinv<T>(L);
+    j.b = b;
+    j.out = out;
+    j.x64 = fold;
+    j.active = active;
+    j.rowdir = L.rowdir;
+    launch_sell<T, SM_F>(L.sF, j, s);
+}
+
+// C sweep over the C rows into out, or (final) into x64 together with the coarsest
+// rows of matrices that end on this level
 template <class T>
 void relax_c(const Level &L, const T *b, const T *in, T *out, double *x64, const T *xco, const int *active,
              cudaStream_t s) {
-    const int k0 = L.nF, kX = L.nF + L.nC, k1 = x64 ? L.n : kX;
-    if (k1 <= k0) return;
-    const T *sv = (const T *)L.sval;
-    const T *dv = lv_dinv<T>(L);
-#define PR_RELAX_C(G)                                                                                          \
-    do {                                                                                                      \
-        long long nb = blocks_for((long long)(k1 - k0) * G, BS);                                              \
-        if (x64)                                                                                              \
-            k_relax_c<T, G, true><<<nb, BS, 0, s>>>(k0, k1, kX, L.srow, L.sptr, L.scol, sv, dv, b, in, nullptr, \
-                                                    x64, xco, active, L.rowdir);                              \
-        else                                                                                                  \
-            k_relax_c<T, G, false><<<nb, BS, 0, s>>>(k0, k1, kX, L.srow, L.sptr, L.scol, sv, dv, b, in, out,    \
-                                                     nullptr, xco, active, L.rowdir);                         \
-    } while (0)
-    switch (pick_group(L.eC, L.nC)) {
-        case 1: PR_RELAX_C(1); break;
-        case 4: PR_RELAX_C(4); break;
-        case 8: PR_RELAX_C(8); break;
-        default: PR_RELAX_C(16); break;
+    SellJob<T> j{};
+    j.in = in;
+    j.dinv = lv_dinv<T>(L);
+    j.b = b;
+    j.out = out;
+    j.x64 = x64;
+    j.active = active;
+    j.rowdir = L.rowdir;
+    if (x64) {
+        launch_sell<T, SM_C_FINAL>(L.sC, j, s);
+        const int kX = L.nF + L.nC;
+        if (L.n > kX) {
+            k_fold_split<T><<<blocks_for(L.n - kX, BS), BS, 0, s>>>(kX, L.n, L.srow, xco, x64, active, L.rowdir);
+            PR_LAUNCH();
+        }
+    } else {
+        launch_sell<T, SM_C>(L.sC, j, s);
     }
-#undef PR_RELAX_C
-    PR_LAUNCH();
 }
 
+// b_c = Z b_F + b_C: one row of Z per coarse point
 template <class T>
 void restrict_(const Level &L, const T *bf, T *bc, cudaStream_t s) {
-    int G = pick_group(L.nnzZ, L.nc);
-    switch (G) {
-        case 1: k_restrict<T, 1><<<blocks_for((long long)L.nc, BS), BS, 0, s>>>(L.nc, L.cpts, L.zrowptr, L.zcol, lv_zval<T>(L), bf, bc); break;
-        case 4: k_restrict<T, 4><<<blocks_for((long long)L.nc * 4, BS), BS, 0, s>>>(L.nc, L.cpts, L.zrowptr, L.zcol, lv_zval<T>(L), bf, bc); break;
-        case 8: k_restrict<T, 8><<<blocks_for((long long)L.nc * 8, BS), BS, 0, s>>>(L.nc, L.cpts, L.zrowptr, L.zcol, lv_zval<T>(L), bf, bc); break;
-        default: k_restrict<T, 16><<<blocks_for((long long)L.nc * 16, BS), BS, 0, s>>>(L.nc, L.cpts, L.zrowptr, L.zcol, lv_zval<T>(L), bf, bc); break;
-    }
-    PR_LAUNCH();
+    SellJob<T> j{};
+    j.in = bf;
+    j.out = bc;
+    j.cpts = L.cpts;
+    launch_sell<T, SM_RESTRICT>(L.sZ, j, s);
 }
 
 template <class T>

@@ -870,9 +870,88 @@ __global__ void k_split_copy(int n, const int *srow, const int *rowptr, const in
     }
 }
 
-// CF-split row storage of one level (see Level): F rows, then C rows, then the rows of
-// matrices that end at this level, with the coarsest segments' split positions
-void build_split(Hier &h, Level &L) {
+// ---- sliced ELL (SELL-32) copies for the V-cycle's row dot products -------------
+// Rows are taken in windows of 256 and ordered inside each window by decreasing
+// length (ties by position); every 32 consecutive positions form a slice whose
+// entries are stored column-major with the slice's first (longest) row setting its
+// width: entry j of the row at lane t of slice s sits at ptr[s] + 32 j + t.
+constexpr int SELL_WIN = 256;
+
+// rows[q] (or q when rows is null), q < nr: CSR row of list position q
+__global__ void k_sell_rank(int nr, const int *rows, const int *rowptr, int *out_row, int *out_len) {
+    __shared__ int sl[SELL_WIN];
+    const int t = threadIdx.x, q = blockIdx.x * SELL_WIN + t;
+    const int r = q < nr ? (rows ? rows[q] : q) : -1;
+    const int len = r >= 0 ? rowptr[r + 1] - rowptr[r] : -1;
+    sl[t] = len;
+    __syncthreads();
+    int rank = 0;
+    for (int u = 0; u < SELL_WIN; ++u) {
+        const int lu = sl[u];
+        rank += (lu > len || (lu == len && u < t)) ? 1 : 0;
+    }
+    const int pos = blockIdx.x * SELL_WIN + rank;
+    out_row[pos] = r;
+    out_len[pos] = len > 0 ? len : 0;
+}
+
+__global__ void k_sell_width(int ns, const int *len, int *w32) {
+    int sl = blockIdx.x * blockDim.x + threadIdx.x;
+    if (sl < ns) w32[sl] = 32 * len[32 * sl];
+}
+
+template <class T>
+__global__ void k_sell_fill(int npos, const int *prow, const int *plen, const int *sptr, const int *rowptr,
+                            const int *col, const double *val, int *scol, T *sval) {
+    int pos = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pos >= npos) return;
+    const int r = prow[pos];
+    if (r < 0) return;
+    const int a = rowptr[r], len = plen[pos];
+    const int base = sptr[pos >> 5] + (pos & 31);
+    for (int j = 0; j < len; ++j) {
+        scol[base + 32 * j] = col[a + j];
+        sval[base + 32 * j] = (T)val[a + j];
+    }
+}
+
+// SELL copy of nr rows of a CSR matrix (list rows, or rows 0..nr-1), values in the
+// V-cycle's precision
+void build_sell(Hier &h, Sell &S, const int *rows, int nr, const int *rowptr, const int *col, const double *val) {
+    cudaStream_t s = h.stream;
+    const int BS = 256;
+    S.nrows = nr;
+    if (nr <= 0) return;
+    const int nwin = (nr + SELL_WIN - 1) / SELL_WIN;
+    S.npos = nwin * SELL_WIN;
+    const int ns = S.npos / 32;
+    S.row = dmalloc<int>(S.npos, s);
+    S.len = dmalloc<int>(S.npos, s);
+    k_sell_rank<<<nwin, SELL_WIN, 0, s>>>(nr, rows, rowptr, S.row, S.len);
+    PR_LAUNCH();
+    int *w32 = dmalloc<int>(ns, s);
+    k_sell_width<<<blocks_for(ns, BS), BS, 0, s>>>(ns, S.len, w32);
+    PR_LAUNCH();
+    S.ptr = dmalloc<int>(ns + 1, s);
+    S.nnz = scan_exclusive(w32, S.ptr, ns, s);
+    dfree(w32, s);
+    S.col = dmalloc<int>(std::max<long long>(S.nnz, 1), s);
+    if (h.prm.precision == 1) {
+        S.val = dmalloc<float>(std::max<long long>(S.nnz, 1), s);
+        k_sell_fill<float><<<blocks_for(S.npos, BS), BS, 0, s>>>(S.npos, S.row, S.len, S.ptr, rowptr, col, val,
+                                                                 S.col, (float *)S.val);
+    } else {
+        S.val = dmalloc<double>(std::max<long long>(S.nnz, 1), s);
+        k_sell_fill<double><<<blocks_for(S.npos, BS), BS, 0, s>>>(S.npos, S.row, S.len, S.ptr, rowptr, col, val,
+                                                                  S.col, (double *)S.val);
+    }
+    PR_LAUNCH();
+}
+
+// CF split of one level (see Level): the row order [F | C | coarsest], SELL copies
+// of the F and C rows (with_fc) and a CSR copy of the coarsest rows with the
+// coarsest segments' positions in it
+void build_split(Hier &h, Level &L, bool with_fc) {
     cudaStream_t s = h.stream;
     const int BS = 256;
     const int n = L.n;
@@ -883,34 +962,32 @@ void build_split(Hier &h, Level &L) {
     PR_REQUIRE(cnt[0] + cnt[1] + cnt[2] == n, PAIR_ERR_DEVICE, "CF split does not cover the level's rows");
     L.nF = cnt[0];
     L.nC = cnt[1];
-    int *len = dmalloc<int>(std::max(n, 1), s);
-    k_split_len<<<blocks_for(std::max(n, 1), BS), BS, 0, s>>>(n, L.srow, L.rowptr, len);
-    PR_LAUNCH();
-    L.sptr = dmalloc<int>(n + 1, s);
-    long long tot = scan_exclusive(len, L.sptr, n, s);
-    dfree(len, s);
-    PR_REQUIRE(tot == L.nnz, PAIR_ERR_DEVICE, "CF split entry count differs from the level's");
-    int b[2] = {0, 0};
-    PR_CUDA(cudaMemcpyAsync(&b[0], L.sptr + L.nF, sizeof(int), cudaMemcpyDeviceToHost, s));
-    PR_CUDA(cudaMemcpyAsync(&b[1], L.sptr + L.nF + L.nC, sizeof(int), cudaMemcpyDeviceToHost, s));
-    PR_CUDA(cudaStreamSynchronize(s));
-    L.eF = b[0];
-    L.eC = (long long)b[1] - b[0];
-    L.scol = dmalloc<int>(std::max<long long>(L.nnz, 1), s);
-    L.sval = dmalloc<char>(std::max<long long>(L.nnz, 1) * es, s);
-    if (n) {
+    const int kX = L.nF + L.nC, nx = n - kX;
+    if (with_fc) {
+        build_sell(h, L.sF, L.srow, L.nF, L.rowptr, L.col, L.val);
+        build_sell(h, L.sC, L.srow + L.nF, L.nC, L.rowptr, L.col, L.val);
+    }
+    if (nx > 0) {
+        int *len = dmalloc<int>(nx, s);
+        k_split_len<<<blocks_for(nx, BS), BS, 0, s>>>(nx, L.srow + kX, L.rowptr, len);
+        PR_LAUNCH();
+        L.sptr = dmalloc<int>(nx + 1, s);
+        long long tot = scan_exclusive(len, L.sptr, nx, s);
+        dfree(len, s);
+        L.scol = dmalloc<int>(std::max<long long>(tot, 1), s);
+        L.sval = dmalloc<char>(std::max<long long>(tot, 1) * es, s);
         if (h.prm.precision == 1)
-            k_split_copy<float><<<blocks_for((long long)n * 8, BS), BS, 0, s>>>(n, L.srow, L.rowptr, L.col, L.val,
-                                                                               L.sptr, L.scol, (float *)L.sval);
+            k_split_copy<float><<<blocks_for((long long)nx * 8, BS), BS, 0, s>>>(
+                nx, L.srow + kX, L.rowptr, L.col, L.val, L.sptr, L.scol, (float *)L.sval);
         else
-            k_split_copy<double><<<blocks_for((long long)n * 8, BS), BS, 0, s>>>(n, L.srow, L.rowptr, L.col, L.val,
-                                                                                L.sptr, L.scol, (double *)L.sval);
+            k_split_copy<double><<<blocks_for((long long)nx * 8, BS), BS, 0, s>>>(
+                nx, L.srow + kX, L.rowptr, L.col, L.val, L.sptr, L.scol, (double *)L.sval);
         PR_LAUNCH();
     }
     // coarsest segments are whole matrices, ascending in row order, so each one is a
-    // contiguous run of the coarsest group
+    // contiguous run of the coarsest group; positions relative to the group's start
     std::vector<int> s0;
-    long long pos = (long long)L.nF + L.nC, prev = -1;
+    long long pos = 0, prev = -1;
     for (int d = 0; d < h.ndir; ++d)
         if (L.nrows[d] > 0 && L.coarsest[d]) {
             PR_REQUIRE(L.row0[d] > prev, PAIR_ERR_DEVICE, "coarsest segments out of row order");
@@ -918,7 +995,7 @@ void build_split(Hier &h, Level &L) {
             s0.push_back((int)pos);
             pos += L.nrows[d];
         }
-    PR_REQUIRE(pos == n, PAIR_ERR_DEVICE, "coarsest rows differ from the coarsest segments");
+    PR_REQUIRE(pos == nx, PAIR_ERR_DEVICE, "coarsest rows differ from the coarsest segments");
     PR_REQUIRE((int)s0.size() == L.n_cseg, PAIR_ERR_DEVICE, "coarsest segment count mismatch");
     if (!s0.empty()) {
         L.d_cseg_s0 = dmalloc<int>(s0.size(), s);
@@ -931,8 +1008,10 @@ void build_split(Hier &h, Level &L) {
 
 void free_level(Level &L, cudaStream_t s) {
     void *ptrs[] = {L.rowptr, L.col, L.val, L.dinv, L.dinv32, L.cf, L.pmap, L.rowdir, L.cpts,
-                    L.zrowptr, L.zcol, L.zval, L.zval32, L.d_row0, L.d_cseg_row0, L.d_cseg_n,
+                    L.zrowptr, L.zcol, L.zval, L.d_row0, L.d_cseg_row0, L.d_cseg_n,
                     L.srow, L.sptr, L.scol, L.sval, L.d_cseg_s0,
+                    L.sF.ptr, L.sF.row, L.sF.len, L.sF.col, L.sF.val, L.sC.ptr, L.sC.row, L.sC.len, L.sC.col,
+                    L.sC.val, L.sZ.ptr, L.sZ.row, L.sZ.len, L.sZ.col, L.sZ.val,
                     L.vb, L.vx, L.vxn, L.vy};
     for (void *p : ptrs) dfree(p, s);
     L = Level();
@@ -1291,19 +1370,12 @@ void build_hierarchy(Hier &h) {
     d2h(&err, h.d_err, 1, s);
     dfree(d_count, s); dfree(dwork, s); dfree(dcont, s); dfree(dnc, s); dfree(dnnz, s);
     PR_REQUIRE(err == 0, PAIR_ERR_DEVICE, "setup kernel reported device error bits " + std::to_string(err));
-    // relaxation storage (CF split, cycle precision) and FP32 copies of Z
-    // (the block-form level 0 relaxes without it; it needs it only for coarsest sweeps)
-    for (size_t l = 0; l < h.lev.size(); ++l)
-        if (!(l == 0 && h.bsr0) || h.lev[l].n_cseg > 0) build_split(h, h.lev[l]);
-    if (prm.precision == 1) {
-        for (size_t l = 0; l < h.lev.size(); ++l) {
-            Level &L = h.lev[l];
-            if (L.nnzZ) {
-                L.zval32 = dmalloc<float>(L.nnzZ, s);
-                k_cast<<<blocks_for(L.nnzZ, BS), BS, 0, s>>>(L.nnzZ, L.zval, L.zval32);
-                PR_LAUNCH();
-            }
-        }
+    // V-cycle storage in the cycle precision: the CF split with SELL copies of the F
+    // and C rows (the block-form level 0 relaxes without them) and of Z
+    for (size_t l = 0; l < h.lev.size(); ++l) {
+        Level &L = h.lev[l];
+        build_split(h, L, !(l == 0 && h.bsr0));
+        if (L.nc > 0) build_sell(h, L.sZ, nullptr, L.nc, L.zrowptr, L.zcol, L.zval);
     }
     PR_CUDA(cudaStreamSynchronize(s));
 }

@@ -352,9 +352,10 @@ size_t bytes_per_dir(const pair_mesh &mesh, int precision, bool gin) {
     size_t nnz0 = hex ? (size_t)hex_nnz(mesh.n, om) : N * 13;
     size_t lvl0 = nnz0 * 12 + (hex ? N * 96 + (precision ? N * 48 : 0) : 0) + E * nb * nb * 8 + (gin ? N * 8 : 0);
     size_t coarse = nnz0 * 12 * 3 / 2 + nnz0 * 8;   // coarse operators, Z, setup scratch
-    // CF-split relaxation copies (column + value in the cycle precision) of the coarse
-    // levels, and of level 0 for the tetrahedral CSR form
-    coarse += (nnz0 * 3 / 2 + (hex ? 0 : nnz0)) * (4 + (precision ? 4 : 8));
+    // SELL copies (column + value in the cycle precision, ~10% padding) of the coarse
+    // levels, of level 0 for the tetrahedral CSR form, and of Z
+    coarse += (size_t)((double)(nnz0 * 3 / 2 + (hex ? 0 : nnz0)) * 1.15 + (double)nnz0 / 2) *
+              (4 + (precision ? 4 : 8));
     size_t vec = N * (8 * 3 + 4 * 8);
     return lvl0 + coarse + vec;
 }
