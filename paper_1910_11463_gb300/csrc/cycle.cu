@@ -298,7 +298,12 @@ __global__ void k_prolong(int n, const int8_t *cf, const int *pmap, const int8_t
     if (c == CF_COARSEST) return;
     int p = pmap[i];
     T v = T(0);
-    if (p >= 0) v = cfc[p] == CF_F ? xcF[p] : xc[p];
+    if (p >= 0) {
+        // both candidates are loaded with the flag (one dependent step, not two)
+        const int8_t cc = cfc[p];
+        const T vf = xcF[p], vc = xc[p];
+        v = cc == CF_F ? vf : vc;
+    }
     y[i] = v;
     if (y2 && c == CF_C) y2[i] = v;
 }
@@ -329,18 +334,30 @@ __global__ void __launch_bounds__(BS) k_relax_bsr(int n, int N, const int8_t *ds
                                                   const T *b, const T *in, T *out, int phase, double *x64,
                                                   const T *xco, const int *active) {
     HexRow q = hex_row(n);
-    if (active && !active[q.m]) return;
     if (!q.valid) return;
-    long long gi = (long long)q.m * N + 8LL * q.e + q.a;
-    int8_t c = cf[gi];
+    const long long gi = (long long)q.m * N + 8LL * q.e + q.a;
+    // Loads that decide nothing are issued before any branch: the sweep is latency-
+    // bound, and a load behind a branch on another load costs one more round trip.
+    // The F sweeps (not final) also compute every row's face terms before knowing
+    // whether the row is an F row (a C row's block values are then read for
+    // nothing: a quarter of the rows, against one round trip saved for all).
+    const int act = active ? active[q.m] : 1;
+    const int8_t c = cf[gi];
+    const T xin = in[gi], bi = b[gi];
+    T acc = T(0);
+    if (!FINAL)
+        acc = bsr_offdiag<T, T>(n, (long long)N / 8, q.m, q.e, q.a, q.idx, dsign, vals, in + (long long)q.m * N);
+    if (!act) return;
     if (c == CF_COARSEST) {   // a matrix whose hierarchy ends at level 0
         if (FINAL) x64[gi] += (double)xco[gi];
         return;
     }
-    T v = in[gi];
+    T v = xin;
     if (c == (phase == 0 ? CF_F : CF_C)) {
-        T acc = bsr_offdiag<T, T>(n, (long long)N / 8, q.m, q.e, q.a, q.idx, dsign, vals, in + (long long)q.m * N);
-        v = v + (b[gi] - (acc + v));
+        if (FINAL)
+            acc = bsr_offdiag<T, T>(n, (long long)N / 8, q.m, q.e, q.a, q.idx, dsign, vals,
+                                    in + (long long)q.m * N);
+        v = v + (bi - (acc + v));
     }
     if (FINAL) x64[gi] += (double)v;
     else out[gi] = v;
