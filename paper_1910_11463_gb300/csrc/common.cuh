@@ -140,6 +140,7 @@ struct Hier {
     int *active = nullptr;                                         // [dir]
     int *d_err = nullptr;
     int *d_n0 = nullptr, *d_row00 = nullptr;  // level-0 rows per matrix and first rows
+    int sms = 1;                              // multiprocessors of the device
     // instrumentation: CUDA events around the level-0 kernels (also inside graphs)
     bool prof = false;
     bool relax_timed = false;   // ev[2], ev[3] recorded by the current cycle

@@ -214,23 +214,23 @@ __global__ void k_sumsq_rows(const int *row0, const int *nrow, const double *v, 
 // added in ascending entry order.
 constexpr int SELL_U = 8;
 
-template <class T>
-__device__ __forceinline__ T sell_dot(int base, int len, const int *col, const T *val, const T *in) {
+template <class T, int G>
+__device__ __forceinline__ T sell_dot(int base, int len, int g, const int *col, const T *val, const T *in) {
     T acc = T(0);
-    for (int j0 = 0; j0 < len; j0 += SELL_U) {
+    for (int j0 = g; j0 < len; j0 += SELL_U * G) {
         int c[SELL_U];
         T v[SELL_U], x[SELL_U];
 #pragma unroll
         for (int u = 0; u < SELL_U; ++u) {
-            const bool ok = j0 + u < len;
-            c[u] = ok ? __ldcs(col + base + 32 * (j0 + u)) : 0;
-            v[u] = ok ? __ldcs(val + base + 32 * (j0 + u)) : T(0);
+            const bool ok = j0 + u * G < len;
+            c[u] = ok ? __ldcs(col + base + 32 * (j0 + u * G)) : 0;
+            v[u] = ok ? __ldcs(val + base + 32 * (j0 + u * G)) : T(0);
         }
 #pragma unroll
-        for (int u = 0; u < SELL_U; ++u) x[u] = j0 + u < len ? in[c[u]] : T(0);
+        for (int u = 0; u < SELL_U; ++u) x[u] = j0 + u * G < len ? in[c[u]] : T(0);
 #pragma unroll
         for (int u = 0; u < SELL_U; ++u)
-            if (j0 + u < len) acc += v[u] * x[u];
+            if (j0 + u * G < len) acc += v[u] * x[u];
     }
     return acc;
 }
@@ -253,25 +253,34 @@ struct SellJob {
 // F sweep:   out[i] = in[i] + dinv[i] (b[i] - A_i in)        (x64[i] += it, if given)
 // C sweep:   same into out, or (final) x64[i] += it
 // restrict:  out[ic] = Z_ic in + in[cpts[ic]]
-template <class T, int MODE>
+// G lanes per row (G > 1 on small levels, where rows are too few to fill the GPU):
+// lane g takes entries g, g+G, ..., then a fixed shuffle tree; the launch covers
+// exactly npos * G threads (npos is a multiple of 256), so every lane reaches the
+// shuffles.
+template <class T, int MODE, int G>
 __global__ void __launch_bounds__(BS) k_sell(SellJob<T> j) {
-    const int q = blockIdx.x * BS + threadIdx.x;
-    if (q >= j.npos) return;
+    const long long t = (long long)blockIdx.x * BS + threadIdx.x;
+    const int q = (int)(t / G), g = (int)(t % G);
     const int r = j.row[q];
-    if (r < 0) return;
-    if (MODE != SM_RESTRICT && j.active && !j.active[j.rowdir[r]]) return;
-    const int len = j.len[q];
+    bool ok = r >= 0;
+    if (MODE != SM_RESTRICT && ok && j.active && !j.active[j.rowdir[r]]) ok = false;
+    const int len = ok ? j.len[q] : 0;
     const int base = j.ptr[q >> 5] + (q & 31);
     // the row's own operands are loaded before the dot product (shorter chain)
-    T own, di = T(0), bi = T(0);
-    if (MODE == SM_RESTRICT) {
-        own = j.in[j.cpts[r]];
-    } else {
-        own = j.in[r];
-        di = j.dinv[r];
-        bi = j.b[r];
+    T own = T(0), di = T(0), bi = T(0);
+    if (ok && g == 0) {
+        if (MODE == SM_RESTRICT) {
+            own = j.in[j.cpts[r]];
+        } else {
+            own = j.in[r];
+            di = j.dinv[r];
+            bi = j.b[r];
+        }
     }
-    const T acc = sell_dot<T>(base, len, j.col, j.val, j.in);
+    T acc = sell_dot<T, G>(base, len, g, j.col, j.val, j.in);
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, G);
+    if (!ok || g != 0) return;
     if (MODE == SM_RESTRICT) {
         j.out[r] = acc + own;
         return;
@@ -290,13 +299,9 @@ __global__ void __launch_bounds__(BS) k_sell(SellJob<T> j) {
 // in xcF, C and coarsest rows in xc.  C rows of y are also written to y2 (the other
 // ping-pong buffer of the F sweeps), so the F sweeps never copy C rows.
 template <class T>
-__global__ void k_prolong(int n, const int8_t *cf, const int *pmap, const int8_t *cfc, const T *xcF, const T *xc,
-                          T *y, T *y2) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int8_t c = cf[i];
+__device__ __forceinline__ void prolong_row(long long i, int8_t c, int p, const int8_t *cfc, const T *xcF,
+                                            const T *xc, T *y, T *y2) {
     if (c == CF_COARSEST) return;
-    int p = pmap[i];
     T v = T(0);
     if (p >= 0) {
         // both candidates are loaded with the flag (one dependent step, not two)
@@ -306,6 +311,39 @@ __global__ void k_prolong(int n, const int8_t *cf, const int *pmap, const int8_t
     }
     y[i] = v;
     if (y2 && c == CF_C) y2[i] = v;
+}
+
+// four consecutive rows per thread (vector loads of cf and pmap, twelve gathers in
+// flight): with one row per thread the kernel is latency-bound
+template <class T>
+__global__ void k_prolong(int n, const int8_t *cf, const int *pmap, const int8_t *cfc, const T *xcF, const T *xc,
+                          T *y, T *y2) {
+    const long long i0 = 4LL * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
+    if (i0 >= n) return;
+    if (i0 + 4 <= n) {
+        const char4 c4 = *reinterpret_cast<const char4 *>(cf + i0);
+        const int4 p4 = *reinterpret_cast<const int4 *>(pmap + i0);
+        const int8_t c[4] = {(int8_t)c4.x, (int8_t)c4.y, (int8_t)c4.z, (int8_t)c4.w};
+        const int p[4] = {p4.x, p4.y, p4.z, p4.w};
+        int8_t cc[4];
+        T vf[4], vc[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const bool gth = c[u] != CF_COARSEST && p[u] >= 0;
+            cc[u] = gth ? cfc[p[u]] : (int8_t)CF_C;
+            vf[u] = gth ? xcF[p[u]] : T(0);
+            vc[u] = gth ? xc[p[u]] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (c[u] == CF_COARSEST) continue;
+            const T v = cc[u] == CF_F ? vf[u] : vc[u];
+            y[i0 + u] = v;
+            if (y2 && c[u] == CF_C) y2[i0 + u] = v;
+        }
+    } else {
+        for (long long i = i0; i < n; ++i) prolong_row<T>(i, cf[i], pmap[i], cfc, xcF, xc, y, y2);
+    }
 }
 
 // single-level hierarchies: x64 += the coarsest solution on active rows
@@ -393,7 +431,7 @@ const float *lv_dinv<float>(const Level &L) { return L.dinv32; }
 template <>
 const double *lv_dinv<double>(const Level &L) { return L.dinv; }
 template <class T, int MODE>
-void launch_sell(const Sell &S, SellJob<T> j, cudaStream_t s) {
+void launch_sell(const Sell &S, SellJob<T> j, int sms, cudaStream_t s) {
     if (S.nrows <= 0) return;
     j.npos = S.npos;
     j.ptr = S.ptr;
@@ -401,13 +439,23 @@ void launch_sell(const Sell &S, SellJob<T> j, cudaStream_t s) {
     j.len = S.len;
     j.col = S.col;
     j.val = (const T *)S.val;
-    k_sell<T, MODE><<<blocks_for(S.npos, BS), BS, 0, s>>>(j);
+    // lanes per row: enough threads to fill the GPU (about 2048 per SM) on small levels
+    const long long want = (long long)sms * 2048;
+    int G = 1;
+    while (G < 8 && (long long)S.npos * G * 2 <= want) G *= 2;
+    switch (G) {
+        case 1: k_sell<T, MODE, 1><<<blocks_for(S.npos, BS), BS, 0, s>>>(j); break;
+        case 2: k_sell<T, MODE, 2><<<blocks_for(2LL * S.npos, BS), BS, 0, s>>>(j); break;
+        case 4: k_sell<T, MODE, 4><<<blocks_for(4LL * S.npos, BS), BS, 0, s>>>(j); break;
+        default: k_sell<T, MODE, 8><<<blocks_for(8LL * S.npos, BS), BS, 0, s>>>(j); break;
+    }
     PR_LAUNCH();
 }
 
 // F sweep over the F rows (fold: x64 += the new values, the last level-0 sweep)
 template <class T>
-void relax_f(const Level &L, const T *b, const T *in, T *out, double *fold, const int *active, cudaStream_t s) {
+void relax_f(const Level &L, const T *b, const T *in, T *out, double *fold, const int *active, int sms,
+             cudaStream_t s) {
     SellJob<T> j{};
     j.in = in;
     j.dinv = lv_dinv<T>(L);
@@ -416,13 +464,13 @@ void relax_f(const Level &L, const T *b, const T *in, T *out, double *fold, cons
     j.x64 = fold;
     j.active = active;
     j.rowdir = L.rowdir;
-    launch_sell<T, SM_F>(L.sF, j, s);
+    launch_sell<T, SM_F>(L.sF, j, sms, s);
 }
 
 // C sweep over the C rows into out, or (final) into x64 together with the coarsest
 // rows of matrices that end on this level
 template <class T>
-void relax_c(const Level &L, const T *b, const T *in, T *out, double *x64, const T *xco, const int *active,
+void relax_c(const Level &L, const T *b, const T *in, T *out, double *x64, const T *xco, const int *active, int sms,
              cudaStream_t s) {
     SellJob<T> j{};
     j.in = in;
@@ -433,25 +481,25 @@ void relax_c(const Level &L, const T *b, const T *in, T *out, double *x64, const
     j.active = active;
     j.rowdir = L.rowdir;
     if (x64) {
-        launch_sell<T, SM_C_FINAL>(L.sC, j, s);
+        launch_sell<T, SM_C_FINAL>(L.sC, j, sms, s);
         const int kX = L.nF + L.nC;
         if (L.n > kX) {
             k_fold_split<T><<<blocks_for(L.n - kX, BS), BS, 0, s>>>(kX, L.n, L.srow, xco, x64, active, L.rowdir);
             PR_LAUNCH();
         }
     } else {
-        launch_sell<T, SM_C>(L.sC, j, s);
+        launch_sell<T, SM_C>(L.sC, j, sms, s);
     }
 }
 
 // b_c = Z b_F + b_C: one row of Z per coarse point
 template <class T>
-void restrict_(const Level &L, const T *bf, T *bc, cudaStream_t s) {
+void restrict_(const Level &L, const T *bf, T *bc, int sms, cudaStream_t s) {
     SellJob<T> j{};
     j.in = bf;
     j.out = bc;
     j.cpts = L.cpts;
-    launch_sell<T, SM_RESTRICT>(L.sZ, j, s);
+    launch_sell<T, SM_RESTRICT>(L.sZ, j, sms, s);
 }
 
 template <class T>
@@ -462,7 +510,7 @@ void vcycle_t(Hier &h, double *x64) {
     for (int l = 0; l < NL; ++l) {
         Level &L = h.lev[l];
         L.vF = L.vx;   // replaced by the F sweeps' buffer once the level relaxes
-        if (l + 1 < NL) restrict_<T>(L, (const T *)L.vb, (T *)h.lev[l + 1].vb, s);
+        if (l + 1 < NL) restrict_<T>(L, (const T *)L.vb, (T *)h.lev[l + 1].vb, h.sms, s);
         if (L.n_cseg) {
             k_coarsest<T><<<L.n_cseg, 256, 0, s>>>(L.d_cseg_row0, L.d_cseg_n, L.d_cseg_s0, L.sptr, L.scol,
                                                    (const T *)L.sval, lv_dinv<T>(L), (const T *)L.vb, (T *)L.vx,
@@ -477,8 +525,8 @@ void vcycle_t(Hier &h, double *x64) {
         const bool bsr = l == 0 && h.bsr0;
         // F sweeps ping-pong between vy and vxn; the C sweep reads the last one
         T *bufs[2] = {(T *)L.vy, (T *)L.vxn};
-        k_prolong<T><<<blocks_for(L.n, BS), BS, 0, s>>>(L.n, L.cf, L.pmap, C.cf, (const T *)C.vF, (const T *)C.vx,
-                                                        bufs[0], bsr ? nullptr : bufs[1]);
+        k_prolong<T><<<blocks_for((L.n + 3) / 4, BS), BS, 0, s>>>(L.n, L.cf, L.pmap, C.cf, (const T *)C.vF,
+                                                                  (const T *)C.vx, bufs[0], bsr ? nullptr : bufs[1]);
         PR_LAUNCH();
         int cur = 0;
         if (bsr) {
@@ -504,8 +552,9 @@ void vcycle_t(Hier &h, double *x64) {
             if (h.prof && l == 0) { rec_event(h.ev[2], s); h.relax_timed = true; }
             for (int f = 0; f < fs; ++f, cur ^= 1)
                 relax_f<T>(L, (const T *)L.vb, bufs[cur], bufs[cur ^ 1], l == 0 && f == fs - 1 ? x64 : nullptr, act,
-                           s);
-            relax_c<T>(L, (const T *)L.vb, bufs[cur], (T *)L.vx, l == 0 ? x64 : nullptr, (const T *)L.vx, act, s);
+                           h.sms, s);
+            relax_c<T>(L, (const T *)L.vb, bufs[cur], (T *)L.vx, l == 0 ? x64 : nullptr, (const T *)L.vx, act,
+                       h.sms, s);
             if (tl) rec_event(h.evl[2 * l + 1], s);
             if (h.prof && l == 0) rec_event(h.ev[3], s);
         }
@@ -542,6 +591,9 @@ void alloc_cycle_vectors(Hier &h) {
     h.bnorm = dmalloc<double>(h.ndir, h.stream);
     h.active = dmalloc<int>(h.ndir, h.stream);
     set_all_active(h);
+    int dev = 0;
+    PR_CUDA(cudaGetDevice(&dev));
+    PR_CUDA(cudaDeviceGetAttribute(&h.sms, cudaDevAttrMultiProcessorCount, dev));
 }
 
 void set_all_active(Hier &h) {
