@@ -281,7 +281,10 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     tet = hasattr(prob, "tets")
     kern = {
-        ("k_res0_csr" if tet else "k_res0_bsr"): ("FP64 outer residual, level 0 " + ("CSR" if tet else "block form"),
+        ("k_res0_csr" if tet else "k_res0_bsr_dd" if args.precision else "k_res0_bsr"): (
+            ("FP64 outer residual, level 0 CSR" if tet else
+             "outer residual in double-float pairs (FP32 pipe), level 0 block form" if args.precision else
+             "FP64 outer residual, level 0 block form"),
                                                   tot("t_res0_ms"), tot("n_res0"), tot("gb_res0")),
         ("k_relax_f+k_relax_c level 0" if tet else "k_relax_bsr"): (
             "FP32 F-F-C Jacobi, level 0 " + ("CF-split CSR; one unit = one V-cycle's three sweeps" if tet
@@ -367,7 +370,8 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 V-cycle + f64 residual/setup" if args.precision else "f64",
+        "vs_baseline": None, "dtype": ("f32 V-cycle + f64 setup/iterate + f32-pair residual" if args.precision and not hasattr(prob, "tets")
+                  else "f32 V-cycle + f64 residual/setup" if args.precision else "f64"),
         "data": "synthetic",
         "config": {"workload": args.config + ": " + WORKLOADS[args.config],
                    "step": ("one complete SI solve from phi=0 (assembly + AIR setup + SI iterations to 1e-8, every "

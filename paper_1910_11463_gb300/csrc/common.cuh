@@ -132,6 +132,12 @@ struct Hier {
     int hex_n = 0;
     double *bsr64 = nullptr;  // [dir][elem][axis][row a][4]
     float *bsr32 = nullptr;
+    // FP32-refined block form: the outer residual in double-float arithmetic (pairs
+    // of floats, hi + lo) instead of the FP64 pipe; block values, b and the solve's
+    // iterate are held as pairs during a solve (bsr64 is then not kept)
+    bool dd = false;
+    float2 *bsr_dd = nullptr;          // same layout as bsr64
+    float2 *b_dd = nullptr, *x_dd = nullptr;   // [rows of the batch]
     int8_t *dsign = nullptr;  // [dir][3] sign of Omega components
     // solve state
     double *partials = nullptr;  // [dir][max blocks]
@@ -170,6 +176,11 @@ void free_level(Level &L, cudaStream_t s);
 // r = b - A0 x (FP64), cast into lev[0].vb; per-matrix ||r||; active[d] = ||r|| > tol ||b||
 void residual0(Hier &h, const double *b, const double *x, double tol, bool update_active);
 void vcycle_correct(Hier &h, double *x);       // x += V(lev[0].vb), zero initial guess
+// double-float mode (h.dd): b and x to pairs before a solve, x back after it; the
+// residual and the final relaxation then work on h.b_dd / h.x_dd
+void dd_enable(Hier &h);            // bsr_dd from bsr64 (frees bsr64), vectors
+void dd_load(Hier &h, const double *b, const double *x);
+void dd_store(Hier &h, double *x);
 void norms0(Hier &h, const double *v, double *out);  // per-matrix 2-norms of a level-0 vector
 void alloc_cycle_vectors(Hier &h);
 void set_all_active(Hier &h);   // every matrix of the batch takes part in the next cycle

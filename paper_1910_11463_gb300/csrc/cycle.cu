@@ -155,6 +155,99 @@ __global__ void __launch_bounds__(BS) k_res0_bsr(int n, int N, const int8_t *dsi
     if (threadIdx.x == 0) partials[(long long)q.m * maxblk + blockIdx.y * gridDim.x + blockIdx.x] = tot;
 }
 
+// ---- double-float arithmetic (error-free transformations) -----------------------
+// A value is the unevaluated sum hi + lo of two floats.  two_sum (Knuth) returns
+// s = fl(a + b) and the exact error; fast_two_sum (Dekker) assumes |a| >= |b|; the
+// exact error of a product comes from one fma.  Products of pairs drop lo*lo
+// (below 2^-48 relative).  With these, r = b - x - A x keeps about 44 bits, far
+// below the 1e-8 relative residuals the refinement resolves, on the FP32 pipe.
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return make_float2(s, e);
+}
+__device__ __forceinline__ float2 fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return make_float2(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+// acc += a * x, all pairs
+__device__ __forceinline__ void dd_fma_acc(float2 &acc, float2 a, float2 x) {
+    const float p = __fmul_rn(a.x, x.x);
+    const float pe = __fmaf_rn(a.x, x.x, -p);
+    const float t = __fmaf_rn(a.x, x.y, __fmaf_rn(a.y, x.x, pe));
+    const float2 s2 = two_sum(acc.x, p);
+    acc.x = s2.x;
+    acc.y = __fadd_rn(acc.y, __fadd_rn(s2.y, t));
+}
+__device__ __forceinline__ float2 dd_split(double d) {
+    const float hi = __double2float_rn(d);
+    return make_float2(hi, __double2float_rn(d - (double)hi));
+}
+
+__device__ __forceinline__ void load_dd4(const float2 *p, float2 *w) {
+    const float4 a = __ldcs(reinterpret_cast<const float4 *>(p));
+    const float4 b = __ldcs(reinterpret_cast<const float4 *>(p) + 1);
+    w[0] = make_float2(a.x, a.y);
+    w[1] = make_float2(a.z, a.w);
+    w[2] = make_float2(b.x, b.y);
+    w[3] = make_float2(b.z, b.w);
+}
+
+// Level-0 residual of the block form in double-float: r = b - x - sum_faces A x_nbr,
+// cast to FP32 for the cycle, FP32 squares for the norm (as in k_res0_bsr<float>)
+__global__ void __launch_bounds__(BS) k_res0_bsr_dd(int n, int N, const int8_t *dsign, const float2 *vals,
+                                                    const float2 *b, const float2 *x, float *r, double *partials,
+                                                    int maxblk, const int *active) {
+    HexRow q = hex_row(n);
+    if (active && !active[q.m]) return;
+    float s2f = 0.0f;
+    if (q.valid) {
+        const long long E = (long long)N / 8;
+        const long long gi = (long long)q.m * N + 8LL * q.e + q.a;
+        const float2 bi = b[gi], xi = x[gi];
+        const float2 *xm = x + (long long)q.m * N;
+        const int stride[3] = {1, n, n * n};
+        const float2 *base = vals + (((long long)q.m * E + q.e) * 3) * 32 + q.a * 4;
+        float2 acc = make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const int sg = dsign[3 * q.m + d];
+            if (sg == 0) continue;
+            const bool has = sg > 0 ? q.idx[d] > 0 : q.idx[d] < n - 1;
+            if (!has) continue;
+            const int ep = sg > 0 ? q.e - stride[d] : q.e + stride[d];
+            const int o = sg > 0 ? 1 : 0;
+            float2 w[4];
+            load_dd4(base + d * 32, w);
+            const float2 *xb = xm + 8LL * ep;
+#pragma unroll
+            for (int t = 0; t < 4; ++t) dd_fma_acc(acc, w[t], xb[face_node(d, o, t)]);
+        }
+        acc = fast_two_sum(acc.x, acc.y);
+        // (b - x) - acc in pairs
+        float2 d0 = two_sum(bi.x, -xi.x);
+        d0.y = __fadd_rn(d0.y, __fsub_rn(bi.y, xi.y));
+        const float2 d1 = two_sum(d0.x, -acc.x);
+        const float lo = __fadd_rn(__fsub_rn(d0.y, acc.y), d1.y);
+        const float rt = __fadd_rn(d1.x, lo);
+        r[gi] = rt;
+        s2f = rt * rt;
+    }
+    const double tot = block_sum_f(s2f);
+    if (threadIdx.x == 0) partials[(long long)q.m * maxblk + blockIdx.y * gridDim.x + blockIdx.x] = tot;
+}
+
+__global__ void k_dd_split(long long n, const double *a, float2 *out) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = dd_split(a[i]);
+}
+
+__global__ void k_dd_join(long long n, const float2 *a, double *out) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (double)a[i].x + (double)a[i].y;
+}
+
 template <class T>
 __global__ void __launch_bounds__(BS) k_res0_csr(const int *row0, const int *nrow, const int *rowptr, const int *col,
                                                  const double *val, const double *b, const double *x, T *r,
@@ -370,7 +463,7 @@ __global__ void k_fold_split(int kX, int n, const int *srow, const T *xco, doubl
 template <class T, bool FINAL>
 __global__ void __launch_bounds__(BS) k_relax_bsr(int n, int N, const int8_t *dsign, const T *vals, const int8_t *cf,
                                                   const T *b, const T *in, T *out, int phase, double *x64,
-                                                  const T *xco, const int *active) {
+                                                  const T *xco, const int *active, float2 *xdd) {
     HexRow q = hex_row(n);
     if (!q.valid) return;
     const long long gi = (long long)q.m * N + 8LL * q.e + q.a;
@@ -386,19 +479,25 @@ __global__ void __launch_bounds__(BS) k_relax_bsr(int n, int N, const int8_t *ds
     if (!FINAL)
         acc = bsr_offdiag<T, T>(n, (long long)N / 8, q.m, q.e, q.a, q.idx, dsign, vals, in + (long long)q.m * N);
     if (!act) return;
-    if (c == CF_COARSEST) {   // a matrix whose hierarchy ends at level 0
-        if (FINAL) x64[gi] += (double)xco[gi];
-        return;
-    }
     T v = xin;
-    if (c == (phase == 0 ? CF_F : CF_C)) {
+    if (c == CF_COARSEST) {   // a matrix whose hierarchy ends at level 0
+        if (!FINAL) return;
+        v = xco[gi];
+    } else if (c == (phase == 0 ? CF_F : CF_C)) {
         if (FINAL)
             acc = bsr_offdiag<T, T>(n, (long long)N / 8, q.m, q.e, q.a, q.idx, dsign, vals,
                                     in + (long long)q.m * N);
         v = v + (bi - (acc + v));
     }
-    if (FINAL) x64[gi] += (double)v;
-    else out[gi] = v;
+    if (!FINAL) {
+        out[gi] = v;
+    } else if (xdd) {   // iterate held as a float pair: x += v without the FP64 pipe
+        const float2 xo = xdd[gi];
+        const float2 s2 = two_sum(xo.x, (float)v);
+        xdd[gi] = fast_two_sum(s2.x, __fadd_rn(xo.y, s2.y));
+    } else {
+        x64[gi] += (double)v;
+    }
 }
 
 // ---- coarsest level: Jacobi sweeps, one CTA per matrix segment ---------------
@@ -536,11 +635,12 @@ void vcycle_t(Hier &h, double *x64) {
             if (h.prof) { rec_event(h.ev[2], s); h.relax_timed = true; }
             for (int f = 0; f < fs; ++f, cur ^= 1) {
                 k_relax_bsr<T, false><<<grid, BS, 0, s>>>(h.hex_n, N, h.dsign, vals, L.cf, (const T *)L.vb, bufs[cur],
-                                                          bufs[cur ^ 1], 0, nullptr, nullptr, active);
+                                                          bufs[cur ^ 1], 0, nullptr, nullptr, active, nullptr);
                 PR_LAUNCH();
             }
             k_relax_bsr<T, true><<<grid, BS, 0, s>>>(h.hex_n, N, h.dsign, vals, L.cf, (const T *)L.vb, bufs[cur],
-                                                     nullptr, 1, x64, (const T *)L.vx, active);
+                                                     nullptr, 1, x64, (const T *)L.vx, active,
+                                                     h.dd ? h.x_dd : nullptr);
             PR_LAUNCH();
             if (h.prof) rec_event(h.ev[3], s);
         } else {
@@ -744,7 +844,12 @@ void residual0(Hier &h, const double *b, const double *x, double tol, bool updat
     Level &L = h.lev[0];
     dim3 grid(h.maxblk, h.ndir);
     bool f32 = h.prm.precision == 1;
-    if (h.bsr0) {
+    if (h.bsr0 && h.dd) {
+        int N = h.n0[0];
+        dim3 g3(blocks_for(h.hex_n, 32), h.hex_n * h.hex_n, h.ndir);
+        k_res0_bsr_dd<<<g3, BS, 0, s>>>(h.hex_n, N, h.dsign, h.bsr_dd, h.b_dd, h.x_dd, (float *)L.vb, h.partials,
+                                        h.maxblk, act);
+    } else if (h.bsr0) {
         int N = h.n0[0];
         dim3 g3(blocks_for(h.hex_n, 32), h.hex_n * h.hex_n, h.ndir);
         if (f32)
@@ -776,6 +881,35 @@ void norms0(Hier &h, const double *v, double *out) {
     PR_LAUNCH();
     k_norm_final<<<blocks_for(32LL * h.ndir, 128), 128, 0, s>>>(h.ndir, h.partials, h.maxblk, out, nullptr, 0.0,
                                                                  nullptr);
+    PR_LAUNCH();
+}
+
+void dd_enable(Hier &h) {
+    if (!h.bsr0 || h.prm.precision != 1 || !h.bsr64) return;
+    cudaStream_t s = h.stream;
+    const long long nv = (long long)h.ndir * (h.n0[0] / 8) * 96;
+    h.bsr_dd = dmalloc<float2>(nv, s);
+    k_dd_split<<<blocks_for(nv, BS), BS, 0, s>>>(nv, h.bsr64, h.bsr_dd);
+    PR_LAUNCH();
+    dfree(h.bsr64, s);
+    h.bsr64 = nullptr;
+    const long long nr = (long long)h.ndir * h.n0[0];
+    h.b_dd = dmalloc<float2>(nr, s);
+    h.x_dd = dmalloc<float2>(nr, s);
+    h.dd = true;
+}
+
+void dd_load(Hier &h, const double *b, const double *x) {
+    const long long nr = (long long)h.ndir * h.n0[0];
+    k_dd_split<<<blocks_for(nr, BS), BS, 0, h.stream>>>(nr, b, h.b_dd);
+    PR_LAUNCH();
+    k_dd_split<<<blocks_for(nr, BS), BS, 0, h.stream>>>(nr, x, h.x_dd);
+    PR_LAUNCH();
+}
+
+void dd_store(Hier &h, double *x) {
+    const long long nr = (long long)h.ndir * h.n0[0];
+    k_dd_join<<<blocks_for(nr, BS), BS, 0, h.stream>>>(nr, h.x_dd, x);
     PR_LAUNCH();
 }
 

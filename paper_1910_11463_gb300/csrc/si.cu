@@ -120,6 +120,7 @@ BatchSolve solve_batch(Hier &h, const double *b, double *x, double tol, int maxi
     norms0(h, b, h.bnorm);
     std::vector<int> ones(nd, 1);
     set_all_active(h);
+    if (h.dd) dd_load(h, b, x);
     residual0(h, b, x, tol, true);
     std::vector<double> r0(nd), rn(nd), bn(nd);
     std::vector<int> act(nd), itd(nd, 0);
@@ -186,6 +187,7 @@ BatchSolve solve_batch(Hier &h, const double *b, double *x, double tol, int maxi
             else if (itd[d] == 0) itd[d] = k;
         }
     }
+    if (h.dd) dd_store(h, x);
     PR_CUDA(cudaMemcpyAsync(rn.data(), h.rnorm, sizeof(double) * nd, cudaMemcpyDeviceToHost, s));
     PR_CUDA(cudaStreamSynchronize(s));
     BatchSolve out;
@@ -329,7 +331,8 @@ Hier::~Hier() {
         if (e) cudaEventDestroy(e);
     if (stream) {
         for (auto &L : lev) free_level(L, stream);
-        void *ptrs[] = {bsr64, bsr32, dsign, partials, rnorm, bnorm, rnorm0, active, d_err, d_n0, d_row00};
+        void *ptrs[] = {bsr64, bsr32, dsign, partials, rnorm, bnorm, rnorm0, active, d_err, d_n0, d_row00,
+                        bsr_dd, b_dd, x_dd};
         for (void *p : ptrs) dfree(p, stream);
         cudaStreamSynchronize(stream);
         cudaStreamDestroy(stream);
@@ -450,6 +453,7 @@ void build_batch(HexBatch &B, const pair_mesh &mesh, const double *omega_h, cons
     build_hierarchy(*h);
     alloc_cycle_vectors(*h);
     level0_bytes(*h);
+    dd_enable(*h);
     prof_enable(*h);
 }
 
