@@ -55,6 +55,31 @@ inline void dfree(void *p, cudaStream_t s) {
 
 inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
+// Programmatic dependent launch: the kernel may start while the previous kernel
+// on the stream finishes; it must begin with pdl_begin() (device side), which waits
+// for the previous grid's completion and memory, then lets the next kernel launch.
+template <typename... KArgs, typename... Args>
+void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cuda_check(cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...), "kernel launch", __FILE__, __LINE__);
+}
+
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_begin() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+#endif
+
 #ifdef __CUDACC__
 // |x| as an ordered integer key: for non-NaN doubles the bit patterns of |x|
 // order exactly as the values, so pivot searches and maxima of magnitudes run

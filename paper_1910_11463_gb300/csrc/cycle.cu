@@ -134,6 +134,7 @@ template <class T>
 __global__ void __launch_bounds__(BS) k_res0_bsr(int n, int N, const int8_t *dsign, const double *bsr64,
                                                  const double *b, const double *x, T *r, double *partials,
                                                  int maxblk, const int *active) {
+    pdl_begin();
     HexRow q = hex_row(n);
     if (active && !active[q.m]) return;
     constexpr bool F32 = std::is_same<T, float>::value;
@@ -199,6 +200,7 @@ __device__ __forceinline__ void load_dd4(const float2 *p, float2 *w) {
 __global__ void __launch_bounds__(BS) k_res0_bsr_dd(int n, int N, const int8_t *dsign, const float2 *vals,
                                                     const float2 *b, const float2 *x, float *r, double *partials,
                                                     int maxblk, const int *active) {
+    pdl_begin();
     HexRow q = hex_row(n);
     if (active && !active[q.m]) return;
     float s2f = 0.0f;
@@ -252,6 +254,7 @@ template <class T>
 __global__ void __launch_bounds__(BS) k_res0_csr(const int *row0, const int *nrow, const int *rowptr, const int *col,
                                                  const double *val, const double *b, const double *x, T *r,
                                                  double *partials, int maxblk, const int *active) {
+    pdl_begin();
     int m = blockIdx.y;
     if (active && !active[m]) return;
     int li = blockIdx.x * blockDim.x + threadIdx.x;
@@ -272,6 +275,7 @@ __global__ void __launch_bounds__(BS) k_res0_csr(const int *row0, const int *nro
 // k, k+32, ... in order, then a fixed shuffle tree (deterministic)
 __global__ void k_norm_final(int ndir, const double *partials, int maxblk, double *out, const double *bnorm,
                              double tol, int *active) {
+    pdl_begin();
     int m = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     int lane = threadIdx.x & 31;
     if (m >= ndir) return;
@@ -352,6 +356,7 @@ struct SellJob {
 // shuffles.
 template <class T, int MODE, int G>
 __global__ void __launch_bounds__(BS) k_sell(SellJob<T> j) {
+    pdl_begin();
     const long long t = (long long)blockIdx.x * BS + threadIdx.x;
     const int q = (int)(t / G), g = (int)(t % G);
     const int r = j.row[q];
@@ -411,6 +416,7 @@ __device__ __forceinline__ void prolong_row(long long i, int8_t c, int p, const 
 template <class T>
 __global__ void k_prolong(int n, const int8_t *cf, const int *pmap, const int8_t *cfc, const T *xcF, const T *xc,
                           T *y, T *y2) {
+    pdl_begin();
     const long long i0 = 4LL * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
     if (i0 >= n) return;
     if (i0 + 4 <= n) {
@@ -442,6 +448,7 @@ __global__ void k_prolong(int n, const int8_t *cf, const int *pmap, const int8_t
 // single-level hierarchies: x64 += the coarsest solution on active rows
 template <class T>
 __global__ void k_fold_coarsest(int n, const T *xco, double *x64, const int *active, const int *rowdir) {
+    pdl_begin();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || (active && !active[rowdir[i]])) return;
     x64[i] += (double)xco[i];
@@ -452,6 +459,7 @@ __global__ void k_fold_coarsest(int n, const T *xco, double *x64, const int *act
 template <class T>
 __global__ void k_fold_split(int kX, int n, const int *srow, const T *xco, double *x64, const int *active,
                              const int *rowdir) {
+    pdl_begin();
     int k = kX + blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     int i = srow[k];
@@ -464,6 +472,7 @@ template <class T, bool FINAL>
 __global__ void __launch_bounds__(BS) k_relax_bsr(int n, int N, const int8_t *dsign, const T *vals, const int8_t *cf,
                                                   const T *b, const T *in, T *out, int phase, double *x64,
                                                   const T *xco, const int *active, float2 *xdd) {
+    pdl_begin();
     HexRow q = hex_row(n);
     if (!q.valid) return;
     const long long gi = (long long)q.m * N + 8LL * q.e + q.a;
@@ -505,6 +514,7 @@ __global__ void __launch_bounds__(BS) k_relax_bsr(int n, int N, const int8_t *ds
 template <class T>
 __global__ void k_coarsest(const int *seg_row0, const int *seg_n, const int *seg_s0, const int *sptr,
                            const int *scol, const T *sval, const T *dinv, const T *b, T *x, T *xt, int sweeps) {
+    pdl_begin();
     int r0 = seg_row0[blockIdx.x], nr = seg_n[blockIdx.x], s0 = seg_s0[blockIdx.x];
     for (int i = threadIdx.x; i < nr; i += blockDim.x) x[r0 + i] = T(0);
     __syncthreads();
@@ -543,10 +553,10 @@ void launch_sell(const Sell &S, SellJob<T> j, int sms, cudaStream_t s) {
     int G = 1;
     while (G < 8 && (long long)S.npos * G * 2 <= want) G *= 2;
     switch (G) {
-        case 1: k_sell<T, MODE, 1><<<blocks_for(S.npos, BS), BS, 0, s>>>(j); break;
-        case 2: k_sell<T, MODE, 2><<<blocks_for(2LL * S.npos, BS), BS, 0, s>>>(j); break;
-        case 4: k_sell<T, MODE, 4><<<blocks_for(4LL * S.npos, BS), BS, 0, s>>>(j); break;
-        default: k_sell<T, MODE, 8><<<blocks_for(8LL * S.npos, BS), BS, 0, s>>>(j); break;
+        case 1: launch_pdl(k_sell<T, MODE, 1>, blocks_for(S.npos, BS), BS, s, j); break;
+        case 2: launch_pdl(k_sell<T, MODE, 2>, blocks_for(2LL * S.npos, BS), BS, s, j); break;
+        case 4: launch_pdl(k_sell<T, MODE, 4>, blocks_for(4LL * S.npos, BS), BS, s, j); break;
+        default: launch_pdl(k_sell<T, MODE, 8>, blocks_for(8LL * S.npos, BS), BS, s, j); break;
     }
     PR_LAUNCH();
 }
@@ -583,7 +593,7 @@ void relax_c(const Level &L, const T *b, const T *in, T *out, double *x64, const
         launch_sell<T, SM_C_FINAL>(L.sC, j, sms, s);
         const int kX = L.nF + L.nC;
         if (L.n > kX) {
-            k_fold_split<T><<<blocks_for(L.n - kX, BS), BS, 0, s>>>(kX, L.n, L.srow, xco, x64, active, L.rowdir);
+            launch_pdl(k_fold_split<T>, blocks_for(L.n - kX, BS), BS, s, kX, L.n, L.srow, xco, x64, active, L.rowdir);
             PR_LAUNCH();
         }
     } else {
@@ -611,7 +621,7 @@ void vcycle_t(Hier &h, double *x64) {
         L.vF = L.vx;   // replaced by the F sweeps' buffer once the level relaxes
         if (l + 1 < NL) restrict_<T>(L, (const T *)L.vb, (T *)h.lev[l + 1].vb, h.sms, s);
         if (L.n_cseg) {
-            k_coarsest<T><<<L.n_cseg, 256, 0, s>>>(L.d_cseg_row0, L.d_cseg_n, L.d_cseg_s0, L.sptr, L.scol,
+            launch_pdl(k_coarsest<T>, L.n_cseg, 256, s, L.d_cseg_row0, L.d_cseg_n, L.d_cseg_s0, L.sptr, L.scol,
                                                    (const T *)L.sval, lv_dinv<T>(L), (const T *)L.vb, (T *)L.vx,
                                                    (T *)L.vxn, h.prm.coarse_sweeps);
             PR_LAUNCH();
@@ -624,7 +634,7 @@ void vcycle_t(Hier &h, double *x64) {
         const bool bsr = l == 0 && h.bsr0;
         // F sweeps ping-pong between vy and vxn; the C sweep reads the last one
         T *bufs[2] = {(T *)L.vy, (T *)L.vxn};
-        k_prolong<T><<<blocks_for((L.n + 3) / 4, BS), BS, 0, s>>>(L.n, L.cf, L.pmap, C.cf, (const T *)C.vF,
+        launch_pdl(k_prolong<T>, blocks_for((L.n + 3) / 4, BS), BS, s, L.n, L.cf, L.pmap, C.cf, (const T *)C.vF,
                                                                   (const T *)C.vx, bufs[0], bsr ? nullptr : bufs[1]);
         PR_LAUNCH();
         int cur = 0;
@@ -634,11 +644,11 @@ void vcycle_t(Hier &h, double *x64) {
             const T *vals = std::is_same<T, float>::value ? (const T *)h.bsr32 : (const T *)h.bsr64;
             if (h.prof) { rec_event(h.ev[2], s); h.relax_timed = true; }
             for (int f = 0; f < fs; ++f, cur ^= 1) {
-                k_relax_bsr<T, false><<<grid, BS, 0, s>>>(h.hex_n, N, h.dsign, vals, L.cf, (const T *)L.vb, bufs[cur],
+                launch_pdl(k_relax_bsr<T, false>, grid, BS, s, h.hex_n, N, h.dsign, vals, L.cf, (const T *)L.vb, bufs[cur],
                                                           bufs[cur ^ 1], 0, nullptr, nullptr, active, nullptr);
                 PR_LAUNCH();
             }
-            k_relax_bsr<T, true><<<grid, BS, 0, s>>>(h.hex_n, N, h.dsign, vals, L.cf, (const T *)L.vb, bufs[cur],
+            launch_pdl(k_relax_bsr<T, true>, grid, BS, s, h.hex_n, N, h.dsign, vals, L.cf, (const T *)L.vb, bufs[cur],
                                                      nullptr, 1, x64, (const T *)L.vx, active,
                                                      h.dd ? h.x_dd : nullptr);
             PR_LAUNCH();
@@ -662,7 +672,7 @@ void vcycle_t(Hier &h, double *x64) {
     }
     if (NL == 1) {   // single-level hierarchies: x += coarsest solution
         Level &L = h.lev[0];
-        k_fold_coarsest<T><<<blocks_for(L.n, BS), BS, 0, s>>>(L.n, (const T *)L.vx, x64, active, L.rowdir);
+        launch_pdl(k_fold_coarsest<T>, blocks_for(L.n, BS), BS, s, L.n, (const T *)L.vx, x64, active, L.rowdir);
         PR_LAUNCH();
     }
 }
@@ -838,7 +848,8 @@ void prof_enable(Hier &h) {
 
 void residual0(Hier &h, const double *b, const double *x, double tol, bool update_active) {
     cudaStream_t s = h.stream;
-    PR_CUDA(cudaMemsetAsync(h.partials, 0, sizeof(double) * h.maxblk * h.ndir, s));
+    // every block of an active matrix writes its partial; inactive matrices' partials
+    // are not read
     int *act = update_active ? h.active : nullptr;
     if (h.prof) rec_event(h.ev[0], s);
     Level &L = h.lev[0];
@@ -847,28 +858,28 @@ void residual0(Hier &h, const double *b, const double *x, double tol, bool updat
     if (h.bsr0 && h.dd) {
         int N = h.n0[0];
         dim3 g3(blocks_for(h.hex_n, 32), h.hex_n * h.hex_n, h.ndir);
-        k_res0_bsr_dd<<<g3, BS, 0, s>>>(h.hex_n, N, h.dsign, h.bsr_dd, h.b_dd, h.x_dd, (float *)L.vb, h.partials,
+        launch_pdl(k_res0_bsr_dd, g3, BS, s, h.hex_n, N, h.dsign, h.bsr_dd, h.b_dd, h.x_dd, (float *)L.vb, h.partials,
                                         h.maxblk, act);
     } else if (h.bsr0) {
         int N = h.n0[0];
         dim3 g3(blocks_for(h.hex_n, 32), h.hex_n * h.hex_n, h.ndir);
         if (f32)
-            k_res0_bsr<float><<<g3, BS, 0, s>>>(h.hex_n, N, h.dsign, h.bsr64, b, x, (float *)L.vb, h.partials,
+            launch_pdl(k_res0_bsr<float>, g3, BS, s, h.hex_n, N, h.dsign, h.bsr64, b, x, (float *)L.vb, h.partials,
                                                   h.maxblk, act);
         else
-            k_res0_bsr<double><<<g3, BS, 0, s>>>(h.hex_n, N, h.dsign, h.bsr64, b, x, (double *)L.vb, h.partials,
+            launch_pdl(k_res0_bsr<double>, g3, BS, s, h.hex_n, N, h.dsign, h.bsr64, b, x, (double *)L.vb, h.partials,
                                                    h.maxblk, act);
     } else {
         if (f32)
-            k_res0_csr<float><<<grid, BS, 0, s>>>(h.d_row00, h.d_n0, L.rowptr, L.col, L.val, b, x, (float *)L.vb,
+            launch_pdl(k_res0_csr<float>, grid, BS, s, h.d_row00, h.d_n0, L.rowptr, L.col, L.val, b, x, (float *)L.vb,
                                                   h.partials, h.maxblk, act);
         else
-            k_res0_csr<double><<<grid, BS, 0, s>>>(h.d_row00, h.d_n0, L.rowptr, L.col, L.val, b, x, (double *)L.vb,
+            launch_pdl(k_res0_csr<double>, grid, BS, s, h.d_row00, h.d_n0, L.rowptr, L.col, L.val, b, x, (double *)L.vb,
                                                    h.partials, h.maxblk, act);
     }
     PR_LAUNCH();
     if (h.prof) rec_event(h.ev[1], s);
-    k_norm_final<<<blocks_for(32LL * h.ndir, 128), 128, 0, s>>>(h.ndir, h.partials, h.maxblk, h.rnorm, h.bnorm, tol,
+    launch_pdl(k_norm_final, blocks_for(32LL * h.ndir, 128), 128, s, h.ndir, h.partials, h.maxblk, h.rnorm, h.bnorm, tol,
                                                                  act);
     PR_LAUNCH();
 }
