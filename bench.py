@@ -286,9 +286,10 @@ def run_ours(args):
              "outer residual in double-float pairs (FP32 pipe), level 0 block form" if args.precision else
              "FP64 outer residual, level 0 block form"),
                                                   tot("t_res0_ms"), tot("n_res0"), tot("gb_res0")),
-        ("k_relax_f+k_relax_c level 0" if tet else "k_relax_bsr"): (
+        ("k_relax_f+k_relax_c level 0" if tet else "k_relax0_split" if args.precision else "k_relax_bsr"): (
             "FP32 F-F-C Jacobi, level 0 " + ("CF-split CSR; one unit = one V-cycle's three sweeps" if tet
-                                             else "block form; one unit = one V-cycle's three sweeps"),
+                                             else "CF-split block copy; one unit = one V-cycle's three sweeps"
+                                             if args.precision else "block form; one unit = one V-cycle's sweeps"),
             tot("t_relax0_ms"), tot("n_relax0"), tot("gb_relax0")),
         "k_relax_f+k_relax_c": ("FP32 F-F-C Jacobi, levels >= 1 (CF-split CSR); one unit = every coarse "
                                 "level's sweeps of one V-cycle", tot("t_relaxc_ms"), tot("n_relaxc"), tot("gb_relaxc")),
@@ -423,6 +424,8 @@ def main():
     ap.add_argument("--si-fixed", dest="si_fixed", type=int, default=None,
                     help="run exactly this many SI iterations per step (default: 2 for hex64_s8 and tet40_s8, "
                          "0 = solve to 1e-8 for the others)")
+    ap.add_argument("--one-iteration", action="store_true",
+                    help="profiling aid: assembly + setup + one SI iteration of the workload, no timing line")
     ap.add_argument("--si-iters", type=int, default=18,
                     help="SI iterations the setup is amortised over in the reference arm (hex32_s4 needs 18)")
     args = ap.parse_args()
@@ -431,7 +434,29 @@ def main():
         args.distance = DISTANCE.get(args.config, 1)
     if args.impl == "reference":
         return run_reference(args)
+    if args.one_iteration:
+        return run_one_iteration(args)
     return run_ours(args)
+
+
+def run_one_iteration(args):
+    """One SI iteration of the workload (the launch sequence an ncu capture of the
+    V-cycle kernels needs, without the bench's repetitions)."""
+    import torch
+    import __graft_entry__ as g
+    torch.cuda.set_device(0)
+    g.build()
+    from paper_1910_11463_gb300 import inputs as I
+    from paper_1910_11463_gb300 import pair
+    prob = I.config(args.config)
+    air = pair.default_air_params(precision=args.precision, theta=args.theta, phi_R=args.phi_R, phi_A=args.phi_A,
+                                  distance=args.distance)
+    si = pair.default_si_params(tol=1e-8, max_iters=1, inner_tol=1e-8, inner_maxit=200)
+    phi, _, info = pair.si_solve_problem(prob, air=air, si=si)
+    torch.cuda.synchronize()
+    print(json.dumps({"workload": args.config, "setup_ms": info["t_setup_ms"], "solve_ms": info["t_solve_ms"],
+                      "vcycles": info["vcycles"], "levels": info["levels_max"]}))
+    return 0
 
 
 if __name__ == "__main__":

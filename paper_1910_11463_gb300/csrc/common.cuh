@@ -160,6 +160,11 @@ struct Hier {
     // FP32-refined block form: the outer residual in double-float arithmetic (pairs
     // of floats, hi + lo) instead of the FP64 pipe; block values, b and the solve's
     // iterate are held as pairs during a solve (bsr64 is then not kept)
+    // FP32 relaxation of the block form on CF-split copies: v0[k] holds the three
+    // face rows (float4 each) of the row at split position k of level 0 (F rows,
+    // then C rows, as lev[0].srow); bsr32 is then not kept
+    bool split0 = false;
+    float4 *v0 = nullptr;
     bool dd = false;
     float2 *bsr_dd = nullptr;          // same layout as bsr64
     float2 *b_dd = nullptr, *x_dd = nullptr;   // [rows of the batch]
@@ -204,6 +209,7 @@ void vcycle_correct(Hier &h, double *x);       // x += V(lev[0].vb), zero initia
 // double-float mode (h.dd): b and x to pairs before a solve, x back after it; the
 // residual and the final relaxation then work on h.b_dd / h.x_dd
 void dd_enable(Hier &h);            // bsr_dd from bsr64 (frees bsr64), vectors
+void split0_enable(Hier &h);        // v0 from bsr32 (frees bsr32)
 void dd_load(Hier &h, const double *b, const double *x);
 void dd_store(Hier &h, double *x);
 void norms0(Hier &h, const double *v, double *out);  // per-matrix 2-norms of a level-0 vector

@@ -458,13 +458,19 @@ __global__ void k_fold_coarsest(int n, const T *xco, double *x64, const int *act
 // matrices that end there (split positions [kX, n))
 template <class T>
 __global__ void k_fold_split(int kX, int n, const int *srow, const T *xco, double *x64, const int *active,
-                             const int *rowdir) {
+                             const int *rowdir, float2 *xdd) {
     pdl_begin();
     int k = kX + blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     int i = srow[k];
     if (active && !active[rowdir[i]]) return;
-    x64[i] += (double)xco[i];
+    if (xdd) {
+        const float2 xo = xdd[i];
+        const float2 s2 = two_sum(xo.x, (float)xco[i]);
+        xdd[i] = fast_two_sum(s2.x, __fadd_rn(xo.y, s2.y));
+    } else {
+        x64[i] += (double)xco[i];
+    }
 }
 
 // ---- BSR (hex level 0) relaxation, unit diagonal ------------------------------
@@ -507,6 +513,82 @@ __global__ void __launch_bounds__(BS) k_relax_bsr(int n, int N, const int8_t *ds
     } else {
         x64[gi] += (double)v;
     }
+}
+
+// ---- level-0 relaxation on the CF-split block copy (FP32) -------------------------
+// One thread per row of the F (or C) group: the row's three face rows are read from
+// v0 at its split position (contiguous across the group, so a sweep reads only its
+// own rows' blocks), the row's element and node follow from its index.  x += v:
+// a float pair (x_dd) or FP64.
+__device__ __forceinline__ void x_add(long long gi, float v, float2 *xdd, double *x64) {
+    if (xdd) {
+        const float2 xo = xdd[gi];
+        const float2 s2 = two_sum(xo.x, v);
+        xdd[gi] = fast_two_sum(s2.x, __fadd_rn(xo.y, s2.y));
+    } else {
+        x64[gi] += (double)v;
+    }
+}
+
+// rows at split positions [k0, k0 + cnt): F sweep (out, optional fold into x) or the
+// final C sweep (into x)
+template <bool FINAL>
+__global__ void __launch_bounds__(BS) k_relax0_split(int n, int N, const int8_t *dsign, const int *srow, int k0,
+                                                     int cnt, const float4 *v0, const float *b, const float *in,
+                                                     float *out, bool fold, float2 *xdd, double *x64,
+                                                     const int *active) {
+    pdl_begin();
+    const int k = blockIdx.x * BS + threadIdx.x;
+    if (k >= cnt) return;
+    const int gi = srow[k0 + k];
+    const int m = gi / N;
+    const int r = gi - m * N;
+    const int e = r >> 3, a = r & 7;
+    const int ix = e % n, t = e / n, iy = t % n, iz = t / n;
+    const int idx[3] = {ix, iy, iz};
+    const int stride[3] = {1, n, n * n};
+    const int act = active ? active[m] : 1;
+    const float xin = in[gi], bi = b[gi];
+    const float *xm = in + (long long)m * N;
+    float acc = 0.0f;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const int sg = dsign[3 * m + d];
+        if (sg == 0) continue;
+        const bool has = sg > 0 ? idx[d] > 0 : idx[d] < n - 1;
+        if (!has) continue;
+        const int ep = sg > 0 ? e - stride[d] : e + stride[d];
+        const int o = sg > 0 ? 1 : 0;
+        const float4 w = __ldcs(v0 + 3LL * (k0 + k) + d);
+        const float *xb = xm + 8LL * ep;
+        acc += w.x * xb[face_node(d, o, 0)];
+        acc += w.y * xb[face_node(d, o, 1)];
+        acc += w.z * xb[face_node(d, o, 2)];
+        acc += w.w * xb[face_node(d, o, 3)];
+    }
+    if (!act) return;
+    const float v = xin + (bi - (acc + xin));
+    if (!FINAL) {
+        out[gi] = v;
+        if (fold) x_add(gi, v, xdd, x64);
+    } else {
+        x_add(gi, v, xdd, x64);
+    }
+}
+
+// v0 from the element-ordered block form, by split position
+__global__ void k_split0_copy(int nrows, int N, const int *srow, const float *bsr32, float4 *v0) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nrows) return;
+    const int gi = srow[k];
+    const long long m = gi / N;
+    const int r = gi - (int)m * N;
+    const int e = r >> 3, a = r & 7;
+    const long long E = N / 8;
+    const float *src = bsr32 + ((m * E + e) * 3) * 32 + a * 4;
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+        v0[3LL * k + d] = make_float4(src[d * 32], src[d * 32 + 1], src[d * 32 + 2], src[d * 32 + 3]);
 }
 
 // ---- coarsest level: Jacobi sweeps, one CTA per matrix segment ---------------
@@ -593,7 +675,8 @@ void relax_c(const Level &L, const T *b, const T *in, T *out, double *x64, const
         launch_sell<T, SM_C_FINAL>(L.sC, j, sms, s);
         const int kX = L.nF + L.nC;
         if (L.n > kX) {
-            launch_pdl(k_fold_split<T>, blocks_for(L.n - kX, BS), BS, s, kX, L.n, L.srow, xco, x64, active, L.rowdir);
+            launch_pdl(k_fold_split<T>, blocks_for(L.n - kX, BS), BS, s, kX, L.n, L.srow, xco, x64, active, L.rowdir,
+                       (float2 *)nullptr);
             PR_LAUNCH();
         }
     } else {
@@ -634,11 +717,38 @@ void vcycle_t(Hier &h, double *x64) {
         const bool bsr = l == 0 && h.bsr0;
         // F sweeps ping-pong between vy and vxn; the C sweep reads the last one
         T *bufs[2] = {(T *)L.vy, (T *)L.vxn};
+        const bool split0 = bsr && h.split0 && std::is_same<T, float>::value;
         launch_pdl(k_prolong<T>, blocks_for((L.n + 3) / 4, BS), BS, s, L.n, L.cf, L.pmap, C.cf, (const T *)C.vF,
-                                                                  (const T *)C.vx, bufs[0], bsr ? nullptr : bufs[1]);
+                   (const T *)C.vx, bufs[0], (bsr && !split0) ? nullptr : bufs[1]);
         PR_LAUNCH();
         int cur = 0;
-        if (bsr) {
+        if (split0) {
+            // F sweeps over the F rows (the last one folds into x), C sweep over the C rows,
+            // then the rows of matrices that end at level 0
+            const int N = h.n0[0];
+            const int kX = L.nF + L.nC;
+            float2 *xdd = h.dd ? h.x_dd : nullptr;
+            if (h.prof) { rec_event(h.ev[2], s); h.relax_timed = true; }
+            for (int f = 0; f < fs; ++f, cur ^= 1)
+                if (L.nF > 0) {
+                    launch_pdl(k_relax0_split<false>, blocks_for(L.nF, BS), BS, s, h.hex_n, N, h.dsign, L.srow, 0,
+                               L.nF, h.v0, (const float *)L.vb, (const float *)bufs[cur], (float *)bufs[cur ^ 1],
+                               f == fs - 1, xdd, x64, active);
+                    PR_LAUNCH();
+                }
+            if (L.nC > 0) {
+                launch_pdl(k_relax0_split<true>, blocks_for(L.nC, BS), BS, s, h.hex_n, N, h.dsign, L.srow, L.nF,
+                           L.nC, h.v0, (const float *)L.vb, (const float *)bufs[cur], (float *)nullptr, true, xdd,
+                           x64, active);
+                PR_LAUNCH();
+            }
+            if (L.n > kX) {
+                launch_pdl(k_fold_split<T>, blocks_for(L.n - kX, BS), BS, s, kX, L.n, L.srow, (const T *)L.vx, x64,
+                           active, L.rowdir, xdd);
+                PR_LAUNCH();
+            }
+            if (h.prof) rec_event(h.ev[3], s);
+        } else if (bsr) {
             int N = h.n0[0];
             dim3 grid(blocks_for(h.hex_n, 32), h.hex_n * h.hex_n, h.ndir);
             const T *vals = std::is_same<T, float>::value ? (const T *)h.bsr32 : (const T *)h.bsr64;
@@ -833,8 +943,16 @@ void level0_bytes(Hier &h) {
         h.bytes_res0[m] = (fF + fC) * 4 * 8 + (nF + nC) * (8 + 8 + sT);
         // each F pass: cf, input and output vector for all rows; A rows and b for F rows
         // C pass: cf, input, x64 (read + write) for all rows; A rows and b for C rows
-        double fpass = fF * 4 * sT + (nF + nC) * (1 + 2 * sT) + nF * sT;
-        h.bytes_relax0[m] = h.prm.f_sweeps * fpass + fC * 4 * sT + (nF + nC) * (1 + sT + 16) + nC * sT;
+        if (h.split0) {
+            // F sweep: per F row its index, input, b and output, and 4 values per upwind
+            // face; the last one also reads and writes x (16 B); C sweep: per C row its
+            // index, input, b, x read + write, and its faces' values
+            double fpass = fF * 4 * sT + nF * (4 + 3 * sT);
+            h.bytes_relax0[m] = h.prm.f_sweeps * fpass + nF * 16 + fC * 4 * sT + nC * (4 + 2 * sT + 16);
+        } else {
+            double fpass = fF * 4 * sT + (nF + nC) * (1 + 2 * sT) + nF * sT;
+            h.bytes_relax0[m] = h.prm.f_sweeps * fpass + fC * 4 * sT + (nF + nC) * (1 + sT + 16) + nC * sT;
+        }
     }
 }
 
@@ -908,6 +1026,19 @@ void dd_enable(Hier &h) {
     h.b_dd = dmalloc<float2>(nr, s);
     h.x_dd = dmalloc<float2>(nr, s);
     h.dd = true;
+}
+
+void split0_enable(Hier &h) {
+    if (!h.bsr0 || h.prm.precision != 1 || !h.bsr32) return;
+    Level &L = h.lev[0];
+    if (!L.srow) return;
+    cudaStream_t s = h.stream;
+    h.v0 = dmalloc<float4>(3LL * std::max(L.n, 1), s);
+    k_split0_copy<<<blocks_for(L.n, BS), BS, 0, s>>>(L.n, h.n0[0], L.srow, h.bsr32, h.v0);
+    PR_LAUNCH();
+    dfree(h.bsr32, s);
+    h.bsr32 = nullptr;
+    h.split0 = true;
 }
 
 void dd_load(Hier &h, const double *b, const double *x) {

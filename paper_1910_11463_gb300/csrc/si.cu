@@ -332,7 +332,7 @@ Hier::~Hier() {
     if (stream) {
         for (auto &L : lev) free_level(L, stream);
         void *ptrs[] = {bsr64, bsr32, dsign, partials, rnorm, bnorm, rnorm0, active, d_err, d_n0, d_row00,
-                        bsr_dd, b_dd, x_dd};
+                        bsr_dd, b_dd, x_dd, v0};
         for (void *p : ptrs) dfree(p, stream);
         cudaStreamSynchronize(stream);
         cudaStreamDestroy(stream);
@@ -452,8 +452,9 @@ void build_batch(HexBatch &B, const pair_mesh &mesh, const double *omega_h, cons
     }
     build_hierarchy(*h);
     alloc_cycle_vectors(*h);
-    level0_bytes(*h);
     dd_enable(*h);
+    split0_enable(*h);
+    level0_bytes(*h);
     prof_enable(*h);
 }
 
