@@ -19,7 +19,7 @@
  *   - exact sweep: block forward substitution in topological order (Sec. 1.1)
  *   - AIR setup (Sec. 1.2, Sec. 4.1.1 Eq. soc, Sec. 4.1.2 filtering): strength,
  *     PMIS CF splitting with seeded hashed keys, one-point P, distance-1/2 lAIR
- *     R = [Z, I], Galerkin R A P
+ *     or degree-1 nAIR R = [Z, I], Galerkin R A P
  *   - V-cycle with FC-Jacobi post-relaxation, AIR solve loop
  *   - source iteration with quadrature sum (Eq. angular_quad, Eq. sn_transport)
  *   - adjoint source iteration and cross-section gradients
@@ -30,6 +30,8 @@
  *   of SplitMix64 at state seed ^ (level << 40) ^ i; lambda_i = 0 -> F;
  *   one-point P takes the strongest C neighbour (first maximum);
  *   distance-2 pattern = strong F neighbours of the distance-1 pattern;
+ *   nAIR degree 1 = the Neumann series of the strong part of A_FF cut after the
+ *   linear term, on the distance-2 pattern (see nair1);
  *   V-cycle: no pre-relaxation; post-relaxation f_sweeps F-Jacobi sweeps then one
  *   C-Jacobi sweep (default 2: the F-F-C ordering usual for AIR); coarsest level
  *   'coarse_sweeps' Jacobi sweeps.
@@ -671,6 +673,7 @@ typedef struct {
     int max_levels, max_coarse, coarse_sweeps;
     uint64_t seed;
     int f_sweeps;   /* F-Jacobi sweeps before the C-Jacobi sweep (1: FC, 2: FFC) */
+    int nair;       /* 0: lAIR; 1: nAIR of degree 1 (Neumann series) */
 } or_params;
 
 typedef struct {
@@ -869,6 +872,95 @@ static int lair(olevel *L, const signed char *SR, int distance, double phi_R)
     return OR_OK;
 }
 
+/* nAIR of degree 1 (Sec. 1.2: the Neumann-expansion variant of AIR; the
+ * best-scaling runs of Sec. 4.1.2 use it with phi_R = 0.1).  With only the strong
+ * (eps_R) entries of A_FF and A_CF kept (marked s), D the diagonal of A_FF and
+ * N = I - D^{-1} A_FF^s, so that A_FF^s = D (I - N), the ideal restriction
+ * -A_CF^s (A_FF^s)^{-1} = -A_CF^s (I + N + N^2 + ...) D^{-1} is cut after the
+ * linear term:
+ *   Z_i = -A_CF^s[i, :] (I + N) D^{-1}
+ * on the strong F neighbours of i and their strong F neighbours.  Entry k:
+ *   t_k = a_ik (k a strong F neighbour of i, else 0), then for every strong F
+ *   neighbour j of i in ascending order and every strong F neighbour k != j of j,
+ *   t_k = fma(a_ij, n_jk, t_k) with n_jk = -(a_jk * (1/a_jj));
+ *   z_k = -(t_k * (1/a_kk)).
+ * A zero diagonal on the way makes the row empty (counted as singular).  Then the
+ * filter of Sec. 4.1.2 as in lAIR. */
+static int nair1(olevel *L, const signed char *SR, double phi_R)
+{
+    int n = L->n, nc = L->nc;
+    L->zrowptr = calloc(nc + 1, sizeof(int));
+    int cap = 1024, used = 0;
+    L->zcol = malloc(sizeof(int) * cap);
+    L->zval = malloc(sizeof(double) * cap);
+    int *pat = malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    int *mark = malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    int *pos = malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    double *t = malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    if (!L->zrowptr || !L->zcol || !L->zval || !pat || !mark || !pos || !t) {
+        free(pat); free(mark); free(pos); free(t); return OR_ERR_OOM;
+    }
+    for (int i = 0; i < n; ++i) mark[i] = -1;
+    L->n_singular = 0;
+    for (int ic = 0; ic < nc; ++ic) {
+        int i = L->cpts[ic];
+        int np = 0;
+        for (int p = L->rowptr[i]; p < L->rowptr[i + 1]; ++p) {
+            int j = L->col[p];
+            if (SR[p] && L->cf[j] == 0 && mark[j] != ic) { mark[j] = ic; pat[np++] = j; }
+        }
+        int n1 = np;
+        for (int a = 0; a < n1; ++a) {
+            int j = pat[a];
+            for (int p = L->rowptr[j]; p < L->rowptr[j + 1]; ++p) {
+                int k = L->col[p];
+                if (SR[p] && L->cf[k] == 0 && mark[k] != ic) { mark[k] = ic; pat[np++] = k; }
+            }
+        }
+        qsort(pat, np, sizeof(int), cmp_int);
+        for (int a = 0; a < np; ++a) { pos[pat[a]] = a; t[a] = 0.0; }
+        int singular = 0;
+        for (int p = L->rowptr[i]; p < L->rowptr[i + 1]; ++p) {
+            int k = L->col[p];
+            if (SR[p] && L->cf[k] == 0) t[pos[k]] = L->val[p];
+        }
+        for (int p = L->rowptr[i]; p < L->rowptr[i + 1] && !singular; ++p) {
+            int j = L->col[p];
+            if (!(SR[p] && L->cf[j] == 0)) continue;
+            double aij = L->val[p], rj = L->dinv[j];
+            if (rj == 0.0) { singular = 1; break; }
+            for (int q = L->rowptr[j]; q < L->rowptr[j + 1]; ++q) {
+                int k = L->col[q];
+                if (k == j || !(SR[q] && L->cf[k] == 0)) continue;
+                double njk = -(L->val[q] * rj);
+                t[pos[k]] = fma(aij, njk, t[pos[k]]);
+            }
+        }
+        for (int a = 0; a < np && !singular; ++a)
+            if (L->dinv[pat[a]] == 0.0) singular = 1;
+        int keep = np;
+        if (singular) { L->n_singular++; keep = 0; }
+        for (int a = 0; a < keep; ++a) t[a] = -(t[a] * L->dinv[pat[a]]);
+        double zmax = 0.0;
+        for (int a = 0; a < keep; ++a) if (fabs(t[a]) > zmax) zmax = fabs(t[a]);
+        double thr = phi_R * zmax;
+        for (int a = 0; a < keep; ++a) {
+            if (phi_R > 0.0 && fabs(t[a]) < thr) continue;
+            if (used == cap) {
+                cap *= 2;
+                L->zcol = realloc(L->zcol, sizeof(int) * cap);
+                L->zval = realloc(L->zval, sizeof(double) * cap);
+                if (!L->zcol || !L->zval) { free(pat); free(mark); free(pos); free(t); return OR_ERR_OOM; }
+            }
+            L->zcol[used] = pat[a]; L->zval[used] = t[a]; ++used;
+        }
+        L->zrowptr[ic + 1] = used;
+    }
+    L->nnzZ = used;
+    free(pat); free(mark); free(pos); free(t);
+    return OR_OK;
+}
+
 /* Galerkin coarse operator A_c = R A P (Sec. 1.2; Sec. 4.1.2 stencil growth).
  * (AP)[k,c] = sum_l a_kl over l ascending with pmap(l) = c;
  * (RAP)[ic,c] = sum_k R[ic,k] (AP)[k,c] over the R row in ascending column
@@ -980,6 +1072,7 @@ void or_params_default(or_params *p)
 {
     p->distance = 1; p->theta = 0.25; p->eps_R = 0.01; p->phi_R = 0.0; p->phi_A = 0.0;
     p->max_levels = 25; p->max_coarse = 100; p->coarse_sweeps = 20; p->seed = 3; p->f_sweeps = 2;
+    p->nair = 0;
 }
 
 /* AIR setup on a CSR matrix with sorted columns (copied). */
@@ -1031,7 +1124,7 @@ void *or_air_setup(int n, const int *rowptr, const int *col, const double *val, 
             L->pmap[i] = best >= 0 ? cmap[best] : -1;
         }
         free(cmap);
-        rc = lair(L, SR, prm->distance, prm->phi_R);
+        rc = prm->nair ? nair1(L, SR, prm->phi_R) : lair(L, SR, prm->distance, prm->phi_R);
         free(S); free(SR);
         if (rc) { *status = rc; break; }
         rc = rap(L, &H->lev[l + 1], prm->phi_A);
