@@ -186,7 +186,7 @@ def run_reference(args):
     # sample); setup amortised over the SI iterations the workload needs
     from oracle import oracle as O
     O.build()
-    air_kw = dict(theta=args.theta, phi_R=args.phi_R, phi_A=args.phi_A, distance=args.distance)
+    air_kw = dict(theta=args.theta, phi_R=args.phi_R, phi_A=args.phi_A, distance=args.distance, nair=args.nair)
     fixed = args.si_fixed if args.si_fixed is not None else FIXED_SI.get(args.config, 0)
     si_iters = fixed or args.si_iters
     times = []
@@ -234,7 +234,7 @@ def run_ours(args):
     N, M = prob.N, prob.M
     geom = pair.TetMesh(prob.verts, prob.tets, prob.nbr) if hasattr(prob, "tets") else prob.n
     fixed = args.si_fixed if args.si_fixed is not None else FIXED_SI.get(args.config, 0)
-    tuned = dict(theta=args.theta, phi_R=args.phi_R, phi_A=args.phi_A, distance=args.distance)
+    tuned = dict(theta=args.theta, phi_R=args.phi_R, phi_A=args.phi_A, distance=args.distance, nair=args.nair)
     air = pair.default_air_params(precision=args.precision, **tuned)
     if fixed:
         si = pair.default_si_params(tol=1e-8, max_iters=fixed, fixed_iters=1, inner_tol=1e-8, inner_maxit=200)
@@ -381,8 +381,9 @@ def run_ours(args):
                            (f"assembly + AIR setup + {fixed} SI iterations from phi=0 (every direction solved from "
                             "psi=0 to 1e-8 relative FP64 residual each iteration); value = DOF*dir*iterations/step "
                             "time (setup included); solve_only_value excludes the setup"),
-                   "air": {"theta": args.theta, "eps_R": 0.01, "phi_R": args.phi_R, "phi_A": args.phi_A,
-                           "distance": args.distance, "relax": "F-F-C Jacobi", "coarsening": "PMIS"},
+                   "air": {"R": "nAIR degree 1" if args.nair else f"lAIR distance {args.distance}",
+                           "theta": args.theta, "eps_R": 0.01, "phi_R": args.phi_R, "phi_A": args.phi_A,
+                           "relax": "F-F-C Jacobi", "coarsening": "PMIS"},
                    "l2": "working set per step >> 129 MB L2 (no flush needed)",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU, all directions in one batch",
                    "precision": "FP32 hierarchy/V-cycle, FP64 refinement" if args.precision else "FP64"},
@@ -419,6 +420,8 @@ def main():
     ap.add_argument("--theta", type=float, default=0.5)
     ap.add_argument("--phi-R", dest="phi_R", type=float, default=0.0)
     ap.add_argument("--phi-A", dest="phi_A", type=float, default=0.05)
+    ap.add_argument("--nair", type=int, default=0, choices=[0, 1],
+                    help="1: R from degree-1 nAIR (Neumann series) instead of lAIR local solves")
     ap.add_argument("--distance", type=int, default=None, choices=[1, 2],
                     help="lAIR distance (default: 2 for tet40_s8, else 1)")
     ap.add_argument("--si-fixed", dest="si_fixed", type=int, default=None,
@@ -450,7 +453,7 @@ def run_one_iteration(args):
     from paper_1910_11463_gb300 import pair
     prob = I.config(args.config)
     air = pair.default_air_params(precision=args.precision, theta=args.theta, phi_R=args.phi_R, phi_A=args.phi_A,
-                                  distance=args.distance)
+                                  distance=args.distance, nair=args.nair)
     si = pair.default_si_params(tol=1e-8, max_iters=1, inner_tol=1e-8, inner_maxit=200)
     phi, _, info = pair.si_solve_problem(prob, air=air, si=si)
     torch.cuda.synchronize()

@@ -62,7 +62,12 @@ typedef struct pair_hier_s *pair_hier;
  *  precision     0: hierarchy values and V-cycle in FP64;
  *                1: FP32 hierarchy and V-cycle under FP64 iterative refinement
  *  f_sweeps      F-point Jacobi sweeps of the post-relaxation before its C-point
- *                sweep (1: F-C, 2: F-F-C) */
+ *                sweep (1: F-C, 2: F-F-C)
+ *  nair          0: R from lAIR local solves; 1: nAIR of degree 1 (Sec. 1.2, the
+ *                Neumann-expansion variant; Sec. 4.1.2 runs it with phi_R = 0.1):
+ *                Z_i = -A_CF^s[i,:] (I + N) D_FF^{-1}, N = I - D_FF^{-1} A_FF^s, where
+ *                ^s keeps the eps_R-strong entries (and the diagonal), on the
+ *                distance-2 pattern; `distance` is then not used */
 typedef struct {
     int distance;
     double theta, eps_R, phi_R, phi_A;
@@ -70,11 +75,12 @@ typedef struct {
     uint64_t seed;
     int precision;
     int f_sweeps;
+    int nair;
 } air_params;
 
 /* Fills the defaults: distance 1, theta 0.25, eps_R 0.01, phi_R 0, phi_A 0,
  * max_levels 25, max_coarse 100, coarse_sweeps 20, seed 3, precision 1,
- * f_sweeps 2. */
+ * f_sweeps 2, nair 0. */
 PAIR_API void air_params_default(air_params *p);
 
 /* A square CSR matrix in device memory. */

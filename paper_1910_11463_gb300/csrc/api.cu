@@ -48,6 +48,7 @@ void check_params(const air_params *p) {
                "max_levels, max_coarse must be >= 1 and coarse_sweeps >= 0");
     PR_REQUIRE(p->precision == 0 || p->precision == 1, PAIR_ERR_ARG, "precision must be 0 (FP64) or 1 (FP32)");
     PR_REQUIRE(p->f_sweeps >= 1 && p->f_sweeps <= 8, PAIR_ERR_ARG, "f_sweeps must lie in [1, 8]");
+    PR_REQUIRE(p->nair == 0 || p->nair == 1, PAIR_ERR_ARG, "nair must be 0 (lAIR) or 1 (nAIR degree 1)");
 }
 
 __global__ void k_concat_rowptr(int n, const int *in, int *out, int off) {
@@ -98,6 +99,7 @@ void air_params_default(air_params *p) {
     p->seed = 3;
     p->precision = 1;
     p->f_sweeps = 2;
+    p->nair = 0;
 }
 
 void si_params_default(si_params *p) {

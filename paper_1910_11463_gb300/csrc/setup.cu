@@ -270,6 +270,69 @@ __device__ __forceinline__ int pat_find(const int *pat, int np, int k) {
     return -1;
 }
 
+// ---- nAIR of degree 1 (Neumann series cut after the linear term) -----------
+// Thread per C point, on the distance-2 pattern (sorted, from k_lair_pattern):
+//   t_k = a_ik for strong F neighbours k of i (else 0); for every strong F
+//   neighbour j of i (ascending) and every strong F neighbour k != j of j
+//   (ascending): t_k = fma(a_ij, n_jk, t_k), n_jk = -(a_jk * (1/a_jj));
+//   z_k = -(t_k * (1/a_kk)), i.e. Z_i = -A_CF^s[i,:] (I + N) D^{-1} with
+//   N = I - D^{-1} A_FF^s.  A zero diagonal on the way empties the row (counted
+//   as singular).  The values are accumulated in the row's slots of zval and the
+//   phi_R filter compacts them in place.
+__global__ void k_nair(int nc, const int *cpts, const int *rowptr, const int *col, const double *val,
+                       const uint8_t *S, const int8_t *cf, const double *dinv, const int *candptr, const int *cand,
+                       const int *npat, const int *zrowptr, int *zcol, double *zval, int *keep, int *nsing_dir,
+                       const int *rowdir, double phi_R) {
+    int ic = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ic >= nc) return;
+    const int i = cpts[ic];
+    const int np = npat[ic];
+    const int *pat = cand + candptr[ic];
+    const int base = zrowptr[ic];
+    double *t = zval + base;
+    for (int e = 0; e < np; ++e) t[e] = 0.0;
+    for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+        int k = col[p];
+        if ((S[p] & 2) && cf[k] == CF_F) t[pat_find(pat, np, k)] = val[p];
+    }
+    bool singular = false;
+    for (int p = rowptr[i]; p < rowptr[i + 1] && !singular; ++p) {
+        int j = col[p];
+        if (!((S[p] & 2) && cf[j] == CF_F)) continue;
+        const double aij = val[p], rj = dinv[j];
+        if (rj == 0.0) { singular = true; break; }
+        for (int q = rowptr[j]; q < rowptr[j + 1]; ++q) {
+            int k = col[q];
+            if (k == j || !((S[q] & 2) && cf[k] == CF_F)) continue;
+            const double njk = -(val[q] * rj);
+            const int e = pat_find(pat, np, k);
+            t[e] = fma(aij, njk, t[e]);
+        }
+    }
+    for (int e = 0; e < np && !singular; ++e)
+        if (dinv[pat[e]] == 0.0) singular = true;
+    int kept = 0;
+    if (singular) {
+        atomicAdd(&nsing_dir[rowdir[i]], 1);
+    } else {
+        long long zmb = 0;
+        for (int e = 0; e < np; ++e) {
+            t[e] = -(t[e] * dinv[pat[e]]);
+            zmb = max(zmb, absbits(t[e]));
+        }
+        const double thr = phi_R * __longlong_as_double(zmb);
+        for (int e = 0; e < np; ++e) {
+            const double z = t[e];
+            if (phi_R > 0.0 && fabs(z) < thr) continue;
+            zcol[base + kept] = pat[e];
+            zval[base + kept] = z;
+            ++kept;
+        }
+    }
+    keep[ic] = kept;
+}
+
+
 // Thread per C row of the worklist for systems of size <= NM: every lane of a
 // warp works on its own system, so each FP64 instruction carries 32 useful
 // operations.  Workspaces live in shared memory interleaved by thread
@@ -1165,15 +1228,16 @@ void build_hierarchy(Hier &h) {
         dfree(cidx, s);
 
         // ---- lAIR -----------------------------------------------------------
+        const int rdist = prm.nair ? 2 : prm.distance;   // nAIR degree 1 uses the distance-2 pattern
         int *ncand = dmalloc<int>(nc, s);
-        k_lair_ncand<<<blocks_for(nc, BS), BS, 0, s>>>(nc, L.cpts, L.rowptr, L.col, S, L.cf, prm.distance, ncand);
+        k_lair_ncand<<<blocks_for(nc, BS), BS, 0, s>>>(nc, L.cpts, L.rowptr, L.col, S, L.cf, rdist, ncand);
         PR_LAUNCH();
         int *candptr = dmalloc<int>(nc + 1, s);
         long long ncandt = scan_exclusive(ncand, candptr, nc, s);
         int *cand = dmalloc<int>(ncandt, s);
         int *npat = ncand;   // reuse
-        k_lair_pattern<<<blocks_for(nc, BS), BS, 0, s>>>(nc, L.cpts, L.rowptr, L.col, S, L.cf, prm.distance, candptr,
-                                                         cand, npat);
+        k_lair_pattern<<<blocks_for(nc, BS), BS, 0, s>>>(nc, L.cpts, L.rowptr, L.col, S, L.cf, rdist, candptr, cand,
+                                                         npat);
         PR_LAUNCH();
         int *zr = dmalloc<int>(nc + 1, s);
         long long nz = scan_exclusive(npat, zr, nc, s);
@@ -1182,7 +1246,11 @@ void build_hierarchy(Hier &h) {
         int *keep = dmalloc<int>(nc, s);
         int *dsing = dmalloc<int>(ND, s);
         PR_CUDA(cudaMemsetAsync(dsing, 0, sizeof(int) * ND, s));
-        {
+        if (prm.nair) {
+            k_nair<<<blocks_for(nc, 128), 128, 0, s>>>(nc, L.cpts, L.rowptr, L.col, L.val, S, L.cf, L.dinv, candptr,
+                                                       cand, npat, zr, zc, zv, keep, dsing, L.rowdir, prm.phi_R);
+            PR_LAUNCH();
+        } else {
             // rows binned by system size; shared memory per warp sized to the bin
             int8_t *ccls = dmalloc<int8_t>(nc, s);
             k_lair_classes<<<blocks_for(nc, BS), BS, 0, s>>>(nc, npat, ccls);

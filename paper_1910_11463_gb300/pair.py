@@ -29,7 +29,7 @@ class air_params(C.Structure):
     _fields_ = [("distance", C.c_int), ("theta", C.c_double), ("eps_R", C.c_double), ("phi_R", C.c_double),
                 ("phi_A", C.c_double), ("max_levels", C.c_int), ("max_coarse", C.c_int),
                 ("coarse_sweeps", C.c_int), ("seed", C.c_uint64), ("precision", C.c_int),
-                ("f_sweeps", C.c_int)]
+                ("f_sweeps", C.c_int), ("nair", C.c_int)]
 
 
 class pair_csr(C.Structure):

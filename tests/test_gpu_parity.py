@@ -64,15 +64,17 @@ def _compare_hierarchies(H_o, H_g, mat):
         assert Lg.n_singular == Lo.n_singular
 
 
-@pytest.mark.parametrize("distance,phi_R", [(1, 0.0), (2, 0.0), (1, 0.1)])
-def test_setup_bit_exact_batched(pair, distance, phi_R):
+@pytest.mark.parametrize("distance,phi_R,nair", [(1, 0.0, 0), (2, 0.0, 0), (1, 0.1, 0), (1, 0.0, 1), (1, 0.1, 1)])
+def test_setup_bit_exact_batched(pair, distance, phi_R, nair):
+    """Every level of a batched hierarchy equals the oracle's bit for bit (lAIR at
+    distance 1 and 2, with and without the R filter; nAIR of degree 1)."""
     prob = I.small_hex(8, order=2, seed=1)
     mats_o, mats_g = [], []
     for m in range(prob.M):
         mats_o.append(O.hex_assemble(prob.n, prob.omega[m], prob.sigma_t))
         mats_g.append(_gpu_csr(pair, prob.n, prob.omega[m], prob.sigma_t))
-    prm_g = pair.default_air_params(distance=distance, phi_R=phi_R, precision=0)
-    prm_o = O.default_params(distance=distance, phi_R=phi_R)
+    prm_g = pair.default_air_params(distance=distance, phi_R=phi_R, precision=0, nair=nair)
+    prm_o = O.default_params(distance=distance, phi_R=phi_R, nair=nair)
     H_g = pair.Hierarchy(mats_g, prm_g)
     for m in range(prob.M):
         H_o = O.Hierarchy(*mats_o[m], prm_o)
@@ -185,6 +187,18 @@ def test_si_fp32_refined_matches_oracle(pair):
     phi = _cpu(phi)
     assert info["max_inner_resid"] <= 1e-9
     assert np.linalg.norm(phi - ref) <= 1e-7 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-7)])
+def test_si_nair_filtered_matches_oracle(pair, precision, tol):
+    """SI with nAIR of degree 1 and the R filter phi_R = 0.1 (the paper's
+    best-scaling configuration) against the oracle with the same parameters."""
+    prob = I.small_hex(10, order=4, seed=9, ratio=0.8)
+    ref, _, _ = O.si_hex(prob, tol=1e-10, inner_tol=1e-11, params=O.default_params(nair=1, phi_R=0.1))
+    phi, _, info = pair.si_solve_problem(prob, air=pair.default_air_params(precision=precision, nair=1, phi_R=0.1),
+                                         si=pair.default_si_params(tol=1e-10, inner_tol=1e-11 if precision == 0
+                                                                   else 1e-9))
+    assert np.linalg.norm(_cpu(phi) - ref) <= tol * np.linalg.norm(ref)
 
 
 @pytest.mark.parametrize("precision", [0, 1])

@@ -37,15 +37,17 @@ def test_tet_assembly_bit_exact(pair, n, order, seed):
         assert np.array_equal(_cpu(gv).view(np.uint64), v.view(np.uint64)), m
 
 
-def test_tet_distance2_hierarchies_bit_exact(pair):
+@pytest.mark.parametrize("nair", [0, 1])
+def test_tet_distance2_hierarchies_bit_exact(pair, nair):
+    """Jittered tets: distance-2 lAIR and degree-1 nAIR hierarchies equal the oracle's."""
     prob = I.small_tet(5, order=4, seed=7)
     mesh = pair.TetMesh(prob.verts, prob.tets, prob.nbr)
     st = torch.as_tensor(prob.sigma_t, device="cuda")
     dirs = (0, 5, 17, 23)
     mats = [pair.dg_assemble_tet(mesh, prob.omega[m], st) for m in dirs]
-    Hg = pair.Hierarchy(mats, pair.default_air_params(distance=2, precision=0))
+    Hg = pair.Hierarchy(mats, pair.default_air_params(distance=2, precision=0, nair=nair))
     for k, m in enumerate(dirs):
-        Ho = O.Hierarchy(*O.tet_assemble(prob, prob.omega[m]), O.default_params(distance=2))
+        Ho = O.Hierarchy(*O.tet_assemble(prob, prob.omega[m]), O.default_params(distance=2, nair=nair))
         assert Hg.nlevels(k) == Ho.nlev
         for l in range(Ho.nlev):
             a, b = Hg.level(k, l), Ho.level(l)
