@@ -281,9 +281,9 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     tet = hasattr(prob, "tets")
     kern = {
-        ("k_res0_csr" if tet else "k_res0_bsr_dd" if args.precision else "k_res0_bsr"): (
+        ("k_res0_csr" if tet else "k_res0_bsr_dd" if args.precision == 2 else "k_res0_bsr"): (
             ("FP64 outer residual, level 0 CSR" if tet else
-             "outer residual in double-float pairs (FP32 pipe), level 0 block form" if args.precision else
+             "outer residual in double-float pairs (FP32 pipe), level 0 block form" if args.precision == 2 else
              "FP64 outer residual, level 0 block form"),
                                                   tot("t_res0_ms"), tot("n_res0"), tot("gb_res0")),
         ("k_relax_f+k_relax_c level 0" if tet else "k_relax0_split" if args.precision else "k_relax_bsr"): (
@@ -363,6 +363,24 @@ def run_ours(args):
                 "setup_ms": i64["t_setup_ms"], "solve_ms": i64["t_solve_ms"],
                 "speedup_of_fp32_refined_batched": value / world / (N * M * i64["si_iters"] / (ms64 * 1e-3)),
                 "phi_rel_diff_fp32_refined_vs_fp64": err}
+    # variant: the outer residual and iterate in double-float pairs on the FP32 pipe
+    # instead of FP64 (hex block form; same hierarchy, same stopping test)
+    dd = None
+    if args.precision == 1 and not hasattr(prob, "tets") and not args.no_variants:
+        air2 = pair.default_air_params(precision=2, **tuned)
+        solve(air2, si, zero)
+        barrier()
+        e0.record(stream)
+        for _ in range(2):
+            phi2, i2 = solve(air2, si, zero)
+        e1.record(stream)
+        barrier()
+        ms2 = e0.elapsed_time(e1) / 2
+        dd = {"value": N * M * i2["si_iters"] / (ms2 * 1e-3), "ms_per_step": ms2, "si_iters": i2["si_iters"],
+              "vcycles_per_direction_per_iteration": i2["vcycles"] / M / max(i2["si_iters"], 1),
+              "max_inner_resid": i2["max_inner_resid"],
+              "phi_rel_diff_vs_fp64_refinement": (torch.linalg.norm(phi2 - phi) / torch.linalg.norm(phi)).item(),
+              "residual_gbs": i2["gb_res0"] / (i2["t_res0_ms"] * 1e-3) if i2["t_res0_ms"] > 0 else None}
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -371,8 +389,9 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": ("f32 V-cycle + f64 setup/iterate + f32-pair residual" if args.precision and not hasattr(prob, "tets")
-                  else "f32 V-cycle + f64 residual/setup" if args.precision else "f64"),
+        "vs_baseline": None, "dtype": ("f32 V-cycle + f32-pair residual/iterate + f64 setup"
+                                       if args.precision == 2 and not hasattr(prob, "tets")
+                                       else "f32 V-cycle + f64 residual/setup" if args.precision else "f64"),
         "data": "synthetic",
         "config": {"workload": args.config + ": " + WORKLOADS[args.config],
                    "step": ("one complete SI solve from phi=0 (assembly + AIR setup + SI iterations to 1e-8, every "
@@ -386,7 +405,8 @@ def run_ours(args):
                            "relax": "F-F-C Jacobi", "coarsening": "PMIS"},
                    "l2": "working set per step >> 129 MB L2 (no flush needed)",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU, all directions in one batch",
-                   "precision": "FP32 hierarchy/V-cycle, FP64 refinement" if args.precision else "FP64"},
+                   "precision": ("FP32 hierarchy/V-cycle, double-float refinement" if args.precision == 2 else
+                                 "FP32 hierarchy/V-cycle, FP64 refinement" if args.precision else "FP64")},
         "si_iterations": iters, "setup_ms": t_setup, "solve_ms": t_solve,
         "solve_only_value": N * M * iters * world / (t_solve * 1e-3) if t_solve > 0 else None,
         "setup_phase_ms": {"strength+pmis": phases[0], "p+lair": phases[1], "rap": phases[2],
@@ -396,6 +416,7 @@ def run_ours(args):
         "op_complexity": last["op_complexity"], "max_inner_resid": last["max_inner_resid"],
         "roofline": roofline, "clocks": clk, "e2e": e2e, "gpu_launches": launches,
         "fp64_one_direction": fp64,
+        "double_float_refinement": dd,
     }
     if world == 1 or rank == 0:
         line["cpu_baseline"] = (cpu_baseline_oracle(prob, iters, tuned, max_seconds=args.cpu_seconds)
@@ -413,10 +434,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", default="hex32_s4", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", type=int, default=1, choices=[0, 1])
+    ap.add_argument("--precision", type=int, default=1, choices=[0, 1, 2],
+                    help="0 FP64; 1 FP32 V-cycle under FP64 refinement (default); 2 FP32 V-cycle under "
+                         "double-float refinement (hex block form)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true", help="skip the double-float refinement variant")
     ap.add_argument("--theta", type=float, default=0.5)
     ap.add_argument("--phi-R", dest="phi_R", type=float, default=0.0)
     ap.add_argument("--phi-A", dest="phi_A", type=float, default=0.05)

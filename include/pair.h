@@ -61,6 +61,12 @@ typedef struct pair_hier_s *pair_hier;
  *  seed          PMIS key hash seed
  *  precision     0: hierarchy values and V-cycle in FP64;
  *                1: FP32 hierarchy and V-cycle under FP64 iterative refinement
+ *                   (FP64 outer residual and iterate);
+ *                2: as 1, but on the structured hex block form the outer residual
+ *                   is computed in double-float arithmetic (pairs of floats with
+ *                   exact two-sum / two-product, ~2^-44 relative) on the FP32 pipe,
+ *                   and the iterate is held as a float pair during each solve
+ *                   (other meshes and generic matrices: as 1)
  *  f_sweeps      F-point Jacobi sweeps of the post-relaxation before its C-point
  *                sweep (1: F-C, 2: F-F-C)
  *  nair          0: R from lAIR local solves; 1: nAIR of degree 1 (Sec. 1.2, the

@@ -46,7 +46,8 @@ void check_params(const air_params *p) {
                "phi_R and phi_A must lie in [0, 1)");
     PR_REQUIRE(p->max_levels >= 1 && p->max_coarse >= 1 && p->coarse_sweeps >= 0, PAIR_ERR_ARG,
                "max_levels, max_coarse must be >= 1 and coarse_sweeps >= 0");
-    PR_REQUIRE(p->precision == 0 || p->precision == 1, PAIR_ERR_ARG, "precision must be 0 (FP64) or 1 (FP32)");
+    PR_REQUIRE(p->precision >= 0 && p->precision <= 2, PAIR_ERR_ARG,
+               "precision must be 0 (FP64), 1 (FP32 cycle, FP64 refinement) or 2 (FP32 cycle, float-pair refinement)");
     PR_REQUIRE(p->f_sweeps >= 1 && p->f_sweeps <= 8, PAIR_ERR_ARG, "f_sweeps must lie in [1, 8]");
     PR_REQUIRE(p->nair == 0 || p->nair == 1, PAIR_ERR_ARG, "nair must be 0 (lAIR) or 1 (nAIR degree 1)");
 }

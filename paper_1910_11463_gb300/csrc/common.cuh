@@ -106,6 +106,7 @@ struct Sell {
     long long nnz = 0;   // stored slots including padding
     int *ptr = nullptr, *row = nullptr, *len = nullptr, *col = nullptr;
     void *val = nullptr;
+    int G = 0;           // lanes per row chosen by the autotuner (0: size heuristic)
 };
 
 struct Level {
@@ -217,6 +218,7 @@ void alloc_cycle_vectors(Hier &h);
 void set_all_active(Hier &h);   // every matrix of the batch takes part in the next cycle
 void level0_bytes(Hier &h);   // fills bytes_res0 / bytes_relax0 (hex block form), bytes_relaxc
 void prof_enable(Hier &h);
+void autotune_cycle(Hier &h);   // lanes per row of every SELL kernel (timed once per shape)
 
 // assemble.cu
 void hex_assemble(int n, int ndir, const double *omega_d, const double *sigma_t, int *rowptr, int *col,

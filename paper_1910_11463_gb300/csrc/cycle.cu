@@ -10,6 +10,9 @@
 // diagonal implicit, three 8 x 4 face blocks per element, 16-byte row loads);
 // coarse levels are CSR with a group of G lanes per row.
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <type_traits>
 
 #include "common.cuh"
@@ -622,18 +625,13 @@ const float *lv_dinv<float>(const Level &L) { return L.dinv32; }
 template <>
 const double *lv_dinv<double>(const Level &L) { return L.dinv; }
 template <class T, int MODE>
-void launch_sell(const Sell &S, SellJob<T> j, int sms, cudaStream_t s) {
-    if (S.nrows <= 0) return;
+void launch_sell_g(const Sell &S, SellJob<T> j, int G, cudaStream_t s) {
     j.npos = S.npos;
     j.ptr = S.ptr;
     j.row = S.row;
     j.len = S.len;
     j.col = S.col;
     j.val = (const T *)S.val;
-    // lanes per row: enough threads to fill the GPU (about 2048 per SM) on small levels
-    const long long want = (long long)sms * 2048;
-    int G = 1;
-    while (G < 8 && (long long)S.npos * G * 2 <= want) G *= 2;
     switch (G) {
         case 1: launch_pdl(k_sell<T, MODE, 1>, blocks_for(S.npos, BS), BS, s, j); break;
         case 2: launch_pdl(k_sell<T, MODE, 2>, blocks_for(2LL * S.npos, BS), BS, s, j); break;
@@ -641,6 +639,22 @@ void launch_sell(const Sell &S, SellJob<T> j, int sms, cudaStream_t s) {
         default: launch_pdl(k_sell<T, MODE, 8>, blocks_for(8LL * S.npos, BS), BS, s, j); break;
     }
     PR_LAUNCH();
+}
+
+// lanes per row: the autotuner's choice, else enough threads to fill the GPU
+// (about 2048 per SM) on small levels
+int sell_lanes(const Sell &S, int sms) {
+    if (S.G > 0) return S.G;
+    const long long want = (long long)sms * 2048;
+    int G = 1;
+    while (G < 8 && (long long)S.npos * G * 2 <= want) G *= 2;
+    return G;
+}
+
+template <class T, int MODE>
+void launch_sell(const Sell &S, SellJob<T> j, int sms, cudaStream_t s) {
+    if (S.nrows <= 0) return;
+    launch_sell_g<T, MODE>(S, j, sell_lanes(S, sms), s);
 }
 
 // F sweep over the F rows (fold: x64 += the new values, the last level-0 sweep)
@@ -790,7 +804,7 @@ void vcycle_t(Hier &h, double *x64) {
 }  // namespace
 
 void alloc_cycle_vectors(Hier &h) {
-    size_t es = h.prm.precision == 1 ? sizeof(float) : sizeof(double);
+    size_t es = h.prm.precision >= 1 ? sizeof(float) : sizeof(double);
     for (auto &L : h.lev) {
         size_t n = (size_t)std::max(L.n, 1);
         L.vb = dmalloc<char>(n * es, h.stream);
@@ -814,6 +828,7 @@ void alloc_cycle_vectors(Hier &h) {
     int dev = 0;
     PR_CUDA(cudaGetDevice(&dev));
     PR_CUDA(cudaDeviceGetAttribute(&h.sms, cudaDevAttrMultiProcessorCount, dev));
+    autotune_cycle(h);
 }
 
 void set_all_active(Hier &h) {
@@ -885,7 +900,7 @@ void level0_bytes(Hier &h) {
         // entry offset), b, dinv and its input value, writes its output value, and reads
         // its entries (column + value); the C sweep likewise over the C rows.  Gathered
         // neighbour values are taken as cached (the vector is far smaller than L2).
-        double sT = h.prm.precision == 1 ? 4.0 : 8.0;
+        double sT = h.prm.precision >= 1 ? 4.0 : 8.0;
         unsigned long long *cnt = dmalloc<unsigned long long>(4, s);
         for (size_t l = 1; l + 1 < h.lev.size(); ++l) {
             Level &L = h.lev[l];
@@ -907,7 +922,7 @@ void level0_bytes(Hier &h) {
         // and x, writes r; the relaxation counts as on coarse levels, except that the
         // last F sweep and the C sweep add into x64 (read + write) instead of writing
         Level &L = h.lev[0];
-        double sT = h.prm.precision == 1 ? 4.0 : 8.0;
+        double sT = h.prm.precision >= 1 ? 4.0 : 8.0;
         unsigned long long *cnt = dmalloc<unsigned long long>(4 * h.ndir, s);
         PR_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * 4 * h.ndir, s));
         k_level_counts_dir<<<blocks_for(std::max(L.n, 1), BS), BS, 0, s>>>(L.n, L.rowptr, L.cf, L.rowdir, cnt);
@@ -936,7 +951,7 @@ void level0_bytes(Hier &h) {
     PR_CUDA(cudaMemcpyAsync(c.data(), cnt, sizeof(unsigned long long) * c.size(), cudaMemcpyDeviceToHost, s));
     PR_CUDA(cudaStreamSynchronize(s));
     dfree(cnt, s);
-    double sT = h.prm.precision == 1 ? 4.0 : 8.0;
+    double sT = h.prm.precision >= 1 ? 4.0 : 8.0;
     for (int m = 0; m < h.ndir; ++m) {
         double nF = (double)c[4 * m], nC = (double)c[4 * m + 1], fF = (double)c[4 * m + 2], fC = (double)c[4 * m + 3];
         // residual: FP64 face rows (4 values each), b, x read, r written (cycle precision)
@@ -972,7 +987,7 @@ void residual0(Hier &h, const double *b, const double *x, double tol, bool updat
     if (h.prof) rec_event(h.ev[0], s);
     Level &L = h.lev[0];
     dim3 grid(h.maxblk, h.ndir);
-    bool f32 = h.prm.precision == 1;
+    bool f32 = h.prm.precision >= 1;
     if (h.bsr0 && h.dd) {
         int N = h.n0[0];
         dim3 g3(blocks_for(h.hex_n, 32), h.hex_n * h.hex_n, h.ndir);
@@ -1014,7 +1029,7 @@ void norms0(Hier &h, const double *v, double *out) {
 }
 
 void dd_enable(Hier &h) {
-    if (!h.bsr0 || h.prm.precision != 1 || !h.bsr64) return;
+    if (!h.bsr0 || h.prm.precision != 2 || !h.bsr64) return;
     cudaStream_t s = h.stream;
     const long long nv = (long long)h.ndir * (h.n0[0] / 8) * 96;
     h.bsr_dd = dmalloc<float2>(nv, s);
@@ -1029,7 +1044,7 @@ void dd_enable(Hier &h) {
 }
 
 void split0_enable(Hier &h) {
-    if (!h.bsr0 || h.prm.precision != 1 || !h.bsr32) return;
+    if (!h.bsr0 || h.prm.precision < 1 || !h.bsr32) return;
     Level &L = h.lev[0];
     if (!L.srow) return;
     cudaStream_t s = h.stream;
@@ -1055,8 +1070,90 @@ void dd_store(Hier &h, double *x) {
     PR_LAUNCH();
 }
 
+// ---- autotuner ---------------------------------------------------------------------
+// For every SELL store (F sweep, C sweep, restriction on every level) the lanes per
+// row G in {1, 2, 4, 8} are timed with CUDA events on the store itself (one warm-up
+// and three timed launches each, on the zeroed cycle vectors, before the hierarchy's
+// first cycle) and the fastest is kept.  Choices are cached for the process by
+// (kernel, precision, positions, stored entries), so rebuilding a hierarchy of the
+// same shape (the next batch, the next source iteration) reuses them.
+namespace {
+std::mutex g_tune_mutex;
+std::map<std::tuple<int, int, int, long long>, int> g_tune;
+
+template <class T, int MODE>
+void tune_store(Sell &S, const SellJob<T> &j, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
+    if (S.nrows <= 0) return;
+    const auto key = std::make_tuple(MODE, (int)sizeof(T), S.npos, S.nnz);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) { S.G = it->second; return; }
+    }
+    int best = 1;
+    float tbest = 0;
+    for (int G = 1; G <= 8; G *= 2) {
+        launch_sell_g<T, MODE>(S, j, G, s);
+        PR_CUDA(cudaEventRecord(e0, s));
+        for (int r = 0; r < 3; ++r) launch_sell_g<T, MODE>(S, j, G, s);
+        PR_CUDA(cudaEventRecord(e1, s));
+        PR_CUDA(cudaEventSynchronize(e1));
+        float ms = 0;
+        PR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (G == 1 || ms < tbest) { tbest = ms; best = G; }
+    }
+    S.G = best;
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune[key] = best;
+}
+
+template <class T>
+void autotune_t(Hier &h) {
+    cudaStream_t s = h.stream;
+    cudaEvent_t e0, e1;
+    PR_CUDA(cudaEventCreate(&e0));
+    PR_CUDA(cudaEventCreate(&e1));
+    struct Ev {
+        cudaEvent_t a, b;
+        ~Ev() { cudaEventDestroy(a); cudaEventDestroy(b); }
+    } ev{e0, e1};
+    const int NL = (int)h.lev.size();
+    for (int l = 0; l < NL; ++l) {
+        Level &L = h.lev[l];
+        SellJob<T> j{};
+        j.in = (const T *)L.vy;
+        j.dinv = lv_dinv<T>(L);
+        j.b = (const T *)L.vb;
+        j.out = (T *)L.vxn;
+        j.rowdir = L.rowdir;
+        tune_store<T, SM_F>(L.sF, j, s, e0, e1);
+        tune_store<T, SM_C>(L.sC, j, s, e0, e1);
+        if (l + 1 < NL && L.sZ.nrows > 0) {
+            SellJob<T> r{};
+            r.in = (const T *)L.vb;
+            r.out = (T *)h.lev[l + 1].vb;
+            r.cpts = L.cpts;
+            tune_store<T, SM_RESTRICT>(L.sZ, r, s, e0, e1);
+        }
+    }
+    // the tuning launches wrote only the zeroed work vectors: clear them again
+    size_t es = sizeof(T);
+    for (auto &L : h.lev) {
+        size_t n = (size_t)std::max(L.n, 1);
+        PR_CUDA(cudaMemsetAsync(L.vb, 0, n * es, s));
+        PR_CUDA(cudaMemsetAsync(L.vxn, 0, n * es, s));
+    }
+    PR_CUDA(cudaStreamSynchronize(s));
+}
+}  // namespace
+
+void autotune_cycle(Hier &h) {
+    if (h.prm.precision >= 1) autotune_t<float>(h);
+    else autotune_t<double>(h);
+}
+
 void vcycle_correct(Hier &h, double *x) {
-    if (h.prm.precision == 1) vcycle_t<float>(h, x);
+    if (h.prm.precision >= 1) vcycle_t<float>(h, x);
     else vcycle_t<double>(h, x);
 }
 

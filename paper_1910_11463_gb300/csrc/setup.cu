@@ -999,7 +999,7 @@ void build_sell(Hier &h, Sell &S, const int *rows, int nr, const int *rowptr, co
     S.nnz = scan_exclusive(w32, S.ptr, ns, s);
     dfree(w32, s);
     S.col = dmalloc<int>(std::max<long long>(S.nnz, 1), s);
-    if (h.prm.precision == 1) {
+    if (h.prm.precision >= 1) {
         S.val = dmalloc<float>(std::max<long long>(S.nnz, 1), s);
         k_sell_fill<float><<<blocks_for(S.npos, BS), BS, 0, s>>>(S.npos, S.row, S.len, S.ptr, rowptr, col, val,
                                                                  S.col, (float *)S.val);
@@ -1018,7 +1018,7 @@ void build_split(Hier &h, Level &L, bool with_fc) {
     cudaStream_t s = h.stream;
     const int BS = 256;
     const int n = L.n;
-    const size_t es = h.prm.precision == 1 ? sizeof(float) : sizeof(double);
+    const size_t es = h.prm.precision >= 1 ? sizeof(float) : sizeof(double);
     int st[3] = {0, 0, 0}, cnt[3] = {0, 0, 0};
     L.srow = dmalloc<int>(std::max(n, 1), s);
     partition_by_class(L.cf, n, 3, L.srow, st, cnt, s);
@@ -1039,7 +1039,7 @@ void build_split(Hier &h, Level &L, bool with_fc) {
         dfree(len, s);
         L.scol = dmalloc<int>(std::max<long long>(tot, 1), s);
         L.sval = dmalloc<char>(std::max<long long>(tot, 1) * es, s);
-        if (h.prm.precision == 1)
+        if (h.prm.precision >= 1)
             k_split_copy<float><<<blocks_for((long long)nx * 8, BS), BS, 0, s>>>(
                 nx, L.srow + kX, L.rowptr, L.col, L.val, L.sptr, L.scol, (float *)L.sval);
         else
@@ -1121,7 +1121,7 @@ void build_hierarchy(Hier &h) {
         Level &L = h.lev[l];
         int n = L.n;
         L.dinv = dmalloc<double>(n, s);
-        if (prm.precision == 1) L.dinv32 = dmalloc<float>(n, s);
+        if (prm.precision >= 1) L.dinv32 = dmalloc<float>(n, s);
         k_dinv<<<blocks_for(n, BS), BS, 0, s>>>(n, L.rowptr, L.col, L.val, L.dinv, L.dinv32);
         PR_LAUNCH();
         L.cf = dmalloc<int8_t>(n, s);

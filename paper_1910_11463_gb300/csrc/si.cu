@@ -429,7 +429,7 @@ void build_batch(HexBatch &B, const pair_mesh &mesh, const double *omega_h, cons
     PR_CUDA(cudaMemcpyAsync(h->d_row00, L.d_row0, sizeof(int) * nd, cudaMemcpyDeviceToDevice, s));
     if (hex && !adjoint) {
         h->bsr64 = dmalloc<double>((size_t)nd * E * 96, s);
-        if (prm.precision == 1) h->bsr32 = dmalloc<float>((size_t)nd * E * 96, s);
+        if (prm.precision >= 1) h->bsr32 = dmalloc<float>((size_t)nd * E * 96, s);
     } else {
         h->bsr0 = false;
     }

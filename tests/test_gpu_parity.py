@@ -179,10 +179,12 @@ def test_si_fp64_matches_oracle_c1(pair):
     assert info["max_inner_resid"] <= 1e-10
 
 
-def test_si_fp32_refined_matches_oracle(pair):
+@pytest.mark.parametrize("precision", [1, 2])
+def test_si_fp32_refined_matches_oracle(pair, precision):
+    """FP32 V-cycle under FP64 refinement (1) or double-float refinement (2)."""
     prob = I.small_hex(10, order=4, seed=8, ratio=0.8)
     ref, _, info_o = O.si_hex(prob, tol=1e-10, inner_tol=1e-11)
-    phi, _, info = pair.si_solve_problem(prob, air=pair.default_air_params(precision=1),
+    phi, _, info = pair.si_solve_problem(prob, air=pair.default_air_params(precision=precision),
                                          si=pair.default_si_params(tol=1e-10, inner_tol=1e-9))
     phi = _cpu(phi)
     assert info["max_inner_resid"] <= 1e-9
