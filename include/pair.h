@@ -225,9 +225,13 @@ typedef struct {
     int fixed_iters;     /* 1: run exactly max_iters SI iterations (stop early only at tol)
                           * and return PAIR_OK with the last change in info; 0: missing
                           * tol after max_iters > 1 iterations is PAIR_ERR_NOT_CONVERGED */
+    int solver;          /* 0: AIR per direction (the method); 1: exact GPU sweep of the
+                          * block-scaled system in upwind wavefronts (Sec. 1.1, the
+                          * comparison of Sec. 6; structured hexahedral meshes only,
+                          * PAIR_ERR_UNSUPPORTED otherwise); air is then not used */
 } si_params;
 
-PAIR_API void si_params_default(si_params *p);   /* 1e-8, 500, 1e-8, 100, 0, 0, 0, 1, 0 */
+PAIR_API void si_params_default(si_params *p);   /* 1e-8, 500, 1e-8, 100, 0, 0, 0, 1, 0, 0 */
 
 typedef struct {
     int si_iters;

@@ -114,6 +114,7 @@ void si_params_default(si_params *p) {
     p->g_inflow = 0;
     p->use_graphs = 1;
     p->fixed_iters = 0;
+    p->solver = 0;
 }
 
 const char *pair_last_error(void) { return g_last_error.c_str(); }
@@ -383,6 +384,7 @@ pair_status si_solve(const pair_mesh *mesh, const pair_quad *quad, const double 
         check_params(air);
         PR_REQUIRE(sp->tol >= 0 && sp->max_iters >= 1 && sp->inner_tol > 0 && sp->inner_maxit >= 1, PAIR_ERR_ARG,
                    "si_solve: bad si_params");
+        PR_REQUIRE(sp->solver == 0 || sp->solver == 1, PAIR_ERR_ARG, "si_solve: solver must be 0 (AIR) or 1 (sweep)");
         for (int m = 0; m < quad->M; ++m)
             for (int k = 0; k < 3; ++k)
                 PR_REQUIRE(std::isfinite(quad->omega[3 * m + k]) && std::isfinite(quad->w[m]), PAIR_ERR_ARG,

@@ -220,6 +220,10 @@ void level0_bytes(Hier &h);   // fills bytes_res0 / bytes_relax0 (hex block form
 void prof_enable(Hier &h);
 void autotune_cycle(Hier &h);   // lanes per row of every SELL kernel (timed once per shape)
 
+// sweep.cu: x = A^{-1} b for every matrix of a structured-hex batch by upwind
+// wavefronts (needs bsr64); graph-captured when use_graph
+void sweep_solve(Hier &h, const double *b, double *x, bool use_graph);
+
 // assemble.cu
 void hex_assemble(int n, int ndir, const double *omega_d, const double *sigma_t, int *rowptr, int *col,
                   double *val, double *bsr64, float *bsr32, double *W, double *Gin, int *d_err, cudaStream_t s);

@@ -379,7 +379,8 @@ void free_batch_ops(HexBatch &B) {
 }
 
 void build_batch(HexBatch &B, const pair_mesh &mesh, const double *omega_h, const double *omega_d,
-                 const double *sigma_t, const air_params &prm, bool gin, bool adjoint = false) {
+                 const double *sigma_t, const air_params &prm, bool gin, bool adjoint = false,
+                 bool sweep_only = false) {
     const int n = mesh.n;
     const bool hex = mesh.kind == PAIR_MESH_HEX;
     Hier *h = new Hier;
@@ -429,7 +430,7 @@ void build_batch(HexBatch &B, const pair_mesh &mesh, const double *omega_h, cons
     PR_CUDA(cudaMemcpyAsync(h->d_row00, L.d_row0, sizeof(int) * nd, cudaMemcpyDeviceToDevice, s));
     if (hex && !adjoint) {
         h->bsr64 = dmalloc<double>((size_t)nd * E * 96, s);
-        if (prm.precision >= 1) h->bsr32 = dmalloc<float>((size_t)nd * E * 96, s);
+        if (prm.precision >= 1 && !sweep_only) h->bsr32 = dmalloc<float>((size_t)nd * E * 96, s);
     } else {
         h->bsr0 = false;
     }
@@ -450,6 +451,10 @@ void build_batch(HexBatch &B, const pair_mesh &mesh, const double *omega_h, cons
         dfree(L.rowptr, s); dfree(L.col, s); dfree(L.val, s);
         L.rowptr = trp; L.col = tcol; L.val = tval;
     }
+    if (sweep_only) {   // the exact sweep needs the block form only
+        PR_CUDA(cudaStreamSynchronize(s));
+        return;
+    }
     build_hierarchy(*h);
     alloc_cycle_vectors(*h);
     dd_enable(*h);
@@ -469,6 +474,8 @@ void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t,
     long long E = hex ? (long long)n * n * n : (long long)mesh.ntet, N = nbk0 * E;
     PR_CUDA(cudaStreamSynchronize(user));
     bool gin = sp.g_inflow != 0.0;
+    const bool sweep = sp.solver == 1;
+    PR_REQUIRE(!sweep || hex, PAIR_ERR_UNSUPPORTED, "si_solve: the GPU sweep solver needs a structured hex mesh");
     // direction batches admitted by memory
     size_t per = bytes_per_dir(mesh, prm.precision, gin);
     size_t freeb = 0, totb = 0;
@@ -551,7 +558,7 @@ void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t,
                 PR_CUDA(cudaStreamCreateWithFlags(&tmp, cudaStreamNonBlocking));
                 PR_CUDA(cudaEventRecord(e0, tmp));
                 PR_CUDA(cudaStreamSynchronize(tmp));
-                build_batch(Bt, mesh, quad.omega, omega_d, sigma_t, prm, gin);
+                build_batch(Bt, mesh, quad.omega, omega_d, sigma_t, prm, gin, false, sweep);
                 PR_CUDA(cudaStreamSynchronize(Bt.h->stream));
                 PR_CUDA(cudaEventRecord(e1, tmp));
                 PR_CUDA(cudaEventSynchronize(e1));
@@ -564,7 +571,7 @@ void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t,
                 Bt.b = dmalloc<double>((size_t)Bt.nd * N, hs);
                 if (!psi) Bt.xown = dmalloc<double>((size_t)Bt.nd * N, hs);
                 Hier &h = *Bt.h;
-                for (int d = 0; d < Bt.nd; ++d) {
+                for (int d = 0; d < Bt.nd && !sweep; ++d) {
                     int nl = 0;
                     long long tot = 0;
                     for (auto &L : h.lev)
@@ -585,8 +592,14 @@ void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t,
                 k_rhs<4><<<blocks_for((long long)Bt.nd * N, BS), BS, 0, hs>>>(E, Bt.nd, Bt.W, Bt.Gin, sp.g_inflow,
                                                                            sigma_s, q, phi, Bt.b);
             PR_LAUNCH();
-            PR_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * Bt.nd * N, hs));
-            BatchSolve bs = solve_batch(h, Bt.b, x, sp.inner_tol, sp.inner_maxit, sp.use_graphs != 0);
+            BatchSolve bs;
+            if (sweep) {
+                sweep_solve(h, Bt.b, x, sp.use_graphs != 0);
+                bs.converged = true;
+            } else {
+                PR_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * Bt.nd * N, hs));
+                bs = solve_batch(h, Bt.b, x, sp.inner_tol, sp.inner_maxit, sp.use_graphs != 0);
+            }
             if (!bs.converged) {
                 char buf[160];
                 snprintf(buf, sizeof buf, "AIR solve reached %d cycles with relative residual %.3e > %.3e", bs.iters,

@@ -92,7 +92,7 @@ class pair_quad(C.Structure):
 class si_params(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iters", C.c_int), ("inner_tol", C.c_double), ("inner_maxit", C.c_int),
                 ("batch", C.c_int), ("mem_budget_gb", C.c_double), ("g_inflow", C.c_double),
-                ("use_graphs", C.c_int), ("fixed_iters", C.c_int)]
+                ("use_graphs", C.c_int), ("fixed_iters", C.c_int), ("solver", C.c_int)]
 
 
 class si_info(C.Structure):

@@ -203,6 +203,26 @@ def test_si_nair_filtered_matches_oracle(pair, precision, tol):
     assert np.linalg.norm(_cpu(phi) - ref) <= tol * np.linalg.norm(ref)
 
 
+def test_si_gpu_sweep_matches_oracle_sweep(pair):
+    """SI with every direction solved by the GPU wavefront sweep equals the oracle's
+    SI with its exact topological-order sweep, and the AIR-solved SI."""
+    prob = I.small_hex(10, order=4, seed=11, ratio=0.8)
+    ref, _, info_o = O.si_hex(prob, tol=1e-12, use_sweep=True)
+    phi, _, info = pair.si_solve_problem(prob, si=pair.default_si_params(tol=1e-12, solver=1))
+    assert info["vcycles"] == 0 and info["si_iters"] == info_o["si_iters"]
+    assert np.linalg.norm(_cpu(phi) - ref) <= 1e-13 * np.linalg.norm(ref)
+    phi_air, _, _ = pair.si_solve_problem(prob, air=pair.default_air_params(precision=0),
+                                          si=pair.default_si_params(tol=1e-12, inner_tol=1e-13))
+    assert np.linalg.norm(_cpu(phi_air) - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+def test_gpu_sweep_rejects_tets(pair):
+    prob = I.small_tet(3, order=2, seed=1)
+    with pytest.raises(pair.PairError) as e:
+        pair.si_solve_problem(prob, si=pair.default_si_params(solver=1))
+    assert e.value.status == -9
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_si_constant_inflow_fixed_point(pair, precision):
     prob = I.hex_uniform(6, 4, 2.0, 0.75, 1.0)
