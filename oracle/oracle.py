@@ -39,7 +39,8 @@ class or_params(C.Structure):
 
 class or_si_params(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iters", C.c_int), ("inner_tol", C.c_double),
-                ("inner_maxit", C.c_int), ("use_sweep", C.c_int), ("g_inflow", C.c_double)]
+                ("inner_maxit", C.c_int), ("use_sweep", C.c_int), ("g_inflow", C.c_double),
+                ("inner_cycles", C.c_int), ("q_ang", C.c_void_p)]
 
 
 _lib = None
@@ -226,10 +227,14 @@ class Hierarchy:
 # ---------------------------------------------------------------------------
 
 def si_hex(prob, tol=1e-8, max_iters=500, inner_tol=1e-10, inner_maxit=200, use_sweep=False,
-           g_inflow=0.0, params: or_params | None = None, phi0=None):
-    """Source iteration on a HexProblem; returns (phi, psi[M,N], info dict)."""
+           g_inflow=0.0, params: or_params | None = None, phi0=None, inner_cycles=0, q_ang=None):
+    """Source iteration on a HexProblem; returns (phi, psi[M,N], info dict).
+    inner_cycles > 0: each direction solved by exactly that many V-cycles from zero;
+    q_ang: optional (M, N) nodal angular source added to each direction's source."""
     n, M, N = prob.n, prob.M, prob.N
-    sp = or_si_params(tol, max_iters, inner_tol, inner_maxit, int(use_sweep), g_inflow)
+    qa = None if q_ang is None else _f64(q_ang).reshape(M * N)
+    sp = or_si_params(tol, max_iters, inner_tol, inner_maxit, int(use_sweep), g_inflow, int(inner_cycles),
+                      qa.ctypes.data if qa is not None else None)
     prm = params or default_params()
     phi = np.zeros(N) if phi0 is None else _f64(phi0).copy()
     psi = np.zeros((M, N))

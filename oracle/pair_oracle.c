@@ -1258,6 +1258,12 @@ typedef struct {
     int inner_maxit;
     int use_sweep;      /* 1: exact sweep instead of AIR */
     double g_inflow;    /* isotropic inflow angular flux on the inflow boundary */
+    int inner_cycles;   /* > 0: every direction's solve is exactly this many V-cycles from
+                           zero, a fixed approximate inverse (Sec. 3: source iteration then
+                           converges to the modified problem with that inverse) */
+    const double *q_ang; /* NULL, or M*N nodal values of an angular source density added to
+                            direction m's right-hand side (direction-major), e.g. a
+                            manufactured-solution source (Appendix) */
 } or_si_params;
 
 /* Mesh descriptor: kind 0 = n^3 hexahedra (Q1), kind 1 = tetrahedra (P1). */
@@ -1335,9 +1341,11 @@ int or_si(const or_mesh *mesh, int M, const double *omega, const double *w, cons
     double *b = malloc(sizeof(double) * (size_t)N);
     double *ginfl = malloc(sizeof(double) * (size_t)N);
     double *phinew = malloc(sizeof(double) * (size_t)N);
-    double *hist = malloc(sizeof(double) * (size_t)(sp->inner_maxit + 1));
+    double *srcm = malloc(sizeof(double) * (size_t)N);
+    int hmax = sp->inner_cycles > sp->inner_maxit ? sp->inner_cycles : sp->inner_maxit;
+    double *hist = malloc(sizeof(double) * (size_t)(hmax + 1));
     int rc = OR_OK;
-    if (!dirs || !src || !b || !ginfl || !phinew || !hist) { rc = OR_ERR_OOM; goto done; }
+    if (!dirs || !src || !b || !ginfl || !phinew || !srcm || !hist) { rc = OR_ERR_OOM; goto done; }
     for (int i = 0; i < N; ++i) ginfl[i] = sp->g_inflow;
     for (int m = 0; m < M; ++m) {
         rc = odir_build(&dirs[m], mesh, omega + 3 * m, sigma_t, prm, !sp->use_sweep);
@@ -1349,11 +1357,24 @@ int or_si(const or_mesh *mesh, int M, const double *omega, const double *w, cons
         for (int i = 0; i < N; ++i) phinew[i] = 0.0;
         for (int m = 0; m < M; ++m) {
             odir *d = &dirs[m];
-            odg_rhs(&d->g, src, sp->g_inflow != 0.0 ? ginfl : NULL, 1, b);
+            const double *sm = src;
+            if (sp->q_ang) {
+                for (int i = 0; i < N; ++i) srcm[i] = src[i] + sp->q_ang[(size_t)m * N + i];
+                sm = srcm;
+            }
+            odg_rhs(&d->g, sm, sp->g_inflow != 0.0 ? ginfl : NULL, 1, b);
             double *x = psi + (size_t)m * N;
             if (sp->use_sweep) {
                 rc = or_sweep(N, nb, d->rowptr, d->col, d->val, b, x, NULL);
                 if (rc) goto done;
+            } else if (sp->inner_cycles > 0) {
+                for (int i = 0; i < N; ++i) x[i] = 0.0;
+                int iters = 0;
+                or_air_solve(d->hier, b, x, 0.0, sp->inner_cycles, &iters, hist);
+                info[2] += iters;
+                double bn = norm2(N, b);
+                double rel = bn > 0 ? hist[iters] / bn : 0.0;
+                if (rel > info[3]) info[3] = rel;
             } else {
                 for (int i = 0; i < N; ++i) x[i] = 0.0;
                 int iters = 0;
@@ -1380,7 +1401,7 @@ int or_si(const or_mesh *mesh, int M, const double *omega, const double *w, cons
     if (info[1] > sp->tol) rc = OR_ERR_NOT_CONVERGED;
 done:
     if (dirs) for (int m = 0; m < M; ++m) odir_free(&dirs[m]);
-    free(dirs); free(src); free(b); free(ginfl); free(phinew); free(hist);
+    free(dirs); free(src); free(b); free(ginfl); free(phinew); free(srcm); free(hist);
     return rc;
 }
 

@@ -305,6 +305,49 @@ def small_tet(n: int = 3, order: int = 2, seed: int = 4, ratio: float = 0.5, jit
                       np.ones(tets.shape[0]), {"order": order, "seed": seed})
 
 
+def node_coordinates(n: int):
+    """(x, y, z) of every Q1 DOF 8e + a on the unit cube (node a = ax + 2 ay + 4 az at
+    ((ix + ax) h, (iy + ay) h, (iz + az) h), h = 1/n), each an array of length 8 n^3."""
+    ix, iy, iz = element_index_grid(n)
+    a = np.arange(8)
+    h = 1.0 / n
+    x = ((ix[:, None] + (a & 1)[None, :]) * h).ravel()
+    y = ((iy[:, None] + ((a >> 1) & 1)[None, :]) * h).ravel()
+    z = ((iz[:, None] + ((a >> 2) & 1)[None, :]) * h).ravel()
+    return x, y, z
+
+
+def mms_hex(n: int, order: int = 4, sigma_t: float = 1.0, ratio: float = 0.5):
+    """Manufactured solution of the paper's appendix on the unit cube (L = 1):
+        psi(x, Omega) = Phi(x) Psi(x, Omega),
+        Phi = sin(pi x) sin(pi y) sin(pi z),
+        Psi = (1 + 2 mu (x - 1/2)) (1 + 2 eta (y - 1/2)) (1 + 2 xi (z - 1/2)).
+    psi vanishes on the boundary (vacuum inflow).  For a level-symmetric set the odd
+    moments of the weights vanish, so sum_m w_m Psi_m = 4 pi and the discrete scalar
+    flux is phi = 4 pi Phi exactly; the scattering source sigma_s phi / (4 pi) is then
+    sigma_s Phi, and the angular source of direction m is
+        q_m = Omega_m . grad(Phi Psi_m) + sigma_t Phi Psi_m - sigma_s Phi
+    (the appendix writes the scattering term with phi normalised as the angular
+    average; with phi = integral of psi over the sphere it is sigma_s Phi).
+    Returns (problem with q = 0, q_ang (M, 8 n^3) nodal values of q_m, phi_exact at
+    the nodes)."""
+    prob = hex_uniform(n, order, sigma_t, ratio, q=0.0, name=f"mms{n}_s{order}")
+    x, y, z = node_coordinates(n)
+    pi = np.pi
+    sx, sy, sz = np.sin(pi * x), np.sin(pi * y), np.sin(pi * z)
+    cx, cy, cz = np.cos(pi * x), np.cos(pi * y), np.cos(pi * z)
+    Phi = sx * sy * sz
+    q_ang = np.empty((prob.M, prob.N))
+    for m, (mu, eta, xi) in enumerate(prob.omega):
+        f, g, k = 1 + 2 * mu * (x - 0.5), 1 + 2 * eta * (y - 0.5), 1 + 2 * xi * (z - 0.5)
+        Psi = f * g * k
+        dx = pi * cx * sy * sz * Psi + Phi * 2 * mu * g * k
+        dy = pi * sx * cy * sz * Psi + Phi * f * 2 * eta * k
+        dz = pi * sx * sy * cz * Psi + Phi * f * g * 2 * xi
+        q_ang[m] = mu * dx + eta * dy + xi * dz + sigma_t * Phi * Psi - sigma_t * ratio * Phi
+    return prob, q_ang, 4 * pi * Phi
+
+
 def small_hex(n: int, order: int = 2, seed: int = 7, ratio: float = 0.5) -> HexProblem:
     """Small seeded problem for parity tests (spans several tiles, ragged sizes)."""
     return hex_random(n, order, ratio, seed=seed, name=f"hex{n}_s{order}_seed{seed}")
