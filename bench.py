@@ -490,6 +490,8 @@ def main():
     ap.add_argument("--si-fixed", dest="si_fixed", type=int, default=None,
                     help="run exactly this many SI iterations per step (default: 2 for hex64_s8 and tet40_s8, "
                          "0 = solve to 1e-8 for the others)")
+    ap.add_argument("--mms-study", action="store_true",
+                    help="error against the manufactured solution vs V-cycles per SI iteration, 8^3/16^3/32^3")
     ap.add_argument("--one-iteration", action="store_true",
                     help="profiling aid: assembly + setup + one SI iteration of the workload, no timing line")
     ap.add_argument("--si-iters", type=int, default=18,
@@ -502,7 +504,41 @@ def main():
         return run_reference(args)
     if args.one_iteration:
         return run_one_iteration(args)
+    if args.mms_study:
+        return run_mms_study(args)
     return run_ours(args)
+
+
+def run_mms_study(args):
+    """Sec. 3 study: error of the scalar flux against the manufactured solution of
+    the appendix when every direction gets a fixed number of V-cycles from zero per
+    SI iteration, on three meshes; 0 cycles = solved to 1e-10 (the converged error).
+    Prints one JSON line."""
+    import numpy as np
+    import torch
+    import __graft_entry__ as g
+    torch.cuda.set_device(0)
+    g.build()
+    from paper_1910_11463_gb300 import inputs as I
+    from paper_1910_11463_gb300 import pair
+    air = pair.default_air_params(precision=args.precision, theta=args.theta, phi_R=args.phi_R, phi_A=args.phi_A,
+                                  nair=args.nair)
+    rows = []
+    for n in (8, 16, 32):
+        prob, q_ang, phi_exact = I.mms_hex(n, order=4)
+        pe = torch.as_tensor(phi_exact, device="cuda")
+        for cyc in (1, 2, 3, 4, 6, 8, 0):
+            si = pair.default_si_params(tol=1e-10, max_iters=500, inner_tol=1e-10, inner_maxit=200,
+                                        inner_cycles=cyc)
+            phi, _, info = pair.si_solve_problem(prob, air=air, si=si, q_ang=q_ang)
+            err = (torch.linalg.norm(phi - pe) / torch.linalg.norm(pe)).item()
+            rows.append({"n": n, "h": 1.0 / n, "cycles": cyc if cyc else "to 1e-10", "rel_l2_error": err,
+                         "si_iters": info["si_iters"], "final_inner_resid": info["max_inner_resid"],
+                         "solve_ms": info["t_solve_ms"]})
+    print(json.dumps({"study": "MMS error vs fixed V-cycles per SI iteration (Sec. 3)", "quadrature": "S4",
+                      "sigma_t": 1.0, "sigma_s": 0.5, "air": "lAIR" if not args.nair else "nAIR",
+                      "precision": args.precision, "rows": rows}))
+    return 0
 
 
 def run_one_iteration(args):

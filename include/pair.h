@@ -229,9 +229,17 @@ typedef struct {
                           * block-scaled system in upwind wavefronts (Sec. 1.1, the
                           * comparison of Sec. 6; structured hexahedral meshes only,
                           * PAIR_ERR_UNSUPPORTED otherwise); air is then not used */
+    int inner_cycles;    /* 0: every direction solved to inner_tol from psi = 0 (the
+                          * method); l > 0: exactly l V-cycles from psi = 0, a fixed
+                          * approximate inverse, so SI converges to the modified problem
+                          * it defines (Sec. 3, inexact solves; inner_tol is not used) */
+    const double *q_ang; /* NULL, or device array M*N (direction-major) of nodal values of
+                          * an angular source density added to each direction's source
+                          * (sigma_s phi + q) / (4 pi), e.g. the manufactured-solution
+                          * source of the Appendix; caller-owned */
 } si_params;
 
-PAIR_API void si_params_default(si_params *p);   /* 1e-8, 500, 1e-8, 100, 0, 0, 0, 1, 0, 0 */
+PAIR_API void si_params_default(si_params *p);   /* 1e-8, 500, 1e-8, 100, 0, 0, 0, 1, 0, 0, 0, NULL */
 
 typedef struct {
     int si_iters;

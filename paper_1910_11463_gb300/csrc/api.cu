@@ -115,6 +115,8 @@ void si_params_default(si_params *p) {
     p->use_graphs = 1;
     p->fixed_iters = 0;
     p->solver = 0;
+    p->inner_cycles = 0;
+    p->q_ang = nullptr;
 }
 
 const char *pair_last_error(void) { return g_last_error.c_str(); }
@@ -385,6 +387,7 @@ pair_status si_solve(const pair_mesh *mesh, const pair_quad *quad, const double 
         PR_REQUIRE(sp->tol >= 0 && sp->max_iters >= 1 && sp->inner_tol > 0 && sp->inner_maxit >= 1, PAIR_ERR_ARG,
                    "si_solve: bad si_params");
         PR_REQUIRE(sp->solver == 0 || sp->solver == 1, PAIR_ERR_ARG, "si_solve: solver must be 0 (AIR) or 1 (sweep)");
+        PR_REQUIRE(sp->inner_cycles >= 0, PAIR_ERR_ARG, "si_solve: inner_cycles must be >= 0");
         for (int m = 0; m < quad->M; ++m)
             for (int k = 0; k < 3; ++k)
                 PR_REQUIRE(std::isfinite(quad->omega[3 * m + k]) && std::isfinite(quad->w[m]), PAIR_ERR_ARG,

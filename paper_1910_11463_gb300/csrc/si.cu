@@ -21,7 +21,7 @@ constexpr int BS = 256;
 
 template <int NB>
 __global__ void k_rhs(long long E, int ndir, const double *W, const double *Gin, double g, const double *sigma_s,
-                      const double *q, const double *phi, double *b) {
+                      const double *q, const double *phi, const double *qa, double *b) {
     long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (tid >= NB * E * ndir) return;
     long long m = tid / (NB * E);
@@ -33,8 +33,14 @@ __global__ void k_rhs(long long E, int ndir, const double *W, const double *Gin,
     const double *w = W + ((m * E + e) * NB + a) * NB;
     const double *ph = phi + NB * e;
     double acc = 0.0;
+    if (qa) {   // angular source of this direction, added to the isotropic one per node
+        const double *qm = qa + (m * E + e) * NB;
 #pragma unroll
-    for (int c = 0; c < NB; ++c) acc += w[c] * ((ss * ph[c] + qq) * inv4pi);
+        for (int c = 0; c < NB; ++c) acc += w[c] * ((ss * ph[c] + qq) * inv4pi + qm[c]);
+    } else {
+#pragma unroll
+        for (int c = 0; c < NB; ++c) acc += w[c] * ((ss * ph[c] + qq) * inv4pi);
+    }
     if (Gin) acc += g * Gin[tid];
     b[tid] = acc;
 }
@@ -584,13 +590,14 @@ void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t,
             Hier &h = *Bt.h;
             cudaStream_t hs = h.stream;
             double *x = psi ? psi + (size_t)Bt.m0 * N : Bt.xown;
+            const double *qa = sp.q_ang ? sp.q_ang + (size_t)Bt.m0 * N : nullptr;
             PR_CUDA(cudaEventRecord(e0, hs));
             if (hex)
                 k_rhs<8><<<blocks_for((long long)Bt.nd * N, BS), BS, 0, hs>>>(E, Bt.nd, Bt.W, Bt.Gin, sp.g_inflow,
-                                                                           sigma_s, q, phi, Bt.b);
+                                                                           sigma_s, q, phi, qa, Bt.b);
             else
                 k_rhs<4><<<blocks_for((long long)Bt.nd * N, BS), BS, 0, hs>>>(E, Bt.nd, Bt.W, Bt.Gin, sp.g_inflow,
-                                                                           sigma_s, q, phi, Bt.b);
+                                                                           sigma_s, q, phi, qa, Bt.b);
             PR_LAUNCH();
             BatchSolve bs;
             if (sweep) {
@@ -598,7 +605,12 @@ void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t,
                 bs.converged = true;
             } else {
                 PR_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * Bt.nd * N, hs));
-                bs = solve_batch(h, Bt.b, x, sp.inner_tol, sp.inner_maxit, sp.use_graphs != 0);
+                if (sp.inner_cycles > 0) {   // fixed approximate inverse: l cycles from zero
+                    bs = solve_batch(h, Bt.b, x, 0.0, sp.inner_cycles, sp.use_graphs != 0);
+                    bs.converged = true;
+                } else {
+                    bs = solve_batch(h, Bt.b, x, sp.inner_tol, sp.inner_maxit, sp.use_graphs != 0);
+                }
             }
             if (!bs.converged) {
                 char buf[160];

@@ -92,7 +92,8 @@ class pair_quad(C.Structure):
 class si_params(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iters", C.c_int), ("inner_tol", C.c_double), ("inner_maxit", C.c_int),
                 ("batch", C.c_int), ("mem_budget_gb", C.c_double), ("g_inflow", C.c_double),
-                ("use_graphs", C.c_int), ("fixed_iters", C.c_int), ("solver", C.c_int)]
+                ("use_graphs", C.c_int), ("fixed_iters", C.c_int), ("solver", C.c_int),
+                ("inner_cycles", C.c_int), ("q_ang", C.c_void_p)]
 
 
 class si_info(C.Structure):
@@ -348,12 +349,18 @@ def dg_assemble_tet(mesh: "TetMesh", omega, sigma_t: torch.Tensor):
 
 
 def si_solve(n, omega, w, sigma_t, sigma_s, q, air: air_params | None = None, si: si_params | None = None,
-             phi0=None, want_psi: bool = False, device="cuda"):
+             phi0=None, want_psi: bool = False, device="cuda", q_ang=None):
     """Source iteration on the n^3 hex mesh (n an int) or on a TetMesh.  Cross
     sections may be CPU or CUDA tensors (CPU inputs are copied to the device and
-    phi is returned on the device).  Returns (phi, psi or None, info dict)."""
+    phi is returned on the device).  q_ang: optional (M, N) angular source density
+    added per direction.  Returns (phi, psi or None, info dict)."""
     air = air or default_air_params()
     si = si or default_si_params()
+    qa_dev = None
+    if q_ang is not None:
+        qa_dev = torch.as_tensor(q_ang, dtype=torch.float64).to(device).contiguous()
+        si = si_params.from_buffer_copy(si)
+        si.q_ang = qa_dev.data_ptr()
     om = np.ascontiguousarray(omega, dtype=np.float64)
     ww = np.ascontiguousarray(w, dtype=np.float64)
     M = om.shape[0]

@@ -216,6 +216,34 @@ def test_si_gpu_sweep_matches_oracle_sweep(pair):
     assert np.linalg.norm(_cpu(phi_air) - ref) <= 1e-10 * np.linalg.norm(ref)
 
 
+@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-6)])
+@pytest.mark.parametrize("cycles", [1, 3])
+def test_si_inexact_fixed_cycles_matches_oracle(pair, precision, tol, cycles):
+    """Sec. 3 inexact solves: l V-cycles from zero per direction per SI iteration (a
+    fixed approximate inverse) against the oracle with the same l."""
+    prob = I.small_hex(8, order=4, seed=13, ratio=0.8)
+    ref, _, info_o = O.si_hex(prob, tol=1e-11, inner_cycles=cycles)
+    assert info_o["rc"] == 0
+    phi, _, info = pair.si_solve_problem(prob, air=pair.default_air_params(precision=precision),
+                                         si=pair.default_si_params(tol=1e-11, inner_cycles=cycles))
+    assert info["vcycles"] == cycles * prob.M * info["si_iters"]
+    assert np.linalg.norm(_cpu(phi) - ref) <= tol * np.linalg.norm(ref)
+
+
+def test_si_mms_angular_source_matches_oracle(pair):
+    """Appendix MMS source as an angular source: the GPU SI equals the oracle's SI with
+    exact sweeps, and both sit at the discretisation error of the manufactured flux."""
+    prob, q_ang, phi_exact = I.mms_hex(6, order=4)
+    ref, _, _ = O.si_hex(prob, tol=1e-12, use_sweep=True, q_ang=q_ang)
+    phi, _, info = pair.si_solve_problem(prob, air=pair.default_air_params(precision=0),
+                                         si=pair.default_si_params(tol=1e-12, inner_tol=1e-13), q_ang=q_ang)
+    phi = _cpu(phi)
+    assert np.linalg.norm(phi - ref) <= 1e-10 * np.linalg.norm(ref)
+    assert np.linalg.norm(phi - phi_exact) <= 0.05 * np.linalg.norm(phi_exact)
+    phs, _, _ = pair.si_solve_problem(prob, si=pair.default_si_params(tol=1e-12, solver=1), q_ang=q_ang)
+    assert np.linalg.norm(_cpu(phs) - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
 def test_gpu_sweep_rejects_tets(pair):
     prob = I.small_tet(3, order=2, seed=1)
     with pytest.raises(pair.PairError) as e:
