@@ -490,6 +490,8 @@ def main():
     ap.add_argument("--si-fixed", dest="si_fixed", type=int, default=None,
                     help="run exactly this many SI iterations per step (default: 2 for hex64_s8 and tet40_s8, "
                          "0 = solve to 1e-8 for the others)")
+    ap.add_argument("--eps-study", action="store_true",
+                    help="eps_R of the R pattern vs convergence, setup and solve time, distance 1 and 2")
     ap.add_argument("--mms-study", action="store_true",
                     help="error against the manufactured solution vs V-cycles per SI iteration, 8^3/16^3/32^3")
     ap.add_argument("--one-iteration", action="store_true",
@@ -506,7 +508,44 @@ def main():
         return run_one_iteration(args)
     if args.mms_study:
         return run_mms_study(args)
+    if args.eps_study:
+        return run_eps_study(args)
     return run_ours(args)
+
+
+def run_eps_study(args):
+    """Sec. 4.1.1 study: the strength threshold eps_R of the R pattern against
+    convergence, setup and solve time, for distance-1 and distance-2 lAIR, on the
+    bench workload (complete SI solve from phi = 0, every direction to 1e-8).
+    The effective convergence factor of a direction solve is 1e-8^(1/cycles).
+    Prints one JSON line."""
+    import torch
+    import __graft_entry__ as g
+    torch.cuda.set_device(0)
+    g.build()
+    from paper_1910_11463_gb300 import inputs as I
+    from paper_1910_11463_gb300 import pair
+    prob = I.config(args.config)
+    st = torch.as_tensor(prob.sigma_t, device="cuda")
+    ss = torch.as_tensor(prob.sigma_s, device="cuda")
+    qq = torch.as_tensor(prob.q, device="cuda")
+    si = pair.default_si_params(tol=1e-8, max_iters=1000, inner_tol=1e-8, inner_maxit=200)
+    rows = []
+    for distance in (1, 2):
+        for eps in (0.001, 0.01, 0.1, 0.25):
+            air = pair.default_air_params(precision=args.precision, theta=args.theta, phi_R=args.phi_R,
+                                          phi_A=args.phi_A, distance=distance, eps_R=eps)
+            for _ in range(2):   # the first run also tunes the new shapes
+                phi, _, info = pair.si_solve(prob.n, prob.omega, prob.w, st, ss, qq, air=air, si=si)
+            torch.cuda.synchronize()
+            cyc = info["vcycles"] / prob.M / max(info["si_iters"], 1)
+            rows.append({"distance": distance, "eps_R": eps, "setup_ms": info["t_setup_ms"],
+                         "solve_ms": info["t_solve_ms"], "si_iters": info["si_iters"],
+                         "vcycles_per_solve": cyc, "conv_factor": 1e-8 ** (1.0 / cyc) if cyc > 0 else None,
+                         "op_complexity": info["op_complexity"], "levels": info["levels_max"]})
+    print(json.dumps({"study": "eps_R of the R pattern (Sec. 4.1.1)", "workload": args.config,
+                      "theta": args.theta, "phi_A": args.phi_A, "rows": rows}))
+    return 0
 
 
 def run_mms_study(args):
