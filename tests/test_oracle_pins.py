@@ -583,3 +583,24 @@ def test_inexact_si_tends_to_exact_si():
     assert all(d[k + 1] < d[k] / 3 for k in range(3)), d
     ph, _, info = O.si_hex(p, tol=1e-12, inner_cycles=30)
     assert np.linalg.norm(ph - ex) <= 1e-12 * np.linalg.norm(ex)
+
+
+def test_mirrored_direction_is_the_transpose():
+    """Upwind DG with exact quadrature: the operator of -Omega is the transpose of the
+    operator of Omega (volume terms by parts, the upwind side of every face flips), on
+    hexes and on jittered tets.  So the adjoint transport solve of direction m is the
+    forward solve of the mirrored direction, which every level-symmetric set contains."""
+    p = I.small_hex(5, order=4, seed=3)
+    for m in (0, 7, 13):
+        r, c, v = O.hex_assemble(p.n, p.omega[m], p.sigma_t, scaled=False)
+        r2, c2, v2 = O.hex_assemble(p.n, -p.omega[m], p.sigma_t, scaled=False)
+        L = sp.csr_matrix((v, c, r), shape=(p.N, p.N))
+        L2 = sp.csr_matrix((v2, c2, r2), shape=(p.N, p.N))
+        assert abs(L2 - L.T).max() <= 1e-14 * abs(L).max()
+    t = I.small_tet(3, order=4, seed=2)
+    for m in (0, 9):
+        r, c, v = O.tet_assemble(t, t.omega[m], scaled=False)
+        r2, c2, v2 = O.tet_assemble(t, -t.omega[m], scaled=False)
+        L = sp.csr_matrix((v, c, r), shape=(t.N, t.N))
+        L2 = sp.csr_matrix((v2, c2, r2), shape=(t.N, t.N))
+        assert abs(L2 - L.T).max() <= 1e-14 * abs(L).max()
