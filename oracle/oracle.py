@@ -274,8 +274,32 @@ def si_adjoint_hex(prob, psi, g, tol=1e-8, max_iters=500, inner_tol=1e-10, inner
     return dst, dss, dq, phis, {"rc": rc, "iters": int(info[0]), "change": info[1]}
 
 
+def si_adjoint_tet(prob, psi, g, tol=1e-8, max_iters=500, inner_tol=1e-10, inner_maxit=200, use_sweep=False,
+                   params: or_params | None = None):
+    """si_adjoint_hex on a TetProblem's mesh (P1, 4 DOFs per tet)."""
+    M, N, E = prob.M, prob.N, prob.E
+    sp = or_si_params(tol, max_iters, inner_tol, inner_maxit, int(use_sweep), 0.0)
+    prm = params or default_params()
+    dst, dss, dq = np.zeros(E), np.zeros(E), np.zeros(E)
+    phis = np.zeros(N)
+    info = np.zeros(2)
+    rc = lib().or_si_adjoint_tet(*_tet_args(prob), C.c_int(M), _p(_f64(prob.omega)), _p(_f64(prob.w)),
+                                 _p(_f64(prob.sigma_t)), _p(_f64(prob.sigma_s)), _p(_f64(prob.q)),
+                                 _p(_f64(np.ascontiguousarray(psi).reshape(-1))), _p(_f64(g)), C.byref(sp),
+                                 C.byref(prm), _p(dst), _p(dss), _p(dq), _p(phis), _p(info))
+    return dst, dss, dq, phis, {"rc": rc, "iters": int(info[0]), "change": info[1]}
+
+
 def detector_weights(prob, mask):
     """g with J = g^T phi = integral of phi_h over the elements in mask: g_K = M_K 1."""
+    if hasattr(prob, "tets"):
+        # P1 mass matrix of a tetrahedron K: |K| (1 + delta_ab) / 20, row sums |K| / 4
+        g = np.zeros(prob.N)
+        for e in np.nonzero(mask)[0]:
+            x = prob.verts[prob.tets[e]]
+            vol = abs(np.linalg.det(np.stack([x[1] - x[0], x[2] - x[0], x[3] - x[0]]))) / 6.0
+            g[4 * e: 4 * e + 4] = vol / 4.0
+        return g
     h = 1.0 / prob.n
     # row sums of the Q1 mass matrix: h^3 / 8 for every node
     g = np.zeros(prob.N)

@@ -1433,12 +1433,13 @@ int or_si_tet(int T, const double *verts, const int *tets, const int *nbr, int M
 /* psi is the converged forward solution (N*M, direction-major).             */
 /* info[0] = adjoint SI iterations, info[1] = last relative change.          */
 /* ------------------------------------------------------------------------- */
-int or_si_adjoint_hex(int n, int M, const double *omega, const double *w, const double *sigma_t,
-                      const double *sigma_s, const double *q, const double *psi, const double *g,
-                      const or_si_params *sp, const or_params *prm, double *dst, double *dss, double *dq,
-                      double *phis, double *info)
+static int or_si_adjoint(const or_mesh *mesh, int M, const double *omega, const double *w,
+                         const double *sigma_t, const double *sigma_s, const double *q, const double *psi,
+                         const double *g, const or_si_params *sp, const or_params *prm, double *dst, double *dss,
+                         double *dq, double *phis, double *info)
 {
-    int E = n * n * n, N = 8 * E;
+    int nb = mesh->kind == 0 ? 8 : 4, nn = nb * nb;
+    int E = mesh->kind == 0 ? mesh->n * mesh->n * mesh->n : mesh->T, N = nb * E;
     double fourpi = 4.0 * OR_PI;
     odir *dirs = calloc(M, sizeof(odir));
     int **trp = calloc(M, sizeof(int *)), **tci = calloc(M, sizeof(int *));
@@ -1453,8 +1454,7 @@ int or_si_adjoint_hex(int n, int M, const double *omega, const double *w, const 
     int rc = OR_OK;
     if (!dirs || !trp || !tci || !tv || !th || !C || !acc || !pnew || !y || !phi || !hist) { rc = OR_ERR_OOM; goto done; }
     for (int m = 0; m < M; ++m) {
-        or_mesh mesh = {0, n, 0, NULL, NULL, NULL};
-        rc = odir_build(&dirs[m], &mesh, omega + 3 * m, sigma_t, prm, 0);
+        rc = odir_build(&dirs[m], mesh, omega + 3 * m, sigma_t, prm, 0);
         if (rc) goto done;
         rc = csr_transpose(N, dirs[m].rowptr, dirs[m].col, dirs[m].val, &trp[m], &tci[m], &tv[m]);
         if (rc) goto done;
@@ -1471,7 +1471,7 @@ int or_si_adjoint_hex(int n, int M, const double *omega, const double *w, const 
         for (int m = 0; m < M; ++m) {
             odg *gd = &dirs[m].g;
             if (sp->use_sweep) {
-                rc = or_sweep(N, 8, trp[m], tci[m], tv[m], phis, y, NULL);
+                rc = or_sweep_scc(N, nb, trp[m], tci[m], tv[m], phis, y, NULL, NULL);
                 if (rc) goto done;
             } else {
                 for (int i = 0; i < N; ++i) y[i] = 0.0;
@@ -1482,20 +1482,20 @@ int or_si_adjoint_hex(int n, int M, const double *omega, const double *w, const 
             }
             double *c = C + (size_t)m * N;
             for (int e = 0; e < E; ++e) {
-                memcpy(c + 8 * e, y + 8 * e, sizeof(double) * 8);
-                lu_solve_transpose(8, gd->D + (size_t)e * 64, gd->piv + (size_t)e * 8, c + 8 * e);
-                const double *Mk = gd->Mass + (size_t)e * 64;
-                for (int a = 0; a < 8; ++a) {
+                memcpy(c + nb * e, y + nb * e, sizeof(double) * nb);
+                lu_solve_transpose(nb, gd->D + (size_t)e * nn, gd->piv + (size_t)e * nb, c + nb * e);
+                const double *Mk = gd->Mass + (size_t)e * nn;
+                for (int a = 0; a < nb; ++a) {
                     double s = 0.0;
-                    for (int b = 0; b < 8; ++b) s = s + Mk[a * 8 + b] * c[8 * e + b];
-                    acc[8 * e + a] = acc[8 * e + a] + w[m] * s;
+                    for (int b = 0; b < nb; ++b) s = s + Mk[a * nb + b] * c[nb * e + b];
+                    acc[nb * e + a] = acc[nb * e + a] + w[m] * s;
                 }
             }
         }
         double dn = 0.0, pn = 0.0;
         for (int e = 0; e < E; ++e)
-            for (int a = 0; a < 8; ++a) {
-                int i = 8 * e + a;
+            for (int a = 0; a < nb; ++a) {
+                int i = nb * e + a;
                 pnew[i] = g[i] + sigma_s[e] * acc[i] / fourpi;
                 double t = pnew[i] - phis[i];
                 dn = dn + t * t;
@@ -1513,18 +1513,18 @@ int or_si_adjoint_hex(int n, int M, const double *omega, const double *w, const 
         const double *ps = psi + (size_t)m * N;
         odg *gd = &dirs[m].g;
         for (int e = 0; e < E; ++e) {
-            const double *Mk = gd->Mass + (size_t)e * 64;
+            const double *Mk = gd->Mass + (size_t)e * nn;
             double t_psi = 0.0, t_phi = 0.0, t_one = 0.0;
-            for (int a = 0; a < 8; ++a) {
+            for (int a = 0; a < nb; ++a) {
                 double mp = 0.0, mf = 0.0, m1 = 0.0;
-                for (int b = 0; b < 8; ++b) {
-                    mp = mp + Mk[a * 8 + b] * ps[8 * e + b];
-                    mf = mf + Mk[a * 8 + b] * phi[8 * e + b];
-                    m1 = m1 + Mk[a * 8 + b];
+                for (int b = 0; b < nb; ++b) {
+                    mp = mp + Mk[a * nb + b] * ps[nb * e + b];
+                    mf = mf + Mk[a * nb + b] * phi[nb * e + b];
+                    m1 = m1 + Mk[a * nb + b];
                 }
-                t_psi = t_psi + c[8 * e + a] * mp;
-                t_phi = t_phi + c[8 * e + a] * mf;
-                t_one = t_one + c[8 * e + a] * m1;
+                t_psi = t_psi + c[nb * e + a] * mp;
+                t_phi = t_phi + c[nb * e + a] * mf;
+                t_one = t_one + c[nb * e + a] * m1;
             }
             dst[e] = dst[e] - w[m] * t_psi;
             dss[e] = dss[e] + w[m] * t_phi / fourpi;
@@ -1537,4 +1537,22 @@ done:
     if (trp) for (int m = 0; m < M; ++m) { free(trp[m]); free(tci[m]); free(tv[m]); if (th[m]) or_hier_free(th[m]); }
     free(dirs); free(trp); free(tci); free(tv); free(th); free(C); free(acc); free(pnew); free(y); free(phi); free(hist);
     return rc;
+}
+
+int or_si_adjoint_hex(int n, int M, const double *omega, const double *w, const double *sigma_t,
+                      const double *sigma_s, const double *q, const double *psi, const double *g,
+                      const or_si_params *sp, const or_params *prm, double *dst, double *dss, double *dq,
+                      double *phis, double *info)
+{
+    or_mesh mesh = {0, n, 0, NULL, NULL, NULL};
+    return or_si_adjoint(&mesh, M, omega, w, sigma_t, sigma_s, q, psi, g, sp, prm, dst, dss, dq, phis, info);
+}
+
+int or_si_adjoint_tet(int T, const double *verts, const int *tets, const int *nbr, int M, const double *omega,
+                      const double *w, const double *sigma_t, const double *sigma_s, const double *q,
+                      const double *psi, const double *g, const or_si_params *sp, const or_params *prm,
+                      double *dst, double *dss, double *dq, double *phis, double *info)
+{
+    or_mesh mesh = {1, 0, T, verts, tets, nbr};
+    return or_si_adjoint(&mesh, M, omega, w, sigma_t, sigma_s, q, psi, g, sp, prm, dst, dss, dq, phis, info);
 }
