@@ -290,10 +290,10 @@ PAIR_API pair_status si_solve(const pair_mesh *mesh, const pair_quad *quad, cons
  * Each A_m^T gets its own AIR hierarchy (all directions batched).
  *   psi            device N*M, the converged forward angular fluxes (si_solve's psi)
  *   g              device N, dJ/dphi (e.g. detector weights)
- *   dJ_dsigma_t, dJ_dsigma_s, dJ_dq   device n^3 outputs
+ *   dJ_dsigma_t, dJ_dsigma_s, dJ_dq   device per-element outputs (n^3 or ntet)
  *   phi_adjoint    device N output (adjoint scalar flux) or NULL
  * Every direction's hierarchy must fit the memory budget (PAIR_ERR_OOM otherwise).
- * Hexahedral meshes only (PAIR_ERR_UNSUPPORTED for tetrahedra). */
+ * Hexahedral (8 DOFs per element) and tetrahedral (4 DOFs per element) meshes. */
 PAIR_API pair_status si_adjoint(const pair_mesh *mesh, const pair_quad *quad, const double *sigma_t,
                                 const double *sigma_s, const double *q, const double *psi, const double *g,
                                 const air_params *air, const si_params *sp, double *dJ_dsigma_t,

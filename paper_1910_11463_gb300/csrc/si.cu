@@ -252,32 +252,36 @@ __global__ void k_broadcast(long long N, int nd, const double *v, double *out) {
     if (t < N * nd) out[t] = v[t % N];
 }
 
-// acc += sum_m w_m (W_m^T y_m)  (M c_m with c_m = D_m^{-T} y_m, since M is symmetric)
+// acc += sum_m w_m (W_m^T y_m)  (M c_m with c_m = D_m^{-T} y_m, since M is symmetric);
+// NB = DOFs per element (8 for Q1 hexahedra, 4 for P1 tetrahedra)
+template <int NB>
 __global__ void k_wty_acc(long long E, int nd, const double *W, const double *w, const double *y, double *acc) {
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= 8 * E) return;
-    long long e = t >> 3;
-    int a = (int)(t & 7);
+    if (t >= NB * E) return;
+    long long e = t / NB;
+    int a = (int)(t % NB);
     double s = acc[t];
     for (int m = 0; m < nd; ++m) {
-        const double *We = W + ((long long)m * E + e) * 64;
-        const double *ye = y + (long long)m * 8 * E + 8 * e;
+        const double *We = W + ((long long)m * E + e) * NB * NB;
+        const double *ye = y + (long long)m * NB * E + NB * e;
         double u = 0.0;
-        for (int b = 0; b < 8; ++b) u += We[b * 8 + a] * ye[b];
+        for (int b = 0; b < NB; ++b) u += We[b * NB + a] * ye[b];
         s += w[m] * u;
     }
     acc[t] = s;
 }
 
 // phis_new = g + sigma_s acc / (4 pi)
+template <int NB>
 __global__ void k_adj_update(long long N, const double *g, const double *sigma_s, const double *acc, double *out) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const double inv4pi = 1.0 / (4.0 * 3.14159265358979323846);
-    out[i] = g[i] + sigma_s[i >> 3] * acc[i] * inv4pi;
+    out[i] = g[i] + sigma_s[i / NB] * acc[i] * inv4pi;
 }
 
 // per element: dst -= sum_m w_m y^T W psi, dss += sum_m w_m y^T W phi / 4pi, dq += sum_m w_m y^T W 1 / 4pi
+template <int NB>
 __global__ void k_adj_grad(long long E, int nd, const double *W, const double *w, const double *y, const double *psi,
                            const double *phi, double *dst, double *dss, double *dq) {
     long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -285,15 +289,15 @@ __global__ void k_adj_grad(long long E, int nd, const double *W, const double *w
     const double inv4pi = 1.0 / (4.0 * 3.14159265358979323846);
     double gs = dst[e], gss = dss[e], gq = dq[e];
     for (int m = 0; m < nd; ++m) {
-        const double *We = W + ((long long)m * E + e) * 64;
-        const double *ye = y + (long long)m * 8 * E + 8 * e;
-        const double *pe = psi + (long long)m * 8 * E + 8 * e;
-        const double *fe = phi + 8 * e;
+        const double *We = W + ((long long)m * E + e) * NB * NB;
+        const double *ye = y + (long long)m * NB * E + NB * e;
+        const double *pe = psi + (long long)m * NB * E + NB * e;
+        const double *fe = phi + NB * e;
         double tp = 0.0, tf = 0.0, t1 = 0.0;
-        for (int a = 0; a < 8; ++a) {
+        for (int a = 0; a < NB; ++a) {
             double mp = 0.0, mf = 0.0, m1 = 0.0;
-            for (int b = 0; b < 8; ++b) {
-                double wab = We[a * 8 + b];
+            for (int b = 0; b < NB; ++b) {
+                double wab = We[a * NB + b];
                 mp += wab * pe[b];
                 mf += wab * fe[b];
                 m1 += wab;
@@ -677,9 +681,9 @@ void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t,
 void si_adjoint_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t, const double *sigma_s,
                     const double *psi, const double *g, const air_params &prm, const si_params &sp, double *dst,
                     double *dss, double *dq, double *phis_out, cudaStream_t user, si_info *info) {
-    PR_REQUIRE(mesh.kind == PAIR_MESH_HEX, PAIR_ERR_UNSUPPORTED, "si_adjoint: hexahedral meshes only");
-    int n = mesh.n, M = quad.M;
-    long long E = (long long)n * n * n, N = 8 * E;
+    const bool hex = mesh.kind == PAIR_MESH_HEX;
+    int M = quad.M;
+    long long E = hex ? (long long)mesh.n * mesh.n * mesh.n : (long long)mesh.ntet, N = (hex ? 8 : 4) * E;
     PR_CUDA(cudaStreamSynchronize(user));
     size_t per = bytes_per_dir(mesh, prm.precision, false) + (size_t)N * 16;
     size_t freeb = 0, totb = 0;
@@ -763,7 +767,10 @@ void si_adjoint_run(const pair_mesh &mesh, const pair_quad &quad, const double *
             }
             vcycles += bs.iters * Bt.nd;
             max_inner = std::max(max_inner, bs.max_rel);
-            k_wty_acc<<<blocks_for(N, BS), BS, 0, hs>>>(E, Bt.nd, Bt.W, w_d + Bt.m0, Bt.xown, acc);
+            if (hex)
+                k_wty_acc<8><<<blocks_for(N, BS), BS, 0, hs>>>(E, Bt.nd, Bt.W, w_d + Bt.m0, Bt.xown, acc);
+            else
+                k_wty_acc<4><<<blocks_for(N, BS), BS, 0, hs>>>(E, Bt.nd, Bt.W, w_d + Bt.m0, Bt.xown, acc);
             PR_LAUNCH();
             PR_CUDA(cudaEventRecord(e1, hs));
             PR_CUDA(cudaEventSynchronize(e1));
@@ -771,7 +778,10 @@ void si_adjoint_run(const pair_mesh &mesh, const pair_quad &quad, const double *
             PR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
             t_solve += ms;
         }
-        k_adj_update<<<blocks_for(N, BS), BS, 0, s>>>(N, g, sigma_s, acc, pnew);
+        if (hex)
+            k_adj_update<8><<<blocks_for(N, BS), BS, 0, s>>>(N, g, sigma_s, acc, pnew);
+        else
+            k_adj_update<4><<<blocks_for(N, BS), BS, 0, s>>>(N, g, sigma_s, acc, pnew);
         PR_LAUNCH();
         k_diff_partials<<<nbk, BS, 0, s>>>(N, pnew, phis, part);
         PR_LAUNCH();
@@ -792,8 +802,12 @@ void si_adjoint_run(const pair_mesh &mesh, const pair_quad &quad, const double *
     PR_CUDA(cudaStreamSynchronize(s));
     for (int b = 0; b < nb; ++b) {
         HexBatch &Bt = batches[b];
-        k_adj_grad<<<blocks_for(E, 128), 128, 0, s>>>(E, Bt.nd, Bt.W, w_d + Bt.m0, Bt.xown, psi + (size_t)Bt.m0 * N,
-                                                      phi, dst, dss, dq);
+        if (hex)
+            k_adj_grad<8><<<blocks_for(E, 128), 128, 0, s>>>(E, Bt.nd, Bt.W, w_d + Bt.m0, Bt.xown,
+                                                             psi + (size_t)Bt.m0 * N, phi, dst, dss, dq);
+        else
+            k_adj_grad<4><<<blocks_for(E, 128), 128, 0, s>>>(E, Bt.nd, Bt.W, w_d + Bt.m0, Bt.xown,
+                                                             psi + (size_t)Bt.m0 * N, phi, dst, dss, dq);
         PR_LAUNCH();
     }
     if (phis_out) PR_CUDA(cudaMemcpyAsync(phis_out, phis, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));

@@ -402,17 +402,19 @@ def csr_transpose(rowptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor):
     return trp, tc, tv
 
 
-def si_adjoint(n: int, omega, w, sigma_t, sigma_s, q, psi: torch.Tensor, g: torch.Tensor,
+def si_adjoint(n, omega, w, sigma_t, sigma_s, q, psi: torch.Tensor, g: torch.Tensor,
                air: air_params | None = None, si: si_params | None = None, device="cuda"):
     """Gradients of J = g^T phi w.r.t. sigma_t, sigma_s and q per element, by
-    adjoint source iteration on the transposed direction operators.
+    adjoint source iteration on the transposed direction operators, on the n^3
+    hex mesh (n an int) or on a TetMesh.
     psi: converged forward angular fluxes (M, N) on the device.
     Returns (dJ/dsigma_t, dJ/dsigma_s, dJ/dq, adjoint scalar flux, info)."""
     air = air or default_air_params()
     si = si or default_si_params()
     om = np.ascontiguousarray(omega, dtype=np.float64)
     ww = np.ascontiguousarray(w, dtype=np.float64)
-    M, E, N = om.shape[0], n ** 3, 8 * n ** 3
+    M = om.shape[0]
+    mstruct, E, N = _mesh_struct(n)
 
     def dev_t(t):
         return torch.as_tensor(t, dtype=torch.float64).to(device).contiguous()
@@ -425,14 +427,14 @@ def si_adjoint(n: int, omega, w, sigma_t, sigma_s, q, psi: torch.Tensor, g: torc
     phis = torch.empty(N, dtype=torch.float64, device=device)
     info = si_info()
     quad = pair_quad(M, om.ctypes.data, ww.ctypes.data)
-    _check(lib().si_adjoint(C.byref(hex_mesh(n)), C.byref(quad), _dptr(st), _dptr(ss), _dptr(qq), _dptr(psi),
+    _check(lib().si_adjoint(C.byref(mstruct), C.byref(quad), _dptr(st), _dptr(ss), _dptr(qq), _dptr(psi),
                             _dptr(gg), C.byref(air), C.byref(si), _dptr(dst), _dptr(dss), _dptr(dq), _dptr(phis),
                             _stream(), C.byref(info)))
     return dst, dss, dq, phis, {f: getattr(info, f) for f, _ in si_info._fields_ if f != "t_setup_phase_ms"}
 
 
 class SIFunction(torch.autograd.Function):
-    """phi = SI(sigma_t, sigma_s, q) on the n^3 hex mesh with a fixed quadrature;
+    """phi = SI(sigma_t, sigma_s, q) on the n^3 hex mesh (or a TetMesh) with a fixed quadrature;
     backward runs the adjoint source iteration (si_adjoint) with g = dL/dphi."""
 
     @staticmethod

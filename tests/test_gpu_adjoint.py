@@ -86,6 +86,55 @@ def test_autograd_function_backward(pair):
         assert np.abs(_cpu(a) - b).max() <= 1e-9 * np.abs(b).max()
 
 
+def _tet_adjoint_case():
+    prob = I.small_tet(4, order=4, seed=8, ratio=0.7)
+    cen = prob.verts[prob.tets].mean(axis=1)
+    det = (cen[:, 0] < 0.3) & (cen[:, 1] < 0.3) & (cen[:, 2] < 0.5)
+    return prob, O.detector_weights(prob, det)
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-9), (1, 1e-6)])
+def test_tet_adjoint_matches_oracle(pair, precision, tol):
+    """P1 tetrahedra (384 tets, S4, distance-2 lAIR): adjoint flux and the three
+    gradients against the oracle's adjoint; sum_K q_K dJ/dq_K reproduces J."""
+    prob, g = _tet_adjoint_case()
+    prm = O.default_params(distance=2)
+    phi_o, psi_o, _ = O.si_tet(prob, tol=1e-14, max_iters=400, inner_tol=1e-13, params=prm)
+    st_o, ss_o, q_o, phis_o, info_o = O.si_adjoint_tet(prob, psi_o, g, tol=1e-14, max_iters=400, inner_tol=1e-13,
+                                                       params=prm)
+    assert info_o["rc"] == 0
+    mesh = pair.TetMesh(prob.verts, prob.tets, prob.nbr)
+    air = pair.default_air_params(distance=2, precision=precision)
+    si = pair.default_si_params(tol=1e-13, max_iters=400, inner_tol=1e-13 if precision == 0 else 1e-11)
+    phi, psi, _ = pair.si_solve_problem(prob, mesh=mesh, air=air, si=si, want_psi=True)
+    st, ss, q, phis, info = pair.si_adjoint(mesh, prob.omega, prob.w, prob.sigma_t, prob.sigma_s, prob.q, psi,
+                                            torch.as_tensor(g, device="cuda"), air=air, si=si)
+    assert st.shape == (prob.E,) and phis.shape == (prob.N,)
+    for a, b in ((st, st_o), (ss, ss_o), (q, q_o), (phis, phis_o)):
+        a = _cpu(a)
+        assert np.abs(a - b).max() <= tol * np.abs(b).max()
+    J = float(np.dot(g, _cpu(phi)))
+    assert abs(float(np.dot(prob.q, _cpu(q))) - J) <= 10 * tol * abs(J)
+
+
+def test_tet_autograd_function_backward(pair):
+    prob, g = _tet_adjoint_case()
+    dev = "cuda"
+    mesh = pair.TetMesh(prob.verts, prob.tets, prob.nbr)
+    st = torch.as_tensor(prob.sigma_t, device=dev).requires_grad_(True)
+    ss = torch.as_tensor(prob.sigma_s, device=dev).requires_grad_(True)
+    q = torch.as_tensor(prob.q, device=dev).requires_grad_(True)
+    air = pair.default_air_params(distance=2, precision=0)
+    si = pair.default_si_params(tol=1e-13, max_iters=400, inner_tol=1e-13)
+    phi = pair.SIFunction.apply(st, ss, q, mesh, prob.omega, prob.w, air, si)
+    (torch.as_tensor(g, device=dev) * phi).sum().backward()
+    prm = O.default_params(distance=2)
+    _, psi_o = O.si_tet(prob, tol=1e-14, max_iters=400, inner_tol=1e-13, params=prm)[:2]
+    st_o, ss_o, q_o, _, _ = O.si_adjoint_tet(prob, psi_o, g, tol=1e-14, max_iters=400, inner_tol=1e-13, params=prm)
+    for a, b in ((st.grad, st_o), (ss.grad, ss_o), (q.grad, q_o)):
+        assert np.abs(_cpu(a) - b).max() <= 1e-9 * np.abs(b).max()
+
+
 def test_adjoint_gradients_vs_central_differences_hex24(pair):
     """24^3 hex, S4 (24 directions), sigma_t ~ U[0.5,2], sigma_s = 0.7 sigma_t, q = 1 in
     the central 8^3 block, J = integral of phi over the corner 4^3 block: gradients on
