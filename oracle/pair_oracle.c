@@ -481,7 +481,8 @@ int or_csr_transpose(int n, const int *rp, const int *ci, const double *v, int *
  * strongly connected components of the element dependency graph, visited in
  * dependency order (Tarjan: a component is emitted after every component it
  * depends on).  A component of one element is x_K = b_K - sum A_KK' x_K'; a
- * cycle (possible on tetrahedra) is solved as one dense system by LU.
+ * cycle (possible on tetrahedra) is solved as one dense system by LU, its
+ * elements in ascending order.
  * order_out (optional): elements in the visiting order.  Returns the number of
  * components with more than one element in *ncyc (optional). */
 int or_sweep_scc(int nrows, int nb, const int *rowptr, const int *col, const double *val, const double *b,
@@ -547,8 +548,10 @@ int or_sweep_scc(int nrows, int nb, const int *rowptr, const int *col, const dou
                 }
                 continue;
             }
-            /* dense solve of the component */
+            /* dense solve of the component, unknowns in ascending element order */
             ++cyc;
+            for (int i = 1; i < k; ++i)
+                for (int j = i; j > 0 && comp[j - 1] > comp[j]; --j) { int t = comp[j]; comp[j] = comp[j - 1]; comp[j - 1] = t; }
             int m = k * nb;
             double *Ad = calloc((size_t)m * m, sizeof(double)), *y = malloc(sizeof(double) * (size_t)m);
             int *pv = malloc(sizeof(int) * (size_t)m), *pos = malloc(sizeof(int) * (size_t)E);

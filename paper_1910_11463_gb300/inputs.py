@@ -351,3 +351,54 @@ def mms_hex(n: int, order: int = 4, sigma_t: float = 1.0, ratio: float = 0.5):
 def small_hex(n: int, order: int = 2, seed: int = 7, ratio: float = 0.5) -> HexProblem:
     """Small seeded problem for parity tests (spans several tiles, ragged sizes)."""
     return hex_random(n, order, ratio, seed=seed, name=f"hex{n}_s{order}_seed{seed}")
+
+
+def cyclic_block_operator(nb: int, ring: int, up: int = 3, down: int = 4, scale: float = 0.2, seed: int = 21):
+    """A block-scaled operator whose element graph holds one cycle: an upstream
+    chain of `up` elements feeds a ring of `ring` elements (ring element i reads
+    ring element i - 1, the first reads the last and the end of the chain), and a
+    downstream chain of `down` elements hangs off the ring.  Element ids are a
+    seeded permutation, so id order is not upwind order.  Diagonal entries are
+    1.0 (identity diagonal blocks, off-diagonal zeros not stored); every coupling
+    is a dense nb x nb block of scale * U[-1, 1] values.  Returns CSR
+    (rowptr, col, val) with ascending columns in every row, numpy int32/float64."""
+    if ring == 1:
+        raise ValueError("a ring has 0 (no cycle) or at least 2 elements")
+    E = up + ring + down
+    perm = (np.argsort(uniform01(seed, E), kind="stable")).astype(np.int64)
+    chain_u = list(range(up))
+    ring_ids = list(range(up, up + ring))
+    chain_d = list(range(up + ring, E))
+    reads = {k: [] for k in range(E)}
+    for i in range(1, up):
+        reads[chain_u[i]].append(chain_u[i - 1])
+    for i, r in enumerate(ring_ids):
+        reads[r].append(ring_ids[i - 1])
+    if up and ring:
+        reads[ring_ids[0]].append(chain_u[-1])
+    prev = ring_ids[-1] if ring else (chain_u[-1] if up else None)
+    for d in chain_d:
+        if prev is not None:
+            reads[d].append(prev)
+        prev = d
+    u = uniform01(seed + 1, E * 2 * nb * nb) * 2.0 - 1.0
+    rows = [[] for _ in range(E * nb)]
+    t = 0
+    for k in range(E):
+        e = int(perm[k])
+        for a in range(nb):
+            rows[e * nb + a].append((e * nb + a, 1.0))
+        for src in reads[k]:
+            f = int(perm[src])
+            for a in range(nb):
+                for b in range(nb):
+                    rows[e * nb + a].append((f * nb + b, scale * u[t]))
+                    t += 1
+    rowptr = np.zeros(E * nb + 1, np.int32)
+    col, val = [], []
+    for r, ent in enumerate(rows):
+        ent.sort()
+        col += [c for c, _ in ent]
+        val += [v for _, v in ent]
+        rowptr[r + 1] = len(col)
+    return rowptr, np.asarray(col, np.int32), np.asarray(val, np.float64)

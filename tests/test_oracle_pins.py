@@ -580,6 +580,20 @@ def test_tet_sweep_with_cycles_equals_dense_solve():
         assert np.abs(x - ref).max() <= 1e-12 * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("nb,ring", [(4, 0), (4, 2), (4, 3), (4, 8), (8, 2), (8, 4)])
+def test_sweep_cyclic_component_equals_dense_solve(nb, ring):
+    """A seeded operator whose element graph holds one ring of `ring` elements
+    (0: none) between an upstream and a downstream chain: the component sweep
+    counts the ring as one cycle and equals a dense solve of the whole system."""
+    r, c, v = I.cyclic_block_operator(nb, ring)
+    n = len(r) - 1
+    b = I.uniform01(5, n) - 0.5
+    x, ncyc = O.sweep_scc(r, c, v, b, nb=nb)
+    assert ncyc == (1 if ring else 0)
+    ref = np.linalg.solve(csr_dense(r, c, v, n), b)
+    assert np.abs(x - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
 def test_tet_air_distance2_equals_sweep_and_si_fixed_point():
     prob = I.small_tet(4, order=4, seed=2, ratio=0.6)
     rng = np.random.default_rng(5)
