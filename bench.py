@@ -416,9 +416,10 @@ def run_ours(args):
                 "speedup_of_fp32_refined_batched": value / world / (N * M * i64["si_iters"] / (ms64 * 1e-3)),
                 "phi_rel_diff_fp32_refined_vs_fp64": err}
     # comparator: the same source iteration with every direction solved exactly by the
-    # GPU wavefront sweep (the solver AIR replaces; structured hex meshes only)
+    # GPU sweep (the solver AIR replaces): upwind wavefronts on hexes, the level
+    # schedule with cyclic components on tets
     gsweep = None
-    if not hasattr(prob, "tets") and not args.no_variants:
+    if not args.no_variants:
         si_sw = pair.default_si_params(tol=si.tol, max_iters=si.max_iters, fixed_iters=si.fixed_iters, solver=1)
         solve(air, si_sw, zero)
         barrier()
@@ -431,7 +432,9 @@ def run_ours(args):
         gsweep = {"value": N * M * isw["si_iters"] / (mss * 1e-3), "ms_per_step": mss, "si_iters": isw["si_iters"],
                   "setup_ms": isw["t_setup_ms"], "solve_ms": isw["t_solve_ms"],
                   "phi_rel_diff_vs_air": (torch.linalg.norm(phis - phi) / torch.linalg.norm(phis)).item(),
-                  "note": "3n-2 upwind wavefronts per solve, all directions of the batch per launch"}
+                  "note": ("level schedule (one launch per upwind level, cyclic components as dense blocks), "
+                           "all directions of the batch per launch" if hasattr(prob, "tets") else
+                           "3n-2 upwind wavefronts per solve, all directions of the batch per launch")}
     # variant: the outer residual and iterate in double-float pairs on the FP32 pipe
     # instead of FP64 (hex block form; same hierarchy, same stopping test)
     dd = None

@@ -226,9 +226,10 @@ typedef struct {
                           * and return PAIR_OK with the last change in info; 0: missing
                           * tol after max_iters > 1 iterations is PAIR_ERR_NOT_CONVERGED */
     int solver;          /* 0: AIR per direction (the method); 1: exact GPU sweep of the
-                          * block-scaled system in upwind wavefronts (Sec. 1.1, the
-                          * comparison of Sec. 6; structured hexahedral meshes only,
-                          * PAIR_ERR_UNSUPPORTED otherwise); air is then not used */
+                          * block-scaled system (Sec. 1.1, the comparison of Sec. 6):
+                          * upwind wavefronts on hexahedral meshes, a level schedule
+                          * with cyclic components solved as dense blocks on
+                          * tetrahedral meshes (see pair_sweep); air is then not used */
     int inner_cycles;    /* 0: every direction solved to inner_tol from psi = 0 (the
                           * method); l > 0: exactly l V-cycles from psi = 0, a fixed
                           * approximate inverse, so SI converges to the modified problem
@@ -303,6 +304,30 @@ PAIR_API pair_status si_adjoint(const pair_mesh *mesh, const pair_quad *quad, co
 /* Transpose of a device CSR matrix into caller-allocated device arrays
  * (trowptr n+1, tcol and tval nnz), columns ascending in every row. */
 PAIR_API pair_status pair_csr_transpose(const pair_csr *A, int *trowptr, int *tcol, double *tval, void *stream);
+
+/* Exact solve A x = b of one block-scaled upwind operator by a level-scheduled
+ * GPU sweep (Sec. 1.1, the transport sweep that pAIR replaces; Sec. 6).  A is
+ * the operator of one direction after block-inverse scaling (Sec. 1.3), as
+ * dg_assemble_* returns it: rows in element blocks of nb = 4 (P1 tetrahedra)
+ * or 8 (Q1 hexahedra) DOFs, each diagonal block the identity.  Elements are
+ * grouped by upwind level (level = 1 + the largest level upwind) and each
+ * level is one launch: x_K = b_K - sum A_KK' x_K' over the rows' entries
+ * outside the element, in stored order, multiply and subtract unfused.  A
+ * cycle of the element graph (possible on tetrahedra) is a strongly connected
+ * component solved as one dense block by LU with partial pivoting; a component
+ * may have at most 32 unknowns (8 tetrahedra), and an element may reference at
+ * most as many elements as it has faces.
+ *   A          device CSR (n = nb * elements rows, global column indices)
+ *   b, x       device, n doubles each (x is written, b is read)
+ *   n_cycles   host, may be NULL: number of cyclic components solved
+ *   n_levels   host, may be NULL: number of levels of the schedule
+ * The schedule is built, used once and released (device memory at most
+ * 50 bytes per element while it runs); the call synchronises the stream.
+ * PAIR_ERR_ARG: nb not 4 or 8, n not a multiple of nb or a column out of
+ * range; PAIR_ERR_UNSUPPORTED: a larger cycle or more references than faces;
+ * PAIR_ERR_SINGULAR: a singular cyclic component. */
+PAIR_API pair_status pair_sweep(const pair_csr *A, int nb, const double *b, double *x, void *stream, int *n_cycles,
+                                int *n_levels);
 
 PAIR_API const char *pair_last_error(void);
 

@@ -18,7 +18,7 @@ ROOT = os.path.dirname(HERE)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
           "--expt-relaxed-constexpr", f"-I{os.path.join(ROOT, 'include')}"]
-NO_FMA = {"assemble.cu", "setup.cu"}
+NO_FMA = {"assemble.cu", "setup.cu", "sweep_dag.cu"}
 
 
 def nvcc() -> str:

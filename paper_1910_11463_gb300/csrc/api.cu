@@ -424,4 +424,14 @@ pair_status pair_csr_transpose(const pair_csr *A, int *trowptr, int *tcol, doubl
     });
 }
 
+pair_status pair_sweep(const pair_csr *A, int nb, const double *b, double *x, void *stream, int *n_cycles,
+                       int *n_levels) {
+    return guarded([&] {
+        PR_REQUIRE(A && A->rowptr && A->col && A->val && b && x && A->n >= 1 && A->nnz >= 0 && (nb == 4 || nb == 8) &&
+                       A->n % nb == 0,
+                   PAIR_ERR_ARG, "pair_sweep: bad argument");
+        pr::sweep_csr(A->n, nb, A->rowptr, A->col, A->val, b, x, (cudaStream_t)stream, n_cycles, n_levels);
+    });
+}
+
 }  // extern "C"

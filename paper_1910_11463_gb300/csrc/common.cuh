@@ -35,6 +35,7 @@ enum : int {
     DERR_PATTERN_TOO_LARGE = 2,
     DERR_BOUNDS = 4,
     DERR_TIMEOUT = 8,
+    DERR_SWEEP = 16,   // sweep plan limits (faces per element, cyclic components) or a singular component
 };
 
 template <class T>
@@ -147,6 +148,19 @@ struct Level {
     void *vF = nullptr;
 };
 
+// Level schedule of an exact sweep of a block-scaled upwind operator (sweep_dag.cu):
+// single elements grouped by upwind level, and the cyclic components (strongly
+// connected sets of at most SD_MAXE elements, solved as dense blocks) per level.
+constexpr int SD_MAXE = 8;
+struct SweepPlan {
+    int nb = 0, nlev = 0, ncomp = 0;
+    int *list = nullptr;                     // single elements, level by level
+    int *comp = nullptr, *compn = nullptr;   // component members (SD_MAXE per row) and sizes
+    std::vector<long long> off;              // list offsets per level (nlev + 1)
+    std::vector<int> comp_off;               // component-table offsets per level (nlev + 1)
+    void release(cudaStream_t s);
+};
+
 struct Hier {
     int ndir = 0;
     air_params prm{};
@@ -196,6 +210,7 @@ struct Hier {
     const double *graph_b = nullptr;
     double *graph_x = nullptr;
     double graph_tol = -1;
+    SweepPlan *dag = nullptr;   // exact-sweep schedule of an unstructured batch
     ~Hier();
 };
 
@@ -223,6 +238,17 @@ void autotune_cycle(Hier &h);   // lanes per row of every SELL kernel (timed onc
 // sweep.cu: x = A^{-1} b for every matrix of a structured-hex batch by upwind
 // wavefronts (needs bsr64); graph-captured when use_graph
 void sweep_solve(Hier &h, const double *b, double *x, bool use_graph);
+
+// sweep_dag.cu: the level schedule of nd matrices of N rows each (nb DOFs per
+// element, identity diagonal blocks) stacked block-diagonally in one CSR
+// (global column indices), on stream s; the launches of one exact solve
+SweepPlan *sweep_plan_build(int nd, long long N, int nb, const int *rowptr, const int *col, int *d_err,
+                            cudaStream_t s);
+void sweep_plan_launch(const SweepPlan &P, const int *rowptr, const int *col, const double *val, const double *b,
+                       double *x, int *d_err, cudaStream_t s);
+// plan, solve and release for one CSR matrix (synchronises s)
+void sweep_csr(int n, int nb, const int *rowptr, const int *col, const double *val, const double *b, double *x,
+               cudaStream_t s, int *ncomp, int *nlev);
 
 // assemble.cu
 void hex_assemble(int n, int ndir, const double *omega_d, const double *sigma_t, int *rowptr, int *col,

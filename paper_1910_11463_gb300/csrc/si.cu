@@ -335,6 +335,10 @@ void csr_transpose_dev(int n, long long nnz, const int *rowptr, const int *col, 
 
 Hier::~Hier() {
     if (graph) cudaGraphExecDestroy(graph);
+    if (dag) {
+        if (stream) dag->release(stream);
+        delete dag;
+    }
     for (auto &e : ev)
         if (e) cudaEventDestroy(e);
     for (auto &e : evl)
@@ -461,7 +465,8 @@ void build_batch(HexBatch &B, const pair_mesh &mesh, const double *omega_h, cons
         dfree(L.rowptr, s); dfree(L.col, s); dfree(L.val, s);
         L.rowptr = trp; L.col = tcol; L.val = tval;
     }
-    if (sweep_only) {   // the exact sweep needs the block form only
+    if (sweep_only) {   // the exact sweep needs the block form (hex) or its level schedule
+        if (!hex) h->dag = sweep_plan_build(nd, N, nb, L.rowptr, L.col, h->d_err, s);
         PR_CUDA(cudaStreamSynchronize(s));
         return;
     }
@@ -485,7 +490,6 @@ void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t,
     PR_CUDA(cudaStreamSynchronize(user));
     bool gin = sp.g_inflow != 0.0;
     const bool sweep = sp.solver == 1;
-    PR_REQUIRE(!sweep || hex, PAIR_ERR_UNSUPPORTED, "si_solve: the GPU sweep solver needs a structured hex mesh");
     // direction batches admitted by memory
     size_t per = bytes_per_dir(mesh, prm.precision, gin);
     size_t freeb = 0, totb = 0;

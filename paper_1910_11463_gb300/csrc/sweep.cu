@@ -69,12 +69,23 @@ void launch_waves(Hier &h, const double *b, double *x) {
     }
 }
 
+void launch_sweep(Hier &h, const double *b, double *x) {
+    if (h.bsr0 && h.bsr64) {
+        launch_waves(h, b, x);
+    } else {
+        const Level &L = h.lev[0];
+        sweep_plan_launch(*h.dag, L.rowptr, L.col, L.val, b, x, h.d_err, h.stream);
+    }
+}
+
 }  // namespace
 
+// Structured hex batches (block form present) take the wavefront sweep, every
+// other batch the level schedule built with it (sweep_dag.cu).
 void sweep_solve(Hier &h, const double *b, double *x, bool use_graph) {
-    PR_REQUIRE(h.bsr0 && h.bsr64, PAIR_ERR_UNSUPPORTED, "GPU sweep: structured hexahedral block form only");
+    PR_REQUIRE((h.bsr0 && h.bsr64) || h.dag, PAIR_ERR_UNSUPPORTED, "GPU sweep: no block form or level schedule");
     if (!use_graph) {
-        launch_waves(h, b, x);
+        launch_sweep(h, b, x);
         return;
     }
     if (!h.graph || h.graph_b != b || h.graph_x != x) {
@@ -83,7 +94,7 @@ void sweep_solve(Hier &h, const double *b, double *x, bool use_graph) {
         const long long before = g_launches;
         PR_CUDA(cudaStreamBeginCapture(h.stream, cudaStreamCaptureModeThreadLocal));
         try {
-            launch_waves(h, b, x);
+            launch_sweep(h, b, x);
         } catch (...) {
             cudaGraph_t dummy;
             cudaStreamEndCapture(h.stream, &dummy);

@@ -124,6 +124,7 @@ def lib():
             "pair_kernel_launches": (C.c_longlong, []),
             "pair_residual_norm_noalloc": (i, [C.POINTER(pair_csr), vp, vp, vp, vp, vp]),
             "pair_csr_transpose": (i, [C.POINTER(pair_csr), vp, vp, vp, vp]),
+            "pair_sweep": (i, [C.POINTER(pair_csr), i, vp, vp, vp, C.POINTER(i), C.POINTER(i)]),
             "si_adjoint": (i, [C.POINTER(pair_mesh), C.POINTER(pair_quad), vp, vp, vp, vp, vp, C.POINTER(air_params),
                                C.POINTER(si_params), vp, vp, vp, vp, vp, C.POINTER(si_info)]),
             "air_setup": (i, [C.POINTER(pair_csr), i, C.POINTER(air_params), vp, C.POINTER(vp)]),
@@ -400,6 +401,18 @@ def csr_transpose(rowptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor):
     desc = pair_csr(n, col.numel(), rowptr.data_ptr(), col.data_ptr(), val.data_ptr())
     _check(lib().pair_csr_transpose(C.byref(desc), _dptr(trp), _dptr(tc), _dptr(tv), _stream()))
     return trp, tc, tv
+
+
+def sweep(rowptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor, b: torch.Tensor, nb: int):
+    """Exact solve of one block-scaled upwind operator (device CSR, nb DOFs per
+    element) by the level-scheduled GPU sweep.  Returns (x, cyclic components, levels)."""
+    n = rowptr.numel() - 1
+    b = b.to(torch.float64).contiguous()
+    x = torch.empty_like(b)
+    nc, nl = C.c_int(), C.c_int()
+    desc = pair_csr(n, col.numel(), rowptr.data_ptr(), col.data_ptr(), val.data_ptr())
+    _check(lib().pair_sweep(C.byref(desc), nb, _dptr(b), _dptr(x), _stream(), C.byref(nc), C.byref(nl)))
+    return x, nc.value, nl.value
 
 
 def si_adjoint(n, omega, w, sigma_t, sigma_s, q, psi: torch.Tensor, g: torch.Tensor,

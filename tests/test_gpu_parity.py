@@ -247,11 +247,21 @@ def test_si_mms_angular_source_matches_oracle(pair):
     assert np.linalg.norm(_cpu(phs) - ref) <= 1e-12 * np.linalg.norm(ref)
 
 
-def test_gpu_sweep_rejects_tets(pair):
-    prob = I.small_tet(3, order=2, seed=1)
-    with pytest.raises(pair.PairError) as e:
-        pair.si_solve_problem(prob, si=pair.default_si_params(solver=1))
-    assert e.value.status == -9
+def test_level_scheduled_sweep_hex_bit_exact(pair):
+    """The level-scheduled sweep (pair_sweep) on hex operators of ragged size equals
+    the oracle's component sweep bit for bit (no cycles, 3n - 2 levels) and the
+    structured wavefront sweep to rounding."""
+    n = 7
+    prob = I.small_hex(n, order=4, seed=12, ratio=0.8)
+    st = torch.as_tensor(prob.sigma_t, device="cuda")
+    for m in (0, 5, 23):
+        r, c, v = O.hex_assemble(n, prob.omega[m], prob.sigma_t)
+        b = I.uniform01(40 + m, prob.N) - 0.25
+        xo, ncyc = O.sweep_scc(r, c, v, b, nb=8)
+        gr, gc, gv = pair.dg_assemble_hex(n, prob.omega[m], st)
+        x, nc, nl = pair.sweep(gr, gc, gv, torch.as_tensor(b, device="cuda"), 8)
+        assert nc == ncyc == 0 and nl == 3 * n - 2
+        assert np.array_equal(_cpu(x).view(np.uint64), xo.view(np.uint64))
 
 
 @pytest.mark.parametrize("precision", [0, 1])

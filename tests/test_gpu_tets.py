@@ -79,3 +79,71 @@ def test_tet40_full_size_directions_bit_exact(pair):
         gr, gc, gv = pair.dg_assemble_tet(mesh, prob.omega[m], st)
         assert np.array_equal(_cpu(gr), r) and np.array_equal(_cpu(gc), c)
         assert np.array_equal(_cpu(gv).view(np.uint64), v.view(np.uint64))
+
+
+def test_tet40_sweep_bit_exact_with_cycles(pair):
+    """Full-size checkerboard tet mesh: the level-scheduled GPU sweep of three S8
+    directions (two of them with cyclic components, faces nearly parallel to Omega)
+    equals the oracle's component sweep bit for bit, cycle counts included."""
+    prob = I.config("tet40_s8")
+    mesh = pair.TetMesh(prob.verts, prob.tets, prob.nbr)
+    st = torch.as_tensor(prob.sigma_t, device="cuda")
+    cycles = 0
+    for m in (0, 5, 75):
+        r, c, v = O.tet_assemble(prob, prob.omega[m])
+        b = I.uniform01(60 + m, prob.N)
+        xo, ncyc = O.sweep_scc(r, c, v, b, nb=4)
+        gr, gc, gv = pair.dg_assemble_tet(mesh, prob.omega[m], st)
+        x, nc, nl = pair.sweep(gr, gc, gv, torch.as_tensor(b, device="cuda"), 4)
+        assert nc == ncyc and nl > 0
+        assert np.array_equal(_cpu(x).view(np.uint64), xo.view(np.uint64))
+        cycles += nc
+    assert cycles > 0
+
+
+@pytest.mark.parametrize("nb,ring", [(4, 0), (4, 2), (4, 3), (4, 8), (8, 2), (8, 4)])
+def test_sweep_cyclic_components_bit_exact(pair, nb, ring):
+    """Seeded operators with one ring of `ring` elements between two chains: the GPU
+    finds the ring as one component and matches the oracle bit for bit."""
+    r, c, v = I.cyclic_block_operator(nb, ring)
+    n = len(r) - 1
+    b = I.uniform01(5, n) - 0.5
+    xo, ncyc = O.sweep_scc(r, c, v, b, nb=nb)
+    dev = lambda a: torch.as_tensor(a, device="cuda")
+    x, nc, nl = pair.sweep(dev(r), dev(c), dev(v), dev(b), nb)
+    assert nc == ncyc
+    assert np.array_equal(_cpu(x).view(np.uint64), xo.view(np.uint64))
+
+
+@pytest.mark.parametrize("nb,ring", [(4, 9), (8, 5)])
+def test_sweep_rejects_oversized_cycles(pair, nb, ring):
+    """A cycle of more than 8 elements or 32 unknowns is reported, not solved."""
+    r, c, v = I.cyclic_block_operator(nb, ring)
+    dev = lambda a: torch.as_tensor(a, device="cuda")
+    with pytest.raises(pair.PairError) as e:
+        pair.sweep(dev(r), dev(c), dev(v), dev(np.ones(len(r) - 1)), nb)
+    assert e.value.status == -9
+
+
+def test_sweep_single_element(pair):
+    """One element, no coupling: the identity system."""
+    r, c, v = np.arange(5, dtype=np.int32), np.arange(4, dtype=np.int32), np.ones(4)
+    dev = lambda a: torch.as_tensor(a, device="cuda")
+    b = np.array([1.5, -2.0, 0.25, 3.0])
+    x, nc, nl = pair.sweep(dev(r), dev(c), dev(v), dev(b), 4)
+    assert np.array_equal(_cpu(x), b) and nc == 0 and nl == 1
+
+
+def test_si_gpu_sweep_tets_matches_oracle_sweep(pair):
+    """SI with every direction solved by the level-scheduled GPU sweep equals the
+    oracle's SI with its component sweep, and the AIR-solved SI."""
+    prob = I.small_tet(6, order=4, seed=5, ratio=0.8)
+    ref, _, info_o = O.si_tet(prob, tol=1e-12, use_sweep=True)
+    assert info_o["rc"] == 0
+    mesh = pair.TetMesh(prob.verts, prob.tets, prob.nbr)
+    phi, _, info = pair.si_solve_problem(prob, mesh=mesh, si=pair.default_si_params(tol=1e-12, solver=1))
+    assert info["vcycles"] == 0 and info["si_iters"] == info_o["si_iters"]
+    assert np.linalg.norm(_cpu(phi) - ref) <= 1e-13 * np.linalg.norm(ref)
+    phi_air, _, _ = pair.si_solve_problem(prob, mesh=mesh, air=pair.default_air_params(distance=2, precision=0),
+                                          si=pair.default_si_params(tol=1e-12, inner_tol=1e-13))
+    assert np.linalg.norm(_cpu(phi_air) - ref) <= 1e-10 * np.linalg.norm(ref)
