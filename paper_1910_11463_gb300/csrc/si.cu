@@ -377,6 +377,18 @@ size_t bytes_per_dir(const pair_mesh &mesh, int precision, bool gin) {
     return lvl0 + coarse + vec;
 }
 
+// the exact sweep keeps the level-0 CSR (at most 13 entries per row on either
+// mesh), the hex block form or the tet level schedule (< 64 B per element while
+// it is built), W, the inflow columns and b, x
+size_t sweep_bytes_per_dir(const pair_mesh &mesh, bool gin) {
+    bool hex = mesh.kind == PAIR_MESH_HEX;
+    size_t nb = hex ? 8 : 4;
+    size_t E = hex ? (size_t)mesh.n * mesh.n * mesh.n : (size_t)mesh.ntet, N = nb * E;
+    double om[3] = {1, 1, 1};
+    size_t nnz0 = hex ? (size_t)hex_nnz(mesh.n, om) : N * 13;
+    return nnz0 * 12 + N * 4 + (hex ? N * 96 : E * 64) + E * nb * nb * 8 + (gin ? N * 8 : 0) + N * 16;
+}
+
 struct HexBatch {
     int m0 = 0, nd = 0;
     Hier *h = nullptr;
@@ -491,13 +503,15 @@ void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t,
     bool gin = sp.g_inflow != 0.0;
     const bool sweep = sp.solver == 1;
     // direction batches admitted by memory
-    size_t per = bytes_per_dir(mesh, prm.precision, gin);
+    size_t per = sweep ? sweep_bytes_per_dir(mesh, gin) : bytes_per_dir(mesh, prm.precision, gin);
     size_t freeb = 0, totb = 0;
     PR_CUDA(cudaMemGetInfo(&freeb, &totb));
     double budget = sp.mem_budget_gb > 0 ? sp.mem_budget_gb * 1e9 : 0.6 * (double)freeb;
     int B = sp.batch > 0 ? std::min(sp.batch, M) : M;
     B = std::min<long long>(B, std::max<long long>(1, (long long)(budget / (double)per)));
-    B = (int)std::min<long long>(B, std::max<long long>(1, (0x7fffffffLL / 64) / N));
+    // 32-bit entry indices: a hierarchy's levels hold up to ~64 entries per level-0
+    // row in total, the sweep's level-0 CSR at most 13
+    B = (int)std::min<long long>(B, std::max<long long>(1, (0x7fffffffLL / (sweep ? 16 : 64)) / N));
     PR_REQUIRE(B >= 1, PAIR_ERR_OOM, "memory budget below one direction hierarchy");
     int nb = (M + B - 1) / B;
     bool resident = (double)per * M <= budget;
