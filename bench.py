@@ -358,7 +358,9 @@ def run_ours(args):
         with open(tfile) as f:
             tj = json.load(f)
         entry = tj.get(dom)
-        if entry and entry.get("source_sha") == pair.kernel_source_sha(entry.get("source", "cycle.cu")):
+        # counters apply to the workload they were captured on, with the same kernel source
+        if (entry and entry.get("workload") == args.config
+                and entry.get("source_sha") == pair.kernel_source_sha(entry.get("source", "cycle.cu"))):
             traffic = entry["bytes_per_launch"] * (rl[dom]["gb_per_launch"] / entry["gb_per_launch_at_capture"])
     achieved = rl[dom]["achieved_gbs"]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

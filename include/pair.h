@@ -288,7 +288,9 @@ PAIR_API pair_status si_solve(const pair_mesh *mesh, const pair_quad *quad, cons
  *   dJ/dsigma_t,K = -sum_m w_m y_{m,K}^T W_{m,K} psi_{m,K}
  *   dJ/dsigma_s,K =  sum_m w_m y_{m,K}^T W_{m,K} phi_K / (4 pi)
  *   dJ/dq_K       =  sum_m w_m y_{m,K}^T W_{m,K} 1 / (4 pi)
- * Each A_m^T gets its own AIR hierarchy (all directions batched).
+ * Each A_m^T gets its own AIR hierarchy (all directions batched); with
+ * sp->solver = 1 each A_m^T y_m = phis is instead solved exactly by the GPU
+ * sweep (the level schedule of pair_sweep on the transposed operator).
  *   psi            device N*M, the converged forward angular fluxes (si_solve's psi)
  *   g              device N, dJ/dphi (e.g. detector weights)
  *   dJ_dsigma_t, dJ_dsigma_s, dJ_dq   device per-element outputs (n^3 or ntet)

@@ -477,8 +477,8 @@ void build_batch(HexBatch &B, const pair_mesh &mesh, const double *omega_h, cons
         dfree(L.rowptr, s); dfree(L.col, s); dfree(L.val, s);
         L.rowptr = trp; L.col = tcol; L.val = tval;
     }
-    if (sweep_only) {   // the exact sweep needs the block form (hex) or its level schedule
-        if (!hex) h->dag = sweep_plan_build(nd, N, nb, L.rowptr, L.col, h->d_err, s);
+    if (sweep_only) {   // the exact sweep needs the hex block form or else a level schedule
+        if (!(h->bsr0 && h->bsr64)) h->dag = sweep_plan_build(nd, N, nb, L.rowptr, L.col, h->d_err, s);
         PR_CUDA(cudaStreamSynchronize(s));
         return;
     }
@@ -702,8 +702,9 @@ void si_adjoint_run(const pair_mesh &mesh, const pair_quad &quad, const double *
     const bool hex = mesh.kind == PAIR_MESH_HEX;
     int M = quad.M;
     long long E = hex ? (long long)mesh.n * mesh.n * mesh.n : (long long)mesh.ntet, N = (hex ? 8 : 4) * E;
+    const bool sweep = sp.solver == 1;   // exact sweeps of the transposed operators instead of AIR
     PR_CUDA(cudaStreamSynchronize(user));
-    size_t per = bytes_per_dir(mesh, prm.precision, false) + (size_t)N * 16;
+    size_t per = (sweep ? sweep_bytes_per_dir(mesh, false) : bytes_per_dir(mesh, prm.precision, false)) + (size_t)N * 16;
     size_t freeb = 0, totb = 0;
     PR_CUDA(cudaMemGetInfo(&freeb, &totb));
     double budget = sp.mem_budget_gb > 0 ? sp.mem_budget_gb * 1e9 : 0.6 * (double)freeb;
@@ -754,7 +755,7 @@ void si_adjoint_run(const pair_mesh &mesh, const pair_quad &quad, const double *
         Bt.nd = std::min(B, M - b * B);
         PR_CUDA(cudaEventRecord(e0, s));
         PR_CUDA(cudaStreamSynchronize(s));
-        build_batch(Bt, mesh, quad.omega, omega_d, sigma_t, prm, false, true);
+        build_batch(Bt, mesh, quad.omega, omega_d, sigma_t, prm, false, true, sweep);
         cudaStream_t hs = Bt.h->stream;
         Bt.b = dmalloc<double>((size_t)Bt.nd * N, hs);
         Bt.xown = dmalloc<double>((size_t)Bt.nd * N, hs);
@@ -775,8 +776,13 @@ void si_adjoint_run(const pair_mesh &mesh, const pair_quad &quad, const double *
             PR_CUDA(cudaEventRecord(e0, hs));
             k_broadcast<<<blocks_for((long long)Bt.nd * N, BS), BS, 0, hs>>>(N, Bt.nd, phis, Bt.b);
             PR_LAUNCH();
-            PR_CUDA(cudaMemsetAsync(Bt.xown, 0, sizeof(double) * Bt.nd * N, hs));
-            BatchSolve bs = solve_batch(h, Bt.b, Bt.xown, sp.inner_tol, sp.inner_maxit, sp.use_graphs != 0);
+            BatchSolve bs;
+            if (sweep) {
+                sweep_solve(h, Bt.b, Bt.xown, sp.use_graphs != 0);
+            } else {
+                PR_CUDA(cudaMemsetAsync(Bt.xown, 0, sizeof(double) * Bt.nd * N, hs));
+                bs = solve_batch(h, Bt.b, Bt.xown, sp.inner_tol, sp.inner_maxit, sp.use_graphs != 0);
+            }
             if (!bs.converged && it > 0) {   // the first right-hand side is zero
                 char buf2[160];
                 snprintf(buf2, sizeof buf2, "adjoint AIR solve reached %d cycles with relative residual %.3e",

@@ -135,6 +135,31 @@ def test_tet_autograd_function_backward(pair):
         assert np.abs(_cpu(a) - b).max() <= 1e-9 * np.abs(b).max()
 
 
+@pytest.mark.parametrize("kind", ["hex", "tet"])
+def test_adjoint_with_exact_sweeps_matches_oracle_sweep(pair, kind):
+    """solver = 1: every transposed system solved by the GPU level-scheduled sweep,
+    against the oracle's adjoint with its exact component sweep."""
+    if kind == "hex":
+        prob, g = _adjoint_case()
+        phi_o, psi_o, _ = O.si_hex(prob, tol=1e-14, max_iters=400, use_sweep=True)
+        ref = O.si_adjoint_hex(prob, psi_o, g, tol=1e-14, max_iters=400, use_sweep=True)
+        mesh = prob.n
+    else:
+        prob, g = _tet_adjoint_case()
+        phi_o, psi_o, _ = O.si_tet(prob, tol=1e-14, max_iters=400, use_sweep=True)
+        ref = O.si_adjoint_tet(prob, psi_o, g, tol=1e-14, max_iters=400, use_sweep=True)
+        mesh = pair.TetMesh(prob.verts, prob.tets, prob.nbr)
+    assert ref[4]["rc"] == 0
+    si = pair.default_si_params(tol=1e-14, max_iters=400, solver=1)
+    phi, psi, _ = pair.si_solve_problem(prob, mesh=None if kind == "hex" else mesh, si=si, want_psi=True)
+    st, ss, q, phis, info = pair.si_adjoint(mesh, prob.omega, prob.w, prob.sigma_t, prob.sigma_s, prob.q, psi,
+                                            torch.as_tensor(g, device="cuda"), si=si)
+    assert info["vcycles"] == 0
+    for a, b in zip((st, ss, q, phis), ref[:4]):
+        a = _cpu(a)
+        assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
+
+
 def test_adjoint_gradients_vs_central_differences_hex24(pair):
     """24^3 hex, S4 (24 directions), sigma_t ~ U[0.5,2], sigma_s = 0.7 sigma_t, q = 1 in
     the central 8^3 block, J = integral of phi over the corner 4^3 block: gradients on
