@@ -879,14 +879,31 @@ __global__ void k_level_counts(int n, const int *rowptr, const int8_t *cf, unsig
     if (threadIdx.x < 4) atomicAdd(&out[threadIdx.x], sh[threadIdx.x]);
 }
 // level 0 in CSR form, per matrix: [F rows, C rows, entries of F rows, entries of C rows]
+// (a warp whose rows all belong to one matrix sums its counts first: one atomic
+// per counter and warp instead of one per row)
 __global__ void k_level_counts_dir(int n, const int *rowptr, const int8_t *cf, const int *rowdir,
                                    unsigned long long *out) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n || cf[i] == CF_COARSEST) return;
-    bool isC = cf[i] == CF_C;
-    unsigned long long *o = out + 4LL * rowdir[i];
-    atomicAdd(&o[isC ? 1 : 0], 1ULL);
-    atomicAdd(&o[isC ? 3 : 2], (unsigned long long)(rowptr[i + 1] - rowptr[i]));
+    const unsigned FULL = 0xffffffffu;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = i < n && cf[i] != CF_COARSEST;
+    const int d = i < n ? rowdir[i] : -1;
+    unsigned long long c[4] = {0, 0, 0, 0};
+    if (valid) {
+        const bool isC = cf[i] == CF_C;
+        c[isC ? 1 : 0] = 1;
+        c[isC ? 3 : 2] = (unsigned long long)(rowptr[i + 1] - rowptr[i]);
+    }
+    const int d0 = __shfl_sync(FULL, d, 0);
+    if (__all_sync(FULL, d == d0 || d < 0)) {
+        for (int k = 0; k < 4; ++k)
+            for (int o = 16; o > 0; o >>= 1) c[k] += __shfl_xor_sync(FULL, c[k], o);
+        if ((threadIdx.x & 31) == 0 && d0 >= 0)
+            for (int k = 0; k < 4; ++k)
+                if (c[k]) atomicAdd(&out[4LL * d0 + k], c[k]);
+    } else if (valid) {
+        for (int k = 0; k < 4; ++k)
+            if (c[k]) atomicAdd(&out[4LL * d + k], c[k]);
+    }
 }
 }  // namespace
 

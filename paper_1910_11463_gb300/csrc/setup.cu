@@ -245,9 +245,13 @@ __global__ void k_lair_pattern(int nc, const int *cpts, const int *rowptr, const
 }
 
 // size class of each lAIR system: 0: n <= 8, 1: <= 12, 2: <= 16, 3: <= 32, 4: <= 64, 5: larger
-constexpr int LAIR_CLASSES = 6;
+// lAIR systems binned by size: thread per system up to 16 unknowns, then a warp per
+// system with a shared-memory workspace sized to the bin (smaller bins keep more
+// systems in flight per SM), global workspaces beyond 64
+constexpr int LAIR_CLASSES = 8;
+constexpr int LAIR_BIG = LAIR_CLASSES - 1;
 __device__ __forceinline__ int lair_class(int np) {
-    return np <= 8 ? 0 : np <= 12 ? 1 : np <= 16 ? 2 : np <= 32 ? 3 : np <= 64 ? 4 : 5;
+    return np <= 8 ? 0 : np <= 12 ? 1 : np <= 16 ? 2 : np <= 24 ? 3 : np <= 32 ? 4 : np <= 48 ? 5 : np <= 64 ? 6 : 7;
 }
 
 
@@ -533,10 +537,20 @@ __global__ void k_lair_solve(int nwork, const int *worklist, const int *cpts, co
             }
             __syncwarp();
             if (act) {
-                int wd = np - k - 1;
-                for (int idx = g; idx < wd * wd; idx += G) {
-                    int r = k + 1 + idx / wd, c = k + 1 + idx % wd;
-                    M[r * np + c] = fma(-M[r * np + k], M[k * np + c], M[r * np + c]);
+                // lane g updates entries g, g + G, ... of the wd x wd trailing block in
+                // row-major order; (row, column) advance by (G / wd, G % wd) per step
+                // with one carry, so no division per entry
+                const int wd = np - k - 1;
+                if (wd > 0) {
+                    const int dr = G / wd, dc = G - dr * wd;
+                    int r = g / wd, c = g - r * wd;
+                    for (int idx = g; idx < wd * wd; idx += G) {
+                        const int R = k + 1 + r, Cc = k + 1 + c;
+                        M[R * np + Cc] = fma(-M[R * np + k], M[k * np + Cc], M[R * np + Cc]);
+                        r += dr;
+                        c += dc;
+                        if (c >= wd) { c -= wd; ++r; }
+                    }
                 }
             }
             __syncwarp();
@@ -1273,8 +1287,8 @@ void build_hierarchy(Hier &h) {
             thread_bin(0, k_lair_solve_thread<8>, 8);
             thread_bin(1, k_lair_solve_thread<12>, 12);
             thread_bin(2, k_lair_solve_thread<16>, 16);
-            const int cls_n[LAIR_CLASSES] = {8, 12, 16, 32, 64, 0};
-            for (int c = 3; c < 5; ++c) {
+            const int cls_n[LAIR_CLASSES] = {8, 12, 16, 24, 32, 48, 64, 0};
+            for (int c = 3; c < LAIR_BIG; ++c) {
                 if (!hc[c]) continue;
                 int nm = cls_n[c];
                 size_t per = ((size_t)nm * nm + 3 * nm) * sizeof(double);   // per warp
@@ -1288,10 +1302,10 @@ void build_hierarchy(Hier &h) {
                                                             prm.phi_R, nm, nullptr, nullptr);
                 PR_LAUNCH();
             }
-            int nbig = hc[5];
+            int nbig = hc[LAIR_BIG];
             if (nbig > 0) {
                 long long *goff = dmalloc<long long>(nbig + 1, s);
-                k_big_rows<<<blocks_for(nbig, BS), BS, 0, s>>>(nbig, list + hstart[5], npat, goff);
+                k_big_rows<<<blocks_for(nbig, BS), BS, 0, s>>>(nbig, list + hstart[LAIR_BIG], npat, goff);
                 PR_LAUNCH();
                 k_prefix_ll<<<1, 1, 0, s>>>(nbig, goff);
                 PR_LAUNCH();
@@ -1299,7 +1313,7 @@ void build_hierarchy(Hier &h) {
                 d2h(&gtot, goff + nbig, 1, s);
                 double *gbuf = dmalloc<double>(gtot, s);
                 k_lair_solve<32><<<std::min<unsigned>(nbig, 152u * 16u), 32, 0, s>>>(
-                    nbig, list + hstart[5], L.cpts, L.rowptr, L.col, L.val, candptr, cand, npat, zr, zc, zv, keep,
+                    nbig, list + hstart[LAIR_BIG], L.cpts, L.rowptr, L.col, L.val, candptr, cand, npat, zr, zc, zv, keep,
                     dsing, L.rowdir, prm.phi_R, 0, goff, gbuf);
                 PR_LAUNCH();
                 dfree(gbuf, s); dfree(goff, s);
