@@ -1273,7 +1273,8 @@ void build_hierarchy(Hier &h) {
             int *list = dmalloc<int>(nc, s);
             partition_by_class(ccls, nc, LAIR_CLASSES, list, hstart, hc, s);
             dfree(ccls, s);
-            // n <= 16: a thread per system; larger: a warp per system
+            // n <= 8: a thread per system; 9..24 unknowns: 32 / G systems per warp (G = 8
+            // lanes each up to 16 unknowns, 16 lanes up to 24); larger: a warp per system
             auto thread_bin = [&](int c, auto kern, int nm) {
                 if (!hc[c]) return;
                 size_t sm = (size_t)64 * (nm * nm + 3 * nm) * sizeof(double);
@@ -1284,24 +1285,26 @@ void build_hierarchy(Hier &h) {
                                                            prm.phi_R);
                 PR_LAUNCH();
             };
-            thread_bin(0, k_lair_solve_thread<8>, 8);
-            thread_bin(1, k_lair_solve_thread<12>, 12);
-            thread_bin(2, k_lair_solve_thread<16>, 16);
             const int cls_n[LAIR_CLASSES] = {8, 12, 16, 24, 32, 48, 64, 0};
-            for (int c = 3; c < LAIR_BIG; ++c) {
-                if (!hc[c]) continue;
-                int nm = cls_n[c];
-                size_t per = ((size_t)nm * nm + 3 * nm) * sizeof(double);   // per warp
+            auto warp_bin = [&](int c, auto kern, int G) {
+                if (!hc[c]) return;
+                const int nm = cls_n[c], spw = 32 / G;
+                size_t per = ((size_t)nm * nm + 3 * nm) * sizeof(double) * spw;   // per warp
                 int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (200 * 1024) / per));
                 size_t sm = per * wpb;
-                unsigned grid = std::min<unsigned>(blocks_for(hc[c], wpb), 152u * 64u);
+                unsigned grid = std::min<unsigned>(blocks_for(hc[c], wpb * spw), 152u * 64u);
                 if (sm > 48 * 1024)
-                    PR_CUDA(cudaFuncSetAttribute(k_lair_solve<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-                k_lair_solve<32><<<grid, 32 * wpb, sm, s>>>(hc[c], list + hstart[c], L.cpts, L.rowptr, L.col, L.val,
-                                                            candptr, cand, npat, zr, zc, zv, keep, dsing, L.rowdir,
-                                                            prm.phi_R, nm, nullptr, nullptr);
+                    PR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+                kern<<<grid, 32 * wpb, sm, s>>>(hc[c], list + hstart[c], L.cpts, L.rowptr, L.col, L.val, candptr,
+                                                cand, npat, zr, zc, zv, keep, dsing, L.rowdir, prm.phi_R, nm, nullptr,
+                                                nullptr);
                 PR_LAUNCH();
-            }
+            };
+            thread_bin(0, k_lair_solve_thread<8>, 8);
+            warp_bin(1, k_lair_solve<8>, 8);
+            warp_bin(2, k_lair_solve<8>, 8);
+            warp_bin(3, k_lair_solve<16>, 16);
+            for (int c = 4; c < LAIR_BIG; ++c) warp_bin(c, k_lair_solve<32>, 32);
             int nbig = hc[LAIR_BIG];
             if (nbig > 0) {
                 long long *goff = dmalloc<long long>(nbig + 1, s);
