@@ -14,15 +14,18 @@
  *
  * Contents (each function cites the passage it follows):
  *   - dense LU with partial pivoting (element blocks, lAIR local systems)
- *   - upwind DG assembly of one direction on the hex Q1 mesh (Eq. weak_form_transport),
- *     block-inverse scaling (Sec. 1.3), right-hand sides (Eq. sn_transport)
- *   - exact sweep: block forward substitution in topological order (Sec. 1.1)
+ *   - upwind DG assembly of one direction on the hex Q1 mesh and on a P1
+ *     tetrahedral mesh (Eq. weak_form_transport), block-inverse scaling (Sec. 1.3),
+ *     right-hand sides (Eq. sn_transport)
+ *   - exact sweep: block forward substitution in topological order (Sec. 1.1);
+ *     cycles of the element graph (possible on tetrahedra) as strongly connected
+ *     components, each solved as one dense block, unknowns in ascending element order
  *   - AIR setup (Sec. 1.2, Sec. 4.1.1 Eq. soc, Sec. 4.1.2 filtering): strength,
  *     PMIS CF splitting with seeded hashed keys, one-point P, distance-1/2 lAIR
  *     or degree-1 nAIR R = [Z, I], Galerkin R A P
  *   - V-cycle with FC-Jacobi post-relaxation, AIR solve loop
  *   - source iteration with quadrature sum (Eq. angular_quad, Eq. sn_transport)
- *   - adjoint source iteration and cross-section gradients
+ *   - adjoint source iteration and cross-section gradients (hex and tetrahedra)
  *
  * Readings where the paper is silent (it defers AIR internals to its refs):
  *   strength uses |a_ij| >= theta * max_{k != i} |a_ik| (empty if the max is 0);
