@@ -322,6 +322,71 @@ def test_rap_equals_dense_product():
                                                  np.ones(levs[l + 1].nnz), nc) > 0)
 
 
+def test_phi_R_filter_drops_small_z_after_the_solve():
+    """Sec. 4.1.2 R filtering: with phi_R = 0.1 every Z row of the finest level is the
+    unfiltered row (same values, bit for bit) restricted to |z_j| >= phi_R max_k |z_k|;
+    the filter acts after the local solve, it does not re-solve on the smaller pattern."""
+    p = I.config("hex8_s2")
+    for m in (0, 5):
+        r, c, v = O.hex_assemble(p.n, p.omega[m], p.sigma_t)
+        L0 = O.Hierarchy(r, c, v, O.default_params()).level(0)
+        L1 = O.Hierarchy(r, c, v, O.default_params(phi_R=0.1)).level(0)
+        assert np.array_equal(L0.cf, L1.cf) and np.array_equal(L0.pmap, L1.pmap)
+        dropped = 0
+        for ic in range(len(L0.cpts)):
+            z0 = L0.zval[L0.zrowptr[ic]:L0.zrowptr[ic + 1]]
+            c0 = L0.zcol[L0.zrowptr[ic]:L0.zrowptr[ic + 1]]
+            keep = np.abs(z0) >= 0.1 * np.abs(z0).max() if len(z0) else np.zeros(0, bool)
+            dropped += int((~keep).sum())
+            assert np.array_equal(L1.zcol[L1.zrowptr[ic]:L1.zrowptr[ic + 1]], c0[keep])
+            assert np.array_equal(L1.zval[L1.zrowptr[ic]:L1.zrowptr[ic + 1]].view(np.uint64),
+                                  z0[keep].view(np.uint64))
+        assert dropped > 0
+
+
+def test_phi_A_filter_is_the_filtered_galerkin_product():
+    """Coarse-operator filtering: with phi_A = 0.05 each coarse operator equals R A P of
+    its own finer level with the off-diagonal entries below phi_A times the row's largest
+    off-diagonal magnitude dropped and the diagonal kept (margins of 1e-12 absorb the
+    different summation order of the dense reference)."""
+    p = I.config("hex8_s2")
+    r, c, v = O.hex_assemble(p.n, p.omega[3], p.sigma_t)
+    H = O.Hierarchy(r, c, v, O.default_params(phi_A=0.05))
+    levs = H.levels()
+    total_dropped = 0
+    for l, L in enumerate(levs[:-1]):
+        A = sp.csr_matrix((L.val, L.col, L.rowptr), shape=(L.n, L.n))
+        nc = len(L.cpts)
+        rows = np.concatenate([np.arange(nc), np.repeat(np.arange(nc), np.diff(L.zrowptr))])
+        cols = np.concatenate([L.cpts, L.zcol])
+        R = sp.csr_matrix((np.concatenate([np.ones(nc), L.zval]), (rows, cols)), shape=(nc, L.n))
+        f = np.nonzero(L.pmap >= 0)[0]
+        P = sp.csr_matrix((np.ones(len(f)), (f, L.pmap[f])), shape=(L.n, nc))
+        ref = (R @ A @ P).toarray()
+        ones = lambda M: sp.csr_matrix((np.ones(M.nnz), M.indices, M.indptr), shape=M.shape)
+        sym = (ones(R) @ ones(A) @ ones(P)).toarray() > 0
+        Cn = levs[l + 1]
+        Ac = csr_dense(Cn.rowptr, Cn.col, Cn.val, nc)
+        stored = csr_dense(Cn.rowptr, Cn.col, np.ones(Cn.nnz), nc) > 0
+        for i in range(nc):
+            off = [j for j in np.nonzero(sym[i])[0] if j != i]
+            mx = max((abs(ref[i, j]) for j in off), default=0.0)
+            thr = 0.05 * mx
+            assert stored[i, i] == sym[i, i]
+            for j in np.nonzero(sym[i])[0]:
+                if j == i:
+                    continue
+                if stored[i, j]:
+                    assert abs(ref[i, j]) >= thr * (1 - 1e-12)
+                    assert abs(Ac[i, j] - ref[i, j]) <= 1e-13 * max(mx, abs(ref[i, i]))
+                else:
+                    assert abs(ref[i, j]) < thr * (1 + 1e-12) + 1e-300
+                    total_dropped += 1
+            assert not np.any(stored[i] & ~sym[i])
+            assert abs(Ac[i, i] - ref[i, i]) <= 1e-13 * max(mx, abs(ref[i, i]))
+    assert total_dropped > 0
+
+
 def _chain(n, seed=0):
     rng = np.random.default_rng(seed)
     sub = -(0.3 + 0.6 * rng.random(n - 1))
