@@ -389,13 +389,15 @@ size_t sweep_bytes_per_dir(const pair_mesh &mesh, bool gin) {
     return nnz0 * 12 + N * 4 + (hex ? N * 96 : E * 64) + E * nb * nb * 8 + (gin ? N * 8 : 0) + N * 16;
 }
 
-struct HexBatch {
+// a batch of directions m0 .. m0 + nd - 1 (either mesh): its hierarchy or sweep
+// schedule, the W and inflow columns of its right-hand sides, and b and x
+struct DirBatch {
     int m0 = 0, nd = 0;
     Hier *h = nullptr;
     double *W = nullptr, *Gin = nullptr, *b = nullptr, *xown = nullptr;
 };
 
-void free_batch_ops(HexBatch &B) {
+void free_batch_ops(DirBatch &B) {
     if (!B.h) return;
     cudaStream_t s = B.h->stream;
     dfree(B.W, s); dfree(B.Gin, s);
@@ -404,7 +406,7 @@ void free_batch_ops(HexBatch &B) {
     B.h = nullptr;
 }
 
-void build_batch(HexBatch &B, const pair_mesh &mesh, const double *omega_h, const double *omega_d,
+void build_batch(DirBatch &B, const pair_mesh &mesh, const double *omega_h, const double *omega_d,
                  const double *sigma_t, const air_params &prm, bool gin, bool adjoint = false,
                  bool sweep_only = false) {
     const int n = mesh.n;
@@ -520,7 +522,7 @@ void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t,
     PR_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
     struct Cleanup {
         cudaStream_t s;
-        std::vector<HexBatch> *bs;
+        std::vector<DirBatch> *bs;
         std::vector<void *> bufs;
         ~Cleanup() {
             for (auto &b : *bs) {
@@ -532,7 +534,7 @@ void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t,
             cudaStreamDestroy(s);
         }
     };
-    std::vector<HexBatch> batches(nb);
+    std::vector<DirBatch> batches(nb);
     Cleanup cl{s, &batches, {}};
     double *omega_d = dmalloc<double>(3 * M, s);
     cl.bufs.push_back(omega_d);
@@ -579,7 +581,7 @@ void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t,
         PR_CUDA(cudaMemsetAsync(phinew, 0, sizeof(double) * N, s));
         PR_CUDA(cudaStreamSynchronize(s));
         for (int bi = 0; bi < nb; ++bi) {
-            HexBatch &Bt = batches[bi];
+            DirBatch &Bt = batches[bi];
             if (!Bt.h) {
                 // setup phase on the batch stream (timed)
                 cudaStream_t tmp;
@@ -716,10 +718,10 @@ void si_adjoint_run(const pair_mesh &mesh, const pair_quad &quad, const double *
     PR_REQUIRE(resident, PAIR_ERR_OOM, "si_adjoint: all direction hierarchies must fit the memory budget");
     cudaStream_t s;
     PR_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
-    std::vector<HexBatch> batches(nb);
+    std::vector<DirBatch> batches(nb);
     struct Cleanup {
         cudaStream_t s;
-        std::vector<HexBatch> *bs;
+        std::vector<DirBatch> *bs;
         std::vector<void *> bufs;
         ~Cleanup() {
             for (auto &b : *bs) {
@@ -750,7 +752,7 @@ void si_adjoint_run(const pair_mesh &mesh, const pair_quad &quad, const double *
     int vcycles = 0, it = 0;
     bool converged = false;
     for (int b = 0; b < nb; ++b) {
-        HexBatch &Bt = batches[b];
+        DirBatch &Bt = batches[b];
         Bt.m0 = b * B;
         Bt.nd = std::min(B, M - b * B);
         PR_CUDA(cudaEventRecord(e0, s));
@@ -770,7 +772,7 @@ void si_adjoint_run(const pair_mesh &mesh, const pair_quad &quad, const double *
         PR_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * N, s));
         PR_CUDA(cudaStreamSynchronize(s));
         for (int b = 0; b < nb; ++b) {
-            HexBatch &Bt = batches[b];
+            DirBatch &Bt = batches[b];
             Hier &h = *Bt.h;
             cudaStream_t hs = h.stream;
             PR_CUDA(cudaEventRecord(e0, hs));
@@ -825,7 +827,7 @@ void si_adjoint_run(const pair_mesh &mesh, const pair_quad &quad, const double *
     PR_CUDA(cudaMemsetAsync(dq, 0, sizeof(double) * E, s));
     PR_CUDA(cudaStreamSynchronize(s));
     for (int b = 0; b < nb; ++b) {
-        HexBatch &Bt = batches[b];
+        DirBatch &Bt = batches[b];
         if (hex)
             k_adj_grad<8><<<blocks_for(E, 128), 128, 0, s>>>(E, Bt.nd, Bt.W, w_d + Bt.m0, Bt.xown,
                                                              psi + (size_t)Bt.m0 * N, phi, dst, dss, dq);
