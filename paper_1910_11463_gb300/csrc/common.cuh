@@ -235,8 +235,9 @@ void level0_bytes(Hier &h);   // fills bytes_res0 / bytes_relax0 (hex block form
 void prof_enable(Hier &h);
 void autotune_cycle(Hier &h);   // lanes per row of every SELL kernel (timed once per shape)
 
-// sweep.cu: x = A^{-1} b for every matrix of a structured-hex batch by upwind
-// wavefronts (needs bsr64); graph-captured when use_graph
+// sweep.cu: x = A^{-1} b for every matrix of a batch: upwind wavefronts on a
+// structured-hex batch with its block form (bsr64), otherwise the batch's level
+// schedule (h.dag, sweep_dag.cu); graph-captured when use_graph
 void sweep_solve(Hier &h, const double *b, double *x, bool use_graph);
 
 // sweep_dag.cu: the level schedule of nd matrices of N rows each (nb DOFs per

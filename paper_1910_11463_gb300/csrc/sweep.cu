@@ -11,6 +11,8 @@
 // wavefront covers every direction of the batch (8 threads per element, one per
 // node); the launches are captured once into a CUDA graph per batch and use
 // programmatic dependent launch, so a wavefront starts as the previous one drains.
+// Batches without the structured block form (tetrahedra, transposed operators)
+// take the level schedule of sweep_dag.cu through the same entry point.
 #include "common.cuh"
 
 namespace pr {
