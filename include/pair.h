@@ -37,7 +37,7 @@ typedef enum {
     PAIR_OK = 0,
     PAIR_ERR_ARG = -1,            /* invalid argument (null pointer, size, parameter range) */
     PAIR_ERR_OOM = -2,            /* device allocation failed */
-    PAIR_ERR_SINGULAR = -3,       /* singular element block (zero pivot) */
+    PAIR_ERR_SINGULAR = -3,       /* singular element block or sweep cycle block (zero pivot) */
     PAIR_ERR_NOT_CONVERGED = -4,  /* iteration limit reached before the tolerance */
     PAIR_ERR_COARSEN_STALL = -5,  /* reserved */
     PAIR_ERR_NAN = -6,            /* NaN/Inf found in an input or a residual */
