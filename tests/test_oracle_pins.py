@@ -166,6 +166,94 @@ def test_lair_defining_identity(distance):
                 assert np.abs(res).max() <= 1e-12 * max(1.0, np.abs(sub).max())
 
 
+# ---------------------------------------------------------------------------
+# lAIR pattern (Sec. 1.2 local ideal restriction; Sec. 4.1.1 strength of the R
+# pattern): rebuilt here from the definitions, independently of the oracle's
+# selection loop, and compared row by row with the oracle's Z columns.
+# ---------------------------------------------------------------------------
+
+def _lair_pattern(L, SR, distance):
+    """Pattern of each C row built from its definition: distance 1 = the
+    eps_R-strong F neighbours of the C point; distance 2 adds the eps_R-strong F
+    neighbours of those F points (the path runs through F points only).  Sorted
+    ascending, as the columns of a CSR row are."""
+    F = L.cf == 0
+    pats = []
+    for i in L.cpts:
+        d1 = {j for j in SR[i] if F[j]}
+        pat = set(d1)
+        if distance >= 2:
+            for j in d1:
+                pat |= {k for k in SR[j] if F[k]}
+        pats.append(sorted(pat))
+    return pats
+
+
+def _pattern_variants(L, SR, Stheta, distance):
+    """Patterns a plausible misreading would give: theta-strength in place of
+    eps_R, a second hop that passes through C points, a second hop without the
+    eps_R test.  The pin only bites where these differ from the definition."""
+    F = L.cf == 0
+    allnb = [set(L.col[L.rowptr[i]:L.rowptr[i + 1]].tolist()) - {i} for i in range(L.n)]
+    out = {"theta": [], "via_C": [], "hop2_unfiltered": []}
+    for i in L.cpts:
+        d1_theta = {j for j in Stheta[i] if F[j]}
+        d1 = {j for j in SR[i] if F[j]}
+        p_theta, p_viaC, p_unf = set(d1_theta), set(d1), set(d1)
+        if distance >= 2:
+            for j in d1_theta:
+                p_theta |= {k for k in Stheta[j] if F[k]}
+            for j in SR[i]:                      # intermediate point may be C
+                p_viaC |= {k for k in SR[j] if F[k]}
+            for j in d1:
+                p_unf |= {k for k in allnb[j] if F[k]}
+        out["theta"].append(sorted(p_theta))
+        out["via_C"].append(sorted(p_viaC))
+        out["hop2_unfiltered"].append(sorted(p_unf))
+    return out
+
+
+def _pattern_cases():
+    p = I.config("hex8_s2")
+    t = I.small_tet(4, order=4, seed=7)
+    cases = []
+    for m in (0, 5):
+        cases.append(("hex8_s2", m, O.hex_assemble(p.n, p.omega[m], p.sigma_t)))
+    for m in (3, 17):
+        cases.append(("tet4_s4", m, O.tet_assemble(t, t.omega[m])))
+    return cases
+
+
+@pytest.mark.parametrize("distance", [1, 2])
+def test_lair_pattern_matches_definition(distance):
+    """Every C row's Z columns on every level equal the pattern built from the
+    definition (phi_R = 0, so no entry is filtered), on hexes and jittered tets.
+    theta = 0.5 and eps_R = 0.01 make the CF strength set differ from the R
+    strength set, and the test asserts that each misreading of the pattern rule
+    changes at least one row somewhere, so each of them fails this pin."""
+    theta, eps_R = 0.5, 0.01
+    differs = {"theta": 0, "via_C": 0, "hop2_unfiltered": 0}
+    rows = 0
+    for name, m, (r, c, v) in _pattern_cases():
+        H = O.Hierarchy(r, c, v, O.default_params(distance=distance, theta=theta, eps_R=eps_R))
+        for L in H.levels()[:-1]:
+            assert L.n_singular == 0
+            SR = _strength_sets(L, eps_R)
+            St = _strength_sets(L, theta)
+            want = _lair_pattern(L, SR, distance)
+            for ic in range(len(L.cpts)):
+                got = L.zcol[L.zrowptr[ic]:L.zrowptr[ic + 1]].tolist()
+                assert got == want[ic], (name, m, ic)
+            rows += len(L.cpts)
+            alt = _pattern_variants(L, SR, St, distance)
+            for k, pats in alt.items():
+                differs[k] += sum(a != b for a, b in zip(pats, want))
+    assert rows > 500
+    assert differs["theta"] > 0
+    if distance == 2:
+        assert differs["via_C"] > 0 and differs["hop2_unfiltered"] > 0
+
+
 def _strong_part(L, eps_R=0.01):
     """A restricted to its diagonal and its eps_R-strong entries (sparse)."""
     S = _strength_sets(L, eps_R)
