@@ -36,12 +36,15 @@ extern "C" {
 typedef enum {
     PAIR_OK = 0,
     PAIR_ERR_ARG = -1,            /* invalid argument (null pointer, size, parameter range) */
-    PAIR_ERR_OOM = -2,            /* device allocation failed */
+    PAIR_ERR_OOM = -2,            /* device allocation failed, or the memory budget
+                                   * holds less than one direction's hierarchy */
     PAIR_ERR_SINGULAR = -3,       /* singular element block or sweep cycle block (zero pivot) */
     PAIR_ERR_NOT_CONVERGED = -4,  /* iteration limit reached before the tolerance */
-    PAIR_ERR_COARSEN_STALL = -5,  /* reserved */
+                                  /* -5 and -7 are not used: coarsening that stalls
+                                   * (n_c = 0 or n_c >= 0.9 n) ends the hierarchy
+                                   * there, which is not an error, and no kernel of
+                                   * this library waits on the device */
     PAIR_ERR_NAN = -6,            /* NaN/Inf found in an input or a residual */
-    PAIR_ERR_DEVICE_TIMEOUT = -7, /* a bounded device-side wait expired */
     PAIR_ERR_CUDA = -8,           /* a CUDA runtime call failed */
     PAIR_ERR_UNSUPPORTED = -9,    /* size outside what this build handles (message says which) */
     PAIR_ERR_DEVICE = -10         /* a kernel reported an internal bound violation */
@@ -124,8 +127,10 @@ typedef struct {
  * interpolation to the strongest C neighbour, lAIR restriction R = [Z, I]
  * from FP64 LU solves on distance-1/2 strong F neighbourhoods (pattern from
  * eps_R), optional phi_R filter, Galerkin A_c = R A P, optional phi_A filter.
- * All setup arithmetic is FP64 with no fused multiply-add, in the order
- * documented with the kernels, so results are reproducible bit for bit.
+ * All setup arithmetic is FP64 in the order documented with the kernels: the
+ * compiler contracts nothing (no implicit fused multiply-add), and the LU
+ * updates, the Neumann series and the Galerkin sums use an explicit fma()
+ * exactly where that order writes one, so results are reproducible bit for bit.
  *   A      host array of 'count' descriptors of device CSR matrices (copied)
  *   out    receives the new handle
  * Errors: PAIR_ERR_ARG (count < 1, null pointers, n < 1, distance not 1/2),
@@ -198,8 +203,10 @@ PAIR_API pair_status dg_hex_nnz(const pair_mesh *mesh, const double *omega, int 
  * scaling of Sec. 1.3) into caller-allocated device CSR arrays (rowptr N+1,
  * col/val dg_hex_nnz entries).  Diagonal block = identity (stored as its
  * diagonal); off-diagonal face blocks D_K^{-1} L_KK' (8 x 4).  FP64, element
- * blocks factored by LU with partial pivoting, no fused multiply-add.
- *   sigma_t  device, n^3 values. */
+ * blocks factored by LU with partial pivoting; no compiler contraction, with an
+ * explicit fma() in each LU update and substitution step.
+ *   sigma_t  device, n^3 values.
+ * PAIR_ERR_SINGULAR: an element block with a zero pivot. */
 PAIR_API pair_status dg_assemble_hex(const pair_mesh *mesh, const double *omega, const double *sigma_t,
                             int *rowptr, int *col, double *val, void *stream);
 
@@ -275,7 +282,15 @@ typedef struct {
  *   phi      device, N DOFs (8 n^3 or 4 ntet): in = initial guess, out = result
  *   psi      device N*M (direction-major) or NULL
  *   air      AIR parameters (precision selects FP64 or FP32-refined)
- *   info     host, may be NULL. */
+ *   info     host, may be NULL.
+ * Errors: PAIR_ERR_NAN if sigma_t, sigma_s, q, the initial phi or q_ang holds a
+ * NaN or Inf (checked before any other work), or a residual or the scalar flux
+ * turns non-finite; PAIR_ERR_SINGULAR for a zero-volume tetrahedron or a
+ * singular element block (checked right after assembly, before the setup);
+ * PAIR_ERR_OOM when sp->mem_budget_gb (or, at 0, the free device memory) is below
+ * the estimated footprint of one direction; PAIR_ERR_NOT_CONVERGED as described
+ * for fixed_iters.  After any error the library holds no state of the call, and
+ * later calls work normally. */
 PAIR_API pair_status si_solve(const pair_mesh *mesh, const pair_quad *quad, const double *sigma_t, const double *sigma_s,
                      const double *q, const air_params *air, const si_params *sp, double *phi, double *psi,
                      void *stream, si_info *info);
@@ -349,7 +364,9 @@ PAIR_API const char *pair_last_error(void);
  * library holds until the process exits.  Matrices with more than
  * PAIR_NOALLOC_MAX_ROWS rows are rejected with PAIR_ERR_UNSUPPORTED.
  * The first call on a device looks up the array's device address; make that
- * first call before any stream capture.  All calls share the one array, so
+ * first call before any stream capture.  The address is kept with the id of
+ * the CUDA context it was found in, so after a device reset the next call
+ * looks it up again (make that call before any capture as well).  All calls share the one array, so
  * calls whose work overlaps on the GPU (different streams, no ordering) race
  * and must not be issued; each call writes every scratch entry it reads, so
  * nothing needs clearing between calls.  Ordered on 'stream'.

@@ -34,7 +34,6 @@ enum : int {
     DERR_HASH_OVERFLOW = 1,
     DERR_PATTERN_TOO_LARGE = 2,
     DERR_BOUNDS = 4,
-    DERR_TIMEOUT = 8,
     DERR_SWEEP = 16,   // sweep plan limits (faces per element, cyclic components) or a singular component
 };
 

@@ -12,9 +12,14 @@
 // The array's name is a host-side stand-in in host code, so the host obtains
 // its device address with cudaGetSymbolAddress once per device (the first
 // call on a device does this; make that first call before any stream capture)
-// and passes the address to the kernels.  Every call shares the array: calls
+// and passes the address to the kernels.  The address is cached with the id of
+// the CUDA context it belongs to: after a device reset (a new primary context,
+// the module loaded again) the next call looks the address up afresh instead
+// of using the old one.  Every call shares the array: calls
 // whose kernels overlap on the GPU race on it.  Each call writes every partial
 // it later reads, so nothing has to be cleared between calls.
+#include <cuda.h>   // CUcontext / CUresult types only; the functions come from the runtime
+
 #include <mutex>
 
 #include "common.cuh"
@@ -64,16 +69,42 @@ __global__ void k_na_norm(int nb, const double *partials, double *out) {
 
 std::mutex g_na_mutex;
 double *g_na_addr[256] = {nullptr};
+unsigned long long g_na_ctx[256] = {0};
+
+// id of the calling thread's current CUDA context (0 if none yet); the driver
+// functions are obtained through the runtime, so libpair does not link libcuda
+unsigned long long current_context_id() {
+    typedef CUresult (*get_current_fn)(CUcontext *);
+    typedef CUresult (*get_id_fn)(CUcontext, unsigned long long *);
+    static get_current_fn get_current = nullptr;
+    static get_id_fn get_id = nullptr;
+    if (!get_current || !get_id) {
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        PR_CUDA(cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1));
+        PR_CUDA(cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2));
+        PR_REQUIRE(f1 && f2 && q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess,
+                   PAIR_ERR_CUDA, "driver context queries unavailable");
+        get_current = reinterpret_cast<get_current_fn>(f1);
+        get_id = reinterpret_cast<get_id_fn>(f2);
+    }
+    CUcontext c = nullptr;
+    if (get_current(&c) != CUDA_SUCCESS || !c) return 0;
+    unsigned long long id = 0;
+    return get_id(c, &id) == CUDA_SUCCESS ? id : 0;
+}
 
 double *scratch_address() {
     int dev = 0;
     PR_CUDA(cudaGetDevice(&dev));
     PR_REQUIRE(dev >= 0 && dev < 256, PAIR_ERR_UNSUPPORTED, "device ordinal out of range");
     std::lock_guard<std::mutex> lock(g_na_mutex);
-    if (!g_na_addr[dev]) {
-        void *p = nullptr;
+    unsigned long long ctx = current_context_id();
+    if (!g_na_addr[dev] || ctx == 0 || ctx != g_na_ctx[dev]) {
+        void *p = nullptr;   // this call also makes the device's primary context current
         PR_CUDA(cudaGetSymbolAddress(&p, g_noalloc_partials));
         g_na_addr[dev] = static_cast<double *>(p);
+        g_na_ctx[dev] = current_context_id();
     }
     return g_na_addr[dev];
 }

@@ -10,6 +10,8 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <initializer_list>
+#include <utility>
 
 #include "common.cuh"
 
@@ -88,6 +90,14 @@ __global__ void k_diff_final(int nb, const double *part, double *out) {
 __global__ void k_fill_dir(int *rowdir, long long N, int ndir) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < N * ndir) rowdir[i] = (int)(i / N);
+}
+
+// flag |= 1 if any of a[0..n) is NaN or Inf (grid-stride)
+__global__ void k_nonfinite(long long n, const double *a, int *flag) {
+    int bad = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        bad |= !isfinite(a[i]);
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
 }
 
 }  // namespace
@@ -356,6 +366,35 @@ Hier::~Hier() {
 // ---- source iteration ---------------------------------------------------------
 namespace {
 
+// PAIR_ERR_OOM when the budget (explicit, or the free device memory) cannot hold
+// one direction's estimated footprint
+void require_budget(size_t per, double avail, bool explicit_budget) {
+    if ((double)per <= avail) return;
+    char buf[200];
+    snprintf(buf, sizeof buf, "%s of %.3f GB is below one direction's estimated footprint of %.3f GB",
+             explicit_budget ? "memory budget" : "free device memory", avail * 1e-9, (double)per * 1e-9);
+    fail(PAIR_ERR_OOM, buf);
+}
+
+// PAIR_ERR_NAN unless every listed device array is finite (checked before any
+// kernel consumes the inputs, so NaN never reaches assembly or setup)
+void require_finite(std::initializer_list<std::pair<const double *, long long>> arrays, const char *what,
+                    cudaStream_t s) {
+    int *flag = dmalloc<int>(1, s);
+    PR_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), s));
+    for (auto &a : arrays) {
+        if (!a.first || a.second <= 0) continue;
+        unsigned g = std::min<unsigned>(blocks_for(a.second, BS), 152u * 8u);
+        k_nonfinite<<<g, BS, 0, s>>>(a.second, a.first, flag);
+        PR_LAUNCH();
+    }
+    int h = 0;
+    PR_CUDA(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    dfree(flag, s);
+    PR_CUDA(cudaStreamSynchronize(s));
+    if (h) fail(PAIR_ERR_NAN, std::string("NaN/Inf in ") + what);
+}
+
 __global__ void k_iota_dirs(int nd, long long N, int *row0, int *n0) {
     int d = blockIdx.x * blockDim.x + threadIdx.x;
     if (d < nd) { row0[d] = (int)(d * N); n0[d] = (int)N; }
@@ -471,6 +510,14 @@ void build_batch(DirBatch &B, const pair_mesh &mesh, const double *omega_h, cons
     else
         tet_assemble(mesh.ntet, nd, omega_d + 3 * B.m0, mesh.verts, mesh.tets, mesh.nbr, sigma_t, L.rowptr, L.col,
                      L.val, B.W, B.Gin, h->d_err, s, false);
+    {   // an element that failed left its rows unwritten: stop before anything reads them
+        int aerr = 0;
+        PR_CUDA(cudaMemcpyAsync(&aerr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+        PR_CUDA(cudaStreamSynchronize(s));
+        PR_REQUIRE(aerr == 0, PAIR_ERR_SINGULAR,
+                   hex ? "assembly: singular element block"
+                       : "assembly: zero-volume tetrahedron, singular element block or face-neighbour mismatch");
+    }
     if (adjoint) {
         // A_m^T: rows of the transpose of the (block-diagonal) batch operator
         int *trp = dmalloc<int>(L.n + 1, s), *tcol = dmalloc<int>(nnz, s);
@@ -509,12 +556,12 @@ void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t,
     size_t freeb = 0, totb = 0;
     PR_CUDA(cudaMemGetInfo(&freeb, &totb));
     double budget = sp.mem_budget_gb > 0 ? sp.mem_budget_gb * 1e9 : 0.6 * (double)freeb;
+    require_budget(per, sp.mem_budget_gb > 0 ? budget : (double)freeb, sp.mem_budget_gb > 0);
     int B = sp.batch > 0 ? std::min(sp.batch, M) : M;
     B = std::min<long long>(B, std::max<long long>(1, (long long)(budget / (double)per)));
     // 32-bit entry indices: a hierarchy's levels hold up to ~64 entries per level-0
     // row in total, the sweep's level-0 CSR at most 13
     B = (int)std::min<long long>(B, std::max<long long>(1, (0x7fffffffLL / (sweep ? 16 : 64)) / N));
-    PR_REQUIRE(B >= 1, PAIR_ERR_OOM, "memory budget below one direction hierarchy");
     int nb = (M + B - 1) / B;
     bool resident = (double)per * M <= budget;
     // per-call device state on a private stream
@@ -536,6 +583,8 @@ void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t,
     };
     std::vector<DirBatch> batches(nb);
     Cleanup cl{s, &batches, {}};
+    require_finite({{sigma_t, E}, {sigma_s, E}, {q, E}, {phi, N}, {sp.q_ang, sp.q_ang ? N * M : 0}},
+                   "sigma_t, sigma_s, q, the initial phi or q_ang", s);
     double *omega_d = dmalloc<double>(3 * M, s);
     cl.bufs.push_back(omega_d);
     PR_CUDA(cudaMemcpyAsync(omega_d, quad.omega, sizeof(double) * 3 * M, cudaMemcpyHostToDevice, s));
@@ -733,6 +782,7 @@ void si_adjoint_run(const pair_mesh &mesh, const pair_quad &quad, const double *
             cudaStreamDestroy(s);
         }
     } cl{s, &batches, {}};
+    require_finite({{sigma_t, E}, {sigma_s, E}, {psi, N * M}, {g, N}}, "sigma_t, sigma_s, psi or g", s);
     auto buf = [&](size_t cnt) { double *p = dmalloc<double>(cnt, s); cl.bufs.push_back(p); return p; };
     double *omega_d = buf(3 * M), *w_d = buf(M), *phi = buf(N), *phis = buf(N), *pnew = buf(N), *acc = buf(N);
     int nbk = (int)blocks_for(N, BS);

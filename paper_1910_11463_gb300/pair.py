@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libpair.so")
 
 PAIR_OK = 0
 STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_OOM", -3: "ERR_SINGULAR", -4: "ERR_NOT_CONVERGED",
-          -5: "ERR_COARSEN_STALL", -6: "ERR_NAN", -7: "ERR_DEVICE_TIMEOUT", -8: "ERR_CUDA",
+          -6: "ERR_NAN", -8: "ERR_CUDA",
           -9: "ERR_UNSUPPORTED", -10: "ERR_DEVICE"}
 
 

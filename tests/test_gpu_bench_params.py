@@ -1,0 +1,156 @@
+"""GPU parity at the AIR parameters the benchmark runs (Sec. 4.1.1 strength of the
+R pattern, Sec. 4.1.2 filtering): theta = 0.5 for the CF splitting, eps_R = 0.01
+for the R pattern, the coarse-operator filter phi_A = 0.05, distance 1 on hexes and
+distance 2 on tets; and nAIR of degree 1 with the R filter phi_R = 0.1 under the
+same phi_A.  Every level of every hierarchy is bit-identical to the oracle's (CF
+splitting, P, R pattern and values, filtered coarse structure and values), on a
+small ragged batch and on full-size directions of the 32^3 hex and 40^3 tet
+workloads; source iteration at those parameters matches the oracle within the
+FP64 (1e-10) and FP32-refined (1e-7, residual <= tol) tolerances."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O
+from paper_1910_11463_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+BENCH = dict(theta=0.5, eps_R=0.01, phi_A=0.05)
+
+
+@pytest.fixture(scope="module")
+def pair():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    from paper_1910_11463_gb300 import pair as P
+    return P
+
+
+def _cpu(t):
+    return t.cpu().numpy()
+
+
+def _compare(Ho, Hg, mat):
+    """Bit-for-bit comparison of one matrix's hierarchy; returns the coarse nnz."""
+    assert Hg.nlevels(mat) == Ho.nlev, mat
+    coarse_nnz = 0
+    for l in range(Ho.nlev):
+        a, b = Hg.level(mat, l), Ho.level(l)
+        assert a.n == b.n and a.coarsest == b.coarsest, (mat, l)
+        assert np.array_equal(a.rowptr, b.rowptr) and np.array_equal(a.col, b.col), (mat, l)
+        assert np.array_equal(a.val.view(np.uint64), b.val.view(np.uint64)), (mat, l)
+        if l > 0:
+            coarse_nnz += b.nnz
+        if b.coarsest:
+            continue
+        assert np.array_equal(a.cf, b.cf) and np.array_equal(a.pmap, b.pmap), (mat, l)
+        assert np.array_equal(a.cpts, b.cpts), (mat, l)
+        assert np.array_equal(a.zrowptr, b.zrowptr) and np.array_equal(a.zcol, b.zcol), (mat, l)
+        assert np.array_equal(a.zval.view(np.uint64), b.zval.view(np.uint64)), (mat, l)
+        assert a.n_singular == b.n_singular, (mat, l)
+    return coarse_nnz
+
+
+def _unfiltered_coarse_nnz(mat, kw):
+    """Coarse-level nnz of the oracle hierarchy without the phi_A filter."""
+    k = dict(kw)
+    k["phi_A"] = 0.0
+    H = O.Hierarchy(*mat, O.default_params(**k))
+    return sum(H.level(l).nnz for l in range(1, H.nlev))
+
+
+@pytest.mark.parametrize("nair,phi_R", [(0, 0.0), (1, 0.1)])
+def test_bench_params_hex_batch_bit_exact(pair, nair, phi_R):
+    """Ragged 9^3 S4 batch (24 directions): every level equals the oracle's; the
+    phi_A filter removes coarse entries (it is active, not a no-op)."""
+    prob = I.small_hex(9, order=4, seed=5, ratio=0.8)
+    kw = dict(BENCH, distance=1, nair=nair, phi_R=phi_R)
+    st = torch.as_tensor(prob.sigma_t, device="cuda")
+    mats_o = [O.hex_assemble(prob.n, prob.omega[m], prob.sigma_t) for m in range(prob.M)]
+    Hg = pair.Hierarchy([pair.dg_assemble_hex(prob.n, prob.omega[m], st) for m in range(prob.M)],
+                        pair.default_air_params(precision=0, **kw))
+    for m in range(prob.M):
+        nnz = _compare(O.Hierarchy(*mats_o[m], O.default_params(**kw)), Hg, m)
+        if m in (0, 11):
+            assert nnz < _unfiltered_coarse_nnz(mats_o[m], kw), m
+
+
+@pytest.mark.parametrize("nair,phi_R", [(0, 0.0), (1, 0.1)])
+def test_bench_params_tet_batch_bit_exact(pair, nair, phi_R):
+    """Jittered 5^3 x 6 tets, distance 2 (nAIR: its distance-2 pattern), S4."""
+    prob = I.small_tet(5, order=4, seed=7)
+    kw = dict(BENCH, distance=2, nair=nair, phi_R=phi_R)
+    mesh = pair.TetMesh(prob.verts, prob.tets, prob.nbr)
+    st = torch.as_tensor(prob.sigma_t, device="cuda")
+    dirs = (0, 5, 9, 17, 23)
+    Hg = pair.Hierarchy([pair.dg_assemble_tet(mesh, prob.omega[m], st) for m in dirs],
+                        pair.default_air_params(precision=0, **kw))
+    for k, m in enumerate(dirs):
+        mat = O.tet_assemble(prob, prob.omega[m])
+        nnz = _compare(O.Hierarchy(*mat, O.default_params(**kw)), Hg, k)
+        if k == 0:
+            assert nnz < _unfiltered_coarse_nnz(mat, kw)
+
+
+def test_bench_params_hex32_full_size_bit_exact(pair):
+    """Two full-size 32^3 S4 directions (262,144 DOFs each), batched as the bench
+    batches them: every level bit-identical at the bench's parameters."""
+    prob = I.config("hex32_s4")
+    kw = dict(BENCH, distance=1)
+    st = torch.as_tensor(prob.sigma_t, device="cuda")
+    dirs = (3, 20)
+    Hg = pair.Hierarchy([pair.dg_assemble_hex(prob.n, prob.omega[m], st) for m in dirs],
+                        pair.default_air_params(precision=0, **kw))
+    for k, m in enumerate(dirs):
+        mat = O.hex_assemble(prob.n, prob.omega[m], prob.sigma_t)
+        _compare(O.Hierarchy(*mat, O.default_params(**kw)), Hg, k)
+
+
+def test_bench_params_tet40_full_size_bit_exact(pair):
+    """Two full-size 40^3 x 6 checkerboard tet directions (1,536,000 DOFs each),
+    distance-2 lAIR at the bench's parameters: every level bit-identical."""
+    prob = I.config("tet40_s8")
+    kw = dict(BENCH, distance=2)
+    mesh = pair.TetMesh(prob.verts, prob.tets, prob.nbr)
+    st = torch.as_tensor(prob.sigma_t, device="cuda")
+    dirs = (5, 41)
+    Hg = pair.Hierarchy([pair.dg_assemble_tet(mesh, prob.omega[m], st) for m in dirs],
+                        pair.default_air_params(precision=0, **kw))
+    for k, m in enumerate(dirs):
+        mat = O.tet_assemble(prob, prob.omega[m])
+        _compare(O.Hierarchy(*mat, O.default_params(**kw)), Hg, k)
+        del mat
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-7), (2, 1e-7)])
+@pytest.mark.parametrize("nair,phi_R", [(0, 0.0), (1, 0.1)])
+def test_bench_params_si_hex_matches_oracle(pair, precision, tol, nair, phi_R):
+    """SI at the bench's parameters, FP64 cycles (0), FP32 cycles under FP64
+    refinement (1, the bench headline) and under double-float refinement (2)."""
+    prob = I.small_hex(10, order=4, seed=8, ratio=0.8)
+    kw = dict(BENCH, distance=1, nair=nair, phi_R=phi_R)
+    ref, _, info_o = O.si_hex(prob, tol=1e-10, inner_tol=1e-11, params=O.default_params(**kw))
+    assert info_o["rc"] == 0
+    inner = 1e-11 if precision == 0 else 1e-9
+    phi, _, info = pair.si_solve_problem(prob, air=pair.default_air_params(precision=precision, **kw),
+                                         si=pair.default_si_params(tol=1e-10, inner_tol=inner))
+    assert info["max_inner_resid"] <= inner
+    assert np.linalg.norm(_cpu(phi) - ref) <= tol * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-7)])
+def test_bench_params_si_tet_matches_oracle(pair, precision, tol):
+    """SI on jittered tets with distance-2 lAIR at the bench's parameters."""
+    prob = I.small_tet(5, order=4, seed=3, ratio=0.7)
+    kw = dict(BENCH, distance=2)
+    ref, _, info_o = O.si_tet(prob, tol=1e-11, inner_tol=1e-12, params=O.default_params(**kw))
+    assert info_o["rc"] == 0
+    inner = 1e-12 if precision == 0 else 1e-10
+    phi, _, info = pair.si_solve_problem(prob, air=pair.default_air_params(precision=precision, **kw),
+                                         si=pair.default_si_params(tol=1e-11, inner_tol=inner))
+    assert info["max_inner_resid"] <= inner
+    assert np.linalg.norm(_cpu(phi) - ref) <= tol * np.linalg.norm(ref)
