@@ -262,6 +262,115 @@ def run_reference(args):
     return 0
 
 
+def kernel_table(infos, steps, ms, tet, precision):
+    """Per kernel group of the timed steps: CUDA-event time inside the steps,
+    algorithmic bytes counted by the library, launches (units), share of the step."""
+    def tot(key):
+        return sum(i[key] for i in infos)
+    kern = {
+        ("k_res0_csr" if tet else "k_res0_bsr_dd" if precision == 2 else "k_res0_bsr"): (
+            ("FP64 outer residual, level 0 CSR" if tet else
+             "outer residual in double-float pairs (FP32 pipe), level 0 block form" if precision == 2 else
+             "FP64 outer residual, level 0 block form"),
+            tot("t_res0_ms"), tot("n_res0"), tot("gb_res0")),
+        ("k_relax_f+k_relax_c level 0" if tet else "k_relax0_split" if precision else "k_relax_bsr"): (
+            "FP32 F-F-C Jacobi, level 0 " + ("CF-split CSR; one unit = one V-cycle's three sweeps" if tet
+                                             else "CF-split block copy; one unit = one V-cycle's three sweeps"
+                                             if precision else "block form; one unit = one V-cycle's sweeps"),
+            tot("t_relax0_ms"), tot("n_relax0"), tot("gb_relax0")),
+        "k_relax_f+k_relax_c": ("FP32 F-F-C Jacobi, levels >= 1 (CF-split CSR); one unit = every coarse "
+                                "level's sweeps of one V-cycle", tot("t_relaxc_ms"), tot("n_relaxc"), tot("gb_relaxc")),
+    }
+    if tot("n_res32") > 0:
+        kern["k_res32_csr" if tet else "k_res32_bsr"] = (
+            "FP32 inner residual r - A d of a refinement step, level 0 " + ("CSR" if tet else "block form"),
+            tot("t_res32_ms"), tot("n_res32"), tot("gb_res32"))
+    rl = {}
+    for name, (what, t_ms, n_l, gb) in kern.items():
+        rl[name] = {"what": what, "achieved_gbs": gb / (t_ms * 1e-3) if t_ms > 0 else None, "launches": n_l,
+                    "ms_per_launch": t_ms / max(n_l, 1), "gb_per_launch": gb / max(n_l, 1),
+                    "share_of_step": t_ms / steps / ms}
+    return rl
+
+
+def measure_workload(name, args, pair, I, torch, steps=2, warmup=1, fp64=False):
+    """One more workload on the current build, timed like the headline (CUDA events
+    on the launching stream around `steps` steps after `warmup` untimed ones): a
+    step is assembly + AIR setup of every direction + the workload's SI iterations,
+    every direction solved from psi = 0 to a 1e-8 relative residual each iteration."""
+    prob = I.config(name)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    st, ss, qq = (torch.as_tensor(a, device=dev) for a in (prob.sigma_t, prob.sigma_s, prob.q))
+    N, M = prob.N, prob.M
+    tet = hasattr(prob, "tets")
+    geom = pair.TetMesh(prob.verts, prob.tets, prob.nbr) if tet else prob.n
+    fixed = FIXED_SI.get(name, 0)
+    distance = DISTANCE.get(name, 1)
+    kw = dict(theta=args.theta, phi_R=args.phi_R, phi_A=args.phi_A, distance=distance, nair=args.nair)
+    air = pair.default_air_params(precision=args.precision, **kw)
+    si = (pair.default_si_params(tol=1e-8, max_iters=fixed, fixed_iters=1, inner_tol=1e-8, inner_maxit=200) if fixed
+          else pair.default_si_params(tol=1e-8, max_iters=1000, inner_tol=1e-8, inner_maxit=200))
+    zero = torch.zeros(N, dtype=torch.float64, device=dev)
+
+    def solve(a, s_):
+        out, _, info = pair.si_solve(geom, prob.omega, prob.w, st, ss, qq, air=a, si=s_, phi0=zero)
+        return out, info
+
+    for _ in range(warmup):
+        solve(air, si)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    infos = []
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        phi, info = solve(air, si)
+        infos.append(info)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    last = infos[-1]
+    iters = last["si_iters"]
+    t_setup = sum(i["t_setup_ms"] for i in infos) / steps
+    t_solve = sum(i["t_solve_ms"] for i in infos) / steps
+    rl = kernel_table(infos, steps, ms, tet, args.precision)
+    peak, peak_kind = measured_peaks()
+    dom = max(rl, key=lambda k: rl[k]["share_of_step"])
+    entry = {"workload": name + ": " + WORKLOADS[name], "value": N * M * iters / (ms * 1e-3), "unit": UNIT,
+             "ms_per_step": ms, "steps": steps, "warmup": warmup,
+             "step": (f"assembly + AIR setup + {fixed} SI iterations from phi=0" if fixed else
+                      "one complete SI solve from phi=0") + " (every direction from psi=0 to a 1e-8 relative "
+                     "residual each iteration); value = DOF*dir*iterations/step time",
+             "air": {"R": "nAIR degree 1" if args.nair else f"lAIR distance {distance}", "theta": args.theta,
+                     "eps_R": 0.01, "phi_A": args.phi_A, "phi_R": args.phi_R},
+             "si_iterations": iters, "setup_ms": t_setup, "solve_ms": t_solve,
+             "solve_only_value": N * M * iters / (t_solve * 1e-3) if t_solve > 0 else None,
+             "batches": last["batches"], "rebuilt_every_iteration": bool(last["rebuilt"]),
+             "vcycles_per_direction_per_iteration": last["vcycles"] / M / max(iters, 1),
+             "outer_residuals_per_direction_per_iteration": last["outer_residuals"] / M / max(iters, 1),
+             "levels": last["levels_max"], "op_complexity": last["op_complexity"],
+             "max_inner_resid": last["max_inner_resid"],
+             "roofline": {"bound": "hbm", "kernel": dom, "achieved": rl[dom]["achieved_gbs"], "peak": peak,
+                          "unit": "GB/s", "frac": (rl[dom]["achieved_gbs"] / peak) if rl[dom]["achieved_gbs"] else None,
+                          "peak_source": f"{peak_kind}: MEASURED_PEAKS.json hbm_gbs (copy test)", "kernels": rl}}
+    if fp64:
+        air64 = pair.default_air_params(precision=0, **kw)
+        si64 = pair.default_si_params(tol=1e-8, max_iters=fixed or 1000, fixed_iters=int(bool(fixed)),
+                                      inner_tol=1e-8, inner_maxit=200, batch=1, use_graphs=0)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        phi64, i64 = solve(air64, si64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        v64 = N * M * i64["si_iters"] / (ms64 * 1e-3)
+        entry["fp64_one_direction"] = {"value": v64, "ms_per_step": ms64, "setup_ms": i64["t_setup_ms"],
+                                       "speedup_of_fp32_refined_batched": entry["value"] / v64,
+                                       "phi_rel_diff_fp32_refined_vs_fp64":
+                                           (torch.linalg.norm(phi64 - phi) / torch.linalg.norm(phi64)).item()}
+    return entry
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -295,8 +404,14 @@ def run_ours(args):
     si_one = pair.default_si_params(tol=1e-8, max_iters=1, inner_tol=1e-8, inner_maxit=200)
     zero = torch.zeros(N, dtype=torch.float64, device=dev)
 
+    from paper_1910_11463_gb300 import angle
+
     def solve(air_p, si_p, phi0):
-        out, _, info = pair.si_solve(geom, prob.omega, prob.w, st, ss, qq, air=air_p, si=si_p, phi0=phi0)
+        if world > 1:   # parallel in angle: this rank's directions, scalar flux all-reduced each iteration
+            out, _, info, _ = angle.si_solve_angle(geom, prob.omega, prob.w, st, ss, qq, rank, world,
+                                                   air=air_p, si=si_p, phi0=phi0)
+        else:
+            out, _, info = pair.si_solve(geom, prob.omega, prob.w, st, ss, qq, air=air_p, si=si_p, phi0=phi0)
         return out, info
 
     def barrier():
@@ -324,7 +439,9 @@ def run_ours(args):
     launches = pair.kernel_launches() - launches0
     ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
     iters = infos[-1]["si_iters"]
-    value = N * M * iters * world / (ms * 1e-3)
+    # one problem whose directions are split over the ranks: the job solves N x M
+    # DOF*directions per SI iteration whatever the number of ranks
+    value = N * M * iters / (ms * 1e-3)
 
     def tot(key):
         return sum(i[key] for i in infos)
@@ -332,25 +449,7 @@ def run_ours(args):
     phases = [sum(i["t_setup_phase_ms"][k] for i in infos) / args.steps for k in range(4)]
     peak, peak_kind = measured_peaks()
     tet = hasattr(prob, "tets")
-    kern = {
-        ("k_res0_csr" if tet else "k_res0_bsr_dd" if args.precision == 2 else "k_res0_bsr"): (
-            ("FP64 outer residual, level 0 CSR" if tet else
-             "outer residual in double-float pairs (FP32 pipe), level 0 block form" if args.precision == 2 else
-             "FP64 outer residual, level 0 block form"),
-                                                  tot("t_res0_ms"), tot("n_res0"), tot("gb_res0")),
-        ("k_relax_f+k_relax_c level 0" if tet else "k_relax0_split" if args.precision else "k_relax_bsr"): (
-            "FP32 F-F-C Jacobi, level 0 " + ("CF-split CSR; one unit = one V-cycle's three sweeps" if tet
-                                             else "CF-split block copy; one unit = one V-cycle's three sweeps"
-                                             if args.precision else "block form; one unit = one V-cycle's sweeps"),
-            tot("t_relax0_ms"), tot("n_relax0"), tot("gb_relax0")),
-        "k_relax_f+k_relax_c": ("FP32 F-F-C Jacobi, levels >= 1 (CF-split CSR); one unit = every coarse "
-                                "level's sweeps of one V-cycle", tot("t_relaxc_ms"), tot("n_relaxc"), tot("gb_relaxc")),
-    }
-    rl = {}
-    for name, (what, t_ms, n_l, gb) in kern.items():
-        rl[name] = {"what": what, "achieved_gbs": gb / (t_ms * 1e-3) if t_ms > 0 else None, "launches": n_l,
-                    "ms_per_launch": t_ms / max(n_l, 1), "gb_per_launch": gb / max(n_l, 1),
-                    "share_of_step": t_ms / args.steps / ms}
+    rl = kernel_table(infos, args.steps, ms, tet, args.precision)
     dom = max(rl, key=lambda k: rl[k]["share_of_step"])
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "traffic.json")
@@ -382,23 +481,30 @@ def run_ours(args):
     rebuild = {"value": N * M / (ms_reb * 1e-3), "ms_per_iteration": ms_reb,
                "note": "assembly + AIR setup + one SI iteration per step (median of 3)"}
 
-    # e2e: the same full solve through the public API with pinned host buffers,
-    # inputs copied in and phi copied back inside the timed region
+    # e2e: the same steps through the C ABI with HOST buffers (pinned): si_solve
+    # itself copies sigma_t, sigma_s, q and the initial phi in and phi back out,
+    # inside the timed region
     h_st = torch.as_tensor(prob.sigma_t).pin_memory()
     h_ss = torch.as_tensor(prob.sigma_s).pin_memory()
     h_q = torch.as_tensor(prob.q).pin_memory()
-    h_phi0 = torch.zeros(N, dtype=torch.float64).pin_memory()
-    e2e_steps = max(1, min(args.steps, 2))
+    h_phi = torch.zeros(N, dtype=torch.float64).pin_memory()
+    om_e, w_e, red_e = prob.omega, prob.w, None
+    if world > 1:
+        m0, m1 = angle.direction_block(M, world, rank)
+        om_e, w_e, red_e = prob.omega[m0:m1], prob.w[m0:m1], angle.allreduce_sum()
+    e2e_steps = args.steps
     barrier()
     e0.record(stream)
     for _ in range(e2e_steps):
-        out, _, info_e = pair.si_solve(geom, prob.omega, prob.w, h_st, h_ss, h_q, air=air, si=si, phi0=h_phi0)
-        h_out = out.cpu()
+        h_phi.zero_()   # the step's initial guess
+        info_e = pair.si_solve_host(geom, om_e, w_e, h_st, h_ss, h_q, h_phi, air=air, si=si, phi_reduce=red_e)
     e1.record(stream)
     barrier()
-    ms_e2e = e0.elapsed_time(e1) / e2e_steps
-    e2e = {"value": N * M * info_e["si_iters"] * world / (ms_e2e * 1e-3), "unit": UNIT,
-           "h2d_bytes_per_step": 3 * prob.E * 8 + N * 8, "d2h_bytes_per_step": N * 8, "ms_per_step": ms_e2e}
+    ms_e2e = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, world, dev)
+    e2e = {"value": N * M * info_e["si_iters"] / (ms_e2e * 1e-3), "unit": UNIT,
+           "h2d_bytes_per_step": 3 * prob.E * 8 + N * 8, "d2h_bytes_per_step": N * 8, "ms_per_step": ms_e2e,
+           "steps": e2e_steps, "phi_rel_diff_vs_device_api": (torch.linalg.norm(h_phi.to(dev) - phi)
+                                                              / torch.linalg.norm(phi)).item()}
 
     # comparator: plain FP64 pAIR, one direction at a time, no graphs (same GPU, same AIR parameters)
     fp64 = None
@@ -506,13 +612,20 @@ def run_ours(args):
         "setup_phase_ms": {"strength+pmis": phases[0], "p+lair": phases[1], "rap": phases[2],
                            "assembly+other": phases[3]},
         "rebuild_every_iteration": rebuild,
-        "vcycles_per_direction_per_iteration": last["vcycles"] / M / max(iters, 1), "levels": last["levels_max"],
+        "vcycles_per_direction_per_iteration": last["vcycles"] / M / max(iters, 1),
+        "outer_residuals_per_direction_per_iteration": last["outer_residuals"] / M / max(iters, 1),
+        "levels": last["levels_max"],
         "op_complexity": last["op_complexity"], "max_inner_resid": last["max_inner_resid"],
         "roofline": roofline, "clocks": clk, "e2e": e2e, "gpu_launches": launches,
         "fp64_one_direction": fp64,
         "gpu_sweep": gsweep,
         "variants": {"double_float_refinement": dd, "nair_degree1_phiR_0.1": nair},
     }
+    # the other synthetic meshes on the same build: unstructured tets (distance-2
+    # lAIR) and the 64^3 scale run, each with its per-kernel roofline
+    if world == 1 and args.config == "hex32_s4" and not args.no_workloads:
+        line["workloads"] = {w: measure_workload(w, args, pair, I, torch, fp64=(w == "tet40_s8"))
+                             for w in ("tet40_s8", "hex64_s8")}
     if world == 1 or rank == 0:
         line["cpu_baseline"] = (cpu_baseline_oracle(prob, iters, tuned, max_seconds=args.cpu_seconds)
                                 if not args.no_cpu else None)
@@ -535,6 +648,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64-baseline", action="store_true")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the tet40_s8 and hex64_s8 entries printed beside the hex32_s4 headline")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the variants (double-float refinement, nAIR with phi_R = 0.1)")
     ap.add_argument("--theta", type=float, default=0.5)

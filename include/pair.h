@@ -47,7 +47,8 @@ typedef enum {
     PAIR_ERR_NAN = -6,            /* NaN/Inf found in an input or a residual */
     PAIR_ERR_CUDA = -8,           /* a CUDA runtime call failed */
     PAIR_ERR_UNSUPPORTED = -9,    /* size outside what this build handles (message says which) */
-    PAIR_ERR_DEVICE = -10         /* a kernel reported an internal bound violation */
+    PAIR_ERR_DEVICE = -10,        /* a kernel reported an internal bound violation */
+    PAIR_ERR_COMM = -11           /* the scalar-flux reduction function reported an error */
 } pair_status;
 
 typedef struct pair_hier_s *pair_hier;
@@ -219,6 +220,21 @@ PAIR_API pair_status dg_assemble_hex(const pair_mesh *mesh, const double *omega,
 PAIR_API pair_status dg_assemble_tet(const pair_mesh *mesh, const double *omega, const double *sigma_t, int *rowptr,
                                      int *col, double *val, int capacity, int *nnz, void *stream);
 
+/* Scalar-flux reduction for angular decomposition (Sec. 5, parallel in angle: each
+ * process holds the whole mesh and a subset of the directions, and the scalar
+ * flux is summed over the processes once per source iteration).  si_solve, given
+ * a quadrature subset, calls it once per SI iteration with v = a device array of
+ * n = N + 1 doubles: the partial flux sum_{m in subset} w_m psi_m (N values), then
+ * this process's status (0, or 1 if one of its direction solves missed inner_tol).
+ * The function must replace all n values by their sums over the processes (for
+ * example an all-reduce) with the work complete on the device when it returns,
+ * and return 0; any other return ends si_solve with PAIR_ERR_COMM.  Every process
+ * then holds the same flux and takes the same stopping decision; a summed status
+ * above 0 ends every process's si_solve with PAIR_ERR_NOT_CONVERGED.  Each process
+ * passes the same mesh, cross sections and initial phi.  The function runs on the
+ * thread that called si_solve, between kernels of the library's private stream. */
+typedef int (*pair_reduce_fn)(double *v, long long n, void *ctx);
+
 /* Source-iteration controls. */
 typedef struct {
     double tol;          /* stop when ||phi^{n+1} - phi^n|| <= tol ||phi^{n+1}|| (2-norm) */
@@ -245,9 +261,12 @@ typedef struct {
                           * an angular source density added to each direction's source
                           * (sigma_s phi + q) / (4 pi), e.g. the manufactured-solution
                           * source of the Appendix; caller-owned */
+    pair_reduce_fn phi_reduce; /* NULL, or the scalar-flux reduction of a direction subset
+                          * (Sec. 5, parallel in angle), see pair_reduce_fn */
+    void *reduce_ctx;    /* passed to phi_reduce unchanged */
 } si_params;
 
-PAIR_API void si_params_default(si_params *p);   /* 1e-8, 500, 1e-8, 100, 0, 0, 0, 1, 0, 0, 0, NULL */
+PAIR_API void si_params_default(si_params *p);   /* 1e-8, 500, 1e-8, 100, 0, 0, 0, 1, 0, 0, 0, NULL, NULL, NULL */
 
 typedef struct {
     int si_iters;
@@ -272,15 +291,24 @@ typedef struct {
     double t_relaxc_ms;      /* F- and C-Jacobi passes on levels >= 1 (CSR), all cycles */
     int n_relaxc;            /* cycles measured */
     double gb_relaxc;        /* algorithmic GB of those passes */
+    double t_res32_ms;       /* FP32 inner residuals r - A d of the refinement steps */
+    int n_res32;
+    double gb_res32;
+    int outer_residuals;     /* outer (FP64-accurate) residuals over all direction solves */
 } si_info;
 
 /* Source iteration (Eq. sn_transport with Eq. angular_quad): each iteration
  * solves every direction m with AIR, A_m psi_m = D_m^{-1} M (sigma_s phi^n + q)/(4 pi),
  * from psi = 0 to inner_tol, then phi^{n+1} = sum_m w_m psi_m (FP64, fixed m
  * order).
- *   sigma_t, sigma_s, q   device, per-element values (n^3 or ntet)
- *   phi      device, N DOFs (8 n^3 or 4 ntet): in = initial guess, out = result
- *   psi      device N*M (direction-major) or NULL
+ *   sigma_t, sigma_s, q   per-element values (n^3 or ntet)
+ *   phi      N DOFs (8 n^3 or 4 ntet): in = initial guess, out = result
+ *   psi      N*M (direction-major) or NULL
+ * These arrays (and sp->q_ang) may be device memory or HOST memory (pinned,
+ * registered or pageable), each on its own: a host array is copied to a device
+ * buffer on 'stream' before the solve and phi / psi are copied back after it (so
+ * a host phi or psi is complete when si_solve returns); pinned host memory makes
+ * the copies asynchronous DMA.
  *   air      AIR parameters (precision selects FP64 or FP32-refined)
  *   info     host, may be NULL.
  * Errors: PAIR_ERR_NAN if sigma_t, sigma_s, q, the initial phi or q_ang holds a

@@ -5,6 +5,9 @@
 #include <cmath>
 #include <cstring>
 
+#include <type_traits>
+#include <vector>
+
 #include "common.cuh"
 
 
@@ -85,6 +88,58 @@ struct StreamJoin {
 
 void pr::set_last_error(const std::string &msg) { g_last_error = msg; }
 
+namespace {
+// true for host memory (pinned, registered or pageable), false for memory a kernel
+// can read (device or managed)
+bool is_host_ptr(const void *p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
+}
+
+// Device copies of the host arrays among a call's arguments: inputs copied in on
+// the stream before the work, outputs copied back after it, staging freed at exit.
+struct HostStage {
+    cudaStream_t s;
+    std::vector<void *> bufs;
+    struct Out {
+        void *host;
+        const void *dev;
+        size_t bytes;
+    };
+    std::vector<Out> outs;
+    explicit HostStage(cudaStream_t st) : s(st) {}
+    ~HostStage() {
+        for (void *b : bufs) cudaFreeAsync(b, s);
+        cudaStreamSynchronize(s);
+    }
+    template <class T>
+    T *in(T *p, size_t count, bool copy_back = false) {
+        if (!p || count == 0 || !is_host_ptr(p)) return p;
+        auto *d = pr::dmalloc<std::remove_const_t<T>>(count, s);
+        bufs.push_back(d);
+        PR_CUDA(cudaMemcpyAsync(d, p, sizeof(T) * count, cudaMemcpyHostToDevice, s));
+        if (copy_back) outs.push_back({(void *)p, d, sizeof(T) * count});
+        return d;
+    }
+    template <class T>
+    T *out(T *p, size_t count) {   // written by the call only
+        if (!p || count == 0 || !is_host_ptr(p)) return p;
+        auto *d = pr::dmalloc<std::remove_const_t<T>>(count, s);
+        bufs.push_back(d);
+        outs.push_back({(void *)p, d, sizeof(T) * count});
+        return d;
+    }
+    void copy_back() {
+        for (auto &o : outs) PR_CUDA(cudaMemcpyAsync(o.host, o.dev, o.bytes, cudaMemcpyDeviceToHost, s));
+        PR_CUDA(cudaStreamSynchronize(s));
+    }
+};
+}  // namespace
+
 extern "C" {
 
 void air_params_default(air_params *p) {
@@ -117,6 +172,8 @@ void si_params_default(si_params *p) {
     p->solver = 0;
     p->inner_cycles = 0;
     p->q_ang = nullptr;
+    p->phi_reduce = nullptr;
+    p->reduce_ctx = nullptr;
 }
 
 const char *pair_last_error(void) { return g_last_error.c_str(); }
@@ -185,6 +242,7 @@ pair_status air_setup(const pair_csr *A, int count, const air_params *prm, void 
                 PR_CUDA(cudaMemcpyAsync(h.d_n0, h.n0.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s));
                 pr::build_hierarchy(h);
                 pr::alloc_cycle_vectors(h);
+                pr::inner_enable(h);
                 PR_CUDA(cudaStreamSynchronize(s));
             }
         } catch (...) {
@@ -376,6 +434,7 @@ pair_status dg_assemble_hex(const pair_mesh *mesh, const double *omega, const do
     });
 }
 
+
 pair_status si_solve(const pair_mesh *mesh, const pair_quad *quad, const double *sigma_t, const double *sigma_s,
                      const double *q, const air_params *air, const si_params *sp, double *phi, double *psi,
                      void *stream, si_info *info) {
@@ -392,7 +451,18 @@ pair_status si_solve(const pair_mesh *mesh, const pair_quad *quad, const double 
             for (int k = 0; k < 3; ++k)
                 PR_REQUIRE(std::isfinite(quad->omega[3 * m + k]) && std::isfinite(quad->w[m]), PAIR_ERR_ARG,
                            "si_solve: non-finite quadrature");
-        pr::si_run(*mesh, *quad, sigma_t, sigma_s, q, *air, *sp, phi, psi, (cudaStream_t)stream, info);
+        // host arrays are staged through device copies on the caller's stream
+        const bool hex = mesh->kind == PAIR_MESH_HEX;
+        const size_t E = hex ? (size_t)mesh->n * mesh->n * mesh->n : (size_t)mesh->ntet, N = (hex ? 8 : 4) * E;
+        const size_t M = (size_t)quad->M;
+        HostStage st((cudaStream_t)stream);
+        si_params spd = *sp;
+        spd.q_ang = st.in(sp->q_ang, N * M);
+        const double *dst = st.in(sigma_t, E), *dss = st.in(sigma_s, E), *dq = st.in(q, E);
+        double *dphi = st.in(phi, N, true);
+        double *dpsi = st.out(psi, N * M);
+        pr::si_run(*mesh, *quad, dst, dss, dq, *air, spd, dphi, dpsi, (cudaStream_t)stream, info);
+        st.copy_back();
     });
 }
 

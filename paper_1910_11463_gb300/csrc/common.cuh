@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -21,9 +22,14 @@ void cuda_check(cudaError_t e, const char *what, const char *file, int line);
 
 #define PR_CUDA(call) ::pr::cuda_check((call), #call, __FILE__, __LINE__)
 // Every kernel launch of the library is followed by PR_LAUNCH(), which also
-// counts it (launches recorded while capturing a graph are counted per replay).
-extern long long g_launches;
-#define PR_LAUNCH() (++::pr::g_launches, ::pr::cuda_check(cudaGetLastError(), "kernel launch", __FILE__, __LINE__))
+// counts it: in the process-wide count (launches recorded while capturing a graph
+// are counted per replay instead) and in the calling thread's own count, which a
+// capture uses to size its graph while other threads launch work.
+extern std::atomic<long long> g_launches;
+extern thread_local long long g_thread_launches;
+#define PR_LAUNCH() \
+    (++::pr::g_launches, ++::pr::g_thread_launches, \
+     ::pr::cuda_check(cudaGetLastError(), "kernel launch", __FILE__, __LINE__))
 #define PR_REQUIRE(cond, st, msg) \
     do {                          \
         if (!(cond)) ::pr::fail((st), (msg)); \
@@ -160,6 +166,31 @@ struct SweepPlan {
     void release(cudaStream_t s);
 };
 
+// CUDA events of one V-cycle (also recorded inside captured graphs): the level-0
+// relaxation, the FP32 inner residual, and the relaxation of every coarse level
+// (2 per level); one slot per cycle position of a graph
+struct ProfSlot {
+    cudaEvent_t relax0[2] = {nullptr, nullptr};
+    cudaEvent_t res32[2] = {nullptr, nullptr};
+    std::vector<cudaEvent_t> lv;
+    bool relax_timed = false;   // relax0 recorded by the cycle
+    bool res_timed = false;     // res32 recorded by the cycle
+};
+
+// A step's inner iteration of matrix m stops once its FP32 residual is at most
+// max(INNER_TOL_FRAC tol ||b||, INNER_ETA ||r||), r the step's outer residual: no
+// deeper than an FP32 iteration resolves in one step (the FP32 rounding of r32 - A d
+// is ~1e-7 ||r||); the next step continues from the new outer residual.  From the
+// second step on ||r|| <= tol ||b|| / INNER_ETA, so that rounding is at most
+// 1e-7 / INNER_ETA = 1% of tol ||b|| and the inner estimate decides the outer test.
+constexpr double INNER_TOL_FRAC = 1.0;
+constexpr double INNER_ETA = 1e-5;
+
+// cycle positions of the inner-cycle graphs: graph g runs 2^g cycles, on the
+// slots [2^g - 1, 2^(g+1) - 1)
+constexpr int INNER_GRAPHS = 5;
+constexpr int INNER_SLOTS = (1 << INNER_GRAPHS) - 1;
+
 struct Hier {
     int ndir = 0;
     air_params prm{};
@@ -191,17 +222,38 @@ struct Hier {
     int *d_err = nullptr;
     int *d_n0 = nullptr, *d_row00 = nullptr;  // level-0 rows per matrix and first rows
     int sms = 1;                              // multiprocessors of the device
-    // instrumentation: CUDA events around the level-0 kernels (also inside graphs)
+    // FP32 inner correction (precision >= 1, solves with tol > 0): a refinement
+    // step casts the outer residual r into r32 and iterates A d = r in FP32, each
+    // inner cycle a V-cycle on the current inner residual (its correction added to
+    // d32) followed by the FP32 residual r32 - A d32 and its norm; the step ends
+    // with x += d and a new outer residual.  A matrix stops cycling (iactive = 0)
+    // once its inner residual is at most ithr, set by the outer residual.
+    bool inner = false;
+    float *r32 = nullptr, *d32 = nullptr;        // [rows of the batch]
+    float *val32 = nullptr;                       // CSR level 0 values in FP32
+    int *iactive = nullptr, *icount = nullptr;    // [dir]: inner flag, cycles this step
+    int *iany = nullptr;                          // 1 while a matrix of the batch still cycles
+    double *ithr = nullptr, *inorm = nullptr;     // [dir]
+    double rho_est = 0.0;                         // contraction of the inner cycles (0: none yet)
+    cudaGraphExec_t gcyc[INNER_GRAPHS] = {};      // 2^g inner cycles
+    long long gcyc_kernels[INNER_GRAPHS] = {};
+    cudaGraphExec_t gclose = nullptr;             // x += d, outer residual and norms
+    long long gclose_kernels = 0;
+    const double *gi_b = nullptr;
+    double *gi_x = nullptr;
+    double gi_tol = -1;
+    // instrumentation: CUDA events around the level-0 kernels and the coarse levels
+    // (also inside graphs); ev[0..1] bracket the outer residual
     bool prof = false;
-    bool relax_timed = false;   // ev[2], ev[3] recorded by the current cycle
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-    double t_res0 = 0, t_relax0 = 0, gb_res0 = 0, gb_relax0 = 0;
-    long long n_res0 = 0, n_relax0 = 0;
-    // per matrix: level-0 algorithmic bytes of one residual / one F+C relaxation pass
-    std::vector<double> bytes_res0, bytes_relax0;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    std::vector<ProfSlot> slots;       // slot 0: the per-cycle path; 0..INNER_SLOTS-1: inner graphs
+    double t_res0 = 0, t_relax0 = 0, gb_res0 = 0, gb_relax0 = 0, t_res32 = 0, gb_res32 = 0;
+    long long n_res0 = 0, n_relax0 = 0, n_res32 = 0;
+    // per matrix: level-0 algorithmic bytes of one outer residual, one F+C relaxation
+    // pass and one FP32 inner residual
+    std::vector<double> bytes_res0, bytes_relax0, bytes_res32;
     double t_phase[4] = {0, 0, 0, 0};   // setup: strength+PMIS, P+lAIR, RAP, other
-    // coarse-level (l >= 1) relaxation: events per level, bytes per cycle
-    std::vector<cudaEvent_t> evl;      // 2 per level
+    // coarse-level (l >= 1) relaxation: bytes per cycle
     double t_relaxc = 0, gb_relaxc = 0, bytes_relaxc = 0;
     long long n_relaxc = 0;
     cudaGraphExec_t graph = nullptr;
@@ -220,7 +272,14 @@ void free_level(Level &L, cudaStream_t s);
 // cycle.cu
 // r = b - A0 x (FP64), cast into lev[0].vb; per-matrix ||r||; active[d] = ||r|| > tol ||b||
 void residual0(Hier &h, const double *b, const double *x, double tol, bool update_active);
-void vcycle_correct(Hier &h, double *x);       // x += V(lev[0].vb), zero initial guess
+void vcycle_correct(Hier &h, double *x, ProfSlot *ps = nullptr);   // x += V(lev[0].vb), zero initial guess
+// inner correction (h.inner): outer residual into lev[0].vb and r32 with the norms,
+// active and inner flags and thresholds; one inner cycle (V-cycle into d32, FP32
+// residual and inner norm); x += d32 (d32 cleared) for the active matrices
+void inner_enable(Hier &h);
+void residual_outer(Hier &h, const double *b, const double *x, double tol);
+void inner_cycle(Hier &h, ProfSlot *ps);
+void fold_delta(Hier &h, double *x);
 // double-float mode (h.dd): b and x to pairs before a solve, x back after it; the
 // residual and the final relaxation then work on h.b_dd / h.x_dd
 void dd_enable(Hier &h);            // bsr_dd from bsr64 (frees bsr64), vectors
@@ -261,7 +320,9 @@ long long tet_assemble(int T, int ndir, const double *omega_d, const double *ver
 // si.cu
 struct BatchSolve {
     bool converged = true;
-    int iters = 0;
+    int iters = 0;          // V-cycles of the slowest matrix
+    long long cycles = 0;   // V-cycles summed over the matrices
+    int outer = 0;          // outer (FP64 / double-float) residuals taken
     double max_rel = 0;
     double rho_sum = 0;
     int rho_cnt = 0;

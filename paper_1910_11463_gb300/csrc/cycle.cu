@@ -135,8 +135,8 @@ __device__ __forceinline__ double block_sum(double v) {
 // ---- level-0 FP64 residual --------------------------------------------------
 template <class T>
 __global__ void __launch_bounds__(BS) k_res0_bsr(int n, int N, const int8_t *dsign, const double *bsr64,
-                                                 const double *b, const double *x, T *r, double *partials,
-                                                 int maxblk, const int *active) {
+                                                 const double *b, const double *x, T *r, float *r2,
+                                                 double *partials, int maxblk, const int *active) {
     pdl_begin();
     HexRow q = hex_row(n);
     if (active && !active[q.m]) return;
@@ -150,6 +150,7 @@ __global__ void __launch_bounds__(BS) k_res0_bsr(int n, int N, const int8_t *dsi
         acc -= bsr_offdiag<double, double>(n, E, q.m, q.e, q.a, q.idx, dsign, bsr64, x + (long long)q.m * N);
         T rt = (T)acc;
         r[gi] = rt;
+        if (r2) r2[gi] = (float)rt;   // the inner iteration's fixed right-hand side
         // the stopping test needs ||r|| to a few digits: with an FP32 cycle the
         // square of the cast value is summed in FP32 inside each warp
         if (F32) s2f = (float)rt * (float)rt;
@@ -201,8 +202,8 @@ __device__ __forceinline__ void load_dd4(const float2 *p, float2 *w) {
 // Level-0 residual of the block form in double-float: r = b - x - sum_faces A x_nbr,
 // cast to FP32 for the cycle, FP32 squares for the norm (as in k_res0_bsr<float>)
 __global__ void __launch_bounds__(BS) k_res0_bsr_dd(int n, int N, const int8_t *dsign, const float2 *vals,
-                                                    const float2 *b, const float2 *x, float *r, double *partials,
-                                                    int maxblk, const int *active) {
+                                                    const float2 *b, const float2 *x, float *r, float *r2,
+                                                    double *partials, int maxblk, const int *active) {
     pdl_begin();
     HexRow q = hex_row(n);
     if (active && !active[q.m]) return;
@@ -237,6 +238,7 @@ __global__ void __launch_bounds__(BS) k_res0_bsr_dd(int n, int N, const int8_t *
         const float lo = __fadd_rn(__fsub_rn(d0.y, acc.y), d1.y);
         const float rt = __fadd_rn(d1.x, lo);
         r[gi] = rt;
+        if (r2) r2[gi] = rt;
         s2f = rt * rt;
     }
     const double tot = block_sum_f(s2f);
@@ -256,7 +258,7 @@ __global__ void k_dd_join(long long n, const float2 *a, double *out) {
 template <class T>
 __global__ void __launch_bounds__(BS) k_res0_csr(const int *row0, const int *nrow, const int *rowptr, const int *col,
                                                  const double *val, const double *b, const double *x, T *r,
-                                                 double *partials, int maxblk, const int *active) {
+                                                 float *r2, double *partials, int maxblk, const int *active) {
     pdl_begin();
     int m = blockIdx.y;
     if (active && !active[m]) return;
@@ -268,10 +270,144 @@ __global__ void __launch_bounds__(BS) k_res0_csr(const int *row0, const int *nro
         for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) acc += val[p] * x[col[p]];
         acc = b[i] - acc;
         r[i] = (T)acc;
+        if (r2) r2[i] = (float)acc;
         s2 = acc * acc;
     }
     double tot = block_sum(s2);
     if (threadIdx.x == 0) partials[(long long)m * maxblk + blockIdx.x] = tot;
+}
+
+// ---- inner correction (FP32) ---------------------------------------------------
+// A refinement step solves A d = r (r = the outer residual, cast to FP32 in r32)
+// by FP32 V-cycles; between cycles the FP32 residual r32 - A d32 is the next
+// cycle's right-hand side.  Block form: identity diagonal, element-ordered FP32
+// face blocks (bsr32), the same grid and norm partials as the outer residual.
+__global__ void __launch_bounds__(BS) k_res32_bsr(int n, int N, const int8_t *dsign, const float *bsr32,
+                                                  const float *r0, const float *d, float *r, double *partials,
+                                                  int maxblk, const int *active) {
+    pdl_begin();
+    HexRow q = hex_row(n);
+    if (active && !active[q.m]) return;
+    float s2f = 0.0f;
+    if (q.valid) {
+        const long long E = (long long)N / 8;
+        const long long gi = (long long)q.m * N + 8LL * q.e + q.a;
+        const float r0i = r0[gi], di = d[gi];
+        const float acc = bsr_offdiag<float, float>(n, E, q.m, q.e, q.a, q.idx, dsign, bsr32, d + (long long)q.m * N);
+        const float rt = r0i - (di + acc);
+        r[gi] = rt;
+        s2f = rt * rt;
+    }
+    const double tot = block_sum_f(s2f);
+    if (threadIdx.x == 0) partials[(long long)q.m * maxblk + blockIdx.y * gridDim.x + blockIdx.x] = tot;
+}
+
+// CSR level 0 (diagonal stored): r = r0 - A d with FP32 values
+__global__ void __launch_bounds__(BS) k_res32_csr(const int *row0, const int *nrow, const int *rowptr, const int *col,
+                                                  const float *val, const float *r0, const float *d, float *r,
+                                                  double *partials, int maxblk, const int *active) {
+    pdl_begin();
+    const int m = blockIdx.y;
+    if (active && !active[m]) return;
+    const int li = blockIdx.x * blockDim.x + threadIdx.x;
+    float s2f = 0.0f;
+    if (li < nrow[m]) {
+        const int i = row0[m] + li;
+        float acc = 0.0f;
+        for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) acc += val[p] * d[col[p]];
+        const float rt = r0[i] - acc;
+        r[i] = rt;
+        s2f = rt * rt;
+    }
+    const double tot = block_sum_f(s2f);
+    if (threadIdx.x == 0) partials[(long long)m * maxblk + blockIdx.x] = tot;
+}
+
+
+// outer norm of a step: ||r||, active (||r|| > tol ||b||), and the step's inner flag
+// and threshold; *any = 1 if a matrix takes part in the step.  One CTA,
+// a warp per matrix in turn, fixed reduction order.
+__global__ void k_norm_outer(int ndir, const double *partials, int maxblk, double *out, const double *bnorm,
+                             double tol, int *active, int *iactive, double *ithr, int *any) {
+    pdl_begin();
+    __shared__ int sany;
+    if (threadIdx.x == 0) sany = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int m = threadIdx.x >> 5; m < ndir; m += nw) {
+        if (!active[m]) {   // converged earlier: its partials were not written
+            if (lane == 0) iactive[m] = 0;
+            continue;
+        }
+        double sum = 0.0;
+        for (int k = lane; k < maxblk; k += 32) sum += partials[(long long)m * maxblk + k];
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (lane == 0) {
+            const double nr = sqrt(sum);
+            out[m] = nr;
+            const int a = nr > tol * bnorm[m] ? 1 : 0;
+            active[m] = a;
+            iactive[m] = a;
+            ithr[m] = fmax(INNER_TOL_FRAC * tol * bnorm[m], INNER_ETA * nr);
+            if (a) atomicOr(&sany, 1);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *any = sany;
+}
+
+// inner norm after a cycle: counts the cycle (icount accumulates over a solve) and
+// clears the inner flag once the FP32 residual reaches the step's threshold; *any =
+// 1 while a matrix still cycles
+__global__ void k_norm_inner(int ndir, const double *partials, int maxblk, double *out, const double *ithr,
+                             int *iactive, int *icount, int *any) {
+    pdl_begin();
+    __shared__ int sany;
+    if (threadIdx.x == 0) sany = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int m = threadIdx.x >> 5; m < ndir; m += nw) {
+        if (!iactive[m]) continue;
+        double sum = 0.0;
+        for (int k = lane; k < maxblk; k += 32) sum += partials[(long long)m * maxblk + k];
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (lane == 0) {
+            const double nr = sqrt(sum);
+            out[m] = nr;
+            icount[m] += 1;
+            const int a = nr > ithr[m] ? 1 : 0;
+            iactive[m] = a;
+            if (a) atomicOr(&sany, 1);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *any = sany;
+}
+
+// end of a step: x += d on the rows of the matrices that took part (d cleared);
+// the iterate is FP64 or, in double-float mode, a float pair
+__global__ void k_fold_delta(const int *row0, const int *nrow, float *d, double *x64, float2 *xdd,
+                             const int *active) {
+    pdl_begin();
+    const int m = blockIdx.y;
+    if (!active[m]) return;
+    const int li = blockIdx.x * blockDim.x + threadIdx.x;
+    if (li >= nrow[m]) return;
+    const long long i = (long long)row0[m] + li;
+    const float v = d[i];
+    d[i] = 0.0f;
+    if (xdd) {
+        const float2 xo = xdd[i];
+        const float2 s2 = two_sum(xo.x, v);
+        xdd[i] = fast_two_sum(s2.x, __fadd_rn(xo.y, s2.y));
+    } else {
+        x64[i] += (double)v;
+    }
+}
+
+__global__ void k_to_f32(long long n, const double *a, float *out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (float)a[i];
 }
 
 // per-matrix norm from the partials: a warp per matrix, lane k sums partials
@@ -346,8 +482,10 @@ struct SellJob {
     const T *dinv, *b;    // sweeps
     T *out;
     double *x64;          // F sweep: optional fold; final C sweep: target
+    float *d32;           // inner correction: fold / final target instead of x64
     const int *cpts;      // restriction: fine row of each coarse point
     const int *active, *rowdir;
+    const int *any;       // inner correction: the launch does nothing once *any == 0
 };
 
 // F sweep:   out[i] = in[i] + dinv[i] (b[i] - A_i in)        (x64[i] += it, if given)
@@ -360,6 +498,7 @@ struct SellJob {
 template <class T, int MODE, int G>
 __global__ void __launch_bounds__(BS) k_sell(SellJob<T> j) {
     pdl_begin();
+    if (j.any && !*j.any) return;
     const long long t = (long long)blockIdx.x * BS + threadIdx.x;
     const int q = (int)(t / G), g = (int)(t % G);
     const int r = j.row[q];
@@ -388,10 +527,12 @@ __global__ void __launch_bounds__(BS) k_sell(SellJob<T> j) {
     }
     const T v = own + di * (bi - acc);
     if (MODE == SM_C_FINAL) {
-        j.x64[r] += (double)v;
+        if (j.d32) j.d32[r] += (float)v;
+        else j.x64[r] += (double)v;
     } else {
         j.out[r] = v;
-        if (MODE == SM_F && j.x64) j.x64[r] += (double)v;
+        if (MODE == SM_F && j.d32) j.d32[r] += (float)v;
+        else if (MODE == SM_F && j.x64) j.x64[r] += (double)v;
     }
 }
 
@@ -418,8 +559,9 @@ __device__ __forceinline__ void prolong_row(long long i, int8_t c, int p, const 
 // flight): with one row per thread the kernel is latency-bound
 template <class T>
 __global__ void k_prolong(int n, const int8_t *cf, const int *pmap, const int8_t *cfc, const T *xcF, const T *xc,
-                          T *y, T *y2) {
+                          T *y, T *y2, const int *any) {
     pdl_begin();
+    if (any && !*any) return;
     const long long i0 = 4LL * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
     if (i0 >= n) return;
     if (i0 + 4 <= n) {
@@ -450,24 +592,36 @@ __global__ void k_prolong(int n, const int8_t *cf, const int *pmap, const int8_t
 
 // single-level hierarchies: x64 += the coarsest solution on active rows
 template <class T>
-__global__ void k_fold_coarsest(int n, const T *xco, double *x64, const int *active, const int *rowdir) {
+__global__ void k_fold_coarsest(int n, const T *xco, double *x64, float *d32, float2 *xdd, const int *active,
+                                const int *rowdir) {
     pdl_begin();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || (active && !active[rowdir[i]])) return;
-    x64[i] += (double)xco[i];
+    if (d32) {
+        d32[i] += (float)xco[i];
+    } else if (xdd) {
+        const float2 xo = xdd[i];
+        const float2 s2 = two_sum(xo.x, (float)xco[i]);
+        xdd[i] = fast_two_sum(s2.x, __fadd_rn(xo.y, s2.y));
+    } else {
+        x64[i] += (double)xco[i];
+    }
 }
 
 // final correction at a CSR level 0: x64 += the coarsest solution on the rows of
 // matrices that end there (split positions [kX, n))
 template <class T>
-__global__ void k_fold_split(int kX, int n, const int *srow, const T *xco, double *x64, const int *active,
-                             const int *rowdir, float2 *xdd) {
+__global__ void k_fold_split(int kX, int n, const int *srow, const T *xco, double *x64, float *d32,
+                             const int *active, const int *rowdir, float2 *xdd, const int *any) {
     pdl_begin();
+    if (any && !*any) return;
     int k = kX + blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     int i = srow[k];
     if (active && !active[rowdir[i]]) return;
-    if (xdd) {
+    if (d32) {
+        d32[i] += (float)xco[i];
+    } else if (xdd) {
         const float2 xo = xdd[i];
         const float2 s2 = two_sum(xo.x, (float)xco[i]);
         xdd[i] = fast_two_sum(s2.x, __fadd_rn(xo.y, s2.y));
@@ -523,8 +677,10 @@ __global__ void __launch_bounds__(BS) k_relax_bsr(int n, int N, const int8_t *ds
 // v0 at its split position (contiguous across the group, so a sweep reads only its
 // own rows' blocks), the row's element and node follow from its index.  x += v:
 // a float pair (x_dd) or FP64.
-__device__ __forceinline__ void x_add(long long gi, float v, float2 *xdd, double *x64) {
-    if (xdd) {
+__device__ __forceinline__ void x_add(long long gi, float v, float *d32, float2 *xdd, double *x64) {
+    if (d32) {   // inner correction: the FP32 correction of the refinement step
+        d32[gi] += v;
+    } else if (xdd) {
         const float2 xo = xdd[gi];
         const float2 s2 = two_sum(xo.x, v);
         xdd[gi] = fast_two_sum(s2.x, __fadd_rn(xo.y, s2.y));
@@ -538,9 +694,10 @@ __device__ __forceinline__ void x_add(long long gi, float v, float2 *xdd, double
 template <bool FINAL>
 __global__ void __launch_bounds__(BS) k_relax0_split(int n, int N, const int8_t *dsign, const int *srow, int k0,
                                                      int cnt, const float4 *v0, const float *b, const float *in,
-                                                     float *out, bool fold, float2 *xdd, double *x64,
-                                                     const int *active) {
+                                                     float *out, bool fold, float *d32, float2 *xdd, double *x64,
+                                                     const int *active, const int *any) {
     pdl_begin();
+    if (any && !*any) return;
     const int k = blockIdx.x * BS + threadIdx.x;
     if (k >= cnt) return;
     const int gi = srow[k0 + k];
@@ -573,9 +730,9 @@ __global__ void __launch_bounds__(BS) k_relax0_split(int n, int N, const int8_t 
     const float v = xin + (bi - (acc + xin));
     if (!FINAL) {
         out[gi] = v;
-        if (fold) x_add(gi, v, xdd, x64);
+        if (fold) x_add(gi, v, d32, xdd, x64);
     } else {
-        x_add(gi, v, xdd, x64);
+        x_add(gi, v, d32, xdd, x64);
     }
 }
 
@@ -598,8 +755,10 @@ __global__ void k_split0_copy(int nrows, int N, const int *srow, const float *bs
 // segment rows r0.. sit at split positions s0.. (the coarsest group of the split)
 template <class T>
 __global__ void k_coarsest(const int *seg_row0, const int *seg_n, const int *seg_s0, const int *sptr,
-                           const int *scol, const T *sval, const T *dinv, const T *b, T *x, T *xt, int sweeps) {
+                           const int *scol, const T *sval, const T *dinv, const T *b, T *x, T *xt, int sweeps,
+                           const int *any) {
     pdl_begin();
+    if (any && !*any) return;
     int r0 = seg_row0[blockIdx.x], nr = seg_n[blockIdx.x], s0 = seg_s0[blockIdx.x];
     for (int i = threadIdx.x; i < nr; i += blockDim.x) x[r0 + i] = T(0);
     __syncthreads();
@@ -659,14 +818,16 @@ void launch_sell(const Sell &S, SellJob<T> j, int sms, cudaStream_t s) {
 
 // F sweep over the F rows (fold: x64 += the new values, the last level-0 sweep)
 template <class T>
-void relax_f(const Level &L, const T *b, const T *in, T *out, double *fold, const int *active, int sms,
-             cudaStream_t s) {
+void relax_f(const Level &L, const T *b, const T *in, T *out, double *fold, float *fold32, const int *active,
+             const int *any, int sms, cudaStream_t s) {
     SellJob<T> j{};
+    j.any = any;
     j.in = in;
     j.dinv = lv_dinv<T>(L);
     j.b = b;
     j.out = out;
     j.x64 = fold;
+    j.d32 = fold32;
     j.active = active;
     j.rowdir = L.rowdir;
     launch_sell<T, SM_F>(L.sF, j, sms, s);
@@ -675,22 +836,24 @@ void relax_f(const Level &L, const T *b, const T *in, T *out, double *fold, cons
 // C sweep over the C rows into out, or (final) into x64 together with the coarsest
 // rows of matrices that end on this level
 template <class T>
-void relax_c(const Level &L, const T *b, const T *in, T *out, double *x64, const T *xco, const int *active, int sms,
-             cudaStream_t s) {
+void relax_c(const Level &L, const T *b, const T *in, T *out, double *x64, float *d32, const T *xco,
+             const int *active, const int *any, int sms, cudaStream_t s) {
     SellJob<T> j{};
+    j.any = any;
     j.in = in;
     j.dinv = lv_dinv<T>(L);
     j.b = b;
     j.out = out;
     j.x64 = x64;
+    j.d32 = d32;
     j.active = active;
     j.rowdir = L.rowdir;
-    if (x64) {
+    if (x64 || d32) {
         launch_sell<T, SM_C_FINAL>(L.sC, j, sms, s);
         const int kX = L.nF + L.nC;
         if (L.n > kX) {
-            launch_pdl(k_fold_split<T>, blocks_for(L.n - kX, BS), BS, s, kX, L.n, L.srow, xco, x64, active, L.rowdir,
-                       (float2 *)nullptr);
+            launch_pdl(k_fold_split<T>, blocks_for(L.n - kX, BS), BS, s, kX, L.n, L.srow, xco, x64, d32, active,
+                       L.rowdir, (float2 *)nullptr, any);
             PR_LAUNCH();
         }
     } else {
@@ -700,31 +863,39 @@ void relax_c(const Level &L, const T *b, const T *in, T *out, double *x64, const
 
 // b_c = Z b_F + b_C: one row of Z per coarse point
 template <class T>
-void restrict_(const Level &L, const T *bf, T *bc, int sms, cudaStream_t s) {
+void restrict_(const Level &L, const T *bf, T *bc, const int *any, int sms, cudaStream_t s) {
     SellJob<T> j{};
+    j.any = any;
     j.in = bf;
     j.out = bc;
     j.cpts = L.cpts;
     launch_sell<T, SM_RESTRICT>(L.sZ, j, sms, s);
 }
 
+// One V-cycle on lev[0].vb from a zero guess; its correction is added to x64 (the
+// FP64 iterate, or the float-pair iterate in double-float mode) or, in the inner
+// correction, to d32.  'active' gates the level-0 kernels per matrix; 'ps' (may be
+// null) receives the level-0 and coarse-level relaxation events.
 template <class T>
-void vcycle_t(Hier &h, double *x64) {
+void vcycle_t(Hier &h, double *x64, float *d32, const int *active, ProfSlot *ps) {
     cudaStream_t s = h.stream;
     int NL = (int)h.lev.size();
-    const int *active = h.active;
+    const bool prof = h.prof && ps;
+    const int *any = d32 ? h.iany : nullptr;
+    if (ps) ps->relax_timed = false;
     for (int l = 0; l < NL; ++l) {
         Level &L = h.lev[l];
         L.vF = L.vx;   // replaced by the F sweeps' buffer once the level relaxes
-        if (l + 1 < NL) restrict_<T>(L, (const T *)L.vb, (T *)h.lev[l + 1].vb, h.sms, s);
+        if (l + 1 < NL) restrict_<T>(L, (const T *)L.vb, (T *)h.lev[l + 1].vb, any, h.sms, s);
         if (L.n_cseg) {
             launch_pdl(k_coarsest<T>, L.n_cseg, 256, s, L.d_cseg_row0, L.d_cseg_n, L.d_cseg_s0, L.sptr, L.scol,
                                                    (const T *)L.sval, lv_dinv<T>(L), (const T *)L.vb, (T *)L.vx,
-                                                   (T *)L.vxn, h.prm.coarse_sweeps);
+                                                   (T *)L.vxn, h.prm.coarse_sweeps, any);
             PR_LAUNCH();
         }
     }
     const int fs = h.prm.f_sweeps;
+    float2 *xdd = (h.dd && !d32) ? h.x_dd : nullptr;
     for (int l = NL - 2; l >= 0; --l) {
         Level &L = h.lev[l];
         const Level &C = h.lev[l + 1];
@@ -733,7 +904,7 @@ void vcycle_t(Hier &h, double *x64) {
         T *bufs[2] = {(T *)L.vy, (T *)L.vxn};
         const bool split0 = bsr && h.split0 && std::is_same<T, float>::value;
         launch_pdl(k_prolong<T>, blocks_for((L.n + 3) / 4, BS), BS, s, L.n, L.cf, L.pmap, C.cf, (const T *)C.vF,
-                   (const T *)C.vx, bufs[0], (bsr && !split0) ? nullptr : bufs[1]);
+                   (const T *)C.vx, bufs[0], (bsr && !split0) ? nullptr : bufs[1], any);
         PR_LAUNCH();
         int cur = 0;
         if (split0) {
@@ -741,62 +912,61 @@ void vcycle_t(Hier &h, double *x64) {
             // then the rows of matrices that end at level 0
             const int N = h.n0[0];
             const int kX = L.nF + L.nC;
-            float2 *xdd = h.dd ? h.x_dd : nullptr;
-            if (h.prof) { rec_event(h.ev[2], s); h.relax_timed = true; }
+            if (prof) { rec_event(ps->relax0[0], s); ps->relax_timed = true; }
             for (int f = 0; f < fs; ++f, cur ^= 1)
                 if (L.nF > 0) {
                     launch_pdl(k_relax0_split<false>, blocks_for(L.nF, BS), BS, s, h.hex_n, N, h.dsign, L.srow, 0,
                                L.nF, h.v0, (const float *)L.vb, (const float *)bufs[cur], (float *)bufs[cur ^ 1],
-                               f == fs - 1, xdd, x64, active);
+                               f == fs - 1, d32, xdd, x64, active, any);
                     PR_LAUNCH();
                 }
             if (L.nC > 0) {
                 launch_pdl(k_relax0_split<true>, blocks_for(L.nC, BS), BS, s, h.hex_n, N, h.dsign, L.srow, L.nF,
-                           L.nC, h.v0, (const float *)L.vb, (const float *)bufs[cur], (float *)nullptr, true, xdd,
-                           x64, active);
+                           L.nC, h.v0, (const float *)L.vb, (const float *)bufs[cur], (float *)nullptr, true, d32,
+                           xdd, x64, active, any);
                 PR_LAUNCH();
             }
             if (L.n > kX) {
                 launch_pdl(k_fold_split<T>, blocks_for(L.n - kX, BS), BS, s, kX, L.n, L.srow, (const T *)L.vx, x64,
-                           active, L.rowdir, xdd);
+                           d32, active, L.rowdir, xdd, any);
                 PR_LAUNCH();
             }
-            if (h.prof) rec_event(h.ev[3], s);
+            if (prof) rec_event(ps->relax0[1], s);
         } else if (bsr) {
             int N = h.n0[0];
             dim3 grid(blocks_for(h.hex_n, 32), h.hex_n * h.hex_n, h.ndir);
             const T *vals = std::is_same<T, float>::value ? (const T *)h.bsr32 : (const T *)h.bsr64;
-            if (h.prof) { rec_event(h.ev[2], s); h.relax_timed = true; }
+            if (prof) { rec_event(ps->relax0[0], s); ps->relax_timed = true; }
             for (int f = 0; f < fs; ++f, cur ^= 1) {
                 launch_pdl(k_relax_bsr<T, false>, grid, BS, s, h.hex_n, N, h.dsign, vals, L.cf, (const T *)L.vb, bufs[cur],
                                                           bufs[cur ^ 1], 0, nullptr, nullptr, active, nullptr);
                 PR_LAUNCH();
             }
             launch_pdl(k_relax_bsr<T, true>, grid, BS, s, h.hex_n, N, h.dsign, vals, L.cf, (const T *)L.vb, bufs[cur],
-                                                     nullptr, 1, x64, (const T *)L.vx, active,
-                                                     h.dd ? h.x_dd : nullptr);
+                                                     nullptr, 1, x64, (const T *)L.vx, active, xdd);
             PR_LAUNCH();
-            if (h.prof) rec_event(h.ev[3], s);
+            if (prof) rec_event(ps->relax0[1], s);
         } else {
             // C rows stay where the prolongation put them (both buffers); F rows end in
-            // bufs[cur], C rows in vx (level 0: both folded into x64 instead)
+            // bufs[cur], C rows in vx (level 0: both folded into the iterate instead)
             const int *act = l == 0 ? active : nullptr;
-            bool tl = h.prof && l >= 1 && (int)h.evl.size() >= 2 * (l + 1);
-            if (tl) rec_event(h.evl[2 * l], s);
-            if (h.prof && l == 0) { rec_event(h.ev[2], s); h.relax_timed = true; }
+            bool tl = prof && l >= 1 && (int)ps->lv.size() >= 2 * (l + 1);
+            if (tl) rec_event(ps->lv[2 * l], s);
+            if (prof && l == 0) { rec_event(ps->relax0[0], s); ps->relax_timed = true; }
             for (int f = 0; f < fs; ++f, cur ^= 1)
-                relax_f<T>(L, (const T *)L.vb, bufs[cur], bufs[cur ^ 1], l == 0 && f == fs - 1 ? x64 : nullptr, act,
-                           h.sms, s);
-            relax_c<T>(L, (const T *)L.vb, bufs[cur], (T *)L.vx, l == 0 ? x64 : nullptr, (const T *)L.vx, act,
-                       h.sms, s);
-            if (tl) rec_event(h.evl[2 * l + 1], s);
-            if (h.prof && l == 0) rec_event(h.ev[3], s);
+                relax_f<T>(L, (const T *)L.vb, bufs[cur], bufs[cur ^ 1], l == 0 && f == fs - 1 ? x64 : nullptr,
+                           l == 0 && f == fs - 1 ? d32 : nullptr, act, any, h.sms, s);
+            relax_c<T>(L, (const T *)L.vb, bufs[cur], (T *)L.vx, l == 0 ? x64 : nullptr, l == 0 ? d32 : nullptr,
+                       (const T *)L.vx, act, any, h.sms, s);
+            if (tl) rec_event(ps->lv[2 * l + 1], s);
+            if (prof && l == 0) rec_event(ps->relax0[1], s);
         }
         L.vF = bufs[cur];
     }
     if (NL == 1) {   // single-level hierarchies: x += coarsest solution
         Level &L = h.lev[0];
-        launch_pdl(k_fold_coarsest<T>, blocks_for(L.n, BS), BS, s, L.n, (const T *)L.vx, x64, active, L.rowdir);
+        launch_pdl(k_fold_coarsest<T>, blocks_for(L.n, BS), BS, s, L.n, (const T *)L.vx, x64, d32, xdd, active,
+                   L.rowdir);
         PR_LAUNCH();
     }
 }
@@ -910,7 +1080,11 @@ __global__ void k_level_counts_dir(int n, const int *rowptr, const int8_t *cf, c
 void level0_bytes(Hier &h) {
     h.bytes_res0.assign(h.ndir, 0.0);
     h.bytes_relax0.assign(h.ndir, 0.0);
+    h.bytes_res32.assign(h.ndir, 0.0);
     h.bytes_relaxc = 0;
+    // the iterate the level-0 relaxation folds into: FP64 x or a float pair (8 B
+    // read + 8 B written per row), or in the inner correction the FP32 d (4 + 4)
+    const double xfold = h.inner ? 8.0 : 16.0;
     cudaStream_t s = h.stream;
     {
         // coarse levels: each F sweep reads, per F row, its split position (row index and
@@ -951,10 +1125,13 @@ void level0_bytes(Hier &h) {
         for (int m = 0; m < h.ndir; ++m) {
             double nF = (double)c[4 * m], nC = (double)c[4 * m + 1], eF = (double)c[4 * m + 2],
                    eC = (double)c[4 * m + 3];
-            h.bytes_res0[m] = (eF + eC) * 12 + (nF + nC) * (16 + sT);
+            // outer residual: entries, b and x read, r written (and its r32 copy)
+            h.bytes_res0[m] = (eF + eC) * 12 + (nF + nC) * (16 + sT + (h.inner ? 4 : 0));
             double fpass = nF * (8 + 4 * sT) + eF * (4 + sT);
-            double cpass = nC * (8 + 3 * sT + 16) + eC * (4 + sT);
-            h.bytes_relax0[m] = h.prm.f_sweeps * fpass + nF * 16 + cpass;
+            double cpass = nC * (8 + 3 * sT + xfold) + eC * (4 + sT);
+            h.bytes_relax0[m] = h.prm.f_sweeps * fpass + nF * xfold + cpass;
+            // inner residual: row pointer, entries (column + FP32 value), r32 and d read, r written
+            if (h.inner) h.bytes_res32[m] = (eF + eC) * 8 + (nF + nC) * 16;
         }
         return;
     }
@@ -972,7 +1149,10 @@ void level0_bytes(Hier &h) {
     for (int m = 0; m < h.ndir; ++m) {
         double nF = (double)c[4 * m], nC = (double)c[4 * m + 1], fF = (double)c[4 * m + 2], fC = (double)c[4 * m + 3];
         // residual: FP64 face rows (4 values each), b, x read, r written (cycle precision)
-        h.bytes_res0[m] = (fF + fC) * 4 * 8 + (nF + nC) * (8 + 8 + sT);
+        // and, in the inner correction, its r32 copy
+        h.bytes_res0[m] = (fF + fC) * 4 * 8 + (nF + nC) * (8 + 8 + sT + (h.inner ? 4 : 0));
+        // inner residual: FP32 face rows, r32 and d read, r written
+        if (h.inner) h.bytes_res32[m] = (fF + fC) * 4 * 4 + (nF + nC) * 12;
         // each F pass: cf, input and output vector for all rows; A rows and b for F rows
         // C pass: cf, input, x64 (read + write) for all rows; A rows and b for C rows
         if (h.split0) {
@@ -980,7 +1160,7 @@ void level0_bytes(Hier &h) {
             // face; the last one also reads and writes x (16 B); C sweep: per C row its
             // index, input, b, x read + write, and its faces' values
             double fpass = fF * 4 * sT + nF * (4 + 3 * sT);
-            h.bytes_relax0[m] = h.prm.f_sweeps * fpass + nF * 16 + fC * 4 * sT + nC * (4 + 2 * sT + 16);
+            h.bytes_relax0[m] = h.prm.f_sweeps * fpass + nF * xfold + fC * 4 * sT + nC * (4 + 2 * sT + xfold);
         } else {
             double fpass = fF * 4 * sT + (nF + nC) * (1 + 2 * sT) + nF * sT;
             h.bytes_relax0[m] = h.prm.f_sweeps * fpass + fC * 4 * sT + (nF + nC) * (1 + sT + 16) + nC * sT;
@@ -991,10 +1171,49 @@ void level0_bytes(Hier &h) {
 void prof_enable(Hier &h) {
     if (h.prof) return;
     for (auto &e : h.ev) PR_CUDA(cudaEventCreate(&e));
-    h.evl.assign(2 * h.lev.size(), nullptr);
-    for (auto &e : h.evl) PR_CUDA(cudaEventCreate(&e));
+    h.slots.resize(h.inner ? INNER_SLOTS : 1);
+    for (auto &ps : h.slots) {
+        for (auto &e : ps.relax0) PR_CUDA(cudaEventCreate(&e));
+        for (auto &e : ps.res32) PR_CUDA(cudaEventCreate(&e));
+        ps.lv.assign(2 * h.lev.size(), nullptr);
+        for (auto &e : ps.lv) PR_CUDA(cudaEventCreate(&e));
+    }
     h.prof = true;
 }
+
+namespace {
+// outer residual kernels: r = b - A0 x into lev[0].vb (and r2, if given), the
+// per-matrix partial sums of squares into h.partials
+void residual0_launch(Hier &h, const double *b, const double *x, const int *act, float *r2) {
+    cudaStream_t s = h.stream;
+    Level &L = h.lev[0];
+    dim3 grid(h.maxblk, h.ndir);
+    bool f32 = h.prm.precision >= 1;
+    if (h.bsr0 && h.dd) {
+        int N = h.n0[0];
+        dim3 g3(blocks_for(h.hex_n, 32), h.hex_n * h.hex_n, h.ndir);
+        launch_pdl(k_res0_bsr_dd, g3, BS, s, h.hex_n, N, h.dsign, h.bsr_dd, h.b_dd, h.x_dd, (float *)L.vb, r2,
+                   h.partials, h.maxblk, act);
+    } else if (h.bsr0) {
+        int N = h.n0[0];
+        dim3 g3(blocks_for(h.hex_n, 32), h.hex_n * h.hex_n, h.ndir);
+        if (f32)
+            launch_pdl(k_res0_bsr<float>, g3, BS, s, h.hex_n, N, h.dsign, h.bsr64, b, x, (float *)L.vb, r2,
+                       h.partials, h.maxblk, act);
+        else
+            launch_pdl(k_res0_bsr<double>, g3, BS, s, h.hex_n, N, h.dsign, h.bsr64, b, x, (double *)L.vb,
+                       (float *)nullptr, h.partials, h.maxblk, act);
+    } else {
+        if (f32)
+            launch_pdl(k_res0_csr<float>, grid, BS, s, h.d_row00, h.d_n0, L.rowptr, L.col, L.val, b, x, (float *)L.vb,
+                       r2, h.partials, h.maxblk, act);
+        else
+            launch_pdl(k_res0_csr<double>, grid, BS, s, h.d_row00, h.d_n0, L.rowptr, L.col, L.val, b, x,
+                       (double *)L.vb, (float *)nullptr, h.partials, h.maxblk, act);
+    }
+    PR_LAUNCH();
+}
+}  // namespace
 
 void residual0(Hier &h, const double *b, const double *x, double tol, bool update_active) {
     cudaStream_t s = h.stream;
@@ -1002,32 +1221,7 @@ void residual0(Hier &h, const double *b, const double *x, double tol, bool updat
     // are not read
     int *act = update_active ? h.active : nullptr;
     if (h.prof) rec_event(h.ev[0], s);
-    Level &L = h.lev[0];
-    dim3 grid(h.maxblk, h.ndir);
-    bool f32 = h.prm.precision >= 1;
-    if (h.bsr0 && h.dd) {
-        int N = h.n0[0];
-        dim3 g3(blocks_for(h.hex_n, 32), h.hex_n * h.hex_n, h.ndir);
-        launch_pdl(k_res0_bsr_dd, g3, BS, s, h.hex_n, N, h.dsign, h.bsr_dd, h.b_dd, h.x_dd, (float *)L.vb, h.partials,
-                                        h.maxblk, act);
-    } else if (h.bsr0) {
-        int N = h.n0[0];
-        dim3 g3(blocks_for(h.hex_n, 32), h.hex_n * h.hex_n, h.ndir);
-        if (f32)
-            launch_pdl(k_res0_bsr<float>, g3, BS, s, h.hex_n, N, h.dsign, h.bsr64, b, x, (float *)L.vb, h.partials,
-                                                  h.maxblk, act);
-        else
-            launch_pdl(k_res0_bsr<double>, g3, BS, s, h.hex_n, N, h.dsign, h.bsr64, b, x, (double *)L.vb, h.partials,
-                                                   h.maxblk, act);
-    } else {
-        if (f32)
-            launch_pdl(k_res0_csr<float>, grid, BS, s, h.d_row00, h.d_n0, L.rowptr, L.col, L.val, b, x, (float *)L.vb,
-                                                  h.partials, h.maxblk, act);
-        else
-            launch_pdl(k_res0_csr<double>, grid, BS, s, h.d_row00, h.d_n0, L.rowptr, L.col, L.val, b, x, (double *)L.vb,
-                                                   h.partials, h.maxblk, act);
-    }
-    PR_LAUNCH();
+    residual0_launch(h, b, x, act, nullptr);
     if (h.prof) rec_event(h.ev[1], s);
     launch_pdl(k_norm_final, blocks_for(32LL * h.ndir, 128), 128, s, h.ndir, h.partials, h.maxblk, h.rnorm, h.bnorm, tol,
                                                                  act);
@@ -1068,8 +1262,10 @@ void split0_enable(Hier &h) {
     h.v0 = dmalloc<float4>(3LL * std::max(L.n, 1), s);
     k_split0_copy<<<blocks_for(L.n, BS), BS, 0, s>>>(L.n, h.n0[0], L.srow, h.bsr32, h.v0);
     PR_LAUNCH();
-    dfree(h.bsr32, s);
-    h.bsr32 = nullptr;
+    if (!h.inner) {   // the inner correction's FP32 residual reads the element-ordered copy
+        dfree(h.bsr32, s);
+        h.bsr32 = nullptr;
+    }
     h.split0 = true;
 }
 
@@ -1169,9 +1365,76 @@ void autotune_cycle(Hier &h) {
     else autotune_t<double>(h);
 }
 
-void vcycle_correct(Hier &h, double *x) {
-    if (h.prm.precision >= 1) vcycle_t<float>(h, x);
-    else vcycle_t<double>(h, x);
+void inner_enable(Hier &h) {
+    if (h.prm.precision < 1 || h.inner) return;
+    cudaStream_t s = h.stream;
+    Level &L = h.lev[0];
+    const size_t rows = (size_t)std::max(L.n, 1);
+    h.r32 = dmalloc<float>(rows, s);
+    h.d32 = dmalloc<float>(rows, s);
+    PR_CUDA(cudaMemsetAsync(h.d32, 0, rows * sizeof(float), s));
+    h.iactive = dmalloc<int>(h.ndir, s);
+    h.icount = dmalloc<int>(h.ndir, s);
+    h.iany = dmalloc<int>(1, s);
+    PR_CUDA(cudaMemsetAsync(h.iany, 0, sizeof(int), s));
+    h.ithr = dmalloc<double>(h.ndir, s);
+    h.inorm = dmalloc<double>(h.ndir, s);
+    PR_CUDA(cudaMemsetAsync(h.iactive, 0, sizeof(int) * h.ndir, s));
+    PR_CUDA(cudaMemsetAsync(h.icount, 0, sizeof(int) * h.ndir, s));
+    if (h.bsr0) {
+        PR_REQUIRE(h.bsr32, PAIR_ERR_DEVICE, "inner correction: no FP32 block form");
+    } else {
+        h.val32 = dmalloc<float>((size_t)std::max<long long>(L.nnz, 1), s);
+        k_to_f32<<<blocks_for(std::max<long long>(L.nnz, 1), BS), BS, 0, s>>>(L.nnz, L.val, h.val32);
+        PR_LAUNCH();
+    }
+    h.inner = true;
+}
+
+void residual_outer(Hier &h, const double *b, const double *x, double tol) {
+    cudaStream_t s = h.stream;
+    if (h.prof) rec_event(h.ev[0], s);
+    residual0_launch(h, b, x, h.active, h.r32);
+    if (h.prof) rec_event(h.ev[1], s);
+    launch_pdl(k_norm_outer, 1, 32 * std::min(h.ndir, 32), s, h.ndir, (const double *)h.partials, h.maxblk, h.rnorm,
+               (const double *)h.bnorm, tol, h.active, h.iactive, h.ithr, h.iany);
+    PR_LAUNCH();
+}
+
+void inner_cycle(Hier &h, ProfSlot *ps) {
+    cudaStream_t s = h.stream;
+    vcycle_t<float>(h, nullptr, h.d32, h.iactive, ps);
+    const bool prof = h.prof && ps;
+    if (ps) ps->res_timed = false;
+    if (prof) { rec_event(ps->res32[0], s); ps->res_timed = true; }
+    Level &L = h.lev[0];
+    if (h.bsr0) {
+        dim3 g3(blocks_for(h.hex_n, 32), h.hex_n * h.hex_n, h.ndir);
+        launch_pdl(k_res32_bsr, g3, BS, s, h.hex_n, h.n0[0], h.dsign, (const float *)h.bsr32, (const float *)h.r32,
+                   (const float *)h.d32, (float *)L.vb, h.partials, h.maxblk, (const int *)h.iactive);
+    } else {
+        dim3 grid(h.maxblk, h.ndir);
+        launch_pdl(k_res32_csr, grid, BS, s, (const int *)h.d_row00, (const int *)h.d_n0, (const int *)L.rowptr,
+                   (const int *)L.col, (const float *)h.val32, (const float *)h.r32, (const float *)h.d32,
+                   (float *)L.vb, h.partials, h.maxblk, (const int *)h.iactive);
+    }
+    PR_LAUNCH();
+    if (prof) rec_event(ps->res32[1], s);
+    launch_pdl(k_norm_inner, 1, 32 * std::min(h.ndir, 32), s, h.ndir, (const double *)h.partials, h.maxblk, h.inorm,
+               (const double *)h.ithr, h.iactive, h.icount, h.iany);
+    PR_LAUNCH();
+}
+
+void fold_delta(Hier &h, double *x) {
+    dim3 grid(h.maxblk, h.ndir);
+    launch_pdl(k_fold_delta, grid, BS, h.stream, (const int *)h.d_row00, (const int *)h.d_n0, h.d32, x,
+               h.dd ? h.x_dd : (float2 *)nullptr, (const int *)h.active);
+    PR_LAUNCH();
+}
+
+void vcycle_correct(Hier &h, double *x, ProfSlot *ps) {
+    if (h.prm.precision >= 1) vcycle_t<float>(h, x, nullptr, h.active, ps);
+    else vcycle_t<double>(h, x, nullptr, h.active, ps);
 }
 
 }  // namespace pr

@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstring>
 #include <initializer_list>
+#include <string>
 #include <utility>
 
 #include "common.cuh"
@@ -103,38 +104,248 @@ __global__ void k_nonfinite(long long n, const double *a, int *flag) {
 }  // namespace
 
 
+// ---- instrumentation --------------------------------------------------------------
+namespace {
+
+float elapsed_ms(cudaEvent_t a, cudaEvent_t b) {
+    float ms = 0;
+    PR_CUDA(cudaEventElapsedTime(&ms, a, b));
+    return ms;
+}
+
+// outer residual (ev[0..1]) of the matrices that took part
+void account_outer(Hier &h, const std::vector<char> &part) {
+    if (!h.prof) return;
+    h.t_res0 += elapsed_ms(h.ev[0], h.ev[1]);
+    h.n_res0 += 1;
+    double br = 0;
+    for (int d = 0; d < h.ndir; ++d)
+        if (part[d]) br += h.bytes_res0[d];
+    h.gb_res0 += br * 1e-9;
+}
+
+// one V-cycle recorded in slot ps: level-0 relaxation and inner residual of the
+// matrices that took part, coarse-level relaxation (every matrix of the batch)
+void account_cycle(Hier &h, const ProfSlot &ps, const std::vector<char> &part) {
+    if (!h.prof) return;
+    double bx = 0, b32 = 0;
+    for (int d = 0; d < h.ndir; ++d)
+        if (part[d]) {
+            bx += h.bytes_relax0[d];
+            if (!h.bytes_res32.empty()) b32 += h.bytes_res32[d];
+        }
+    if (ps.lv.size() >= 4) {
+        double tl = 0;
+        int nl = 0;
+        for (size_t l = 1; l + 1 < h.lev.size() && 2 * l + 1 < ps.lv.size(); ++l) {
+            if (!h.lev[l].n) continue;
+            tl += elapsed_ms(ps.lv[2 * l], ps.lv[2 * l + 1]);
+            ++nl;
+        }
+        if (nl) {
+            h.t_relaxc += tl;
+            h.n_relaxc += 1;
+            h.gb_relaxc += h.bytes_relaxc * 1e-9;
+        }
+    }
+    if (ps.relax_timed) {
+        h.t_relax0 += elapsed_ms(ps.relax0[0], ps.relax0[1]);
+        h.n_relax0 += 1;
+        h.gb_relax0 += bx * 1e-9;
+    }
+    if (ps.res_timed) {
+        h.t_res32 += elapsed_ms(ps.res32[0], ps.res32[1]);
+        h.n_res32 += 1;
+        h.gb_res32 += b32 * 1e-9;
+    }
+}
+
+template <class F>
+cudaGraphExec_t capture(Hier &h, long long &kernels, F &&body) {
+    cudaGraph_t g;
+    const long long before = g_thread_launches;
+    PR_CUDA(cudaStreamBeginCapture(h.stream, cudaStreamCaptureModeThreadLocal));
+    try {
+        body();
+    } catch (...) {
+        cudaGraph_t dummy = nullptr;
+        cudaStreamEndCapture(h.stream, &dummy);
+        if (dummy) cudaGraphDestroy(dummy);
+        g_launches -= g_thread_launches - before;
+        throw;
+    }
+    PR_CUDA(cudaStreamEndCapture(h.stream, &g));
+    kernels = g_thread_launches - before;
+    g_launches -= kernels;   // counted per replay instead
+    cudaGraphExec_t ex = nullptr;
+    cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    PR_CUDA(e);
+    return ex;
+}
+
+ProfSlot *slot(Hier &h, int k) { return h.prof && k < (int)h.slots.size() ? &h.slots[k] : nullptr; }
+
+}  // namespace
+
 // One-time capture of [V-cycle correction; residual] for fixed (b, x, tol).
 static void ensure_graph(Hier &h, const double *b, double *x, double tol) {
     if (h.graph && h.graph_b == b && h.graph_x == x && h.graph_tol == tol) return;
     if (h.graph) { cudaGraphExecDestroy(h.graph); h.graph = nullptr; }
-    cudaGraph_t g;
-    long long before = g_launches;
-    PR_CUDA(cudaStreamBeginCapture(h.stream, cudaStreamCaptureModeThreadLocal));
-    try {
-        vcycle_correct(h, x);
+    h.graph = capture(h, h.graph_kernels, [&] {
+        vcycle_correct(h, x, slot(h, 0));
         residual0(h, b, x, tol, true);
-    } catch (...) {
-        cudaGraph_t dummy;
-        cudaStreamEndCapture(h.stream, &dummy);
-        if (dummy) cudaGraphDestroy(dummy);
-        throw;
-    }
-    PR_CUDA(cudaStreamEndCapture(h.stream, &g));
-    h.graph_kernels = g_launches - before;
-    g_launches = before;
-    PR_CUDA(cudaGraphInstantiate(&h.graph, g, 0));
-    cudaGraphDestroy(g);
+    });
     h.graph_b = b;
     h.graph_x = x;
     h.graph_tol = tol;
 }
 
+namespace {
+
+// 2^g inner cycles on the slots [2^g - 1, 2^(g+1) - 1): one graph launch, or the
+// launches themselves
+void run_inner(Hier &h, int g, bool use_graph) {
+    const int k = 1 << g;
+    if (use_graph) {
+        if (!h.gcyc[g])
+            h.gcyc[g] = capture(h, h.gcyc_kernels[g], [&] {
+                for (int t = 0; t < k; ++t) inner_cycle(h, slot(h, k - 1 + t));
+            });
+        PR_CUDA(cudaGraphLaunch(h.gcyc[g], h.stream));
+        g_launches += h.gcyc_kernels[g];
+    } else {
+        for (int t = 0; t < k; ++t) inner_cycle(h, slot(h, k - 1 + t));
+    }
+}
+
+// end of a refinement step: x += d, new outer residual, norms and flags
+void run_close(Hier &h, const double *b, double *x, double tol, bool use_graph) {
+    if (use_graph) {
+        if (!h.gclose || h.gi_b != b || h.gi_x != x || h.gi_tol != tol) {
+            if (h.gclose) { cudaGraphExecDestroy(h.gclose); h.gclose = nullptr; }
+            h.gclose = capture(h, h.gclose_kernels, [&] {
+                fold_delta(h, x);
+                residual_outer(h, b, x, tol);
+            });
+            h.gi_b = b;
+            h.gi_x = x;
+            h.gi_tol = tol;
+        }
+        PR_CUDA(cudaGraphLaunch(h.gclose, h.stream));
+        g_launches += h.gclose_kernels;
+    } else {
+        fold_delta(h, x);
+        residual_outer(h, b, x, tol);
+    }
+}
+
+// Iterative refinement with an FP32 inner iteration (Sec. 2.1 solve loop; the
+// precision split of the method's FP32-refined form): each step takes the outer
+// residual r = b - A x (FP64, or double-float on the hex block form), iterates
+// A d = r with FP32 V-cycles and FP32 residuals until every matrix reaches its step
+// threshold, then x += d.  The host reads flags and norms once per step; the
+// cycles of a step are launched back to back (the count predicted from the
+// measured contraction, as graphs of 1, 2, 4 and 8 cycles), and matrices (and, once
+// none is left, whole launches) that reached their threshold do no work.
+BatchSolve solve_batch_inner(Hier &h, const double *b, double *x, double tol, int maxit, bool use_graph) {
+    cudaStream_t s = h.stream;
+    const int nd = h.ndir;
+    norms0(h, b, h.bnorm);
+    set_all_active(h);
+    PR_CUDA(cudaMemsetAsync(h.icount, 0, sizeof(int) * nd, s));
+    if (h.dd) dd_load(h, b, x);
+    residual_outer(h, b, x, tol);
+    std::vector<double> r0(nd), rn(nd), bn(nd), inn(nd);
+    std::vector<int> act(nd), cnt(nd, 0), cyc(nd, 0);
+    PR_CUDA(cudaMemcpyAsync(r0.data(), h.rnorm, sizeof(double) * nd, cudaMemcpyDeviceToHost, s));
+    PR_CUDA(cudaMemcpyAsync(bn.data(), h.bnorm, sizeof(double) * nd, cudaMemcpyDeviceToHost, s));
+    PR_CUDA(cudaMemcpyAsync(act.data(), h.active, sizeof(int) * nd, cudaMemcpyDeviceToHost, s));
+    PR_CUDA(cudaStreamSynchronize(s));
+    account_outer(h, std::vector<char>(nd, 1));
+    for (int d = 0; d < nd; ++d)
+        if (!std::isfinite(r0[d]) || !std::isfinite(bn[d])) fail(PAIR_ERR_NAN, "NaN/Inf in right-hand side or residual");
+    rn = r0;
+    int outer = 1;
+    bool any = std::any_of(act.begin(), act.end(), [](int a) { return a != 0; });
+    while (any) {
+        int done = 0;
+        for (int d = 0; d < nd; ++d)
+            if (act[d]) done = std::max(done, cyc[d]);
+        if (done >= maxit) break;
+        // cycles this step: enough for the slowest matrix at the measured contraction
+        const double rho = h.rho_est > 0 ? h.rho_est : 0.3;
+        double want = 1;
+        for (int d = 0; d < nd; ++d) {
+            if (!act[d] || !(rn[d] > 0)) continue;
+            const double target = std::max(INNER_TOL_FRAC * tol * bn[d], INNER_ETA * rn[d]);
+            want = std::max(want, std::log(target / rn[d]) / std::log(rho));
+        }
+        int need = std::min({(int)std::ceil(want + 0.1), INNER_SLOTS, maxit - done});
+        need = std::max(need, 1);
+        std::vector<int> launched;
+        for (int g = INNER_GRAPHS - 1, rem = need; g >= 0; --g)
+            if (rem >= (1 << g)) { run_inner(h, g, use_graph); launched.push_back(g); rem -= 1 << g; }
+        std::vector<char> was(nd);
+        for (int d = 0; d < nd; ++d) was[d] = act[d] != 0;
+        run_close(h, b, x, tol, use_graph);
+        std::vector<double> rprev = rn;
+        PR_CUDA(cudaMemcpyAsync(cnt.data(), h.icount, sizeof(int) * nd, cudaMemcpyDeviceToHost, s));
+        PR_CUDA(cudaMemcpyAsync(inn.data(), h.inorm, sizeof(double) * nd, cudaMemcpyDeviceToHost, s));
+        PR_CUDA(cudaMemcpyAsync(rn.data(), h.rnorm, sizeof(double) * nd, cudaMemcpyDeviceToHost, s));
+        PR_CUDA(cudaMemcpyAsync(act.data(), h.active, sizeof(int) * nd, cudaMemcpyDeviceToHost, s));
+        PR_CUDA(cudaStreamSynchronize(s));
+        ++outer;
+        std::vector<int> sc(nd);   // cycles of this step per matrix (icount accumulates)
+        for (int d = 0; d < nd; ++d) sc[d] = cnt[d] - cyc[d];
+        // cycle j of the step ran for the matrices with more than j cycles
+        if (h.prof) {
+            int j = 0;
+            for (int g : launched)
+                for (int t = 0; t < (1 << g); ++t, ++j) {
+                    std::vector<char> part(nd);
+                    for (int d = 0; d < nd; ++d) part[d] = was[d] && sc[d] > j;
+                    account_cycle(h, h.slots[(1 << g) - 1 + t], part);
+                }
+            account_outer(h, was);
+        }
+        double rho_obs = 0;
+        for (int d = 0; d < nd; ++d) {
+            if (!was[d]) continue;
+            cyc[d] += sc[d];
+            if (sc[d] > 0 && rprev[d] > 0 && inn[d] > 0)
+                rho_obs = std::max(rho_obs, std::pow(inn[d] / rprev[d], 1.0 / sc[d]));
+            if (!std::isfinite(rn[d])) fail(PAIR_ERR_NAN, "NaN/Inf in a residual during the AIR solve");
+        }
+        if (rho_obs > 0) h.rho_est = std::min(0.95, std::max(0.02, rho_obs));
+        any = std::any_of(act.begin(), act.end(), [](int a) { return a != 0; });
+    }
+    if (h.dd) dd_store(h, x);
+    PR_CUDA(cudaStreamSynchronize(s));
+    BatchSolve out;
+    out.outer = outer;
+    for (int d = 0; d < nd; ++d) {
+        out.iters = std::max(out.iters, cyc[d]);
+        out.cycles += cyc[d];
+        double rel = bn[d] > 0 ? rn[d] / bn[d] : 0.0;
+        out.max_rel = std::max(out.max_rel, rel);
+        if (cyc[d] > 0 && r0[d] > 0 && rn[d] > 0) {
+            out.rho_sum += std::pow(rn[d] / r0[d], 1.0 / cyc[d]);
+            out.rho_cnt++;
+        }
+    }
+    out.converged = !any;
+    return out;
+}
+
+}  // namespace
+
 // Solves every matrix of the hierarchy from the given x to ||b - A x|| <= tol ||b||.
 BatchSolve solve_batch(Hier &h, const double *b, double *x, double tol, int maxit, bool use_graph) {
+    if (h.inner && tol > 0.0) return solve_batch_inner(h, b, x, tol, maxit, use_graph);
     cudaStream_t s = h.stream;
     int nd = h.ndir;
     norms0(h, b, h.bnorm);
-    std::vector<int> ones(nd, 1);
     set_all_active(h);
     if (h.dd) dd_load(h, b, x);
     residual0(h, b, x, tol, true);
@@ -144,41 +355,7 @@ BatchSolve solve_batch(Hier &h, const double *b, double *x, double tol, int maxi
     PR_CUDA(cudaMemcpyAsync(bn.data(), h.bnorm, sizeof(double) * nd, cudaMemcpyDeviceToHost, s));
     PR_CUDA(cudaMemcpyAsync(act.data(), h.active, sizeof(int) * nd, cudaMemcpyDeviceToHost, s));
     PR_CUDA(cudaStreamSynchronize(s));
-    auto account = [&](const std::vector<int> &was_active, bool relax) {
-        if (!h.prof) return;
-        float ms = 0;
-        PR_CUDA(cudaEventElapsedTime(&ms, h.ev[0], h.ev[1]));
-        h.t_res0 += ms;
-        h.n_res0 += 1;
-        double br = 0, bx = 0;
-        for (int d = 0; d < nd; ++d)
-            if (was_active[d]) { br += h.bytes_res0[d]; bx += h.bytes_relax0[d]; }
-        h.gb_res0 += br * 1e-9;
-        if (relax && h.evl.size() >= 4) {
-            // coarse levels run for every direction of the batch
-            double tl = 0;
-            int nl = 0;
-            for (size_t l = 1; l + 1 < h.lev.size(); ++l) {
-                if (!h.lev[l].n) continue;
-                float m2 = 0;
-                PR_CUDA(cudaEventElapsedTime(&m2, h.evl[2 * l], h.evl[2 * l + 1]));
-                tl += m2;
-                ++nl;
-            }
-            if (nl) {
-                h.t_relaxc += tl;
-                h.n_relaxc += 1;
-                h.gb_relaxc += h.bytes_relaxc * 1e-9;
-            }
-        }
-        if (relax && h.relax_timed) {
-            PR_CUDA(cudaEventElapsedTime(&ms, h.ev[2], h.ev[3]));
-            h.t_relax0 += ms;
-            h.n_relax0 += 1;
-            h.gb_relax0 += bx * 1e-9;
-        }
-    };
-    account(ones, false);
+    account_outer(h, std::vector<char>(nd, 1));
     for (int d = 0; d < nd; ++d)
         if (!std::isfinite(r0[d]) || !std::isfinite(bn[d])) fail(PAIR_ERR_NAN, "NaN/Inf in right-hand side or residual");
     if (use_graph) ensure_graph(h, b, x, tol);
@@ -189,14 +366,18 @@ BatchSolve solve_batch(Hier &h, const double *b, double *x, double tol, int maxi
             PR_CUDA(cudaGraphLaunch(h.graph, s));
             g_launches += h.graph_kernels;
         } else {
-            vcycle_correct(h, x);
+            vcycle_correct(h, x, slot(h, 0));
             residual0(h, b, x, tol, true);
         }
         ++k;
-        std::vector<int> was = act;
+        std::vector<char> was(nd);
+        for (int d = 0; d < nd; ++d) was[d] = act[d] != 0;
         PR_CUDA(cudaMemcpyAsync(act.data(), h.active, sizeof(int) * nd, cudaMemcpyDeviceToHost, s));
         PR_CUDA(cudaStreamSynchronize(s));
-        account(was, true);
+        if (h.prof) {
+            account_cycle(h, h.slots[0], was);
+            account_outer(h, was);
+        }
         any = false;
         for (int d = 0; d < nd; ++d) {
             if (act[d]) { any = true; itd[d] = k + 1; }
@@ -208,11 +389,13 @@ BatchSolve solve_batch(Hier &h, const double *b, double *x, double tol, int maxi
     PR_CUDA(cudaStreamSynchronize(s));
     BatchSolve out;
     out.iters = k;
+    out.outer = k + 1;
     for (int d = 0; d < nd; ++d) {
         if (!std::isfinite(rn[d])) fail(PAIR_ERR_NAN, "NaN/Inf in a residual during the AIR solve");
         double rel = bn[d] > 0 ? rn[d] / bn[d] : 0.0;
         out.max_rel = std::max(out.max_rel, rel);
         int kd = std::min(itd[d], k);
+        out.cycles += kd;
         if (kd > 0 && r0[d] > 0 && rn[d] > 0) {
             out.rho_sum += std::pow(rn[d] / r0[d], 1.0 / kd);
             out.rho_cnt++;
@@ -345,18 +528,27 @@ void csr_transpose_dev(int n, long long nnz, const int *rowptr, const int *col, 
 
 Hier::~Hier() {
     if (graph) cudaGraphExecDestroy(graph);
+    for (auto &g : gcyc)
+        if (g) cudaGraphExecDestroy(g);
+    if (gclose) cudaGraphExecDestroy(gclose);
     if (dag) {
         if (stream) dag->release(stream);
         delete dag;
     }
     for (auto &e : ev)
         if (e) cudaEventDestroy(e);
-    for (auto &e : evl)
-        if (e) cudaEventDestroy(e);
+    for (auto &ps : slots) {
+        for (auto &e : ps.relax0)
+            if (e) cudaEventDestroy(e);
+        for (auto &e : ps.res32)
+            if (e) cudaEventDestroy(e);
+        for (auto &e : ps.lv)
+            if (e) cudaEventDestroy(e);
+    }
     if (stream) {
         for (auto &L : lev) free_level(L, stream);
         void *ptrs[] = {bsr64, bsr32, dsign, partials, rnorm, bnorm, rnorm0, active, d_err, d_n0, d_row00,
-                        bsr_dd, b_dd, x_dd, v0};
+                        bsr_dd, b_dd, x_dd, v0, r32, d32, val32, iactive, icount, iany, ithr, inorm};
         for (void *p : ptrs) dfree(p, stream);
         cudaStreamSynchronize(stream);
         cudaStreamDestroy(stream);
@@ -407,6 +599,9 @@ size_t bytes_per_dir(const pair_mesh &mesh, int precision, bool gin) {
     double om[3] = {1, 1, 1};
     size_t nnz0 = hex ? (size_t)hex_nnz(mesh.n, om) : N * 13;
     size_t lvl0 = nnz0 * 12 + (hex ? N * 96 + (precision ? N * 48 : 0) : 0) + E * nb * nb * 8 + (gin ? N * 8 : 0);
+    // FP32 inner correction: the FP32 operator copy its residual reads (element-ordered
+    // blocks, or CSR values) and its right-hand side and correction
+    if (precision) lvl0 += (hex ? N * 48 : nnz0 * 4) + N * 8;
     size_t coarse = nnz0 * 12 * 3 / 2 + nnz0 * 8;   // coarse operators, Z, setup scratch
     // SELL copies (column + value in the cycle precision, ~10% padding) of the coarse
     // levels, of level 0 for the tetrahedral CSR form, and of Z
@@ -534,6 +729,7 @@ void build_batch(DirBatch &B, const pair_mesh &mesh, const double *omega_h, cons
     build_hierarchy(*h);
     alloc_cycle_vectors(*h);
     dd_enable(*h);
+    inner_enable(*h);
     split0_enable(*h);
     level0_bytes(*h);
     prof_enable(*h);
@@ -591,7 +787,8 @@ void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t,
     double *w_d = dmalloc<double>(M, s);
     cl.bufs.push_back(w_d);
     PR_CUDA(cudaMemcpyAsync(w_d, quad.w, sizeof(double) * M, cudaMemcpyHostToDevice, s));
-    double *phinew = dmalloc<double>(N, s);
+    // the new flux, and one status slot for the reduction of a direction subset
+    double *phinew = dmalloc<double>(N + 1, s);
     cl.bufs.push_back(phinew);
     int nbk = (int)blocks_for(N, BS);
     double *part = dmalloc<double>(2 * (size_t)nbk, s);
@@ -609,14 +806,15 @@ void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t,
     double max_inner = 0, opc_sum = 0, change = 0;
     int opc_cnt = 0, it = 0;
     double t_res0 = 0, t_relax0 = 0, gb_res0 = 0, gb_relax0 = 0, tph[4] = {0, 0, 0, 0};
-    double t_relaxc = 0, gb_relaxc = 0;
-    long long n_res0 = 0, n_relax0 = 0, n_relaxc = 0;
+    double t_relaxc = 0, gb_relaxc = 0, t_res32 = 0, gb_res32 = 0;
+    long long n_res0 = 0, n_relax0 = 0, n_relaxc = 0, n_res32 = 0, outer_res = 0;
     auto harvest = [&](Hier &h) {
         t_res0 += h.t_res0; t_relax0 += h.t_relax0; gb_res0 += h.gb_res0; gb_relax0 += h.gb_relax0;
         n_res0 += h.n_res0; n_relax0 += h.n_relax0;
         t_relaxc += h.t_relaxc; gb_relaxc += h.gb_relaxc; n_relaxc += h.n_relaxc;
-        h.t_res0 = h.t_relax0 = h.gb_res0 = h.gb_relax0 = h.t_relaxc = h.gb_relaxc = 0;
-        h.n_res0 = h.n_relax0 = h.n_relaxc = 0;
+        t_res32 += h.t_res32; gb_res32 += h.gb_res32; n_res32 += h.n_res32;
+        h.t_res0 = h.t_relax0 = h.gb_res0 = h.gb_relax0 = h.t_relaxc = h.gb_relaxc = h.t_res32 = h.gb_res32 = 0;
+        h.n_res0 = h.n_relax0 = h.n_relaxc = h.n_res32 = 0;
     };
     bool converged = false;
     auto elapsed = [&](cudaStream_t st) {
@@ -626,9 +824,11 @@ void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t,
         PR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
         return (double)ms;
     };
+    std::string local_fail;   // with a reduction: the first unconverged solve of this iteration
     for (it = 0; it < sp.max_iters; ++it) {
-        PR_CUDA(cudaMemsetAsync(phinew, 0, sizeof(double) * N, s));
+        PR_CUDA(cudaMemsetAsync(phinew, 0, sizeof(double) * (N + 1), s));
         PR_CUDA(cudaStreamSynchronize(s));
+        local_fail.clear();
         for (int bi = 0; bi < nb; ++bi) {
             DirBatch &Bt = batches[bi];
             if (!Bt.h) {
@@ -689,9 +889,12 @@ void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t,
                 char buf[160];
                 snprintf(buf, sizeof buf, "AIR solve reached %d cycles with relative residual %.3e > %.3e", bs.iters,
                          bs.max_rel, sp.inner_tol);
-                fail(PAIR_ERR_NOT_CONVERGED, buf);
+                // with a reduction the other processes wait for this one: report after it
+                if (!sp.phi_reduce) fail(PAIR_ERR_NOT_CONVERGED, buf);
+                if (local_fail.empty()) local_fail = buf;
             }
-            vcycles += bs.iters * Bt.nd;
+            vcycles += bs.cycles;
+            outer_res += bs.outer;
             max_inner = std::max(max_inner, bs.max_rel);
             k_phi_acc<<<blocks_for(N, BS), BS, 0, hs>>>(N, Bt.nd, w_d + Bt.m0, x, phinew);
             PR_LAUNCH();
@@ -702,6 +905,20 @@ void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t,
                 Bt.b = Bt.xown = nullptr;
                 free_batch_ops(Bt);
             }
+        }
+        if (sp.phi_reduce) {   // angular decomposition: sum the partial fluxes and statuses
+            const double st = local_fail.empty() ? 0.0 : 1.0;
+            PR_CUDA(cudaMemcpyAsync(phinew + N, &st, sizeof(double), cudaMemcpyHostToDevice, s));
+            PR_CUDA(cudaStreamSynchronize(s));
+            const int rc = sp.phi_reduce(phinew, N + 1, sp.reduce_ctx);
+            PR_REQUIRE(rc == 0, PAIR_ERR_COMM, "scalar-flux reduction returned " + std::to_string(rc));
+            double tot = 0;
+            PR_CUDA(cudaMemcpyAsync(&tot, phinew + N, sizeof(double), cudaMemcpyDeviceToHost, s));
+            PR_CUDA(cudaStreamSynchronize(s));
+            if (tot > 0)
+                fail(PAIR_ERR_NOT_CONVERGED, local_fail.empty() ? "a direction solve of another process missed "
+                                                                  "inner_tol"
+                                                                : local_fail);
         }
         k_diff_partials<<<nbk, BS, 0, s>>>(N, phinew, phi, part);
         PR_LAUNCH();
@@ -737,6 +954,10 @@ void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t,
         info->t_relaxc_ms = t_relaxc;
         info->n_relaxc = (int)n_relaxc;
         info->gb_relaxc = gb_relaxc;
+        info->t_res32_ms = t_res32;
+        info->n_res32 = (int)n_res32;
+        info->gb_res32 = gb_res32;
+        info->outer_residuals = (int)outer_res;
         for (int k = 0; k < 3; ++k) info->t_setup_phase_ms[k] = tph[k];
         info->t_setup_phase_ms[3] = t_setup - (tph[0] + tph[1] + tph[2]);
     }
@@ -841,7 +1062,7 @@ void si_adjoint_run(const pair_mesh &mesh, const pair_quad &quad, const double *
                          bs.iters, bs.max_rel);
                 fail(PAIR_ERR_NOT_CONVERGED, buf2);
             }
-            vcycles += bs.iters * Bt.nd;
+            vcycles += (int)bs.cycles;
             max_inner = std::max(max_inner, bs.max_rel);
             if (hex)
                 k_wty_acc<8><<<blocks_for(N, BS), BS, 0, hs>>>(E, Bt.nd, Bt.W, w_d + Bt.m0, Bt.xown, acc);

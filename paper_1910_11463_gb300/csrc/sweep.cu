@@ -93,19 +93,20 @@ void sweep_solve(Hier &h, const double *b, double *x, bool use_graph) {
     if (!h.graph || h.graph_b != b || h.graph_x != x) {
         if (h.graph) { cudaGraphExecDestroy(h.graph); h.graph = nullptr; }
         cudaGraph_t g;
-        const long long before = g_launches;
+        const long long before = g_thread_launches;
         PR_CUDA(cudaStreamBeginCapture(h.stream, cudaStreamCaptureModeThreadLocal));
         try {
             launch_sweep(h, b, x);
         } catch (...) {
-            cudaGraph_t dummy;
+            cudaGraph_t dummy = nullptr;
             cudaStreamEndCapture(h.stream, &dummy);
             if (dummy) cudaGraphDestroy(dummy);
+            g_launches -= g_thread_launches - before;
             throw;
         }
         PR_CUDA(cudaStreamEndCapture(h.stream, &g));
-        h.graph_kernels = g_launches - before;
-        g_launches = before;
+        h.graph_kernels = g_thread_launches - before;
+        g_launches -= h.graph_kernels;   // counted per replay instead
         PR_CUDA(cudaGraphInstantiate(&h.graph, g, 0));
         cudaGraphDestroy(g);
         h.graph_b = b;

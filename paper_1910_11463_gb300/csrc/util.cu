@@ -6,7 +6,8 @@
 
 namespace pr {
 
-long long g_launches = 0;
+std::atomic<long long> g_launches{0};
+thread_local long long g_thread_launches = 0;
 
 void fail(pair_status st, const std::string &msg) { throw Error{st, msg}; }
 

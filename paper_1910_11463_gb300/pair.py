@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libpair.so")
 PAIR_OK = 0
 STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_OOM", -3: "ERR_SINGULAR", -4: "ERR_NOT_CONVERGED",
           -6: "ERR_NAN", -8: "ERR_CUDA",
-          -9: "ERR_UNSUPPORTED", -10: "ERR_DEVICE"}
+          -9: "ERR_UNSUPPORTED", -10: "ERR_DEVICE", -11: "ERR_COMM"}
 
 
 class PairError(RuntimeError):
@@ -89,11 +89,16 @@ class pair_quad(C.Structure):
     _fields_ = [("M", C.c_int), ("omega", C.c_void_p), ("w", C.c_void_p)]
 
 
+# pair_reduce_fn: int (*)(double *v, long long n, void *ctx)
+REDUCE_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_longlong, C.c_void_p)
+
+
 class si_params(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iters", C.c_int), ("inner_tol", C.c_double), ("inner_maxit", C.c_int),
                 ("batch", C.c_int), ("mem_budget_gb", C.c_double), ("g_inflow", C.c_double),
                 ("use_graphs", C.c_int), ("fixed_iters", C.c_int), ("solver", C.c_int),
-                ("inner_cycles", C.c_int), ("q_ang", C.c_void_p)]
+                ("inner_cycles", C.c_int), ("q_ang", C.c_void_p), ("phi_reduce", REDUCE_FN),
+                ("reduce_ctx", C.c_void_p)]
 
 
 class si_info(C.Structure):
@@ -103,7 +108,8 @@ class si_info(C.Structure):
                 ("op_complexity", C.c_double), ("t_res0_ms", C.c_double), ("n_res0", C.c_int),
                 ("gb_res0", C.c_double), ("t_relax0_ms", C.c_double), ("n_relax0", C.c_int),
                 ("gb_relax0", C.c_double), ("t_setup_phase_ms", C.c_double * 4), ("t_relaxc_ms", C.c_double),
-                ("n_relaxc", C.c_int), ("gb_relaxc", C.c_double)]
+                ("n_relaxc", C.c_int), ("gb_relaxc", C.c_double), ("t_res32_ms", C.c_double),
+                ("n_res32", C.c_int), ("gb_res32", C.c_double), ("outer_residuals", C.c_int)]
 
 
 _lib = None
@@ -349,12 +355,50 @@ def dg_assemble_tet(mesh: "TetMesh", omega, sigma_t: torch.Tensor):
     return rowptr, col, val
 
 
+class _CudaView:
+    """Zero-copy view of library-owned device memory (CUDA array interface)."""
+
+    def __init__(self, ptr: int, n: int):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<f8", "data": (ptr, False), "version": 3,
+                                         "strides": None}
+
+
+class ReduceCallback:
+    """The ctypes function for si_params.phi_reduce around fn(v): v is the library's
+    array (N partial scalar-flux values, then one status value) as a float64 tensor
+    view, on `device` ("cuda", or "cpu" for host memory), and fn must sum it over
+    the processes in place, e.g. torch.distributed.all_reduce(v).  An exception in
+    fn makes the library return PAIR_ERR_COMM; it is kept in .error."""
+
+    def __init__(self, fn, device="cuda"):
+        self.fn = fn
+        self.device = torch.device(device)
+        self.error = None
+        self.cfunc = REDUCE_FN(self._call)
+
+    def _call(self, ptr, n, ctx):
+        try:
+            if self.device.type == "cuda":
+                v = torch.as_tensor(_CudaView(ptr, n), device=self.device)
+            else:
+                v = torch.from_numpy(np.ctypeslib.as_array((C.c_double * n).from_address(ptr)))
+            self.fn(v)
+            if self.device.type == "cuda":
+                torch.cuda.synchronize(self.device)
+            return 0
+        except Exception as e:   # reported to the library as a status, re-raised by si_solve
+            self.error = e
+            return 1
+
+
 def si_solve(n, omega, w, sigma_t, sigma_s, q, air: air_params | None = None, si: si_params | None = None,
-             phi0=None, want_psi: bool = False, device="cuda", q_ang=None):
+             phi0=None, want_psi: bool = False, device="cuda", q_ang=None, phi_reduce=None):
     """Source iteration on the n^3 hex mesh (n an int) or on a TetMesh.  Cross
     sections may be CPU or CUDA tensors (CPU inputs are copied to the device and
     phi is returned on the device).  q_ang: optional (M, N) angular source density
-    added per direction.  Returns (phi, psi or None, info dict)."""
+    added per direction.  phi_reduce: optional fn(v) summing the partial scalar
+    flux of this direction subset over the processes in place (see
+    ReduceCallback).  Returns (phi, psi or None, info dict)."""
     air = air or default_air_params()
     si = si or default_si_params()
     qa_dev = None
@@ -362,6 +406,11 @@ def si_solve(n, omega, w, sigma_t, sigma_s, q, air: air_params | None = None, si
         qa_dev = torch.as_tensor(q_ang, dtype=torch.float64).to(device).contiguous()
         si = si_params.from_buffer_copy(si)
         si.q_ang = qa_dev.data_ptr()
+    red = None
+    if phi_reduce is not None:
+        red = phi_reduce if isinstance(phi_reduce, ReduceCallback) else ReduceCallback(phi_reduce, device)
+        si = si_params.from_buffer_copy(si)
+        si.phi_reduce = red.cfunc
     om = np.ascontiguousarray(omega, dtype=np.float64)
     ww = np.ascontiguousarray(w, dtype=np.float64)
     M = om.shape[0]
@@ -378,10 +427,52 @@ def si_solve(n, omega, w, sigma_t, sigma_s, q, air: air_params | None = None, si
     quad = pair_quad(M, om.ctypes.data, ww.ctypes.data)
     rc = lib().si_solve(C.byref(mstruct), C.byref(quad), _dptr(st), _dptr(ss), _dptr(qq), C.byref(air),
                         C.byref(si), _dptr(phi), _dptr(psi) if psi is not None else None, _stream(), C.byref(info))
+    if red is not None and red.error is not None and rc == -11:
+        raise PairError(rc, lib().pair_last_error().decode()) from red.error
     _check(rc)
     out = {f: getattr(info, f) for f, _ in si_info._fields_}
     out["t_setup_phase_ms"] = list(info.t_setup_phase_ms)
     return phi, psi, out
+
+
+def _host_ptr(a, name):
+    if a is None:
+        return None
+    if isinstance(a, torch.Tensor):
+        if a.is_cuda or not a.is_contiguous() or a.dtype != torch.float64:
+            raise ValueError(f"{name}: a contiguous float64 CPU tensor is required")
+        return C.c_void_p(a.data_ptr())
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
+        raise ValueError(f"{name}: a contiguous float64 numpy array is required")
+    return C.c_void_p(a.ctypes.data)
+
+
+def si_solve_host(n, omega, w, sigma_t, sigma_s, q, phi, psi=None, air: air_params | None = None,
+                  si: si_params | None = None, phi_reduce=None):
+    """si_solve on HOST arrays (float64 numpy arrays or CPU tensors; pinned tensors
+    make the copies asynchronous): the library copies sigma_t, sigma_s, q and the
+    initial phi to the device on the current stream, solves, and writes phi (and
+    psi, (M, N), if given) back in place.  Returns the info dict."""
+    air = air or default_air_params()
+    si = si or default_si_params()
+    red = None
+    if phi_reduce is not None:
+        red = phi_reduce if isinstance(phi_reduce, ReduceCallback) else ReduceCallback(phi_reduce)
+        si = si_params.from_buffer_copy(si)
+        si.phi_reduce = red.cfunc
+    om = np.ascontiguousarray(omega, dtype=np.float64)
+    ww = np.ascontiguousarray(w, dtype=np.float64)
+    mstruct, _, _ = _mesh_struct(n)
+    info = si_info()
+    quad = pair_quad(om.shape[0], om.ctypes.data, ww.ctypes.data)
+    rc = lib().si_solve(C.byref(mstruct), C.byref(quad), _host_ptr(sigma_t, "sigma_t"), _host_ptr(sigma_s, "sigma_s"),
+                        _host_ptr(q, "q"), C.byref(air), C.byref(si), _host_ptr(phi, "phi"), _host_ptr(psi, "psi"),
+                        _stream(), C.byref(info))
+    if red is not None and red.error is not None and rc == -11:
+        raise PairError(rc, lib().pair_last_error().decode()) from red.error
+    _check(rc)
+    return {f: getattr(info, f) if not isinstance(getattr(info, f), C.Array) else list(getattr(info, f))
+            for f, _ in si_info._fields_}
 
 
 def si_solve_problem(prob, mesh=None, **kw):

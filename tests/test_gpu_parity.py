@@ -319,3 +319,23 @@ def test_c2_direction_full_size_setup_bit_exact(pair):
         assert np.array_equal(_cpu(mg[2]).view(np.uint64), mo[2].view(np.uint64))
         H_g = pair.Hierarchy([mg], pair.default_air_params(precision=0))
         _compare_hierarchies(O.Hierarchy(*mo), H_g, 0)
+
+
+def test_si_host_buffers_equal_device_buffers(pair):
+    """si_solve given HOST arrays (pageable numpy, and pinned tensors) stages them
+    through device copies itself: phi and psi equal the device call bit for bit."""
+    prob = I.small_hex(6, order=4, seed=14, ratio=0.8)
+    air = pair.default_air_params(precision=1)
+    si = pair.default_si_params(tol=1e-9, inner_tol=1e-9)
+    phi_d, psi_d, info_d = pair.si_solve_problem(prob, air=air, si=si, want_psi=True)
+    phi_h = np.zeros(prob.N)
+    psi_h = np.zeros((prob.M, prob.N))
+    info_h = pair.si_solve_host(prob.n, prob.omega, prob.w, prob.sigma_t.copy(), prob.sigma_s.copy(), prob.q.copy(),
+                                phi_h, psi_h, air=air, si=si)
+    assert info_h["si_iters"] == info_d["si_iters"]
+    assert np.array_equal(phi_h.view(np.uint64), _cpu(phi_d).view(np.uint64))
+    assert np.array_equal(psi_h.view(np.uint64), _cpu(psi_d).view(np.uint64))
+    pin = [torch.as_tensor(a).pin_memory() for a in (prob.sigma_t, prob.sigma_s, prob.q)]
+    phi_p = torch.zeros(prob.N, dtype=torch.float64).pin_memory()
+    pair.si_solve_host(prob.n, prob.omega, prob.w, *pin, phi_p, air=air, si=si)
+    assert np.array_equal(phi_p.numpy().view(np.uint64), phi_h.view(np.uint64))
