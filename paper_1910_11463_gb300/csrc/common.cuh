@@ -111,6 +111,7 @@ struct Sell {
     int nrows = 0, npos = 0;
     long long nnz = 0;   // stored slots including padding
     int *ptr = nullptr, *row = nullptr, *len = nullptr, *col = nullptr;
+    short *col16 = nullptr;   // instead of col: column minus row, when every entry fits 16 bits
     void *val = nullptr;
     int G = 0;           // lanes per row chosen by the autotuner (0: size heuristic)
 };
@@ -233,6 +234,7 @@ struct Hier {
     float *val32 = nullptr;                       // CSR level 0 values in FP32
     int *iactive = nullptr, *icount = nullptr;    // [dir]: inner flag, cycles this step
     int *iany = nullptr;                          // 1 while a matrix of the batch still cycles
+    unsigned *iticket = nullptr;                  // CTA ticket of the norm kernels (0 between launches)
     double *ithr = nullptr, *inorm = nullptr;     // [dir]
     double rho_est = 0.0;                         // contraction of the inner cycles (0: none yet)
     cudaGraphExec_t gcyc[INNER_GRAPHS] = {};      // 2^g inner cycles

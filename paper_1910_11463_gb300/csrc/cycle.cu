@@ -324,70 +324,88 @@ __global__ void __launch_bounds__(BS) k_res32_csr(const int *row0, const int *nr
 }
 
 
-// outer norm of a step: ||r||, active (||r|| > tol ||b||), and the step's inner flag
-// and threshold; *any = 1 if a matrix takes part in the step.  One CTA,
-// a warp per matrix in turn, fixed reduction order.
-__global__ void k_norm_outer(int ndir, const double *partials, int maxblk, double *out, const double *bnorm,
-                             double tol, int *active, int *iactive, double *ithr, int *any) {
-    pdl_begin();
-    __shared__ int sany;
-    if (threadIdx.x == 0) sany = 0;
+// Step norms: one CTA per matrix.  Thread t sums the matrix's partials t, t +
+// NORM_BS, ... in order, then a fixed tree (deterministic); every CTA then takes a
+// ticket, and the last one sets *any from the flags of all matrices.
+constexpr int NORM_BS = 256;
+
+__device__ __forceinline__ double cta_sum_partials(const double *p, int cnt) {
+    __shared__ double sh[NORM_BS];
+    double s = 0.0;
+    for (int k = threadIdx.x; k < cnt; k += NORM_BS) s += p[k];
+    sh[threadIdx.x] = s;
     __syncthreads();
-    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int m = threadIdx.x >> 5; m < ndir; m += nw) {
-        if (!active[m]) {   // converged earlier: its partials were not written
-            if (lane == 0) iactive[m] = 0;
-            continue;
-        }
-        double sum = 0.0;
-        for (int k = lane; k < maxblk; k += 32) sum += partials[(long long)m * maxblk + k];
-        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-        if (lane == 0) {
-            const double nr = sqrt(sum);
+    for (int h = NORM_BS / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ void any_from_last_cta(int ndir, const int *flags, int *any, unsigned *ticket) {
+    __shared__ bool last;
+    __threadfence();   // this CTA's flag before its ticket
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == (unsigned)ndir - 1u;
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        int a = 0;
+        for (int d = 0; d < ndir; ++d) a |= ((volatile const int *)flags)[d];
+        *any = a;
+        *ticket = 0u;
+    }
+}
+
+// outer norm of a step: ||r||, active (||r|| > tol ||b||), and the step's inner flag
+// and threshold; *any = 1 if a matrix takes part in the step
+__global__ void __launch_bounds__(NORM_BS) k_norm_outer(int ndir, const double *partials, int maxblk, double *out,
+                                                        const double *bnorm, double tol, int *active, int *iactive,
+                                                        double *ithr, int *any, unsigned *ticket) {
+    pdl_begin();
+    const int m = blockIdx.x;
+    const int was = active[m];   // converged earlier: its partials were not written
+    if (was) {
+        const double nr = sqrt(cta_sum_partials(partials + (long long)m * maxblk, maxblk));
+        if (threadIdx.x == 0) {
             out[m] = nr;
             const int a = nr > tol * bnorm[m] ? 1 : 0;
             active[m] = a;
             iactive[m] = a;
             ithr[m] = fmax(INNER_TOL_FRAC * tol * bnorm[m], INNER_ETA * nr);
-            if (a) atomicOr(&sany, 1);
         }
+    } else if (threadIdx.x == 0) {
+        iactive[m] = 0;
     }
-    __syncthreads();
-    if (threadIdx.x == 0) *any = sany;
+    any_from_last_cta(ndir, iactive, any, ticket);
 }
 
 // inner norm after a cycle: counts the cycle (icount accumulates over a solve) and
 // clears the inner flag once the FP32 residual reaches the step's threshold; *any =
 // 1 while a matrix still cycles
-__global__ void k_norm_inner(int ndir, const double *partials, int maxblk, double *out, const double *ithr,
-                             int *iactive, int *icount, int *any) {
+__global__ void __launch_bounds__(NORM_BS) k_norm_inner(int ndir, const double *partials, int maxblk, double *out,
+                                                        const double *ithr, int *iactive, int *icount, int *any,
+                                                        unsigned *ticket) {
     pdl_begin();
-    __shared__ int sany;
-    if (threadIdx.x == 0) sany = 0;
-    __syncthreads();
-    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int m = threadIdx.x >> 5; m < ndir; m += nw) {
-        if (!iactive[m]) continue;
-        double sum = 0.0;
-        for (int k = lane; k < maxblk; k += 32) sum += partials[(long long)m * maxblk + k];
-        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-        if (lane == 0) {
-            const double nr = sqrt(sum);
+    const int m = blockIdx.x;
+    if (iactive[m]) {
+        const double nr = sqrt(cta_sum_partials(partials + (long long)m * maxblk, maxblk));
+        if (threadIdx.x == 0) {
             out[m] = nr;
             icount[m] += 1;
-            const int a = nr > ithr[m] ? 1 : 0;
-            iactive[m] = a;
-            if (a) atomicOr(&sany, 1);
+            iactive[m] = nr > ithr[m] ? 1 : 0;
         }
     }
-    __syncthreads();
-    if (threadIdx.x == 0) *any = sany;
+    any_from_last_cta(ndir, iactive, any, ticket);
 }
 
 // end of a step: x += d on the rows of the matrices that took part (d cleared);
 // the iterate is FP64 or, in double-float mode, a float pair
-__global__ void k_fold_delta(const int *row0, const int *nrow, float *d, double *x64, float2 *xdd,
-                             const int *active) {
+// (every load is issued before the stores: a load behind a store to a pointer that
+// may alias it waits for that store to complete)
+__global__ void k_fold_delta(const int *row0, const int *nrow, float *__restrict__ d, double *__restrict__ x64,
+                             float2 *__restrict__ xdd, const int *active) {
     pdl_begin();
     const int m = blockIdx.y;
     if (!active[m]) return;
@@ -395,13 +413,15 @@ __global__ void k_fold_delta(const int *row0, const int *nrow, float *d, double 
     if (li >= nrow[m]) return;
     const long long i = (long long)row0[m] + li;
     const float v = d[i];
-    d[i] = 0.0f;
     if (xdd) {
         const float2 xo = xdd[i];
         const float2 s2 = two_sum(xo.x, v);
+        d[i] = 0.0f;
         xdd[i] = fast_two_sum(s2.x, __fadd_rn(xo.y, s2.y));
     } else {
-        x64[i] += (double)v;
+        const double xo = x64[i];
+        d[i] = 0.0f;
+        x64[i] = xo + (double)v;
     }
 }
 
@@ -429,15 +449,20 @@ __global__ void k_norm_final(int ndir, const double *partials, int maxblk, doubl
     }
 }
 
+// F32: squares of the values cast to FP32, summed in FP32 inside each warp (a norm
+// for a stopping test, without the narrow FP64 pipe); else FP64 throughout
+template <bool F32>
 __global__ void k_sumsq_rows(const int *row0, const int *nrow, const double *v, double *partials, int maxblk) {
     int m = blockIdx.y;
     int li = blockIdx.x * blockDim.x + threadIdx.x;
     double s2 = 0.0;
+    float s2f = 0.0f;
     if (li < nrow[m]) {
         double a = v[row0[m] + li];
-        s2 = a * a;
+        if (F32) s2f = (float)a * (float)a;
+        else s2 = a * a;
     }
-    double tot = block_sum(s2);
+    double tot = F32 ? block_sum_f(s2f) : block_sum(s2);
     if (threadIdx.x == 0) partials[(long long)m * maxblk + blockIdx.x] = tot;
 }
 
@@ -471,12 +496,36 @@ __device__ __forceinline__ T sell_dot(int base, int len, int g, const int *col, 
     return acc;
 }
 
+// the same with 16-bit column offsets from the row r (col = r + offset)
+template <class T, int G>
+__device__ __forceinline__ T sell_dot16(int base, int len, int g, int r, const short *col16, const T *val,
+                                        const T *in) {
+    T acc = T(0);
+    for (int j0 = g; j0 < len; j0 += SELL_U * G) {
+        int c[SELL_U];
+        T v[SELL_U], x[SELL_U];
+#pragma unroll
+        for (int u = 0; u < SELL_U; ++u) {
+            const bool ok = j0 + u * G < len;
+            c[u] = ok ? r + (int)__ldcs(col16 + base + 32 * (j0 + u * G)) : 0;
+            v[u] = ok ? __ldcs(val + base + 32 * (j0 + u * G)) : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < SELL_U; ++u) x[u] = j0 + u * G < len ? in[c[u]] : T(0);
+#pragma unroll
+        for (int u = 0; u < SELL_U; ++u)
+            if (j0 + u * G < len) acc += v[u] * x[u];
+    }
+    return acc;
+}
+
 enum SellMode : int { SM_F = 0, SM_C = 1, SM_C_FINAL = 2, SM_RESTRICT = 3 };
 
 template <class T>
 struct SellJob {
     int npos;
     const int *ptr, *row, *len, *col;
+    const short *col16;   // the relaxation stores' row-relative columns (col is then null)
     const T *val;
     const T *in;          // vector the rows multiply
     const T *dinv, *b;    // sweeps
@@ -517,7 +566,8 @@ __global__ void __launch_bounds__(BS) k_sell(SellJob<T> j) {
             bi = j.b[r];
         }
     }
-    T acc = sell_dot<T, G>(base, len, g, j.col, j.val, j.in);
+    T acc = (MODE != SM_RESTRICT && j.col16) ? sell_dot16<T, G>(base, len, g, r, j.col16, j.val, j.in)
+                                             : sell_dot<T, G>(base, len, g, j.col, j.val, j.in);
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, G);
     if (!ok || g != 0) return;
@@ -530,9 +580,10 @@ __global__ void __launch_bounds__(BS) k_sell(SellJob<T> j) {
         if (j.d32) j.d32[r] += (float)v;
         else j.x64[r] += (double)v;
     } else {
-        j.out[r] = v;
+        // the fold's load before the store to out
         if (MODE == SM_F && j.d32) j.d32[r] += (float)v;
         else if (MODE == SM_F && j.x64) j.x64[r] += (double)v;
+        j.out[r] = v;
     }
 }
 
@@ -703,7 +754,7 @@ __global__ void __launch_bounds__(BS) k_relax0_split(int n, int N, const int8_t 
     const int gi = srow[k0 + k];
     const int m = gi / N;
     const int r = gi - m * N;
-    const int e = r >> 3, a = r & 7;
+    const int e = r >> 3;   // the row's node is implicit in its face rows of v0
     const int ix = e % n, t = e / n, iy = t % n, iz = t / n;
     const int idx[3] = {ix, iy, iz};
     const int stride[3] = {1, n, n * n};
@@ -729,8 +780,8 @@ __global__ void __launch_bounds__(BS) k_relax0_split(int n, int N, const int8_t 
     if (!act) return;
     const float v = xin + (bi - (acc + xin));
     if (!FINAL) {
+        if (fold) x_add(gi, v, d32, xdd, x64);   // its load before the store to out
         out[gi] = v;
-        if (fold) x_add(gi, v, d32, xdd, x64);
     } else {
         x_add(gi, v, d32, xdd, x64);
     }
@@ -790,6 +841,7 @@ void launch_sell_g(const Sell &S, SellJob<T> j, int G, cudaStream_t s) {
     j.row = S.row;
     j.len = S.len;
     j.col = S.col;
+    j.col16 = S.col16;
     j.val = (const T *)S.val;
     switch (G) {
         case 1: launch_pdl(k_sell<T, MODE, 1>, blocks_for(S.npos, BS), BS, s, j); break;
@@ -1102,8 +1154,10 @@ void level0_bytes(Hier &h) {
             unsigned long long c[4];
             PR_CUDA(cudaMemcpyAsync(c, cnt, sizeof c, cudaMemcpyDeviceToHost, s));
             PR_CUDA(cudaStreamSynchronize(s));
-            double fpass = (double)c[0] * (8 + 4 * sT) + (double)c[2] * (4 + sT);
-            double cpass = (double)c[1] * (8 + 4 * sT) + (double)c[3] * (4 + sT);
+            // column index: 4 bytes, or 2 in a store with 16-bit offsets
+            const double cbF = L.sF.col16 ? 2.0 : 4.0, cbC = L.sC.col16 ? 2.0 : 4.0;
+            double fpass = (double)c[0] * (8 + 4 * sT) + (double)c[2] * (cbF + sT);
+            double cpass = (double)c[1] * (8 + 4 * sT) + (double)c[3] * (cbC + sT);
             h.bytes_relaxc += h.prm.f_sweeps * fpass + cpass;
         }
         dfree(cnt, s);
@@ -1232,7 +1286,8 @@ void norms0(Hier &h, const double *v, double *out) {
     cudaStream_t s = h.stream;
     PR_CUDA(cudaMemsetAsync(h.partials, 0, sizeof(double) * h.maxblk * h.ndir, s));
     dim3 grid(h.maxblk, h.ndir);
-    k_sumsq_rows<<<grid, BS, 0, s>>>(h.d_row00, h.d_n0, v, h.partials, h.maxblk);
+    if (h.prm.precision >= 1) k_sumsq_rows<true><<<grid, BS, 0, s>>>(h.d_row00, h.d_n0, v, h.partials, h.maxblk);
+    else k_sumsq_rows<false><<<grid, BS, 0, s>>>(h.d_row00, h.d_n0, v, h.partials, h.maxblk);
     PR_LAUNCH();
     k_norm_final<<<blocks_for(32LL * h.ndir, 128), 128, 0, s>>>(h.ndir, h.partials, h.maxblk, out, nullptr, 0.0,
                                                                  nullptr);
@@ -1377,6 +1432,8 @@ void inner_enable(Hier &h) {
     h.icount = dmalloc<int>(h.ndir, s);
     h.iany = dmalloc<int>(1, s);
     PR_CUDA(cudaMemsetAsync(h.iany, 0, sizeof(int), s));
+    h.iticket = dmalloc<unsigned>(1, s);
+    PR_CUDA(cudaMemsetAsync(h.iticket, 0, sizeof(unsigned), s));
     h.ithr = dmalloc<double>(h.ndir, s);
     h.inorm = dmalloc<double>(h.ndir, s);
     PR_CUDA(cudaMemsetAsync(h.iactive, 0, sizeof(int) * h.ndir, s));
@@ -1396,8 +1453,8 @@ void residual_outer(Hier &h, const double *b, const double *x, double tol) {
     if (h.prof) rec_event(h.ev[0], s);
     residual0_launch(h, b, x, h.active, h.r32);
     if (h.prof) rec_event(h.ev[1], s);
-    launch_pdl(k_norm_outer, 1, 32 * std::min(h.ndir, 32), s, h.ndir, (const double *)h.partials, h.maxblk, h.rnorm,
-               (const double *)h.bnorm, tol, h.active, h.iactive, h.ithr, h.iany);
+    launch_pdl(k_norm_outer, h.ndir, NORM_BS, s, h.ndir, (const double *)h.partials, h.maxblk, h.rnorm,
+               (const double *)h.bnorm, tol, h.active, h.iactive, h.ithr, h.iany, h.iticket);
     PR_LAUNCH();
 }
 
@@ -1420,8 +1477,8 @@ void inner_cycle(Hier &h, ProfSlot *ps) {
     }
     PR_LAUNCH();
     if (prof) rec_event(ps->res32[1], s);
-    launch_pdl(k_norm_inner, 1, 32 * std::min(h.ndir, 32), s, h.ndir, (const double *)h.partials, h.maxblk, h.inorm,
-               (const double *)h.ithr, h.iactive, h.icount, h.iany);
+    launch_pdl(k_norm_inner, h.ndir, NORM_BS, s, h.ndir, (const double *)h.partials, h.maxblk, h.inorm,
+               (const double *)h.ithr, h.iactive, h.icount, h.iany, h.iticket);
     PR_LAUNCH();
 }
 

@@ -256,11 +256,6 @@ __device__ __forceinline__ int lair_class(int np) {
 
 
 
-__global__ void k_max_int(const int *v, int n, int *out) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) atomicMax(out, v[i]);
-}
-
 // Warp per C row.  Shared memory per warp: M (nmax^2 doubles), y (nmax
 // doubles), pattern (nmax ints), pivots (nmax ints).
 __device__ __forceinline__ int pat_find(const int *pat, int np, int k) {
@@ -729,18 +724,42 @@ __global__ void k_rap(int nrows_work, const int *worklist, const int *cpts, cons
         int nr = has ? z1 - z0 + 1 : 0;   // R row entries, identity included
         int nrmax = nr;
         for (int o = 16; o > 0; o >>= 1) nrmax = max(nrmax, __shfl_xor_sync(FULL, nrmax, o));
+        // The R row in ascending column order (the identity at column i); each step's
+        // chain of loads (its column, then its AP row, then the AP row's first entry
+        // of this lane) is issued one step ahead, while the previous step's entries
+        // go into the table.  The additions into each slot keep the R-row order.
         bool placed = false;
         int t = z0;
+        int zc = (t < z1) ? zcol[t] : 0x7fffffff;   // the next Z column
+        auto advance = [&](int &k, double &r) {
+            if (!placed && zc > i) { k = i; r = 1.0; placed = true; }
+            else { k = zc; r = zval[t]; ++t; zc = (t < z1) ? zcol[t] : 0x7fffffff; }
+        };
+        int k_c = 0, a_c = 0, l_c = 0, c_c = 0;
+        double r_c = 0.0, v_c = 0.0;
+        if (nr > 0) {
+            advance(k_c, r_c);
+            a_c = aprow[k_c];
+            l_c = aplen[k_c];
+            if (g < l_c) { c_c = apcol[a_c + g]; v_c = apval[a_c + g]; }
+        }
         for (int step = 0; step < nrmax; ++step) {
+            int k_n = 0, a_n = 0, l_n = 0, c_n = 0;
+            double r_n = 0.0, v_n = 0.0;
+            if (step + 1 < nr) {
+                advance(k_n, r_n);
+                a_n = aprow[k_n];
+                l_n = aplen[k_n];
+                if (g < l_n) { c_n = apcol[a_n + g]; v_n = apval[a_n + g]; }
+            }
             if (step < nr) {
-                int k;
-                double r;
-                if (!placed && (t == z1 || zcol[t] > i)) { k = i; r = 1.0; placed = true; }
-                else { k = zcol[t]; r = zval[t]; ++t; }
-                int a0 = aprow[k], al = aplen[k];
+                const double r = r_c;
+                const int a0 = a_c, al = l_c;
                 for (int qq = g; qq < al; qq += G) {
-                    int c = apcol[a0 + qq];
-                    double v = apval[a0 + qq];
+                    int c;
+                    double v;
+                    if (qq == g) { c = c_c; v = v_c; }
+                    else { c = apcol[a0 + qq]; v = apval[a0 + qq]; }
                     unsigned hs = hslot(c, mask);
                     int probes = 0;
                     bool ok = false;
@@ -755,6 +774,7 @@ __global__ void k_rap(int nrows_work, const int *worklist, const int *cpts, cons
                 }
             }
             __syncwarp();
+            k_c = k_n; r_c = r_n; a_c = a_n; l_c = l_n; c_c = c_n; v_c = v_n;
         }
         // compact to the scratch output (unsorted), then rank-sort back into the table
         int base = has ? uptr[ic] : 0;
@@ -808,6 +828,11 @@ __global__ void k_rap(int nrows_work, const int *worklist, const int *cpts, cons
     }
 }
 
+__global__ void k_gather_int(int n, const int *src, const int *idx, int *out) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) out[k] = src[idx[k]];
+}
+
 __global__ void k_gather_rowdir(int nc, const int *cpts, const int *rowdir, int *rowdir_c) {
     int ic = blockIdx.x * blockDim.x + threadIdx.x;
     if (ic < nc) rowdir_c[ic] = rowdir[cpts[ic]];
@@ -818,11 +843,6 @@ __global__ void k_rowlen_dir(int n, const int *rowptr, const int *rowdir, unsign
     bool valid = i < n;
     int d = valid ? rowdir[i] : 0;
     add_by_dir<unsigned long long>(nnzdir, d, valid ? (unsigned long long)(rowptr[i + 1] - rowptr[i]) : 0ULL, valid);
-}
-
-__global__ void k_cast(long long n, const double *a, float *b) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) b[i] = (float)a[i];
 }
 
 __global__ void k_fill_int8(int n, int8_t *a, int8_t v) {
@@ -847,21 +867,6 @@ __global__ void k_overflow_caps(int nover, const int *list, const int *U, long l
     capw[w] = c;
 }
 
-__global__ void k_overflow_list(int nc, const int *cnt, int *flag) {
-    int ic = blockIdx.x * blockDim.x + threadIdx.x;
-    if (ic < nc) flag[ic] = cnt[ic] < 0 ? 1 : 0;
-}
-
-__global__ void k_overflow_rows(int nc, const int *flag, const int *pos, const int *U, int *list, long long *capw) {
-    int ic = blockIdx.x * blockDim.x + threadIdx.x;
-    if (ic >= nc || !flag[ic]) return;
-    int w = pos[ic];
-    list[w] = ic;
-    long long c = 64;
-    while (c < 2LL * U[ic]) c <<= 1;
-    capw[w] = c;
-}
-
 __global__ void k_big_rows(int nbig, const int *list, const int *npat, long long *goff) {
     int w = blockIdx.x * blockDim.x + threadIdx.x;
     if (w >= nbig) return;
@@ -875,16 +880,6 @@ __global__ void k_prefix_ll(int n, long long *v) {
     long long s = 0;
     for (int i = 0; i < n; ++i) { long long t = v[i]; v[i] = s; s += t; }
     v[n] = s;
-}
-
-__global__ void k_flag_eq(int n, const int8_t *cls, int c, int *flag) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) flag[i] = cls[i] == c ? 1 : 0;
-}
-
-__global__ void k_scatter_eq(int n, const int8_t *cls, int c, const int *pos, int start, int *list) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n && cls[i] == c) list[start + pos[i]] = i;
 }
 
 __global__ void k_lair_classes(int nc, const int *npat, int8_t *cls) {
@@ -904,24 +899,76 @@ void d2h(T *h, const T *d, size_t count, cudaStream_t s) {
 }
 
 // Rows 0..n-1 grouped by class (ascending row order inside each class):
-// list[start[c] .. start[c] + count[c]).  Deterministic.
-void partition_by_class(const int8_t *cls, int n, int nclass, int *list, int *start, int *count, cudaStream_t s) {
-    const int BS = 256;
-    int *flag = dmalloc<int>(n, s), *pos = dmalloc<int>(n + 1, s);
-    int acc = 0;
-    for (int c = 0; c < nclass; ++c) {
-        k_flag_eq<<<blocks_for(n, BS), BS, 0, s>>>(n, cls, c, flag);
-        PR_LAUNCH();
-        count[c] = (int)scan_exclusive(flag, pos, n, s);
-        start[c] = acc;
-        if (count[c]) {
-            k_scatter_eq<<<blocks_for(n, BS), BS, 0, s>>>(n, cls, c, pos, acc, list);
-            PR_LAUNCH();
-        }
-        acc += count[c];
+// list[start[c] .. start[c] + count[c]).  A counting sort, deterministic: per
+// block of PART_BS rows the rows of each class (counted by warp ballots), an
+// exclusive scan over (class, block), and a scatter at each row's rank among the
+// rows of its class before it.  One host read (the class counts).
+constexpr int PART_BS = 256;
+constexpr int PART_MAXC = 8;
+
+__global__ void __launch_bounds__(PART_BS) k_class_hist(int n, const int8_t *cls, int nclass, int nblk, int *hist) {
+    __shared__ int wc[PART_BS / 32][PART_MAXC];
+    const int i = blockIdx.x * PART_BS + threadIdx.x;
+    const int c = (i < n && cls[i] >= 0 && cls[i] < nclass) ? cls[i] : -1;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int k = 0; k < nclass; ++k) {
+        const unsigned m = __ballot_sync(0xffffffffu, c == k);
+        if (lane == 0) wc[w][k] = __popc(m);
     }
-    dfree(flag, s);
-    dfree(pos, s);
+    __syncthreads();
+    if ((int)threadIdx.x < nclass) {
+        int t = 0;
+        for (int ww = 0; ww < PART_BS / 32; ++ww) t += wc[ww][threadIdx.x];
+        hist[threadIdx.x * nblk + blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(PART_BS) k_class_scatter(int n, const int8_t *cls, int nclass, int nblk,
+                                                           const int *off, int *list) {
+    __shared__ int wc[PART_BS / 32][PART_MAXC];
+    const int i = blockIdx.x * PART_BS + threadIdx.x;
+    const int c = (i < n && cls[i] >= 0 && cls[i] < nclass) ? cls[i] : -1;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int rank_in_warp = 0;
+    for (int k = 0; k < nclass; ++k) {
+        const unsigned m = __ballot_sync(0xffffffffu, c == k);
+        if (lane == 0) wc[w][k] = __popc(m);
+        if (c == k) rank_in_warp = __popc(m & ((1u << lane) - 1u));
+    }
+    __syncthreads();
+    if (c < 0) return;
+    int before = 0;
+    for (int ww = 0; ww < w; ++ww) before += wc[ww][c];
+    list[off[c * nblk + blockIdx.x] + before + rank_in_warp] = i;
+}
+
+__global__ void k_class_counts(int nclass, int nblk, const int *off, int *out) {
+    const int c = threadIdx.x;
+    if (c <= nclass) out[c] = off[c * nblk];   // class starts, and the total
+}
+
+void partition_by_class(const int8_t *cls, int n, int nclass, int *list, int *start, int *count, cudaStream_t s) {
+    PR_REQUIRE(nclass >= 1 && nclass <= PART_MAXC, PAIR_ERR_DEVICE, "partition_by_class: too many classes");
+    if (n <= 0) {
+        for (int c = 0; c < nclass; ++c) { start[c] = 0; count[c] = 0; }
+        return;
+    }
+    const int nblk = (int)blocks_for(n, PART_BS);
+    const int nh = nclass * nblk;
+    int *hist = dmalloc<int>(nh, s), *off = dmalloc<int>(nh + 1, s), *cs = dmalloc<int>(nclass + 1, s);
+    k_class_hist<<<nblk, PART_BS, 0, s>>>(n, cls, nclass, nblk, hist);
+    PR_LAUNCH();
+    scan_exclusive(hist, off, nh, s, false);
+    k_class_scatter<<<nblk, PART_BS, 0, s>>>(n, cls, nclass, nblk, off, list);
+    PR_LAUNCH();
+    k_class_counts<<<1, 32, 0, s>>>(nclass, nblk, off, cs);
+    PR_LAUNCH();
+    int h[PART_MAXC + 1];
+    d2h(h, cs, nclass + 1, s);
+    for (int c = 0; c < nclass; ++c) { start[c] = h[c]; count[c] = h[c + 1] - h[c]; }
+    dfree(hist, s);
+    dfree(off, s);
+    dfree(cs, s);
 }
 
 __global__ void k_split_len(int n, const int *srow, const int *rowptr, int *len) {
@@ -992,6 +1039,51 @@ __global__ void k_sell_fill(int npos, const int *prow, const int *plen, const in
     }
 }
 
+// 16-bit column offsets: an entry's column minus its row, when every stored entry
+// of a store fits (the relaxation stores of the coarse levels: their stencils stay
+// within a few mesh planes of the row); the padding slots are never read
+__global__ void k_sell_off_check(int npos, const int *prow, const int *plen, const int *sptr, const int *scol,
+                                 int *bad) {
+    const int pos = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pos >= npos) return;
+    const int r = prow[pos];
+    if (r < 0) return;
+    const int len = plen[pos], base = sptr[pos >> 5] + (pos & 31);
+    for (int j = 0; j < len; ++j) {
+        const int off = scol[base + 32 * j] - r;
+        if (off < -32768 || off > 32767) { atomicOr(bad, 1); return; }
+    }
+}
+
+__global__ void k_sell_to16(int npos, const int *prow, const int *plen, const int *sptr, const int *scol,
+                            short *col16) {
+    const int pos = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pos >= npos) return;
+    const int r = prow[pos];
+    if (r < 0) return;
+    const int len = plen[pos], base = sptr[pos >> 5] + (pos & 31);
+    for (int j = 0; j < len; ++j) col16[base + 32 * j] = (short)(scol[base + 32 * j] - r);
+}
+
+void sell_compress_cols(Hier &h, Sell &S) {
+    if (S.nrows <= 0 || !S.col) return;
+    cudaStream_t s = h.stream;
+    const int BS = 256;
+    int *bad = dmalloc<int>(1, s);
+    PR_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+    k_sell_off_check<<<blocks_for(S.npos, BS), BS, 0, s>>>(S.npos, S.row, S.len, S.ptr, S.col, bad);
+    PR_LAUNCH();
+    int hb = 0;
+    d2h(&hb, bad, 1, s);
+    dfree(bad, s);
+    if (hb) return;
+    S.col16 = dmalloc<short>(std::max<long long>(S.nnz, 1), s);
+    k_sell_to16<<<blocks_for(S.npos, BS), BS, 0, s>>>(S.npos, S.row, S.len, S.ptr, S.col, S.col16);
+    PR_LAUNCH();
+    dfree(S.col, s);
+    S.col = nullptr;
+}
+
 // SELL copy of nr rows of a CSR matrix (list rows, or rows 0..nr-1), values in the
 // V-cycle's precision
 void build_sell(Hier &h, Sell &S, const int *rows, int nr, const int *rowptr, const int *col, const double *val) {
@@ -1043,6 +1135,8 @@ void build_split(Hier &h, Level &L, bool with_fc) {
     if (with_fc) {
         build_sell(h, L.sF, L.srow, L.nF, L.rowptr, L.col, L.val);
         build_sell(h, L.sC, L.srow + L.nF, L.nC, L.rowptr, L.col, L.val);
+        sell_compress_cols(h, L.sF);
+        sell_compress_cols(h, L.sC);
     }
     if (nx > 0) {
         int *len = dmalloc<int>(nx, s);
@@ -1087,8 +1181,8 @@ void free_level(Level &L, cudaStream_t s) {
     void *ptrs[] = {L.rowptr, L.col, L.val, L.dinv, L.dinv32, L.cf, L.pmap, L.rowdir, L.cpts,
                     L.zrowptr, L.zcol, L.zval, L.d_row0, L.d_cseg_row0, L.d_cseg_n,
                     L.srow, L.sptr, L.scol, L.sval, L.d_cseg_s0,
-                    L.sF.ptr, L.sF.row, L.sF.len, L.sF.col, L.sF.val, L.sC.ptr, L.sC.row, L.sC.len, L.sC.col,
-                    L.sC.val, L.sZ.ptr, L.sZ.row, L.sZ.len, L.sZ.col, L.sZ.val,
+                    L.sF.ptr, L.sF.row, L.sF.len, L.sF.col, L.sF.col16, L.sF.val, L.sC.ptr, L.sC.row, L.sC.len,
+                    L.sC.col, L.sC.col16, L.sC.val, L.sZ.ptr, L.sZ.row, L.sZ.len, L.sZ.col, L.sZ.val,
                     L.vb, L.vx, L.vxn, L.vy};
     for (void *p : ptrs) dfree(p, s);
     L = Level();
@@ -1428,19 +1522,28 @@ void build_hierarchy(Hier &h) {
         C.rowdir = dmalloc<int>(nc, s);
         k_gather_rowdir<<<blocks_for(nc, BS), BS, 0, s>>>(nc, L.cpts, L.rowdir, C.rowdir);
         PR_LAUNCH();
-        // nnz of Z per matrix (host, from the coarse row ranges)
+        // nnz of Z per matrix (host, from the Z row pointer at the coarse row ranges)
         {
-            std::vector<int> zrh(nc + 1);
-            d2h(zrh.data(), L.zrowptr, nc + 1, s);
             C.row0.assign(ND, 0);
             C.nrows.assign(ND, 0);
+            std::vector<int> bidx(ND + 1);
             int r = 0;
             for (int d = 0; d < ND; ++d) {
                 C.row0[d] = r;
                 C.nrows[d] = cont[d] ? L.ncdir[d] : 0;
-                L.nnzZdir[d] = zrh[r + C.nrows[d]] - zrh[r];
+                bidx[d] = r;
                 r += C.nrows[d];
             }
+            bidx[ND] = r;
+            int *didx = dmalloc<int>(ND + 1, s), *dz = dmalloc<int>(ND + 1, s);
+            PR_CUDA(cudaMemcpyAsync(didx, bidx.data(), sizeof(int) * (ND + 1), cudaMemcpyHostToDevice, s));
+            k_gather_int<<<blocks_for(ND + 1, BS), BS, 0, s>>>(ND + 1, L.zrowptr, didx, dz);
+            PR_LAUNCH();
+            std::vector<int> zb(ND + 1);
+            d2h(zb.data(), dz, ND + 1, s);   // also orders the host copy of bidx before it is freed
+            for (int d = 0; d < ND; ++d) L.nnzZdir[d] = zb[d + 1] - zb[d];
+            dfree(didx, s);
+            dfree(dz, s);
         }
         C.d_row0 = dmalloc<int>(ND, s);
         PR_CUDA(cudaMemcpyAsync(C.d_row0, C.row0.data(), sizeof(int) * ND, cudaMemcpyHostToDevice, s));

@@ -22,27 +22,44 @@ namespace {
 
 constexpr int BS = 256;
 
+// isotropic source per DOF: src = (sigma_s phi + q) / (4 pi)
 template <int NB>
-__global__ void k_rhs(long long E, int ndir, const double *W, const double *Gin, double g, const double *sigma_s,
-                      const double *q, const double *phi, const double *qa, double *b) {
+__global__ void k_src(long long N, const double *sigma_s, const double *q, const double *phi, double *src) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double inv4pi = 1.0 / (4.0 * 3.14159265358979323846);
+    const long long e = i / NB;
+    src[i] = (sigma_s[e] * phi[i] + q[e]) * inv4pi;
+}
+
+// b = W src (+ W q_ang of the direction) (+ g Gin): thread per row of a direction,
+// the row of W in 16-byte loads
+template <int NB>
+__global__ void k_rhs(long long E, int ndir, const double *W, const double *Gin, double g, const double *src,
+                      const double *qa, double *b) {
     long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (tid >= NB * E * ndir) return;
     long long m = tid / (NB * E);
     long long r = tid % (NB * E);
     long long e = r / NB;
     int a = (int)(r % NB);
-    const double inv4pi = 1.0 / (4.0 * 3.14159265358979323846);
-    double ss = sigma_s[e], qq = q[e];
-    const double *w = W + ((m * E + e) * NB + a) * NB;
-    const double *ph = phi + NB * e;
+    const double2 *w2 = reinterpret_cast<const double2 *>(W + ((m * E + e) * NB + a) * NB);
+    double w[NB];
+#pragma unroll
+    for (int c = 0; c < NB / 2; ++c) {
+        const double2 t = __ldcs(w2 + c);
+        w[2 * c] = t.x;
+        w[2 * c + 1] = t.y;
+    }
+    const double *se = src + NB * e;
     double acc = 0.0;
     if (qa) {   // angular source of this direction, added to the isotropic one per node
         const double *qm = qa + (m * E + e) * NB;
 #pragma unroll
-        for (int c = 0; c < NB; ++c) acc += w[c] * ((ss * ph[c] + qq) * inv4pi + qm[c]);
+        for (int c = 0; c < NB; ++c) acc += w[c] * (se[c] + qm[c]);
     } else {
 #pragma unroll
-        for (int c = 0; c < NB; ++c) acc += w[c] * ((ss * ph[c] + qq) * inv4pi);
+        for (int c = 0; c < NB; ++c) acc += w[c] * se[c];
     }
     if (Gin) acc += g * Gin[tid];
     b[tid] = acc;
@@ -80,12 +97,27 @@ __global__ void k_diff_partials(long long N, const double *a, const double *b, d
     }
 }
 
+// one block of DIFF_BS threads: thread t sums partials t, t + DIFF_BS, ... in order,
+// then a fixed tree (deterministic)
+constexpr int DIFF_BS = 256;
 __global__ void k_diff_final(int nb, const double *part, double *out) {
-    if (blockIdx.x || threadIdx.x) return;
+    __shared__ double sh[2][DIFF_BS];
     double s0 = 0, s1 = 0;
-    for (int k = 0; k < nb; ++k) { s0 += part[2 * k]; s1 += part[2 * k + 1]; }
-    out[0] = sqrt(s0);
-    out[1] = sqrt(s1);
+    for (int k = threadIdx.x; k < nb; k += DIFF_BS) { s0 += part[2 * k]; s1 += part[2 * k + 1]; }
+    sh[0][threadIdx.x] = s0;
+    sh[1][threadIdx.x] = s1;
+    __syncthreads();
+    for (int h = DIFF_BS / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + h];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = sqrt(sh[0][0]);
+        out[1] = sqrt(sh[1][0]);
+    }
 }
 
 __global__ void k_fill_dir(int *rowdir, long long N, int ndir) {
@@ -548,7 +580,7 @@ Hier::~Hier() {
     if (stream) {
         for (auto &L : lev) free_level(L, stream);
         void *ptrs[] = {bsr64, bsr32, dsign, partials, rnorm, bnorm, rnorm0, active, d_err, d_n0, d_row00,
-                        bsr_dd, b_dd, x_dd, v0, r32, d32, val32, iactive, icount, iany, ithr, inorm};
+                        bsr_dd, b_dd, x_dd, v0, r32, d32, val32, iactive, icount, iany, iticket, ithr, inorm};
         for (void *p : ptrs) dfree(p, stream);
         cudaStreamSynchronize(stream);
         cudaStreamDestroy(stream);
@@ -790,6 +822,9 @@ void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t,
     // the new flux, and one status slot for the reduction of a direction subset
     double *phinew = dmalloc<double>(N + 1, s);
     cl.bufs.push_back(phinew);
+    double *src = dmalloc<double>(N, s);   // isotropic source of the current iteration
+    cl.bufs.push_back(src);
+    bool src_ready = false;
     int nbk = (int)blocks_for(N, BS);
     double *part = dmalloc<double>(2 * (size_t)nbk, s);
     cl.bufs.push_back(part);
@@ -829,6 +864,7 @@ void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t,
         PR_CUDA(cudaMemsetAsync(phinew, 0, sizeof(double) * (N + 1), s));
         PR_CUDA(cudaStreamSynchronize(s));
         local_fail.clear();
+        src_ready = false;
         for (int bi = 0; bi < nb; ++bi) {
             DirBatch &Bt = batches[bi];
             if (!Bt.h) {
@@ -865,12 +901,18 @@ void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t,
             double *x = psi ? psi + (size_t)Bt.m0 * N : Bt.xown;
             const double *qa = sp.q_ang ? sp.q_ang + (size_t)Bt.m0 * N : nullptr;
             PR_CUDA(cudaEventRecord(e0, hs));
+            if (bi == 0 || !src_ready) {   // the source of this iteration, once for every batch
+                if (hex) k_src<8><<<blocks_for(N, BS), BS, 0, hs>>>(N, sigma_s, q, phi, src);
+                else k_src<4><<<blocks_for(N, BS), BS, 0, hs>>>(N, sigma_s, q, phi, src);
+                PR_LAUNCH();
+                src_ready = true;
+            }
             if (hex)
                 k_rhs<8><<<blocks_for((long long)Bt.nd * N, BS), BS, 0, hs>>>(E, Bt.nd, Bt.W, Bt.Gin, sp.g_inflow,
-                                                                           sigma_s, q, phi, qa, Bt.b);
+                                                                           src, qa, Bt.b);
             else
                 k_rhs<4><<<blocks_for((long long)Bt.nd * N, BS), BS, 0, hs>>>(E, Bt.nd, Bt.W, Bt.Gin, sp.g_inflow,
-                                                                           sigma_s, q, phi, qa, Bt.b);
+                                                                           src, qa, Bt.b);
             PR_LAUNCH();
             BatchSolve bs;
             if (sweep) {
@@ -922,7 +964,7 @@ void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t,
         }
         k_diff_partials<<<nbk, BS, 0, s>>>(N, phinew, phi, part);
         PR_LAUNCH();
-        k_diff_final<<<1, 1, 0, s>>>(nbk, part, dres);
+        k_diff_final<<<1, DIFF_BS, 0, s>>>(nbk, part, dres);
         PR_LAUNCH();
         double hr[2];
         PR_CUDA(cudaMemcpyAsync(hr, dres, sizeof hr, cudaMemcpyDeviceToHost, s));
@@ -1082,7 +1124,7 @@ void si_adjoint_run(const pair_mesh &mesh, const pair_quad &quad, const double *
         PR_LAUNCH();
         k_diff_partials<<<nbk, BS, 0, s>>>(N, pnew, phis, part);
         PR_LAUNCH();
-        k_diff_final<<<1, 1, 0, s>>>(nbk, part, dres);
+        k_diff_final<<<1, DIFF_BS, 0, s>>>(nbk, part, dres);
         PR_LAUNCH();
         double hr[2];
         PR_CUDA(cudaMemcpyAsync(hr, dres, sizeof hr, cudaMemcpyDeviceToHost, s));
