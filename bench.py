@@ -228,6 +228,27 @@ def cpu_oracle_sweep(prob):
             "sample": f"exact sweep of {nd} directions (assembly excluded), single-threaded"}
 
 
+def bench_config(args, world):
+    """The workload configuration both arms print (the reference arm's own step is
+    described in its cpu_baseline.sample)."""
+    fixed = args.si_fixed if args.si_fixed is not None else FIXED_SI.get(args.config, 0)
+    return {"workload": args.config + ": " + WORKLOADS[args.config],
+            "step": ("one complete SI solve from phi=0 (assembly + AIR setup + SI iterations to 1e-8, every "
+                     "direction solved from psi=0 to 1e-8 relative FP64 residual each iteration); value = "
+                     "DOF*dir*iterations/step time") if not fixed else
+                    (f"assembly + AIR setup + {fixed} SI iterations from phi=0 (every direction solved from "
+                     "psi=0 to 1e-8 relative FP64 residual each iteration); value = DOF*dir*iterations/step "
+                     "time (setup included); solve_only_value excludes the setup"),
+            "air": {"R": "nAIR degree 1" if args.nair else f"lAIR distance {args.distance}",
+                    "theta": args.theta, "eps_R": 0.01, "phi_R": args.phi_R, "phi_A": args.phi_A,
+                    "relax": "F-F-C Jacobi", "coarsening": "PMIS"},
+            "l2": "working set per step >> 129 MB L2 (no flush needed)",
+            "parallelism": (f"angular decomposition over {world} GPUs (directions split, scalar flux all-reduced "
+                            "every SI iteration)") if world > 1 else "1 GPU, all directions in one batch",
+            "precision": ("FP32 hierarchy/V-cycle, double-float refinement" if args.precision == 2 else
+                          "FP32 hierarchy/V-cycle, FP64 refinement" if args.precision else "FP64")}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -250,13 +271,13 @@ def run_reference(args):
     value = prob.N / t
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.config + ": " + WORKLOADS[args.config],
-                       "step": "one direction of the workload per step: oracle assembly + AIR setup (amortised over "
-                               f"{si_iters} SI iterations) + one 1e-8 solve"},
+            "scaling": "strong" if world > 1 else "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": bench_config(args, world),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{args.steps} timed directions (after {args.warmup} warm-up), "
-                                       "single-threaded C oracle"},
+                                       "single-threaded C oracle; a step = one direction of the workload: "
+                                       "oracle assembly + AIR setup (amortised over "
+                                       f"{si_iters} SI iterations) + one 1e-8 solve"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -345,6 +366,8 @@ def measure_workload(name, args, pair, I, torch, steps=2, warmup=1, fp64=False):
                      "eps_R": 0.01, "phi_A": args.phi_A, "phi_R": args.phi_R},
              "si_iterations": iters, "setup_ms": t_setup, "solve_ms": t_solve,
              "solve_only_value": N * M * iters / (t_solve * 1e-3) if t_solve > 0 else None,
+             "setup_phase_ms": dict(zip(("strength+pmis", "p+lair", "rap", "assembly+other"),
+                                        [sum(i["t_setup_phase_ms"][k] for i in infos) / steps for k in range(4)])),
              "batches": last["batches"], "rebuilt_every_iteration": bool(last["rebuilt"]),
              "vcycles_per_direction_per_iteration": last["vcycles"] / M / max(iters, 1),
              "outer_residuals_per_direction_per_iteration": last["outer_residuals"] / M / max(iters, 1),
@@ -588,25 +611,13 @@ def run_ours(args):
     last = infos[-1]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "strong" if world > 1 else "weak",
         "vs_baseline": None, "dtype": ("f32 V-cycle + f32-pair residual/iterate + f64 setup"
                                        if args.precision == 2 and not hasattr(prob, "tets")
                                        else "f32 V-cycle + f64 residual/setup" if args.precision else "f64"),
         "data": "synthetic",
-        "config": {"workload": args.config + ": " + WORKLOADS[args.config],
-                   "step": ("one complete SI solve from phi=0 (assembly + AIR setup + SI iterations to 1e-8, every "
-                            "direction solved from psi=0 to 1e-8 relative FP64 residual each iteration); value = "
-                            "DOF*dir*iterations/step time") if not fixed else
-                           (f"assembly + AIR setup + {fixed} SI iterations from phi=0 (every direction solved from "
-                            "psi=0 to 1e-8 relative FP64 residual each iteration); value = DOF*dir*iterations/step "
-                            "time (setup included); solve_only_value excludes the setup"),
-                   "air": {"R": "nAIR degree 1" if args.nair else f"lAIR distance {args.distance}",
-                           "theta": args.theta, "eps_R": 0.01, "phi_R": args.phi_R, "phi_A": args.phi_A,
-                           "relax": "F-F-C Jacobi", "coarsening": "PMIS"},
-                   "l2": "working set per step >> 129 MB L2 (no flush needed)",
-                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU, all directions in one batch",
-                   "precision": ("FP32 hierarchy/V-cycle, double-float refinement" if args.precision == 2 else
-                                 "FP32 hierarchy/V-cycle, FP64 refinement" if args.precision else "FP64")},
+        "config": bench_config(args, world),
         "si_iterations": iters, "setup_ms": t_setup, "solve_ms": t_solve,
         "solve_only_value": N * M * iters * world / (t_solve * 1e-3) if t_solve > 0 else None,
         "setup_phase_ms": {"strength+pmis": phases[0], "p+lair": phases[1], "rap": phases[2],
@@ -614,6 +625,9 @@ def run_ours(args):
         "rebuild_every_iteration": rebuild,
         "vcycles_per_direction_per_iteration": last["vcycles"] / M / max(iters, 1),
         "outer_residuals_per_direction_per_iteration": last["outer_residuals"] / M / max(iters, 1),
+        "coarse_relax_ms_per_cycle_by_level": [
+            sum(i["t_relaxc_level_ms"][k] for i in infos) / max(sum(i["n_relaxc"] for i in infos), 1)
+            for k in range(8)],
         "levels": last["levels_max"],
         "op_complexity": last["op_complexity"], "max_inner_resid": last["max_inner_resid"],
         "roofline": roofline, "clocks": clk, "e2e": e2e, "gpu_launches": launches,

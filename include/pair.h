@@ -17,6 +17,9 @@
  *  - Indices are 0-based int32; CSR column indices must be sorted ascending
  *    within each row.  Floating point data is IEEE binary64 unless stated.
  *  - A handle must not be used from two streams at the same time.
+ *  - Device memory the library allocates comes from its own stream-ordered memory
+ *    pool on each device; memory a call frees stays in that pool for later calls
+ *    (the pool keeps its peak size until the process exits).
  */
 #ifndef PAIR_H
 #define PAIR_H
@@ -295,6 +298,8 @@ typedef struct {
     int n_res32;
     double gb_res32;
     int outer_residuals;     /* outer (FP64-accurate) residuals over all direction solves */
+    double t_relaxc_level_ms[8]; /* t_relaxc_ms by level: entry k is level k + 1 (the last
+                                  * entry also holds deeper levels) */
 } si_info;
 
 /* Source iteration (Eq. sn_transport with Eq. angular_quad): each iteration

@@ -43,11 +43,18 @@ enum : int {
     DERR_SWEEP = 16,   // sweep plan limits (faces per element, cyclic components) or a singular component
 };
 
+// The library's stream-ordered memory pool on the current device: created on first
+// use with no release threshold, so memory a call frees stays mapped for the next
+// call's allocations (a complete solve allocates and frees gigabytes of hierarchy
+// and setup scratch; without this every call would map them afresh).  The pool's
+// memory returns to the system when the process exits.
+cudaMemPool_t device_pool();
+
 template <class T>
 T *dmalloc(size_t count, cudaStream_t s) {
     if (count == 0) count = 1;
     void *p = nullptr;
-    cudaError_t e = cudaMallocAsync(&p, count * sizeof(T), s);
+    cudaError_t e = cudaMallocFromPoolAsync(&p, count * sizeof(T), device_pool(), s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         fail(PAIR_ERR_OOM, std::string("device allocation of ") + std::to_string(count * sizeof(T)) +
@@ -257,6 +264,7 @@ struct Hier {
     double t_phase[4] = {0, 0, 0, 0};   // setup: strength+PMIS, P+lAIR, RAP, other
     // coarse-level (l >= 1) relaxation: bytes per cycle
     double t_relaxc = 0, gb_relaxc = 0, bytes_relaxc = 0;
+    double t_relaxc_level[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // by level (entry k: level k + 1)
     long long n_relaxc = 0;
     cudaGraphExec_t graph = nullptr;
     long long graph_kernels = 0;

@@ -244,14 +244,15 @@ __global__ void k_lair_pattern(int nc, const int *cpts, const int *rowptr, const
     npat[ic] = m;
 }
 
-// size class of each lAIR system: 0: n <= 8, 1: <= 12, 2: <= 16, 3: <= 32, 4: <= 64, 5: larger
-// lAIR systems binned by size: thread per system up to 16 unknowns, then a warp per
-// system with a shared-memory workspace sized to the bin (smaller bins keep more
-// systems in flight per SM), global workspaces beyond 64
-constexpr int LAIR_CLASSES = 8;
+// lAIR systems binned by size: a thread per system up to 8 unknowns (bins of 4, 6
+// and 8, whose shared workspaces keep more systems in flight per SM the smaller
+// they are), 8 lanes per system up to 16, then a warp per system with a
+// shared-memory workspace sized to the bin, global workspaces beyond 64
+constexpr int LAIR_CLASSES = 10;
 constexpr int LAIR_BIG = LAIR_CLASSES - 1;
 __device__ __forceinline__ int lair_class(int np) {
-    return np <= 8 ? 0 : np <= 12 ? 1 : np <= 16 ? 2 : np <= 24 ? 3 : np <= 32 ? 4 : np <= 48 ? 5 : np <= 64 ? 6 : 7;
+    return np <= 4 ? 0 : np <= 6 ? 1 : np <= 8 ? 2 : np <= 12 ? 3 : np <= 16 ? 4 : np <= 24 ? 5 : np <= 32 ? 6
+         : np <= 48 ? 7 : np <= 64 ? 8 : 9;
 }
 
 
@@ -904,7 +905,7 @@ void d2h(T *h, const T *d, size_t count, cudaStream_t s) {
 // exclusive scan over (class, block), and a scatter at each row's rank among the
 // rows of its class before it.  One host read (the class counts).
 constexpr int PART_BS = 256;
-constexpr int PART_MAXC = 8;
+constexpr int PART_MAXC = 16;
 
 __global__ void __launch_bounds__(PART_BS) k_class_hist(int n, const int8_t *cls, int nclass, int nblk, int *hist) {
     __shared__ int wc[PART_BS / 32][PART_MAXC];
@@ -1379,7 +1380,7 @@ void build_hierarchy(Hier &h) {
                                                            prm.phi_R);
                 PR_LAUNCH();
             };
-            const int cls_n[LAIR_CLASSES] = {8, 12, 16, 24, 32, 48, 64, 0};
+            const int cls_n[LAIR_CLASSES] = {4, 6, 8, 12, 16, 24, 32, 48, 64, 0};
             auto warp_bin = [&](int c, auto kern, int G) {
                 if (!hc[c]) return;
                 const int nm = cls_n[c], spw = 32 / G;
@@ -1394,11 +1395,13 @@ void build_hierarchy(Hier &h) {
                                                 nullptr);
                 PR_LAUNCH();
             };
-            thread_bin(0, k_lair_solve_thread<8>, 8);
-            warp_bin(1, k_lair_solve<8>, 8);
-            warp_bin(2, k_lair_solve<8>, 8);
-            warp_bin(3, k_lair_solve<16>, 16);
-            for (int c = 4; c < LAIR_BIG; ++c) warp_bin(c, k_lair_solve<32>, 32);
+            thread_bin(0, k_lair_solve_thread<4>, 4);
+            thread_bin(1, k_lair_solve_thread<6>, 6);
+            thread_bin(2, k_lair_solve_thread<8>, 8);
+            warp_bin(3, k_lair_solve<8>, 8);
+            warp_bin(4, k_lair_solve<8>, 8);
+            warp_bin(5, k_lair_solve<16>, 16);
+            for (int c = 6; c < LAIR_BIG; ++c) warp_bin(c, k_lair_solve<32>, 32);
             int nbig = hc[LAIR_BIG];
             if (nbig > 0) {
                 long long *goff = dmalloc<long long>(nbig + 1, s);

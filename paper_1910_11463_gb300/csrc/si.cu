@@ -171,7 +171,9 @@ void account_cycle(Hier &h, const ProfSlot &ps, const std::vector<char> &part) {
         int nl = 0;
         for (size_t l = 1; l + 1 < h.lev.size() && 2 * l + 1 < ps.lv.size(); ++l) {
             if (!h.lev[l].n) continue;
-            tl += elapsed_ms(ps.lv[2 * l], ps.lv[2 * l + 1]);
+            const float t = elapsed_ms(ps.lv[2 * l], ps.lv[2 * l + 1]);
+            tl += t;
+            h.t_relaxc_level[std::min<size_t>(l, 8) - 1] += t;
             ++nl;
         }
         if (nl) {
@@ -841,13 +843,14 @@ void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t,
     double max_inner = 0, opc_sum = 0, change = 0;
     int opc_cnt = 0, it = 0;
     double t_res0 = 0, t_relax0 = 0, gb_res0 = 0, gb_relax0 = 0, tph[4] = {0, 0, 0, 0};
-    double t_relaxc = 0, gb_relaxc = 0, t_res32 = 0, gb_res32 = 0;
+    double t_relaxc = 0, gb_relaxc = 0, t_res32 = 0, gb_res32 = 0, t_lvl[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     long long n_res0 = 0, n_relax0 = 0, n_relaxc = 0, n_res32 = 0, outer_res = 0;
     auto harvest = [&](Hier &h) {
         t_res0 += h.t_res0; t_relax0 += h.t_relax0; gb_res0 += h.gb_res0; gb_relax0 += h.gb_relax0;
         n_res0 += h.n_res0; n_relax0 += h.n_relax0;
         t_relaxc += h.t_relaxc; gb_relaxc += h.gb_relaxc; n_relaxc += h.n_relaxc;
         t_res32 += h.t_res32; gb_res32 += h.gb_res32; n_res32 += h.n_res32;
+        for (int k = 0; k < 8; ++k) { t_lvl[k] += h.t_relaxc_level[k]; h.t_relaxc_level[k] = 0; }
         h.t_res0 = h.t_relax0 = h.gb_res0 = h.gb_relax0 = h.t_relaxc = h.gb_relaxc = h.t_res32 = h.gb_res32 = 0;
         h.n_res0 = h.n_relax0 = h.n_relaxc = h.n_res32 = 0;
     };
@@ -1000,6 +1003,7 @@ void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t,
         info->n_res32 = (int)n_res32;
         info->gb_res32 = gb_res32;
         info->outer_residuals = (int)outer_res;
+        for (int k = 0; k < 8; ++k) info->t_relaxc_level_ms[k] = t_lvl[k];
         for (int k = 0; k < 3; ++k) info->t_setup_phase_ms[k] = tph[k];
         info->t_setup_phase_ms[3] = t_setup - (tph[0] + tph[1] + tph[2]);
     }

@@ -1,6 +1,7 @@
 // Error plumbing and the device exclusive scan used by setup (coarse
 // numbering, row pointers of R, A_c and scratch buffers).
 #include <cstdio>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -10,6 +11,29 @@ std::atomic<long long> g_launches{0};
 thread_local long long g_thread_launches = 0;
 
 void fail(pair_status st, const std::string &msg) { throw Error{st, msg}; }
+
+cudaMemPool_t device_pool() {
+    static std::mutex mu;
+    static cudaMemPool_t pools[256] = {};
+    int dev = 0;
+    cuda_check(cudaGetDevice(&dev), "cudaGetDevice", __FILE__, __LINE__);
+    if (dev < 0 || dev >= 256) fail(PAIR_ERR_UNSUPPORTED, "device ordinal out of range");
+    std::lock_guard<std::mutex> lock(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        cuda_check(cudaMemPoolCreate(&pool, &props), "cudaMemPoolCreate", __FILE__, __LINE__);
+        unsigned long long keep = ~0ULL;
+        cuda_check(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep),
+                   "cudaMemPoolSetAttribute", __FILE__, __LINE__);
+        pools[dev] = pool;
+    }
+    return pools[dev];
+}
 
 void cuda_check(cudaError_t e, const char *what, const char *file, int line) {
     if (e == cudaSuccess) return;
