@@ -329,8 +329,10 @@ def measure_workload(name, args, pair, I, torch, steps=2, warmup=1, fp64=False):
     distance = DISTANCE.get(name, 1)
     kw = dict(theta=args.theta, phi_R=args.phi_R, phi_A=args.phi_A, distance=distance, nair=args.nair)
     air = pair.default_air_params(precision=args.precision, **kw)
-    si = (pair.default_si_params(tol=1e-8, max_iters=fixed, fixed_iters=1, inner_tol=1e-8, inner_maxit=200) if fixed
-          else pair.default_si_params(tol=1e-8, max_iters=1000, inner_tol=1e-8, inner_maxit=200))
+    si = (pair.default_si_params(tol=1e-8, max_iters=fixed, fixed_iters=1, inner_tol=1e-8, inner_maxit=200,
+                                 use_graphs=args.graphs) if fixed
+          else pair.default_si_params(tol=1e-8, max_iters=1000, inner_tol=1e-8, inner_maxit=200,
+                                      use_graphs=args.graphs))
     zero = torch.zeros(N, dtype=torch.float64, device=dev)
 
     def solve(a, s_):
@@ -421,10 +423,13 @@ def run_ours(args):
     tuned = dict(theta=args.theta, phi_R=args.phi_R, phi_A=args.phi_A, distance=args.distance, nair=args.nair)
     air = pair.default_air_params(precision=args.precision, **tuned)
     if fixed:
-        si = pair.default_si_params(tol=1e-8, max_iters=fixed, fixed_iters=1, inner_tol=1e-8, inner_maxit=200)
+        si = pair.default_si_params(tol=1e-8, max_iters=fixed, fixed_iters=1, inner_tol=1e-8, inner_maxit=200,
+                                    use_graphs=args.graphs)
     else:
-        si = pair.default_si_params(tol=1e-8, max_iters=1000, inner_tol=1e-8, inner_maxit=200)
-    si_one = pair.default_si_params(tol=1e-8, max_iters=1, inner_tol=1e-8, inner_maxit=200)
+        si = pair.default_si_params(tol=1e-8, max_iters=1000, inner_tol=1e-8, inner_maxit=200,
+                                    use_graphs=args.graphs)
+    si_one = pair.default_si_params(tol=1e-8, max_iters=1, inner_tol=1e-8, inner_maxit=200,
+                                    use_graphs=args.graphs)
     zero = torch.zeros(N, dtype=torch.float64, device=dev)
 
     from paper_1910_11463_gb300 import angle
@@ -659,6 +664,8 @@ def main():
     ap.add_argument("--precision", type=int, default=1, choices=[0, 1, 2],
                     help="0 FP64; 1 FP32 V-cycle under FP64 refinement (default); 2 FP32 V-cycle under "
                          "double-float refinement (hex block form)")
+    ap.add_argument("--graphs", type=int, default=1, choices=[0, 1],
+                    help="1: V-cycles launched as CUDA graphs (default); 0: launched directly")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64-baseline", action="store_true")

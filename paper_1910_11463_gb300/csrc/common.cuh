@@ -49,6 +49,7 @@ enum : int {
 // and setup scratch; without this every call would map them afresh).  The pool's
 // memory returns to the system when the process exits.
 cudaMemPool_t device_pool();
+size_t available_device_bytes();   // free device memory plus the pool's mapped, unused memory
 
 template <class T>
 T *dmalloc(size_t count, cudaStream_t s) {

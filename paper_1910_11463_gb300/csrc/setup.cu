@@ -365,16 +365,28 @@ __global__ void __launch_bounds__(64) k_lair_solve_thread(int nwork, const int *
     for (int e = 0; e < np; ++e) { PAT(e) = cp[e]; YY(e) = -0.0; }
     for (int e = 0; e < np * np; ++e) MM(e) = 0.0;
     for (int c = 0; c < np; ++c) {
-        int j = PAT(c);
-        for (int p = rowptr[j]; p < rowptr[j + 1]; ++p) {
-            int k = col[p], lo = 0, hi = np - 1, r = -1;
-            while (lo <= hi) {
-                int m = (lo + hi) >> 1;
-                int v = PAT(m);
-                if (v == k) { r = m; break; }
-                if (v < k) lo = m + 1; else hi = m - 1;
+        const int j = PAT(c), p1 = rowptr[j + 1];
+        for (int p = rowptr[j]; p < p1; p += 4) {   // four entries' loads before their lookups
+            int kk[4];
+            double vv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                kk[u] = p + u < p1 ? col[p + u] : -1;
+                vv[u] = p + u < p1 ? val[p + u] : 0.0;
             }
-            if (r >= 0) MM(r * np + c) = val[p];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int k = kk[u];
+                if (k < 0) continue;
+                int lo = 0, hi = np - 1, r = -1;
+                while (lo <= hi) {
+                    int m = (lo + hi) >> 1;
+                    int v = PAT(m);
+                    if (v == k) { r = m; break; }
+                    if (v < k) lo = m + 1; else hi = m - 1;
+                }
+                if (r >= 0) MM(r * np + c) = vv[u];
+            }
         }
     }
     for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) {
@@ -480,12 +492,24 @@ __global__ void k_lair_solve(int nwork, const int *worklist, const int *cpts, co
         }
         __syncwarp();
         if (has) {
-            // M[r][c] = a(pat[c], pat[r]): lane per pattern row, one pass over it
+            // M[r][c] = a(pat[c], pat[r]): lane per pattern row, one pass over it, the
+            // loads of four entries issued before their lookups
             for (int c = g; c < np; c += G) {
-                int j = pat[c];
-                for (int p = rowptr[j]; p < rowptr[j + 1]; ++p) {
-                    int r = pat_find(pat, np, col[p]);
-                    if (r >= 0) M[r * np + c] = val[p];
+                const int j = pat[c], p1 = rowptr[j + 1];
+                for (int p = rowptr[j]; p < p1; p += 4) {
+                    int cc[4];
+                    double vv[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        cc[u] = p + u < p1 ? col[p + u] : -1;
+                        vv[u] = p + u < p1 ? val[p + u] : 0.0;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        if (cc[u] < 0) continue;
+                        const int r = pat_find(pat, np, cc[u]);
+                        if (r >= 0) M[r * np + c] = vv[u];
+                    }
                 }
             }
             for (int p = rowptr[i] + g; p < rowptr[i + 1]; p += G) {
@@ -526,26 +550,36 @@ __global__ void k_lair_solve(int nwork, const int *worklist, const int *cpts, co
                     }
             }
             __syncwarp();
-            if (act) {
-                double rd = 1.0 / M[k * np + k];
-                if (g == 0) rv[k] = rd;
-                for (int r = k + 1 + g; r < np; r += G) M[r * np + k] = M[r * np + k] * rd;
+            // the pivot's reciprocal: one lane of the group divides, the others take it
+            double rd = 0.0;
+            if (act && g == 0) {
+                rd = 1.0 / M[k * np + k];
+                rv[k] = rd;
             }
+            rd = __shfl_sync(FULL, rd, q * G);
+            if (act)
+                for (int r = k + 1 + g; r < np; r += G) M[r * np + k] = M[r * np + k] * rd;
             __syncwarp();
             if (act) {
-                // lane g updates entries g, g + G, ... of the wd x wd trailing block in
-                // row-major order; (row, column) advance by (G / wd, G % wd) per step
-                // with one carry, so no division per entry
+                // each lane owns a column of the trailing block and runs down its rows
+                // (independent updates, unrolled; the multiplier column is read by the
+                // lanes at once).  A block narrower than the group splits its rows among
+                // H = G / wd lane sets, so no lane idles while others update.
                 const int wd = np - k - 1;
-                if (wd > 0) {
-                    const int dr = G / wd, dc = G - dr * wd;
-                    int r = g / wd, c = g - r * wd;
-                    for (int idx = g; idx < wd * wd; idx += G) {
-                        const int R = k + 1 + r, Cc = k + 1 + c;
-                        M[R * np + Cc] = fma(-M[R * np + k], M[k * np + Cc], M[R * np + Cc]);
-                        r += dr;
-                        c += dc;
-                        if (c >= wd) { c -= wd; ++r; }
+                if (wd >= G) {
+                    for (int cc = g; cc < wd; cc += G) {
+                        const int C = k + 1 + cc;
+                        const double u = M[k * np + C];
+#pragma unroll 4
+                        for (int R = k + 1; R < np; ++R) M[R * np + C] = fma(-M[R * np + k], u, M[R * np + C]);
+                    }
+                } else if (wd > 0) {
+                    const int H = G / wd;
+                    if (g < H * wd) {
+                        const int h = g / wd, C = k + 1 + (g - h * wd);
+                        const double u = M[k * np + C];
+#pragma unroll 4
+                        for (int R = k + 1 + h; R < np; R += H) M[R * np + C] = fma(-M[R * np + k], u, M[R * np + C]);
                     }
                 }
             }

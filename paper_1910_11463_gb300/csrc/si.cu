@@ -783,8 +783,7 @@ void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t,
     const bool sweep = sp.solver == 1;
     // direction batches admitted by memory
     size_t per = sweep ? sweep_bytes_per_dir(mesh, gin) : bytes_per_dir(mesh, prm.precision, gin);
-    size_t freeb = 0, totb = 0;
-    PR_CUDA(cudaMemGetInfo(&freeb, &totb));
+    const size_t freeb = available_device_bytes();
     double budget = sp.mem_budget_gb > 0 ? sp.mem_budget_gb * 1e9 : 0.6 * (double)freeb;
     require_budget(per, sp.mem_budget_gb > 0 ? budget : (double)freeb, sp.mem_budget_gb > 0);
     int B = sp.batch > 0 ? std::min(sp.batch, M) : M;
@@ -1023,8 +1022,7 @@ void si_adjoint_run(const pair_mesh &mesh, const pair_quad &quad, const double *
     const bool sweep = sp.solver == 1;   // exact sweeps of the transposed operators instead of AIR
     PR_CUDA(cudaStreamSynchronize(user));
     size_t per = (sweep ? sweep_bytes_per_dir(mesh, false) : bytes_per_dir(mesh, prm.precision, false)) + (size_t)N * 16;
-    size_t freeb = 0, totb = 0;
-    PR_CUDA(cudaMemGetInfo(&freeb, &totb));
+    const size_t freeb = available_device_bytes();
     double budget = sp.mem_budget_gb > 0 ? sp.mem_budget_gb * 1e9 : 0.6 * (double)freeb;
     int B = sp.batch > 0 ? std::min(sp.batch, M) : M;
     B = std::min<long long>(B, std::max<long long>(1, (long long)(budget / (double)per)));

@@ -12,6 +12,20 @@ thread_local long long g_thread_launches = 0;
 
 void fail(pair_status st, const std::string &msg) { throw Error{st, msg}; }
 
+// free device memory as the library can use it: what the device reports free plus
+// what its pool holds mapped but unused
+size_t available_device_bytes() {
+    size_t freeb = 0, totb = 0;
+    cuda_check(cudaMemGetInfo(&freeb, &totb), "cudaMemGetInfo", __FILE__, __LINE__);
+    cudaMemPool_t pool = device_pool();
+    unsigned long long reserved = 0, used = 0;
+    cuda_check(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved),
+               "cudaMemPoolGetAttribute", __FILE__, __LINE__);
+    cuda_check(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used), "cudaMemPoolGetAttribute",
+               __FILE__, __LINE__);
+    return freeb + (size_t)(reserved > used ? reserved - used : 0);
+}
+
 cudaMemPool_t device_pool() {
     static std::mutex mu;
     static cudaMemPool_t pools[256] = {};
