@@ -561,25 +561,35 @@ __global__ void k_lair_solve(int nwork, const int *worklist, const int *cpts, co
                 for (int r = k + 1 + g; r < np; r += G) M[r * np + k] = M[r * np + k] * rd;
             __syncwarp();
             if (act) {
-                // each lane owns a column of the trailing block and runs down its rows
-                // (independent updates, unrolled; the multiplier column is read by the
-                // lanes at once).  A block narrower than the group splits its rows among
-                // H = G / wd lane sets, so no lane idles while others update.
+                // lane g updates entries g, g + G, ... of the wd x wd trailing block in
+                // row-major order (the fewest FP64 instructions: every lane busy until the
+                // last entries), four entries per pass with all their loads issued
+                // before the updates; (row, column) advance by (G / wd, G % wd) per entry
+                // with at most one carry, so no division per entry
                 const int wd = np - k - 1;
-                if (wd >= G) {
-                    for (int cc = g; cc < wd; cc += G) {
-                        const int C = k + 1 + cc;
-                        const double u = M[k * np + C];
-#pragma unroll 4
-                        for (int R = k + 1; R < np; ++R) M[R * np + C] = fma(-M[R * np + k], u, M[R * np + C]);
-                    }
-                } else if (wd > 0) {
-                    const int H = G / wd;
-                    if (g < H * wd) {
-                        const int h = g / wd, C = k + 1 + (g - h * wd);
-                        const double u = M[k * np + C];
-#pragma unroll 4
-                        for (int R = k + 1 + h; R < np; R += H) M[R * np + C] = fma(-M[R * np + k], u, M[R * np + C]);
+                if (wd > 0) {
+                    const int tot = wd * wd;
+                    const int dr = G / wd, dc = G - dr * wd;
+                    int r = g / wd, c = g - r * wd;
+                    for (int e = g; e < tot; e += 4 * G) {
+                        int Ro[4], Co[4];
+                        bool ok[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            ok[u] = e + u * G < tot;
+                            Ro[u] = (k + 1 + r) * np;
+                            Co[u] = k + 1 + c;
+                            r += dr;
+                            c += dc;
+                            if (c >= wd) { c -= wd; ++r; }
+                        }
+                        double a[4], b[4], m[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            if (ok[u]) { a[u] = M[Ro[u] + k]; b[u] = M[k * np + Co[u]]; m[u] = M[Ro[u] + Co[u]]; }
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            if (ok[u]) M[Ro[u] + Co[u]] = fma(-a[u], b[u], m[u]);
                     }
                 }
             }
