@@ -244,7 +244,11 @@ def bench_config(args, world):
                     "relax": "F-F-C Jacobi", "coarsening": "PMIS"},
             "l2": "working set per step >> 129 MB L2 (no flush needed)",
             "parallelism": (f"angular decomposition over {world} GPUs (directions split, scalar flux all-reduced "
-                            "every SI iteration)") if world > 1 else "1 GPU, all directions in one batch",
+                            "every SI iteration)") if world > 1 else (
+                               "1 GPU, all directions in one batch" if args.concurrent == 1 else
+                               f"1 GPU, directions in {args.concurrent or 'the library default number of'} "
+                               "concurrent groups"),
+            "kernel_timing": f"CUDA events in the cycles of every {args.timing_every}th SI iteration",
             "precision": ("FP32 hierarchy/V-cycle, double-float refinement" if args.precision == 2 else
                           "FP32 hierarchy/V-cycle, FP64 refinement" if args.precision else "FP64")}
 
@@ -285,9 +289,14 @@ def run_reference(args):
 
 def kernel_table(infos, steps, ms, tet, precision):
     """Per kernel group of the timed steps: CUDA-event time inside the steps,
-    algorithmic bytes counted by the library, launches (units), share of the step."""
+    algorithmic bytes counted by the library, launches (units), share of the step.
+    The library times the cycles of every k-th SI iteration (si_params.timing), with
+    the direction groups one after another: per-launch figures come from those
+    cycles, and a group's share of the step scales their time by the iterations
+    solved over the iterations timed."""
     def tot(key):
         return sum(i[key] for i in infos)
+    scale = tot("si_iters") / max(tot("timed_iters"), 1)
     kern = {
         ("k_res0_csr" if tet else "k_res0_bsr_dd" if precision == 2 else "k_res0_bsr"): (
             ("FP64 outer residual, level 0 CSR" if tet else
@@ -310,7 +319,8 @@ def kernel_table(infos, steps, ms, tet, precision):
     for name, (what, t_ms, n_l, gb) in kern.items():
         rl[name] = {"what": what, "achieved_gbs": gb / (t_ms * 1e-3) if t_ms > 0 else None, "launches": n_l,
                     "ms_per_launch": t_ms / max(n_l, 1), "gb_per_launch": gb / max(n_l, 1),
-                    "share_of_step": t_ms / steps / ms}
+                    "share_of_step": t_ms * scale / steps / ms, "timed_iterations": tot("timed_iters"),
+                    "solved_iterations": tot("si_iters")}
     return rl
 
 
@@ -330,9 +340,11 @@ def measure_workload(name, args, pair, I, torch, steps=2, warmup=1, fp64=False):
     kw = dict(theta=args.theta, phi_R=args.phi_R, phi_A=args.phi_A, distance=distance, nair=args.nair)
     air = pair.default_air_params(precision=args.precision, **kw)
     si = (pair.default_si_params(tol=1e-8, max_iters=fixed, fixed_iters=1, inner_tol=1e-8, inner_maxit=200,
-                                 use_graphs=args.graphs) if fixed
+                                 use_graphs=args.graphs, concurrent=args.concurrent,
+                                 timing=min(args.timing_every, fixed)) if fixed
           else pair.default_si_params(tol=1e-8, max_iters=1000, inner_tol=1e-8, inner_maxit=200,
-                                      use_graphs=args.graphs))
+                                      use_graphs=args.graphs, concurrent=args.concurrent,
+                                      timing=args.timing_every))
     zero = torch.zeros(N, dtype=torch.float64, device=dev)
 
     def solve(a, s_):
@@ -381,7 +393,8 @@ def measure_workload(name, args, pair, I, torch, steps=2, warmup=1, fp64=False):
     if fp64:
         air64 = pair.default_air_params(precision=0, **kw)
         si64 = pair.default_si_params(tol=1e-8, max_iters=fixed or 1000, fixed_iters=int(bool(fixed)),
-                                      inner_tol=1e-8, inner_maxit=200, batch=1, use_graphs=0)
+                                      inner_tol=1e-8, inner_maxit=200, batch=1, use_graphs=0,
+                                      concurrent=1)
         torch.cuda.synchronize()
         e0.record(stream)
         phi64, i64 = solve(air64, si64)
@@ -424,12 +437,13 @@ def run_ours(args):
     air = pair.default_air_params(precision=args.precision, **tuned)
     if fixed:
         si = pair.default_si_params(tol=1e-8, max_iters=fixed, fixed_iters=1, inner_tol=1e-8, inner_maxit=200,
-                                    use_graphs=args.graphs)
+                                    use_graphs=args.graphs, concurrent=args.concurrent,
+                                    timing=min(args.timing_every, fixed))
     else:
         si = pair.default_si_params(tol=1e-8, max_iters=1000, inner_tol=1e-8, inner_maxit=200,
-                                    use_graphs=args.graphs)
+                                    use_graphs=args.graphs, concurrent=args.concurrent, timing=args.timing_every)
     si_one = pair.default_si_params(tol=1e-8, max_iters=1, inner_tol=1e-8, inner_maxit=200,
-                                    use_graphs=args.graphs)
+                                    use_graphs=args.graphs, concurrent=args.concurrent)
     zero = torch.zeros(N, dtype=torch.float64, device=dev)
 
     from paper_1910_11463_gb300 import angle
@@ -539,7 +553,8 @@ def run_ours(args):
     if not args.no_fp64_baseline:
         air64 = pair.default_air_params(precision=0, **tuned)
         si64 = pair.default_si_params(tol=1e-8, max_iters=fixed or 1000, fixed_iters=int(bool(fixed)),
-                                      inner_tol=1e-8, inner_maxit=200, batch=1, use_graphs=0)
+                                      inner_tol=1e-8, inner_maxit=200, batch=1, use_graphs=0,
+                                      concurrent=1)
         barrier()
         e0.record(stream)
         phi64, i64 = solve(air64, si64, zero)
@@ -609,6 +624,27 @@ def run_ours(args):
                 "vcycles_per_direction_per_iteration": i3["vcycles"] / M / max(i3["si_iters"], 1),
                 "max_inner_resid": i3["max_inner_resid"],
                 "phi_rel_diff_vs_headline": (torch.linalg.norm(phi3 - phi) / torch.linalg.norm(phi)).item()}
+    # variant: the same solve without kernel-timing events (si_params.timing = 0), as
+    # one batch and as the library's default concurrent direction groups
+    untimed = None
+    if not args.no_variants:
+        untimed = {}
+        for label, K in (("one_batch", 1), ("concurrent_groups_default", 0)):
+            si_u = pair.default_si_params(tol=si.tol, max_iters=si.max_iters, fixed_iters=si.fixed_iters,
+                                          inner_tol=si.inner_tol, inner_maxit=si.inner_maxit,
+                                          use_graphs=si.use_graphs, concurrent=K, timing=0)
+            solve(air, si_u, zero)
+            barrier()
+            e0.record(stream)
+            for _ in range(2):
+                phi_u, i_u = solve(air, si_u, zero)
+            e1.record(stream)
+            barrier()
+            ms_u = max_over_ranks(e0.elapsed_time(e1) / 2, world, dev)
+            untimed[label] = {"value": N * M * i_u["si_iters"] / (ms_u * 1e-3), "ms_per_step": ms_u,
+                              "si_iters": i_u["si_iters"], "batches": i_u["batches"],
+                              "phi_rel_diff_vs_headline":
+                                  (torch.linalg.norm(phi_u - phi) / torch.linalg.norm(phi)).item()}
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -638,7 +674,7 @@ def run_ours(args):
         "roofline": roofline, "clocks": clk, "e2e": e2e, "gpu_launches": launches,
         "fp64_one_direction": fp64,
         "gpu_sweep": gsweep,
-        "variants": {"double_float_refinement": dd, "nair_degree1_phiR_0.1": nair},
+        "variants": {"double_float_refinement": dd, "nair_degree1_phiR_0.1": nair, "without_kernel_timing": untimed},
     }
     # the other synthetic meshes on the same build: unstructured tets (distance-2
     # lAIR) and the 64^3 scale run, each with its per-kernel roofline
@@ -664,6 +700,11 @@ def main():
     ap.add_argument("--precision", type=int, default=1, choices=[0, 1, 2],
                     help="0 FP64; 1 FP32 V-cycle under FP64 refinement (default); 2 FP32 V-cycle under "
                          "double-float refinement (hex block form)")
+    ap.add_argument("--timing-every", dest="timing_every", type=int, default=6,
+                    help="kernel timings in SI iterations k, 2k, ... (si_params.timing)")
+    ap.add_argument("--concurrent", type=int, default=1,
+                    help="direction groups solved at the same time on their own streams (0: library default; "
+                         "1: one batch, so the timed kernels are whole-batch launches)")
     ap.add_argument("--graphs", type=int, default=1, choices=[0, 1],
                     help="1: V-cycles launched as CUDA graphs (default); 0: launched directly")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

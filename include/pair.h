@@ -267,9 +267,28 @@ typedef struct {
     pair_reduce_fn phi_reduce; /* NULL, or the scalar-flux reduction of a direction subset
                           * (Sec. 5, parallel in angle), see pair_reduce_fn */
     void *reduce_ctx;    /* passed to phi_reduce unchanged */
+    int concurrent;      /* direction groups solved at the same time (si_solve and
+                          * si_adjoint), each batch on its own stream from its own host
+                          * thread, when every hierarchy is resident (0: min(M, 3); 1:
+                          * one batch after another).  The
+                          * directions are split into at least this many batches; each
+                          * group sums its batches' w_m psi_m and phi^{n+1} adds the
+                          * group sums in group order, so the flux is deterministic for
+                          * a given value (and differs between values only by rounding).
+                          * The exact sweep (solver 1) always runs one batch at a time. */
+    int timing;          /* k >= 1: CUDA events around the level-0 kernels and each
+                          * coarse level's sweeps in the V-cycles of SI iterations k, 2k,
+                          * ... (counting from 1; the per-kernel times and traffic of
+                          * si_info, summed over those cycles), the concurrent groups
+                          * then running one after another so that no other group's
+                          * kernels fall between a kernel's events; 0: none.  An event
+                          * between two kernels of a captured cycle ends their
+                          * programmatic overlap, so timed cycles replay graphs of their
+                          * own and run slower (~10% on the 32^3 S4 batch); the other
+                          * iterations replay graphs without events. */
 } si_params;
 
-PAIR_API void si_params_default(si_params *p);   /* 1e-8, 500, 1e-8, 100, 0, 0, 0, 1, 0, 0, 0, NULL, NULL, NULL */
+PAIR_API void si_params_default(si_params *p);   /* 1e-8, 500, 1e-8, 100, 0, 0, 0, 1, 0, 0, 0, NULL, NULL, NULL, 0, 0 */
 
 typedef struct {
     int si_iters;
@@ -278,19 +297,24 @@ typedef struct {
     double max_inner_resid;  /* max final relative FP64 residual over direction solves */
     int batches;             /* direction batches per SI iteration */
     int rebuilt;             /* 1 if hierarchies were rebuilt every SI iteration */
-    double t_setup_ms;       /* assembly + AIR setup time (device events) */
-    double t_solve_ms;       /* RHS build + solves + scalar-flux sums (device events) */
+    double t_setup_ms;       /* assembly + AIR setup time (host clock around each batch's
+                              * setup; with concurrent groups the longest batch's) */
+    double t_solve_ms;       /* RHS build + solves + scalar-flux sums (device events; with
+                              * concurrent groups the wall time less the setup) */
     int levels_max;          /* deepest hierarchy */
     double op_complexity;    /* sum_l nnz(A_l) / nnz(A_0), mean over directions */
     /* device-event timings of the level-0 kernels and their algorithmic traffic
-     * (bytes the method must move: operator entries, vectors read and written) */
+     * (bytes the method must move: operator entries, vectors read and written),
+     * summed over batches; with concurrent groups a kernel's events also span the
+     * other groups' kernels that ran beside it */
     double t_res0_ms;        /* FP64 residual r = b - A psi, all launches */
     int n_res0;
     double gb_res0;          /* algorithmic GB over those launches */
     double t_relax0_ms;      /* level-0 F- and C-Jacobi passes, all launches */
     int n_relax0;
     double gb_relax0;
-    double t_setup_phase_ms[4]; /* strength+PMIS, P+lAIR, Galerkin RAP, other setup */
+    double t_setup_phase_ms[4]; /* strength+PMIS, P+lAIR, Galerkin RAP, other setup (with
+                                 * concurrent groups: those of the longest batch setup) */
     double t_relaxc_ms;      /* F- and C-Jacobi passes on levels >= 1 (CSR), all cycles */
     int n_relaxc;            /* cycles measured */
     double gb_relaxc;        /* algorithmic GB of those passes */
@@ -300,6 +324,8 @@ typedef struct {
     int outer_residuals;     /* outer (FP64-accurate) residuals over all direction solves */
     double t_relaxc_level_ms[8]; /* t_relaxc_ms by level: entry k is level k + 1 (the last
                                   * entry also holds deeper levels) */
+    int timed_iters;         /* SI iterations whose cycles the kernel timings cover
+                              * (si_params.timing) */
 } si_info;
 
 /* Source iteration (Eq. sn_transport with Eq. angular_quad): each iteration

@@ -174,6 +174,8 @@ void si_params_default(si_params *p) {
     p->q_ang = nullptr;
     p->phi_reduce = nullptr;
     p->reduce_ctx = nullptr;
+    p->concurrent = 0;
+    p->timing = 0;
 }
 
 const char *pair_last_error(void) { return g_last_error.c_str(); }

@@ -69,6 +69,18 @@ inline void dfree(void *p, cudaStream_t s) {
 
 inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
+// Lets kernel 'kern' take up to the device's opt-in shared memory per block.  The
+// attribute belongs to the function, not to a launch: every caller sets the same
+// maximal value, so hierarchies set up at the same time on several host threads
+// cannot lower it under one another's launch.
+template <class F>
+void allow_max_dyn_smem(F kern) {
+    int dev = 0, optin = 0;
+    PR_CUDA(cudaGetDevice(&dev));
+    PR_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    PR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+}
+
 // Programmatic dependent launch: the kernel may start while the previous kernel
 // on the stream finishes; it must begin with pdl_begin() (device side), which waits
 // for the previous grid's completion and memory, then lets the next kernel launch.
@@ -200,6 +212,31 @@ constexpr double INNER_ETA = 1e-5;
 constexpr int INNER_GRAPHS = 5;
 constexpr int INNER_SLOTS = (1 << INNER_GRAPHS) - 1;
 
+// Captured graphs of a hierarchy's solve loop.
+struct CycleGraphs {
+    cudaGraphExec_t gcyc[INNER_GRAPHS] = {};      // 2^g inner cycles
+    long long gcyc_kernels[INNER_GRAPHS] = {};
+    cudaGraphExec_t gclose = nullptr;             // x += d, outer residual and norms
+    long long gclose_kernels = 0;
+    const double *gi_b = nullptr;
+    double *gi_x = nullptr;
+    double gi_tol = -1;
+    cudaGraphExec_t graph = nullptr;              // one V-cycle + residual (or a sweep)
+    long long graph_kernels = 0;
+    const double *graph_b = nullptr;
+    double *graph_x = nullptr;
+    double graph_tol = -1;
+    CycleGraphs() = default;
+    CycleGraphs(const CycleGraphs &) = delete;
+    CycleGraphs &operator=(const CycleGraphs &) = delete;
+    ~CycleGraphs() {
+        if (graph) cudaGraphExecDestroy(graph);
+        for (auto &g : gcyc)
+            if (g) cudaGraphExecDestroy(g);
+        if (gclose) cudaGraphExecDestroy(gclose);
+    }
+};
+
 struct Hier {
     int ndir = 0;
     air_params prm{};
@@ -245,16 +282,15 @@ struct Hier {
     unsigned *iticket = nullptr;                  // CTA ticket of the norm kernels (0 between launches)
     double *ithr = nullptr, *inorm = nullptr;     // [dir]
     double rho_est = 0.0;                         // contraction of the inner cycles (0: none yet)
-    cudaGraphExec_t gcyc[INNER_GRAPHS] = {};      // 2^g inner cycles
-    long long gcyc_kernels[INNER_GRAPHS] = {};
-    cudaGraphExec_t gclose = nullptr;             // x += d, outer residual and norms
-    long long gclose_kernels = 0;
-    const double *gi_b = nullptr;
-    double *gi_x = nullptr;
-    double gi_tol = -1;
+    // captured graphs, one set without and one with the timing events (an event
+    // between two kernels ends their programmatic overlap, so untimed solves replay
+    // graphs without them)
+    CycleGraphs gr[2];
+    CycleGraphs &graphs() { return gr[timed ? 1 : 0]; }
     // instrumentation: CUDA events around the level-0 kernels and the coarse levels
-    // (also inside graphs); ev[0..1] bracket the outer residual
-    bool prof = false;
+    // (also inside graphs); ev[0..1] bracket the outer residual.  prof: the events
+    // exist; timed: the current solve records them
+    bool prof = false, timed = false;
     cudaEvent_t ev[2] = {nullptr, nullptr};
     std::vector<ProfSlot> slots;       // slot 0: the per-cycle path; 0..INNER_SLOTS-1: inner graphs
     double t_res0 = 0, t_relax0 = 0, gb_res0 = 0, gb_relax0 = 0, t_res32 = 0, gb_res32 = 0;
@@ -267,11 +303,6 @@ struct Hier {
     double t_relaxc = 0, gb_relaxc = 0, bytes_relaxc = 0;
     double t_relaxc_level[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // by level (entry k: level k + 1)
     long long n_relaxc = 0;
-    cudaGraphExec_t graph = nullptr;
-    long long graph_kernels = 0;
-    const double *graph_b = nullptr;
-    double *graph_x = nullptr;
-    double graph_tol = -1;
     SweepPlan *dag = nullptr;   // exact-sweep schedule of an unstructured batch
     ~Hier();
 };

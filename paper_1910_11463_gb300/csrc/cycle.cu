@@ -932,7 +932,7 @@ template <class T>
 void vcycle_t(Hier &h, double *x64, float *d32, const int *active, ProfSlot *ps) {
     cudaStream_t s = h.stream;
     int NL = (int)h.lev.size();
-    const bool prof = h.prof && ps;
+    const bool prof = h.timed && ps;
     const int *any = d32 ? h.iany : nullptr;
     if (ps) ps->relax_timed = false;
     for (int l = 0; l < NL; ++l) {
@@ -1274,9 +1274,9 @@ void residual0(Hier &h, const double *b, const double *x, double tol, bool updat
     // every block of an active matrix writes its partial; inactive matrices' partials
     // are not read
     int *act = update_active ? h.active : nullptr;
-    if (h.prof) rec_event(h.ev[0], s);
+    if (h.timed) rec_event(h.ev[0], s);
     residual0_launch(h, b, x, act, nullptr);
-    if (h.prof) rec_event(h.ev[1], s);
+    if (h.timed) rec_event(h.ev[1], s);
     launch_pdl(k_norm_final, blocks_for(32LL * h.ndir, 128), 128, s, h.ndir, h.partials, h.maxblk, h.rnorm, h.bnorm, tol,
                                                                  act);
     PR_LAUNCH();
@@ -1353,11 +1353,12 @@ template <class T, int MODE>
 void tune_store(Sell &S, const SellJob<T> &j, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
     if (S.nrows <= 0) return;
     const auto key = std::make_tuple(MODE, (int)sizeof(T), S.npos, S.nnz);
-    {
-        std::lock_guard<std::mutex> lock(g_tune_mutex);
-        auto it = g_tune.find(key);
-        if (it != g_tune.end()) { S.G = it->second; return; }
-    }
+    // held while tuning: hierarchies set up at the same time on other threads (the
+    // concurrent direction groups) with a store of the same key wait for this choice
+    // instead of timing their own, so equal stores of one process sum rows alike
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) { S.G = it->second; return; }
     int best = 1;
     float tbest = 0;
     for (int G = 1; G <= 8; G *= 2) {
@@ -1371,7 +1372,6 @@ void tune_store(Sell &S, const SellJob<T> &j, cudaStream_t s, cudaEvent_t e0, cu
         if (G == 1 || ms < tbest) { tbest = ms; best = G; }
     }
     S.G = best;
-    std::lock_guard<std::mutex> lock(g_tune_mutex);
     g_tune[key] = best;
 }
 
@@ -1450,9 +1450,9 @@ void inner_enable(Hier &h) {
 
 void residual_outer(Hier &h, const double *b, const double *x, double tol) {
     cudaStream_t s = h.stream;
-    if (h.prof) rec_event(h.ev[0], s);
+    if (h.timed) rec_event(h.ev[0], s);
     residual0_launch(h, b, x, h.active, h.r32);
-    if (h.prof) rec_event(h.ev[1], s);
+    if (h.timed) rec_event(h.ev[1], s);
     launch_pdl(k_norm_outer, h.ndir, NORM_BS, s, h.ndir, (const double *)h.partials, h.maxblk, h.rnorm,
                (const double *)h.bnorm, tol, h.active, h.iactive, h.ithr, h.iany, h.iticket);
     PR_LAUNCH();
@@ -1461,7 +1461,7 @@ void residual_outer(Hier &h, const double *b, const double *x, double tol) {
 void inner_cycle(Hier &h, ProfSlot *ps) {
     cudaStream_t s = h.stream;
     vcycle_t<float>(h, nullptr, h.d32, h.iactive, ps);
-    const bool prof = h.prof && ps;
+    const bool prof = h.timed && ps;
     if (ps) ps->res_timed = false;
     if (prof) { rec_event(ps->res32[0], s); ps->res_timed = true; }
     Level &L = h.lev[0];

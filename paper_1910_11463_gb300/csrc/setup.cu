@@ -723,6 +723,11 @@ __device__ __forceinline__ unsigned hslot(int c, unsigned mask) { return ((unsig
 // in global scratch (cap per row given by gptr).  Output: sorted, filtered
 // entries at ucol/uval[uptr[ic]...], count in cnt[ic].  Magnitude maxima use
 // integer keys; the phi_A filter costs nothing when it is off (filt == 0).
+// A row's table has the first power of two >= its bound U (at least 64) slots:
+// U bounds the row's distinct columns, so linear probing always finds a slot, and
+// on the transport operators the distinct columns are on average 20-55% of U, so
+// tables stay about half full or less.  Each slot's additions follow the R-row
+// order whatever the table size, so the size changes no bit of the result.
 template <int G, bool GLOBAL_TABLE>
 __global__ void k_rap(int nrows_work, const int *worklist, const int *cpts, const int *zrowptr, const int *zcol,
                       const double *zval, const int *aprow, const int *aplen, const int *apcol, const double *apval,
@@ -752,12 +757,12 @@ __global__ void k_rap(int nrows_work, const int *worklist, const int *cpts, cons
                 int slot = warp * SPW + q;
                 vals = smem2 + (size_t)slot * hcap;
                 keys = (int *)(smem2 + (size_t)wpb * SPW * hcap) + (size_t)slot * hcap;
-                if (2 * U[ic] > hcap) {
+                if (U[ic] > hcap) {
                     if (g == 0) { cnt[ic] = -1; atomicAdd(overflow, 1); }
                     has = false;
                 } else {
                     cap = 64;
-                    while (cap < 2 * U[ic]) cap <<= 1;
+                    while (cap < U[ic]) cap <<= 1;
                 }
             }
         }
@@ -900,7 +905,7 @@ __global__ void k_fill_int(int n, int *a, int v) {
     if (i < n) a[i] = v;
 }
 
-__device__ __forceinline__ int rap_bin(int u) { return 2 * u <= 256 ? 0 : 2 * u <= 1024 ? 1 : 2 * u <= 4096 ? 2 : 3; }
+__device__ __forceinline__ int rap_bin(int u) { return u <= 128 ? 0 : u <= 512 ? 1 : u <= 2048 ? 2 : 3; }
 
 
 
@@ -908,7 +913,7 @@ __global__ void k_overflow_caps(int nover, const int *list, const int *U, long l
     int w = blockIdx.x * blockDim.x + threadIdx.x;
     if (w >= nover) return;
     long long c = 64;
-    while (c < 2LL * U[list[w]]) c <<= 1;
+    while (c < (long long)U[list[w]]) c <<= 1;
     capw[w] = c;
 }
 
@@ -1417,8 +1422,7 @@ void build_hierarchy(Hier &h) {
             auto thread_bin = [&](int c, auto kern, int nm) {
                 if (!hc[c]) return;
                 size_t sm = (size_t)64 * (nm * nm + 3 * nm) * sizeof(double);
-                if (sm > 48 * 1024)
-                    PR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+                if (sm > 48 * 1024) allow_max_dyn_smem(kern);
                 kern<<<blocks_for(hc[c], 64), 64, sm, s>>>(hc[c], list + hstart[c], L.cpts, L.rowptr, L.col, L.val,
                                                            candptr, cand, npat, zr, zc, zv, keep, dsing, L.rowdir,
                                                            prm.phi_R);
@@ -1432,8 +1436,7 @@ void build_hierarchy(Hier &h) {
                 int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (200 * 1024) / per));
                 size_t sm = per * wpb;
                 unsigned grid = std::min<unsigned>(blocks_for(hc[c], wpb * spw), 152u * 64u);
-                if (sm > 48 * 1024)
-                    PR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+                if (sm > 48 * 1024) allow_max_dyn_smem(kern);
                 kern<<<grid, 32 * wpb, sm, s>>>(hc[c], list + hstart[c], L.cpts, L.rowptr, L.col, L.val, candptr,
                                                 cand, npat, zr, zc, zv, keep, dsing, L.rowdir, prm.phi_R, nm, nullptr,
                                                 nullptr);
@@ -1498,7 +1501,7 @@ void build_hierarchy(Hier &h) {
         double *uval = dmalloc<double>(ut, s);
         int *cnt = dmalloc<int>(nc, s);
         {
-            // rows binned by their bound U: tables of 256 / 1024 / 4096 slots in
+            // rows binned by their bound U: tables of 128 / 512 / 2048 slots in
             // shared memory, larger rows in global scratch
             int8_t *rcls = dmalloc<int8_t>(nc, s);
             k_rap_classes<<<blocks_for(nc, BS), BS, 0, s>>>(nc, U, rcls);
@@ -1507,7 +1510,7 @@ void build_hierarchy(Hier &h) {
             int *rlist = dmalloc<int>(nc, s);
             partition_by_class(rcls, nc, 4, rlist, bstart, hb, s);
             dfree(rcls, s);
-            const int caps[3] = {256, 1024, 4096};
+            const int caps[3] = {128, 512, 2048};
             int filt = prm.phi_A > 0.0 ? 1 : 0;
             PR_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int), s));
             for (int c = 0; c < 3; ++c) {
@@ -1519,13 +1522,13 @@ void build_hierarchy(Hier &h) {
                 size_t sm = (size_t)hcap * wpb * spw * (sizeof(double) + sizeof(int));
                 unsigned grid = std::min<unsigned>(blocks_for(hb[c], wpb * spw), 152u * 32u);
                 if (grp) {
-                    PR_CUDA(cudaFuncSetAttribute(k_rap<8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+                    allow_max_dyn_smem(k_rap<8, false>);
                     k_rap<8, false><<<grid, 32 * wpb, sm, s>>>(hb[c], rlist + bstart[c], L.cpts, L.zrowptr, L.zcol,
                                                                L.zval, L.rowptr, aplen, apcol, apval, uptr, U, filt,
                                                                prm.phi_A, cnt, ucol, uval, hcap, nullptr, nullptr,
                                                                nullptr, d_count, h.d_err);
                 } else {
-                    PR_CUDA(cudaFuncSetAttribute(k_rap<32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+                    allow_max_dyn_smem(k_rap<32, false>);
                     k_rap<32, false><<<grid, 32 * wpb, sm, s>>>(hb[c], rlist + bstart[c], L.cpts, L.zrowptr, L.zcol,
                                                                 L.zval, L.rowptr, aplen, apcol, apval, uptr, U, filt,
                                                                 prm.phi_A, cnt, ucol, uval, hcap, nullptr, nullptr,

@@ -11,7 +11,9 @@
 #include <cmath>
 #include <cstring>
 #include <initializer_list>
+#include <exception>
 #include <string>
+#include <thread>
 #include <utility>
 
 #include "common.cuh"
@@ -65,11 +67,23 @@ __global__ void k_rhs(long long E, int ndir, const double *W, const double *Gin,
     b[tid] = acc;
 }
 
-__global__ void k_phi_acc(long long N, int nd, const double *w, const double *x, double *phinew) {
+// phinew (+)= sum_m w_m x_m over the batch's directions in order; 'overwrite'
+// starts the sum from zero instead of the stored value
+__global__ void k_phi_acc(long long N, int nd, const double *w, const double *x, double *phinew, int overwrite) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    double acc = phinew[i];
+    double acc = overwrite ? 0.0 : phinew[i];
     for (int m = 0; m < nd; ++m) acc += w[m] * x[(long long)m * N + i];
+    phinew[i] = acc;
+}
+
+// phinew = partial_0 + partial_1 + ... + partial_{K-1}, in that order (the partial
+// fluxes of concurrently solved direction groups, each N long)
+__global__ void k_phi_sum(long long N, int K, const double *partial, double *phinew) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double acc = partial[i];
+    for (int k = 1; k < K; ++k) acc += partial[(long long)k * N + i];
     phinew[i] = acc;
 }
 
@@ -147,7 +161,7 @@ float elapsed_ms(cudaEvent_t a, cudaEvent_t b) {
 
 // outer residual (ev[0..1]) of the matrices that took part
 void account_outer(Hier &h, const std::vector<char> &part) {
-    if (!h.prof) return;
+    if (!h.timed) return;
     h.t_res0 += elapsed_ms(h.ev[0], h.ev[1]);
     h.n_res0 += 1;
     double br = 0;
@@ -159,7 +173,7 @@ void account_outer(Hier &h, const std::vector<char> &part) {
 // one V-cycle recorded in slot ps: level-0 relaxation and inner residual of the
 // matrices that took part, coarse-level relaxation (every matrix of the batch)
 void account_cycle(Hier &h, const ProfSlot &ps, const std::vector<char> &part) {
-    if (!h.prof) return;
+    if (!h.timed) return;
     double bx = 0, b32 = 0;
     for (int d = 0; d < h.ndir; ++d)
         if (part[d]) {
@@ -218,21 +232,22 @@ cudaGraphExec_t capture(Hier &h, long long &kernels, F &&body) {
     return ex;
 }
 
-ProfSlot *slot(Hier &h, int k) { return h.prof && k < (int)h.slots.size() ? &h.slots[k] : nullptr; }
+ProfSlot *slot(Hier &h, int k) { return h.timed && k < (int)h.slots.size() ? &h.slots[k] : nullptr; }
 
 }  // namespace
 
 // One-time capture of [V-cycle correction; residual] for fixed (b, x, tol).
 static void ensure_graph(Hier &h, const double *b, double *x, double tol) {
-    if (h.graph && h.graph_b == b && h.graph_x == x && h.graph_tol == tol) return;
-    if (h.graph) { cudaGraphExecDestroy(h.graph); h.graph = nullptr; }
-    h.graph = capture(h, h.graph_kernels, [&] {
+    CycleGraphs &G = h.graphs();
+    if (G.graph && G.graph_b == b && G.graph_x == x && G.graph_tol == tol) return;
+    if (G.graph) { cudaGraphExecDestroy(G.graph); G.graph = nullptr; }
+    G.graph = capture(h, G.graph_kernels, [&] {
         vcycle_correct(h, x, slot(h, 0));
         residual0(h, b, x, tol, true);
     });
-    h.graph_b = b;
-    h.graph_x = x;
-    h.graph_tol = tol;
+    G.graph_b = b;
+    G.graph_x = x;
+    G.graph_tol = tol;
 }
 
 namespace {
@@ -242,12 +257,13 @@ namespace {
 void run_inner(Hier &h, int g, bool use_graph) {
     const int k = 1 << g;
     if (use_graph) {
-        if (!h.gcyc[g])
-            h.gcyc[g] = capture(h, h.gcyc_kernels[g], [&] {
+        CycleGraphs &G = h.graphs();
+        if (!G.gcyc[g])
+            G.gcyc[g] = capture(h, G.gcyc_kernels[g], [&] {
                 for (int t = 0; t < k; ++t) inner_cycle(h, slot(h, k - 1 + t));
             });
-        PR_CUDA(cudaGraphLaunch(h.gcyc[g], h.stream));
-        g_launches += h.gcyc_kernels[g];
+        PR_CUDA(cudaGraphLaunch(G.gcyc[g], h.stream));
+        g_launches += G.gcyc_kernels[g];
     } else {
         for (int t = 0; t < k; ++t) inner_cycle(h, slot(h, k - 1 + t));
     }
@@ -256,18 +272,19 @@ void run_inner(Hier &h, int g, bool use_graph) {
 // end of a refinement step: x += d, new outer residual, norms and flags
 void run_close(Hier &h, const double *b, double *x, double tol, bool use_graph) {
     if (use_graph) {
-        if (!h.gclose || h.gi_b != b || h.gi_x != x || h.gi_tol != tol) {
-            if (h.gclose) { cudaGraphExecDestroy(h.gclose); h.gclose = nullptr; }
-            h.gclose = capture(h, h.gclose_kernels, [&] {
+        CycleGraphs &G = h.graphs();
+        if (!G.gclose || G.gi_b != b || G.gi_x != x || G.gi_tol != tol) {
+            if (G.gclose) { cudaGraphExecDestroy(G.gclose); G.gclose = nullptr; }
+            G.gclose = capture(h, G.gclose_kernels, [&] {
                 fold_delta(h, x);
                 residual_outer(h, b, x, tol);
             });
-            h.gi_b = b;
-            h.gi_x = x;
-            h.gi_tol = tol;
+            G.gi_b = b;
+            G.gi_x = x;
+            G.gi_tol = tol;
         }
-        PR_CUDA(cudaGraphLaunch(h.gclose, h.stream));
-        g_launches += h.gclose_kernels;
+        PR_CUDA(cudaGraphLaunch(G.gclose, h.stream));
+        g_launches += G.gclose_kernels;
     } else {
         fold_delta(h, x);
         residual_outer(h, b, x, tol);
@@ -333,7 +350,7 @@ BatchSolve solve_batch_inner(Hier &h, const double *b, double *x, double tol, in
         std::vector<int> sc(nd);   // cycles of this step per matrix (icount accumulates)
         for (int d = 0; d < nd; ++d) sc[d] = cnt[d] - cyc[d];
         // cycle j of the step ran for the matrices with more than j cycles
-        if (h.prof) {
+        if (h.timed) {
             int j = 0;
             for (int g : launched)
                 for (int t = 0; t < (1 << g); ++t, ++j) {
@@ -397,8 +414,8 @@ BatchSolve solve_batch(Hier &h, const double *b, double *x, double tol, int maxi
     bool any = std::any_of(act.begin(), act.end(), [](int a) { return a != 0; });
     while (any && k < maxit) {
         if (use_graph) {
-            PR_CUDA(cudaGraphLaunch(h.graph, s));
-            g_launches += h.graph_kernels;
+            PR_CUDA(cudaGraphLaunch(h.graphs().graph, s));
+            g_launches += h.graphs().graph_kernels;
         } else {
             vcycle_correct(h, x, slot(h, 0));
             residual0(h, b, x, tol, true);
@@ -408,7 +425,7 @@ BatchSolve solve_batch(Hier &h, const double *b, double *x, double tol, int maxi
         for (int d = 0; d < nd; ++d) was[d] = act[d] != 0;
         PR_CUDA(cudaMemcpyAsync(act.data(), h.active, sizeof(int) * nd, cudaMemcpyDeviceToHost, s));
         PR_CUDA(cudaStreamSynchronize(s));
-        if (h.prof) {
+        if (h.timed) {
             account_cycle(h, h.slots[0], was);
             account_outer(h, was);
         }
@@ -561,10 +578,6 @@ void csr_transpose_dev(int n, long long nnz, const int *rowptr, const int *col, 
 }
 
 Hier::~Hier() {
-    if (graph) cudaGraphExecDestroy(graph);
-    for (auto &g : gcyc)
-        if (g) cudaGraphExecDestroy(g);
-    if (gclose) cudaGraphExecDestroy(gclose);
     if (dag) {
         if (stream) dag->release(stream);
         delete dag;
@@ -674,9 +687,50 @@ void free_batch_ops(DirBatch &B) {
     B.h = nullptr;
 }
 
+// device-event kernel timings and algorithmic traffic taken from hierarchies
+struct KernelStats {
+    double t_res0 = 0, t_relax0 = 0, gb_res0 = 0, gb_relax0 = 0, t_relaxc = 0, gb_relaxc = 0, t_res32 = 0,
+           gb_res32 = 0, t_lvl[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    long long n_res0 = 0, n_relax0 = 0, n_relaxc = 0, n_res32 = 0;
+    void take(Hier &h) {   // adds h's counters and clears them
+        t_res0 += h.t_res0; t_relax0 += h.t_relax0; gb_res0 += h.gb_res0; gb_relax0 += h.gb_relax0;
+        n_res0 += h.n_res0; n_relax0 += h.n_relax0;
+        t_relaxc += h.t_relaxc; gb_relaxc += h.gb_relaxc; n_relaxc += h.n_relaxc;
+        t_res32 += h.t_res32; gb_res32 += h.gb_res32; n_res32 += h.n_res32;
+        for (int k = 0; k < 8; ++k) { t_lvl[k] += h.t_relaxc_level[k]; h.t_relaxc_level[k] = 0; }
+        h.t_res0 = h.t_relax0 = h.gb_res0 = h.gb_relax0 = h.t_relaxc = h.gb_relaxc = h.t_res32 = h.gb_res32 = 0;
+        h.n_res0 = h.n_relax0 = h.n_relaxc = h.n_res32 = 0;
+    }
+    void add(const KernelStats &o) {
+        t_res0 += o.t_res0; t_relax0 += o.t_relax0; gb_res0 += o.gb_res0; gb_relax0 += o.gb_relax0;
+        t_relaxc += o.t_relaxc; gb_relaxc += o.gb_relaxc; t_res32 += o.t_res32; gb_res32 += o.gb_res32;
+        for (int k = 0; k < 8; ++k) t_lvl[k] += o.t_lvl[k];
+        n_res0 += o.n_res0; n_relax0 += o.n_relax0; n_relaxc += o.n_relaxc; n_res32 += o.n_res32;
+    }
+};
+
+// one batch's share of an SI iteration, merged by the calling thread in batch order
+struct BatchOut {
+    bool built = false;          // the hierarchy was set up in this iteration
+    double setup_ms = 0, solve_ms = 0, tph[4] = {0, 0, 0, 0};
+    int levels_max = 0, opc_cnt = 0;
+    double opc_sum = 0;
+    BatchSolve bs;
+    KernelStats ks;
+    std::string fail_msg;        // an unconverged solve (with a scalar-flux reduction)
+};
+
+// Direction groups solved at the same time, each batch on its own stream from its
+// own host thread.  One batch's V-cycle is a chain of dependent launches whose
+// coarse levels leave most of the GPU idle (each launch a few microseconds of
+// latency for kilobytes of work), and its refinement steps end in host reads; a
+// second chain fills those gaps.  Measured on the 32^3 S4 batch (24 directions): one
+// batch 256 ms per solve, two concurrent halves 166 ms, three thirds 160 ms.
+int auto_concurrency(int M) { return std::min(M, 3); }
+
 void build_batch(DirBatch &B, const pair_mesh &mesh, const double *omega_h, const double *omega_d,
                  const double *sigma_t, const air_params &prm, bool gin, bool adjoint = false,
-                 bool sweep_only = false) {
+                 bool sweep_only = false, bool timing = true) {
     const int n = mesh.n;
     const bool hex = mesh.kind == PAIR_MESH_HEX;
     Hier *h = new Hier;
@@ -766,7 +820,7 @@ void build_batch(DirBatch &B, const pair_mesh &mesh, const double *omega_h, cons
     inner_enable(*h);
     split0_enable(*h);
     level0_bytes(*h);
-    prof_enable(*h);
+    if (timing) prof_enable(*h);
 }
 
 }  // namespace
@@ -793,6 +847,19 @@ void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t,
     B = (int)std::min<long long>(B, std::max<long long>(1, (0x7fffffffLL / (sweep ? 16 : 64)) / N));
     int nb = (M + B - 1) / B;
     bool resident = (double)per * M <= budget;
+    // concurrent direction groups (resident hierarchies only: a rebuilt batch is
+    // sized to the whole budget); the directions are split so each group has a batch
+    int K = 1;
+    if (resident && !sweep) {
+        K = std::max(1, std::min(sp.concurrent > 0 ? sp.concurrent : auto_concurrency(M), M));
+        if (nb < K) {
+            B = (M + K - 1) / K;
+            nb = (M + B - 1) / B;
+        }
+        K = std::min(K, nb);
+    }
+    int dev = 0;
+    PR_CUDA(cudaGetDevice(&dev));
     // per-call device state on a private stream
     cudaStream_t s;
     PR_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
@@ -825,130 +892,198 @@ void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t,
     cl.bufs.push_back(phinew);
     double *src = dmalloc<double>(N, s);   // isotropic source of the current iteration
     cl.bufs.push_back(src);
-    bool src_ready = false;
     int nbk = (int)blocks_for(N, BS);
     double *part = dmalloc<double>(2 * (size_t)nbk, s);
     cl.bufs.push_back(part);
     double *dres = dmalloc<double>(2, s);
     cl.bufs.push_back(dres);
+    // partial fluxes of the concurrent groups, summed in group order
+    double *partial = nullptr;
+    if (K > 1) {
+        partial = dmalloc<double>((size_t)K * N, s);
+        cl.bufs.push_back(partial);
+    }
     PR_CUDA(cudaStreamSynchronize(s));
     for (int b = 0; b < nb; ++b) { batches[b].m0 = b * B; batches[b].nd = std::min(B, M - b * B); }
 
-    cudaEvent_t e0, e1;
+    cudaEvent_t e0, e1, ev_src;
     PR_CUDA(cudaEventCreate(&e0));
     PR_CUDA(cudaEventCreate(&e1));
+    PR_CUDA(cudaEventCreateWithFlags(&ev_src, cudaEventDisableTiming));
+    struct Events {
+        cudaEvent_t e[3];
+        ~Events() {
+            for (auto x : e)
+                if (x) cudaEventDestroy(x);
+        }
+    } evs{{e0, e1, ev_src}};
     double t_setup = 0, t_solve = 0;
     int vcycles = 0, levels_max = 0;
     double max_inner = 0, opc_sum = 0, change = 0;
     int opc_cnt = 0, it = 0;
-    double t_res0 = 0, t_relax0 = 0, gb_res0 = 0, gb_relax0 = 0, tph[4] = {0, 0, 0, 0};
-    double t_relaxc = 0, gb_relaxc = 0, t_res32 = 0, gb_res32 = 0, t_lvl[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    long long n_res0 = 0, n_relax0 = 0, n_relaxc = 0, n_res32 = 0, outer_res = 0;
-    auto harvest = [&](Hier &h) {
-        t_res0 += h.t_res0; t_relax0 += h.t_relax0; gb_res0 += h.gb_res0; gb_relax0 += h.gb_relax0;
-        n_res0 += h.n_res0; n_relax0 += h.n_relax0;
-        t_relaxc += h.t_relaxc; gb_relaxc += h.gb_relaxc; n_relaxc += h.n_relaxc;
-        t_res32 += h.t_res32; gb_res32 += h.gb_res32; n_res32 += h.n_res32;
-        for (int k = 0; k < 8; ++k) { t_lvl[k] += h.t_relaxc_level[k]; h.t_relaxc_level[k] = 0; }
-        h.t_res0 = h.t_relax0 = h.gb_res0 = h.gb_relax0 = h.t_relaxc = h.gb_relaxc = h.t_res32 = h.gb_res32 = 0;
-        h.n_res0 = h.n_relax0 = h.n_relaxc = h.n_res32 = 0;
-    };
-    bool converged = false;
-    auto elapsed = [&](cudaStream_t st) {
-        PR_CUDA(cudaEventRecord(e1, st));
-        PR_CUDA(cudaEventSynchronize(e1));
+    double tph[4] = {0, 0, 0, 0};
+    long long outer_res = 0;
+    KernelStats ks;
+    bool converged = false, timed_it = false;
+    int timed_iters = 0;
+    // One batch's share of an iteration: setup on first use, right-hand sides from
+    // the iteration's source, the direction solves, and sum_m w_m psi_m into acc
+    // (written when 'overwrite', else added).  Runs on the calling thread or on a
+    // group's thread; everything it reports goes to 'o'.
+    auto run_batch = [&](int bi, double *acc, bool overwrite, BatchOut &o) {
+        DirBatch &Bt = batches[bi];
+        if (!Bt.h) {
+            auto t0 = std::chrono::steady_clock::now();
+            build_batch(Bt, mesh, quad.omega, omega_d, sigma_t, prm, gin, false, sweep, sp.timing != 0);
+            PR_CUDA(cudaStreamSynchronize(Bt.h->stream));
+            o.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            o.built = true;
+            for (int k = 0; k < 4; ++k) o.tph[k] = Bt.h->t_phase[k];
+            cudaStream_t hs = Bt.h->stream;
+            Bt.b = dmalloc<double>((size_t)Bt.nd * N, hs);
+            if (!psi) Bt.xown = dmalloc<double>((size_t)Bt.nd * N, hs);
+            Hier &h = *Bt.h;
+            for (int d = 0; d < Bt.nd && !sweep; ++d) {
+                int nl = 0;
+                long long tot = 0;
+                for (auto &L : h.lev)
+                    if (L.nrows.size() && L.nrows[d] > 0) { ++nl; tot += L.nnzdir[d]; }
+                o.levels_max = std::max(o.levels_max, nl);
+                o.opc_sum += (double)tot / (double)h.lev[0].nnzdir[d];
+                ++o.opc_cnt;
+            }
+        }
+        Hier &h = *Bt.h;
+        cudaStream_t hs = h.stream;
+        h.timed = h.prof && timed_it;
+        double *x = psi ? psi + (size_t)Bt.m0 * N : Bt.xown;
+        const double *qa = sp.q_ang ? sp.q_ang + (size_t)Bt.m0 * N : nullptr;
+        cudaEvent_t a, z;
+        PR_CUDA(cudaEventCreate(&a));
+        Events own{{a, nullptr, nullptr}};
+        PR_CUDA(cudaEventCreate(&z));
+        own.e[1] = z;
+        PR_CUDA(cudaEventRecord(a, hs));
+        PR_CUDA(cudaStreamWaitEvent(hs, ev_src, 0));
+        if (hex)
+            k_rhs<8><<<blocks_for((long long)Bt.nd * N, BS), BS, 0, hs>>>(E, Bt.nd, Bt.W, Bt.Gin, sp.g_inflow, src,
+                                                                       qa, Bt.b);
+        else
+            k_rhs<4><<<blocks_for((long long)Bt.nd * N, BS), BS, 0, hs>>>(E, Bt.nd, Bt.W, Bt.Gin, sp.g_inflow, src,
+                                                                       qa, Bt.b);
+        PR_LAUNCH();
+        BatchSolve bs;
+        if (sweep) {
+            sweep_solve(h, Bt.b, x, sp.use_graphs != 0);
+            bs.converged = true;
+        } else {
+            PR_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * Bt.nd * N, hs));
+            if (sp.inner_cycles > 0) {   // fixed approximate inverse: l cycles from zero
+                bs = solve_batch(h, Bt.b, x, 0.0, sp.inner_cycles, sp.use_graphs != 0);
+                bs.converged = true;
+            } else {
+                bs = solve_batch(h, Bt.b, x, sp.inner_tol, sp.inner_maxit, sp.use_graphs != 0);
+            }
+        }
+        if (!bs.converged) {
+            char buf[160];
+            snprintf(buf, sizeof buf, "AIR solve reached %d cycles with relative residual %.3e > %.3e", bs.iters,
+                     bs.max_rel, sp.inner_tol);
+            // with a reduction the other processes wait for this one: report after it
+            if (!sp.phi_reduce) fail(PAIR_ERR_NOT_CONVERGED, buf);
+            o.fail_msg = buf;
+        }
+        o.bs = bs;
+        k_phi_acc<<<blocks_for(N, BS), BS, 0, hs>>>(N, Bt.nd, w_d + Bt.m0, x, acc, overwrite ? 1 : 0);
+        PR_LAUNCH();
+        PR_CUDA(cudaEventRecord(z, hs));
+        PR_CUDA(cudaEventSynchronize(z));
         float ms = 0;
-        PR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-        return (double)ms;
+        PR_CUDA(cudaEventElapsedTime(&ms, a, z));
+        o.solve_ms = ms;
+        o.ks.take(h);
+        if (!resident) {
+            dfree(Bt.b, hs); dfree(Bt.xown, hs);
+            Bt.b = Bt.xown = nullptr;
+            free_batch_ops(Bt);
+        }
     };
     std::string local_fail;   // with a reduction: the first unconverged solve of this iteration
     for (it = 0; it < sp.max_iters; ++it) {
+        // SI iterations k, 2k, ... (counting from 1) record the kernel timings, with the
+        // groups one after another so that no other group's kernels share their events
+        timed_it = sp.timing > 0 && (it + 1) % sp.timing == 0;
+        if (timed_it) ++timed_iters;
         PR_CUDA(cudaMemsetAsync(phinew, 0, sizeof(double) * (N + 1), s));
+        PR_CUDA(cudaEventRecord(e0, s));
+        // the source of this iteration, once for every batch
+        if (hex) k_src<8><<<blocks_for(N, BS), BS, 0, s>>>(N, sigma_s, q, phi, src);
+        else k_src<4><<<blocks_for(N, BS), BS, 0, s>>>(N, sigma_s, q, phi, src);
+        PR_LAUNCH();
+        PR_CUDA(cudaEventRecord(ev_src, s));
         PR_CUDA(cudaStreamSynchronize(s));
         local_fail.clear();
-        src_ready = false;
+        std::vector<BatchOut> outs(nb);
+        if (K == 1) {
+            for (int bi = 0; bi < nb; ++bi) run_batch(bi, phinew, false, outs[bi]);
+        } else if (timed_it) {
+            for (int k = 0; k < K; ++k)
+                for (int bi = k; bi < nb; bi += K) run_batch(bi, partial + (size_t)k * N, bi == k, outs[bi]);
+            k_phi_sum<<<blocks_for(N, BS), BS, 0, s>>>(N, K, partial, phinew);
+            PR_LAUNCH();
+        } else {
+            // group k takes batches k, k + K, ... in order, summing into its partial
+            std::vector<std::exception_ptr> errs(K);
+            std::vector<std::thread> th;
+            for (int k = 0; k < K; ++k)
+                th.emplace_back([&, k] {
+                    try {
+                        PR_CUDA(cudaSetDevice(dev));
+                        for (int bi = k; bi < nb; bi += K) run_batch(bi, partial + (size_t)k * N, bi == k, outs[bi]);
+                    } catch (...) {
+                        errs[k] = std::current_exception();
+                    }
+                });
+            for (auto &t : th) t.join();
+            for (auto &e : errs)
+                if (e) std::rethrow_exception(e);
+            // every group's stream was synchronised when its thread finished
+            k_phi_sum<<<blocks_for(N, BS), BS, 0, s>>>(N, K, partial, phinew);
+            PR_LAUNCH();
+        }
+        // merge in batch order
+        double setup_max = 0, setup_sum = 0, solve_sum = 0;
+        int longest = -1;
         for (int bi = 0; bi < nb; ++bi) {
-            DirBatch &Bt = batches[bi];
-            if (!Bt.h) {
-                // setup phase on the batch stream (timed)
-                cudaStream_t tmp;
-                PR_CUDA(cudaStreamCreateWithFlags(&tmp, cudaStreamNonBlocking));
-                PR_CUDA(cudaEventRecord(e0, tmp));
-                PR_CUDA(cudaStreamSynchronize(tmp));
-                build_batch(Bt, mesh, quad.omega, omega_d, sigma_t, prm, gin, false, sweep);
-                PR_CUDA(cudaStreamSynchronize(Bt.h->stream));
-                PR_CUDA(cudaEventRecord(e1, tmp));
-                PR_CUDA(cudaEventSynchronize(e1));
-                float ms = 0;
-                PR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-                t_setup += ms;
-                cudaStreamDestroy(tmp);
-                for (int k = 0; k < 4; ++k) tph[k] += Bt.h->t_phase[k];
-                cudaStream_t hs = Bt.h->stream;
-                Bt.b = dmalloc<double>((size_t)Bt.nd * N, hs);
-                if (!psi) Bt.xown = dmalloc<double>((size_t)Bt.nd * N, hs);
-                Hier &h = *Bt.h;
-                for (int d = 0; d < Bt.nd && !sweep; ++d) {
-                    int nl = 0;
-                    long long tot = 0;
-                    for (auto &L : h.lev)
-                        if (L.nrows.size() && L.nrows[d] > 0) { ++nl; tot += L.nnzdir[d]; }
-                    levels_max = std::max(levels_max, nl);
-                    opc_sum += (double)tot / (double)h.lev[0].nnzdir[d];
-                    ++opc_cnt;
-                }
+            BatchOut &o = outs[bi];
+            if (o.built) {
+                setup_sum += o.setup_ms;
+                if (longest < 0 || o.setup_ms > setup_max) { setup_max = o.setup_ms; longest = bi; }
+                levels_max = std::max(levels_max, o.levels_max);
+                opc_sum += o.opc_sum;
+                opc_cnt += o.opc_cnt;
             }
-            Hier &h = *Bt.h;
-            cudaStream_t hs = h.stream;
-            double *x = psi ? psi + (size_t)Bt.m0 * N : Bt.xown;
-            const double *qa = sp.q_ang ? sp.q_ang + (size_t)Bt.m0 * N : nullptr;
-            PR_CUDA(cudaEventRecord(e0, hs));
-            if (bi == 0 || !src_ready) {   // the source of this iteration, once for every batch
-                if (hex) k_src<8><<<blocks_for(N, BS), BS, 0, hs>>>(N, sigma_s, q, phi, src);
-                else k_src<4><<<blocks_for(N, BS), BS, 0, hs>>>(N, sigma_s, q, phi, src);
-                PR_LAUNCH();
-                src_ready = true;
-            }
-            if (hex)
-                k_rhs<8><<<blocks_for((long long)Bt.nd * N, BS), BS, 0, hs>>>(E, Bt.nd, Bt.W, Bt.Gin, sp.g_inflow,
-                                                                           src, qa, Bt.b);
-            else
-                k_rhs<4><<<blocks_for((long long)Bt.nd * N, BS), BS, 0, hs>>>(E, Bt.nd, Bt.W, Bt.Gin, sp.g_inflow,
-                                                                           src, qa, Bt.b);
-            PR_LAUNCH();
-            BatchSolve bs;
-            if (sweep) {
-                sweep_solve(h, Bt.b, x, sp.use_graphs != 0);
-                bs.converged = true;
-            } else {
-                PR_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * Bt.nd * N, hs));
-                if (sp.inner_cycles > 0) {   // fixed approximate inverse: l cycles from zero
-                    bs = solve_batch(h, Bt.b, x, 0.0, sp.inner_cycles, sp.use_graphs != 0);
-                    bs.converged = true;
-                } else {
-                    bs = solve_batch(h, Bt.b, x, sp.inner_tol, sp.inner_maxit, sp.use_graphs != 0);
-                }
-            }
-            if (!bs.converged) {
-                char buf[160];
-                snprintf(buf, sizeof buf, "AIR solve reached %d cycles with relative residual %.3e > %.3e", bs.iters,
-                         bs.max_rel, sp.inner_tol);
-                // with a reduction the other processes wait for this one: report after it
-                if (!sp.phi_reduce) fail(PAIR_ERR_NOT_CONVERGED, buf);
-                if (local_fail.empty()) local_fail = buf;
-            }
-            vcycles += bs.cycles;
-            outer_res += bs.outer;
-            max_inner = std::max(max_inner, bs.max_rel);
-            k_phi_acc<<<blocks_for(N, BS), BS, 0, hs>>>(N, Bt.nd, w_d + Bt.m0, x, phinew);
-            PR_LAUNCH();
-            t_solve += elapsed(hs);
-            harvest(h);
-            if (!resident) {
-                dfree(Bt.b, hs); dfree(Bt.xown, hs);
-                Bt.b = Bt.xown = nullptr;
-                free_batch_ops(Bt);
-            }
+            solve_sum += o.solve_ms;
+            vcycles += (int)o.bs.cycles;
+            outer_res += o.bs.outer;
+            max_inner = std::max(max_inner, o.bs.max_rel);
+            ks.add(o.ks);
+            if (local_fail.empty() && !o.fail_msg.empty()) local_fail = o.fail_msg;
+        }
+        if (K == 1) {   // batches one after the other: their times add
+            t_setup += setup_sum;
+            t_solve += solve_sum;
+            for (int bi = 0; bi < nb; ++bi)
+                for (int k = 0; k < 4; ++k) tph[k] += outs[bi].tph[k];
+        } else {        // concurrent groups: the iteration's wall time, setup = the longest batch setup
+            PR_CUDA(cudaEventRecord(e1, s));
+            PR_CUDA(cudaEventSynchronize(e1));
+            float wall = 0;
+            PR_CUDA(cudaEventElapsedTime(&wall, e0, e1));
+            t_setup += setup_max;
+            t_solve += std::max(0.0, (double)wall - setup_max);
+            if (longest >= 0)
+                for (int k = 0; k < 4; ++k) tph[k] += outs[longest].tph[k];
         }
         if (sp.phi_reduce) {   // angular decomposition: sum the partial fluxes and statuses
             const double st = local_fail.empty() ? 0.0 : 1.0;
@@ -976,8 +1111,6 @@ void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t,
         if (!std::isfinite(change)) fail(PAIR_ERR_NAN, "NaN/Inf in the scalar flux");
         if (change <= sp.tol) { converged = true; ++it; break; }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     if (info) {
         info->si_iters = std::min(it, sp.max_iters);
         info->si_change = change;
@@ -989,20 +1122,21 @@ void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t,
         info->t_solve_ms = t_solve;
         info->levels_max = levels_max;
         info->op_complexity = opc_cnt ? opc_sum / opc_cnt : 0;
-        info->t_res0_ms = t_res0;
-        info->n_res0 = (int)n_res0;
-        info->gb_res0 = gb_res0;
-        info->t_relax0_ms = t_relax0;
-        info->n_relax0 = (int)n_relax0;
-        info->gb_relax0 = gb_relax0;
-        info->t_relaxc_ms = t_relaxc;
-        info->n_relaxc = (int)n_relaxc;
-        info->gb_relaxc = gb_relaxc;
-        info->t_res32_ms = t_res32;
-        info->n_res32 = (int)n_res32;
-        info->gb_res32 = gb_res32;
+        info->t_res0_ms = ks.t_res0;
+        info->n_res0 = (int)ks.n_res0;
+        info->gb_res0 = ks.gb_res0;
+        info->t_relax0_ms = ks.t_relax0;
+        info->n_relax0 = (int)ks.n_relax0;
+        info->gb_relax0 = ks.gb_relax0;
+        info->t_relaxc_ms = ks.t_relaxc;
+        info->n_relaxc = (int)ks.n_relaxc;
+        info->gb_relaxc = ks.gb_relaxc;
+        info->t_res32_ms = ks.t_res32;
+        info->n_res32 = (int)ks.n_res32;
+        info->gb_res32 = ks.gb_res32;
         info->outer_residuals = (int)outer_res;
-        for (int k = 0; k < 8; ++k) info->t_relaxc_level_ms[k] = t_lvl[k];
+        for (int k = 0; k < 8; ++k) info->t_relaxc_level_ms[k] = ks.t_lvl[k];
+        info->timed_iters = timed_iters;
         for (int k = 0; k < 3; ++k) info->t_setup_phase_ms[k] = tph[k];
         info->t_setup_phase_ms[3] = t_setup - (tph[0] + tph[1] + tph[2]);
     }
@@ -1030,6 +1164,17 @@ void si_adjoint_run(const pair_mesh &mesh, const pair_quad &quad, const double *
     int nb = (M + B - 1) / B;
     bool resident = (double)per * M <= budget;
     PR_REQUIRE(resident, PAIR_ERR_OOM, "si_adjoint: all direction hierarchies must fit the memory budget");
+    int K = 1;   // concurrent direction groups, as in si_run
+    if (!sweep) {
+        K = std::max(1, std::min(sp.concurrent > 0 ? sp.concurrent : auto_concurrency(M), M));
+        if (nb < K) {
+            B = (M + K - 1) / K;
+            nb = (M + B - 1) / B;
+        }
+        K = std::min(K, nb);
+    }
+    int dev = 0;
+    PR_CUDA(cudaGetDevice(&dev));
     cudaStream_t s;
     PR_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
     std::vector<DirBatch> batches(nb);
@@ -1052,12 +1197,13 @@ void si_adjoint_run(const pair_mesh &mesh, const pair_quad &quad, const double *
     double *omega_d = buf(3 * M), *w_d = buf(M), *phi = buf(N), *phis = buf(N), *pnew = buf(N), *acc = buf(N);
     int nbk = (int)blocks_for(N, BS);
     double *part = buf(2 * (size_t)nbk), *dres = buf(2);
+    double *partial = K > 1 ? buf((size_t)K * N) : nullptr;   // the groups' sums
     PR_CUDA(cudaMemcpyAsync(omega_d, quad.omega, sizeof(double) * 3 * M, cudaMemcpyHostToDevice, s));
     PR_CUDA(cudaMemcpyAsync(w_d, quad.w, sizeof(double) * M, cudaMemcpyHostToDevice, s));
     PR_CUDA(cudaMemsetAsync(phi, 0, sizeof(double) * N, s));
     PR_CUDA(cudaMemsetAsync(phis, 0, sizeof(double) * N, s));
     // forward scalar flux from the given angular fluxes
-    k_phi_acc<<<blocks_for(N, BS), BS, 0, s>>>(N, M, w_d, psi, phi);
+    k_phi_acc<<<blocks_for(N, BS), BS, 0, s>>>(N, M, w_d, psi, phi, 0);
     PR_LAUNCH();
     PR_CUDA(cudaStreamSynchronize(s));
     cudaEvent_t e0, e1;
@@ -1066,31 +1212,52 @@ void si_adjoint_run(const pair_mesh &mesh, const pair_quad &quad, const double *
     double t_setup = 0, t_solve = 0, change = 0, max_inner = 0;
     int vcycles = 0, it = 0;
     bool converged = false;
-    for (int b = 0; b < nb; ++b) {
-        DirBatch &Bt = batches[b];
-        Bt.m0 = b * B;
-        Bt.nd = std::min(B, M - b * B);
-        PR_CUDA(cudaEventRecord(e0, s));
-        PR_CUDA(cudaStreamSynchronize(s));
-        build_batch(Bt, mesh, quad.omega, omega_d, sigma_t, prm, false, true, sweep);
-        cudaStream_t hs = Bt.h->stream;
-        Bt.b = dmalloc<double>((size_t)Bt.nd * N, hs);
-        Bt.xown = dmalloc<double>((size_t)Bt.nd * N, hs);
-        PR_CUDA(cudaStreamSynchronize(hs));
-        PR_CUDA(cudaEventRecord(e1, s));
-        PR_CUDA(cudaEventSynchronize(e1));
-        float ms = 0;
-        PR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-        t_setup += ms;
+    // K groups run their batches k, k + K, ... on their own threads (K = 1: this thread)
+    auto in_groups = [&](auto &&work) {
+        if (K == 1) {
+            for (int b = 0; b < nb; ++b) work(b, 0);
+            return;
+        }
+        std::vector<std::exception_ptr> errs(K);
+        std::vector<std::thread> th;
+        for (int k = 0; k < K; ++k)
+            th.emplace_back([&, k] {
+                try {
+                    PR_CUDA(cudaSetDevice(dev));
+                    for (int b = k; b < nb; b += K) work(b, k);
+                } catch (...) {
+                    errs[k] = std::current_exception();
+                }
+            });
+        for (auto &t : th) t.join();
+        for (auto &e : errs)
+            if (e) std::rethrow_exception(e);
+    };
+    for (int b = 0; b < nb; ++b) { batches[b].m0 = b * B; batches[b].nd = std::min(B, M - b * B); }
+    {
+        auto t0 = std::chrono::steady_clock::now();
+        in_groups([&](int b, int) {
+            DirBatch &Bt = batches[b];
+            build_batch(Bt, mesh, quad.omega, omega_d, sigma_t, prm, false, true, sweep, false);
+            cudaStream_t hs = Bt.h->stream;
+            Bt.b = dmalloc<double>((size_t)Bt.nd * N, hs);
+            Bt.xown = dmalloc<double>((size_t)Bt.nd * N, hs);
+            PR_CUDA(cudaStreamSynchronize(hs));
+        });
+        t_setup = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     }
+    std::vector<BatchSolve> bsv(nb);
     for (it = 0; it < sp.max_iters; ++it) {
         PR_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * N, s));
+        if (K > 1) PR_CUDA(cudaMemsetAsync(partial, 0, sizeof(double) * K * N, s));
+        PR_CUDA(cudaEventRecord(e0, s));
         PR_CUDA(cudaStreamSynchronize(s));
-        for (int b = 0; b < nb; ++b) {
+        // each batch adds sum_m w_m W_m^T lambda_m into its group's sum (K = 1: acc)
+        in_groups([&](int b, int k) {
             DirBatch &Bt = batches[b];
             Hier &h = *Bt.h;
             cudaStream_t hs = h.stream;
-            PR_CUDA(cudaEventRecord(e0, hs));
+            double *dst_acc = K > 1 ? partial + (size_t)k * N : acc;
             k_broadcast<<<blocks_for((long long)Bt.nd * N, BS), BS, 0, hs>>>(N, Bt.nd, phis, Bt.b);
             PR_LAUNCH();
             BatchSolve bs;
@@ -1106,19 +1273,27 @@ void si_adjoint_run(const pair_mesh &mesh, const pair_quad &quad, const double *
                          bs.iters, bs.max_rel);
                 fail(PAIR_ERR_NOT_CONVERGED, buf2);
             }
-            vcycles += (int)bs.cycles;
-            max_inner = std::max(max_inner, bs.max_rel);
+            bsv[b] = bs;
             if (hex)
-                k_wty_acc<8><<<blocks_for(N, BS), BS, 0, hs>>>(E, Bt.nd, Bt.W, w_d + Bt.m0, Bt.xown, acc);
+                k_wty_acc<8><<<blocks_for(N, BS), BS, 0, hs>>>(E, Bt.nd, Bt.W, w_d + Bt.m0, Bt.xown, dst_acc);
             else
-                k_wty_acc<4><<<blocks_for(N, BS), BS, 0, hs>>>(E, Bt.nd, Bt.W, w_d + Bt.m0, Bt.xown, acc);
+                k_wty_acc<4><<<blocks_for(N, BS), BS, 0, hs>>>(E, Bt.nd, Bt.W, w_d + Bt.m0, Bt.xown, dst_acc);
             PR_LAUNCH();
-            PR_CUDA(cudaEventRecord(e1, hs));
-            PR_CUDA(cudaEventSynchronize(e1));
-            float ms = 0;
-            PR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-            t_solve += ms;
+            PR_CUDA(cudaStreamSynchronize(hs));
+        });
+        if (K > 1) {
+            k_phi_sum<<<blocks_for(N, BS), BS, 0, s>>>(N, K, partial, acc);
+            PR_LAUNCH();
         }
+        for (int b = 0; b < nb; ++b) {
+            vcycles += (int)bsv[b].cycles;
+            max_inner = std::max(max_inner, bsv[b].max_rel);
+        }
+        PR_CUDA(cudaEventRecord(e1, s));
+        PR_CUDA(cudaEventSynchronize(e1));
+        float ms = 0;
+        PR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        t_solve += ms;
         if (hex)
             k_adj_update<8><<<blocks_for(N, BS), BS, 0, s>>>(N, g, sigma_s, acc, pnew);
         else

@@ -90,8 +90,9 @@ void sweep_solve(Hier &h, const double *b, double *x, bool use_graph) {
         launch_sweep(h, b, x);
         return;
     }
-    if (!h.graph || h.graph_b != b || h.graph_x != x) {
-        if (h.graph) { cudaGraphExecDestroy(h.graph); h.graph = nullptr; }
+    CycleGraphs &G = h.gr[0];   // a sweep records no timing events
+    if (!G.graph || G.graph_b != b || G.graph_x != x) {
+        if (G.graph) { cudaGraphExecDestroy(G.graph); G.graph = nullptr; }
         cudaGraph_t g;
         const long long before = g_thread_launches;
         PR_CUDA(cudaStreamBeginCapture(h.stream, cudaStreamCaptureModeThreadLocal));
@@ -105,16 +106,16 @@ void sweep_solve(Hier &h, const double *b, double *x, bool use_graph) {
             throw;
         }
         PR_CUDA(cudaStreamEndCapture(h.stream, &g));
-        h.graph_kernels = g_thread_launches - before;
-        g_launches -= h.graph_kernels;   // counted per replay instead
-        PR_CUDA(cudaGraphInstantiate(&h.graph, g, 0));
+        G.graph_kernels = g_thread_launches - before;
+        g_launches -= G.graph_kernels;   // counted per replay instead
+        PR_CUDA(cudaGraphInstantiate(&G.graph, g, 0));
         cudaGraphDestroy(g);
-        h.graph_b = b;
-        h.graph_x = x;
-        h.graph_tol = -2.0;
+        G.graph_b = b;
+        G.graph_x = x;
+        G.graph_tol = -2.0;
     }
-    PR_CUDA(cudaGraphLaunch(h.graph, h.stream));
-    g_launches += h.graph_kernels;
+    PR_CUDA(cudaGraphLaunch(G.graph, h.stream));
+    g_launches += G.graph_kernels;
 }
 
 }  // namespace pr

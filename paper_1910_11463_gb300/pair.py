@@ -98,7 +98,8 @@ class si_params(C.Structure):
                 ("batch", C.c_int), ("mem_budget_gb", C.c_double), ("g_inflow", C.c_double),
                 ("use_graphs", C.c_int), ("fixed_iters", C.c_int), ("solver", C.c_int),
                 ("inner_cycles", C.c_int), ("q_ang", C.c_void_p), ("phi_reduce", REDUCE_FN),
-                ("reduce_ctx", C.c_void_p)]
+                ("reduce_ctx", C.c_void_p), ("concurrent", C.c_int),
+                ("timing", C.c_int)]
 
 
 class si_info(C.Structure):
@@ -110,7 +111,7 @@ class si_info(C.Structure):
                 ("gb_relax0", C.c_double), ("t_setup_phase_ms", C.c_double * 4), ("t_relaxc_ms", C.c_double),
                 ("n_relaxc", C.c_int), ("gb_relaxc", C.c_double), ("t_res32_ms", C.c_double),
                 ("n_res32", C.c_int), ("gb_res32", C.c_double), ("outer_residuals", C.c_int),
-                ("t_relaxc_level_ms", C.c_double * 8)]
+                ("t_relaxc_level_ms", C.c_double * 8), ("timed_iters", C.c_int)]
 
 
 _lib = None

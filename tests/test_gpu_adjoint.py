@@ -58,7 +58,8 @@ def test_adjoint_matches_oracle(pair, precision, tol):
     phi_o, psi_o, _ = O.si_hex(prob, tol=1e-14, max_iters=400, inner_tol=1e-13)
     st_o, ss_o, q_o, phis_o, info_o = O.si_adjoint_hex(prob, psi_o, g, tol=1e-14, max_iters=400, inner_tol=1e-13)
     air = pair.default_air_params(precision=precision)
-    si = pair.default_si_params(tol=1e-13, max_iters=400, inner_tol=1e-13 if precision == 0 else 1e-11)
+    si = pair.default_si_params(tol=1e-13 if precision == 0 else 1e-12, max_iters=400,
+                                inner_tol=1e-13 if precision == 0 else 1e-11)
     phi, psi, _ = pair.si_solve_problem(prob, air=air, si=si, want_psi=True)
     st, ss, q, phis, info = pair.si_adjoint(prob.n, prob.omega, prob.w, prob.sigma_t, prob.sigma_s, prob.q, psi,
                                             torch.as_tensor(g, device="cuda"), air=air, si=si)
@@ -105,7 +106,10 @@ def test_tet_adjoint_matches_oracle(pair, precision, tol):
     assert info_o["rc"] == 0
     mesh = pair.TetMesh(prob.verts, prob.tets, prob.nbr)
     air = pair.default_air_params(distance=2, precision=precision)
-    si = pair.default_si_params(tol=1e-13, max_iters=400, inner_tol=1e-13 if precision == 0 else 1e-11)
+    # FP32-refined solves to 1e-11 leave the SI change a noise floor near 1e-13 (where
+    # exactly depends on the rounding of the direction groups): stop that path at 1e-12
+    si = pair.default_si_params(tol=1e-13 if precision == 0 else 1e-12, max_iters=400,
+                                inner_tol=1e-13 if precision == 0 else 1e-11)
     phi, psi, _ = pair.si_solve_problem(prob, mesh=mesh, air=air, si=si, want_psi=True)
     st, ss, q, phis, info = pair.si_adjoint(mesh, prob.omega, prob.w, prob.sigma_t, prob.sigma_s, prob.q, psi,
                                             torch.as_tensor(g, device="cuda"), air=air, si=si)
