@@ -61,8 +61,11 @@ static const double OR_PI = 3.14159265358979323846;
 /* swapped (LAPACK convention P A = L U); multipliers l = a_rk * (1 / a_kk)   */
 /* stored below the diagonal; updates a_rc <- fma(-l, a_kc, a_rc) (one        */
 /* rounding).  Singular if the pivot magnitude is not above 'tiny'.           */
+/* skip_zero: a row whose multiplier is zero gets no update (its update adds   */
+/* exact zeros, so only the sign of a zero entry could differ); the lAIR local */
+/* systems use it, where most multipliers are zero.                          */
 /* ------------------------------------------------------------------------- */
-static int lu_factor(int n, double *a, int *piv, double tiny)
+static int lu_factor(int n, double *a, int *piv, double tiny, int skip_zero)
 {
     for (int k = 0; k < n; ++k) {
         int p = k;
@@ -82,6 +85,7 @@ static int lu_factor(int n, double *a, int *piv, double tiny)
         for (int r = k + 1; r < n; ++r) {
             double l = a[r * n + k] * rd;
             a[r * n + k] = l;
+            if (skip_zero && l == 0.0) continue;
             for (int c = k + 1; c < n; ++c) a[r * n + c] = fma(-l, a[k * n + c], a[r * n + c]);
         }
     }
@@ -172,7 +176,7 @@ static int odg_factor(odg *g)
     int nb = g->nb;
     for (int e = 0; e < g->E; ++e) {
         memcpy(g->D + (size_t)e * nb * nb, g->D0 + (size_t)e * nb * nb, sizeof(double) * nb * nb);
-        if (lu_factor(nb, g->D + (size_t)e * nb * nb, g->piv + (size_t)e * nb, 0.0)) return OR_ERR_SINGULAR;
+        if (lu_factor(nb, g->D + (size_t)e * nb * nb, g->piv + (size_t)e * nb, 0.0, 0)) return OR_ERR_SINGULAR;
     }
     return OR_OK;
 }
@@ -572,7 +576,7 @@ int or_sweep_scc(int nrows, int nb, const int *rowptr, const int *col, const dou
                     }
                     y[rr] = sacc;
                 }
-            if (lu_factor(m, Ad, pv, 0.0)) rc = OR_ERR_SINGULAR;
+            if (lu_factor(m, Ad, pv, 0.0, 0)) rc = OR_ERR_SINGULAR;
             else {
                 lu_solve(m, Ad, pv, y);
                 for (int i = 0; i < k; ++i)
@@ -854,7 +858,7 @@ static int lair(olevel *L, const signed char *SR, int distance, double phi_R)
         }
         int keep = np;
         if (np > 0) {
-            if (lu_factor(np, M, piv, 1e-14 * mx)) { L->n_singular++; keep = 0; }
+            if (lu_factor(np, M, piv, 1e-14 * mx, 1)) { L->n_singular++; keep = 0; }
             else lu_solve(np, M, piv, z);
         }
         double zmax = 0.0;

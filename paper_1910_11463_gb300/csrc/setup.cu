@@ -419,6 +419,7 @@ __global__ void __launch_bounds__(64) k_lair_solve_thread(int nwork, const int *
         for (int r = k + 1; r < np; ++r) {
             double l = MM(r * np + k) * rd;
             MM(r * np + k) = l;
+            if (l == 0.0) continue;   // adds exact zeros: skipped, as in the reference LU
             for (int c = k + 1; c < np; ++c) MM(r * np + c) = fma(-l, MM(k * np + c), MM(r * np + c));
         }
     }
@@ -473,6 +474,7 @@ __global__ void k_lair_solve(int nwork, const int *worklist, const int *cpts, co
     int g = lane % G, q = lane / G;
     int wpb = blockDim.x >> 5;
     constexpr int SPW = 32 / G;   // systems per warp
+    const unsigned gmask = (G == 32) ? FULL : (((1u << (G & 31)) - 1u) << (q * G));   // this group's lanes
     for (int wb = (blockIdx.x * wpb + warp) * SPW; wb < nwork; wb += gridDim.x * wpb * SPW) {
         int w = wb + q;
         bool has = w < nwork;
@@ -480,11 +482,12 @@ __global__ void k_lair_solve(int nwork, const int *worklist, const int *cpts, co
         int i = has ? cpts[ic] : 0;
         int np = has ? npat[ic] : 0;
         double *M = gbuf ? gbuf + (has ? goff[w] : 0)
-                         : smem + ((size_t)warp * SPW + q) * ((size_t)nmax * nmax + 3 * nmax);
+                         : smem + ((size_t)warp * SPW + q) * ((size_t)nmax * nmax + 4 * nmax);
         double *y = M + (size_t)np * np;
         double *rv = y + np;                  // pivot reciprocals
         int *pat = (int *)(rv + np);
         int *piv = pat + np;
+        int *rl = piv + np;                   // rows below the pivot with a nonzero multiplier
         if (has) {
             const int *cp = cand + candptr[ic];
             for (int t = g; t < np; t += G) { pat[t] = cp[t]; y[t] = -0.0; }
@@ -557,18 +560,35 @@ __global__ void k_lair_solve(int nwork, const int *worklist, const int *cpts, co
                 rv[k] = rd;
             }
             rd = __shfl_sync(FULL, rd, q * G);
-            if (act)
-                for (int r = k + 1 + g; r < np; r += G) M[r * np + k] = M[r * np + k] * rd;
+            // multipliers, and the list of rows whose multiplier is not zero: a zero
+            // multiplier's update adds exact zeros, so those rows are skipped, as in the
+            // reference LU (in the local systems of these operators most multipliers are
+            // zero).  The bound on the rows below the pivot is uniform over the warp, so
+            // every lane reaches each ballot.
+            int m = 0;
+            for (int j0 = 0; j0 < kmax - k - 1; j0 += G) {
+                const int r = k + 1 + j0 + g;
+                bool nzr = false;
+                if (act && r < np) {
+                    const double l = M[r * np + k] * rd;
+                    M[r * np + k] = l;
+                    nzr = l != 0.0;
+                }
+                const unsigned msk = __ballot_sync(FULL, nzr) & gmask;
+                if (nzr) rl[m + __popc(msk & ((1u << lane) - 1u))] = r;
+                m += __popc(msk);
+            }
             __syncwarp();
             if (act) {
-                // lane g updates entries g, g + G, ... of the wd x wd trailing block in
-                // row-major order (the fewest FP64 instructions: every lane busy until the
-                // last entries), four entries per pass with all their loads issued
-                // before the updates; (row, column) advance by (G / wd, G % wd) per entry
-                // with at most one carry, so no division per entry
+                // lane g updates entries g, g + G, ... of the m x wd block (listed rows,
+                // trailing columns) in row-major order (the fewest FP64 instructions:
+                // every lane busy until the last entries), four entries per pass with all
+                // their loads issued before the updates; (list index, column) advance by
+                // (G / wd, G % wd) per entry with at most one carry, so no division per
+                // entry
                 const int wd = np - k - 1;
-                if (wd > 0) {
-                    const int tot = wd * wd;
+                if (wd > 0 && m > 0) {
+                    const int tot = m * wd;
                     const int dr = G / wd, dc = G - dr * wd;
                     int r = g / wd, c = g - r * wd;
                     for (int e = g; e < tot; e += 4 * G) {
@@ -577,7 +597,7 @@ __global__ void k_lair_solve(int nwork, const int *worklist, const int *cpts, co
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
                             ok[u] = e + u * G < tot;
-                            Ro[u] = (k + 1 + r) * np;
+                            Ro[u] = ok[u] ? rl[r] * np : 0;
                             Co[u] = k + 1 + c;
                             r += dr;
                             c += dc;
@@ -626,7 +646,6 @@ __global__ void k_lair_solve(int nwork, const int *worklist, const int *cpts, co
         int tmax = np;
         for (int o = 16; o > 0; o >>= 1) tmax = max(tmax, __shfl_xor_sync(FULL, tmax, o));
         // keep in ascending order: ballot-compacted write within the group
-        unsigned gmask = (G == 32) ? FULL : (((1u << G) - 1u) << (q * G));
         for (int t0 = 0; t0 < tmax; t0 += G) {
             int t = t0 + g;
             bool k_ = solve && t < np && !(phi_R > 0.0 && fabs(y[t]) < thr);
@@ -921,7 +940,7 @@ __global__ void k_big_rows(int nbig, const int *list, const int *npat, long long
     int w = blockIdx.x * blockDim.x + threadIdx.x;
     if (w >= nbig) return;
     long long np = npat[list[w]];
-    goff[w] = np * np + 3 * np;
+    goff[w] = np * np + 4 * np;
 }
 
 __global__ void k_prefix_ll(int n, long long *v) {
@@ -1432,7 +1451,7 @@ void build_hierarchy(Hier &h) {
             auto warp_bin = [&](int c, auto kern, int G) {
                 if (!hc[c]) return;
                 const int nm = cls_n[c], spw = 32 / G;
-                size_t per = ((size_t)nm * nm + 3 * nm) * sizeof(double) * spw;   // per warp
+                size_t per = ((size_t)nm * nm + 4 * nm) * sizeof(double) * spw;   // per warp
                 int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (200 * 1024) / per));
                 size_t sm = per * wpb;
                 unsigned grid = std::min<unsigned>(blocks_for(hc[c], wpb * spw), 152u * 64u);
