@@ -829,7 +829,8 @@ def run_one_iteration(args):
     prob = I.config(args.config)
     air = pair.default_air_params(precision=args.precision, theta=args.theta, phi_R=args.phi_R, phi_A=args.phi_A,
                                   distance=args.distance, nair=args.nair)
-    si = pair.default_si_params(tol=1e-8, max_iters=1, inner_tol=1e-8, inner_maxit=200)
+    si = pair.default_si_params(tol=1e-8, max_iters=1, inner_tol=1e-8, inner_maxit=200,
+                                use_graphs=args.graphs, concurrent=args.concurrent, timing=0)
     phi, _, info = pair.si_solve_problem(prob, air=air, si=si)
     torch.cuda.synchronize()
     print(json.dumps({"workload": args.config, "setup_ms": info["t_setup_ms"], "solve_ms": info["t_solve_ms"],
