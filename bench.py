@@ -700,7 +700,7 @@ def main():
     ap.add_argument("--precision", type=int, default=1, choices=[0, 1, 2],
                     help="0 FP64; 1 FP32 V-cycle under FP64 refinement (default); 2 FP32 V-cycle under "
                          "double-float refinement (hex block form)")
-    ap.add_argument("--timing-every", dest="timing_every", type=int, default=6,
+    ap.add_argument("--timing-every", dest="timing_every", type=int, default=9,
                     help="kernel timings in SI iterations k, 2k, ... (si_params.timing)")
     ap.add_argument("--concurrent", type=int, default=1,
                     help="direction groups solved at the same time on their own streams (0: library default; "

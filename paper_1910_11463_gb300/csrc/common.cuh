@@ -116,6 +116,8 @@ __device__ __forceinline__ long long absbits(double x) { return __double_as_long
 // Exclusive scan of int counts (n entries) into out (n+1 entries, out[n] = total);
 // returns the total (synchronises the stream).
 long long scan_exclusive(const int *in, int *out, int n, cudaStream_t s, bool want_total = true);
+// in place: v[0..n) becomes its exclusive prefix sums, v[n] (and the return) the total
+long long scan_exclusive_ll(long long *v, int n, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Hierarchy storage.  A hierarchy holds a batch of independent matrices

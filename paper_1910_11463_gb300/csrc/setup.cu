@@ -333,6 +333,32 @@ __global__ void k_nair(int nc, const int *cpts, const int *rowptr, const int *co
 }
 
 
+// 1 / p for a pivot p.  A pivot of magnitude 1 (the unit diagonal of the
+// block-scaled level 0, which most eliminations leave untouched) is its own
+// reciprocal, exactly, so it takes no division: an FP64 division occupies the FP64
+// pipe for a whole warp instruction however few lanes take part, and one per pivot
+// was most of the FP64 work left once zero-multiplier rows are skipped.
+__device__ __forceinline__ double pivot_recip(double p) {
+    const long long mag = __double_as_longlong(p) & 0x7fffffffffffffffLL;   // |p| == 1, integer test
+    return mag == 0x3ff0000000000000LL ? p : 1.0 / p;
+}
+
+// The FP64 pipe takes a whole warp instruction for any number of active lanes, so
+// the O(n^2) passes of the local solves keep their zero tests and signed zeros on
+// the integer pipe.
+__device__ __forceinline__ bool is_zero_bits(double x) { return (__double_as_longlong(x) & 0x7fffffffffffffffLL) == 0; }
+// a * r for a zero a and a finite nonzero r: the zero with the product's sign
+__device__ __forceinline__ double zero_times(double a, double r) {
+    return __longlong_as_double((__double_as_longlong(a) ^ __double_as_longlong(r)) & (long long)0x8000000000000000ULL);
+}
+// y * r for a reciprocal r of magnitude 1 (unit pivot): exact sign flip or y itself
+__device__ __forceinline__ double times_recip(double y, double r) {
+    const long long rb = __double_as_longlong(r);
+    if ((rb & 0x7fffffffffffffffLL) == 0x3ff0000000000000LL)
+        return __longlong_as_double(__double_as_longlong(y) ^ (rb & (long long)0x8000000000000000ULL));
+    return y * r;
+}
+
 // Thread per C row of the worklist for systems of size <= NM: every lane of a
 // warp works on its own system, so each FP64 instruction carries 32 useful
 // operations.  Workspaces live in shared memory interleaved by thread
@@ -414,12 +440,17 @@ __global__ void __launch_bounds__(64) k_lair_solve_thread(int nwork, const int *
         if (!(pv > tinyb)) { singular = true; break; }
         if (p != k)
             for (int c = 0; c < np; ++c) { double tt = MM(k * np + c); MM(k * np + c) = MM(p * np + c); MM(p * np + c) = tt; }
-        double rd = 1.0 / MM(k * np + k);
+        double rd = pivot_recip(MM(k * np + k));
         RR(k) = rd;
         for (int r = k + 1; r < np; ++r) {
-            double l = MM(r * np + k) * rd;
+            const double a = MM(r * np + k);
+            if (is_zero_bits(a)) {   // adds exact zeros: skipped, as in the reference LU
+                MM(r * np + k) = zero_times(a, rd);
+                continue;
+            }
+            const double l = a * rd;
             MM(r * np + k) = l;
-            if (l == 0.0) continue;   // adds exact zeros: skipped, as in the reference LU
+            if (is_zero_bits(l)) continue;   // (an underflowed multiplier likewise)
             for (int c = k + 1; c < np; ++c) MM(r * np + c) = fma(-l, MM(k * np + c), MM(r * np + c));
         }
     }
@@ -436,7 +467,7 @@ __global__ void __launch_bounds__(64) k_lair_solve_thread(int nwork, const int *
             for (int r = k + 1; r < np; ++r) YY(r) = fma(-MM(r * np + k), yk, YY(r));
         }
         for (int k = np - 1; k >= 0; --k) {
-            double yk = YY(k) * RR(k);
+            double yk = times_recip(YY(k), RR(k));
             YY(k) = yk;
             for (int r = 0; r < k; ++r) YY(r) = fma(-MM(r * np + k), yk, YY(r));
         }
@@ -532,15 +563,27 @@ __global__ void k_lair_solve(int nwork, const int *worklist, const int *cpts, co
             bool act = k < np && !singular;
             long long bv = -1;
             int br = k;
+            bool nzb = false;   // a nonzero below the diagonal among this lane's rows
             if (act)
                 for (int r = k + g; r < np; r += G) {
                     long long v = absbits(M[r * np + k]);
+                    if (r > k && v != 0) nzb = true;
                     if (v > bv) { bv = v; br = r; }
                 }
-            for (int o = G / 2; o > 0; o >>= 1) {
-                long long ov = __shfl_xor_sync(FULL, bv, o, G);
-                int orr = __shfl_xor_sync(FULL, br, o, G);
-                if (ov > bv || (ov == bv && orr < br)) { bv = ov; br = orr; }
+            // Most columns have nothing below the diagonal: when no group of the warp has,
+            // every pivot stays on the diagonal (the only candidate that is not zero,
+            // held by the group's first lane) and the step has no multipliers to compute
+            // and nothing to update.
+            const bool any_nz = __ballot_sync(FULL, nzb) != 0u;
+            if (any_nz) {
+                for (int o = G / 2; o > 0; o >>= 1) {
+                    long long ov = __shfl_xor_sync(FULL, bv, o, G);
+                    int orr = __shfl_xor_sync(FULL, br, o, G);
+                    if (ov > bv || (ov == bv && orr < br)) { bv = ov; br = orr; }
+                }
+            } else {
+                bv = __shfl_sync(FULL, bv, q * G);
+                br = k;
             }
             if (act && !(bv > tinyb)) { singular = true; act = false; }
             if (act) {
@@ -556,7 +599,7 @@ __global__ void k_lair_solve(int nwork, const int *worklist, const int *cpts, co
             // the pivot's reciprocal: one lane of the group divides, the others take it
             double rd = 0.0;
             if (act && g == 0) {
-                rd = 1.0 / M[k * np + k];
+                rd = pivot_recip(M[k * np + k]);
                 rv[k] = rd;
             }
             rd = __shfl_sync(FULL, rd, q * G);
@@ -565,19 +608,36 @@ __global__ void k_lair_solve(int nwork, const int *worklist, const int *cpts, co
             // reference LU (in the local systems of these operators most multipliers are
             // zero).  The bound on the rows below the pivot is uniform over the warp, so
             // every lane reaches each ballot.
+            // (a zero entry's multiplier is the signed zero a * rd gives, set with
+            // integer operations; the others are computed for the listed rows only)
             int m = 0;
+            if (!any_nz) {
+                // only zeros below: their multipliers are those zeros, with the sign
+                // flipped under a negative pivot
+                if (act && __double_as_longlong(rd) < 0)
+                    for (int r = k + 1 + g; r < np; r += G) M[r * np + k] = zero_times(M[r * np + k], rd);
+                __syncwarp();
+                continue;
+            }
             for (int j0 = 0; j0 < kmax - k - 1; j0 += G) {
                 const int r = k + 1 + j0 + g;
                 bool nzr = false;
                 if (act && r < np) {
-                    const double l = M[r * np + k] * rd;
-                    M[r * np + k] = l;
-                    nzr = l != 0.0;
+                    const double a = M[r * np + k];
+                    nzr = !is_zero_bits(a);
+                    if (!nzr) M[r * np + k] = zero_times(a, rd);
                 }
                 const unsigned msk = __ballot_sync(FULL, nzr) & gmask;
                 if (nzr) rl[m + __popc(msk & ((1u << lane) - 1u))] = r;
                 m += __popc(msk);
             }
+            __syncwarp();
+            if (act)
+                for (int t = g; t < m; t += G) {
+                    const double l = M[rl[t] * np + k] * rd;
+                    M[rl[t] * np + k] = l;
+                    if (is_zero_bits(l)) rl[t] = -1;   // underflowed to zero: skipped too
+                }
             __syncwarp();
             if (act) {
                 // lane g updates entries g, g + G, ... of the m x wd block (listed rows,
@@ -596,20 +656,21 @@ __global__ void k_lair_solve(int nwork, const int *worklist, const int *cpts, co
                         bool ok[4];
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
-                            ok[u] = e + u * G < tot;
-                            Ro[u] = ok[u] ? rl[r] * np : 0;
+                            const int rr = e + u * G < tot ? rl[r] : -1;
+                            ok[u] = rr >= 0;
+                            Ro[u] = ok[u] ? rr * np : 0;
                             Co[u] = k + 1 + c;
                             r += dr;
                             c += dc;
                             if (c >= wd) { c -= wd; ++r; }
                         }
-                        double a[4], b[4], m[4];
+                        double a[4], b[4], mv[4];
 #pragma unroll
                         for (int u = 0; u < 4; ++u)
-                            if (ok[u]) { a[u] = M[Ro[u] + k]; b[u] = M[k * np + Co[u]]; m[u] = M[Ro[u] + Co[u]]; }
+                            if (ok[u]) { a[u] = M[Ro[u] + k]; b[u] = M[k * np + Co[u]]; mv[u] = M[Ro[u] + Co[u]]; }
 #pragma unroll
                         for (int u = 0; u < 4; ++u)
-                            if (ok[u]) M[Ro[u] + Co[u]] = fma(-a[u], b[u], m[u]);
+                            if (ok[u]) M[Ro[u] + Co[u]] = fma(-a[u], b[u], mv[u]);
                     }
                 }
             }
@@ -628,7 +689,7 @@ __global__ void k_lair_solve(int nwork, const int *worklist, const int *cpts, co
             __syncwarp();
         }
         for (int k = kmax - 1; k >= 0; --k) {
-            if (solve && k < np && g == 0) y[k] = y[k] * rv[k];
+            if (solve && k < np && g == 0) y[k] = times_recip(y[k], rv[k]);
             __syncwarp();
             if (solve && k < np) {
                 double yk = y[k];
@@ -943,13 +1004,6 @@ __global__ void k_big_rows(int nbig, const int *list, const int *npat, long long
     goff[w] = np * np + 4 * np;
 }
 
-__global__ void k_prefix_ll(int n, long long *v) {
-    // single thread: exclusive prefix in place, v[n] = total (overflow rows are few)
-    if (blockIdx.x || threadIdx.x) return;
-    long long s = 0;
-    for (int i = 0; i < n; ++i) { long long t = v[i]; v[i] = s; s += t; }
-    v[n] = s;
-}
 
 __global__ void k_lair_classes(int nc, const int *npat, int8_t *cls) {
     int ic = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1473,10 +1527,7 @@ void build_hierarchy(Hier &h) {
                 long long *goff = dmalloc<long long>(nbig + 1, s);
                 k_big_rows<<<blocks_for(nbig, BS), BS, 0, s>>>(nbig, list + hstart[LAIR_BIG], npat, goff);
                 PR_LAUNCH();
-                k_prefix_ll<<<1, 1, 0, s>>>(nbig, goff);
-                PR_LAUNCH();
-                long long gtot = 0;
-                d2h(&gtot, goff + nbig, 1, s);
+                const long long gtot = scan_exclusive_ll(goff, nbig, s);
                 double *gbuf = dmalloc<double>(gtot, s);
                 k_lair_solve<32><<<std::min<unsigned>(nbig, 152u * 16u), 32, 0, s>>>(
                     nbig, list + hstart[LAIR_BIG], L.cpts, L.rowptr, L.col, L.val, candptr, cand, npat, zr, zc, zv, keep,
@@ -1561,10 +1612,7 @@ void build_hierarchy(Hier &h) {
                 long long *capw = dmalloc<long long>(nover + 1, s);
                 k_overflow_caps<<<blocks_for(nover, BS), BS, 0, s>>>(nover, list, U, capw);
                 PR_LAUNCH();
-                k_prefix_ll<<<1, 1, 0, s>>>(nover, capw);
-                PR_LAUNCH();
-                long long gtot = 0;
-                d2h(&gtot, capw + nover, 1, s);
+                const long long gtot = scan_exclusive_ll(capw, nover, s);
                 int *gk = dmalloc<int>(gtot, s);
                 double *gv = dmalloc<double>(gtot, s);
                 k_rap<32, true><<<std::min<unsigned>(nover, 152u * 16u), 32, 0, s>>>(

@@ -80,7 +80,8 @@ __device__ long long block_excl_scan(long long v, long long *sh, long long *tota
     return incl - v;
 }
 
-__global__ void k_tile_sums(const int *in, int n, long long *sums) {
+template <class In>
+__global__ void k_tile_sums(const In *in, int n, long long *sums) {
     __shared__ long long sh[SCAN_BS];
     long long base = (long long)blockIdx.x * SCAN_TILE;
     long long s = 0;
@@ -108,7 +109,9 @@ __global__ void k_scan_sums(long long *sums, int nb) {
     if (threadIdx.x == 0) sums[nb] = carry;
 }
 
-__global__ void k_scan_tiles(const int *in, int n, const long long *sums, int *out, long long *total_out,
+// (in may be out: each thread reads its items before writing them)
+template <class In, class Out>
+__global__ void k_scan_tiles(const In *in, int n, const long long *sums, Out *out, long long *total_out,
                              int nb) {
     __shared__ long long sh[SCAN_BS];
     long long base = (long long)blockIdx.x * SCAN_TILE;
@@ -123,11 +126,11 @@ __global__ void k_scan_tiles(const int *in, int n, const long long *sums, int *o
     long long ex = block_excl_scan(s, sh, &tot) + sums[blockIdx.x];
     for (int k = 0; k < SCAN_ITEMS; ++k) {
         long long i = base + (long long)threadIdx.x * SCAN_ITEMS + k;
-        if (i < n) out[i] = (int)ex;
+        if (i < n) out[i] = (Out)ex;
         ex += v[k];
     }
     if (blockIdx.x == nb - 1 && threadIdx.x == 0) {
-        out[n] = (int)sums[nb];
+        out[n] = (Out)sums[nb];
         *total_out = sums[nb];
     }
 }
@@ -140,11 +143,11 @@ long long scan_exclusive(const int *in, int *out, int n, cudaStream_t s, bool wa
     }
     int nb = (int)blocks_for(n, SCAN_TILE);
     long long *sums = dmalloc<long long>(nb + 2, s);
-    k_tile_sums<<<nb, SCAN_BS, 0, s>>>(in, n, sums);
+    k_tile_sums<int><<<nb, SCAN_BS, 0, s>>>(in, n, sums);
     PR_LAUNCH();
     k_scan_sums<<<1, SCAN_BS, 0, s>>>(sums, nb);
     PR_LAUNCH();
-    k_scan_tiles<<<nb, SCAN_BS, 0, s>>>(in, n, sums, out, sums + nb + 1, nb);
+    k_scan_tiles<int, int><<<nb, SCAN_BS, 0, s>>>(in, n, sums, out, sums + nb + 1, nb);
     PR_LAUNCH();
     long long total = 0;
     if (want_total) {
@@ -153,6 +156,26 @@ long long scan_exclusive(const int *in, int *out, int n, cudaStream_t s, bool wa
         if (total > 0x7fffffffLL)
             fail(PAIR_ERR_UNSUPPORTED, "scan total exceeds int32: batch too large for 32-bit indices");
     }
+    dfree(sums, s);
+    return total;
+}
+
+long long scan_exclusive_ll(long long *v, int n, cudaStream_t s) {
+    if (n <= 0) {
+        PR_CUDA(cudaMemsetAsync(v, 0, sizeof(long long), s));
+        return 0;
+    }
+    int nb = (int)blocks_for(n, SCAN_TILE);
+    long long *sums = dmalloc<long long>(nb + 2, s);
+    k_tile_sums<long long><<<nb, SCAN_BS, 0, s>>>(v, n, sums);
+    PR_LAUNCH();
+    k_scan_sums<<<1, SCAN_BS, 0, s>>>(sums, nb);
+    PR_LAUNCH();
+    k_scan_tiles<long long, long long><<<nb, SCAN_BS, 0, s>>>(v, n, sums, v, sums + nb + 1, nb);
+    PR_LAUNCH();
+    long long total = 0;
+    PR_CUDA(cudaMemcpyAsync(&total, sums + nb + 1, sizeof(long long), cudaMemcpyDeviceToHost, s));
+    PR_CUDA(cudaStreamSynchronize(s));
     dfree(sums, s);
     return total;
 }
