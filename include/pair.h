@@ -321,7 +321,8 @@ typedef struct {
     double t_res32_ms;       /* FP32 inner residuals r - A d of the refinement steps */
     int n_res32;
     double gb_res32;
-    int outer_residuals;     /* outer (FP64-accurate) residuals over all direction solves */
+    int outer_residuals;     /* outer (FP64-accurate) residuals that read the operator, over all
+                              * direction solves (the first one of a solve from psi = 0 is b) */
     double t_relaxc_level_ms[8]; /* t_relaxc_ms by level: entry k is level k + 1 (the last
                                   * entry also holds deeper levels) */
     int timed_iters;         /* SI iterations whose cycles the kernel timings cover

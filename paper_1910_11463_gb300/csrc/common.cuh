@@ -315,13 +315,14 @@ void free_level(Level &L, cudaStream_t s);
 
 // cycle.cu
 // r = b - A0 x (FP64), cast into lev[0].vb; per-matrix ||r||; active[d] = ||r|| > tol ||b||
-void residual0(Hier &h, const double *b, const double *x, double tol, bool update_active);
+// zero_x: x is known to be zero (r = b; the operator is not read, the launch not timed)
+void residual0(Hier &h, const double *b, const double *x, double tol, bool update_active, bool zero_x = false);
 void vcycle_correct(Hier &h, double *x, ProfSlot *ps = nullptr);   // x += V(lev[0].vb), zero initial guess
 // inner correction (h.inner): outer residual into lev[0].vb and r32 with the norms,
 // active and inner flags and thresholds; one inner cycle (V-cycle into d32, FP32
 // residual and inner norm); x += d32 (d32 cleared) for the active matrices
 void inner_enable(Hier &h);
-void residual_outer(Hier &h, const double *b, const double *x, double tol);
+void residual_outer(Hier &h, const double *b, const double *x, double tol, bool zero_x = false);
 void inner_cycle(Hier &h, ProfSlot *ps);
 void fold_delta(Hier &h, double *x);
 // double-float mode (h.dd): b and x to pairs before a solve, x back after it; the
@@ -371,7 +372,9 @@ struct BatchSolve {
     double rho_sum = 0;
     int rho_cnt = 0;
 };
-BatchSolve solve_batch(Hier &h, const double *b, double *x, double tol, int maxit, bool use_graph);
+// x_zero: x holds zeros on entry (the first residual is then b itself)
+BatchSolve solve_batch(Hier &h, const double *b, double *x, double tol, int maxit, bool use_graph,
+                       bool x_zero = false);
 void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t, const double *sigma_s,
             const double *q, const air_params &prm, const si_params &sp, double *phi, double *psi,
             cudaStream_t user, si_info *info);

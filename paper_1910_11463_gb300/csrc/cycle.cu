@@ -136,7 +136,7 @@ __device__ __forceinline__ double block_sum(double v) {
 template <class T>
 __global__ void __launch_bounds__(BS) k_res0_bsr(int n, int N, const int8_t *dsign, const double *bsr64,
                                                  const double *b, const double *x, T *r, float *r2,
-                                                 double *partials, int maxblk, const int *active) {
+                                                 double *partials, int maxblk, const int *active, int zero_x) {
     pdl_begin();
     HexRow q = hex_row(n);
     if (active && !active[q.m]) return;
@@ -146,8 +146,12 @@ __global__ void __launch_bounds__(BS) k_res0_bsr(int n, int N, const int8_t *dsi
     long long E = (long long)N / 8;
     if (q.valid) {
         long long gi = (long long)q.m * N + 8LL * q.e + q.a;
-        double acc = b[gi] - x[gi];
-        acc -= bsr_offdiag<double, double>(n, E, q.m, q.e, q.a, q.idx, dsign, bsr64, x + (long long)q.m * N);
+        // x = 0 (a solve's first residual): r = b, no operator read
+        double acc = b[gi];
+        if (!zero_x) {
+            acc -= x[gi];
+            acc -= bsr_offdiag<double, double>(n, E, q.m, q.e, q.a, q.idx, dsign, bsr64, x + (long long)q.m * N);
+        }
         T rt = (T)acc;
         r[gi] = rt;
         if (r2) r2[gi] = (float)rt;   // the inner iteration's fixed right-hand side
@@ -258,7 +262,8 @@ __global__ void k_dd_join(long long n, const float2 *a, double *out) {
 template <class T>
 __global__ void __launch_bounds__(BS) k_res0_csr(const int *row0, const int *nrow, const int *rowptr, const int *col,
                                                  const double *val, const double *b, const double *x, T *r,
-                                                 float *r2, double *partials, int maxblk, const int *active) {
+                                                 float *r2, double *partials, int maxblk, const int *active,
+                                                 int zero_x) {
     pdl_begin();
     int m = blockIdx.y;
     if (active && !active[m]) return;
@@ -267,7 +272,8 @@ __global__ void __launch_bounds__(BS) k_res0_csr(const int *row0, const int *nro
     if (li < nrow[m]) {
         int i = row0[m] + li;
         double acc = 0.0;
-        for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) acc += val[p] * x[col[p]];
+        if (!zero_x)   // x = 0 (a solve's first residual): r = b, no operator read
+            for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) acc += val[p] * x[col[p]];
         acc = b[i] - acc;
         r[i] = (T)acc;
         if (r2) r2[i] = (float)acc;
@@ -1290,7 +1296,7 @@ void prof_enable(Hier &h) {
 namespace {
 // outer residual kernels: r = b - A0 x into lev[0].vb (and r2, if given), the
 // per-matrix partial sums of squares into h.partials
-void residual0_launch(Hier &h, const double *b, const double *x, const int *act, float *r2) {
+void residual0_launch(Hier &h, const double *b, const double *x, const int *act, float *r2, bool zero_x = false) {
     cudaStream_t s = h.stream;
     Level &L = h.lev[0];
     dim3 grid(h.maxblk, h.ndir);
@@ -1305,30 +1311,31 @@ void residual0_launch(Hier &h, const double *b, const double *x, const int *act,
         dim3 g3(blocks_for(h.hex_n, 32), h.hex_n * h.hex_n, h.ndir);
         if (f32)
             launch_pdl(k_res0_bsr<float>, g3, BS, s, h.hex_n, N, h.dsign, h.bsr64, b, x, (float *)L.vb, r2,
-                       h.partials, h.maxblk, act);
+                       h.partials, h.maxblk, act, zero_x ? 1 : 0);
         else
             launch_pdl(k_res0_bsr<double>, g3, BS, s, h.hex_n, N, h.dsign, h.bsr64, b, x, (double *)L.vb,
-                       (float *)nullptr, h.partials, h.maxblk, act);
+                       (float *)nullptr, h.partials, h.maxblk, act, zero_x ? 1 : 0);
     } else {
         if (f32)
             launch_pdl(k_res0_csr<float>, grid, BS, s, h.d_row00, h.d_n0, L.rowptr, L.col, L.val, b, x, (float *)L.vb,
-                       r2, h.partials, h.maxblk, act);
+                       r2, h.partials, h.maxblk, act, zero_x ? 1 : 0);
         else
             launch_pdl(k_res0_csr<double>, grid, BS, s, h.d_row00, h.d_n0, L.rowptr, L.col, L.val, b, x,
-                       (double *)L.vb, (float *)nullptr, h.partials, h.maxblk, act);
+                       (double *)L.vb, (float *)nullptr, h.partials, h.maxblk, act, zero_x ? 1 : 0);
     }
     PR_LAUNCH();
 }
 }  // namespace
 
-void residual0(Hier &h, const double *b, const double *x, double tol, bool update_active) {
+void residual0(Hier &h, const double *b, const double *x, double tol, bool update_active, bool zero_x) {
     cudaStream_t s = h.stream;
     // every block of an active matrix writes its partial; inactive matrices' partials
     // are not read
     int *act = update_active ? h.active : nullptr;
-    if (h.timed) rec_event(h.ev[0], s);
-    residual0_launch(h, b, x, act, nullptr);
-    if (h.timed) rec_event(h.ev[1], s);
+    const bool tm = h.timed && !zero_x;   // timings cover the residuals that read the operator
+    if (tm) rec_event(h.ev[0], s);
+    residual0_launch(h, b, x, act, nullptr, zero_x && !h.dd);
+    if (tm) rec_event(h.ev[1], s);
     launch_pdl(k_norm_final, blocks_for(32LL * h.ndir, 128), 128, s, h.ndir, h.partials, h.maxblk, h.rnorm, h.bnorm, tol,
                                                                  act);
     PR_LAUNCH();
@@ -1500,11 +1507,12 @@ void inner_enable(Hier &h) {
     h.inner = true;
 }
 
-void residual_outer(Hier &h, const double *b, const double *x, double tol) {
+void residual_outer(Hier &h, const double *b, const double *x, double tol, bool zero_x) {
     cudaStream_t s = h.stream;
-    if (h.timed) rec_event(h.ev[0], s);
-    residual0_launch(h, b, x, h.active, h.r32);
-    if (h.timed) rec_event(h.ev[1], s);
+    const bool tm = h.timed && !zero_x;   // timings cover the residuals that read the operator
+    if (tm) rec_event(h.ev[0], s);
+    residual0_launch(h, b, x, h.active, h.r32, zero_x && !h.dd);
+    if (tm) rec_event(h.ev[1], s);
     launch_pdl(k_norm_outer, h.ndir, NORM_BS, s, h.ndir, (const double *)h.partials, h.maxblk, h.rnorm,
                (const double *)h.bnorm, tol, h.active, h.iactive, h.ithr, h.iany, h.iticket);
     PR_LAUNCH();

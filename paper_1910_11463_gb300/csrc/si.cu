@@ -299,25 +299,26 @@ void run_close(Hier &h, const double *b, double *x, double tol, bool use_graph) 
 // cycles of a step are launched back to back (the count predicted from the
 // measured contraction, as graphs of 1, 2, 4 and 8 cycles), and matrices (and, once
 // none is left, whole launches) that reached their threshold do no work.
-BatchSolve solve_batch_inner(Hier &h, const double *b, double *x, double tol, int maxit, bool use_graph) {
+BatchSolve solve_batch_inner(Hier &h, const double *b, double *x, double tol, int maxit, bool use_graph,
+                             bool x_zero) {
     cudaStream_t s = h.stream;
     const int nd = h.ndir;
     norms0(h, b, h.bnorm);
     set_all_active(h);
     PR_CUDA(cudaMemsetAsync(h.icount, 0, sizeof(int) * nd, s));
     if (h.dd) dd_load(h, b, x);
-    residual_outer(h, b, x, tol);
+    residual_outer(h, b, x, tol, x_zero);
     std::vector<double> r0(nd), rn(nd), bn(nd), inn(nd);
     std::vector<int> act(nd), cnt(nd, 0), cyc(nd, 0);
     PR_CUDA(cudaMemcpyAsync(r0.data(), h.rnorm, sizeof(double) * nd, cudaMemcpyDeviceToHost, s));
     PR_CUDA(cudaMemcpyAsync(bn.data(), h.bnorm, sizeof(double) * nd, cudaMemcpyDeviceToHost, s));
     PR_CUDA(cudaMemcpyAsync(act.data(), h.active, sizeof(int) * nd, cudaMemcpyDeviceToHost, s));
     PR_CUDA(cudaStreamSynchronize(s));
-    account_outer(h, std::vector<char>(nd, 1));
+    if (!x_zero) account_outer(h, std::vector<char>(nd, 1));
     for (int d = 0; d < nd; ++d)
         if (!std::isfinite(r0[d]) || !std::isfinite(bn[d])) fail(PAIR_ERR_NAN, "NaN/Inf in right-hand side or residual");
     rn = r0;
-    int outer = 1;
+    int outer = x_zero ? 0 : 1;   // residuals that read the operator
     bool any = std::any_of(act.begin(), act.end(), [](int a) { return a != 0; });
     while (any) {
         int done = 0;
@@ -392,21 +393,21 @@ BatchSolve solve_batch_inner(Hier &h, const double *b, double *x, double tol, in
 }  // namespace
 
 // Solves every matrix of the hierarchy from the given x to ||b - A x|| <= tol ||b||.
-BatchSolve solve_batch(Hier &h, const double *b, double *x, double tol, int maxit, bool use_graph) {
-    if (h.inner && tol > 0.0) return solve_batch_inner(h, b, x, tol, maxit, use_graph);
+BatchSolve solve_batch(Hier &h, const double *b, double *x, double tol, int maxit, bool use_graph, bool x_zero) {
+    if (h.inner && tol > 0.0) return solve_batch_inner(h, b, x, tol, maxit, use_graph, x_zero);
     cudaStream_t s = h.stream;
     int nd = h.ndir;
     norms0(h, b, h.bnorm);
     set_all_active(h);
     if (h.dd) dd_load(h, b, x);
-    residual0(h, b, x, tol, true);
+    residual0(h, b, x, tol, true, x_zero);
     std::vector<double> r0(nd), rn(nd), bn(nd);
     std::vector<int> act(nd), itd(nd, 0);
     PR_CUDA(cudaMemcpyAsync(r0.data(), h.rnorm, sizeof(double) * nd, cudaMemcpyDeviceToHost, s));
     PR_CUDA(cudaMemcpyAsync(bn.data(), h.bnorm, sizeof(double) * nd, cudaMemcpyDeviceToHost, s));
     PR_CUDA(cudaMemcpyAsync(act.data(), h.active, sizeof(int) * nd, cudaMemcpyDeviceToHost, s));
     PR_CUDA(cudaStreamSynchronize(s));
-    account_outer(h, std::vector<char>(nd, 1));
+    if (!x_zero) account_outer(h, std::vector<char>(nd, 1));
     for (int d = 0; d < nd; ++d)
         if (!std::isfinite(r0[d]) || !std::isfinite(bn[d])) fail(PAIR_ERR_NAN, "NaN/Inf in right-hand side or residual");
     if (use_graph) ensure_graph(h, b, x, tol);
@@ -440,7 +441,7 @@ BatchSolve solve_batch(Hier &h, const double *b, double *x, double tol, int maxi
     PR_CUDA(cudaStreamSynchronize(s));
     BatchSolve out;
     out.iters = k;
-    out.outer = k + 1;
+    out.outer = k + (x_zero ? 0 : 1);
     for (int d = 0; d < nd; ++d) {
         if (!std::isfinite(rn[d])) fail(PAIR_ERR_NAN, "NaN/Inf in a residual during the AIR solve");
         double rel = bn[d] > 0 ? rn[d] / bn[d] : 0.0;
@@ -979,10 +980,10 @@ void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t,
         } else {
             PR_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * Bt.nd * N, hs));
             if (sp.inner_cycles > 0) {   // fixed approximate inverse: l cycles from zero
-                bs = solve_batch(h, Bt.b, x, 0.0, sp.inner_cycles, sp.use_graphs != 0);
+                bs = solve_batch(h, Bt.b, x, 0.0, sp.inner_cycles, sp.use_graphs != 0, true);
                 bs.converged = true;
             } else {
-                bs = solve_batch(h, Bt.b, x, sp.inner_tol, sp.inner_maxit, sp.use_graphs != 0);
+                bs = solve_batch(h, Bt.b, x, sp.inner_tol, sp.inner_maxit, sp.use_graphs != 0, true);
             }
         }
         if (!bs.converged) {
@@ -1265,7 +1266,7 @@ void si_adjoint_run(const pair_mesh &mesh, const pair_quad &quad, const double *
                 sweep_solve(h, Bt.b, Bt.xown, sp.use_graphs != 0);
             } else {
                 PR_CUDA(cudaMemsetAsync(Bt.xown, 0, sizeof(double) * Bt.nd * N, hs));
-                bs = solve_batch(h, Bt.b, Bt.xown, sp.inner_tol, sp.inner_maxit, sp.use_graphs != 0);
+                bs = solve_batch(h, Bt.b, Bt.xown, sp.inner_tol, sp.inner_maxit, sp.use_graphs != 0, true);
             }
             if (!bs.converged && it > 0) {   // the first right-hand side is zero
                 char buf2[160];
