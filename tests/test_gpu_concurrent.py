@@ -109,3 +109,24 @@ def test_adjoint_groups_agree(pair):
             assert np.array_equal(got.view(np.uint64), out[K].view(np.uint64))
         out[K] = got
     assert np.linalg.norm(out[3] - out[1]) <= 1e-10 * np.linalg.norm(out[1])
+
+
+def test_kernel_timing_changes_no_bit(pair):
+    """si_params.timing records CUDA events in the cycles of every k-th SI iteration
+    (its own captured graphs); it changes no arithmetic: the flux is bit-identical
+    with timing off, every iteration, or every second one, and the kernel timings
+    cover exactly the iterations asked for."""
+    prob = I.small_hex(6, order=4, seed=17, ratio=0.6)
+    air = pair.default_air_params(precision=1, theta=0.5, phi_A=0.05)
+    out = {}
+    for k in (0, 1, 2):
+        si = pair.default_si_params(tol=1e-12, max_iters=4, fixed_iters=1, inner_tol=1e-9, concurrent=1, timing=k)
+        phi, _, info = pair.si_solve(prob.n, prob.omega, prob.w, prob.sigma_t, prob.sigma_s, prob.q, air=air, si=si)
+        out[k] = (_np(phi).view(np.uint64), info)
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][0], out[2][0])
+    assert out[0][1]["timed_iters"] == 0 and out[0][1]["n_relax0"] == 0 and out[0][1]["t_relax0_ms"] == 0
+    assert out[1][1]["timed_iters"] == 4 and out[2][1]["timed_iters"] == 2
+    for k in (1, 2):
+        i = out[k][1]
+        assert i["n_relax0"] > 0 and i["t_relax0_ms"] > 0 and i["n_relaxc"] > 0 and i["n_res32"] > 0
+    assert out[1][1]["n_relax0"] > out[2][1]["n_relax0"]
