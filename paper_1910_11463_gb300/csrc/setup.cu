@@ -1407,18 +1407,32 @@ void build_hierarchy(Hier &h) {
         PR_LAUNCH();
         int und = 0;
         d2h(&und, d_count, 1, s);
+        // rounds in groups of PMIS_GROUP between host reads: a round after the last
+        // undecided point is gone changes nothing, and the per-round counts give the
+        // exact round count
+        constexpr int PMIS_GROUP = 4;
+        int *rcount = dmalloc<int>(PMIS_GROUP, s);
         int round = 0;
         while (und > 0) {
-            ++round;
             PR_REQUIRE(round < 10000, PAIR_ERR_DEVICE, "PMIS did not terminate");
-            k_pmis_mark<<<blocks_for(n, BS), BS, 0, s>>>(n, L.rowptr, L.col, S, key, st0, notmax, round);
-            PR_LAUNCH();
-            PR_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int), s));
-            k_pmis_update<<<blocks_for(n, BS), BS, 0, s>>>(n, L.rowptr, L.col, S, st0, st1, notmax, round, d_count);
-            PR_LAUNCH();
-            std::swap(st0, st1);
-            d2h(&und, d_count, 1, s);
+            PR_CUDA(cudaMemsetAsync(rcount, 0, sizeof(int) * PMIS_GROUP, s));
+            for (int g = 0; g < PMIS_GROUP; ++g) {
+                const int rd = round + 1 + g;
+                k_pmis_mark<<<blocks_for(n, BS), BS, 0, s>>>(n, L.rowptr, L.col, S, key, st0, notmax, rd);
+                PR_LAUNCH();
+                k_pmis_update<<<blocks_for(n, BS), BS, 0, s>>>(n, L.rowptr, L.col, S, st0, st1, notmax, rd,
+                                                               rcount + g);
+                PR_LAUNCH();
+                std::swap(st0, st1);
+            }
+            int cnt[PMIS_GROUP];
+            d2h(cnt, rcount, PMIS_GROUP, s);
+            int g = 0;
+            while (g < PMIS_GROUP - 1 && cnt[g] > 0) ++g;
+            round += g + 1;
+            und = cnt[g];
         }
+        dfree(rcount, s);
         L.pmis_rounds = round;
         PR_CUDA(cudaEventRecord(ev[1], s));
         PR_CUDA(cudaMemsetAsync(dnc, 0, sizeof(int) * ND, s));
