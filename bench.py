@@ -241,7 +241,8 @@ def bench_config(args, world):
                      "time (setup included); solve_only_value excludes the setup"),
             "air": {"R": "nAIR degree 1" if args.nair else f"lAIR distance {args.distance}",
                     "theta": args.theta, "eps_R": 0.01, "phi_R": args.phi_R, "phi_A": args.phi_A,
-                    "relax": "F-F-C Jacobi", "coarsening": "PMIS"},
+                    "relax": "F-F-C Jacobi", "coarsening": "PMIS", "max_coarse": args.max_coarse,
+                    "coarse_sweeps": args.coarse_sweeps},
             "l2": "working set per step >> 129 MB L2 (no flush needed)",
             "parallelism": (f"angular decomposition over {world} GPUs (directions split, scalar flux all-reduced "
                             "every SI iteration)") if world > 1 else (
@@ -251,6 +252,13 @@ def bench_config(args, world):
             "kernel_timing": f"CUDA events in the cycles of every {args.timing_every}th SI iteration",
             "precision": ("FP32 hierarchy/V-cycle, double-float refinement" if args.precision == 2 else
                           "FP32 hierarchy/V-cycle, FP64 refinement" if args.precision else "FP64")}
+
+
+def air_settings(args, distance=None):
+    """The AIR parameters of the timed runs (both arms)."""
+    return dict(theta=args.theta, phi_R=args.phi_R, phi_A=args.phi_A,
+                distance=args.distance if distance is None else distance, nair=args.nair,
+                max_coarse=args.max_coarse, coarse_sweeps=args.coarse_sweeps)
 
 
 def run_reference(args):
@@ -263,12 +271,12 @@ def run_reference(args):
     # sample); setup amortised over the SI iterations the workload needs
     from oracle import oracle as O
     O.build()
-    air_kw = dict(theta=args.theta, phi_R=args.phi_R, phi_A=args.phi_A, distance=args.distance, nair=args.nair)
+    akw = air_settings(args)
     fixed = args.si_fixed if args.si_fixed is not None else FIXED_SI.get(args.config, 0)
     si_iters = fixed or args.si_iters
     times = []
     for k in range(args.warmup + args.steps):
-        a, b = oracle_direction_times(prob, k % prob.M, air_kw)
+        a, b = oracle_direction_times(prob, k % prob.M, akw)
         if k >= args.warmup:
             times.append(a / si_iters + b)
     t = sum(times) / len(times)
@@ -308,8 +316,9 @@ def kernel_table(infos, steps, ms, tet, precision):
                                              else "CF-split block copy; one unit = one V-cycle's three sweeps"
                                              if precision else "block form; one unit = one V-cycle's sweeps"),
             tot("t_relax0_ms"), tot("n_relax0"), tot("gb_relax0")),
-        "k_relax_f+k_relax_c": ("FP32 F-F-C Jacobi, levels >= 1 (CF-split CSR); one unit = every coarse "
-                                "level's sweeps of one V-cycle", tot("t_relaxc_ms"), tot("n_relaxc"), tot("gb_relaxc")),
+        "k_relax_f+k_relax_c": ("FP32 F-F-C Jacobi, levels >= 1 (CF-split SELL copies), and the grid-wide "
+                                "coarsest-level Jacobi sweeps; one unit = every coarse level's sweeps of one "
+                                "V-cycle", tot("t_relaxc_ms"), tot("n_relaxc"), tot("gb_relaxc")),
     }
     if tot("n_res32") > 0:
         kern["k_res32_csr" if tet else "k_res32_bsr"] = (
@@ -337,7 +346,7 @@ def measure_workload(name, args, pair, I, torch, steps=2, warmup=1, fp64=False):
     geom = pair.TetMesh(prob.verts, prob.tets, prob.nbr) if tet else prob.n
     fixed = FIXED_SI.get(name, 0)
     distance = DISTANCE.get(name, 1)
-    kw = dict(theta=args.theta, phi_R=args.phi_R, phi_A=args.phi_A, distance=distance, nair=args.nair)
+    kw = air_settings(args, distance)
     air = pair.default_air_params(precision=args.precision, **kw)
     si = (pair.default_si_params(tol=1e-8, max_iters=fixed, fixed_iters=1, inner_tol=1e-8, inner_maxit=200,
                                  use_graphs=args.graphs, concurrent=args.concurrent,
@@ -377,7 +386,8 @@ def measure_workload(name, args, pair, I, torch, steps=2, warmup=1, fp64=False):
                       "one complete SI solve from phi=0") + " (every direction from psi=0 to a 1e-8 relative "
                      "residual each iteration); value = DOF*dir*iterations/step time",
              "air": {"R": "nAIR degree 1" if args.nair else f"lAIR distance {distance}", "theta": args.theta,
-                     "eps_R": 0.01, "phi_A": args.phi_A, "phi_R": args.phi_R},
+                     "eps_R": 0.01, "phi_A": args.phi_A, "phi_R": args.phi_R, "max_coarse": args.max_coarse,
+                     "coarse_sweeps": args.coarse_sweeps},
              "si_iterations": iters, "setup_ms": t_setup, "solve_ms": t_solve,
              "solve_only_value": N * M * iters / (t_solve * 1e-3) if t_solve > 0 else None,
              "setup_phase_ms": dict(zip(("strength+pmis", "p+lair", "rap", "assembly+other"),
@@ -433,7 +443,7 @@ def run_ours(args):
     N, M = prob.N, prob.M
     geom = pair.TetMesh(prob.verts, prob.tets, prob.nbr) if hasattr(prob, "tets") else prob.n
     fixed = args.si_fixed if args.si_fixed is not None else FIXED_SI.get(args.config, 0)
-    tuned = dict(theta=args.theta, phi_R=args.phi_R, phi_A=args.phi_A, distance=args.distance, nair=args.nair)
+    tuned = air_settings(args)
     air = pair.default_air_params(precision=args.precision, **tuned)
     if fixed:
         si = pair.default_si_params(tol=1e-8, max_iters=fixed, fixed_iters=1, inner_tol=1e-8, inner_maxit=200,
@@ -717,6 +727,10 @@ def main():
     ap.add_argument("--theta", type=float, default=0.5)
     ap.add_argument("--phi-R", dest="phi_R", type=float, default=0.0)
     ap.add_argument("--phi-A", dest="phi_A", type=float, default=0.05)
+    ap.add_argument("--max-coarse", dest="max_coarse", type=int, default=8000,
+                    help="a level with at most this many rows per direction is the coarsest (library default 100)")
+    ap.add_argument("--coarse-sweeps", dest="coarse_sweeps", type=int, default=2,
+                    help="Jacobi sweeps from zero on the coarsest level (library default 20)")
     ap.add_argument("--nair", type=int, default=0, choices=[0, 1],
                     help="1: R from degree-1 nAIR (Neumann series) instead of lAIR local solves")
     ap.add_argument("--distance", type=int, default=None, choices=[1, 2],
@@ -767,8 +781,7 @@ def run_eps_study(args):
     rows = []
     for distance in (1, 2):
         for eps in (0.001, 0.01, 0.1, 0.25):
-            air = pair.default_air_params(precision=args.precision, theta=args.theta, phi_R=args.phi_R,
-                                          phi_A=args.phi_A, distance=distance, eps_R=eps)
+            air = pair.default_air_params(precision=args.precision, eps_R=eps, **air_settings(args, distance))
             for _ in range(2):   # the first run also tunes the new shapes
                 phi, _, info = pair.si_solve(prob.n, prob.omega, prob.w, st, ss, qq, air=air, si=si)
             torch.cuda.synchronize()
@@ -827,8 +840,7 @@ def run_one_iteration(args):
     from paper_1910_11463_gb300 import inputs as I
     from paper_1910_11463_gb300 import pair
     prob = I.config(args.config)
-    air = pair.default_air_params(precision=args.precision, theta=args.theta, phi_R=args.phi_R, phi_A=args.phi_A,
-                                  distance=args.distance, nair=args.nair)
+    air = pair.default_air_params(precision=args.precision, **air_settings(args))
     si = pair.default_si_params(tol=1e-8, max_iters=1, inner_tol=1e-8, inner_maxit=200,
                                 use_graphs=args.graphs, concurrent=args.concurrent, timing=0)
     phi, _, info = pair.si_solve_problem(prob, air=air, si=si)

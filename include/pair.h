@@ -64,7 +64,9 @@ typedef struct pair_hier_s *pair_hier;
  *  phi_A         filter applied to every coarse operator, diagonal kept (0 = off)
  *  max_levels    level cap (including the finest)
  *  max_coarse    a level with at most this many rows is the coarsest
- *  coarse_sweeps pointwise Jacobi sweeps on the coarsest level
+ *  coarse_sweeps pointwise Jacobi sweeps from zero on the coarsest level (one CTA
+ *                per matrix in shared memory while a matrix's coarsest level fits
+ *                40 KB; larger coarsest levels sweep grid-wide, one launch per sweep)
  *  seed          PMIS key hash seed
  *  precision     0: hierarchy values and V-cycle in FP64;
  *                1: FP32 hierarchy and V-cycle under FP64 iterative refinement
@@ -315,7 +317,8 @@ typedef struct {
     double gb_relax0;
     double t_setup_phase_ms[4]; /* strength+PMIS, P+lAIR, Galerkin RAP, other setup (with
                                  * concurrent groups: those of the longest batch setup) */
-    double t_relaxc_ms;      /* F- and C-Jacobi passes on levels >= 1 (CSR), all cycles */
+    double t_relaxc_ms;      /* F- and C-Jacobi passes on levels >= 1 (SELL copies) and
+                              * the grid-wide coarsest sweeps of levels >= 1, all cycles */
     int n_relaxc;            /* cycles measured */
     double gb_relaxc;        /* algorithmic GB of those passes */
     double t_res32_ms;       /* FP32 inner residuals r - A d of the refinement steps */

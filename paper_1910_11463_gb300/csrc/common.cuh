@@ -164,12 +164,14 @@ struct Level {
     // CF split for the V-cycle: srow lists the rows in the order [F | C | coarsest],
     // ascending within each group; sF, sC: SELL copies of the F and C rows, sZ of Z
     // (values in the cycle precision); sptr/scol/sval: CSR copy of the coarsest rows
-    // in split order, d_cseg_s0: each coarsest segment's first position in it
+    // in split order, d_cseg_s0: each coarsest segment's first position in it; sX:
+    // SELL copy of the coarsest rows, built when a coarsest segment is too large for
+    // the one-CTA shared-memory sweeps (its Jacobi sweeps then run grid-wide)
     int nF = 0, nC = 0;
     int *srow = nullptr, *sptr = nullptr, *scol = nullptr;
     void *sval = nullptr;
     int *d_cseg_s0 = nullptr;
-    Sell sF, sC, sZ;
+    Sell sF, sC, sZ, sX;
     // V-cycle work vectors (precision of the hierarchy); vF is the buffer (vy or vxn)
     // that holds the F rows after the last F sweep, C rows are then in vx
     void *vb = nullptr, *vx = nullptr, *vxn = nullptr, *vy = nullptr;
@@ -180,6 +182,11 @@ struct Level {
 // single elements grouped by upwind level, and the cyclic components (strongly
 // connected sets of at most SD_MAXE elements, solved as dense blocks) per level.
 constexpr int SD_MAXE = 8;
+
+// Shared memory of the one-CTA coarsest-level sweeps: a coarsest segment whose
+// entries (value + column), four vectors and row pointer fit is swept in shared
+// memory; a level with a larger one gets a SELL copy of its coarsest rows instead.
+constexpr int CS_SMEM = 40 * 1024;
 struct SweepPlan {
     int nb = 0, nlev = 0, ncomp = 0;
     int *list = nullptr;                     // single elements, level by level
@@ -196,6 +203,7 @@ struct ProfSlot {
     cudaEvent_t relax0[2] = {nullptr, nullptr};
     cudaEvent_t res32[2] = {nullptr, nullptr};
     std::vector<cudaEvent_t> lv;
+    std::vector<cudaEvent_t> lvx;   // grid-wide coarsest sweeps of a level (2 per level)
     bool relax_timed = false;   // relax0 recorded by the cycle
     bool res_timed = false;     // res32 recorded by the cycle
 };

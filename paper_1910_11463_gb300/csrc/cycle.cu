@@ -665,6 +665,20 @@ __global__ void k_fold_coarsest(int n, const T *xco, double *x64, float *d32, fl
     }
 }
 
+// first coarsest Jacobi sweep from x = 0 on the coarsest rows of the split (positions
+// [kX, n)): x = D^{-1} b, the value x + D^{-1}(b - A x) takes at x = 0 (zero: no
+// sweep, x = 0)
+template <class T>
+__global__ void k_jacobi0(int kX, int n, const int *srow, const T *dinv, const T *b, T *x, int zero,
+                          const int *any) {
+    pdl_begin();
+    if (any && !*any) return;
+    const long long p = kX + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int i = srow[p];
+    x[i] = zero ? T(0) : dinv[i] * b[i];
+}
+
 // final correction at a CSR level 0: x64 += the coarsest solution on the rows of
 // matrices that end there (split positions [kX, n))
 template <class T>
@@ -814,7 +828,9 @@ __global__ void k_split0_copy(int nrows, int N, const int *srow, const float *bs
 // shared memory once and swept there (each sweep of a global-memory segment is a
 // chain of L2 round trips: 20 sweeps of a 31-row segment took ~15 us); columns are
 // rebased to the segment, so the sums run in the same order and round alike.
-constexpr int CS_SMEM = 40 * 1024;
+// Levels with a larger segment sweep grid-wide on a SELL copy of their coarsest
+// rows instead (coarsest_sell); the global-memory path below remains for segments
+// whose columns leave the segment.
 
 // The Jacobi sweeps of one segment by the whole CTA (sm: CS_SMEM bytes of shared
 // memory, bad: one shared int)
@@ -971,6 +987,32 @@ void relax_c(const Level &L, const T *b, const T *in, T *out, double *x64, float
     }
 }
 
+// coarse_sweeps Jacobi sweeps from 0 over the coarsest rows of a level that has a
+// SELL copy of them: the first is x = D^{-1} b, each further one a grid-wide SELL
+// sweep; the buffers alternate so that the last sweep writes vx (which the
+// prolongation and the level-0 fold read)
+template <class T>
+void coarsest_sell(const Level &L, int sweeps, const int *any, int sms, cudaStream_t s) {
+    T *vx = (T *)L.vx, *vxn = (T *)L.vxn;
+    const int kX = L.nF + L.nC;
+    T *cur = (sweeps > 1 && (sweeps - 1) % 2 == 1) ? vxn : vx;
+    launch_pdl(k_jacobi0<T>, blocks_for(L.n - kX, BS), BS, s, kX, L.n, L.srow, lv_dinv<T>(L), (const T *)L.vb, cur,
+               sweeps == 0 ? 1 : 0, any);
+    PR_LAUNCH();
+    for (int k = 1; k < sweeps; ++k) {
+        T *nxt = cur == vx ? vxn : vx;
+        SellJob<T> j{};
+        j.any = any;
+        j.in = cur;
+        j.dinv = lv_dinv<T>(L);
+        j.b = (const T *)L.vb;
+        j.out = nxt;
+        j.rowdir = L.rowdir;
+        launch_sell<T, SM_F>(L.sX, j, sms, s);
+        cur = nxt;
+    }
+}
+
 // b_c = Z b_F + b_C: one row of Z per coarse point
 template <class T>
 void restrict_(const Level &L, const T *bf, T *bc, const int *any, int sms, cudaStream_t s) {
@@ -997,7 +1039,12 @@ void vcycle_t(Hier &h, double *x64, float *d32, const int *active, ProfSlot *ps)
         Level &L = h.lev[l];
         L.vF = L.vx;   // replaced by the F sweeps' buffer once the level relaxes
         if (l + 1 < NL) restrict_<T>(L, (const T *)L.vb, (T *)h.lev[l + 1].vb, any, h.sms, s);
-        if (L.n_cseg) {
+        if (L.n_cseg && L.sX.nrows > 0) {
+            const bool tx = prof && l >= 1 && (int)ps->lvx.size() >= 2 * (l + 1);
+            if (tx) rec_event(ps->lvx[2 * l], s);
+            coarsest_sell<T>(L, h.prm.coarse_sweeps, any, h.sms, s);
+            if (tx) rec_event(ps->lvx[2 * l + 1], s);
+        } else if (L.n_cseg) {
             launch_pdl(k_coarsest<T>, L.n_cseg, 256, s, L.d_cseg_row0, L.d_cseg_n, L.d_cseg_s0, L.sptr, L.scol,
                                                    (const T *)L.sval, lv_dinv<T>(L), (const T *)L.vb, (T *)L.vx,
                                                    (T *)L.vxn, h.prm.coarse_sweeps, any);
@@ -1219,6 +1266,17 @@ void level0_bytes(Hier &h) {
             h.bytes_relaxc += h.prm.f_sweeps * fpass + cpass;
         }
         dfree(cnt, s);
+        // grid-wide coarsest sweeps: the first reads each row's split position, b and
+        // dinv and writes its value; each further one counts as an F sweep
+        for (size_t l = 1; l < h.lev.size(); ++l) {
+            const Level &L = h.lev[l];
+            if (L.sX.nrows <= 0 || h.prm.coarse_sweeps <= 0) continue;
+            double nz = 0;
+            for (int d = 0; d < h.ndir; ++d)
+                if (L.nrows[d] > 0 && L.coarsest[d]) nz += L.nnzdir[d];
+            const double nx = L.sX.nrows, cb = L.sX.col16 ? 2.0 : 4.0;
+            h.bytes_relaxc += nx * (4 + 3 * sT) + (h.prm.coarse_sweeps - 1) * (nx * (8 + 4 * sT) + nz * (cb + sT));
+        }
     }
     if (!h.bsr0) {
         // CSR level 0 (tetrahedra): residual reads every entry (column + FP64 value), b
@@ -1289,6 +1347,8 @@ void prof_enable(Hier &h) {
         for (auto &e : ps.res32) PR_CUDA(cudaEventCreate(&e));
         ps.lv.assign(2 * h.lev.size(), nullptr);
         for (auto &e : ps.lv) PR_CUDA(cudaEventCreate(&e));
+        ps.lvx.assign(2 * h.lev.size(), nullptr);
+        for (auto &e : ps.lvx) PR_CUDA(cudaEventCreate(&e));
     }
     h.prof = true;
 }
@@ -1455,6 +1515,7 @@ void autotune_t(Hier &h) {
         j.rowdir = L.rowdir;
         tune_store<T, SM_F>(L.sF, j, s, e0, e1);
         tune_store<T, SM_C>(L.sC, j, s, e0, e1);
+        tune_store<T, SM_F>(L.sX, j, s, e0, e1);
         if (l + 1 < NL && L.sZ.nrows > 0) {
             SellJob<T> r{};
             r.in = (const T *)L.vb;

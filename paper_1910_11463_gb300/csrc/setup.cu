@@ -1291,6 +1291,18 @@ void build_split(Hier &h, Level &L, bool with_fc) {
         }
     PR_REQUIRE(pos == nx, PAIR_ERR_DEVICE, "coarsest rows differ from the coarsest segments");
     PR_REQUIRE((int)s0.size() == L.n_cseg, PAIR_ERR_DEVICE, "coarsest segment count mismatch");
+    // a segment too large for the one-CTA shared-memory sweeps: SELL copy of every
+    // coarsest row of the level, swept grid-wide
+    bool big = false;
+    for (int d = 0; d < h.ndir; ++d)
+        if (L.nrows[d] > 0 && L.coarsest[d]) {
+            const size_t nr = (size_t)L.nrows[d], nz = (size_t)L.nnzdir[d];
+            big |= nz * (es + sizeof(int)) + 4 * nr * es + (nr + 1) * sizeof(int) > (size_t)CS_SMEM;
+        }
+    if (big) {
+        build_sell(h, L.sX, L.srow + kX, nx, L.rowptr, L.col, L.val);
+        sell_compress_cols(h, L.sX);
+    }
     if (!s0.empty()) {
         L.d_cseg_s0 = dmalloc<int>(s0.size(), s);
         PR_CUDA(cudaMemcpyAsync(L.d_cseg_s0, s0.data(), sizeof(int) * s0.size(), cudaMemcpyHostToDevice, s));
@@ -1306,7 +1318,7 @@ void free_level(Level &L, cudaStream_t s) {
                     L.srow, L.sptr, L.scol, L.sval, L.d_cseg_s0,
                     L.sF.ptr, L.sF.row, L.sF.len, L.sF.col, L.sF.col16, L.sF.val, L.sC.ptr, L.sC.row, L.sC.len,
                     L.sC.col, L.sC.col16, L.sC.val, L.sZ.ptr, L.sZ.row, L.sZ.len, L.sZ.col, L.sZ.val,
-                    L.vb, L.vx, L.vxn, L.vy};
+                    L.sX.ptr, L.sX.row, L.sX.len, L.sX.col, L.sX.col16, L.sX.val, L.vb, L.vx, L.vxn, L.vy};
     for (void *p : ptrs) dfree(p, s);
     L = Level();
 }

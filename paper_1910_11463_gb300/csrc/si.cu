@@ -190,6 +190,14 @@ void account_cycle(Hier &h, const ProfSlot &ps, const std::vector<char> &part) {
             h.t_relaxc_level[std::min<size_t>(l, 8) - 1] += t;
             ++nl;
         }
+        // grid-wide coarsest sweeps (levels with a SELL copy of their coarsest rows)
+        for (size_t l = 1; l < h.lev.size() && 2 * l + 1 < ps.lvx.size(); ++l) {
+            if (h.lev[l].sX.nrows <= 0) continue;
+            const float t = elapsed_ms(ps.lvx[2 * l], ps.lvx[2 * l + 1]);
+            tl += t;
+            h.t_relaxc_level[std::min<size_t>(l, 8) - 1] += t;
+            ++nl;
+        }
         if (nl) {
             h.t_relaxc += tl;
             h.n_relaxc += 1;
@@ -591,6 +599,8 @@ Hier::~Hier() {
         for (auto &e : ps.res32)
             if (e) cudaEventDestroy(e);
         for (auto &e : ps.lv)
+            if (e) cudaEventDestroy(e);
+        for (auto &e : ps.lvx)
             if (e) cudaEventDestroy(e);
     }
     if (stream) {

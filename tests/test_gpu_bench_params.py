@@ -2,11 +2,16 @@
 R pattern, Sec. 4.1.2 filtering): theta = 0.5 for the CF splitting, eps_R = 0.01
 for the R pattern, the coarse-operator filter phi_A = 0.05, distance 1 on hexes and
 distance 2 on tets; and nAIR of degree 1 with the R filter phi_R = 0.1 under the
-same phi_A.  Every level of every hierarchy is bit-identical to the oracle's (CF
-splitting, P, R pattern and values, filtered coarse structure and values), on a
+same phi_A.  The benchmark's coarsest level is the first with at most 8000 rows,
+relaxed by two Jacobi sweeps from zero (a grid-wide sweep on a SELL copy of the
+coarsest rows).  Every level of every hierarchy is bit-identical to the oracle's
+(CF splitting, P, R pattern and values, filtered coarse structure and values), on a
 small ragged batch and on full-size directions of the 32^3 hex and 40^3 tet
-workloads; source iteration at those parameters matches the oracle within the
-FP64 (1e-10) and FP32-refined (1e-7, residual <= tol) tolerances."""
+workloads at the benchmark's coarsest size; source iteration at those parameters
+matches the oracle within the FP64 (1e-10) and FP32-refined (1e-7, residual <= tol)
+tolerances, with the library's coarsest level and with a coarsest level of about
+900 rows (hex) / 600 rows (tets) per direction under two sweeps, the small-mesh
+counterpart of the benchmark's."""
 import numpy as np
 import pytest
 
@@ -18,6 +23,9 @@ from paper_1910_11463_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 BENCH = dict(theta=0.5, eps_R=0.01, phi_A=0.05)
+BENCH_COARSE = dict(max_coarse=8000, coarse_sweeps=2)
+# small meshes: a coarsest level too large for the one-CTA shared-memory sweeps
+SMALL_COARSE = [dict(max_coarse=100, coarse_sweeps=20), dict(max_coarse=1000, coarse_sweeps=2)]
 
 
 @pytest.fixture(scope="module")
@@ -100,7 +108,7 @@ def test_bench_params_hex32_full_size_bit_exact(pair):
     """Two full-size 32^3 S4 directions (262,144 DOFs each), batched as the bench
     batches them: every level bit-identical at the bench's parameters."""
     prob = I.config("hex32_s4")
-    kw = dict(BENCH, distance=1)
+    kw = dict(BENCH, distance=1, **BENCH_COARSE)
     st = torch.as_tensor(prob.sigma_t, device="cuda")
     dirs = (3, 20)
     Hg = pair.Hierarchy([pair.dg_assemble_hex(prob.n, prob.omega[m], st) for m in dirs],
@@ -114,7 +122,7 @@ def test_bench_params_tet40_full_size_bit_exact(pair):
     """Two full-size 40^3 x 6 checkerboard tet directions (1,536,000 DOFs each),
     distance-2 lAIR at the bench's parameters: every level bit-identical."""
     prob = I.config("tet40_s8")
-    kw = dict(BENCH, distance=2)
+    kw = dict(BENCH, distance=2, **BENCH_COARSE)
     mesh = pair.TetMesh(prob.verts, prob.tets, prob.nbr)
     st = torch.as_tensor(prob.sigma_t, device="cuda")
     dirs = (5, 41)
@@ -126,13 +134,14 @@ def test_bench_params_tet40_full_size_bit_exact(pair):
         del mat
 
 
+@pytest.mark.parametrize("coarse", SMALL_COARSE)
 @pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-7), (2, 1e-7)])
 @pytest.mark.parametrize("nair,phi_R", [(0, 0.0), (1, 0.1)])
-def test_bench_params_si_hex_matches_oracle(pair, precision, tol, nair, phi_R):
+def test_bench_params_si_hex_matches_oracle(pair, precision, tol, nair, phi_R, coarse):
     """SI at the bench's parameters, FP64 cycles (0), FP32 cycles under FP64
     refinement (1, the bench headline) and under double-float refinement (2)."""
     prob = I.small_hex(10, order=4, seed=8, ratio=0.8)
-    kw = dict(BENCH, distance=1, nair=nair, phi_R=phi_R)
+    kw = dict(BENCH, distance=1, nair=nair, phi_R=phi_R, **coarse)
     ref, _, info_o = O.si_hex(prob, tol=1e-10, inner_tol=1e-11, params=O.default_params(**kw))
     assert info_o["rc"] == 0
     inner = 1e-11 if precision == 0 else 1e-9
@@ -142,11 +151,12 @@ def test_bench_params_si_hex_matches_oracle(pair, precision, tol, nair, phi_R):
     assert np.linalg.norm(_cpu(phi) - ref) <= tol * np.linalg.norm(ref)
 
 
+@pytest.mark.parametrize("coarse", SMALL_COARSE)
 @pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-7)])
-def test_bench_params_si_tet_matches_oracle(pair, precision, tol):
+def test_bench_params_si_tet_matches_oracle(pair, precision, tol, coarse):
     """SI on jittered tets with distance-2 lAIR at the bench's parameters."""
     prob = I.small_tet(5, order=4, seed=3, ratio=0.7)
-    kw = dict(BENCH, distance=2)
+    kw = dict(BENCH, distance=2, **coarse)
     ref, _, info_o = O.si_tet(prob, tol=1e-11, inner_tol=1e-12, params=O.default_params(**kw))
     assert info_o["rc"] == 0
     inner = 1e-12 if precision == 0 else 1e-10

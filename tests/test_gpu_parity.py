@@ -137,6 +137,42 @@ def test_vcycle_fp64_matches_oracle(pair):
         assert np.linalg.norm(xg[sl] - xo) <= 1e-12 * np.linalg.norm(xo)
 
 
+def _coarsest_smem_bytes(L, es):
+    """Shared memory the one-CTA coarsest sweeps need for a matrix's coarsest level
+    (entries as value + column, four vectors, row pointer)."""
+    return L.nnz * (es + 4) + 4 * L.n * es + (L.n + 1) * 4
+
+
+@pytest.mark.parametrize("sweeps", [0, 1, 2, 3])
+def test_vcycle_fp64_grid_coarsest_matches_oracle(pair, sweeps):
+    """Coarsest levels too large for the one-CTA shared-memory sweeps (335-368 rows of
+    an 8^3 direction at max_coarse 350): their Jacobi sweeps run grid-wide on a SELL
+    copy.  Four of the eight directions end on level 2 and four continue to level 3,
+    so level 2 holds both F/C rows and coarsest rows; 0-3 sweeps cover the buffer
+    alternation.  One FP64 V-cycle matches the oracle's to 1e-12."""
+    prob = I.small_hex(8, order=2, seed=4)
+    rng = np.random.default_rng(1)
+    kw = dict(max_coarse=350, coarse_sweeps=sweeps)
+    mats_o = [O.hex_assemble(prob.n, prob.omega[m], prob.sigma_t) for m in range(prob.M)]
+    mats_g = [_gpu_csr(pair, prob.n, prob.omega[m], prob.sigma_t) for m in range(prob.M)]
+    H_g = pair.Hierarchy(mats_g, pair.default_air_params(precision=0, **kw))
+    depth = [H_g.nlevels(m) for m in range(prob.M)]
+    assert 3 in depth and 4 in depth, depth
+    big = [_coarsest_smem_bytes(H_g.level(m, 2), 8) for m in range(prob.M) if depth[m] == 3]
+    assert min(big) > 40 * 1024, big
+    b = rng.random(prob.M * prob.N)
+    x0 = rng.random(prob.M * prob.N)
+    xg = torch.as_tensor(x0, device="cuda").clone()
+    H_g.vcycle(torch.as_tensor(b, device="cuda"), xg)
+    xg = _cpu(xg)
+    for m in range(prob.M):
+        sl = slice(m * prob.N, (m + 1) * prob.N)
+        H_o = O.Hierarchy(*mats_o[m], O.default_params(**kw))
+        assert H_o.nlev == depth[m]
+        xo = H_o.vcycle(b[sl], x0[sl])
+        assert np.linalg.norm(xg[sl] - xo) <= 1e-12 * np.linalg.norm(xo), m
+
+
 @pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-10)])
 def test_air_solve_equals_sweep(pair, precision, tol):
     prob = I.small_hex(7, order=2, seed=6)
