@@ -2,15 +2,15 @@
 R pattern, Sec. 4.1.2 filtering): theta = 0.5 for the CF splitting, eps_R = 0.01
 for the R pattern, the coarse-operator filter phi_A = 0.05, distance 1 on hexes and
 distance 2 on tets; and nAIR of degree 1 with the R filter phi_R = 0.1 under the
-same phi_A.  The benchmark's coarsest level is the first with at most 8000 rows,
-relaxed by two Jacobi sweeps from zero (a grid-wide sweep on a SELL copy of the
+same phi_A.  The benchmark's coarsest level is the first with at most 40000 rows,
+relaxed by three Jacobi sweeps from zero (grid-wide sweeps on a SELL copy of the
 coarsest rows).  Every level of every hierarchy is bit-identical to the oracle's
 (CF splitting, P, R pattern and values, filtered coarse structure and values), on a
 small ragged batch and on full-size directions of the 32^3 hex and 40^3 tet
 workloads at the benchmark's coarsest size; source iteration at those parameters
 matches the oracle within the FP64 (1e-10) and FP32-refined (1e-7, residual <= tol)
 tolerances, with the library's coarsest level and with a coarsest level of about
-900 rows (hex) / 600 rows (tets) per direction under two sweeps, the small-mesh
+900 rows (hex) / 600 rows (tets) per direction under three sweeps, the small-mesh
 counterpart of the benchmark's."""
 import numpy as np
 import pytest
@@ -23,9 +23,9 @@ from paper_1910_11463_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 BENCH = dict(theta=0.5, eps_R=0.01, phi_A=0.05)
-BENCH_COARSE = dict(max_coarse=8000, coarse_sweeps=2)
+BENCH_COARSE = dict(max_coarse=40000, coarse_sweeps=3)
 # small meshes: a coarsest level too large for the one-CTA shared-memory sweeps
-SMALL_COARSE = [dict(max_coarse=100, coarse_sweeps=20), dict(max_coarse=1000, coarse_sweeps=2)]
+SMALL_COARSE = [dict(max_coarse=100, coarse_sweeps=20), dict(max_coarse=1000, coarse_sweeps=3)]
 
 
 @pytest.fixture(scope="module")
