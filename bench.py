@@ -320,6 +320,10 @@ def kernel_table(infos, steps, ms, tet, precision):
                                 "coarsest-level Jacobi sweeps; one unit = every coarse level's sweeps of one "
                                 "V-cycle", tot("t_relaxc_ms"), tot("n_relaxc"), tot("gb_relaxc")),
     }
+    if tot("n_xfer") > 0:
+        kern["k_restrict+k_prolong"] = (
+            "grid transfers: every level's restriction b_l+1 = R_l b_l (SELL copy of Z) and one-point "
+            "prolongation; one unit = one V-cycle's", tot("t_xfer_ms"), tot("n_xfer"), tot("gb_xfer"))
     if tot("n_res32") > 0:
         kern["k_res32_csr" if tet else "k_res32_bsr"] = (
             "FP32 inner residual r - A d of a refinement step, level 0 " + ("CSR" if tet else "block form"),

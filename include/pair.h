@@ -330,6 +330,10 @@ typedef struct {
                                   * entry also holds deeper levels) */
     int timed_iters;         /* SI iterations whose cycles the kernel timings cover
                               * (si_params.timing) */
+    double t_xfer_ms;        /* grid transfers: every level's restriction (R_l applied to
+                              * b_l) and one-point prolongation, all cycles */
+    int n_xfer;              /* cycles measured */
+    double gb_xfer;          /* algorithmic GB of those transfers */
 } si_info;
 
 /* Source iteration (Eq. sn_transport with Eq. angular_quad): each iteration

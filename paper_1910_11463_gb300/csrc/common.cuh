@@ -204,6 +204,7 @@ struct ProfSlot {
     cudaEvent_t res32[2] = {nullptr, nullptr};
     std::vector<cudaEvent_t> lv;
     std::vector<cudaEvent_t> lvx;   // grid-wide coarsest sweeps of a level (2 per level)
+    std::vector<cudaEvent_t> lvt;   // a level's restriction and prolongation (4 per level)
     bool relax_timed = false;   // relax0 recorded by the cycle
     bool res_timed = false;     // res32 recorded by the cycle
 };
@@ -313,6 +314,9 @@ struct Hier {
     double t_relaxc = 0, gb_relaxc = 0, bytes_relaxc = 0;
     double t_relaxc_level[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // by level (entry k: level k + 1)
     long long n_relaxc = 0;
+    // grid transfers (every level's restriction and prolongation): bytes per cycle
+    double t_xfer = 0, gb_xfer = 0, bytes_xfer = 0;
+    long long n_xfer = 0;
     SweepPlan *dag = nullptr;   // exact-sweep schedule of an unstructured batch
     ~Hier();
 };

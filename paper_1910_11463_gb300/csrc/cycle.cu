@@ -481,57 +481,68 @@ __global__ void k_sumsq_rows(const int *row0, const int *nrow, const double *v, 
 // added in ascending entry order.
 constexpr int SELL_U = 8;
 
-template <class T, int G>
+template <class T, int G, int U>
 __device__ __forceinline__ T sell_dot(int base, int len, int g, const int *col, const T *val, const T *in) {
     T acc = T(0);
-    for (int j0 = g; j0 < len; j0 += SELL_U * G) {
-        int c[SELL_U];
-        T v[SELL_U], x[SELL_U];
+    for (int j0 = g; j0 < len; j0 += U * G) {
+        int c[U];
+        T v[U], x[U];
 #pragma unroll
-        for (int u = 0; u < SELL_U; ++u) {
+        for (int u = 0; u < U; ++u) {
             const bool ok = j0 + u * G < len;
             c[u] = ok ? __ldcs(col + base + 32 * (j0 + u * G)) : 0;
             v[u] = ok ? __ldcs(val + base + 32 * (j0 + u * G)) : T(0);
         }
 #pragma unroll
-        for (int u = 0; u < SELL_U; ++u) x[u] = j0 + u * G < len ? in[c[u]] : T(0);
+        for (int u = 0; u < U; ++u) x[u] = j0 + u * G < len ? in[c[u]] : T(0);
 #pragma unroll
-        for (int u = 0; u < SELL_U; ++u)
+        for (int u = 0; u < U; ++u)
             if (j0 + u * G < len) acc += v[u] * x[u];
     }
     return acc;
 }
 
 // the same with 16-bit column offsets from the row r (col = r + offset)
-template <class T, int G>
+template <class T, int G, int U>
 __device__ __forceinline__ T sell_dot16(int base, int len, int g, int r, const short *col16, const T *val,
                                         const T *in) {
     T acc = T(0);
-    for (int j0 = g; j0 < len; j0 += SELL_U * G) {
-        int c[SELL_U];
-        T v[SELL_U], x[SELL_U];
+    for (int j0 = g; j0 < len; j0 += U * G) {
+        int c[U];
+        T v[U], x[U];
 #pragma unroll
-        for (int u = 0; u < SELL_U; ++u) {
+        for (int u = 0; u < U; ++u) {
             const bool ok = j0 + u * G < len;
             c[u] = ok ? r + (int)__ldcs(col16 + base + 32 * (j0 + u * G)) : 0;
             v[u] = ok ? __ldcs(val + base + 32 * (j0 + u * G)) : T(0);
         }
 #pragma unroll
-        for (int u = 0; u < SELL_U; ++u) x[u] = j0 + u * G < len ? in[c[u]] : T(0);
+        for (int u = 0; u < U; ++u) x[u] = j0 + u * G < len ? in[c[u]] : T(0);
 #pragma unroll
-        for (int u = 0; u < SELL_U; ++u)
+        for (int u = 0; u < U; ++u)
             if (j0 + u * G < len) acc += v[u] * x[u];
     }
     return acc;
 }
 
+
 enum SellMode : int { SM_F = 0, SM_C = 1, SM_C_FINAL = 2, SM_RESTRICT = 3 };
+
+// entries per lane issued together: SELL_U for the sweeps; the restriction's short
+// rows (6-9 entries) take SELL_U / G, so a row's G lanes together still cover SELL_U
+// entries per pass without predicated-off slots (the same for the sweeps measured no
+// faster)
+template <int MODE, int G>
+constexpr int sell_unroll() {
+    return MODE == SM_RESTRICT ? (SELL_U / G > 1 ? SELL_U / G : 1) : SELL_U;
+}
 
 template <class T>
 struct SellJob {
     int npos;
     const int *ptr, *row, *len, *col;
-    const short *col16;   // the relaxation stores' row-relative columns (col is then null)
+    const short *col16;   // 16-bit column offsets from the row (restriction: from its coarse
+                          // point's fine row); col is then null
     const T *val;
     const T *in;          // vector the rows multiply
     const T *dinv, *b;    // sweeps
@@ -561,19 +572,22 @@ __global__ void __launch_bounds__(BS) k_sell(SellJob<T> j) {
     if (MODE != SM_RESTRICT && ok && j.active && !j.active[j.rowdir[r]]) ok = false;
     const int len = ok ? j.len[q] : 0;
     const int base = j.ptr[q >> 5] + (q & 31);
-    // the row's own operands are loaded before the dot product (shorter chain)
+    // the row's own operands are loaded before the dot product (shorter chain); a
+    // restriction row's 16-bit columns are offsets from its coarse point's fine row
     T own = T(0), di = T(0), bi = T(0);
+    const int rb = (MODE == SM_RESTRICT && ok && j.col16) ? j.cpts[r] : r;
     if (ok && g == 0) {
         if (MODE == SM_RESTRICT) {
-            own = j.in[j.cpts[r]];
+            own = j.in[j.col16 ? rb : j.cpts[r]];
         } else {
             own = j.in[r];
             di = j.dinv[r];
             bi = j.b[r];
         }
     }
-    T acc = (MODE != SM_RESTRICT && j.col16) ? sell_dot16<T, G>(base, len, g, r, j.col16, j.val, j.in)
-                                             : sell_dot<T, G>(base, len, g, j.col, j.val, j.in);
+    constexpr int U = sell_unroll<MODE, G>();
+    T acc = j.col16 ? sell_dot16<T, G, U>(base, len, g, rb, j.col16, j.val, j.in)
+                    : sell_dot<T, G, U>(base, len, g, j.col, j.val, j.in);
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, G);
     if (!ok || g != 0) return;
@@ -1038,7 +1052,12 @@ void vcycle_t(Hier &h, double *x64, float *d32, const int *active, ProfSlot *ps)
     for (int l = 0; l < NL; ++l) {
         Level &L = h.lev[l];
         L.vF = L.vx;   // replaced by the F sweeps' buffer once the level relaxes
-        if (l + 1 < NL) restrict_<T>(L, (const T *)L.vb, (T *)h.lev[l + 1].vb, any, h.sms, s);
+        if (l + 1 < NL) {
+            const bool tr = prof && (int)ps->lvt.size() >= 4 * (l + 1);
+            if (tr) rec_event(ps->lvt[4 * l], s);
+            restrict_<T>(L, (const T *)L.vb, (T *)h.lev[l + 1].vb, any, h.sms, s);
+            if (tr) rec_event(ps->lvt[4 * l + 1], s);
+        }
         if (L.n_cseg && L.sX.nrows > 0) {
             const bool tx = prof && l >= 1 && (int)ps->lvx.size() >= 2 * (l + 1);
             if (tx) rec_event(ps->lvx[2 * l], s);
@@ -1060,9 +1079,12 @@ void vcycle_t(Hier &h, double *x64, float *d32, const int *active, ProfSlot *ps)
         // F sweeps ping-pong between vy and vxn; the C sweep reads the last one
         T *bufs[2] = {(T *)L.vy, (T *)L.vxn};
         const bool split0 = bsr && h.split0 && std::is_same<T, float>::value;
+        const bool tp = prof && (int)ps->lvt.size() >= 4 * (l + 1);
+        if (tp) rec_event(ps->lvt[4 * l + 2], s);
         launch_pdl(k_prolong<T>, blocks_for((L.n + 3) / 4, BS), BS, s, L.n, L.cf, L.pmap, C.cf, (const T *)C.vF,
                    (const T *)C.vx, bufs[0], (bsr && !split0) ? nullptr : bufs[1], any);
         PR_LAUNCH();
+        if (tp) rec_event(ps->lvt[4 * l + 3], s);
         int cur = 0;
         if (split0) {
             // F sweeps over the F rows (the last one folds into x), C sweep over the C rows,
@@ -1239,6 +1261,22 @@ void level0_bytes(Hier &h) {
     h.bytes_relax0.assign(h.ndir, 0.0);
     h.bytes_res32.assign(h.ndir, 0.0);
     h.bytes_relaxc = 0;
+    h.bytes_xfer = 0;
+    {
+        // grid transfers: each restriction row reads its position (row index, entry
+        // count), its coarse point's fine row and value, writes its coarse value, and
+        // reads its entries (column + value); each prolongation reads the CF flag and P
+        // column of every non-coarsest fine row and writes its value (and, for C rows,
+        // the copy for the F sweeps).  Gathered values are taken as cached.
+        const double sT = h.prm.precision >= 1 ? 4.0 : 8.0;
+        for (size_t l = 0; l + 1 < h.lev.size(); ++l) {
+            const Level &L = h.lev[l];
+            if (L.nc <= 0) continue;
+            const double cb = L.sZ.col16 ? 2.0 : 4.0;
+            h.bytes_xfer += (double)L.nc * (12 + 2 * sT) + (double)L.nnzZ * (cb + sT);
+            h.bytes_xfer += (double)(L.nF + L.nC) * (5 + sT) + (double)L.nC * sT;
+        }
+    }
     // the iterate the level-0 relaxation folds into: FP64 x or a float pair (8 B
     // read + 8 B written per row), or in the inner correction the FP32 d (4 + 4)
     const double xfold = h.inner ? 8.0 : 16.0;
@@ -1349,6 +1387,8 @@ void prof_enable(Hier &h) {
         for (auto &e : ps.lv) PR_CUDA(cudaEventCreate(&e));
         ps.lvx.assign(2 * h.lev.size(), nullptr);
         for (auto &e : ps.lvx) PR_CUDA(cudaEventCreate(&e));
+        ps.lvt.assign(4 * h.lev.size(), nullptr);
+        for (auto &e : ps.lvt) PR_CUDA(cudaEventCreate(&e));
     }
     h.prof = true;
 }

@@ -1165,12 +1165,15 @@ __global__ void k_sell_fill(int npos, const int *prow, const int *plen, const in
 // 16-bit column offsets: an entry's column minus its row, when every stored entry
 // of a store fits (the relaxation stores of the coarse levels: their stencils stay
 // within a few mesh planes of the row); the padding slots are never read
+// offsets are taken from the row's own index, or (rowbase, the restriction's Z
+// rows) from the fine row of its coarse point
 __global__ void k_sell_off_check(int npos, const int *prow, const int *plen, const int *sptr, const int *scol,
-                                 int *bad) {
+                                 const int *rowbase, int *bad) {
     const int pos = blockIdx.x * blockDim.x + threadIdx.x;
     if (pos >= npos) return;
-    const int r = prow[pos];
-    if (r < 0) return;
+    const int q = prow[pos];
+    if (q < 0) return;
+    const int r = rowbase ? rowbase[q] : q;
     const int len = plen[pos], base = sptr[pos >> 5] + (pos & 31);
     for (int j = 0; j < len; ++j) {
         const int off = scol[base + 32 * j] - r;
@@ -1179,29 +1182,30 @@ __global__ void k_sell_off_check(int npos, const int *prow, const int *plen, con
 }
 
 __global__ void k_sell_to16(int npos, const int *prow, const int *plen, const int *sptr, const int *scol,
-                            short *col16) {
+                            const int *rowbase, short *col16) {
     const int pos = blockIdx.x * blockDim.x + threadIdx.x;
     if (pos >= npos) return;
-    const int r = prow[pos];
-    if (r < 0) return;
+    const int q = prow[pos];
+    if (q < 0) return;
+    const int r = rowbase ? rowbase[q] : q;
     const int len = plen[pos], base = sptr[pos >> 5] + (pos & 31);
     for (int j = 0; j < len; ++j) col16[base + 32 * j] = (short)(scol[base + 32 * j] - r);
 }
 
-void sell_compress_cols(Hier &h, Sell &S) {
+void sell_compress_cols(Hier &h, Sell &S, const int *rowbase = nullptr) {
     if (S.nrows <= 0 || !S.col) return;
     cudaStream_t s = h.stream;
     const int BS = 256;
     int *bad = dmalloc<int>(1, s);
     PR_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
-    k_sell_off_check<<<blocks_for(S.npos, BS), BS, 0, s>>>(S.npos, S.row, S.len, S.ptr, S.col, bad);
+    k_sell_off_check<<<blocks_for(S.npos, BS), BS, 0, s>>>(S.npos, S.row, S.len, S.ptr, S.col, rowbase, bad);
     PR_LAUNCH();
     int hb = 0;
     d2h(&hb, bad, 1, s);
     dfree(bad, s);
     if (hb) return;
     S.col16 = dmalloc<short>(std::max<long long>(S.nnz, 1), s);
-    k_sell_to16<<<blocks_for(S.npos, BS), BS, 0, s>>>(S.npos, S.row, S.len, S.ptr, S.col, S.col16);
+    k_sell_to16<<<blocks_for(S.npos, BS), BS, 0, s>>>(S.npos, S.row, S.len, S.ptr, S.col, rowbase, S.col16);
     PR_LAUNCH();
     dfree(S.col, s);
     S.col = nullptr;
@@ -1317,7 +1321,7 @@ void free_level(Level &L, cudaStream_t s) {
                     L.zrowptr, L.zcol, L.zval, L.d_row0, L.d_cseg_row0, L.d_cseg_n,
                     L.srow, L.sptr, L.scol, L.sval, L.d_cseg_s0,
                     L.sF.ptr, L.sF.row, L.sF.len, L.sF.col, L.sF.col16, L.sF.val, L.sC.ptr, L.sC.row, L.sC.len,
-                    L.sC.col, L.sC.col16, L.sC.val, L.sZ.ptr, L.sZ.row, L.sZ.len, L.sZ.col, L.sZ.val,
+                    L.sC.col, L.sC.col16, L.sC.val, L.sZ.ptr, L.sZ.row, L.sZ.len, L.sZ.col, L.sZ.col16, L.sZ.val,
                     L.sX.ptr, L.sX.row, L.sX.len, L.sX.col, L.sX.col16, L.sX.val, L.vb, L.vx, L.vxn, L.vy};
     for (void *p : ptrs) dfree(p, s);
     L = Level();
@@ -1706,7 +1710,10 @@ void build_hierarchy(Hier &h) {
     for (size_t l = 0; l < h.lev.size(); ++l) {
         Level &L = h.lev[l];
         build_split(h, L, !(l == 0 && h.bsr0));
-        if (L.nc > 0) build_sell(h, L.sZ, nullptr, L.nc, L.zrowptr, L.zcol, L.zval);
+        if (L.nc > 0) {
+            build_sell(h, L.sZ, nullptr, L.nc, L.zrowptr, L.zcol, L.zval);
+            sell_compress_cols(h, L.sZ, L.cpts);   // offsets from each coarse point's fine row
+        }
     }
     PR_CUDA(cudaStreamSynchronize(s));
 }

@@ -204,6 +204,14 @@ void account_cycle(Hier &h, const ProfSlot &ps, const std::vector<char> &part) {
             h.gb_relaxc += h.bytes_relaxc * 1e-9;
         }
     }
+    if (ps.lvt.size() >= 4 && h.lev.size() >= 2) {
+        double tx = 0;
+        for (size_t l = 0; l + 1 < h.lev.size() && 4 * l + 3 < ps.lvt.size(); ++l)
+            tx += elapsed_ms(ps.lvt[4 * l], ps.lvt[4 * l + 1]) + elapsed_ms(ps.lvt[4 * l + 2], ps.lvt[4 * l + 3]);
+        h.t_xfer += tx;
+        h.n_xfer += 1;
+        h.gb_xfer += h.bytes_xfer * 1e-9;
+    }
     if (ps.relax_timed) {
         h.t_relax0 += elapsed_ms(ps.relax0[0], ps.relax0[1]);
         h.n_relax0 += 1;
@@ -602,6 +610,8 @@ Hier::~Hier() {
             if (e) cudaEventDestroy(e);
         for (auto &e : ps.lvx)
             if (e) cudaEventDestroy(e);
+        for (auto &e : ps.lvt)
+            if (e) cudaEventDestroy(e);
     }
     if (stream) {
         for (auto &L : lev) free_level(L, stream);
@@ -701,22 +711,25 @@ void free_batch_ops(DirBatch &B) {
 // device-event kernel timings and algorithmic traffic taken from hierarchies
 struct KernelStats {
     double t_res0 = 0, t_relax0 = 0, gb_res0 = 0, gb_relax0 = 0, t_relaxc = 0, gb_relaxc = 0, t_res32 = 0,
-           gb_res32 = 0, t_lvl[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    long long n_res0 = 0, n_relax0 = 0, n_relaxc = 0, n_res32 = 0;
+           gb_res32 = 0, t_xfer = 0, gb_xfer = 0, t_lvl[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    long long n_res0 = 0, n_relax0 = 0, n_relaxc = 0, n_res32 = 0, n_xfer = 0;
     void take(Hier &h) {   // adds h's counters and clears them
         t_res0 += h.t_res0; t_relax0 += h.t_relax0; gb_res0 += h.gb_res0; gb_relax0 += h.gb_relax0;
         n_res0 += h.n_res0; n_relax0 += h.n_relax0;
         t_relaxc += h.t_relaxc; gb_relaxc += h.gb_relaxc; n_relaxc += h.n_relaxc;
         t_res32 += h.t_res32; gb_res32 += h.gb_res32; n_res32 += h.n_res32;
+        t_xfer += h.t_xfer; gb_xfer += h.gb_xfer; n_xfer += h.n_xfer;
         for (int k = 0; k < 8; ++k) { t_lvl[k] += h.t_relaxc_level[k]; h.t_relaxc_level[k] = 0; }
         h.t_res0 = h.t_relax0 = h.gb_res0 = h.gb_relax0 = h.t_relaxc = h.gb_relaxc = h.t_res32 = h.gb_res32 = 0;
-        h.n_res0 = h.n_relax0 = h.n_relaxc = h.n_res32 = 0;
+        h.t_xfer = h.gb_xfer = 0;
+        h.n_res0 = h.n_relax0 = h.n_relaxc = h.n_res32 = h.n_xfer = 0;
     }
     void add(const KernelStats &o) {
         t_res0 += o.t_res0; t_relax0 += o.t_relax0; gb_res0 += o.gb_res0; gb_relax0 += o.gb_relax0;
         t_relaxc += o.t_relaxc; gb_relaxc += o.gb_relaxc; t_res32 += o.t_res32; gb_res32 += o.gb_res32;
+        t_xfer += o.t_xfer; gb_xfer += o.gb_xfer;
         for (int k = 0; k < 8; ++k) t_lvl[k] += o.t_lvl[k];
-        n_res0 += o.n_res0; n_relax0 += o.n_relax0; n_relaxc += o.n_relaxc; n_res32 += o.n_res32;
+        n_res0 += o.n_res0; n_relax0 += o.n_relax0; n_relaxc += o.n_relaxc; n_res32 += o.n_res32; n_xfer += o.n_xfer;
     }
 };
 
@@ -1148,6 +1161,9 @@ void si_run(const pair_mesh &mesh, const pair_quad &quad, const double *sigma_t,
         info->outer_residuals = (int)outer_res;
         for (int k = 0; k < 8; ++k) info->t_relaxc_level_ms[k] = ks.t_lvl[k];
         info->timed_iters = timed_iters;
+        info->t_xfer_ms = ks.t_xfer;
+        info->n_xfer = (int)ks.n_xfer;
+        info->gb_xfer = ks.gb_xfer;
         for (int k = 0; k < 3; ++k) info->t_setup_phase_ms[k] = tph[k];
         info->t_setup_phase_ms[3] = t_setup - (tph[0] + tph[1] + tph[2]);
     }

@@ -111,7 +111,8 @@ class si_info(C.Structure):
                 ("gb_relax0", C.c_double), ("t_setup_phase_ms", C.c_double * 4), ("t_relaxc_ms", C.c_double),
                 ("n_relaxc", C.c_int), ("gb_relaxc", C.c_double), ("t_res32_ms", C.c_double),
                 ("n_res32", C.c_int), ("gb_res32", C.c_double), ("outer_residuals", C.c_int),
-                ("t_relaxc_level_ms", C.c_double * 8), ("timed_iters", C.c_int)]
+                ("t_relaxc_level_ms", C.c_double * 8), ("timed_iters", C.c_int),
+                ("t_xfer_ms", C.c_double), ("n_xfer", C.c_int), ("gb_xfer", C.c_double)]
 
 
 _lib = None
