@@ -227,6 +227,22 @@ def test_si_fp32_refined_matches_oracle(pair, precision):
     assert np.linalg.norm(phi - ref) <= 1e-7 * np.linalg.norm(ref)
 
 
+def test_fp32_cycles_reduce_error_like_fp64(pair):
+    """FP32 V-cycles (CF-split level-0 sweeps, FP32 inner residual) under FP64
+    refinement reduce the error like FP64 cycles: the same SI iterations, V-cycle
+    counts within 5%, phi within the FP32-refined tolerance of the FP64 path."""
+    prob = I.small_hex(12, order=4, seed=21, ratio=0.8)
+    si = dict(tol=1e-10, inner_tol=1e-9)
+    phi0, _, i0 = pair.si_solve_problem(prob, air=pair.default_air_params(precision=0),
+                                        si=pair.default_si_params(**si))
+    phi1, _, i1 = pair.si_solve_problem(prob, air=pair.default_air_params(precision=1),
+                                        si=pair.default_si_params(**si))
+    assert i1["si_iters"] == i0["si_iters"]
+    assert abs(i1["vcycles"] - i0["vcycles"]) <= 0.05 * i0["vcycles"], (i0["vcycles"], i1["vcycles"])
+    assert i1["max_inner_resid"] <= 1e-9
+    assert torch.linalg.norm(phi1 - phi0).item() <= 1e-7 * torch.linalg.norm(phi0).item()
+
+
 @pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-7)])
 def test_si_nair_filtered_matches_oracle(pair, precision, tol):
     """SI with nAIR of degree 1 and the R filter phi_R = 0.1 (the paper's

@@ -88,6 +88,42 @@ def test_scaled_operator_structure():
         assert np.all(cols // 8 <= i // 8)                      # all-positive direction: upwind = lower index
 
 
+def _face_node(d, o, t):
+    """Node of a Q1 hexahedron (a = ax + 2 ay + 4 az) on the face normal to axis d at
+    side o, face position t (t = t0 + 2 t1 over the two other axes in order)."""
+    return (o | (t << 1)) if d == 0 else (((t & 1) | (o << 1) | ((t >> 1) << 2)) if d == 1 else (t | (o << 2)))
+
+
+def test_hex_upwind_face_coupling_closed_form():
+    """Eq. weak_form_transport on the uniform Q1 mesh: the inflow face term couples
+    element K's node on its inflow face at face position u with the upwind
+    element's node at position t by -|Omega_d| int_F phi_u phi_t = -|Omega_d| (h/6)^2
+    c(u0, t0) c(u1, t1), c = 2 where the positions agree and 1 otherwise (the 1-D
+    mass [[2, 1], [1, 2]] h / 6 along each face axis), and K's other nodes are not
+    coupled to that neighbour."""
+    prob = I.small_hex(4, order=4, seed=3)
+    n, h = prob.n, 1.0 / prob.n
+    for m in (0, 7, 13, 22):
+        om = prob.omega[m]
+        rp, c, v = O.hex_assemble(n, om, prob.sigma_t, scaled=False)
+        A = sp.csr_matrix((v, c, rp), shape=(len(rp) - 1, len(rp) - 1)).todok()
+        for e in range(n ** 3):
+            idx = (e % n, (e // n) % n, e // (n * n))
+            for d in range(3):
+                sg = np.sign(om[d])
+                if not (idx[d] > 0 if sg > 0 else idx[d] < n - 1):
+                    continue
+                ep = e - n ** d if sg > 0 else e + n ** d
+                o = 1 if sg > 0 else 0   # the upwind element's face side
+                for t in range(4):
+                    b = 8 * ep + _face_node(d, o, t)
+                    for u in range(4):
+                        want = -abs(om[d]) * (h / 6) ** 2 * (2 if (u & 1) == (t & 1) else 1) * \
+                            (2 if (u >> 1) == (t >> 1) else 1)
+                        assert abs(A[8 * e + _face_node(d, 1 - o, u), b] - want) <= 1e-15 * abs(want)
+                        assert A[8 * e + _face_node(d, o, u), b] == 0.0
+
+
 def test_sweep_equals_dense_solve():
     n = 3
     rng = np.random.default_rng(5)
