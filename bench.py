@@ -49,11 +49,13 @@ WORKLOADS = {
                 "sigma_t~logU[0.1,100], sigma_s=0.95 sigma_t, q=1",
     "tet40_s8": "unit cube 40^3 cubes x 6 Kuhn tets jittered 0.2h (1,536,000 P1 DOFs/dir), S8 (80 dirs), sigma_t "
                 "checkerboard {1,100} over 4^3 regions, sigma_s=0.9 sigma_t, q=1 where sigma_t=1, distance-2 AIR",
+    "tet16_s8": "the tet40_s8 construction on 16^3 cubes x 6 tets (98,304 P1 DOFs/dir), S8 (80 dirs), distance-2 "
+                "AIR (a small case of the same setup kernels, for profiling)",
 }
 # workloads whose scattering ratio needs hundreds of SI iterations: a step runs a
 # fixed number of iterations instead of the whole solve
-FIXED_SI = {"hex64_s8": 2, "tet40_s8": 2}
-DISTANCE = {"tet40_s8": 2}
+FIXED_SI = {"hex64_s8": 2, "tet40_s8": 2, "tet16_s8": 2}
+DISTANCE = {"tet40_s8": 2, "tet16_s8": 2}
 
 
 def dist_env():

@@ -596,13 +596,6 @@ __global__ void k_lair_solve(int nwork, const int *worklist, const int *cpts, co
                     }
             }
             __syncwarp();
-            // the pivot's reciprocal: one lane of the group divides, the others take it
-            double rd = 0.0;
-            if (act && g == 0) {
-                rd = pivot_recip(M[k * np + k]);
-                rv[k] = rd;
-            }
-            rd = __shfl_sync(FULL, rd, q * G);
             // multipliers, and the list of rows whose multiplier is not zero: a zero
             // multiplier's update adds exact zeros, so those rows are skipped, as in the
             // reference LU (in the local systems of these operators most multipliers are
@@ -613,12 +606,19 @@ __global__ void k_lair_solve(int nwork, const int *worklist, const int *cpts, co
             int m = 0;
             if (!any_nz) {
                 // only zeros below: their multipliers are those zeros, with the sign
-                // flipped under a negative pivot
-                if (act && __double_as_longlong(rd) < 0)
-                    for (int r = k + 1 + g; r < np; r += G) M[r * np + k] = zero_times(M[r * np + k], rd);
+                // flipped under a negative pivot (the sign of 1 / pivot, so no division
+                // here: the reciprocals of such pivots are taken together after the
+                // elimination)
+                const double pk = act ? M[k * np + k] : 0.0;   // k < np only for an active group
+                if (act && __double_as_longlong(pk) < 0)
+                    for (int r = k + 1 + g; r < np; r += G) M[r * np + k] = zero_times(M[r * np + k], pk);
                 __syncwarp();
                 continue;
             }
+            // the pivot's reciprocal: one lane of the group divides, the others take it
+            double rd = 0.0;
+            if (act && g == 0) rd = pivot_recip(M[k * np + k]);
+            rd = __shfl_sync(FULL, rd, q * G);
             for (int j0 = 0; j0 < kmax - k - 1; j0 += G) {
                 const int r = k + 1 + j0 + g;
                 bool nzr = false;
@@ -677,6 +677,10 @@ __global__ void k_lair_solve(int nwork, const int *worklist, const int *cpts, co
             __syncwarp();
         }
         bool solve = has && !singular && np > 0;
+        // every pivot's reciprocal for the back substitution, G at a time (the same
+        // values the elimination took for its multipliers)
+        if (solve)
+            for (int k = g; k < np; k += G) rv[k] = pivot_recip(M[k * np + k]);
         if (solve && g == 0)
             for (int k = 0; k < np; ++k)
                 if (piv[k] != k) { double t = y[k]; y[k] = y[piv[k]]; y[piv[k]] = t; }

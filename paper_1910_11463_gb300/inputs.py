@@ -188,6 +188,9 @@ def config(name: str) -> HexProblem:
                   sigma_s = 0.7 sigma_t, q = 1 in the central 8^3 block.
     hex64_s8    : 64^3 hex (2,097,152 DOFs/direction), S8 (80 directions),
                   sigma_t ~ log-U[0.1, 100], sigma_s = 0.95 sigma_t, q = 1.
+    tet40_s8    : 40^3 cubes x 6 jittered Kuhn tets (1,536,000 DOFs/direction), S8,
+                  sigma_t checkerboard {1, 100} over 4^3 regions (tet_checkerboard).
+    tet16_s8    : the same construction on 16^3 cubes (98,304 DOFs/direction).
     """
     if name == "hex8_s2":
         return hex_uniform(8, 2, 1.0, 0.5, 1.0, name)
@@ -199,6 +202,8 @@ def config(name: str) -> HexProblem:
         return hex_random(64, 8, 0.95, seed=1, lo=0.1, hi=100.0, log_uniform=True, name=name)
     if name == "tet40_s8":
         return tet_checkerboard(40, 8, 4, 0.9, 0.2, 1, name)
+    if name == "tet16_s8":
+        return tet_checkerboard(16, 8, 4, 0.9, 0.2, 1, name)
     raise KeyError(name)
 
 
