@@ -173,6 +173,35 @@ def test_vcycle_fp64_grid_coarsest_matches_oracle(pair, sweeps):
         assert np.linalg.norm(xg[sl] - xo) <= 1e-12 * np.linalg.norm(xo), m
 
 
+def test_single_level_grid_coarsest_equals_sweep(pair):
+    """A single-level batch (max_coarse above every matrix) whose 512-row matrices are
+    too large for the one-CTA shared-memory sweeps: level 0 is the coarsest and is
+    swept grid-wide on its SELL copy.  With 3n - 2 Jacobi sweeps the cycle is the exact
+    solve (the scaled operator is I plus a nilpotent part of index 3n - 2); with 3n - 3
+    it is not."""
+    n = 4
+    om, _ = I.level_symmetric(2)
+    st = 0.5 + np.random.default_rng(0).random(n ** 3)
+    dirs = (3, 6)
+    mats_o = [O.hex_assemble(n, om[m], st) for m in dirs]
+    mats_g = [_gpu_csr(pair, n, om[m], st) for m in dirs]
+    N = 8 * n ** 3
+    b = np.random.default_rng(1).random(len(dirs) * N)
+    for cs, exact in ((3 * n - 3, False), (3 * n - 2, True)):
+        H_g = pair.Hierarchy(mats_g, pair.default_air_params(precision=0, max_coarse=10 ** 6, coarse_sweeps=cs))
+        for k in range(len(dirs)):
+            assert H_g.nlevels(k) == 1
+            assert _coarsest_smem_bytes(H_g.level(k, 0), 8) > 40 * 1024
+        xg = torch.zeros(len(dirs) * N, dtype=torch.float64, device="cuda")
+        H_g.vcycle(torch.as_tensor(b, device="cuda"), xg)
+        xg = _cpu(xg)
+        for k in range(len(dirs)):
+            sl = slice(k * N, (k + 1) * N)
+            xs, _ = O.sweep(*mats_o[k], b[sl])
+            err = np.linalg.norm(xg[sl] - xs) / np.linalg.norm(xs)
+            assert (err < 1e-13) if exact else (err > 1e-4), (cs, k, err)
+
+
 @pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-10)])
 def test_air_solve_equals_sweep(pair, precision, tol):
     prob = I.small_hex(7, order=2, seed=6)

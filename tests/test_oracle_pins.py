@@ -124,6 +124,25 @@ def test_hex_upwind_face_coupling_closed_form():
                         assert A[8 * e + _face_node(d, o, u), b] == 0.0
 
 
+def test_single_level_jacobi_is_exact_after_the_wavefront_count():
+    """Coarsest-level relaxation (pointwise Jacobi from zero, reading 9) on a
+    single-level hierarchy: the scaled hex operator is I + N with N strictly lower
+    triangular in upwind element order and nilpotent of index 3n - 2 (the number of
+    upwind wavefronts of the n^3 mesh), so 3n - 2 sweeps give the exact solution (the
+    sweep) and 3n - 3 do not."""
+    n = 4
+    om = I.level_symmetric(2)[0][3]
+    st = 0.5 + np.random.default_rng(0).random(n ** 3)
+    r, c, v = O.hex_assemble(n, om, st)
+    b = np.random.default_rng(1).random(8 * n ** 3)
+    xs, _ = O.sweep(r, c, v, b)
+    for cs, exact in ((3 * n - 3, False), (3 * n - 2, True)):
+        H = O.Hierarchy(r, c, v, O.default_params(max_coarse=10 ** 6, coarse_sweeps=cs))
+        assert H.nlev == 1
+        err = np.linalg.norm(H.vcycle(b, np.zeros_like(b)) - xs) / np.linalg.norm(xs)
+        assert (err < 1e-14) if exact else (err > 1e-4), (cs, err)
+
+
 def test_sweep_equals_dense_solve():
     n = 3
     rng = np.random.default_rng(5)
