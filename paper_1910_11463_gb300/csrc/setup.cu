@@ -1536,11 +1536,19 @@ void build_hierarchy(Hier &h) {
                 PR_LAUNCH();
             };
             const int cls_n[LAIR_CLASSES] = {4, 6, 8, 12, 16, 24, 32, 48, 64, 0};
+            int smem_optin = 0;
+            {
+                int dev = 0;
+                PR_CUDA(cudaGetDevice(&dev));
+                PR_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+            }
             auto warp_bin = [&](int c, auto kern, int G) {
                 if (!hc[c]) return;
                 const int nm = cls_n[c], spw = 32 / G;
                 size_t per = ((size_t)nm * nm + 4 * nm) * sizeof(double) * spw;   // per warp
-                int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (200 * 1024) / per));
+                // as many warps per block as the shared memory of one block holds (the
+                // solves are latency- and FP64-bound, so resident warps decide)
+                int wpb = (int)std::max<size_t>(1, std::min<size_t>(32, (size_t)smem_optin / per));
                 size_t sm = per * wpb;
                 unsigned grid = std::min<unsigned>(blocks_for(hc[c], wpb * spw), 152u * 64u);
                 if (sm > 48 * 1024) allow_max_dyn_smem(kern);
