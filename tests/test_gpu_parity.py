@@ -303,12 +303,14 @@ def test_si_inexact_fixed_cycles_matches_oracle(pair, precision, tol, cycles):
     """Sec. 3 inexact solves: l V-cycles from zero per direction per SI iteration (a
     fixed approximate inverse) against the oracle with the same l.  With FP32 cycles
     the approximate inverse carries FP32 rounding (~1e-7 relative per application),
-    so the SI change stalls near 1e-10 and the SI tolerance is 1e-9 there."""
+    so the SI change stalls at that noise, between 1e-10 and 1.1e-9 as measured (the
+    FP32 sums' order follows the lanes per row the autotuner picks by timing), and
+    the SI tolerance is 5e-9 there."""
     prob = I.small_hex(8, order=4, seed=13, ratio=0.8)
     ref, _, info_o = O.si_hex(prob, tol=1e-11, inner_cycles=cycles)
     assert info_o["rc"] == 0
     phi, _, info = pair.si_solve_problem(prob, air=pair.default_air_params(precision=precision),
-                                         si=pair.default_si_params(tol=1e-11 if precision == 0 else 1e-9,
+                                         si=pair.default_si_params(tol=1e-11 if precision == 0 else 5e-9,
                                                                    inner_cycles=cycles))
     assert info["vcycles"] == cycles * prob.M * info["si_iters"]
     assert np.linalg.norm(_cpu(phi) - ref) <= tol * np.linalg.norm(ref)
