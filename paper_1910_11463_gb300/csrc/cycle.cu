@@ -2,8 +2,7 @@
 // Jacobi).  Correction form with zero initial guess on every level:
 //   level 0: r = b - A x (FP64, cast to the cycle precision T), per-matrix ||r||
 //   down:    b_{l+1} = R_l b_l, R row = [Z_i, 1] (restriction of the residual)
-//   coarsest: coarse_sweeps Jacobi sweeps from 0 (one CTA per matrix segment in
-//            shared memory, or grid-wide on a SELL copy of large coarsest levels)
+//   coarsest: coarse_sweeps Jacobi sweeps from 0 (one CTA per matrix segment)
 //   up:      y_l = P x_{l+1} (one-point: y_i = x_{l+1}[pmap(i)])
 //            F rows: xn = y + D^{-1}(b - A y);  C rows: xn = y
 //            C rows: x = xn + D^{-1}(b - A xn); F rows: x = xn   (level 0: x_FP64 += x)
