@@ -1549,6 +1549,9 @@ void build_hierarchy(Hier &h) {
                 // as many warps per block as the shared memory of one block holds (the
                 // solves are latency- and FP64-bound, so resident warps decide)
                 int wpb = (int)std::max<size_t>(1, std::min<size_t>(32, (size_t)smem_optin / per));
+                cudaFuncAttributes fa;   // and no more threads than its registers allow
+                PR_CUDA(cudaFuncGetAttributes(&fa, kern));
+                wpb = std::max(1, std::min(wpb, fa.maxThreadsPerBlock / 32));
                 size_t sm = per * wpb;
                 unsigned grid = std::min<unsigned>(blocks_for(hc[c], wpb * spw), 152u * 64u);
                 if (sm > 48 * 1024) allow_max_dyn_smem(kern);
