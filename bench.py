@@ -56,6 +56,11 @@ WORKLOADS = {
 # fixed number of iterations instead of the whole solve
 FIXED_SI = {"hex64_s8": 2, "tet40_s8": 2, "tet16_s8": 2}
 DISTANCE = {"tet40_s8": 2, "tet16_s8": 2}
+# coarsest level (max_coarse rows, Jacobi sweeps) of the large workloads: the first
+# level with at most 40,000 rows per direction, 3 sweeps (V-cycle counts unchanged
+# against the library's 100 rows / 20 sweeps, measured with the oracle); the small
+# meshes keep the library's, which a 40,000-row bound would reduce to one level
+COARSEST = {"hex32_s4": (40000, 3), "hex64_s8": (40000, 3), "tet40_s8": (40000, 3)}
 
 
 def dist_env():
@@ -243,8 +248,8 @@ def bench_config(args, world):
                      "time (setup included); solve_only_value excludes the setup"),
             "air": {"R": "nAIR degree 1" if args.nair else f"lAIR distance {args.distance}",
                     "theta": args.theta, "eps_R": 0.01, "phi_R": args.phi_R, "phi_A": args.phi_A,
-                    "relax": "F-F-C Jacobi", "coarsening": "PMIS", "max_coarse": args.max_coarse,
-                    "coarse_sweeps": args.coarse_sweeps},
+                    "relax": "F-F-C Jacobi", "coarsening": "PMIS", "max_coarse": coarsest(args)[0],
+                    "coarse_sweeps": coarsest(args)[1]},
             "l2": "working set per step >> 129 MB L2 (no flush needed)",
             "parallelism": (f"angular decomposition over {world} GPUs (directions split, scalar flux all-reduced "
                             "every SI iteration)") if world > 1 else (
@@ -256,11 +261,21 @@ def bench_config(args, world):
                           "FP32 hierarchy/V-cycle, FP64 refinement" if args.precision else "FP64")}
 
 
-def air_settings(args, distance=None):
-    """The AIR parameters of the timed runs (both arms)."""
+def coarsest(args, name=None):
+    """(max_coarse, coarse_sweeps) of a workload: the command line's, else COARSEST's,
+    else the library's defaults."""
+    mc, cs = COARSEST.get(name or args.config, (100, 20))
+    return (mc if args.max_coarse is None else args.max_coarse,
+            cs if args.coarse_sweeps is None else args.coarse_sweeps)
+
+
+def air_settings(args, distance=None, name=None):
+    """The AIR parameters of the timed runs (both arms) of a workload (default: the
+    command line's)."""
+    mc, cs = coarsest(args, name)
     return dict(theta=args.theta, phi_R=args.phi_R, phi_A=args.phi_A,
                 distance=args.distance if distance is None else distance, nair=args.nair,
-                max_coarse=args.max_coarse, coarse_sweeps=args.coarse_sweeps)
+                max_coarse=mc, coarse_sweeps=cs)
 
 
 def run_reference(args):
@@ -352,7 +367,7 @@ def measure_workload(name, args, pair, I, torch, steps=2, warmup=1, fp64=False):
     geom = pair.TetMesh(prob.verts, prob.tets, prob.nbr) if tet else prob.n
     fixed = FIXED_SI.get(name, 0)
     distance = DISTANCE.get(name, 1)
-    kw = air_settings(args, distance)
+    kw = air_settings(args, distance, name)
     air = pair.default_air_params(precision=args.precision, **kw)
     si = (pair.default_si_params(tol=1e-8, max_iters=fixed, fixed_iters=1, inner_tol=1e-8, inner_maxit=200,
                                  use_graphs=args.graphs, concurrent=args.concurrent,
@@ -392,8 +407,8 @@ def measure_workload(name, args, pair, I, torch, steps=2, warmup=1, fp64=False):
                       "one complete SI solve from phi=0") + " (every direction from psi=0 to a 1e-8 relative "
                      "residual each iteration); value = DOF*dir*iterations/step time",
              "air": {"R": "nAIR degree 1" if args.nair else f"lAIR distance {distance}", "theta": args.theta,
-                     "eps_R": 0.01, "phi_A": args.phi_A, "phi_R": args.phi_R, "max_coarse": args.max_coarse,
-                     "coarse_sweeps": args.coarse_sweeps},
+                     "eps_R": 0.01, "phi_A": args.phi_A, "phi_R": args.phi_R, "max_coarse": kw["max_coarse"],
+                     "coarse_sweeps": kw["coarse_sweeps"]},
              "si_iterations": iters, "setup_ms": t_setup, "solve_ms": t_solve,
              "solve_only_value": N * M * iters / (t_solve * 1e-3) if t_solve > 0 else None,
              "setup_phase_ms": dict(zip(("strength+pmis", "p+lair", "rap", "assembly+other"),
@@ -733,10 +748,12 @@ def main():
     ap.add_argument("--theta", type=float, default=0.5)
     ap.add_argument("--phi-R", dest="phi_R", type=float, default=0.0)
     ap.add_argument("--phi-A", dest="phi_A", type=float, default=0.05)
-    ap.add_argument("--max-coarse", dest="max_coarse", type=int, default=40000,
-                    help="a level with at most this many rows per direction is the coarsest (library default 100)")
-    ap.add_argument("--coarse-sweeps", dest="coarse_sweeps", type=int, default=3,
-                    help="Jacobi sweeps from zero on the coarsest level (library default 20)")
+    ap.add_argument("--max-coarse", dest="max_coarse", type=int, default=None,
+                    help="a level with at most this many rows per direction is the coarsest (default: 40000 for "
+                         "hex32_s4, hex64_s8 and tet40_s8, else the library's 100)")
+    ap.add_argument("--coarse-sweeps", dest="coarse_sweeps", type=int, default=None,
+                    help="Jacobi sweeps from zero on the coarsest level (default: 3 for those workloads, else the "
+                         "library's 20)")
     ap.add_argument("--nair", type=int, default=0, choices=[0, 1],
                     help="1: R from degree-1 nAIR (Neumann series) instead of lAIR local solves")
     ap.add_argument("--distance", type=int, default=None, choices=[1, 2],
